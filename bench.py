@@ -1,0 +1,324 @@
+"""Benchmark of the pseudo-spectral NS + Cahn-Hilliard channel time step.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Prints ONE JSON line (rank 0).  A step is one full time step (Sec. 2.2 steps i)-v)) of one
+channel: Chebyshev-tau z-line kernel, y backward pass, fused x-line kernel, y forward pass.
+Default workload: the 128 x 128 x 129 FP64 channel (Re_tau = 150, 8 drops).  Points = nx ny nz
+(unpadded); the metric is Mpoints * steps / s of the whole job.
+
+* value: device time of K steps on the handle's stream (CUDA events, barrier + synchronize on
+  both sides, max over ranks); the per-step working set (~0.8 GB at 128^3) is larger than L2.
+* e2e: the user path through the C ABI with host buffers: upload of u, v, w, phi from pinned host
+  memory, K steps, download of u, v, w, phi, timed on the host clock after a synchronize.
+* roofline: the dominant kernel of the step, its algorithmic FLOPs (or bytes) per launch over
+  its CUDA-event launch time, against the float64 ALU peak (no float64 figure is in the
+  measured-peaks file: 152 SMs x 2.07 GHz x 4 flop/clk/SM = 1.26 TFLOP/s nominal) or the
+  measured HBM copy bandwidth.
+* cpu_baseline: the CPU oracle on a bounded sample of the same workload (rank 0, N = 1).
+* N > 1: N independent replicas, one per rank ("replicas only": the single-grid step does not
+  shard without all-to-all transposes); value = all ranks' points * steps / max time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time steps/s & Mpoints·step/s per grid; % HBM roofline; mixed vs FP64"
+UNIT = "Mpoints*step/s"
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 DFMA per clock per SM (recipe: 1.25 TF/s)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6785.9), "measured"
+    return 6800.0, "fallback"
+
+
+# ---- algorithmic work per launch (see the module docstring of DESIGN notes in this file) ----
+def fft_flops(n):
+    """5 n log2 n: the conventional flop count of a complex FFT of length n."""
+    return 5.0 * n * math.log2(n)
+
+
+def kernel_work(w, prec):
+    """Algorithmic flops and bytes per launch of the four step kernels."""
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    Mx, Px, Py, N = nx // 2, 3 * nx // 2, 3 * ny // 2, nz - 1
+    b = 16 if prec == 0 else 8
+    S = Mx * ny * nz           # spectral points per field
+    Y = Mx * Py * nz           # y-padded points per field
+    lines = Mx * ny
+    # z-line: 17 complex DCT-I (2N-point complex FFT each), ~12 real tau solves (~10 flop/row),
+    # assembly and derivatives (~200 flop per coefficient)
+    z_fl = lines * (17 * fft_flops(2 * N) + 12 * 10 * nz + 200 * nz)
+    z_by = S * 16 * 12 + S * b * 17    # state+history in/out (fp64) + 10 NL in + 7 fields out
+    yb_fl = 7 * Mx * nz * fft_flops(Py)
+    yb_by = 7 * (S + Y) * b
+    x_fl = Py * nz * (17 * 0.5 * fft_flops(Px) + 60 * Px)   # packed real FFTs + products
+    x_by = 17 * Y * b
+    yf_fl = 10 * Mx * nz * fft_flops(Py)
+    yf_by = 10 * (S + Y) * b
+    return {"zline": (z_fl, z_by), "ybwd": (yb_fl, yb_by), "xline": (x_fl, x_by),
+            "yfwd": (yf_fl, yf_by)}
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(w, nsample_lines=None, steps=1):
+    """Time the CPU oracle on one step of the workload: the full non-linear evaluation plus the
+    implicit solves of a sample of wavenumber lines, scaled to all lines."""
+    import numpy as np
+    from oracle.channel import Channel, Params
+    from paper_2406_01322_gb300 import inputs
+    p = Params(nx=w["nx"], ny=w["ny"], nz=w["nz"], re_tau=w["re_tau"], we=w["we"], ch=w["ch"],
+               pe=w["pe"], dt=w["dt"])
+    c = Channel(p)
+    c.set_fields(*inputs.initial_fields(**w))
+    lines = c.all_lines()
+    if nsample_lines is None or nsample_lines >= len(lines):
+        sample = lines
+    else:
+        rng = np.random.default_rng(0)
+        idx = rng.choice(len(lines), size=nsample_lines, replace=False)
+        sample = [lines[i] for i in sorted(idx)]
+    total = 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        nl = c.nonlinear_spectral()
+        h = c.assemble(nl)
+        prev = h if c.hist is None else c.hist
+        H = tuple(1.5 * a - 0.5 * b for a, b in zip(h, prev))
+        r = c.rhs(H)
+        t1 = time.perf_counter()
+        for (j, m) in sample:
+            c.solve_line(j, m, r[0][:, j, m], r[1][:, j, m], r[2][:, j, m])
+        t2 = time.perf_counter()
+        total += (t1 - t0) + (t2 - t1) * len(lines) / len(sample)
+    pts = w["nx"] * w["ny"] * w["nz"]
+    return pts * steps / total / 1e6, total / steps, len(sample), len(lines)
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count()
+    nsample = max(64, (w["nx"] // 2) * w["ny"] // 64)
+    if args.warmup:
+        oracle_sample(w, nsample_lines=8, steps=1)
+    val, t_step, ns, nl = oracle_sample(w, nsample_lines=nsample, steps=max(1, args.steps))
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]],
+                      "precision": "fp64"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"full non-linear evaluation + implicit solves of {ns} of "
+                                      f"{nl} wavenumber lines per step, solve time scaled to "
+                                      f"all lines; numpy FP64 oracle, {args.steps} step(s)"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="channel_128x128x129")
+    ap.add_argument("--precision", type=int, default=None, help="0 fp64, 1 mixed")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    from paper_2406_01322_gb300 import inputs
+    w = dict(inputs.WORKLOADS[args.workload])
+    prec = w["precision"] if args.precision is None else args.precision
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2406_01322_gb300 import build
+    if rank == 0:
+        build.build_library()
+    if world > 1:
+        dist.barrier()
+    from paper_2406_01322_gb300 import binding
+
+    fields = inputs.initial_fields(**dict(w, seed=w["seed"] + rank))
+    kw = dict(re_tau=w["re_tau"], we=w["we"], ch=w["ch"], pe=w["pe"], dt=w["dt"])
+    g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=prec, device=f"cuda:{local}", **kw)
+    g.set_fields(*[torch.from_numpy(f) for f in fields])
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed region
+    barrier()
+    with ClockSampler(local) as clk:
+        tot_ms, kms = g.step_timed(args.steps)
+    barrier()
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    pts = w["nx"] * w["ny"] * w["nz"]
+    value = world * pts * args.steps / (tot_ms * 1e-3) / 1e6
+    ms_step = tot_ms / args.steps
+
+    # ---- e2e through the C ABI with host buffers
+    host = [torch.from_numpy(f).pin_memory() for f in fields]
+    outs = [torch.empty_like(h).pin_memory() for h in host]
+    barrier()
+    t0 = time.perf_counter()
+    g.set_fields_host(*host)
+    g.step(args.steps)
+    g.get_fields_host(outs)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = world * pts * args.steps / e2e_s / 1e6
+    nbytes = 4 * pts * 8
+
+    # ---- roofline of the dominant kernel
+    names = ["zline", "ybwd", "xline", "yfwd"]
+    work = kernel_work(w, prec)
+    k = max(range(4), key=lambda i: kms[i])
+    name = names[k]
+    per_launch_ms = kms[k] / args.steps
+    fl, by = work[name]
+    hbm, hbm_kind = peaks()
+    fp64_like = (prec == 0) or name == "zline"
+    if fp64_like:
+        ach = fl / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": name,
+                "peak_kind": "float64 FMA pipe: 152 SMs x 2.07 GHz x 4 flop/clk (nominal)"}
+    else:
+        ach = by / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": name, "peak_kind": f"{hbm_kind} copy bandwidth"}
+    roof["kernel_share"] = {n: kms[i] / sum(kms) for i, n in enumerate(names)}
+    roof["kernel_ms_per_step"] = {n: kms[i] / args.steps for i, n in enumerate(names)}
+    roof["hbm_frac_step"] = (sum(v[1] for v in work.values()) / (ms_step * 1e-3) / 1e9) / hbm
+
+    if rank != 0:
+        g.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "steps_per_s": 1e3 / ms_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if prec == 0 else "f32 transforms/products + f64 solves",
+           "data": "synthetic",
+           "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]],
+                      "precision": "fp64" if prec == 0 else "mixed",
+                      "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "step working set larger than L2 (no flush)"},
+           "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes / args.steps,
+                   "d2h_bytes_per_step": nbytes / args.steps,
+                   "note": "set_fields_host + K steps + get_fields_host per job, bytes / K"},
+           "gpu_launches": g.launches_per_step() * args.steps,
+           "roofline": roof,
+           "clocks": clk.summary()}
+    g.close()
+    if world == 1 and not args.no_cpu_baseline:
+        nsample = max(64, (w["nx"] // 2) * w["ny"] // 64)
+        val, t_step, ns, nl = oracle_sample(w, nsample_lines=nsample, steps=1)
+        out["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": f"1 step: full non-linear evaluation + implicit solves "
+                                         f"of {ns} of {nl} lines, solve time scaled to all lines"}
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * ch_flow.h - C ABI of the GB300 pseudo-spectral channel solver.
+ *
+ * The library advances the coupled incompressible Navier-Stokes + Cahn-Hilliard (phase-field)
+ * equations in a plane channel, x, y periodic, walls at z = +-1, exactly as stated in Roccon,
+ * "A GPU-ready pseudo-spectral method for direct numerical simulations of multiphase turbulence"
+ * (arXiv:2406.01322):
+ *   - Sec. 2.1.1, Eq. (CHE) and the chemical potential: Cahn-Hilliard with mobility 1/Pe;
+ *   - Sec. 2.1.2, Eqs. (cont), (NSE), (kort): NS with the Korteweg capillary stress;
+ *   - Sec. 2.2, Eqs. (omegaz), (ww), (omegadef), (phisplit): wall-normal velocity-vorticity
+ *     formulation, split CH operator, Fourier x Fourier x Chebyshev discretisation (3/2 rule in
+ *     x and y), AB2 on non-linear terms, Crank-Nicolson on NS linear terms, implicit Euler on CH
+ *     linear terms, step sequence i)-v);
+ *   - Sec. 3.2.1: Chebyshev transform as a DCT-I; Sec. 3.2.2: batched tridiagonal (tau)
+ *     Helmholtz solves per (kx, ky).
+ * Every step of the time step runs in this library's own sm_103a CUDA kernels.
+ *
+ * Conventions
+ *   Physical fields: float64, C order (nz, ny, nx), x_i = i lx/nx, y_j = j ly/ny,
+ *     z_k = cos(pi k/(nz-1)) (k = 0 is the top wall z = +1).
+ *   Spectral fields: complex float64 stored as interleaved (re, im) pairs, layout
+ *     [mx][j][n] (n fastest): mx = 0..nx/2-1, j = 0..ny-1 in FFT order (my = j for j < ny/2,
+ *     my = j - ny for j > ny/2; j = ny/2 is the y Nyquist row and is kept zero),
+ *     n = 0..nz-1 the Chebyshev index.  Coefficient of T_n(z) exp(i(kx x + ky y)) with
+ *     kx = 2 pi mx / lx, ky = 2 pi my / ly; forward transforms are normalised by 1/(nx ny).
+ *   Pointers: every field pointer passed to a ch_* call is DEVICE memory of the current CUDA
+ *     device unless the function name ends in _host (then it is host memory, pinned or not).
+ *     The caller owns every buffer it passes; the library owns its internal buffers, obtained
+ *     through the allocator callbacks given to ch_init_grid (cudaMalloc when they are NULL).
+ *   Streams: all work is enqueued on the stream given to ch_init_grid (or ch_set_stream);
+ *     calls return once the work is enqueued unless stated otherwise.
+ *   Errors: every call returns CH_OK (0) or a negative CH_ERR_* code; no exception or abort
+ *     crosses the ABI.  A handle is not thread-safe; use one handle per stream.
+ */
+#ifndef CH_FLOW_H
+#define CH_FLOW_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CH_OK 0
+#define CH_ERR_ARG (-1)      /* null pointer, non-positive dt, bad enum value            */
+#define CH_ERR_SIZE (-2)     /* nx, ny not even and {2,3}-smooth, nz-1 not {2,3}-smooth   */
+#define CH_ERR_ALLOC (-3)    /* allocator callback or cudaMalloc returned NULL / failed   */
+#define CH_ERR_CUDA (-4)     /* a CUDA runtime call or kernel launch failed               */
+#define CH_ERR_DIVERGED (-5) /* diagnostics found NaN/Inf                                 */
+#define CH_ERR_TIMEOUT (-6)  /* reserved: bounded device-side wait gave up                */
+#define CH_ERR_STATE (-7)    /* call out of order, e.g. ch_step before ch_set_fields      */
+
+#define CH_PREC_FP64 0  /* every stage in float64                                         */
+#define CH_PREC_MIXED 1 /* x/y transforms and physical-space products in float32; the
+                           Chebyshev transform, tau solves, state and mass stay float64      */
+
+typedef struct ch_grid ch_grid; /* opaque, owned by the library */
+
+typedef struct {
+  int nx, ny, nz;     /* collocation points; nx, ny even with nx/2, ny/2 and 3nx/2, 3ny/2
+                         {2,3}-smooth (radix 2, 3, 4 FFTs); nz - 1 even, {2,3}-smooth, >= 4 */
+  double lx, ly;      /* box lengths in x, y (walls at z = +-1, half height h = 1)           */
+  double re_tau;      /* friction Reynolds number, Eq. (Re)                                */
+  double we;          /* Weber number, Eq. (We)                                            */
+  double ch;          /* Cahn number (interface thickness)                                 */
+  double pe;          /* Peclet number                                                     */
+  double dt;          /* time step (> 0)                                                   */
+  double gx, gy;      /* mean pressure gradient -dp/dx, -dp/dy driving the mean flow       */
+  int precision;      /* CH_PREC_FP64 or CH_PREC_MIXED                                     */
+  int dealias_z;      /* must be 0: no padding of the Chebyshev direction                  */
+  int bc;             /* must be 0: no-slip walls for velocity, no-flux for phi            */
+} ch_params;
+
+typedef void* (*ch_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*ch_free_fn)(void* ptr, void* ctx);
+
+typedef struct {
+  double t;           /* simulated time                                                    */
+  long long step;     /* number of steps taken since ch_set_fields / ch_set_state          */
+  double mass;        /* integral of phi, exact Clenshaw-Curtis sum of its (0,0) line      */
+  double kinetic;     /* 1/2 integral |u|^2 (uniform x,y weights, Clenshaw-Curtis in z)    */
+  double grad2;       /* integral |grad phi|^2 (interfacial area measure)                  */
+  double free_energy; /* integral 1/4 (phi^2-1)^2 + Ch^2/2 |grad phi|^2, Sec. 2.1.1         */
+  double cfl;         /* dt max(|u|/dx + |v|/dy + |w|/dz_k)                                */
+  double max_phi;     /* max |phi| on the grid                                             */
+  int nan;            /* 1 if any u, v, w, phi sample is NaN or Inf                        */
+} ch_diag;
+
+/* Create a solver for one channel.  Validates sizes (CH_ERR_SIZE) and parameters (CH_ERR_ARG),
+ * allocates every internal buffer through alloc/free (or cudaMalloc/cudaFree when alloc is
+ * NULL), builds FFT plans and twiddle tables.  stream is a cudaStream_t (NULL = default
+ * stream).  On success *out receives the handle.  Synchronous. */
+int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void* alloc_ctx,
+                 void* stream, ch_grid** out);
+
+/* Replace the stream used by every later call. */
+int ch_set_stream(ch_grid* g, void* stream);
+
+/* Step i) of Sec. 2.2: physical u, v, w, phi (device, (nz,ny,nx) float64) -> spectral state
+ * (omega_z = dv/dx - du/dy, w, mean flow, phi; Eq. (omegadef)).  Modes that the grid cannot hold
+ * (x and y Nyquist) are dropped and a non-solenoidal velocity is projected.  Resets the
+ * Adams-Bashforth history (the next step is forward Euler on the non-linear terms), t and step,
+ * and evaluates the non-linear terms of the new state. */
+int ch_set_fields(ch_grid* g, const double* u, const double* v, const double* w, const double* phi);
+
+/* As ch_set_fields with HOST input arrays (copied to the device on the handle's stream). */
+int ch_set_fields_host(ch_grid* g, const double* u, const double* v, const double* w,
+                       const double* phi);
+
+/* Advance nsteps full time steps (Sec. 2.2 steps i)-v)), asynchronously on the stream.  After
+ * the first step the per-step launch sequence is replayed from a captured CUDA graph. */
+int ch_step(ch_grid* g, int nsteps);
+
+/* As ch_step, but launched without the graph and bracketed by CUDA events on the stream: on
+ * return (the stream is synchronised) kernel_ms[0..3] hold the summed device time of the z-line,
+ * y-backward, x-line and y-forward launches and *total_ms the time from the first launch to the
+ * end of the last.  kernel_ms may be NULL.  Used by the benchmark to attribute step time. */
+int ch_step_timed(ch_grid* g, int nsteps, double* kernel_ms, double* total_ms);
+
+/* Number of kernel launches one ch_step makes per time step. */
+int ch_launches_per_step(const ch_grid* g);
+
+/* Spectral state -> physical u, v, w, phi (device, (nz,ny,nx) float64) on the unpadded grid. */
+int ch_get_fields(ch_grid* g, double* u, double* v, double* w, double* phi);
+
+/* As ch_get_fields into HOST arrays; synchronises the stream before returning. */
+int ch_get_fields_host(ch_grid* g, double* u, double* v, double* w, double* phi);
+
+/* Diagnostics of the current state (fills *out, synchronises the stream).  Returns
+ * CH_ERR_DIVERGED when NaN/Inf is found (out->nan = 1). */
+int ch_diagnostics(ch_grid* g, ch_diag* out);
+
+/* Bytes of the checkpoint written by ch_get_state: spectral state, Adams-Bashforth history,
+ * time, step count and start flag.  Restoring it with ch_set_state resumes bit-for-bit. */
+size_t ch_state_bytes(const ch_grid* g);
+int ch_get_state(ch_grid* g, void* dev_buf);
+int ch_set_state(ch_grid* g, const void* dev_buf);
+
+/* Spectral state (device, complex float64, layout above): omega_z (its (0,0) line holds
+ * ubar + i vbar), w, phi.  Any pointer may be NULL to skip that field. */
+int ch_get_spectral(ch_grid* g, double* omega, double* w, double* phi);
+int ch_set_spectral(ch_grid* g, const double* omega, const double* w, const double* phi);
+
+/* Stage-level entry points (used by the parity tests; each runs the same kernels as ch_step).
+ *
+ * ch_transform_forward: physical (nz,ny,nx) float64 -> spectral coefficients (layout above),
+ *   Fourier in x and y (1/(nx ny)) then the Chebyshev DCT-I (Sec. 3.2.1).
+ * ch_transform_backward: the inverse, evaluated on the unpadded grid.
+ * ch_nonlinear: the ten non-linear coefficient arrays of the current state, in the order
+ *   Sxx, Syy, Szz, Sxy, Sxz, Syz (Sigma_ij = -u_i u_j + kappa T_ij, Eq. (kort)), phi^3, u phi,
+ *   v phi, w phi, formed on the 3/2-padded grid and returned as complex float64 coefficients
+ *   (10 consecutive spectral fields) - steps ii) and vi) of Sec. 2.2. */
+int ch_transform_forward(ch_grid* g, const double* phys, double* spec);
+int ch_transform_backward(ch_grid* g, const double* spec, double* phys);
+int ch_nonlinear(ch_grid* g, double* out10);
+
+/* Release every buffer owned by the handle (synchronises its stream). */
+void ch_destroy(ch_grid* g);
+
+/* Static string for a status code. */
+const char* ch_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CH_FLOW_H */

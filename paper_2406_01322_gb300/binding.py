@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libchflow.so (include/ch_flow.h): argument marshalling only.
+
+Every computation happens in the library's CUDA kernels.  PyTorch provides device memory (the
+library's internal buffers come from torch's caching allocator through the allocator callbacks)
+and the CUDA stream.  Importing this module loads the library and raises if it is missing; there
+is no CPU fallback.
+"""
+import ctypes
+import math
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchflow.so")
+
+CH_OK = 0
+STATUS = {0: "ok", -1: "CH_ERR_ARG", -2: "CH_ERR_SIZE", -3: "CH_ERR_ALLOC", -4: "CH_ERR_CUDA",
+          -5: "CH_ERR_DIVERGED", -6: "CH_ERR_TIMEOUT", -7: "CH_ERR_STATE"}
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+
+class ChError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} failed: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+                ("re_tau", ctypes.c_double), ("we", ctypes.c_double), ("ch", ctypes.c_double),
+                ("pe", ctypes.c_double), ("dt", ctypes.c_double), ("gx", ctypes.c_double),
+                ("gy", ctypes.c_double), ("precision", ctypes.c_int), ("dealias_z", ctypes.c_int),
+                ("bc", ctypes.c_int)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("step", ctypes.c_longlong), ("mass", ctypes.c_double),
+                ("kinetic", ctypes.c_double), ("grad2", ctypes.c_double),
+                ("free_energy", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("max_phi", ctypes.c_double), ("nan", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+# exported names of include/ch_flow.h and their signatures
+_P = ctypes.c_void_p
+_SIGS = {
+    "ch_init_grid": (ctypes.c_int, [ctypes.POINTER(Params), ALLOC_FN, FREE_FN, _P, _P,
+                                    ctypes.POINTER(_P)]),
+    "ch_set_stream": (ctypes.c_int, [_P, _P]),
+    "ch_set_fields": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "ch_set_fields_host": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "ch_step": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ch_step_timed": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "ch_launches_per_step": (ctypes.c_int, [_P]),
+    "ch_get_fields": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "ch_get_fields_host": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "ch_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(Diag)]),
+    "ch_state_bytes": (ctypes.c_size_t, [_P]),
+    "ch_get_state": (ctypes.c_int, [_P, _P]),
+    "ch_set_state": (ctypes.c_int, [_P, _P]),
+    "ch_get_spectral": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ch_set_spectral": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ch_transform_forward": (ctypes.c_int, [_P, _P, _P]),
+    "ch_transform_backward": (ctypes.c_int, [_P, _P, _P]),
+    "ch_nonlinear": (ctypes.c_int, [_P, _P]),
+    "ch_destroy": (None, [_P]),
+    "ch_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2406_01322_gb300.build")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _ck(name, code):
+    if code != CH_OK:
+        raise ChError(name, code)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class TorchAllocator:
+    """Allocator callbacks backed by torch's CUDA caching allocator."""
+
+    def __init__(self, device):
+        self.device = device
+        self.live = {}
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, _ctx):
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        except Exception:  # noqa: BLE001 - the C side sees NULL and returns CH_ERR_ALLOC
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, ptr, _ctx):
+        self.live.pop(ptr, None)
+
+
+class Grid:
+    """One channel on one GPU.  Fields are torch float64 CUDA tensors shaped (nz, ny, nx);
+    spectral arrays are complex128 tensors shaped (nx/2, ny, nz) ([mx][j][n] layout)."""
+
+    def __init__(self, nx, ny, nz, re_tau=150.0, we=1.0, ch=0.05, pe=20.0, dt=1e-4,
+                 lx=4 * math.pi, ly=2 * math.pi, gx=1.0, gy=0.0, precision=PREC_FP64,
+                 device="cuda:0", stream=None, use_torch_allocator=True):
+        self.device = torch.device(device)
+        self.shape = (nz, ny, nx)
+        self.spec_shape = (nx // 2, ny, nz)
+        self.params = Params(nx, ny, nz, lx, ly, re_tau, we, ch, pe, dt, gx, gy, precision, 0, 0)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._alloc = TorchAllocator(self.device) if use_torch_allocator else None
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            code = lib().ch_init_grid(
+                ctypes.byref(self.params),
+                self._alloc.alloc_cb if self._alloc else ALLOC_FN(),
+                self._alloc.free_cb if self._alloc else FREE_FN(),
+                None, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        _ck("ch_init_grid", code)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def _f64(self, a):
+        t = torch.as_tensor(a, dtype=torch.float64, device=self.device).contiguous()
+        if tuple(t.shape) != self.shape:
+            raise ValueError(f"expected shape {self.shape}, got {tuple(t.shape)}")
+        return t
+
+    def set_fields(self, u, v, w, phi):
+        ts = [self._f64(a) for a in (u, v, w, phi)]
+        _ck("ch_set_fields", lib().ch_set_fields(self.h, *[_ptr(t) for t in ts]))
+        self._keep = ts
+
+    def set_fields_host(self, u, v, w, phi):
+        """Host float64 arrays/tensors (C-contiguous); copies happen inside the library."""
+        ts = [torch.as_tensor(a, dtype=torch.float64).contiguous() for a in (u, v, w, phi)]
+        _ck("ch_set_fields_host", lib().ch_set_fields_host(self.h, *[_ptr(t) for t in ts]))
+
+    def step(self, n=1):
+        _ck("ch_step", lib().ch_step(self.h, int(n)))
+
+    def step_timed(self, n):
+        """n steps with CUDA events between launches; returns (total_ms, [zline, ybwd, xline,
+        yfwd] summed ms).  Synchronises the stream."""
+        ks = (ctypes.c_double * 4)()
+        tot = ctypes.c_double()
+        _ck("ch_step_timed", lib().ch_step_timed(self.h, int(n), ks, ctypes.byref(tot)))
+        return tot.value, list(ks)
+
+    def launches_per_step(self):
+        return int(lib().ch_launches_per_step(self.h))
+
+    def get_fields(self):
+        outs = [torch.empty(self.shape, dtype=torch.float64, device=self.device) for _ in range(4)]
+        _ck("ch_get_fields", lib().ch_get_fields(self.h, *[_ptr(t) for t in outs]))
+        return outs
+
+    def get_fields_host(self, outs=None):
+        if outs is None:
+            outs = [torch.empty(self.shape, dtype=torch.float64).pin_memory() for _ in range(4)]
+        _ck("ch_get_fields_host", lib().ch_get_fields_host(self.h, *[_ptr(t) for t in outs]))
+        return outs
+
+    def diagnostics(self):
+        d = Diag()
+        code = lib().ch_diagnostics(self.h, ctypes.byref(d))
+        if code not in (CH_OK, -5):
+            _ck("ch_diagnostics", code)
+        return {k: getattr(d, k) for k, _ in Diag._fields_}
+
+    def state_bytes(self):
+        return int(lib().ch_state_bytes(self.h))
+
+    def get_state(self):
+        buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        _ck("ch_get_state", lib().ch_get_state(self.h, _ptr(buf)))
+        return buf
+
+    def set_state(self, buf):
+        _ck("ch_set_state", lib().ch_set_state(self.h, _ptr(buf)))
+
+    def get_spectral(self):
+        outs = [torch.empty(self.spec_shape, dtype=torch.complex128, device=self.device)
+                for _ in range(3)]
+        _ck("ch_get_spectral", lib().ch_get_spectral(self.h, *[_ptr(t) for t in outs]))
+        return outs
+
+    def set_spectral(self, om, w, phi):
+        ts = [torch.as_tensor(a, dtype=torch.complex128, device=self.device).contiguous()
+              for a in (om, w, phi)]
+        _ck("ch_set_spectral", lib().ch_set_spectral(self.h, *[_ptr(t) for t in ts]))
+        self._keep = ts
+
+    def transform_forward(self, phys):
+        f = self._f64(phys)
+        out = torch.empty(self.spec_shape, dtype=torch.complex128, device=self.device)
+        _ck("ch_transform_forward", lib().ch_transform_forward(self.h, _ptr(f), _ptr(out)))
+        return out
+
+    def transform_backward(self, spec):
+        s = torch.as_tensor(spec, dtype=torch.complex128, device=self.device).contiguous()
+        out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        _ck("ch_transform_backward", lib().ch_transform_backward(self.h, _ptr(s), _ptr(out)))
+        return out
+
+    def nonlinear(self):
+        out = torch.empty((10,) + self.spec_shape, dtype=torch.complex128, device=self.device)
+        _ck("ch_nonlinear", lib().ch_nonlinear(self.h, _ptr(out)))
+        return out

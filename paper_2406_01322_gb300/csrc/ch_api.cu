@@ -1,0 +1,652 @@
+// C-ABI of the channel solver (declared in include/ch_flow.h): validation, plans, twiddle
+// tables, internal buffers, the per-step launch schedule and its CUDA-graph replay.
+//
+// One time step (paper Sec. 2.2, steps i)-v)) is four launches on the handle's stream:
+//   zline (mode 0)  : Chebyshev DCT of the 10 non-linear fields, assembly, AB2/CN/IE, tau
+//                     solves, state update, backward DCT of the 7 fields the next products need;
+//   ypass backward  : 7 fields, ky -> y with 3/2 zero padding;
+//   xline           : 7 fields kx -> x (padded), 10 products, x -> kx (truncated);
+//   ypass forward   : 10 fields, y -> ky, truncation and the 1/(Px Py) normalisation.
+// The non-linear buffer therefore always holds the products of the current state.
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/ch_flow.h"
+#include "ch_internal.h"
+
+using chf::FftPlan;
+using chf::GridDev;
+
+namespace {
+
+const int kMaxSmem = 227 * 1024;
+
+struct Tw {
+  void* d64 = nullptr;  // double2[n]
+  void* d32 = nullptr;  // float2[n]
+};
+
+}  // namespace
+
+struct ch_grid {
+  ch_params p;
+  GridDev g;
+  int prec;
+  cudaStream_t stream;
+  ch_alloc_fn af;
+  ch_free_fn ff;
+  void* actx;
+  std::vector<void*> allocs;
+
+  // state and Adams-Bashforth history, (Mx, Ny, Nz) complex float64
+  double2 *om, *w, *phi, *hom, *hw, *hphi;
+  // step buffers in working precision
+  void *nl, *bw, *ya, *yb;
+  // auxiliary float64 buffers for set/get/diagnostics/stage entry points
+  double2 *auxA, *auxB;
+  double* phys7;
+  // small tables and diagnostics scratch
+  double* tab;  // go1 go2 go3 ccw dzl qint, nz each
+  double* diag_part;
+  double* diag_out;
+
+  FftPlan px[2], py[2], pz, pxu, pyu;
+  std::vector<Tw> tws;
+
+  long long fs;      // elements per (Mx, Ny, Nz) field
+  long long fsy;     // elements per (Mx, Py, Nz) field
+  long long fsp;     // elements per physical (Nz, Ny, Nx) field
+  int first;         // next step starts Adams-Bashforth
+  int fields_set;
+  long long nstep;
+  double t;
+  cudaGraphExec_t gexec;
+  int graph_ok;
+};
+
+namespace {
+
+bool smooth23(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+void* galloc(ch_grid* G, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 256;
+  if (G->af) {
+    p = G->af(bytes, G->actx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) G->allocs.push_back(p);
+  return p;
+}
+
+void release_all(ch_grid* G) {
+  for (void* p : G->allocs) {
+    if (G->ff) G->ff(p, G->actx);
+    else if (!G->af) cudaFree(p);
+  }
+  G->allocs.clear();
+}
+
+// radix schedule: 8 once if the power of two is odd (>= 3), 4s, a 2 if needed, then 3s
+bool make_radices(int n, FftPlan* pl) {
+  int a = 0, b = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  if (m != 1) return false;
+  int k = 0;
+  if (a % 2 == 1 && a >= 3) { pl->rad[k++] = 8; a -= 3; }
+  while (a >= 2) { pl->rad[k++] = 4; a -= 2; }
+  if (a == 1) { pl->rad[k++] = 2; a = 0; }
+  while (b > 0) { pl->rad[k++] = 3; --b; }
+  if (k > CHF_MAX_STAGES) return false;
+  if (k == 0) { pl->rad[k++] = 2; }  // n == 1 never used
+  pl->nst = k;
+  pl->n = n;
+  return true;
+}
+
+// twiddles exp(-2 pi i t / n) in extended precision, rounded once
+int make_plan(ch_grid* G, int n, int prec, FftPlan* pl) {
+  if (!make_radices(n, pl)) return CH_ERR_SIZE;
+  std::vector<double2> h64(n);
+  std::vector<float2> h32(n);
+  const long double pi2 = 6.283185307179586476925286766559L;
+  for (int t = 0; t < n; ++t) {
+    const long double a = pi2 * (long double)t / (long double)n;
+    const long double c = cosl(a), s = -sinl(a);
+    h64[t] = make_double2((double)c, (double)s);
+    h32[t] = make_float2((float)c, (float)s);
+  }
+  Tw tw;
+  tw.d64 = galloc(G, n * sizeof(double2));
+  tw.d32 = galloc(G, n * sizeof(float2));
+  if (!tw.d64 || !tw.d32) return CH_ERR_ALLOC;
+  if (cudaMemcpy(tw.d64, h64.data(), n * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(tw.d32, h32.data(), n * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+    return CH_ERR_CUDA;
+  G->tws.push_back(tw);
+  pl->tw = prec == 0 ? tw.d64 : tw.d32;
+  return CH_OK;
+}
+
+#define CK(x)                                       \
+  do {                                              \
+    cudaError_t e__ = (x);                          \
+    if (e__ != cudaSuccess) return CH_ERR_CUDA;     \
+  } while (0)
+
+// non-linear terms of the current state: bw <- 7 fields; ya <- y backward; yb <- x line;
+// nl <- y forward (normalised)
+int eval_nonlinear(ch_grid* G) {
+  const GridDev& g = G->g;
+  cudaStream_t s = G->stream;
+  CK(chf::launch_zline(1, G->prec, g, G->nl, G->bw, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
+                       G->hphi, 0, G->pz, s));
+  CK(chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s));
+  CK(chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s));
+  CK(chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, 10, G->fsy, G->fs,
+                       1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s));
+  return CH_OK;
+}
+
+int launch_step(ch_grid* G, int first) {
+  const GridDev& g = G->g;
+  cudaStream_t s = G->stream;
+  CK(chf::launch_zline(0, G->prec, g, G->nl, G->bw, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
+                       G->hphi, first, G->pz, s));
+  CK(chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s));
+  CK(chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s));
+  CK(chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, 10, G->fsy, G->fs,
+                       1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s));
+  return CH_OK;
+}
+
+// the 7 backward fields of the state, evaluated on the unpadded grid, into phys7
+int state_to_phys7(ch_grid* G, int nf) {
+  const GridDev& g = G->g;
+  cudaStream_t s = G->stream;
+  CK(chf::launch_zline(1, 0, g, nullptr, G->auxA, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
+                       G->hphi, 0, G->pz, s));
+  CK(chf::launch_ypass(1, 0, g, g.ny, G->auxA, G->auxB, nf, G->fs, G->fs, 1.0, G->pyu, s));
+  CK(chf::launch_x_c2r(g, G->auxB, G->phys7, nf, G->fs, G->fsp, G->pxu, s));
+  return CH_OK;
+}
+
+void drop_graph(ch_grid* G) {
+  if (G->graph_ok) cudaGraphExecDestroy(G->gexec);
+  G->graph_ok = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ch_status_string(int st) {
+  switch (st) {
+    case CH_OK: return "ok";
+    case CH_ERR_ARG: return "invalid argument";
+    case CH_ERR_SIZE: return "unsupported grid size";
+    case CH_ERR_ALLOC: return "allocation failed";
+    case CH_ERR_CUDA: return "CUDA error";
+    case CH_ERR_DIVERGED: return "solution diverged (NaN/Inf)";
+    case CH_ERR_TIMEOUT: return "device wait timed out";
+    case CH_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void* alloc_ctx,
+                 void* stream, ch_grid** out) {
+  if (!p || !out) return CH_ERR_ARG;
+  *out = nullptr;
+  if (!(p->dt > 0) || !(p->lx > 0) || !(p->ly > 0) || !(p->re_tau > 0) || !(p->we > 0) ||
+      !(p->ch > 0) || !(p->pe > 0))
+    return CH_ERR_ARG;
+  if (p->precision != CH_PREC_FP64 && p->precision != CH_PREC_MIXED) return CH_ERR_ARG;
+  if (p->dealias_z != 0 || p->bc != 0) return CH_ERR_ARG;
+  if ((alloc == nullptr) != (free_fn == nullptr)) return CH_ERR_ARG;
+  const int nx = p->nx, ny = p->ny, nz = p->nz;
+  if (nx < 4 || ny < 4 || nz < 5 || nx % 2 || ny % 2) return CH_ERR_SIZE;
+  if (!smooth23(nx) || !smooth23(ny) || !smooth23(3 * nx / 2) || !smooth23(3 * ny / 2) ||
+      (nz - 1) % 2 || !smooth23(2 * (nz - 1)))
+    return CH_ERR_SIZE;
+  if (3 * nx / 2 > 8192 || 3 * ny / 2 > 8192 || nz > 4097) return CH_ERR_SIZE;
+
+  ch_grid* G = new (std::nothrow) ch_grid();
+  if (!G) return CH_ERR_ALLOC;
+  G->p = *p;
+  G->prec = p->precision;
+  G->stream = (cudaStream_t)stream;
+  G->af = alloc;
+  G->ff = free_fn;
+  G->actx = alloc_ctx;
+  G->gexec = nullptr;
+  G->graph_ok = 0;
+  GridDev& g = G->g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.N = nz - 1;
+  g.Mx = nx / 2;
+  g.Px = 3 * nx / 2;
+  g.Py = 3 * ny / 2;
+  g.lx = p->lx;
+  g.ly = p->ly;
+  g.re = p->re_tau;
+  g.we = p->we;
+  g.ch = p->ch;
+  g.pe = p->pe;
+  g.dt = p->dt;
+  g.gx = p->gx;
+  g.gy = p->gy;
+  g.beta = 2.0 * p->re_tau / p->dt;
+  g.lam = sqrt(p->pe / (p->ch * p->ch * p->dt));
+  g.shat = 2.0 * g.lam * p->ch * p->ch;
+  g.kappa = 3.0 / sqrt(8.0) * p->ch / p->we;
+
+  const size_t esz = G->prec == 0 ? sizeof(double2) : sizeof(float2);
+  G->fs = (long long)g.Mx * ny * nz;
+  G->fsy = (long long)g.Mx * g.Py * nz;
+  G->fsp = (long long)nx * ny * nz;
+  int st = CH_OK;
+  auto A = [&](size_t bytes) -> void* {
+    void* q = galloc(G, bytes);
+    if (!q) st = CH_ERR_ALLOC;
+    return q;
+  };
+  const size_t sb = (size_t)G->fs * sizeof(double2);
+  G->om = (double2*)A(sb);
+  G->w = (double2*)A(sb);
+  G->phi = (double2*)A(sb);
+  G->hom = (double2*)A(sb);
+  G->hw = (double2*)A(sb);
+  G->hphi = (double2*)A(sb);
+  G->nl = A((size_t)10 * G->fs * esz);
+  G->bw = A((size_t)7 * G->fs * esz);
+  G->ya = A((size_t)7 * G->fsy * esz);
+  G->yb = A((size_t)10 * G->fsy * esz);
+  G->auxA = (double2*)A((size_t)7 * sb);
+  G->auxB = (double2*)A((size_t)7 * sb);
+  G->phys7 = (double*)A((size_t)7 * G->fsp * sizeof(double));
+  G->tab = (double*)A((size_t)6 * nz * sizeof(double));
+  G->diag_part = (double*)A((size_t)(304 * 6 + 16) * sizeof(double));
+  G->diag_out = G->diag_part + 304 * 6;
+  if (st != CH_OK) {
+    release_all(G);
+    delete G;
+    return st;
+  }
+  // plans
+  int e = CH_OK;
+  if (e == CH_OK) e = make_plan(G, g.Px, 0, &G->px[0]);
+  if (e == CH_OK) { G->px[1] = G->px[0]; G->px[1].tw = G->tws.back().d32; }
+  if (e == CH_OK) e = make_plan(G, g.Py, 0, &G->py[0]);
+  if (e == CH_OK) { G->py[1] = G->py[0]; G->py[1].tw = G->tws.back().d32; }
+  if (e == CH_OK) e = make_plan(G, 2 * g.N, 0, &G->pz);
+  if (e == CH_OK) e = make_plan(G, nx, 0, &G->pxu);
+  if (e == CH_OK) e = make_plan(G, ny, 0, &G->pyu);
+  if (e != CH_OK) {
+    release_all(G);
+    delete G;
+    return e;
+  }
+  // tables: Gottlieb-Orszag rows, Clenshaw-Curtis weights, local z spacing, integrals of T_n
+  {
+    const int N = g.N;
+    std::vector<double> h(6 * (size_t)nz, 0.0);
+    double* t1 = h.data();
+    double* t2 = t1 + nz;
+    double* t3 = t2 + nz;
+    double* ccw = t3 + nz;
+    double* dzl = ccw + nz;
+    double* qint = dzl + nz;
+    for (int n = 2; n <= N; ++n) {
+      const double cnm2 = (n - 2 == 0) ? 2.0 : 1.0;
+      t1[n] = cnm2 / (4.0 * n * (n - 1));
+      t2[n] = (n <= N - 2) ? 1.0 / (2.0 * ((double)n * n - 1.0)) : 0.0;
+      t3[n] = (n + 2 <= N - 2) ? 1.0 / (4.0 * n * (n + 1)) : 0.0;
+    }
+    for (int n = 0; n <= N; n += 2) qint[n] = 2.0 / (1.0 - (double)n * n);
+    // ccw_j = sum_n qint_n * 2/(cbar_n N) cos(pi n j / N) / cbar_j (exact for degree <= N)
+    const long double pi = 3.141592653589793238462643383279L;
+    for (int j = 0; j <= N; ++j) {
+      long double acc = 0.0L;
+      for (int n = 0; n <= N; n += 2) {
+        const long double cbn = (n == 0 || n == N) ? 2.0L : 1.0L;
+        acc += (long double)qint[n] * 2.0L / (cbn * N) * cosl(pi * (long double)((n * j) % (2 * N)) / N);
+      }
+      const long double cbj = (j == 0 || j == N) ? 2.0L : 1.0L;
+      ccw[j] = (double)(acc / cbj);
+    }
+    std::vector<double> z(nz);
+    for (int j = 0; j <= N; ++j) z[j] = cos(3.14159265358979323846 * j / N);
+    for (int j = 1; j < N; ++j) dzl[j] = 0.5 * (z[j - 1] - z[j + 1]);
+    dzl[0] = z[0] - z[1];
+    dzl[N] = z[N - 1] - z[N];
+    if (cudaMemcpy(G->tab, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+      release_all(G);
+      delete G;
+      return CH_ERR_CUDA;
+    }
+    g.go1 = G->tab;
+    g.go2 = G->tab + nz;
+    g.go3 = G->tab + 2 * nz;
+  }
+  if (chf::zline_smem(g) > (size_t)kMaxSmem || (size_t)17 * g.Px * sizeof(double2) > (size_t)kMaxSmem) {
+    release_all(G);
+    delete G;
+    return CH_ERR_SIZE;
+  }
+  G->first = 1;
+  G->fields_set = 0;
+  G->nstep = 0;
+  G->t = 0.0;
+  for (double2* q : {G->om, G->w, G->phi, G->hom, G->hw, G->hphi})
+    if (cudaMemset(q, 0, sb) != cudaSuccess) {
+      release_all(G);
+      delete G;
+      return CH_ERR_CUDA;
+    }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    release_all(G);
+    delete G;
+    return CH_ERR_CUDA;
+  }
+  *out = G;
+  return CH_OK;
+}
+
+int ch_set_stream(ch_grid* G, void* stream) {
+  if (!G) return CH_ERR_ARG;
+  G->stream = (cudaStream_t)stream;
+  drop_graph(G);
+  return CH_OK;
+}
+
+static int set_from_phys(ch_grid* G, const double* u, const double* v, const double* w,
+                         const double* phi) {
+  const GridDev& g = G->g;
+  cudaStream_t s = G->stream;
+  const double* f4[4] = {u, v, w, phi};
+  for (int f = 0; f < 4; ++f)
+    CK(chf::launch_x_r2c(g, f4[f], G->auxA + f * G->fs, 1, G->fsp, G->fs, G->pxu, s));
+  CK(chf::launch_ypass(0, 0, g, g.ny, G->auxA, G->auxB, 4, G->fs, G->fs,
+                       1.0 / ((double)g.nx * (double)g.ny), G->pyu, s));
+  CK(chf::launch_project(g, G->auxB, G->fs, G->om, G->w, G->phi, G->hom, G->hw, G->hphi, G->pz, s));
+  G->first = 1;
+  G->nstep = 0;
+  G->t = 0.0;
+  G->fields_set = 1;
+  return eval_nonlinear(G);
+}
+
+int ch_set_fields(ch_grid* G, const double* u, const double* v, const double* w,
+                  const double* phi) {
+  if (!G || !u || !v || !w || !phi) return CH_ERR_ARG;
+  return set_from_phys(G, u, v, w, phi);
+}
+
+int ch_set_fields_host(ch_grid* G, const double* u, const double* v, const double* w,
+                       const double* phi) {
+  if (!G || !u || !v || !w || !phi) return CH_ERR_ARG;
+  const size_t b = (size_t)G->fsp * sizeof(double);
+  const double* f4[4] = {u, v, w, phi};
+  for (int f = 0; f < 4; ++f)
+    CK(cudaMemcpyAsync(G->phys7 + f * G->fsp, f4[f], b, cudaMemcpyHostToDevice, G->stream));
+  return set_from_phys(G, G->phys7, G->phys7 + G->fsp, G->phys7 + 2 * G->fsp,
+                       G->phys7 + 3 * G->fsp);
+}
+
+int ch_step(ch_grid* G, int nsteps) {
+  if (!G || nsteps < 0) return CH_ERR_ARG;
+  if (!G->fields_set) return CH_ERR_STATE;
+  for (int i = 0; i < nsteps; ++i) {
+    if (G->first) {
+      int r = launch_step(G, 1);
+      if (r != CH_OK) return r;
+      G->first = 0;
+    } else {
+      if (!G->graph_ok) {
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(G->stream, cudaStreamCaptureModeThreadLocal));
+        int r = launch_step(G, 0);
+        cudaError_t e = cudaStreamEndCapture(G->stream, &graph);
+        if (r != CH_OK || e != cudaSuccess) return CH_ERR_CUDA;
+        e = cudaGraphInstantiate(&G->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return CH_ERR_CUDA;
+        G->graph_ok = 1;
+      }
+      CK(cudaGraphLaunch(G->gexec, G->stream));
+    }
+    G->nstep += 1;
+    G->t += G->p.dt;
+  }
+  return CH_OK;
+}
+
+int ch_launches_per_step(const ch_grid* G) { return G ? 4 : 0; }
+
+int ch_step_timed(ch_grid* G, int nsteps, double* kernel_ms, double* total_ms) {
+  if (!G || nsteps < 0 || !total_ms) return CH_ERR_ARG;
+  if (!G->fields_set) return CH_ERR_STATE;
+  const int nev = 4 * nsteps + 1;
+  std::vector<cudaEvent_t> ev(nev);
+  for (int i = 0; i < nev; ++i) CK(cudaEventCreate(&ev[i]));
+  const GridDev& g = G->g;
+  cudaStream_t s = G->stream;
+  int st = CH_OK;
+  CK(cudaEventRecord(ev[0], s));
+  for (int i = 0; i < nsteps && st == CH_OK; ++i) {
+    const int first = G->first;
+    cudaEvent_t* e = &ev[4 * i];
+#define TK(k, call)                          \
+  if ((call) != cudaSuccess) st = CH_ERR_CUDA; \
+  cudaEventRecord(e[k + 1], s);
+    TK(0, chf::launch_zline(0, G->prec, g, G->nl, G->bw, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
+                            G->hphi, first, G->pz, s))
+    TK(1, chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s))
+    TK(2, chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s))
+    TK(3, chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, 10, G->fsy, G->fs,
+                            1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s))
+#undef TK
+    G->first = 0;
+    G->nstep += 1;
+    G->t += G->p.dt;
+  }
+  CK(cudaEventSynchronize(ev[nev - 1]));
+  double ks[4] = {0, 0, 0, 0};
+  for (int i = 0; i < nsteps; ++i)
+    for (int k = 0; k < 4; ++k) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev[4 * i + k], ev[4 * i + k + 1]));
+      ks[k] += ms;
+    }
+  float tot = 0.f;
+  CK(cudaEventElapsedTime(&tot, ev[0], ev[nev - 1]));
+  for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+  if (kernel_ms)
+    for (int k = 0; k < 4; ++k) kernel_ms[k] = ks[k];
+  *total_ms = tot;
+  return st;
+}
+
+int ch_get_fields(ch_grid* G, double* u, double* v, double* w, double* phi) {
+  if (!G || !u || !v || !w || !phi) return CH_ERR_ARG;
+  const GridDev& g = G->g;
+  cudaStream_t s = G->stream;
+  CK(chf::launch_zline(1, 0, g, nullptr, G->auxA, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
+                       G->hphi, 0, G->pz, s));
+  CK(chf::launch_ypass(1, 0, g, g.ny, G->auxA, G->auxB, 4, G->fs, G->fs, 1.0, G->pyu, s));
+  double* f4[4] = {u, v, w, phi};
+  for (int f = 0; f < 4; ++f)
+    CK(chf::launch_x_c2r(g, G->auxB + f * G->fs, f4[f], 1, G->fs, G->fsp, G->pxu, s));
+  return CH_OK;
+}
+
+int ch_get_fields_host(ch_grid* G, double* u, double* v, double* w, double* phi) {
+  if (!G || !u || !v || !w || !phi) return CH_ERR_ARG;
+  int r = ch_get_fields(G, G->phys7, G->phys7 + G->fsp, G->phys7 + 2 * G->fsp,
+                        G->phys7 + 3 * G->fsp);
+  if (r != CH_OK) return r;
+  const size_t b = (size_t)G->fsp * sizeof(double);
+  double* f4[4] = {u, v, w, phi};
+  for (int f = 0; f < 4; ++f)
+    CK(cudaMemcpyAsync(f4[f], G->phys7 + f * G->fsp, b, cudaMemcpyDeviceToHost, G->stream));
+  CK(cudaStreamSynchronize(G->stream));
+  return CH_OK;
+}
+
+int ch_diagnostics(ch_grid* G, ch_diag* out) {
+  if (!G || !out) return CH_ERR_ARG;
+  int r = state_to_phys7(G, 7);
+  if (r != CH_OK) return r;
+  const GridDev& g = G->g;
+  const int nz = g.nz;
+  CK(chf::launch_diag(g, G->phys7, G->fsp, G->phi, G->tab + 3 * nz, G->tab + 4 * nz,
+                      G->tab + 5 * nz, G->diag_part, G->diag_out, G->stream));
+  double h[8];
+  CK(cudaMemcpyAsync(h, G->diag_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, G->stream));
+  CK(cudaStreamSynchronize(G->stream));
+  out->t = G->t;
+  out->step = G->nstep;
+  out->mass = h[0];
+  out->kinetic = h[1];
+  out->grad2 = h[2];
+  out->free_energy = h[3];
+  out->cfl = h[4];
+  out->max_phi = h[5];
+  out->nan = h[6] != 0.0 ? 1 : 0;
+  if (!isfinite(h[0]) || !isfinite(h[1])) out->nan = 1;
+  return out->nan ? CH_ERR_DIVERGED : CH_OK;
+}
+
+// checkpoint layout: 64-byte header, then om w phi hom hw hphi
+struct StateHeader {
+  uint64_t magic;
+  int32_t nx, ny, nz, first;
+  int64_t nstep;
+  double t;
+  int32_t fields_set, pad0;
+  uint64_t pad[2];
+};
+static_assert(sizeof(StateHeader) == 64, "header size");
+
+size_t ch_state_bytes(const ch_grid* G) {
+  if (!G) return 0;
+  return sizeof(StateHeader) + (size_t)6 * G->fs * sizeof(double2);
+}
+
+int ch_get_state(ch_grid* G, void* buf) {
+  if (!G || !buf) return CH_ERR_ARG;
+  StateHeader h;
+  memset(&h, 0, sizeof(h));
+  h.magic = 0x3130333234303632ULL;
+  h.nx = G->g.nx;
+  h.ny = G->g.ny;
+  h.nz = G->g.nz;
+  h.first = G->first;
+  h.nstep = G->nstep;
+  h.t = G->t;
+  h.fields_set = G->fields_set;
+  char* b = (char*)buf;
+  CK(cudaMemcpyAsync(b, &h, sizeof(h), cudaMemcpyHostToDevice, G->stream));
+  const size_t sb = (size_t)G->fs * sizeof(double2);
+  const double2* src[6] = {G->om, G->w, G->phi, G->hom, G->hw, G->hphi};
+  for (int i = 0; i < 6; ++i)
+    CK(cudaMemcpyAsync(b + sizeof(h) + i * sb, src[i], sb, cudaMemcpyDeviceToDevice, G->stream));
+  CK(cudaStreamSynchronize(G->stream));
+  return CH_OK;
+}
+
+int ch_set_state(ch_grid* G, const void* buf) {
+  if (!G || !buf) return CH_ERR_ARG;
+  StateHeader h;
+  const char* b = (const char*)buf;
+  CK(cudaMemcpyAsync(&h, b, sizeof(h), cudaMemcpyDeviceToHost, G->stream));
+  CK(cudaStreamSynchronize(G->stream));
+  if (h.magic != 0x3130333234303632ULL || h.nx != G->g.nx || h.ny != G->g.ny || h.nz != G->g.nz)
+    return CH_ERR_ARG;
+  const size_t sb = (size_t)G->fs * sizeof(double2);
+  double2* dst[6] = {G->om, G->w, G->phi, G->hom, G->hw, G->hphi};
+  for (int i = 0; i < 6; ++i)
+    CK(cudaMemcpyAsync(dst[i], b + sizeof(h) + i * sb, sb, cudaMemcpyDeviceToDevice, G->stream));
+  G->first = h.first;
+  G->nstep = h.nstep;
+  G->t = h.t;
+  G->fields_set = h.fields_set;
+  if (!G->fields_set) return CH_OK;
+  return eval_nonlinear(G);
+}
+
+int ch_get_spectral(ch_grid* G, double* om, double* w, double* phi) {
+  if (!G) return CH_ERR_ARG;
+  const size_t sb = (size_t)G->fs * sizeof(double2);
+  if (om) CK(cudaMemcpyAsync(om, G->om, sb, cudaMemcpyDeviceToDevice, G->stream));
+  if (w) CK(cudaMemcpyAsync(w, G->w, sb, cudaMemcpyDeviceToDevice, G->stream));
+  if (phi) CK(cudaMemcpyAsync(phi, G->phi, sb, cudaMemcpyDeviceToDevice, G->stream));
+  return CH_OK;
+}
+
+int ch_set_spectral(ch_grid* G, const double* om, const double* w, const double* phi) {
+  if (!G) return CH_ERR_ARG;
+  const size_t sb = (size_t)G->fs * sizeof(double2);
+  if (om) CK(cudaMemcpyAsync(G->om, om, sb, cudaMemcpyDeviceToDevice, G->stream));
+  if (w) CK(cudaMemcpyAsync(G->w, w, sb, cudaMemcpyDeviceToDevice, G->stream));
+  if (phi) CK(cudaMemcpyAsync(G->phi, phi, sb, cudaMemcpyDeviceToDevice, G->stream));
+  for (double2* q : {G->hom, G->hw, G->hphi}) CK(cudaMemsetAsync(q, 0, sb, G->stream));
+  G->first = 1;
+  G->nstep = 0;
+  G->t = 0.0;
+  G->fields_set = 1;
+  return eval_nonlinear(G);
+}
+
+int ch_transform_forward(ch_grid* G, const double* phys, double* spec) {
+  if (!G || !phys || !spec) return CH_ERR_ARG;
+  const GridDev& g = G->g;
+  cudaStream_t s = G->stream;
+  CK(chf::launch_x_r2c(g, phys, G->auxA, 1, G->fsp, G->fs, G->pxu, s));
+  CK(chf::launch_ypass(0, 0, g, g.ny, G->auxA, G->auxB, 1, G->fs, G->fs,
+                       1.0 / ((double)g.nx * (double)g.ny), G->pyu, s));
+  CK(chf::launch_dct_lines(0, 0, g, G->auxB, (double2*)spec, 1, G->fs, G->pz, s));
+  return CH_OK;
+}
+
+int ch_transform_backward(ch_grid* G, const double* spec, double* phys) {
+  if (!G || !phys || !spec) return CH_ERR_ARG;
+  const GridDev& g = G->g;
+  cudaStream_t s = G->stream;
+  CK(chf::launch_dct_lines(1, 0, g, spec, G->auxA, 1, G->fs, G->pz, s));
+  CK(chf::launch_ypass(1, 0, g, g.ny, G->auxA, G->auxB, 1, G->fs, G->fs, 1.0, G->pyu, s));
+  CK(chf::launch_x_c2r(g, G->auxB, phys, 1, G->fs, G->fsp, G->pxu, s));
+  return CH_OK;
+}
+
+int ch_nonlinear(ch_grid* G, double* out10) {
+  if (!G || !out10) return CH_ERR_ARG;
+  if (!G->fields_set) return CH_ERR_STATE;
+  CK(chf::launch_dct_lines(0, G->prec, G->g, G->nl, (double2*)out10, 10, G->fs, G->pz, G->stream));
+  return CH_OK;
+}
+
+void ch_destroy(ch_grid* G) {
+  if (!G) return;
+  cudaStreamSynchronize(G->stream);
+  drop_graph(G);
+  release_all(G);
+  delete G;
+}
+
+}  // extern "C"

@@ -1,0 +1,208 @@
+// Device-side building blocks shared by the solver kernels: complex helpers, radix-2/3/4/8
+// butterflies and a block-cooperative Stockham FFT over lines held in shared memory.
+//
+// The transforms are those of Sec. 3.2.1 of the paper (batched Fourier transforms in x and y,
+// the Chebyshev transform as a DCT-I computed through a 2N-point FFT of the even extension),
+// written here as hand-rolled mixed-radix Stockham passes instead of library calls.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace chf {
+
+// ---------------------------------------------------------------------------------------------
+// complex helpers (double2 / float2)
+template <typename T> struct C2;
+template <> struct C2<double> { typedef double2 t; };
+template <> struct C2<float> { typedef float2 t; };
+
+__device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ float2 mk(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+
+// a * b
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// i * a and -i * a
+template <typename T2> __device__ __forceinline__ T2 mul_i(T2 a) { return mk(-a.y, a.x); }
+template <typename T2> __device__ __forceinline__ T2 mul_mi(T2 a) { return mk(a.y, -a.x); }
+
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2((double)a.x, (double)a.y); }
+template <typename T2> __device__ __forceinline__ T2 from_d2(double2 a);
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+
+// ---------------------------------------------------------------------------------------------
+// FFT plan: length n = product of radices (each 2, 3, 4 or 8), twiddle table
+// tw[t] = exp(-2 pi i t / n), t = 0..n-1, in the working precision.
+#define CHF_MAX_STAGES 16
+struct FftPlan {
+  int n;
+  int nst;
+  int rad[CHF_MAX_STAGES];
+  const void* tw;
+};
+
+// radix-R DFT of v[0..R-1] in registers; INV selects exp(+2 pi i / R).
+template <typename T, int R, bool INV> struct Dft;
+
+template <typename T, bool INV> struct Dft<T, 2, INV> {
+  typedef typename C2<T>::t T2;
+  __device__ __forceinline__ static void run(T2* v) {
+    T2 a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+  }
+};
+
+template <typename T, bool INV> struct Dft<T, 3, INV> {
+  typedef typename C2<T>::t T2;
+  __device__ __forceinline__ static void run(T2* v) {
+    const T s3 = (T)0.86602540378443864676;  // sin(2 pi / 3)
+    T2 t = v[1] + v[2];
+    T2 d = v[1] - v[2];
+    T2 m = mk(v[0].x - (T)0.5 * t.x, v[0].y - (T)0.5 * t.y);
+    v[0] = v[0] + t;
+    // forward: y1 = m - i s3 d, y2 = m + i s3 d ; inverse swaps the sign
+    T2 r = INV ? mk(-s3 * d.y, s3 * d.x) : mk(s3 * d.y, -s3 * d.x);
+    v[1] = m + r;
+    v[2] = m - r;
+  }
+};
+
+template <typename T, bool INV> struct Dft<T, 4, INV> {
+  typedef typename C2<T>::t T2;
+  __device__ __forceinline__ static void run(T2* v) {
+    T2 t0 = v[0] + v[2], t1 = v[0] - v[2];
+    T2 t2 = v[1] + v[3], t3 = v[1] - v[3];
+    t3 = INV ? mul_i(t3) : mul_mi(t3);
+    v[0] = t0 + t2;
+    v[2] = t0 - t2;
+    v[1] = t1 + t3;
+    v[3] = t1 - t3;
+  }
+};
+
+template <typename T, bool INV> struct Dft<T, 8, INV> {
+  typedef typename C2<T>::t T2;
+  __device__ __forceinline__ static void run(T2* v) {
+    const T h = (T)0.70710678118654752440;  // sqrt(2)/2
+    // radix-2 layer on (r, r+4)
+    T2 a0 = v[0] + v[4], a4 = v[0] - v[4];
+    T2 a1 = v[1] + v[5], a5 = v[1] - v[5];
+    T2 a2 = v[2] + v[6], a6 = v[2] - v[6];
+    T2 a3 = v[3] + v[7], a7 = v[3] - v[7];
+    // twiddles w8^1, w8^2, w8^3 on the odd half
+    if (!INV) {
+      a5 = mk(h * (a5.x + a5.y), h * (a5.y - a5.x));     // * (1 - i)/sqrt2
+      a6 = mul_mi(a6);                                   // * -i
+      a7 = mk(h * (a7.y - a7.x), -h * (a7.x + a7.y));    // * (-1 - i)/sqrt2
+    } else {
+      a5 = mk(h * (a5.x - a5.y), h * (a5.x + a5.y));     // * (1 + i)/sqrt2
+      a6 = mul_i(a6);                                    // * i
+      a7 = mk(-h * (a7.x + a7.y), h * (a7.x - a7.y));    // * (-1 + i)/sqrt2
+    }
+    // two radix-4 DFTs: even outputs from a0..a3, odd outputs from a4..a7
+    T2 e[4] = {a0, a1, a2, a3};
+    T2 o[4] = {a4, a5, a6, a7};
+    Dft<T, 4, INV>::run(e);
+    Dft<T, 4, INV>::run(o);
+    v[0] = e[0]; v[2] = e[1]; v[4] = e[2]; v[6] = e[3];
+    v[1] = o[0]; v[3] = o[1]; v[5] = o[2]; v[7] = o[3];
+  }
+};
+
+// one Stockham pass of radix R over `nlines` lines of length n (line stride ls) in shared memory
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void stockham_pass(const typename C2<T>::t* __restrict__ A,
+                                              typename C2<T>::t* __restrict__ B, int nlines,
+                                              int ls, int n, int Ns,
+                                              const typename C2<T>::t* __restrict__ tw) {
+  typedef typename C2<T>::t T2;
+  const int nb = n / R;
+  const int tot = nlines * nb;
+  const int tws = n / (Ns * R);
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int line = t / nb;
+    const int j = t - line * nb;
+    const T2* in = A + line * ls;
+    T2* out = B + line * ls;
+    const int k = j % Ns;
+    T2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
+    if (k != 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const T2 w = tw[r * k * tws];
+        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+      }
+    }
+    Dft<T, R, INV>::run(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+  }
+}
+
+// Block-cooperative FFT of nlines lines (stride ls) held in A; B is a scratch buffer of the same
+// shape.  Returns the buffer holding the result (A or B).  Unnormalised; INV = exp(+).
+// Every thread of the block must call it (it contains __syncthreads()).
+template <typename T, bool INV>
+__device__ typename C2<T>::t* block_fft(typename C2<T>::t* A, typename C2<T>::t* B, int nlines,
+                                        int ls, const FftPlan& pl) {
+  typedef typename C2<T>::t T2;
+  const T2* tw = reinterpret_cast<const T2*>(pl.tw);
+  int Ns = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int R = pl.rad[s];
+    if (R == 4) stockham_pass<T, 4, INV>(A, B, nlines, ls, pl.n, Ns, tw);
+    else if (R == 8) stockham_pass<T, 8, INV>(A, B, nlines, ls, pl.n, Ns, tw);
+    else if (R == 2) stockham_pass<T, 2, INV>(A, B, nlines, ls, pl.n, Ns, tw);
+    else stockham_pass<T, 3, INV>(A, B, nlines, ls, pl.n, Ns, tw);
+    __syncthreads();
+    T2* tmp = A;
+    A = B;
+    B = tmp;
+    Ns *= R;
+  }
+  return A;
+}
+
+// ---------------------------------------------------------------------------------------------
+// per-grid constants handed to the kernels by value
+struct GridDev {
+  int nx, ny, nz, N, Mx, Px, Py;
+  double lx, ly, re, we, ch, pe, dt, gx, gy;
+  double beta;   // 2 Re / dt
+  double lam;    // sqrt(Pe / (Ch^2 dt))
+  double shat;   // 2 lam Ch^2
+  double kappa;  // 3/sqrt(8) Ch / We
+  // Gottlieb-Orszag row coefficients (device arrays of length nz):
+  // t1[n] = c_{n-2}/(4n(n-1)), t2[n] = [n<=N-2]/(2(n^2-1)), t3[n] = [n+2<=N-2]/(4n(n+1))
+  const double* go1;
+  const double* go2;
+  const double* go3;
+};
+
+}  // namespace chf

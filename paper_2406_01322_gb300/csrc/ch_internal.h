@@ -1,0 +1,59 @@
+// Host-side launchers of the solver kernels (internal to libchflow; not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ch_common.cuh"
+
+namespace chf {
+
+// opt-in dynamic shared memory limit of one CTA on sm_103a
+constexpr int kSmemMax = 227 * 1024;
+
+// z-line kernel: one CTA per (mx, j) wavenumber line.
+//   mode 0: full step (forward DCT of the 10 non-linear fields, assembly, AB2, tau solves,
+//           state update, 7 backward fields);  mode 1: the 7 backward fields of the state only.
+// nl / bw hold fields of (Mx, Ny, Nz) complex samples in precision `prec` (0 fp64, 1 fp32),
+// field stride fs elements.
+cudaError_t launch_zline(int mode, int prec, const GridDev& g, const void* nl, void* bw,
+                         long long fs, double2* st_om, double2* st_w, double2* st_phi,
+                         double2* h_om, double2* h_w, double2* h_phi, int first,
+                         const FftPlan& pz, cudaStream_t s);
+size_t zline_smem(const GridDev& g);
+
+// Projection of four physical-z fields (u, v, w, phi as (Mx, Ny, Nz) complex, already
+// Fourier-transformed in x, y) onto the state (omega_z / mean flow, w, phi); zeroes history.
+cudaError_t launch_project(const GridDev& g, const double2* uvwp, long long fs, double2* st_om,
+                           double2* st_w, double2* st_phi, double2* h_om, double2* h_w,
+                           double2* h_phi, const FftPlan& pz, cudaStream_t s);
+
+// DCT-I of nf fields of (Mx, Ny, Nz) lines: dir 0 = samples -> coefficients (input precision
+// prec), dir 1 = coefficients -> samples (fp64 in and out).
+cudaError_t launch_dct_lines(int dir, int prec, const GridDev& g, const void* in, double2* out,
+                             int nf, long long fs, const FftPlan& pz, cudaStream_t s);
+
+// y-direction pass.  dir 1: (Mx, Ny, Nz) modes -> (Mx, P, Nz) samples (zero padding);
+// dir 0: (Mx, P, Nz) samples -> (Mx, Ny, Nz) modes (truncation, Nyquist row zeroed), times scale.
+cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void* in, void* out,
+                         int nf, long long fs_in, long long fs_out, double scale,
+                         const FftPlan& py, cudaStream_t s);
+
+// fused x-line kernel: 7 fields (Mx, Py, Nz) -> c2r (Px) -> 10 products -> r2c -> 10 fields.
+cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out10, long long fs,
+                         double scale, const FftPlan& px, cudaStream_t s);
+
+// plain x transforms on the unpadded grid (fp64): physical (Nz, Ny, Nx) <-> (Mx, Ny, Nz).
+cudaError_t launch_x_r2c(const GridDev& g, const double* phys, double2* out, int nf,
+                         long long fs_phys, long long fs_spec, const FftPlan& px,
+                         cudaStream_t s);
+cudaError_t launch_x_c2r(const GridDev& g, const double2* in, double* phys, int nf,
+                         long long fs_spec, long long fs_phys, const FftPlan& px,
+                         cudaStream_t s);
+
+// diagnostics reduction over the 7 physical unpadded fields u v w phi phix phiy phiz
+// (each (Nz, Ny, Nx)); out[0..8] as in ch_diag (t and step filled by the host).
+cudaError_t launch_diag(const GridDev& g, const double* phys7, long long fs,
+                        const double2* st_phi, const double* ccw, const double* dzl,
+                        const double* qint, double* part, double* out, cudaStream_t s);
+
+}  // namespace chf

@@ -1,0 +1,305 @@
+// Periodic-direction kernels: the y pass and the fused x-line kernel of the pseudo-spectral step.
+//
+// Paper Sec. 3.2.1: batched real-to-complex transforms along x and complex transforms along y
+// (3/2-rule zero padding on the way to physical space, truncation on the way back), and
+// Sec. 3.2.2: element-wise (Hadamard) products of collocated fields in physical space.  Here the
+// x transforms and the products are one kernel, so the padded physical fields live only in
+// shared memory and never reach HBM.
+//
+// Layout of every intermediate array: (mx, y or ky, z) with z fastest; a CTA owns a tile of
+// lines and does the layout change through shared memory.
+#include "ch_internal.h"
+
+namespace chf {
+
+namespace {
+
+constexpr int YT = 256;   // threads of a y-pass CTA
+constexpr int XT = 256;   // threads of an x-line CTA
+
+// y pass: one CTA per (z tile, mx, field).
+//   INV (backward): in (Mx, Ny, Nz) modes -> out (Mx, P, Nz) samples, modes |my| < Ny/2 placed,
+//   the rest zero.  Forward: in (Mx, P, Nz) samples -> out (Mx, Ny, Nz) kept modes * scale.
+template <typename T, bool INV>
+__global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __restrict__ in,
+                                                   typename C2<T>::t* __restrict__ out, int Mx,
+                                                   int Ny, int P, int Nz, int TZ, long long fs_in,
+                                                   long long fs_out, T scale, FftPlan pl) {
+  typedef typename C2<T>::t T2;
+  extern __shared__ unsigned char ysm_raw[];
+  T2* A = reinterpret_cast<T2*>(ysm_raw);
+  T2* B = A + TZ * P;
+  const int z0 = blockIdx.x * TZ;
+  const int mx = blockIdx.y;
+  const int f = blockIdx.z;
+  const int h = Ny / 2;
+  const T2 zero = mk((T)0, (T)0);
+  if (INV) {
+    const T2* src = in + f * fs_in + (size_t)mx * Ny * Nz;
+    for (int idx = threadIdx.x; idx < Ny * TZ; idx += blockDim.x) {
+      const int jj = idx / TZ, zz = idx - jj * TZ;
+      const int z = z0 + zz;
+      T2 v = zero;
+      if (z < Nz && jj != h) v = src[(size_t)jj * Nz + z];
+      const int p = (jj < h) ? jj : P - Ny + jj;
+      A[zz * P + p] = v;
+    }
+    for (int idx = threadIdx.x; idx < (P - Ny) * TZ; idx += blockDim.x) {
+      const int q = idx / TZ, zz = idx - q * TZ;
+      A[zz * P + h + q] = zero;  // positions h .. P-h-1 hold no mode
+    }
+  } else {
+    const T2* src = in + f * fs_in + (size_t)mx * P * Nz;
+    for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
+      const int y = idx / TZ, zz = idx - y * TZ;
+      const int z = z0 + zz;
+      A[zz * P + y] = (z < Nz) ? src[(size_t)y * Nz + z] : zero;
+    }
+  }
+  __syncthreads();
+  const T2* R = block_fft<T, INV>(A, B, TZ, P, pl);
+  if (INV) {
+    T2* dst = out + f * fs_out + (size_t)mx * P * Nz;
+    for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
+      const int y = idx / TZ, zz = idx - y * TZ;
+      const int z = z0 + zz;
+      if (z < Nz) dst[(size_t)y * Nz + z] = R[zz * P + y];
+    }
+  } else {
+    T2* dst = out + f * fs_out + (size_t)mx * Ny * Nz;
+    for (int idx = threadIdx.x; idx < Ny * TZ; idx += blockDim.x) {
+      const int jj = idx / TZ, zz = idx - jj * TZ;
+      const int z = z0 + zz;
+      if (z >= Nz) continue;
+      const int p = (jj < h) ? jj : P - Ny + jj;
+      dst[(size_t)jj * Nz + z] = (jj == h) ? zero : scale * R[zz * P + p];
+    }
+  }
+}
+
+// Fused x-line kernel.  One CTA per (pair of z rows, y).  The two rows z0, z0+1 of a field are
+// packed as one complex signal a + i b, so one complex FFT of length Px transforms both.
+//   1. seven inputs u, v, w, phi, phi_x, phi_y, phi_z: spectra (kx < Mx) -> c2r (zero padded);
+//   2. ten products Sigma_ij = -u_i u_j + kappa (|grad phi|^2 delta_ij - phi_i phi_j),
+//      phi^3, u phi, v phi, w phi at every padded point;
+//   3. r2c, keep kx < Mx, times `scale`.
+// Shared memory: 7 + 5 + 5 lines of Px complex values.
+template <typename T>
+__global__ void __launch_bounds__(XT) xline_kernel(const typename C2<T>::t* __restrict__ in,
+                                                   typename C2<T>::t* __restrict__ out, int Mx,
+                                                   int Px, int Py, int Nz, long long fs, T kappa,
+                                                   T scale, FftPlan pl) {
+  typedef typename C2<T>::t T2;
+  extern __shared__ unsigned char xsm_raw[];
+  T2* S = reinterpret_cast<T2*>(xsm_raw);
+  const int z0 = 2 * blockIdx.x;
+  const int y = blockIdx.y;
+  const bool two = (z0 + 1 < Nz);
+  const T2 zero = mk((T)0, (T)0);
+  const size_t base = (size_t)y * Nz + z0;
+  const size_t mstride = (size_t)Py * Nz;
+  // Start in S[0..6] for an even number of passes, in S[7..13] for an odd number, so that the
+  // seven physical lines always end in S[0..6] and S[7..16] (ten lines) are free afterwards.
+  T2* X = S;
+  T2* Y = S + 7 * Px;
+  T2* L0 = (pl.nst & 1) ? Y : X;
+  // ---- 1. packed spectra of the seven inputs
+  for (int idx = threadIdx.x; idx < 7 * Mx; idx += blockDim.x) {
+    const int f = idx / Mx, m = idx - f * Mx;
+    const T2* src = in + f * fs + (size_t)m * mstride + base;
+    const T2 a = src[0];
+    const T2 b = two ? src[1] : zero;
+    T2* L = L0 + f * Px;
+    if (m == 0) {
+      L[0] = mk(a.x, b.x);  // the imaginary part of a DC coefficient is not used by c2r
+    } else {
+      L[m] = mk(a.x - b.y, a.y + b.x);         // a + i b
+      L[Px - m] = mk(a.x + b.y, b.x - a.y);    // conj(a) + i conj(b)
+    }
+  }
+  {
+    const int w = Px - 2 * Mx + 1;  // kx = Mx .. Px - Mx carry no mode
+    for (int idx = threadIdx.x; idx < 7 * w; idx += blockDim.x) {
+      const int f = idx / w, q = idx - f * w;
+      L0[f * Px + Mx + q] = zero;
+    }
+  }
+  __syncthreads();
+  const T2* in7 = block_fft<T, true>(L0, (L0 == X) ? Y : X, 7, Px, pl);  // == X
+  T2* prod = S + 7 * Px;   // five product lines
+  T2* scr = S + 12 * Px;   // five scratch lines
+  for (int g0 = 0; g0 < 10; g0 += 5) {
+    // ---- 2. products for outputs g0 .. g0+4 (rows z0 in .x, z0+1 in .y)
+    for (int x = threadIdx.x; x < Px; x += blockDim.x) {
+      const T2 u = in7[x], v = in7[Px + x], w = in7[2 * Px + x], ph = in7[3 * Px + x];
+      const T2 fx = in7[4 * Px + x], fy = in7[5 * Px + x], fz = in7[6 * Px + x];
+      const T g2x = fx.x * fx.x + fy.x * fy.x + fz.x * fz.x;
+      const T g2y = fx.y * fx.y + fy.y * fy.y + fz.y * fz.y;
+      T2 o[5];
+      if (g0 == 0) {
+        o[0] = mk(-u.x * u.x + kappa * (g2x - fx.x * fx.x), -u.y * u.y + kappa * (g2y - fx.y * fx.y));
+        o[1] = mk(-v.x * v.x + kappa * (g2x - fy.x * fy.x), -v.y * v.y + kappa * (g2y - fy.y * fy.y));
+        o[2] = mk(-w.x * w.x + kappa * (g2x - fz.x * fz.x), -w.y * w.y + kappa * (g2y - fz.y * fz.y));
+        o[3] = mk(-u.x * v.x - kappa * fx.x * fy.x, -u.y * v.y - kappa * fx.y * fy.y);
+        o[4] = mk(-u.x * w.x - kappa * fx.x * fz.x, -u.y * w.y - kappa * fx.y * fz.y);
+      } else {
+        o[0] = mk(-v.x * w.x - kappa * fy.x * fz.x, -v.y * w.y - kappa * fy.y * fz.y);
+        o[1] = mk(ph.x * ph.x * ph.x, ph.y * ph.y * ph.y);
+        o[2] = mk(u.x * ph.x, u.y * ph.y);
+        o[3] = mk(v.x * ph.x, v.y * ph.y);
+        o[4] = mk(w.x * ph.x, w.y * ph.y);
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) prod[q * Px + x] = o[q];
+    }
+    __syncthreads();
+    const T2* R = block_fft<T, false>(prod, scr, 5, Px, pl);
+    // ---- 3. unpack: A_k = (Z_k + conj Z_{-k}) / 2, B_k = (Z_k - conj Z_{-k}) / (2 i)
+    const T hs = (T)0.5 * scale;
+    for (int idx = threadIdx.x; idx < 5 * Mx; idx += blockDim.x) {
+      const int q = idx / Mx, m = idx - q * Mx;
+      const T2 Zk = R[q * Px + m];
+      const T2 Zm = R[q * Px + (m == 0 ? 0 : Px - m)];
+      T2* dst = out + (g0 + q) * fs + (size_t)m * mstride + base;
+      dst[0] = mk(hs * (Zk.x + Zm.x), hs * (Zk.y - Zm.y));
+      if (two) dst[1] = mk(hs * (Zk.y + Zm.y), hs * (Zm.x - Zk.x));
+    }
+    __syncthreads();
+  }
+}
+
+// plain r2c along x of physical rows (Nz, Ny, Nx) -> (Mx, Ny, Nz); two z rows per CTA
+__global__ void __launch_bounds__(128) x_r2c_kernel(const double* __restrict__ phys,
+                                                    double2* __restrict__ out, int Nx, int Ny,
+                                                    int Nz, long long fs_phys, long long fs_spec,
+                                                    FftPlan pl) {
+  extern __shared__ double2 xs[];
+  double2* A = xs;
+  double2* B = xs + Nx;
+  const int z0 = 2 * blockIdx.x, y = blockIdx.y, f = blockIdx.z;
+  const bool two = (z0 + 1 < Nz);
+  const int Mx = Nx / 2;
+  const double* r0 = phys + f * fs_phys + ((size_t)z0 * Ny + y) * Nx;
+  const double* r1 = r0 + (size_t)Ny * Nx;
+  for (int x = threadIdx.x; x < Nx; x += blockDim.x) A[x] = make_double2(r0[x], two ? r1[x] : 0.0);
+  __syncthreads();
+  const double2* R = block_fft<double, false>(A, B, 1, Nx, pl);
+  double2* dst = out + f * fs_spec + (size_t)y * Nz + z0;
+  for (int m = threadIdx.x; m < Mx; m += blockDim.x) {
+    const double2 Zk = R[m], Zm = R[m == 0 ? 0 : Nx - m];
+    dst[(size_t)m * Ny * Nz] = make_double2(0.5 * (Zk.x + Zm.x), 0.5 * (Zk.y - Zm.y));
+    if (two) dst[(size_t)m * Ny * Nz + 1] = make_double2(0.5 * (Zk.y + Zm.y), 0.5 * (Zm.x - Zk.x));
+  }
+}
+
+// plain c2r along x: (Mx, Ny, Nz) -> physical rows (Nz, Ny, Nx)
+__global__ void __launch_bounds__(128) x_c2r_kernel(const double2* __restrict__ in,
+                                                    double* __restrict__ phys, int Nx, int Ny,
+                                                    int Nz, long long fs_spec, long long fs_phys,
+                                                    FftPlan pl) {
+  extern __shared__ double2 xs[];
+  double2* A = xs;
+  double2* B = xs + Nx;
+  const int z0 = 2 * blockIdx.x, y = blockIdx.y, f = blockIdx.z;
+  const bool two = (z0 + 1 < Nz);
+  const int Mx = Nx / 2;
+  const double2* src = in + f * fs_spec + (size_t)y * Nz + z0;
+  for (int m = threadIdx.x; m < Mx; m += blockDim.x) {
+    const double2 a = src[(size_t)m * Ny * Nz];
+    const double2 b = two ? src[(size_t)m * Ny * Nz + 1] : make_double2(0.0, 0.0);
+    if (m == 0) {
+      A[0] = make_double2(a.x, b.x);
+      A[Mx] = make_double2(0.0, 0.0);  // x Nyquist
+    } else {
+      A[m] = make_double2(a.x - b.y, a.y + b.x);
+      A[Nx - m] = make_double2(a.x + b.y, b.x - a.y);
+    }
+  }
+  __syncthreads();
+  const double2* R = block_fft<double, true>(A, B, 1, Nx, pl);
+  double* r0 = phys + f * fs_phys + ((size_t)z0 * Ny + y) * Nx;
+  double* r1 = r0 + (size_t)Ny * Nx;
+  for (int x = threadIdx.x; x < Nx; x += blockDim.x) {
+    r0[x] = R[x].x;
+    if (two) r1[x] = R[x].y;
+  }
+}
+
+int ytile(int P, size_t elem) {
+  // z tile: 8 columns (128 B of fp64 complex), fewer when the lines are long
+  int tz = 8;
+  while (tz > 1 && (size_t)2 * tz * P * elem > 160 * 1024) tz /= 2;
+  return tz;
+}
+
+}  // namespace
+
+cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void* in, void* out,
+                         int nf, long long fs_in, long long fs_out, double scale,
+                         const FftPlan& py, cudaStream_t s) {
+  const size_t elem = prec == 0 ? sizeof(double2) : sizeof(float2);
+  const int TZ = ytile(P, elem);
+  const size_t smem = (size_t)2 * TZ * P * elem;
+  dim3 grid((g.nz + TZ - 1) / TZ, g.Mx, nf);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(ypass_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(ypass_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(ypass_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(ypass_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
+    attr = true;
+  }
+#define YL(T, INV)                                                                            \
+  ypass_kernel<T, INV><<<grid, YT, smem, s>>>((const C2<T>::t*)in, (C2<T>::t*)out, g.Mx, g.ny, \
+                                              P, g.nz, TZ, fs_in, fs_out, (T)scale, py);
+  if (prec == 0) {
+    if (dir == 1) { YL(double, true) } else { YL(double, false) }
+  } else {
+    if (dir == 1) { YL(float, true) } else { YL(float, false) }
+  }
+#undef YL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out10, long long fs,
+                         double scale, const FftPlan& px, cudaStream_t s) {
+  const size_t elem = prec == 0 ? sizeof(double2) : sizeof(float2);
+  const size_t smem = (size_t)17 * g.Px * elem;
+  dim3 grid((g.nz + 1) / 2, g.Py);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(xline_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(xline_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
+    attr = true;
+  }
+  if (prec == 0) {
+    xline_kernel<double><<<grid, XT, smem, s>>>((const double2*)in7, (double2*)out10, g.Mx, g.Px,
+                                                g.Py, g.nz, fs, g.kappa, scale, px);
+  } else {
+    xline_kernel<float><<<grid, XT, smem, s>>>((const float2*)in7, (float2*)out10, g.Mx, g.Px,
+                                               g.Py, g.nz, fs, (float)g.kappa, (float)scale, px);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x_r2c(const GridDev& g, const double* phys, double2* out, int nf,
+                         long long fs_phys, long long fs_spec, const FftPlan& px,
+                         cudaStream_t s) {
+  dim3 grid((g.nz + 1) / 2, g.ny, nf);
+  x_r2c_kernel<<<grid, 128, 2 * g.nx * sizeof(double2), s>>>(phys, out, g.nx, g.ny, g.nz, fs_phys,
+                                                             fs_spec, px);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x_c2r(const GridDev& g, const double2* in, double* phys, int nf,
+                         long long fs_spec, long long fs_phys, const FftPlan& px,
+                         cudaStream_t s) {
+  dim3 grid((g.nz + 1) / 2, g.ny, nf);
+  x_c2r_kernel<<<grid, 128, 2 * g.nx * sizeof(double2), s>>>(in, phys, g.nx, g.ny, g.nz, fs_spec,
+                                                             fs_phys, px);
+  return cudaGetLastError();
+}
+
+}  // namespace chf

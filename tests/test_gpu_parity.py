@@ -1,0 +1,227 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerance (FP64 path): max relative field error max|a - b| / max|b| per field of at most 1e-10
+after 10 steps (u, v, w, phi on the unpadded grid); single-stage comparisons are held to the
+rounding level of the stage (1e-12 relative).  Inputs come from the seeded generators.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.channel import Channel, Params  # noqa: E402
+from paper_2406_01322_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def binding():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_01322_gb300 import build
+    build.build_library()
+    from paper_2406_01322_gb300 import binding as b
+    b.lib()
+    return b
+
+
+def workload(name, **over):
+    w = dict(inputs.WORKLOADS[name])
+    w.update(over)
+    return w
+
+
+def phys_kw(w):
+    return dict(re_tau=w["re_tau"], we=w["we"], ch=w["ch"], pe=w["pe"], dt=w["dt"])
+
+
+def make_pair(binding, w, precision=0, fields=None):
+    if fields is None:
+        fields = inputs.initial_fields(**w)
+    g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=precision, **phys_kw(w))
+    g.set_fields(*[torch.from_numpy(f) for f in fields])
+    o = Channel(Params(nx=w["nx"], ny=w["ny"], nz=w["nz"], **phys_kw(w)))
+    o.set_fields(*fields)
+    return g, o
+
+
+def spec_to_oracle(t):
+    """(Mx, Ny, Nz) device complex tensor -> (Nz, Ny, Mx) numpy (oracle layout)."""
+    return t.cpu().numpy().transpose(2, 1, 0)
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+SIZES = [
+    ("channel_32x32x33", {}),
+    ("channel_32x32x33", dict(nx=24, ny=18, nz=17)),    # radix-3 lengths, ragged z tile
+    ("channel_32x32x33", dict(nx=16, ny=36, nz=25)),    # Py = 54, N = 24
+]
+
+
+@pytest.mark.parametrize("name,over", SIZES)
+def test_transform_forward_backward(binding, name, over):
+    w = workload(name, **over)
+    g, o = make_pair(binding, w)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((w["nz"], w["ny"], w["nx"]))
+    spec = g.transform_forward(torch.from_numpy(f))
+    ref = o.physical_to_spectral(f)
+    assert rel(spec_to_oracle(spec), ref) < 1e-13
+    back = g.transform_backward(spec).cpu().numpy()
+    assert rel(back, o.spectral_to_physical(ref)) < 1e-13
+
+
+@pytest.mark.parametrize("name,over", SIZES)
+def test_set_fields_projection(binding, name, over):
+    w = workload(name, **over)
+    g, o = make_pair(binding, w)
+    om, ww, ph = g.get_spectral()
+    assert rel(spec_to_oracle(om), o.omega) < 1e-13
+    assert rel(spec_to_oracle(ww), o.w) < 1e-13
+    assert rel(spec_to_oracle(ph), o.phi) < 1e-13
+    for a, b in zip(g.get_fields(), o.get_fields()):
+        assert rel(a.cpu().numpy(), b) < 1e-13
+
+
+@pytest.mark.parametrize("name,over", SIZES)
+def test_nonlinear_terms(binding, name, over):
+    w = workload(name, **over)
+    g, o = make_pair(binding, w)
+    got = g.nonlinear()
+    ref = o.nonlinear_spectral()
+    for k in range(10):
+        assert rel(spec_to_oracle(got[k]), ref[k]) < 1e-12, k
+
+
+@pytest.mark.parametrize("name,over", SIZES)
+def test_one_step_state(binding, name, over):
+    w = workload(name, **over)
+    g, o = make_pair(binding, w)
+    g.step(1)
+    o.step()
+    om, ww, ph = g.get_spectral()
+    assert rel(spec_to_oracle(om), o.omega) < 1e-11
+    assert rel(spec_to_oracle(ww), o.w) < 1e-11
+    assert rel(spec_to_oracle(ph), o.phi) < 1e-11
+
+
+@pytest.mark.parametrize("name,over", SIZES)
+def test_ten_steps_fp64_within_1e_10(binding, name, over):
+    w = workload(name, **over)
+    g, o = make_pair(binding, w)
+    g.step(10)
+    for _ in range(10):
+        o.step()
+    for a, b, f in zip(g.get_fields(), o.get_fields(), "uvwp"):
+        assert rel(a.cpu().numpy(), b) <= 1e-10, f
+
+
+def test_diagnostics_match_oracle(binding):
+    w = workload("channel_32x32x33")
+    g, o = make_pair(binding, w)
+    g.step(3)
+    for _ in range(3):
+        o.step()
+    d = g.diagnostics()
+    r = o.diagnostics()
+    assert d["step"] == 3 and d["nan"] == 0
+    for k in ("mass", "kinetic", "grad2", "free_energy", "cfl", "max_phi"):
+        assert math.isclose(d[k], r[k], rel_tol=1e-10, abs_tol=1e-12), k
+
+
+def test_poiseuille_fixed_point_on_gpu(binding):
+    w = workload("channel_32x32x33")
+    nz, ny, nx = w["nz"], w["ny"], w["nx"]
+    z = np.cos(np.pi * np.arange(nz) / (nz - 1))
+    u = np.broadcast_to((0.5 * w["re_tau"] * (1 - z * z))[:, None, None], (nz, ny, nx)).copy()
+    zero = np.zeros((nz, ny, nx))
+    g = binding.Grid(nx, ny, nz, **phys_kw(w))
+    g.set_fields(*[torch.from_numpy(a) for a in (u, zero, zero, zero - 1.0)])
+    g.step(20)
+    uu, vv, ww, pp = [t.cpu().numpy() for t in g.get_fields()]
+    assert rel(uu, u) < 1e-13
+    assert np.max(np.abs(vv)) < 1e-12 and np.max(np.abs(ww)) < 1e-12
+    assert np.max(np.abs(pp + 1.0)) < 1e-14
+
+
+def test_checkpoint_resume_is_bitwise(binding):
+    w = workload("channel_32x32x33", nx=24, ny=18, nz=17)
+    g, _ = make_pair(binding, w)
+    g.step(3)
+    st = g.get_state()
+    g.step(4)
+    a = [t.clone() for t in g.get_fields()]
+    g.set_state(st)
+    g.step(4)
+    b = g.get_fields()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_host_entry_points_match_device(binding):
+    w = workload("channel_32x32x33", nx=24, ny=18, nz=17)
+    fields = inputs.initial_fields(**w)
+    g = binding.Grid(w["nx"], w["ny"], w["nz"], **phys_kw(w))
+    g.set_fields_host(*fields)
+    g.step(2)
+    h = g.get_fields_host()
+    d = g.get_fields()
+    for x, y in zip(h, d):
+        assert torch.equal(x, y.cpu())
+
+
+def test_mixed_precision_error_bounds(binding):
+    w = workload("channel_32x32x33")
+    fields = inputs.initial_fields(**w)
+    g64, o = make_pair(binding, w, 0, fields)
+    g32, _ = make_pair(binding, w, 1, fields)
+    g64.step(10)
+    g32.step(10)
+    for _ in range(10):
+        o.step()
+    for a, b, c, f in zip(g32.get_fields(), g64.get_fields(), o.get_fields(), "uvwp"):
+        e = rel(a.cpu().numpy(), b.cpu().numpy())
+        assert e < 1e-4, (f, e)
+        assert rel(b.cpu().numpy(), c) < 1e-10
+    d32, d64 = g32.diagnostics(), g64.diagnostics()
+    assert abs(d32["mass"] - d64["mass"]) <= 1e-6 * abs(d64["mass"])
+
+
+def test_error_codes(binding):
+    with pytest.raises(binding.ChError) as e:
+        binding.Grid(10, 16, 17)            # 10 = 2 * 5 is not {2,3}-smooth
+    assert e.value.code == -2
+    with pytest.raises(binding.ChError) as e:
+        binding.Grid(16, 16, 18)            # nz - 1 odd
+    assert e.value.code == -2
+    with pytest.raises(binding.ChError) as e:
+        binding.Grid(16, 16, 17, dt=0.0)
+    assert e.value.code == -1
+    g = binding.Grid(16, 16, 17)
+    with pytest.raises(binding.ChError) as e:
+        g.step(1)                           # no fields yet
+    assert e.value.code == -7
+
+
+def test_medium_channel_one_step_sampled_lines(binding):
+    """128x128x129 workload: one GPU step against the oracle on a sample of wavenumber lines
+    (the oracle forms every non-linear term but solves only the sampled lines)."""
+    w = workload("channel_128x128x129")
+    g, o = make_pair(binding, w)
+    g.step(1)
+    rng = np.random.default_rng(3)
+    lines = [(0, 0), (1, 0), (0, 1), (w["ny"] - 1, 0), (5, 7), (w["ny"] // 2 + 3, 63)]
+    lines += [(int(rng.integers(0, w["ny"])), int(rng.integers(0, w["nx"] // 2))) for _ in range(10)]
+    lines = [(j, m) for (j, m) in lines if j != w["ny"] // 2]
+    res = o.step(lines=lines)
+    om, ww, ph = (spec_to_oracle(t) for t in g.get_spectral())
+    for (j, m), (a, b, c) in res.items():
+        for got, ref in ((om[:, j, m], a), (ww[:, j, m], b), (ph[:, j, m], c)):
+            scale = max(np.max(np.abs(ref)), 1e-300)
+            assert np.max(np.abs(got - ref)) / scale < 1e-10, (j, m)
