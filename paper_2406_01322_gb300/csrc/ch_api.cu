@@ -24,7 +24,7 @@ using chf::GridDev;
 
 namespace {
 
-const int kMaxSmem = 227 * 1024;
+const int kMaxSmem = 227 * 1024 - 1024;  // opt-in limit less room for static shared memory
 
 struct Tw {
   void* d64 = nullptr;  // double2[n]
@@ -67,6 +67,7 @@ struct ch_grid {
   double t;
   cudaGraphExec_t gexec;
   int graph_ok;
+  cudaStream_t cap;  // private non-blocking stream used only to capture the step graph
 };
 
 namespace {
@@ -143,7 +144,10 @@ int make_plan(ch_grid* G, int n, int prec, FftPlan* pl) {
 #define CK(x)                                       \
   do {                                              \
     cudaError_t e__ = (x);                          \
-    if (e__ != cudaSuccess) return CH_ERR_CUDA;     \
+    if (e__ != cudaSuccess) {                       \
+      cudaGetLastError();                           \
+      return CH_ERR_CUDA;                           \
+    }                                               \
   } while (0)
 
 // non-linear terms of the current state: bw <- 7 fields; ya <- y backward; yb <- x line;
@@ -160,9 +164,8 @@ int eval_nonlinear(ch_grid* G) {
   return CH_OK;
 }
 
-int launch_step(ch_grid* G, int first) {
+int launch_step(ch_grid* G, int first, cudaStream_t s) {
   const GridDev& g = G->g;
-  cudaStream_t s = G->stream;
   CK(chf::launch_zline(0, G->prec, g, G->nl, G->bw, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
                        G->hphi, first, G->pz, s));
   CK(chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s));
@@ -181,6 +184,14 @@ int state_to_phys7(ch_grid* G, int nf) {
   CK(chf::launch_ypass(1, 0, g, g.ny, G->auxA, G->auxB, nf, G->fs, G->fs, 1.0, G->pyu, s));
   CK(chf::launch_x_c2r(g, G->auxB, G->phys7, nf, G->fs, G->fsp, G->pxu, s));
   return CH_OK;
+}
+
+// failure exit of ch_init_grid: free what was obtained so far
+int bail(ch_grid* G, int code) {
+  release_all(G);
+  cudaStreamDestroy(G->cap);
+  delete G;
+  return code;
 }
 
 void drop_graph(ch_grid* G) {
@@ -233,6 +244,10 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   G->actx = alloc_ctx;
   G->gexec = nullptr;
   G->graph_ok = 0;
+  if (cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    delete G;
+    return CH_ERR_CUDA;
+  }
   GridDev& g = G->g;
   g.nx = nx;
   g.ny = ny;
@@ -283,9 +298,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   G->diag_part = (double*)A((size_t)(304 * 6 + 16) * sizeof(double));
   G->diag_out = G->diag_part + 304 * 6;
   if (st != CH_OK) {
-    release_all(G);
-    delete G;
-    return st;
+    return bail(G, st);
   }
   // plans
   int e = CH_OK;
@@ -297,9 +310,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   if (e == CH_OK) e = make_plan(G, nx, 0, &G->pxu);
   if (e == CH_OK) e = make_plan(G, ny, 0, &G->pyu);
   if (e != CH_OK) {
-    release_all(G);
-    delete G;
-    return e;
+    return bail(G, e);
   }
   // tables: Gottlieb-Orszag rows, Clenshaw-Curtis weights, local z spacing, integrals of T_n
   {
@@ -335,18 +346,14 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
     dzl[0] = z[0] - z[1];
     dzl[N] = z[N - 1] - z[N];
     if (cudaMemcpy(G->tab, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-      release_all(G);
-      delete G;
-      return CH_ERR_CUDA;
+      return bail(G, CH_ERR_CUDA);
     }
     g.go1 = G->tab;
     g.go2 = G->tab + nz;
     g.go3 = G->tab + 2 * nz;
   }
   if (chf::zline_smem(g) > (size_t)kMaxSmem || (size_t)17 * g.Px * sizeof(double2) > (size_t)kMaxSmem) {
-    release_all(G);
-    delete G;
-    return CH_ERR_SIZE;
+    return bail(G, CH_ERR_SIZE);
   }
   G->first = 1;
   G->fields_set = 0;
@@ -354,14 +361,10 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   G->t = 0.0;
   for (double2* q : {G->om, G->w, G->phi, G->hom, G->hw, G->hphi})
     if (cudaMemset(q, 0, sb) != cudaSuccess) {
-      release_all(G);
-      delete G;
-      return CH_ERR_CUDA;
+      return bail(G, CH_ERR_CUDA);
     }
   if (cudaDeviceSynchronize() != cudaSuccess) {
-    release_all(G);
-    delete G;
-    return CH_ERR_CUDA;
+    return bail(G, CH_ERR_CUDA);
   }
   *out = G;
   return CH_OK;
@@ -413,16 +416,21 @@ int ch_step(ch_grid* G, int nsteps) {
   if (!G->fields_set) return CH_ERR_STATE;
   for (int i = 0; i < nsteps; ++i) {
     if (G->first) {
-      int r = launch_step(G, 1);
+      int r = launch_step(G, 1, G->stream);
       if (r != CH_OK) return r;
       G->first = 0;
     } else {
       if (!G->graph_ok) {
+        // capture on the private stream (the caller's stream may be the legacy default
+        // stream, which cannot be captured); the graph is then launched on the caller's stream
         cudaGraph_t graph;
-        CK(cudaStreamBeginCapture(G->stream, cudaStreamCaptureModeThreadLocal));
-        int r = launch_step(G, 0);
-        cudaError_t e = cudaStreamEndCapture(G->stream, &graph);
-        if (r != CH_OK || e != cudaSuccess) return CH_ERR_CUDA;
+        CK(cudaStreamBeginCapture(G->cap, cudaStreamCaptureModeThreadLocal));
+        int r = launch_step(G, 0, G->cap);
+        cudaError_t e = cudaStreamEndCapture(G->cap, &graph);
+        if (r != CH_OK || e != cudaSuccess) {
+          cudaGetLastError();
+          return CH_ERR_CUDA;
+        }
         e = cudaGraphInstantiate(&G->gexec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return CH_ERR_CUDA;
@@ -646,6 +654,7 @@ void ch_destroy(ch_grid* G) {
   cudaStreamSynchronize(G->stream);
   drop_graph(G);
   release_all(G);
+  cudaStreamDestroy(G->cap);
   delete G;
 }
 

@@ -7,8 +7,20 @@
 
 namespace chf {
 
-// opt-in dynamic shared memory limit of one CTA on sm_103a
-constexpr int kSmemMax = 227 * 1024;
+// Raise a kernel's dynamic shared-memory limit to `bytes` if it is below that.  The limit is
+// per kernel; *cur remembers what was set.  Never called while a stream is being captured (the
+// first, uncaptured launch of every size comes first).
+template <typename K>
+inline cudaError_t ensure_smem(K* kernel, size_t bytes, int* cur) {
+  if ((int)bytes <= *cur || bytes <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // do not leave a non-sticky error behind
+    return e;
+  }
+  *cur = (int)bytes;
+  return cudaSuccess;
+}
 
 // z-line kernel: one CTA per (mx, j) wavenumber line.
 //   mode 0: full step (forward DCT of the 10 non-linear fields, assembly, AB2, tau solves,

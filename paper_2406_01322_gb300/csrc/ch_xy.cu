@@ -241,15 +241,13 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
   const int TZ = ytile(P, elem);
   const size_t smem = (size_t)2 * TZ * P * elem;
   dim3 grid((g.nz + TZ - 1) / TZ, g.Mx, nf);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(ypass_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(ypass_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(ypass_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(ypass_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
-    attr = true;
-  }
+  static int cur[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaSuccess;
+  if (prec == 0) e = dir == 1 ? ensure_smem(ypass_kernel<double, true>, smem, &cur[0])
+                              : ensure_smem(ypass_kernel<double, false>, smem, &cur[1]);
+  else e = dir == 1 ? ensure_smem(ypass_kernel<float, true>, smem, &cur[2])
+                    : ensure_smem(ypass_kernel<float, false>, smem, &cur[3]);
+  if (e != cudaSuccess) return e;
 #define YL(T, INV)                                                                            \
   ypass_kernel<T, INV><<<grid, YT, smem, s>>>((const C2<T>::t*)in, (C2<T>::t*)out, g.Mx, g.ny, \
                                               P, g.nz, TZ, fs_in, fs_out, (T)scale, py);
@@ -267,13 +265,10 @@ cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out1
   const size_t elem = prec == 0 ? sizeof(double2) : sizeof(float2);
   const size_t smem = (size_t)17 * g.Px * elem;
   dim3 grid((g.nz + 1) / 2, g.Py);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(xline_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(xline_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax)) != cudaSuccess) return e;
-    attr = true;
-  }
+  static int cur64 = 0, cur32 = 0;
+  cudaError_t e = prec == 0 ? ensure_smem(xline_kernel<double>, smem, &cur64)
+                            : ensure_smem(xline_kernel<float>, smem, &cur32);
+  if (e != cudaSuccess) return e;
   if (prec == 0) {
     xline_kernel<double><<<grid, XT, smem, s>>>((const double2*)in7, (double2*)out10, g.Mx, g.Px,
                                                 g.Py, g.nz, fs, g.kappa, scale, px);

@@ -581,13 +581,9 @@ static cudaError_t launch_zline_t(const GridDev& g, const void* nl, void* bw, lo
                                   cudaStream_t s) {
   typedef typename C2<T>::t T2;
   const size_t smem = zline_smem(g);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(zline_kernel<T, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static int cur = 0;
+  cudaError_t e = ensure_smem(zline_kernel<T, MODE>, smem, &cur);
+  if (e != cudaSuccess) return e;
   zline_kernel<T, MODE><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const T2*)nl, (T2*)bw, fs, st_om, st_w,
                                                      st_phi, h_om, h_w, h_phi, first, pz);
   return cudaGetLastError();
@@ -611,13 +607,9 @@ cudaError_t launch_project(const GridDev& g, const double2* uvwp, long long fs, 
                            double2* st_w, double2* st_phi, double2* h_om, double2* h_w,
                            double2* h_phi, const FftPlan& pz, cudaStream_t s) {
   const size_t smem = zline_smem(g);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemMax);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static int cur = 0;
+  cudaError_t e = ensure_smem(project_kernel, smem, &cur);
+  if (e != cudaSuccess) return e;
   project_kernel<<<g.Mx * g.ny, ZT, smem, s>>>(g, uvwp, fs, st_om, st_w, st_phi, h_om, h_w, h_phi, pz);
   return cudaGetLastError();
 }
@@ -625,14 +617,10 @@ cudaError_t launch_project(const GridDev& g, const double2* uvwp, long long fs, 
 cudaError_t launch_dct_lines(int dir, int prec, const GridDev& g, const void* in, double2* out,
                              int nf, long long fs, const FftPlan& pz, cudaStream_t s) {
   const size_t smem = zline_smem(g);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(dct_lines_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(dct_lines_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static int cur64 = 0, cur32 = 0;
+  cudaError_t e = ensure_smem(dct_lines_kernel<double>, smem, &cur64);
+  if (e == cudaSuccess) e = ensure_smem(dct_lines_kernel<float>, smem, &cur32);
+  if (e != cudaSuccess) return e;
   if (prec == 0) {
     dct_lines_kernel<double><<<g.Mx * g.ny, ZT, smem, s>>>(g, dir, (const double2*)in, out, nf, fs, pz);
   } else {
