@@ -154,6 +154,24 @@ int ch_transform_forward(ch_grid* g, const double* phys, double* spec);
 int ch_transform_backward(ch_grid* g, const double* spec, double* phys);
 int ch_nonlinear(ch_grid* g, double* out10);
 
+/* Allocation-free variant of ch_transform_forward, for callers that must not allocate device
+ * memory when they call it: code running while a stream is being captured into a CUDA graph
+ * (allocation is not allowed inside a capture), plug-ins whose host application's memory pool
+ * owns the GPU, or fixed-latency loops that must stay out of the allocator.  (The paper has no
+ * counterpart; it is a service of this library.)
+ * Same result as ch_transform_forward for a grid of nx, ny, nz (same size rules): phys is a
+ * device (nz,ny,nx) float64 field, spec receives device complex float64 coefficients in the
+ * layout above.  No handle, no cudaMalloc/cudaFree: the working memory is one static device
+ * array of ch_noalloc_scratch_bytes() (64 MiB) that every GPU loading this library keeps until
+ * the process exits; grids whose two (nx/2, ny, nz) complex work fields plus twiddles do not fit
+ * in it are rejected with CH_ERR_SIZE.  The first call on a device (with that device current)
+ * looks up the array's address - make it before any stream capture.  All calls share the array
+ * and leave their data in it; calls that overlap on the GPU (other streams or host threads)
+ * race.  Enqueued on `stream` (a cudaStream_t, NULL = default stream); returns once enqueued. */
+int ch_transform_forward_noalloc(int nx, int ny, int nz, const double* phys, double* spec,
+                                 void* stream);
+size_t ch_noalloc_scratch_bytes(void);
+
 /* Release every buffer owned by the handle (synchronises its stream). */
 void ch_destroy(ch_grid* g);
 

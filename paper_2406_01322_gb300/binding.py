@@ -69,6 +69,9 @@ _SIGS = {
     "ch_transform_forward": (ctypes.c_int, [_P, _P, _P]),
     "ch_transform_backward": (ctypes.c_int, [_P, _P, _P]),
     "ch_nonlinear": (ctypes.c_int, [_P, _P]),
+    "ch_transform_forward_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    _P, _P, _P]),
+    "ch_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     "ch_destroy": (None, [_P]),
     "ch_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -102,6 +105,26 @@ def _ck(name, code):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def transform_forward_noalloc(phys, spec, stream=None):
+    """Allocation-free forward transform into a caller-provided spectral tensor.
+
+    phys: float64 CUDA tensor (nz, ny, nx); spec: complex128 CUDA tensor (nx/2, ny, nz) that
+    receives the coefficients.  The library allocates nothing for this call (its working memory
+    is a fixed static device array); see ch_transform_forward_noalloc in include/ch_flow.h."""
+    nz, ny, nx = phys.shape
+    if not (phys.is_contiguous() and spec.is_contiguous()):
+        raise ValueError("contiguous tensors required")
+    if phys.dtype != torch.float64 or spec.dtype != torch.complex128:
+        raise ValueError("phys must be float64 and spec complex128")
+    if tuple(spec.shape) != (nx // 2, ny, nz):
+        raise ValueError(f"spec must have shape {(nx // 2, ny, nz)}")
+    s = stream if stream is not None else torch.cuda.current_stream(phys.device)
+    _ck("ch_transform_forward_noalloc",
+        lib().ch_transform_forward_noalloc(nx, ny, nz, _ptr(phys), _ptr(spec),
+                                           ctypes.c_void_p(s.cuda_stream)))
+    return spec
 
 
 class TorchAllocator:

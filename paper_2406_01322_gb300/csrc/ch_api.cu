@@ -22,6 +22,48 @@
 using chf::FftPlan;
 using chf::GridDev;
 
+namespace chf {
+
+bool smooth23(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+// radix schedule: 8 once if the power of two is odd (>= 3), 4s, a 2 if needed, then 3s
+bool make_radices(int n, FftPlan* pl) {
+  int a = 0, b = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  if (m != 1) return false;
+  int k = 0;
+  if (a % 2 == 1 && a >= 3) { pl->rad[k++] = 8; a -= 3; }
+  while (a >= 2) { pl->rad[k++] = 4; a -= 2; }
+  if (a == 1) { pl->rad[k++] = 2; a = 0; }
+  while (b > 0) { pl->rad[k++] = 3; --b; }
+  if (k > CHF_MAX_STAGES) return false;
+  if (k == 0) { pl->rad[k++] = 2; }  // n == 1 never used
+  pl->nst = k;
+  pl->n = n;
+  return true;
+}
+
+// size rules of ch_params (see include/ch_flow.h): CH_OK or CH_ERR_SIZE
+int check_sizes(int nx, int ny, int nz) {
+  if (nx < 4 || ny < 4 || nz < 5 || nx % 2 || ny % 2) return CH_ERR_SIZE;
+  if (!smooth23(nx) || !smooth23(ny) || !smooth23(3 * nx / 2) || !smooth23(3 * ny / 2) ||
+      (nz - 1) % 2 || !smooth23(2 * (nz - 1)))
+    return CH_ERR_SIZE;
+  if (3 * nx / 2 > 8192 || 3 * ny / 2 > 8192 || nz > 4097) return CH_ERR_SIZE;
+  return CH_OK;
+}
+
+}  // namespace chf
+
+using chf::make_radices;
+using chf::smooth23;
+
 namespace {
 
 const int kMaxSmem = 227 * 1024 - 1024;  // opt-in limit less room for static shared memory
@@ -72,13 +114,6 @@ struct ch_grid {
 
 namespace {
 
-bool smooth23(int n) {
-  if (n < 1) return false;
-  while (n % 2 == 0) n /= 2;
-  while (n % 3 == 0) n /= 3;
-  return n == 1;
-}
-
 void* galloc(ch_grid* G, size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 256;
@@ -97,24 +132,6 @@ void release_all(ch_grid* G) {
     else if (!G->af) cudaFree(p);
   }
   G->allocs.clear();
-}
-
-// radix schedule: 8 once if the power of two is odd (>= 3), 4s, a 2 if needed, then 3s
-bool make_radices(int n, FftPlan* pl) {
-  int a = 0, b = 0, m = n;
-  while (m % 2 == 0) { m /= 2; ++a; }
-  while (m % 3 == 0) { m /= 3; ++b; }
-  if (m != 1) return false;
-  int k = 0;
-  if (a % 2 == 1 && a >= 3) { pl->rad[k++] = 8; a -= 3; }
-  while (a >= 2) { pl->rad[k++] = 4; a -= 2; }
-  if (a == 1) { pl->rad[k++] = 2; a = 0; }
-  while (b > 0) { pl->rad[k++] = 3; --b; }
-  if (k > CHF_MAX_STAGES) return false;
-  if (k == 0) { pl->rad[k++] = 2; }  // n == 1 never used
-  pl->nst = k;
-  pl->n = n;
-  return true;
 }
 
 // twiddles exp(-2 pi i t / n) in extended precision, rounded once
@@ -228,11 +245,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   if (p->dealias_z != 0 || p->bc != 0) return CH_ERR_ARG;
   if ((alloc == nullptr) != (free_fn == nullptr)) return CH_ERR_ARG;
   const int nx = p->nx, ny = p->ny, nz = p->nz;
-  if (nx < 4 || ny < 4 || nz < 5 || nx % 2 || ny % 2) return CH_ERR_SIZE;
-  if (!smooth23(nx) || !smooth23(ny) || !smooth23(3 * nx / 2) || !smooth23(3 * ny / 2) ||
-      (nz - 1) % 2 || !smooth23(2 * (nz - 1)))
-    return CH_ERR_SIZE;
-  if (3 * nx / 2 > 8192 || 3 * ny / 2 > 8192 || nz > 4097) return CH_ERR_SIZE;
+  if (chf::check_sizes(nx, ny, nz) != CH_OK) return CH_ERR_SIZE;
 
   ch_grid* G = new (std::nothrow) ch_grid();
   if (!G) return CH_ERR_ALLOC;

@@ -7,6 +7,14 @@
 
 namespace chf {
 
+// n = 2^a 3^b?
+bool smooth23(int n);
+// radix schedule (8 once for an odd power of two >= 3, then 4s, a 2, then 3s); false if n is
+// not {2,3}-smooth or needs too many passes.  Sets pl->n, pl->nst, pl->rad (not pl->tw).
+bool make_radices(int n, FftPlan* pl);
+// the grid-size rules of the C ABI: 0 or a negative CH_ERR_* code
+int check_sizes(int nx, int ny, int nz);
+
 // Raise a kernel's dynamic shared-memory limit to `bytes` if it is below that.  The limit is
 // per kernel; *cur remembers what was set.  Never called while a stream is being captured (the
 // first, uncaptured launch of every size comes first).
