@@ -53,24 +53,29 @@ def fft_flops(n):
 
 
 def kernel_work(w, prec):
-    """Algorithmic flops and bytes per launch of the four step kernels."""
+    """Algorithmic flops (an FMA counts 2) and bytes per launch of the six step kernels."""
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     Mx, Px, Py, N = nx // 2, 3 * nx // 2, 3 * ny // 2, nz - 1
     b = 16 if prec == 0 else 8
     S = Mx * ny * nz           # spectral points per field
     Y = Mx * Py * nz           # y-padded points per field
     lines = Mx * ny
-    # z-line: 17 complex DCT-I (2N-point complex FFT each), ~12 real tau solves (~10 flop/row),
-    # assembly and derivatives (~200 flop per coefficient)
-    z_fl = lines * (17 * fft_flops(2 * N) + 12 * 10 * nz + 200 * nz)
-    z_by = S * 16 * 12 + S * b * 17    # state+history in/out (fp64) + 10 NL in + 7 fields out
+    # complex DCT-I of a line = complex FFT of 2N points; a derivative = 4 flops per coefficient
+    dct = fft_flops(2 * N)
+    zrhs_fl = lines * (10 * dct + 9 * 4 * nz + 120 * nz)
+    zrhs_by = S * (b * 10 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)   # NL, state, hist in/out, R out
+    zsolve_fl = lines * nz * (5 * 30 + 8)                       # 5 sweeps + influence correction
+    zsolve_by = S * 16 * 3 * 2
+    zbwd_fl = lines * (7 * dct + 2 * 4 * nz + 40 * nz)
+    zbwd_by = S * (16 * 3 + 16 * 2 + 16 * 3 + b * 7)             # R, state in, state out, 7 out
     yb_fl = 7 * Mx * nz * fft_flops(Py)
     yb_by = 7 * (S + Y) * b
-    x_fl = Py * nz * (17 * 0.5 * fft_flops(Px) + 60 * Px)   # packed real FFTs + products
+    x_fl = Py * nz * (17 * 0.5 * fft_flops(Px) + 60 * Px)       # packed real FFTs + products
     x_by = 17 * Y * b
     yf_fl = 10 * Mx * nz * fft_flops(Py)
     yf_by = 10 * (S + Y) * b
-    return {"zline": (z_fl, z_by), "ybwd": (yb_fl, yb_by), "xline": (x_fl, x_by),
+    return {"zrhs": (zrhs_fl, zrhs_by), "zsolve": (zsolve_fl, zsolve_by),
+            "zbwd": (zbwd_fl, zbwd_by), "ybwd": (yb_fl, yb_by), "xline": (x_fl, x_by),
             "yfwd": (yf_fl, yf_by)}
 
 
@@ -266,14 +271,14 @@ def main():
     nbytes = 4 * pts * 8
 
     # ---- roofline of the dominant kernel
-    names = ["zline", "ybwd", "xline", "yfwd"]
+    names = list(binding.Grid.KERNELS)
     work = kernel_work(w, prec)
-    k = max(range(4), key=lambda i: kms[i])
+    k = max(range(len(names)), key=lambda i: kms[i])
     name = names[k]
     per_launch_ms = kms[k] / args.steps
     fl, by = work[name]
     hbm, hbm_kind = peaks()
-    fp64_like = (prec == 0) or name == "zline"
+    fp64_like = (prec == 0) or name.startswith("z")
     if fp64_like:
         ach = fl / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -111,10 +111,15 @@ int ch_set_fields_host(ch_grid* g, const double* u, const double* v, const doubl
  * the first step the per-step launch sequence is replayed from a captured CUDA graph. */
 int ch_step(ch_grid* g, int nsteps);
 
+/* Number of kernels in one time step and the order ch_step_timed reports them in:
+ * zrhs (DCT, assembly, AB2, right-hand sides), zsolve (tau solves), zbwd (update, velocity,
+ * backward DCT), y backward, x line, y forward. */
+#define CH_STEP_KERNELS 6
+
 /* As ch_step, but launched without the graph and bracketed by CUDA events on the stream: on
- * return (the stream is synchronised) kernel_ms[0..3] hold the summed device time of the z-line,
- * y-backward, x-line and y-forward launches and *total_ms the time from the first launch to the
- * end of the last.  kernel_ms may be NULL.  Used by the benchmark to attribute step time. */
+ * return (the stream is synchronised) kernel_ms[0..CH_STEP_KERNELS-1] hold the summed device
+ * time of each of the step's kernels and *total_ms the time from the first launch to the end of
+ * the last.  kernel_ms may be NULL.  Used by the benchmark to attribute step time. */
 int ch_step_timed(ch_grid* g, int nsteps, double* kernel_ms, double* total_ms);
 
 /* Number of kernel launches one ch_step makes per time step. */

@@ -202,10 +202,12 @@ class Grid:
     def step(self, n=1):
         _ck("ch_step", lib().ch_step(self.h, int(n)))
 
+    KERNELS = ("zrhs", "zsolve", "zbwd", "ybwd", "xline", "yfwd")
+
     def step_timed(self, n):
-        """n steps with CUDA events between launches; returns (total_ms, [zline, ybwd, xline,
-        yfwd] summed ms).  Synchronises the stream."""
-        ks = (ctypes.c_double * 4)()
+        """n steps with CUDA events between launches; returns (total_ms, per-kernel summed ms in
+        the order of Grid.KERNELS).  Synchronises the stream."""
+        ks = (ctypes.c_double * len(self.KERNELS))()
         tot = ctypes.c_double()
         _ck("ch_step_timed", lib().ch_step_timed(self.h, int(n), ks, ctypes.byref(tot)))
         return tot.value, list(ks)

@@ -92,6 +92,9 @@ struct ch_grid {
   // auxiliary float64 buffers for set/get/diagnostics/stage entry points
   double2 *auxA, *auxB;
   double* phys7;
+  // right-hand sides / solved sums of the three implicit problems (3 fields), operator table
+  double2* R;
+  double* fac;
   // small tables and diagnostics scratch
   double* tab;  // go1 go2 go3 ccw dzl qint, nz each
   double* diag_part;
@@ -172,8 +175,7 @@ int make_plan(ch_grid* G, int n, int prec, FftPlan* pl) {
 int eval_nonlinear(ch_grid* G) {
   const GridDev& g = G->g;
   cudaStream_t s = G->stream;
-  CK(chf::launch_zline(1, G->prec, g, G->nl, G->bw, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
-                       G->hphi, 0, G->pz, s));
+  CK(chf::launch_zbwd(0, G->prec, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s));
   CK(chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s));
   CK(chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s));
   CK(chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, 10, G->fsy, G->fs,
@@ -183,8 +185,10 @@ int eval_nonlinear(ch_grid* G) {
 
 int launch_step(ch_grid* G, int first, cudaStream_t s) {
   const GridDev& g = G->g;
-  CK(chf::launch_zline(0, G->prec, g, G->nl, G->bw, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
-                       G->hphi, first, G->pz, s));
+  CK(chf::launch_zrhs(G->prec, g, G->nl, G->fs, G->om, G->w, G->phi, G->hom, G->hw, G->hphi, G->R,
+                      first, G->pz, s));
+  CK(chf::launch_zsolve(g, G->R, G->fs, s));
+  CK(chf::launch_zbwd(1, G->prec, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s));
   CK(chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s));
   CK(chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s));
   CK(chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, 10, G->fsy, G->fs,
@@ -196,8 +200,7 @@ int launch_step(ch_grid* G, int first, cudaStream_t s) {
 int state_to_phys7(ch_grid* G, int nf) {
   const GridDev& g = G->g;
   cudaStream_t s = G->stream;
-  CK(chf::launch_zline(1, 0, g, nullptr, G->auxA, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
-                       G->hphi, 0, G->pz, s));
+  CK(chf::launch_zbwd(0, 0, g, G->R, G->om, G->w, G->phi, G->auxA, G->fs, G->pz, s));
   CK(chf::launch_ypass(1, 0, g, g.ny, G->auxA, G->auxB, nf, G->fs, G->fs, 1.0, G->pyu, s));
   CK(chf::launch_x_c2r(g, G->auxB, G->phys7, nf, G->fs, G->fsp, G->pxu, s));
   return CH_OK;
@@ -308,6 +311,9 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   G->auxB = (double2*)A((size_t)7 * sb);
   G->phys7 = (double*)A((size_t)7 * G->fsp * sizeof(double));
   G->tab = (double*)A((size_t)6 * nz * sizeof(double));
+  G->R = (double2*)A((size_t)3 * sb);
+  g.NK = g.Mx * (ny / 2 + 1);
+  G->fac = (double*)A(chf::fac_doubles(g) * sizeof(double));
   G->diag_part = (double*)A((size_t)(304 * 6 + 16) * sizeof(double));
   G->diag_out = G->diag_part + 304 * 6;
   if (st != CH_OK) {
@@ -364,6 +370,8 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
     g.go1 = G->tab;
     g.go2 = G->tab + nz;
     g.go3 = G->tab + 2 * nz;
+    g.fac = G->fac;
+    if (chf::build_factor_table(g, G->fac, 0) != cudaSuccess) return bail(G, CH_ERR_CUDA);
   }
   if (chf::zline_smem(g) > (size_t)kMaxSmem || (size_t)17 * g.Px * sizeof(double2) > (size_t)kMaxSmem) {
     return bail(G, CH_ERR_SIZE);
@@ -457,12 +465,13 @@ int ch_step(ch_grid* G, int nsteps) {
   return CH_OK;
 }
 
-int ch_launches_per_step(const ch_grid* G) { return G ? 4 : 0; }
+int ch_launches_per_step(const ch_grid* G) { return G ? CH_STEP_KERNELS : 0; }
 
 int ch_step_timed(ch_grid* G, int nsteps, double* kernel_ms, double* total_ms) {
   if (!G || nsteps < 0 || !total_ms) return CH_ERR_ARG;
   if (!G->fields_set) return CH_ERR_STATE;
-  const int nev = 4 * nsteps + 1;
+  const int NKER = CH_STEP_KERNELS;
+  const int nev = NKER * nsteps + 1;
   std::vector<cudaEvent_t> ev(nev);
   for (int i = 0; i < nev; ++i) CK(cudaEventCreate(&ev[i]));
   const GridDev& g = G->g;
@@ -471,15 +480,17 @@ int ch_step_timed(ch_grid* G, int nsteps, double* kernel_ms, double* total_ms) {
   CK(cudaEventRecord(ev[0], s));
   for (int i = 0; i < nsteps && st == CH_OK; ++i) {
     const int first = G->first;
-    cudaEvent_t* e = &ev[4 * i];
-#define TK(k, call)                          \
+    cudaEvent_t* e = &ev[NKER * i];
+#define TK(k, call)                            \
   if ((call) != cudaSuccess) st = CH_ERR_CUDA; \
   cudaEventRecord(e[k + 1], s);
-    TK(0, chf::launch_zline(0, G->prec, g, G->nl, G->bw, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
-                            G->hphi, first, G->pz, s))
-    TK(1, chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s))
-    TK(2, chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s))
-    TK(3, chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, 10, G->fsy, G->fs,
+    TK(0, chf::launch_zrhs(G->prec, g, G->nl, G->fs, G->om, G->w, G->phi, G->hom, G->hw, G->hphi,
+                           G->R, first, G->pz, s))
+    TK(1, chf::launch_zsolve(g, G->R, G->fs, s))
+    TK(2, chf::launch_zbwd(1, G->prec, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s))
+    TK(3, chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s))
+    TK(4, chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s))
+    TK(5, chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, 10, G->fsy, G->fs,
                             1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s))
 #undef TK
     G->first = 0;
@@ -487,18 +498,18 @@ int ch_step_timed(ch_grid* G, int nsteps, double* kernel_ms, double* total_ms) {
     G->t += G->p.dt;
   }
   CK(cudaEventSynchronize(ev[nev - 1]));
-  double ks[4] = {0, 0, 0, 0};
+  double ks[CH_STEP_KERNELS] = {0};
   for (int i = 0; i < nsteps; ++i)
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NKER; ++k) {
       float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, ev[4 * i + k], ev[4 * i + k + 1]));
+      CK(cudaEventElapsedTime(&ms, ev[NKER * i + k], ev[NKER * i + k + 1]));
       ks[k] += ms;
     }
   float tot = 0.f;
   CK(cudaEventElapsedTime(&tot, ev[0], ev[nev - 1]));
   for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
   if (kernel_ms)
-    for (int k = 0; k < 4; ++k) kernel_ms[k] = ks[k];
+    for (int k = 0; k < NKER; ++k) kernel_ms[k] = ks[k];
   *total_ms = tot;
   return st;
 }
@@ -507,8 +518,7 @@ int ch_get_fields(ch_grid* G, double* u, double* v, double* w, double* phi) {
   if (!G || !u || !v || !w || !phi) return CH_ERR_ARG;
   const GridDev& g = G->g;
   cudaStream_t s = G->stream;
-  CK(chf::launch_zline(1, 0, g, nullptr, G->auxA, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
-                       G->hphi, 0, G->pz, s));
+  CK(chf::launch_zbwd(0, 0, g, G->R, G->om, G->w, G->phi, G->auxA, G->fs, G->pz, s));
   CK(chf::launch_ypass(1, 0, g, g.ny, G->auxA, G->auxB, 4, G->fs, G->fs, 1.0, G->pyu, s));
   double* f4[4] = {u, v, w, phi};
   for (int f = 0; f < 4; ++f)

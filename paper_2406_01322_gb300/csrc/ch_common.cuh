@@ -203,6 +203,10 @@ struct GridDev {
   const double* go1;
   const double* go2;
   const double* go3;
+  // time-independent tau-operator tables, one column per distinct k^2 (index
+  // K = mx (ny/2 + 1) + |my|, NK columns), layout described in ch_zline.cu
+  const double* fac;
+  int NK;
 };
 
 }  // namespace chf

@@ -30,16 +30,26 @@ inline cudaError_t ensure_smem(K* kernel, size_t bytes, int* cur) {
   return cudaSuccess;
 }
 
-// z-line kernel: one CTA per (mx, j) wavenumber line.
-//   mode 0: full step (forward DCT of the 10 non-linear fields, assembly, AB2, tau solves,
-//           state update, 7 backward fields);  mode 1: the 7 backward fields of the state only.
-// nl / bw hold fields of (Mx, Ny, Nz) complex samples in precision `prec` (0 fp64, 1 fp32),
-// field stride fs elements.
-cudaError_t launch_zline(int mode, int prec, const GridDev& g, const void* nl, void* bw,
-                         long long fs, double2* st_om, double2* st_w, double2* st_phi,
-                         double2* h_om, double2* h_w, double2* h_phi, int first,
-                         const FftPlan& pz, cudaStream_t s);
+// z-line kernels (one CTA per (mx, j) wavenumber line unless stated).
+// zrhs: forward DCT of the 10 non-linear fields (working precision `prec`, 0 fp64 / 1 fp32),
+//   assembly, AB2 (history h_* updated), right-hand sides R = [omega | theta-w | phi] (3 fields).
+// zsolve: tau solves of every line (tiles of lines, one thread per elimination chain), in place
+//   on R: sums omega^{n+1}+omega^n, w^{n+1}+w^n and phi^{n+1}.
+// zbwd: update = 1: new state from R; then the 7 fields for the non-linear terms, backward DCT
+//   into bw (precision prec).  update = 0: from the state as is.
+// Fields are (Mx, Ny, Nz) complex with field stride fs elements.
+cudaError_t launch_zrhs(int prec, const GridDev& g, const void* nl, long long fs,
+                        const double2* st_om, const double2* st_w, const double2* st_phi,
+                        double2* h_om, double2* h_w, double2* h_phi, double2* R, int first,
+                        const FftPlan& pz, cudaStream_t s);
+cudaError_t launch_zsolve(const GridDev& g, double2* R, long long fs, cudaStream_t s);
+cudaError_t launch_zbwd(int update, int prec, const GridDev& g, const double2* R,
+                        double2* st_om, double2* st_w, double2* st_phi, void* bw, long long fs,
+                        const FftPlan& pz, cudaStream_t s);
 size_t zline_smem(const GridDev& g);
+// time-independent tau-operator table (g.fac, fac_doubles(g) doubles), built once
+size_t fac_doubles(const GridDev& g);
+cudaError_t build_factor_table(const GridDev& g, double* fac, cudaStream_t s);
 
 // Projection of four physical-z fields (u, v, w, phi as (Mx, Ny, Nz) complex, already
 // Fourier-transformed in x, y) onto the state (omega_z / mean flow, w, phi); zeroes history.

@@ -1,6 +1,6 @@
-// Wall-normal (z-line) kernels: everything that happens along one (kx, ky) Chebyshev line.
+// Wall-normal (z-line) kernels: everything that happens along (kx, ky) Chebyshev lines.
 //
-// Per line (paper Sec. 2.2, steps ii)-v), and Sec. 3.2.1-3.2.2):
+// Per line (paper Sec. 2.2 steps ii)-v), Sec. 3.2.1-3.2.2):
 //   forward DCT-I of the ten non-linear fields (Chebyshev coefficients, Sec. 3.2.1);
 //   spectral assembly of h_omega (Eq. (omegaz)), h_w (Eq. (ww)) and S_phi (Eq. (phisplit));
 //   Adams-Bashforth 2 on the non-linear terms, Crank-Nicolson on omega_z / lap(w) / mean flow,
@@ -11,107 +11,114 @@
 //   velocity from continuity and the omega_z definition (Eqs. (cont), (omegadef));
 //   backward DCT-I of the seven fields the next non-linear evaluation needs.
 //
+// Three step kernels:
+//   zrhs   (one CTA per line): DCTs, derivatives, assembly, AB2, right-hand sides -> R buffers;
+//   zsolve (one CTA per tile of lines, one thread per (line, parity) elimination chain): the
+//          sequential sweeps run on full warps, with operator factors from a table built once;
+//   zbwd   (one CTA per line): state update, velocity recovery, backward DCTs.
+//
 // Crank-Nicolson is applied in "sum form": for q in {omega_z, lap(w), ubar + i vbar},
 //   (D^2 - k^2 - beta)(q^{n+1} + q^n) = -2 beta q^n - 2 Re AB2(h),   beta = 2 Re / dt,
 // which is the CN equation (D^2-k^2-beta) q^{n+1} = -(D^2-k^2+beta) q^n - 2 Re AB2(h) with
 // (D^2-k^2-beta) q^n added to both sides; q^{n+1} + q^n satisfies the same homogeneous
 // wall conditions, so the same tau problem gives it and only D^2 (not D^4) of w^n is needed.
 //
-// All arithmetic in this file is float64.  One CTA of 128 threads owns one line.
+// Operator table (built once by ch_init_grid; K = mx (ny/2+1) + |my| indexes distinct k^2):
+//   for op in {0: D^2-(k^2+beta) Dirichlet, 1: D^2-k^2 Dirichlet, 2: D^2-(k^2+lam) Neumann}
+//     Y[op][n][K], RD[op][n][K] (1/pivot), Q[op][n][K]  (n = 0..N, both parities interleaved)
+//     rsq[op][p][K] = 1 / (boundary-row sum of Q for parity p)
+//   Oh[n][K]  homogeneous Omega_h of the w problem, rsh[p][K] = 1 / sum_n n^2 Oh (parity p).
+//
+// All arithmetic in this file is float64.
 #include "ch_internal.h"
 
 namespace chf {
 
 namespace {
 
-constexpr int ZT = 128;   // threads per z-line CTA
+constexpr int ZT = 128;   // threads of a per-line CTA
 constexpr int NBF = 2;    // DCT lines transformed per FFT call
 constexpr int NLINES = 16;
+constexpr int TL = 32;    // lines per zsolve CTA (64 threads: one per (line, parity))
 
-// d/dz in Chebyshev coefficient space for one real component (comp 0 = re, 1 = im):
-// c_n b_n = b_{n+2} + 2 (n+1) a_{n+1}, run downward from n = N.  src may alias dst.
-__device__ void dz_component(const double2* src, double2* dst, int comp, int N) {
+__device__ __forceinline__ const double* fac_ptr(const GridDev& g, int op, int arr, int K) {
+  return g.fac + ((size_t)(op * 3 + arr) * g.nz) * g.NK + K;
+}
+__device__ __forceinline__ double fac_rsq(const GridDev& g, int op, int p, int K) {
+  return g.fac[(size_t)9 * g.nz * g.NK + (size_t)(op * 2 + p) * g.NK + K];
+}
+__device__ __forceinline__ const double* fac_oh(const GridDev& g, int K) {
+  return g.fac + (size_t)9 * g.nz * g.NK + (size_t)6 * g.NK + K;
+}
+__device__ __forceinline__ double fac_rsh(const GridDev& g, int p, int K) {
+  return g.fac[(size_t)10 * g.nz * g.NK + (size_t)6 * g.NK + (size_t)p * g.NK + K];
+}
+
+__device__ __forceinline__ void line_wavenumbers(const GridDev& g, int line, int& mx, int& j,
+                                                 double& kx, double& ky) {
+  mx = line / g.ny;
+  j = line - mx * g.ny;
+  const int my = (j < g.ny / 2) ? j : j - g.ny;
+  kx = 6.283185307179586476925 * mx / g.lx;
+  ky = 6.283185307179586476925 * my / g.ly;
+}
+
+__device__ __forceinline__ int line_K(const GridDev& g, int mx, int j) {
+  const int h = g.ny / 2;
+  const int amy = (j <= h) ? j : g.ny - j;
+  return mx * (h + 1) + amy;
+}
+
+// ---- d/dz in Chebyshev coefficient space as warp-parallel suffix sums ----------------------
+// dst_n = (2 / c_n) sum_{p > n, p + n odd} p src_p.  For output parity q the sum runs over the
+// source class p = (1-q) + 2m, m >= i + q where n = q + 2i: a suffix sum over that class.
+// One warp per (component, output parity); tmp holds >= N/2 + 2 doubles for this warp.
+__device__ void dz_scan(const double2* src, double2* dst, int comp, int q, int N, double* tmp) {
   const double* s = reinterpret_cast<const double*>(src) + comp;
   double* d = reinterpret_cast<double*>(dst) + comp;
-  double bp1 = 0.0, bp2 = 0.0, ap1 = 0.0;
-  for (int n = N; n >= 0; --n) {
-    const double an = s[2 * n];
-    const double bn = fma(2.0 * (n + 1), ap1, bp2);
-    d[2 * n] = (n == 0) ? 0.5 * bn : bn;
-    bp2 = bp1;
-    bp1 = bn;
-    ap1 = an;
+  const int lane = threadIdx.x & 31;
+  const int ps = 1 - q;
+  const int cnt = (N - ps) / 2 + 1;
+  const int E = (cnt + 31) / 32;
+  const int m0 = lane * E;
+  double acc = 0.0;
+  for (int e = E - 1; e >= 0; --e) {
+    const int m = m0 + e;
+    if (m < cnt) {
+      const int p = ps + 2 * m;
+      acc = fma((double)p, s[2 * p], acc);
+      tmp[m] = acc;
+    }
   }
+  double v = acc;  // inclusive suffix scan of chunk totals over lanes
+  for (int off = 1; off < 32; off <<= 1) {
+    const double o = __shfl_down_sync(0xffffffffu, v, off);
+    if (lane + off < 32) v += o;
+  }
+  const double nxt = __shfl_down_sync(0xffffffffu, v, 1);
+  const double excl = (lane < 31) ? nxt : 0.0;
+  for (int e = 0; e < E; ++e) {
+    const int m = m0 + e;
+    if (m < cnt) tmp[m] += excl;
+  }
+  __syncwarp();
+  const int nout = (N - q) / 2 + 1;
+  for (int i = lane; i < nout; i += 32) {
+    const int n = q + 2 * i;
+    const int m = i + q;
+    const double T = (m < cnt) ? tmp[m] : 0.0;
+    d[2 * n] = (n == 0) ? T : 2.0 * T;
+  }
+  __syncwarp();
 }
 
-// run up to 8 derivative tasks (src -> dst) in parallel, one thread per (task, component)
-__device__ void dz_tasks(double2* const* src, double2* const* dst, int ntask, int N) {
-  const int t = threadIdx.x;
-  if (t < 2 * ntask) dz_component(src[t >> 1], dst[t >> 1], t & 1, N);
-}
-
-// Gottlieb-Orszag factorisation of (D^2 - alpha) for one parity p (elimination from the top
-// coefficient down; the boundary row closes the system at n = p).  Stores Y[n], RD[n] (=1/den)
-// and Q[n] for n = p, p+2, ..., returns SQ = sum_i beta_i Q_i (beta = 1 Dirichlet, n^2 Neumann).
-__device__ double tau_factor(double alpha, int p, int N, bool neumann, const double* t1,
-                             const double* t2, const double* t3, double* Y, double* RD,
-                             double* Q) {
-  const int I = (N - p) / 2;
-  double ynext = 0.0;
-  for (int i = I; i >= 1; --i) {
-    const int n = p + 2 * i;
-    const double L = -alpha * t1[n];
-    const double Dg = 1.0 + alpha * t2[n];
-    const double U = -alpha * t3[n];
-    const double rd = 1.0 / fma(U, ynext, Dg);
-    const double y = -L * rd;
-    Y[n] = y;
-    RD[n] = rd;
-    ynext = y;
-  }
-  double q = 1.0;
-  Q[p] = 1.0;
-  double sq = neumann ? (double)(p * p) : 1.0;
-  for (int i = 1; i <= I; ++i) {
-    const int n = p + 2 * i;
-    q *= Y[n];
-    Q[n] = q;
-    sq = fma(neumann ? (double)n * (double)n : 1.0, q, sq);
-  }
-  return sq;
-}
-
-// Solve (D^2 - alpha) a = f (tau rows in Gottlieb-Orszag form) for parity p of one component,
-// in place: x[2n] holds f_n on entry and a_n on exit (n of parity p).  g0 = boundary value
-// (sum of the parity-p coefficients, or of n^2 times them for Neumann).
-__device__ void tau_sweep(double* x, int p, int N, double alpha, bool neumann, double g0,
-                          const double* t1, const double* t2, const double* t3,
-                          const double* Y, const double* RD, const double* Q, double sq) {
-  const int I = (N - p) / 2;
-  double xn = 0.0, fnp2 = 0.0;
-  for (int i = I; i >= 1; --i) {
-    const int n = p + 2 * i;
-    const double fn = x[2 * n];
-    const double fnm2 = x[2 * (n - 2)];
-    const double gi = fma(t1[n], fnm2, fma(-t2[n], fn, t3[n] * fnp2));
-    const double U = -alpha * t3[n];
-    const double xi = fma(-U, xn, gi) * RD[n];
-    x[2 * n] = xi;
-    fnp2 = fn;
-    xn = xi;
-  }
-  double P = 0.0, sp = 0.0;
-  for (int i = 1; i <= I; ++i) {
-    const int n = p + 2 * i;
-    P = fma(Y[n], P, x[2 * n]);
-    x[2 * n] = P;
-    sp = fma(neumann ? (double)n * (double)n : 1.0, P, sp);
-  }
-  const double a0 = (g0 - sp) / sq;
-  x[2 * p] = a0;
-  for (int i = 1; i <= I; ++i) {
-    const int n = p + 2 * i;
-    x[2 * n] = fma(Q[n], a0, x[2 * n]);
+// several derivatives src[t] -> dst[t] (no aliasing): 4 scans per task spread over the warps
+__device__ void dz_tasks(double2* const* src, double2* const* dst, int ntask, int N, double* tmp) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* mytmp = tmp + warp * (N / 2 + 2);
+  for (int s = warp; s < 4 * ntask; s += nw) {
+    const int t = s >> 2, comp = (s >> 1) & 1, q = s & 1;
+    dz_scan(src[t], dst[t], comp, q, N, mytmp);
   }
 }
 
@@ -119,12 +126,7 @@ struct ZSmem {
   double2* L;   // NLINES lines of Nz
   double2* FA;  // NBF * 2N
   double2* FB;
-  double* Y;    // 3 * Nz
-  double* RD;
-  double* Q;
-  double* t1;   // Nz each: Gottlieb-Orszag row tables
-  double* t2;
-  double* t3;
+  double* tmp;  // scan scratch, (ZT/32) * (N/2 + 2)
 };
 
 __device__ __forceinline__ ZSmem carve(double2* sm, int Nz, int N) {
@@ -132,13 +134,7 @@ __device__ __forceinline__ ZSmem carve(double2* sm, int Nz, int N) {
   z.L = sm;
   z.FA = sm + NLINES * Nz;
   z.FB = z.FA + NBF * 2 * N;
-  double* d = reinterpret_cast<double*>(z.FB + NBF * 2 * N);
-  z.Y = d;
-  z.RD = d + 3 * Nz;
-  z.Q = d + 6 * Nz;
-  z.t1 = d + 9 * Nz;
-  z.t2 = d + 10 * Nz;
-  z.t3 = d + 11 * Nz;
+  z.tmp = reinterpret_cast<double*>(z.FB + NBF * 2 * N);
   return z;
 }
 
@@ -167,7 +163,7 @@ __device__ void dct_forward_lines(const ZSmem& z, int first, int cnt, int Nz, in
 
 // backward DCT-I of cnt lines starting at line `first`: f_j = sum_n a_n cos(pi n j / N),
 // evaluated as half the 2N-point DFT of the even extension of (2 a_0, a_1, .., a_{N-1}, 2 a_N).
-// Results are written to out[(first+f) * fs + off + j].
+// Results are written to out[(out_first+f) * fs + off + j].
 template <typename T2>
 __device__ void dct_backward_lines_store(const ZSmem& z, int first, int cnt, int Nz, int N,
                                          const FftPlan& pz, T2* out, long long fs, size_t off,
@@ -189,31 +185,395 @@ __device__ void dct_backward_lines_store(const ZSmem& z, int first, int cnt, int
   __syncthreads();
 }
 
-__device__ __forceinline__ void line_wavenumbers(const GridDev& g, int line, int& mx, int& j,
-                                                 double& kx, double& ky) {
-  mx = line / g.ny;
-  j = line - mx * g.ny;
-  const int my = (j < g.ny / 2) ? j : j - g.ny;
-  kx = 6.283185307179586476925 * mx / g.lx;
-  ky = 6.283185307179586476925 * my / g.ly;
+// ---- zrhs: right-hand sides of the three implicit problems ---------------------------------
+template <typename T>
+__global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T>::t* __restrict__ nl,
+                                                  long long fs, const double2* __restrict__ st_om,
+                                                  const double2* __restrict__ st_w,
+                                                  const double2* __restrict__ st_phi,
+                                                  double2* __restrict__ h_om,
+                                                  double2* __restrict__ h_w,
+                                                  double2* __restrict__ h_phi,
+                                                  double2* __restrict__ R, int first, FftPlan pz) {
+  extern __shared__ double2 zsm[];
+  const int Nz = g.nz, N = g.N;
+  const int line = blockIdx.x;
+  int mx, j;
+  double kx, ky;
+  line_wavenumbers(g, line, mx, j, kx, ky);
+  const size_t off = (size_t)line * Nz;
+  const int tid = threadIdx.x;
+  double2* Rom = R;
+  double2* Rth = R + fs;
+  double2* Rps = R + 2 * fs;
+  if (j == g.ny / 2) {  // y Nyquist row: identically zero
+    for (int n = tid; n < Nz; n += blockDim.x) {
+      Rom[off + n] = make_double2(0.0, 0.0);
+      Rth[off + n] = make_double2(0.0, 0.0);
+      Rps[off + n] = make_double2(0.0, 0.0);
+    }
+    return;
+  }
+  const ZSmem z = carve(zsm, Nz, N);
+  const bool is00 = (mx == 0 && j == 0);
+  const double k2 = kx * kx + ky * ky;
+  for (int n = tid; n < Nz; n += blockDim.x) {
+    LN(z, 10, Nz)[n] = st_om[off + n];
+    LN(z, 11, Nz)[n] = st_w[off + n];
+    LN(z, 12, Nz)[n] = st_phi[off + n];
+  }
+  for (int idx = tid; idx < 10 * Nz; idx += blockDim.x) {
+    const int f = idx / Nz, n = idx - f * Nz;
+    LN(z, f, Nz)[n] = to_d2(nl[(long long)f * fs + off + n]);
+  }
+  __syncthreads();
+  for (int f0 = 0; f0 < 10; f0 += NBF) dct_forward_lines(z, f0, NBF, Nz, N, pz);
+  // lines: 0 Sxx 1 Syy 2 Szz 3 Sxy 4 Sxz 5 Syz 6 phi^3 7 u phi 8 v phi 9 w phi
+  {
+    double2* src[3] = {LN(z, 4, Nz), LN(z, 5, Nz), LN(z, 2, Nz)};
+    double2* dst[3] = {LN(z, 13, Nz), LN(z, 14, Nz), LN(z, 15, Nz)};
+    dz_tasks(src, dst, 3, N, z.tmp);
+  }
+  __syncthreads();
+  // S_i = i kx Sigma_ix + i ky Sigma_iy + D Sigma_iz
+  for (int n = tid; n < Nz; n += blockDim.x) {
+    const double2 sxx = LN(z, 0, Nz)[n], syy = LN(z, 1, Nz)[n];
+    const double2 sxy = LN(z, 3, Nz)[n], sxz = LN(z, 4, Nz)[n], syz = LN(z, 5, Nz)[n];
+    const double2 Sx = mul_i(kx * sxx + ky * sxy) + LN(z, 13, Nz)[n];
+    const double2 Sy = mul_i(kx * sxy + ky * syy) + LN(z, 14, Nz)[n];
+    const double2 Sz = mul_i(kx * sxz + ky * syz) + LN(z, 15, Nz)[n];
+    double2 hom;
+    if (is00) {  // mean flow: Sbar_x + i Sbar_y + (gx + i gy) delta_{n0}
+      hom = make_double2(Sx.x + (n == 0 ? g.gx : 0.0), Sy.x + (n == 0 ? g.gy : 0.0));
+    } else {
+      hom = mul_i(kx * Sy - ky * Sx);  // i kx S_y - i ky S_x
+    }
+    LN(z, 2, Nz)[n] = Sz;
+    LN(z, 3, Nz)[n] = hom;
+    LN(z, 4, Nz)[n] = mul_i(kx * Sx + ky * Sy);  // i kx S_x + i ky S_y
+    const double2 ph = LN(z, 12, Nz)[n];
+    LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * ph;  // G = phi^3 - (1+shat) phi
+    LN(z, 7, Nz)[n] = -1.0 * mul_i(kx * LN(z, 7, Nz)[n] + ky * LN(z, 8, Nz)[n]);
+  }
+  __syncthreads();
+  {
+    double2* src[4] = {LN(z, 9, Nz), LN(z, 4, Nz), LN(z, 6, Nz), LN(z, 11, Nz)};
+    double2* dst[4] = {LN(z, 13, Nz), LN(z, 14, Nz), LN(z, 15, Nz), LN(z, 5, Nz)};
+    dz_tasks(src, dst, 4, N, z.tmp);
+  }
+  __syncthreads();
+  {
+    double2* src[2] = {LN(z, 15, Nz), LN(z, 5, Nz)};
+    double2* dst[2] = {LN(z, 8, Nz), LN(z, 9, Nz)};
+    dz_tasks(src, dst, 2, N, z.tmp);
+  }
+  __syncthreads();
+  // h_w, S_phi, theta^n = (D^2 - k^2) w^n; AB2; right-hand sides
+  const double twoRe = 2.0 * g.re;
+  const double cphi = g.pe / (g.ch * g.ch);
+  const double rdt = 1.0 / g.dt;
+  const double rpe = 1.0 / g.pe;
+  for (int n = tid; n < Nz; n += blockDim.x) {
+    const double2 hw = is00 ? make_double2(0.0, 0.0)
+                            : (-k2) * LN(z, 2, Nz)[n] - LN(z, 14, Nz)[n];
+    const double2 sphi = LN(z, 7, Nz)[n] - LN(z, 13, Nz)[n] +
+                         rpe * (LN(z, 8, Nz)[n] - k2 * LN(z, 6, Nz)[n]);
+    const double2 hom = LN(z, 3, Nz)[n];
+    const double2 th = LN(z, 9, Nz)[n] - k2 * LN(z, 11, Nz)[n];
+    double2 Hom = hom, Hw = hw, Hphi = sphi;
+    if (!first) {
+      Hom = 1.5 * hom - 0.5 * h_om[off + n];
+      Hw = 1.5 * hw - 0.5 * h_w[off + n];
+      Hphi = 1.5 * sphi - 0.5 * h_phi[off + n];
+    }
+    h_om[off + n] = hom;
+    h_w[off + n] = hw;
+    h_phi[off + n] = sphi;
+    Rom[off + n] = (-2.0 * g.beta) * LN(z, 10, Nz)[n] - twoRe * Hom;
+    Rth[off + n] = (-2.0 * g.beta) * th - twoRe * Hw;
+    Rps[off + n] = cphi * (rdt * LN(z, 12, Nz)[n] + Hphi);
+  }
 }
 
-// the seven fields the non-linear terms need, from the state held in lines 10 (omega / mean),
-// 11 (w), 12 (phi): u, v (continuity + omega_z definition), w, phi, i kx phi, i ky phi, D phi.
-template <typename T2>
-__device__ void backward_fields(const ZSmem& z, const GridDev& g, double kx, double ky,
-                                bool is00, const FftPlan& pz, T2* bw, long long fs,
-                                size_t off) {
+// ---- tau elimination with tabulated factors -----------------------------------------------
+// Solve (D^2 - alpha) a = f (Gottlieb-Orszag rows n >= 2, homogeneous boundary row) for the
+// coefficients of parity p of one complex line, in place (x[n] = f_n on entry, a_n on exit).
+// Y, RD, Q point at (op, arr, n = 0, K) with stride NK per n; wb = 1 (Dirichlet) or n^2.
+__device__ void tau_sweep_c(double2* x, int p, int N, double alpha, bool neumann,
+                            const double* t1, const double* t2, const double* t3,
+                            const double* Y, const double* RD, const double* Q, int NK,
+                            double rsq) {
+  const int I = (N - p) / 2;
+  double2 xn = make_double2(0.0, 0.0), fnp2 = make_double2(0.0, 0.0);
+  for (int i = I; i >= 1; --i) {
+    const int n = p + 2 * i;
+    const double2 fn = x[n];
+    const double2 fnm2 = x[n - 2];
+    const double a1 = t1[n], a2 = t2[n], a3 = t3[n];
+    const double U = -alpha * a3;
+    const double rd = RD[(size_t)n * NK];
+    double2 xi;
+    xi.x = fma(-U, xn.x, fma(a1, fnm2.x, fma(-a2, fn.x, a3 * fnp2.x))) * rd;
+    xi.y = fma(-U, xn.y, fma(a1, fnm2.y, fma(-a2, fn.y, a3 * fnp2.y))) * rd;
+    x[n] = xi;
+    fnp2 = fn;
+    xn = xi;
+  }
+  double2 P = make_double2(0.0, 0.0), sp = make_double2(0.0, 0.0);
+  for (int i = 1; i <= I; ++i) {
+    const int n = p + 2 * i;
+    const double y = Y[(size_t)n * NK];
+    const double2 xv = x[n];
+    P.x = fma(y, P.x, xv.x);
+    P.y = fma(y, P.y, xv.y);
+    x[n] = P;
+    const double wb = neumann ? (double)n * (double)n : 1.0;
+    sp.x = fma(wb, P.x, sp.x);
+    sp.y = fma(wb, P.y, sp.y);
+  }
+  const double2 a0 = make_double2(-sp.x * rsq, -sp.y * rsq);
+  x[p] = a0;
+  for (int i = 1; i <= I; ++i) {
+    const int n = p + 2 * i;
+    const double q = Q[(size_t)n * NK];
+    double2 v = x[n];
+    v.x = fma(q, a0.x, v.x);
+    v.y = fma(q, a0.y, v.y);
+    x[n] = v;
+  }
+}
+
+// zsolve: TL lines per CTA, thread = (line, parity).  R holds [omega | theta-w | phi] right-hand
+// sides on entry and the solved sums / new phi on exit (line-major, like the state).
+__global__ void __launch_bounds__(2 * TL) zsolve_kernel(GridDev g, double2* __restrict__ R,
+                                                        long long fs, int nlines) {
+  extern __shared__ double2 ssm[];
   const int Nz = g.nz, N = g.N;
+  double2* tile = ssm;
+  double* t1 = reinterpret_cast<double*>(ssm + TL * Nz);
+  double* t2 = t1 + Nz;
+  double* t3 = t2 + Nz;
+  const int tid = threadIdx.x;
+  const int l = tid >> 1, p = tid & 1;
+  const int line0 = blockIdx.x * TL;
+  const int line = line0 + l;
+  for (int n = tid; n < Nz; n += blockDim.x) {
+    t1[n] = g.go1[n];
+    t2[n] = g.go2[n];
+    t3[n] = g.go3[n];
+  }
+  int mx = 0, j = 0, K = 0;
+  double kx = 0.0, ky = 0.0;
+  const bool valid = line < nlines;
+  if (valid) {
+    line_wavenumbers(g, line, mx, j, kx, ky);
+    K = line_K(g, mx, j);
+  }
+  const double k2 = kx * kx + ky * ky;
+  const bool is00 = (mx == 0 && j == 0);
+  const int ntile = min(TL, nlines - line0);
+  for (int prob = 0; prob < 3; ++prob) {
+    double2* Rp = R + prob * fs + (size_t)line0 * Nz;
+    for (int idx = tid; idx < ntile * Nz; idx += blockDim.x) tile[idx] = Rp[idx];
+    __syncthreads();
+    if (valid) {
+      double2* row = tile + l * Nz;
+      if (prob == 0) {
+        tau_sweep_c(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
+                    fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
+      } else if (prob == 1) {
+        if (is00) {
+          for (int n = p; n <= N; n += 2) row[n] = make_double2(0.0, 0.0);
+        } else {
+          tau_sweep_c(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
+                      fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
+          tau_sweep_c(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K),
+                      fac_ptr(g, 1, 1, K), fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
+          // influence matrix: Omega = Omega_p + c Omega_h with D Omega(+-1) = 0 (parity p)
+          const double* oh = fac_oh(g, K);
+          double2 s = make_double2(0.0, 0.0);
+          for (int n = p; n <= N; n += 2) {
+            const double n2 = (double)n * (double)n;
+            s.x = fma(n2, row[n].x, s.x);
+            s.y = fma(n2, row[n].y, s.y);
+          }
+          const double rsh = fac_rsh(g, p, K);
+          const double2 c = make_double2(-s.x * rsh, -s.y * rsh);
+          for (int n = p; n <= N; n += 2) {
+            const double h = oh[(size_t)n * g.NK];
+            double2 v = row[n];
+            v.x = fma(c.x, h, v.x);
+            v.y = fma(c.y, h, v.y);
+            row[n] = v;
+          }
+        }
+      } else {
+        const double a = k2 + g.lam;
+        for (int rep = 0; rep < 2; ++rep)
+          tau_sweep_c(row, p, N, a, true, t1, t2, t3, fac_ptr(g, 2, 0, K), fac_ptr(g, 2, 1, K),
+                      fac_ptr(g, 2, 2, K), g.NK, fac_rsq(g, 2, p, K));
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < ntile * Nz; idx += blockDim.x) Rp[idx] = tile[idx];
+    __syncthreads();
+  }
+}
+
+// ---- operator table (init time) -------------------------------------------------------------
+__device__ __forceinline__ void K_wavenumbers(const GridDev& g, int K, double& k2) {
+  const int h = g.ny / 2;
+  const int mx = K / (h + 1), amy = K - mx * (h + 1);
+  const double kx = 6.283185307179586476925 * mx / g.lx;
+  const double ky = 6.283185307179586476925 * amy / g.ly;
+  k2 = kx * kx + ky * ky;
+}
+
+// thread = (K, op, parity): elimination from the top coefficient down; the boundary row
+// closes the system at n = p
+__global__ void factor_kernel(GridDev g, double* __restrict__ fac) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.NK * 6) return;
+  const int K = t / 6, op = (t % 6) >> 1, p = t & 1;
+  double k2;
+  K_wavenumbers(g, K, k2);
+  const double alpha = (op == 0) ? k2 + g.beta : (op == 1) ? k2 : k2 + g.lam;
+  const bool neumann = (op == 2);
+  const int N = g.N, NK = g.NK, Nz = g.nz;
+  double* Y = fac + ((size_t)(op * 3 + 0) * Nz) * NK + K;
+  double* RD = fac + ((size_t)(op * 3 + 1) * Nz) * NK + K;
+  double* Q = fac + ((size_t)(op * 3 + 2) * Nz) * NK + K;
+  const int I = (N - p) / 2;
+  double ynext = 0.0;
+  for (int i = I; i >= 1; --i) {
+    const int n = p + 2 * i;
+    const double L = -alpha * g.go1[n];
+    const double Dg = 1.0 + alpha * g.go2[n];
+    const double U = -alpha * g.go3[n];
+    const double rd = 1.0 / fma(U, ynext, Dg);
+    const double y = -L * rd;
+    Y[(size_t)n * NK] = y;
+    RD[(size_t)n * NK] = rd;
+    ynext = y;
+  }
+  double q = 1.0;
+  Y[(size_t)p * NK] = 0.0;
+  RD[(size_t)p * NK] = 0.0;
+  Q[(size_t)p * NK] = 1.0;
+  double sq = neumann ? (double)(p * p) : 1.0;
+  for (int i = 1; i <= I; ++i) {
+    const int n = p + 2 * i;
+    q *= Y[(size_t)n * NK];
+    Q[(size_t)n * NK] = q;
+    sq = fma(neumann ? (double)n * (double)n : 1.0, q, sq);
+  }
+  fac[(size_t)9 * Nz * NK + (size_t)(op * 2 + p) * NK + K] = 1.0 / sq;
+}
+
+// thread = (K, parity): Psi_h = Q_0 / SQ_0 (operator 0 with unit wall value), then
+// (D^2 - k^2) Omega_h = Psi_h with Dirichlet walls; also 1 / sum n^2 Omega_h
+__global__ void homog_kernel(GridDev g, double* __restrict__ fac) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.NK * 2) return;
+  const int K = t >> 1, p = t & 1;
+  const int N = g.N, NK = g.NK, Nz = g.nz;
+  double k2;
+  K_wavenumbers(g, K, k2);
+  double* oh = fac + (size_t)9 * Nz * NK + (size_t)6 * NK + K;
+  const double* Q0 = fac + ((size_t)(0 * 3 + 2) * Nz) * NK + K;
+  const double rsq0 = fac[(size_t)9 * Nz * NK + (size_t)(0 * 2 + p) * NK + K];
+  for (int n = p; n <= N; n += 2) oh[(size_t)n * NK] = Q0[(size_t)n * NK] * rsq0;
+  // Dirichlet sweep with operator 1 (real, strided)
+  const double* Y = fac + ((size_t)(1 * 3 + 0) * Nz) * NK + K;
+  const double* RD = fac + ((size_t)(1 * 3 + 1) * Nz) * NK + K;
+  const double* Q = fac + ((size_t)(1 * 3 + 2) * Nz) * NK + K;
+  const double rsq = fac[(size_t)9 * Nz * NK + (size_t)(1 * 2 + p) * NK + K];
+  const int I = (N - p) / 2;
+  double xn = 0.0, fnp2 = 0.0;
+  for (int i = I; i >= 1; --i) {
+    const int n = p + 2 * i;
+    const double fn = oh[(size_t)n * NK];
+    const double fnm2 = oh[(size_t)(n - 2) * NK];
+    const double U = -k2 * g.go3[n];
+    const double xi = fma(-U, xn, fma(g.go1[n], fnm2, fma(-g.go2[n], fn, g.go3[n] * fnp2))) *
+                      RD[(size_t)n * NK];
+    oh[(size_t)n * NK] = xi;
+    fnp2 = fn;
+    xn = xi;
+  }
+  double P = 0.0, sp = 0.0;
+  for (int i = 1; i <= I; ++i) {
+    const int n = p + 2 * i;
+    P = fma(Y[(size_t)n * NK], P, oh[(size_t)n * NK]);
+    oh[(size_t)n * NK] = P;
+    sp += P;
+  }
+  const double a0 = -sp * rsq;
+  oh[(size_t)p * NK] = a0;
+  double sh = 0.0;
+  for (int i = 0; i <= I; ++i) {
+    const int n = p + 2 * i;
+    double v = oh[(size_t)n * NK];
+    if (i > 0) v = fma(Q[(size_t)n * NK], a0, v);
+    oh[(size_t)n * NK] = v;
+    sh = fma((double)n * (double)n, v, sh);
+  }
+  fac[(size_t)10 * Nz * NK + (size_t)6 * NK + (size_t)p * NK + K] = (sh != 0.0) ? 1.0 / sh : 0.0;
+}
+
+// ---- zbwd: update + the seven fields for the non-linear terms ------------------------------
+// UPDATE = 1: new state = (solved sums - old state) for omega, w and phi from R; = 0: state as is.
+// Output: u, v (continuity + omega_z definition), w, phi, i kx phi, i ky phi, D phi, backward
+// DCT-I to samples in z.
+template <typename T, int UPDATE>
+__global__ void __launch_bounds__(ZT) zbwd_kernel(GridDev g, const double2* __restrict__ R,
+                                                  double2* __restrict__ st_om,
+                                                  double2* __restrict__ st_w,
+                                                  double2* __restrict__ st_phi,
+                                                  typename C2<T>::t* __restrict__ bw,
+                                                  long long fs, FftPlan pz) {
+  typedef typename C2<T>::t T2;
+  extern __shared__ double2 zsm[];
+  const int Nz = g.nz, N = g.N;
+  const int line = blockIdx.x;
+  int mx, j;
+  double kx, ky;
+  line_wavenumbers(g, line, mx, j, kx, ky);
+  const size_t off = (size_t)line * Nz;
+  const int tid = threadIdx.x;
+  if (j == g.ny / 2) {
+    for (int idx = tid; idx < 7 * Nz; idx += blockDim.x) {
+      const int f = idx / Nz, n = idx - f * Nz;
+      bw[(long long)f * fs + off + n] = from_d2<T2>(make_double2(0.0, 0.0));
+    }
+    return;
+  }
+  const ZSmem z = carve(zsm, Nz, N);
+  const bool is00 = (mx == 0 && j == 0);
+  for (int n = tid; n < Nz; n += blockDim.x) {
+    double2 om = st_om[off + n], w = st_w[off + n], ph = st_phi[off + n];
+    if (UPDATE) {
+      om = R[off + n] - om;           // (q^{n+1} + q^n) - q^n
+      w = R[fs + off + n] - w;
+      ph = R[2 * fs + off + n];
+      st_om[off + n] = om;
+      st_w[off + n] = w;
+      st_phi[off + n] = ph;
+    }
+    LN(z, 10, Nz)[n] = om;
+    LN(z, 11, Nz)[n] = w;
+    LN(z, 12, Nz)[n] = ph;
+  }
+  __syncthreads();
   {
     double2* src[2] = {LN(z, 11, Nz), LN(z, 12, Nz)};
     double2* dst[2] = {LN(z, 13, Nz), LN(z, 14, Nz)};
-    dz_tasks(src, dst, 2, N);
+    dz_tasks(src, dst, 2, N, z.tmp);
   }
   __syncthreads();
   const double k2 = kx * kx + ky * ky;
   const double rk2 = is00 ? 0.0 : 1.0 / k2;
-  for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
+  for (int n = tid; n < Nz; n += blockDim.x) {
     const double2 om = LN(z, 10, Nz)[n];
     const double2 dw = LN(z, 13, Nz)[n];
     const double2 ph = LN(z, 12, Nz)[n];
@@ -239,202 +599,6 @@ __device__ void backward_fields(const ZSmem& z, const GridDev& g, double kx, dou
     const int cnt = (7 - f0 < NBF) ? 7 - f0 : NBF;
     dct_backward_lines_store<T2>(z, f0, cnt, Nz, N, pz, bw, fs, off, f0);
   }
-}
-
-template <typename T, int MODE>
-__global__ void __launch_bounds__(ZT) zline_kernel(GridDev g, const typename C2<T>::t* __restrict__ nl,
-                                                   typename C2<T>::t* __restrict__ bw, long long fs,
-                                                   double2* __restrict__ st_om,
-                                                   double2* __restrict__ st_w,
-                                                   double2* __restrict__ st_phi,
-                                                   double2* __restrict__ h_om,
-                                                   double2* __restrict__ h_w,
-                                                   double2* __restrict__ h_phi, int first,
-                                                   FftPlan pz) {
-  typedef typename C2<T>::t T2;
-  extern __shared__ double2 zsm[];
-  __shared__ double sq[6];
-  const int Nz = g.nz, N = g.N;
-  const int line = blockIdx.x;
-  int mx, j;
-  double kx, ky;
-  line_wavenumbers(g, line, mx, j, kx, ky);
-  const size_t off = (size_t)line * Nz;
-  const int tid = threadIdx.x;
-
-  if (j == g.ny / 2) {  // y Nyquist row: identically zero
-    for (int idx = tid; idx < 7 * Nz; idx += blockDim.x) {
-      const int f = idx / Nz, n = idx - f * Nz;
-      bw[(long long)f * fs + off + n] = from_d2<T2>(make_double2(0.0, 0.0));
-    }
-    return;
-  }
-  const ZSmem z = carve(zsm, Nz, N);
-  const bool is00 = (mx == 0 && j == 0);
-  const double k2 = kx * kx + ky * ky;
-
-  for (int n = tid; n < Nz; n += blockDim.x) {
-    LN(z, 10, Nz)[n] = st_om[off + n];
-    LN(z, 11, Nz)[n] = st_w[off + n];
-    LN(z, 12, Nz)[n] = st_phi[off + n];
-    z.t1[n] = g.go1[n];
-    z.t2[n] = g.go2[n];
-    z.t3[n] = g.go3[n];
-  }
-
-  if (MODE == 0) {
-    // ---- ten non-linear fields: samples -> Chebyshev coefficients
-    for (int idx = tid; idx < 10 * Nz; idx += blockDim.x) {
-      const int f = idx / Nz, n = idx - f * Nz;
-      LN(z, f, Nz)[n] = to_d2(nl[(long long)f * fs + off + n]);
-    }
-    __syncthreads();
-    for (int f0 = 0; f0 < 10; f0 += NBF) dct_forward_lines(z, f0, NBF, Nz, N, pz);
-    // lines: 0 Sxx 1 Syy 2 Szz 3 Sxy 4 Sxz 5 Syz 6 phi^3 7 u phi 8 v phi 9 w phi
-    {
-      double2* src[3] = {LN(z, 4, Nz), LN(z, 5, Nz), LN(z, 2, Nz)};
-      double2* dst[3] = {LN(z, 13, Nz), LN(z, 14, Nz), LN(z, 15, Nz)};
-      dz_tasks(src, dst, 3, N);
-    }
-    __syncthreads();
-    // S_i = i kx Sigma_ix + i ky Sigma_iy + D Sigma_iz
-    for (int n = tid; n < Nz; n += blockDim.x) {
-      const double2 sxx = LN(z, 0, Nz)[n], syy = LN(z, 1, Nz)[n];
-      const double2 sxy = LN(z, 3, Nz)[n], sxz = LN(z, 4, Nz)[n], syz = LN(z, 5, Nz)[n];
-      const double2 Sx = mul_i(kx * sxx + ky * sxy) + LN(z, 13, Nz)[n];
-      const double2 Sy = mul_i(kx * sxy + ky * syy) + LN(z, 14, Nz)[n];
-      const double2 Sz = mul_i(kx * sxz + ky * syz) + LN(z, 15, Nz)[n];
-      double2 hom;
-      if (is00) {  // mean flow: Sbar_x + i Sbar_y + (gx + i gy) delta_{n0}
-        hom = make_double2(Sx.x + (n == 0 ? g.gx : 0.0), Sy.x + (n == 0 ? g.gy : 0.0));
-      } else {
-        hom = mul_i(kx * Sy - ky * Sx);  // i kx S_y - i ky S_x
-      }
-      LN(z, 2, Nz)[n] = Sz;
-      LN(z, 3, Nz)[n] = hom;
-      LN(z, 4, Nz)[n] = mul_i(kx * Sx + ky * Sy);  // i kx S_x + i ky S_y
-      const double2 ph = LN(z, 12, Nz)[n];
-      LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * ph;  // G = phi^3 - (1+shat) phi
-      LN(z, 7, Nz)[n] = -1.0 * mul_i(kx * LN(z, 7, Nz)[n] + ky * LN(z, 8, Nz)[n]);
-    }
-    __syncthreads();
-    {
-      double2* src[4] = {LN(z, 9, Nz), LN(z, 4, Nz), LN(z, 6, Nz), LN(z, 11, Nz)};
-      double2* dst[4] = {LN(z, 13, Nz), LN(z, 14, Nz), LN(z, 15, Nz), LN(z, 5, Nz)};
-      dz_tasks(src, dst, 4, N);
-    }
-    __syncthreads();
-    {
-      double2* src[2] = {LN(z, 15, Nz), LN(z, 5, Nz)};
-      double2* dst[2] = {LN(z, 8, Nz), LN(z, 9, Nz)};
-      dz_tasks(src, dst, 2, N);
-    }
-    __syncthreads();
-    // h_w, S_phi, theta^n = (D^2 - k^2) w^n; AB2; right-hand sides
-    const double twoRe = 2.0 * g.re;
-    const double cphi = g.pe / (g.ch * g.ch);
-    const double rdt = 1.0 / g.dt;
-    const double rpe = 1.0 / g.pe;
-    for (int n = tid; n < Nz; n += blockDim.x) {
-      const double2 hw = is00 ? make_double2(0.0, 0.0)
-                              : (-k2) * LN(z, 2, Nz)[n] - LN(z, 14, Nz)[n];
-      const double2 sphi = LN(z, 7, Nz)[n] - LN(z, 13, Nz)[n] +
-                           rpe * (LN(z, 8, Nz)[n] - k2 * LN(z, 6, Nz)[n]);
-      const double2 hom = LN(z, 3, Nz)[n];
-      const double2 th = LN(z, 9, Nz)[n] - k2 * LN(z, 11, Nz)[n];
-      double2 Hom = hom, Hw = hw, Hphi = sphi;
-      if (!first) {
-        Hom = 1.5 * hom - 0.5 * h_om[off + n];
-        Hw = 1.5 * hw - 0.5 * h_w[off + n];
-        Hphi = 1.5 * sphi - 0.5 * h_phi[off + n];
-      }
-      h_om[off + n] = hom;
-      h_w[off + n] = hw;
-      h_phi[off + n] = sphi;
-      LN(z, 0, Nz)[n] = (-2.0 * g.beta) * LN(z, 10, Nz)[n] - twoRe * Hom;
-      LN(z, 1, Nz)[n] = (-2.0 * g.beta) * th - twoRe * Hw;
-      LN(z, 4, Nz)[n] = cphi * (rdt * LN(z, 12, Nz)[n] + Hphi);
-    }
-    // ---- factor the three operators (both parities)
-    if (tid < 6) {
-      const int op = tid >> 1, p = tid & 1;
-      const double alpha = (op == 0) ? k2 + g.beta : (op == 1) ? k2 : k2 + g.lam;
-      sq[tid] = tau_factor(alpha, p, N, op == 2, z.t1, z.t2, z.t3, z.Y + op * Nz,
-                           z.RD + op * Nz, z.Q + op * Nz);
-    }
-    __syncthreads();
-    // ---- solves: warp 0 omega / mean flow, warp 1 w (influence matrix), warp 2 phi
-    {
-      const int warp = tid >> 5, lane = tid & 31;
-      if (warp < 3 && lane < 4) {
-        const int p = lane & 1, comp = lane >> 1;
-        const int I = (N - p) / 2;
-        if (warp == 0) {
-          double* x = reinterpret_cast<double*>(LN(z, 0, Nz)) + comp;
-          tau_sweep(x, p, N, k2 + g.beta, false, 0.0, z.t1, z.t2, z.t3, z.Y, z.RD, z.Q, sq[p]);
-          double* o = reinterpret_cast<double*>(LN(z, 10, Nz)) + comp;
-          for (int i = 0; i <= I; ++i) {
-            const int n = p + 2 * i;
-            o[2 * n] = x[2 * n] - o[2 * n];
-          }
-        } else if (warp == 1) {
-          double* o = reinterpret_cast<double*>(LN(z, 11, Nz)) + comp;
-          if (is00) {
-            for (int i = 0; i <= I; ++i) o[2 * (p + 2 * i)] = 0.0;
-          } else {
-            double* x = reinterpret_cast<double*>(LN(z, 1, Nz)) + comp;
-            double* hx = reinterpret_cast<double*>(LN(z, 2, Nz)) + comp;
-            // particular pair: (D^2-k^2-beta) Psi = r, (D^2-k^2) Omega_p = Psi, Dirichlet 0
-            tau_sweep(x, p, N, k2 + g.beta, false, 0.0, z.t1, z.t2, z.t3, z.Y, z.RD, z.Q, sq[p]);
-            tau_sweep(x, p, N, k2, false, 0.0, z.t1, z.t2, z.t3, z.Y + Nz, z.RD + Nz, z.Q + Nz,
-                      sq[2 + p]);
-            // homogeneous pair of parity p: Psi_h = 1 at both walls (even) or +-1 (odd),
-            // i.e. Psi_h = Q / SQ of the beta operator; then (D^2 - k^2) Omega_h = Psi_h
-            for (int i = 0; i <= I; ++i) {
-              const int n = p + 2 * i;
-              hx[2 * n] = z.Q[n] / sq[p];
-            }
-            tau_sweep(hx, p, N, k2, false, 0.0, z.t1, z.t2, z.t3, z.Y + Nz, z.RD + Nz,
-                      z.Q + Nz, sq[2 + p]);
-            // choose c so that D Omega(+-1) = 0: sum n^2 (Omega_p + c Omega_h) = 0 per parity
-            double sp = 0.0, sh = 0.0;
-            for (int i = 0; i <= I; ++i) {
-              const int n = p + 2 * i;
-              const double n2 = (double)n * (double)n;
-              sp = fma(n2, x[2 * n], sp);
-              sh = fma(n2, hx[2 * n], sh);
-            }
-            const double c = -sp / sh;
-            for (int i = 0; i <= I; ++i) {
-              const int n = p + 2 * i;
-              o[2 * n] = fma(c, hx[2 * n], x[2 * n]) - o[2 * n];
-            }
-          }
-        } else {
-          double* x = reinterpret_cast<double*>(LN(z, 4, Nz)) + comp;
-          const double a = k2 + g.lam;
-          tau_sweep(x, p, N, a, true, 0.0, z.t1, z.t2, z.t3, z.Y + 2 * Nz, z.RD + 2 * Nz,
-                    z.Q + 2 * Nz, sq[4 + p]);
-          tau_sweep(x, p, N, a, true, 0.0, z.t1, z.t2, z.t3, z.Y + 2 * Nz, z.RD + 2 * Nz,
-                    z.Q + 2 * Nz, sq[4 + p]);
-          double* o = reinterpret_cast<double*>(LN(z, 12, Nz)) + comp;
-          for (int i = 0; i <= I; ++i) {
-            const int n = p + 2 * i;
-            o[2 * n] = x[2 * n];
-          }
-        }
-      }
-    }
-    __syncthreads();
-    for (int n = tid; n < Nz; n += blockDim.x) {
-      st_om[off + n] = LN(z, 10, Nz)[n];
-      st_w[off + n] = LN(z, 11, Nz)[n];
-      st_phi[off + n] = LN(z, 12, Nz)[n];
-    }
-  } else {
-    __syncthreads();
-  }
-  backward_fields<T2>(z, g, kx, ky, is00, pz, bw, fs, off);
 }
 
 // set_fields projection: u, v, w, phi samples (after the x/y transforms) -> state
@@ -571,36 +735,71 @@ __global__ void diag_final_kernel(GridDev g, int nblk, const double* __restrict_
 
 size_t zline_smem(const GridDev& g) {
   return (size_t)(NLINES * g.nz + 2 * NBF * 2 * g.N) * sizeof(double2) +
-         (size_t)12 * g.nz * sizeof(double);
+         (size_t)(ZT / 32) * (g.N / 2 + 2) * sizeof(double);
 }
 
-template <typename T, int MODE>
-static cudaError_t launch_zline_t(const GridDev& g, const void* nl, void* bw, long long fs,
-                                  double2* st_om, double2* st_w, double2* st_phi, double2* h_om,
-                                  double2* h_w, double2* h_phi, int first, const FftPlan& pz,
-                                  cudaStream_t s) {
-  typedef typename C2<T>::t T2;
-  const size_t smem = zline_smem(g);
-  static int cur = 0;
-  cudaError_t e = ensure_smem(zline_kernel<T, MODE>, smem, &cur);
+size_t fac_doubles(const GridDev& g) { return ((size_t)10 * g.nz + 8) * g.NK; }
+
+cudaError_t build_factor_table(const GridDev& g, double* fac, cudaStream_t s) {
+  const int n1 = g.NK * 6, n2 = g.NK * 2;
+  factor_kernel<<<(n1 + 127) / 128, 128, 0, s>>>(g, fac);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  zline_kernel<T, MODE><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const T2*)nl, (T2*)bw, fs, st_om, st_w,
-                                                     st_phi, h_om, h_w, h_phi, first, pz);
+  homog_kernel<<<(n2 + 127) / 128, 128, 0, s>>>(g, fac);
   return cudaGetLastError();
 }
 
-cudaError_t launch_zline(int mode, int prec, const GridDev& g, const void* nl, void* bw,
-                         long long fs, double2* st_om, double2* st_w, double2* st_phi,
-                         double2* h_om, double2* h_w, double2* h_phi, int first,
-                         const FftPlan& pz, cudaStream_t s) {
+cudaError_t launch_zrhs(int prec, const GridDev& g, const void* nl, long long fs,
+                        const double2* st_om, const double2* st_w, const double2* st_phi,
+                        double2* h_om, double2* h_w, double2* h_phi, double2* R, int first,
+                        const FftPlan& pz, cudaStream_t s) {
+  const size_t smem = zline_smem(g);
+  cudaError_t e;
   if (prec == 0) {
-    if (mode == 0)
-      return launch_zline_t<double, 0>(g, nl, bw, fs, st_om, st_w, st_phi, h_om, h_w, h_phi, first, pz, s);
-    return launch_zline_t<double, 1>(g, nl, bw, fs, st_om, st_w, st_phi, h_om, h_w, h_phi, first, pz, s);
+    static int cur = 0;
+    if ((e = ensure_smem(zrhs_kernel<double>, smem, &cur)) != cudaSuccess) return e;
+    zrhs_kernel<double><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const double2*)nl, fs, st_om, st_w, st_phi,
+                                                      h_om, h_w, h_phi, R, first, pz);
+  } else {
+    static int cur = 0;
+    if ((e = ensure_smem(zrhs_kernel<float>, smem, &cur)) != cudaSuccess) return e;
+    zrhs_kernel<float><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const float2*)nl, fs, st_om, st_w, st_phi,
+                                                     h_om, h_w, h_phi, R, first, pz);
   }
-  if (mode == 0)
-    return launch_zline_t<float, 0>(g, nl, bw, fs, st_om, st_w, st_phi, h_om, h_w, h_phi, first, pz, s);
-  return launch_zline_t<float, 1>(g, nl, bw, fs, st_om, st_w, st_phi, h_om, h_w, h_phi, first, pz, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zsolve(const GridDev& g, double2* R, long long fs, cudaStream_t s) {
+  const size_t smem = (size_t)TL * g.nz * sizeof(double2) + (size_t)3 * g.nz * sizeof(double);
+  static int cur = 0;
+  cudaError_t e = ensure_smem(zsolve_kernel, smem, &cur);
+  if (e != cudaSuccess) return e;
+  const int nlines = g.Mx * g.ny;
+  zsolve_kernel<<<(nlines + TL - 1) / TL, 2 * TL, smem, s>>>(g, R, fs, nlines);
+  return cudaGetLastError();
+}
+
+template <typename T, int UPDATE>
+static cudaError_t launch_zbwd_t(const GridDev& g, const double2* R, double2* st_om,
+                                 double2* st_w, double2* st_phi, void* bw, long long fs,
+                                 const FftPlan& pz, cudaStream_t s) {
+  typedef typename C2<T>::t T2;
+  const size_t smem = zline_smem(g);
+  static int cur = 0;
+  cudaError_t e = ensure_smem(zbwd_kernel<T, UPDATE>, smem, &cur);
+  if (e != cudaSuccess) return e;
+  zbwd_kernel<T, UPDATE><<<g.Mx * g.ny, ZT, smem, s>>>(g, R, st_om, st_w, st_phi, (T2*)bw, fs, pz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zbwd(int update, int prec, const GridDev& g, const double2* R,
+                        double2* st_om, double2* st_w, double2* st_phi, void* bw, long long fs,
+                        const FftPlan& pz, cudaStream_t s) {
+  if (prec == 0)
+    return update ? launch_zbwd_t<double, 1>(g, R, st_om, st_w, st_phi, bw, fs, pz, s)
+                  : launch_zbwd_t<double, 0>(g, R, st_om, st_w, st_phi, bw, fs, pz, s);
+  return update ? launch_zbwd_t<float, 1>(g, R, st_om, st_w, st_phi, bw, fs, pz, s)
+                : launch_zbwd_t<float, 0>(g, R, st_om, st_w, st_phi, bw, fs, pz, s);
 }
 
 cudaError_t launch_project(const GridDev& g, const double2* uvwp, long long fs, double2* st_om,
