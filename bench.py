@@ -3,7 +3,8 @@
 python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
 Prints ONE JSON line (rank 0).  A step is one full time step (Sec. 2.2 steps i)-v)) of one
-channel: Chebyshev-tau z-line kernel, y backward pass, fused x-line kernel, y forward pass.
+channel: six kernels - z right-hand sides (Chebyshev DCTs, assembly, AB2), tau solves, z update
++ backward DCTs, y backward pass, fused x-line kernel (transforms + products), y forward pass.
 Default workload: the 128 x 128 x 129 FP64 channel (Re_tau = 150, 8 drops).  Points = nx ny nz
 (unpadded); the metric is Mpoints * steps / s of the whole job.
 
@@ -62,18 +63,19 @@ def kernel_work(w, prec):
     lines = Mx * ny
     # complex DCT-I of a line = complex FFT of 2N points; a derivative = 4 flops per coefficient
     dct = fft_flops(2 * N)
-    zrhs_fl = lines * (10 * dct + 9 * 4 * nz + 120 * nz)
-    zrhs_by = S * (b * 10 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)   # NL, state, hist in/out, R out
+    # zrhs: 9 non-linear fields in, combined to 7 lines, 7 DCTs, 9 derivatives, assembly
+    zrhs_fl = lines * (7 * dct + 9 * 4 * nz + 150 * nz)
+    zrhs_by = S * (b * 9 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)   # NL, state, hist in/out, R out
     zsolve_fl = lines * nz * (5 * 30 + 8)                       # 5 sweeps + influence correction
     zsolve_by = S * 16 * 3 * 2
-    zbwd_fl = lines * (7 * dct + 2 * 4 * nz + 40 * nz)
-    zbwd_by = S * (16 * 3 + 16 * 2 + 16 * 3 + b * 7)             # R, state in, state out, 7 out
-    yb_fl = 7 * Mx * nz * fft_flops(Py)
-    yb_by = 7 * (S + Y) * b
-    x_fl = Py * nz * (17 * 0.5 * fft_flops(Px) + 60 * Px)       # packed real FFTs + products
-    x_by = 17 * Y * b
-    yf_fl = 10 * Mx * nz * fft_flops(Py)
-    yf_by = 10 * (S + Y) * b
+    zbwd_fl = lines * (5 * dct + 2 * 4 * nz + 40 * nz)
+    zbwd_by = S * (16 * 3 + 16 * 2 + 16 * 3 + b * 5)             # R, state in, state out, 5 out
+    yb_fl = 6 * Mx * nz * fft_flops(Py)
+    yb_by = (5 * S + 6 * Y) * b
+    x_fl = Py * nz * (16 * 0.5 * fft_flops(Px) + 45 * Px)       # packed real FFTs + products
+    x_by = 15 * Y * b
+    yf_fl = 9 * Mx * nz * fft_flops(Py)
+    yf_by = 9 * (S + Y) * b
     return {"zrhs": (zrhs_fl, zrhs_by), "zsolve": (zsolve_fl, zsolve_by),
             "zbwd": (zbwd_fl, zbwd_by), "ybwd": (yb_fl, yb_by), "xline": (x_fl, x_by),
             "yfwd": (yf_fl, yf_by)}

@@ -151,13 +151,14 @@ int ch_set_spectral(ch_grid* g, const double* omega, const double* w, const doub
  * ch_transform_forward: physical (nz,ny,nx) float64 -> spectral coefficients (layout above),
  *   Fourier in x and y (1/(nx ny)) then the Chebyshev DCT-I (Sec. 3.2.1).
  * ch_transform_backward: the inverse, evaluated on the unpadded grid.
- * ch_nonlinear: the ten non-linear coefficient arrays of the current state, in the order
- *   Sxx, Syy, Szz, Sxy, Sxz, Syz (Sigma_ij = -u_i u_j + kappa T_ij, Eq. (kort)), phi^3, u phi,
- *   v phi, w phi, formed on the 3/2-padded grid and returned as complex float64 coefficients
- *   (10 consecutive spectral fields) - steps ii) and vi) of Sec. 2.2. */
+ * ch_nonlinear: the nine non-linear coefficient arrays of the current state the step uses, in
+ *   the order Sxx - Szz, Syy - Szz, Sxy, Sxz, Syz (Sigma_ij = -u_i u_j + kappa T_ij, Eq. (kort);
+ *   the isotropic part Szz delta_ij is a gradient and does not enter Eqs. (omegaz), (ww)), phi^3,
+ *   u phi, v phi, w phi, formed on the 3/2-padded grid and returned as complex float64
+ *   coefficients (9 consecutive spectral fields) - steps ii) and vi) of Sec. 2.2. */
 int ch_transform_forward(ch_grid* g, const double* phys, double* spec);
 int ch_transform_backward(ch_grid* g, const double* spec, double* phys);
-int ch_nonlinear(ch_grid* g, double* out10);
+int ch_nonlinear(ch_grid* g, double* out9);
 
 /* Allocation-free variant of ch_transform_forward, for callers that must not allocate device
  * memory when they call it: code running while a stream is being captured into a CUDA graph

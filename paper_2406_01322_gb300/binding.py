@@ -269,6 +269,6 @@ class Grid:
         return out
 
     def nonlinear(self):
-        out = torch.empty((10,) + self.spec_shape, dtype=torch.complex128, device=self.device)
+        out = torch.empty((9,) + self.spec_shape, dtype=torch.complex128, device=self.device)
         _ck("ch_nonlinear", lib().ch_nonlinear(self.h, _ptr(out)))
         return out

@@ -161,6 +161,19 @@ int make_plan(ch_grid* G, int n, int prec, FftPlan* pl) {
   return CH_OK;
 }
 
+// fields through the step: 5 backward (u v w phi Dphi) -> 6 y-padded (phi_y added by the y
+// pass) -> 9 products (Sxx-Szz Syy-Szz Sxy Sxz Syz phi^3 u phi v phi w phi)
+constexpr int kBw = 5, kYa = 6, kNl = 9;
+
+chf::YMap step_ymap() {
+  chf::YMap m;
+  const int src[kYa] = {0, 1, 2, 3, 3, 4};  // u v w phi (phi -> i ky phi) Dphi
+  for (int f = 0; f < chf::YMap::kMax; ++f) m.src[f] = f < kYa ? src[f] : 0;
+  m.dy_mask = 1u << 4;
+  m.kys = 0.0;
+  return m;
+}
+
 #define CK(x)                                       \
   do {                                              \
     cudaError_t e__ = (x);                          \
@@ -175,24 +188,41 @@ int make_plan(ch_grid* G, int n, int prec, FftPlan* pl) {
 int eval_nonlinear(ch_grid* G) {
   const GridDev& g = G->g;
   cudaStream_t s = G->stream;
-  CK(chf::launch_zbwd(0, G->prec, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s));
-  CK(chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s));
+  const chf::YMap ym = step_ymap();
+  CK(chf::launch_zbwd(0, G->prec, kBw, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s));
+  CK(chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, kYa, G->fs, G->fsy, 1.0, G->py[G->prec], s, &ym));
   CK(chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s));
-  CK(chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, 10, G->fsy, G->fs,
+  CK(chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, kNl, G->fsy, G->fs,
                        1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s));
   return CH_OK;
 }
 
-int launch_step(ch_grid* G, int first, cudaStream_t s) {
+// The step's launch schedule (the only copy): zrhs, zsolve, zbwd, y backward, x line, y forward.
+// ev, when given, holds CH_STEP_KERNELS events recorded after each launch.
+int launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   const GridDev& g = G->g;
-  CK(chf::launch_zrhs(G->prec, g, G->nl, G->fs, G->om, G->w, G->phi, G->hom, G->hw, G->hphi, G->R,
-                      first, G->pz, s));
-  CK(chf::launch_zsolve(g, G->R, G->fs, s));
-  CK(chf::launch_zbwd(1, G->prec, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s));
-  CK(chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s));
-  CK(chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s));
-  CK(chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, 10, G->fsy, G->fs,
-                       1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s));
+  const chf::YMap ym = step_ymap();
+  cudaError_t e[CH_STEP_KERNELS];
+  e[0] = chf::launch_zrhs(G->prec, g, G->nl, G->fs, G->om, G->w, G->phi, G->hom, G->hw, G->hphi,
+                          G->R, first, G->pz, s);
+  if (ev) cudaEventRecord(ev[0], s);
+  e[1] = chf::launch_zsolve(g, G->R, G->fs, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  e[2] = chf::launch_zbwd(1, G->prec, kBw, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s);
+  if (ev) cudaEventRecord(ev[2], s);
+  e[3] = chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, kYa, G->fs, G->fsy, 1.0,
+                           G->py[G->prec], s, &ym);
+  if (ev) cudaEventRecord(ev[3], s);
+  e[4] = chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s);
+  if (ev) cudaEventRecord(ev[4], s);
+  e[5] = chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, kNl, G->fsy, G->fs,
+                           1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s);
+  if (ev) cudaEventRecord(ev[5], s);
+  for (int k = 0; k < CH_STEP_KERNELS; ++k)
+    if (e[k] != cudaSuccess) {
+      cudaGetLastError();
+      return CH_ERR_CUDA;
+    }
   return CH_OK;
 }
 
@@ -200,7 +230,7 @@ int launch_step(ch_grid* G, int first, cudaStream_t s) {
 int state_to_phys7(ch_grid* G, int nf) {
   const GridDev& g = G->g;
   cudaStream_t s = G->stream;
-  CK(chf::launch_zbwd(0, 0, g, G->R, G->om, G->w, G->phi, G->auxA, G->fs, G->pz, s));
+  CK(chf::launch_zbwd(0, 0, 7, g, G->R, G->om, G->w, G->phi, G->auxA, G->fs, G->pz, s));
   CK(chf::launch_ypass(1, 0, g, g.ny, G->auxA, G->auxB, nf, G->fs, G->fs, 1.0, G->pyu, s));
   CK(chf::launch_x_c2r(g, G->auxB, G->phys7, nf, G->fs, G->fsp, G->pxu, s));
   return CH_OK;
@@ -303,10 +333,10 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   G->hom = (double2*)A(sb);
   G->hw = (double2*)A(sb);
   G->hphi = (double2*)A(sb);
-  G->nl = A((size_t)10 * G->fs * esz);
-  G->bw = A((size_t)7 * G->fs * esz);
-  G->ya = A((size_t)7 * G->fsy * esz);
-  G->yb = A((size_t)10 * G->fsy * esz);
+  G->nl = A((size_t)kNl * G->fs * esz);
+  G->bw = A((size_t)kBw * G->fs * esz);
+  G->ya = A((size_t)kYa * G->fsy * esz);
+  G->yb = A((size_t)kNl * G->fsy * esz);
   G->auxA = (double2*)A((size_t)7 * sb);
   G->auxB = (double2*)A((size_t)7 * sb);
   G->phys7 = (double*)A((size_t)7 * G->fsp * sizeof(double));
@@ -474,25 +504,10 @@ int ch_step_timed(ch_grid* G, int nsteps, double* kernel_ms, double* total_ms) {
   const int nev = NKER * nsteps + 1;
   std::vector<cudaEvent_t> ev(nev);
   for (int i = 0; i < nev; ++i) CK(cudaEventCreate(&ev[i]));
-  const GridDev& g = G->g;
-  cudaStream_t s = G->stream;
   int st = CH_OK;
-  CK(cudaEventRecord(ev[0], s));
+  CK(cudaEventRecord(ev[0], G->stream));
   for (int i = 0; i < nsteps && st == CH_OK; ++i) {
-    const int first = G->first;
-    cudaEvent_t* e = &ev[NKER * i];
-#define TK(k, call)                            \
-  if ((call) != cudaSuccess) st = CH_ERR_CUDA; \
-  cudaEventRecord(e[k + 1], s);
-    TK(0, chf::launch_zrhs(G->prec, g, G->nl, G->fs, G->om, G->w, G->phi, G->hom, G->hw, G->hphi,
-                           G->R, first, G->pz, s))
-    TK(1, chf::launch_zsolve(g, G->R, G->fs, s))
-    TK(2, chf::launch_zbwd(1, G->prec, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s))
-    TK(3, chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, 7, G->fs, G->fsy, 1.0, G->py[G->prec], s))
-    TK(4, chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s))
-    TK(5, chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, 10, G->fsy, G->fs,
-                            1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s))
-#undef TK
+    st = launch_step(G, G->first, G->stream, &ev[NKER * i + 1]);
     G->first = 0;
     G->nstep += 1;
     G->t += G->p.dt;
@@ -518,7 +533,7 @@ int ch_get_fields(ch_grid* G, double* u, double* v, double* w, double* phi) {
   if (!G || !u || !v || !w || !phi) return CH_ERR_ARG;
   const GridDev& g = G->g;
   cudaStream_t s = G->stream;
-  CK(chf::launch_zbwd(0, 0, g, G->R, G->om, G->w, G->phi, G->auxA, G->fs, G->pz, s));
+  CK(chf::launch_zbwd(0, 0, 7, g, G->R, G->om, G->w, G->phi, G->auxA, G->fs, G->pz, s));
   CK(chf::launch_ypass(1, 0, g, g.ny, G->auxA, G->auxB, 4, G->fs, G->fs, 1.0, G->pyu, s));
   double* f4[4] = {u, v, w, phi};
   for (int f = 0; f < 4; ++f)
@@ -668,7 +683,7 @@ int ch_transform_backward(ch_grid* G, const double* spec, double* phys) {
 int ch_nonlinear(ch_grid* G, double* out10) {
   if (!G || !out10) return CH_ERR_ARG;
   if (!G->fields_set) return CH_ERR_STATE;
-  CK(chf::launch_dct_lines(0, G->prec, G->g, G->nl, (double2*)out10, 10, G->fs, G->pz, G->stream));
+  CK(chf::launch_dct_lines(0, G->prec, G->g, G->nl, (double2*)out10, kNl, G->fs, G->pz, G->stream));
   return CH_OK;
 }
 

@@ -35,15 +35,16 @@ inline cudaError_t ensure_smem(K* kernel, size_t bytes, int* cur) {
 //   assembly, AB2 (history h_* updated), right-hand sides R = [omega | theta-w | phi] (3 fields).
 // zsolve: tau solves of every line (tiles of lines, one thread per elimination chain), in place
 //   on R: sums omega^{n+1}+omega^n, w^{n+1}+w^n and phi^{n+1}.
-// zbwd: update = 1: new state from R; then the 7 fields for the non-linear terms, backward DCT
-//   into bw (precision prec).  update = 0: from the state as is.
+// zbwd: update = 1: new state from R; then the fields for the non-linear terms, backward DCT
+//   into bw (precision prec).  update = 0: from the state as is.  nout = 5: u v w phi D phi
+//   (the step); nout = 7: u v w phi i kx phi, i ky phi, D phi (fp64, update = 0 only).
 // Fields are (Mx, Ny, Nz) complex with field stride fs elements.
 cudaError_t launch_zrhs(int prec, const GridDev& g, const void* nl, long long fs,
                         const double2* st_om, const double2* st_w, const double2* st_phi,
                         double2* h_om, double2* h_w, double2* h_phi, double2* R, int first,
                         const FftPlan& pz, cudaStream_t s);
 cudaError_t launch_zsolve(const GridDev& g, double2* R, long long fs, cudaStream_t s);
-cudaError_t launch_zbwd(int update, int prec, const GridDev& g, const double2* R,
+cudaError_t launch_zbwd(int update, int prec, int nout, const GridDev& g, const double2* R,
                         double2* st_om, double2* st_w, double2* st_phi, void* bw, long long fs,
                         const FftPlan& pz, cudaStream_t s);
 size_t zline_smem(const GridDev& g);
@@ -62,13 +63,24 @@ cudaError_t launch_project(const GridDev& g, const double2* uvwp, long long fs, 
 cudaError_t launch_dct_lines(int dir, int prec, const GridDev& g, const void* in, double2* out,
                              int nf, long long fs, const FftPlan& pz, cudaStream_t s);
 
+// y pass field map: output field f reads input field src[f]; bit f of dy_mask makes the
+// backward pass output i ky times the input (d/dy); kys = 2 pi / ly (set by the launcher).
+struct YMap {
+  static const int kMax = 16;
+  int src[kMax];
+  unsigned dy_mask;
+  double kys;
+};
+
 // y-direction pass.  dir 1: (Mx, Ny, Nz) modes -> (Mx, P, Nz) samples (zero padding);
 // dir 0: (Mx, P, Nz) samples -> (Mx, Ny, Nz) modes (truncation, Nyquist row zeroed), times scale.
+// nf output fields; map == nullptr is the identity map.
 cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void* in, void* out,
                          int nf, long long fs_in, long long fs_out, double scale,
-                         const FftPlan& py, cudaStream_t s);
+                         const FftPlan& py, cudaStream_t s, const YMap* map = nullptr);
 
-// fused x-line kernel: 7 fields (Mx, Py, Nz) -> c2r (Px) -> 10 products -> r2c -> 10 fields.
+// fused x-line kernel: 6 fields u v w phi phi_y phi_z (Mx, Py, Nz) -> 7 c2r (Px, with
+// phi_x = i kx phi) -> 9 products -> r2c -> 9 fields.
 cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out10, long long fs,
                          double scale, const FftPlan& px, cudaStream_t s);
 

@@ -24,23 +24,29 @@ template <typename T, bool INV>
 __global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __restrict__ in,
                                                    typename C2<T>::t* __restrict__ out, int Mx,
                                                    int Ny, int P, int Nz, int TZ, long long fs_in,
-                                                   long long fs_out, T scale, FftPlan pl) {
+                                                   long long fs_out, T scale, FftPlan pl,
+                                                   YMap map) {
   typedef typename C2<T>::t T2;
   extern __shared__ unsigned char ysm_raw[];
   T2* A = reinterpret_cast<T2*>(ysm_raw);
   T2* B = A + TZ * P;
   const int z0 = blockIdx.x * TZ;
   const int mx = blockIdx.y;
-  const int f = blockIdx.z;
+  const int f = blockIdx.z;          // output field
   const int h = Ny / 2;
   const T2 zero = mk((T)0, (T)0);
   if (INV) {
-    const T2* src = in + f * fs_in + (size_t)mx * Ny * Nz;
+    const T2* src = in + map.src[f] * fs_in + (size_t)mx * Ny * Nz;
+    const bool dy = (map.dy_mask >> f) & 1;   // output d/dy of the input field (times i ky)
     for (int idx = threadIdx.x; idx < Ny * TZ; idx += blockDim.x) {
       const int jj = idx / TZ, zz = idx - jj * TZ;
       const int z = z0 + zz;
       T2 v = zero;
       if (z < Nz && jj != h) v = src[(size_t)jj * Nz + z];
+      if (dy) {
+        const T ky = (T)(map.kys * (double)((jj < h) ? jj : jj - Ny));
+        v = mk(-ky * v.y, ky * v.x);
+      }
       const int p = (jj < h) ? jj : P - Ny + jj;
       A[zz * P + p] = v;
     }
@@ -49,7 +55,7 @@ __global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __re
       A[zz * P + h + q] = zero;  // positions h .. P-h-1 hold no mode
     }
   } else {
-    const T2* src = in + f * fs_in + (size_t)mx * P * Nz;
+    const T2* src = in + map.src[f] * fs_in + (size_t)mx * P * Nz;
     for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
       const int y = idx / TZ, zz = idx - y * TZ;
       const int z = z0 + zz;
@@ -79,16 +85,19 @@ __global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __re
 
 // Fused x-line kernel.  One CTA per (pair of z rows, y).  The two rows z0, z0+1 of a field are
 // packed as one complex signal a + i b, so one complex FFT of length Px transforms both.
-//   1. seven inputs u, v, w, phi, phi_x, phi_y, phi_z: spectra (kx < Mx) -> c2r (zero padded);
-//   2. ten products Sigma_ij = -u_i u_j + kappa (|grad phi|^2 delta_ij - phi_i phi_j),
-//      phi^3, u phi, v phi, w phi at every padded point;
+//   1. six inputs u, v, w, phi, phi_y, phi_z (spectra kx < Mx); phi_x = i kx phi is formed from
+//      phi's spectrum; seven c2r transforms (zero padded);
+//   2. nine products at every padded point: Sigma_xx - Sigma_zz, Sigma_yy - Sigma_zz, Sigma_xy,
+//      Sigma_xz, Sigma_yz (Sigma_ij = -u_i u_j + kappa (|grad phi|^2 delta_ij - phi_i phi_j);
+//      the isotropic part Sigma_zz delta_ij is a gradient and drops out of h_omega and h_w),
+//      phi^3, u phi, v phi, w phi;
 //   3. r2c, keep kx < Mx, times `scale`.
 // Shared memory: 7 + 5 + 5 lines of Px complex values.
 template <typename T>
 __global__ void __launch_bounds__(XT) xline_kernel(const typename C2<T>::t* __restrict__ in,
                                                    typename C2<T>::t* __restrict__ out, int Mx,
                                                    int Px, int Py, int Nz, long long fs, T kappa,
-                                                   T scale, FftPlan pl) {
+                                                   T scale, T kxs, FftPlan pl) {
   typedef typename C2<T>::t T2;
   extern __shared__ unsigned char xsm_raw[];
   T2* S = reinterpret_cast<T2*>(xsm_raw);
@@ -103,12 +112,18 @@ __global__ void __launch_bounds__(XT) xline_kernel(const typename C2<T>::t* __re
   T2* X = S;
   T2* Y = S + 7 * Px;
   T2* L0 = (pl.nst & 1) ? Y : X;
-  // ---- 1. packed spectra of the seven inputs
+  // ---- 1. packed spectra: lines u v w phi phi_x phi_y phi_z
   for (int idx = threadIdx.x; idx < 7 * Mx; idx += blockDim.x) {
     const int f = idx / Mx, m = idx - f * Mx;
-    const T2* src = in + f * fs + (size_t)m * mstride + base;
-    const T2 a = src[0];
-    const T2 b = two ? src[1] : zero;
+    const int src_f = (f < 4) ? f : f - 1;      // phi_x (line 4) comes from phi (input 3)
+    const T2* src = in + src_f * fs + (size_t)m * mstride + base;
+    T2 a = src[0];
+    T2 b = two ? src[1] : zero;
+    if (f == 4) {                                // i kx phi
+      const T kx = kxs * (T)m;
+      a = mk(-kx * a.y, kx * a.x);
+      b = mk(-kx * b.y, kx * b.x);
+    }
     T2* L = L0 + f * Px;
     if (m == 0) {
       L[0] = mk(a.x, b.x);  // the imaginary part of a DC coefficient is not used by c2r
@@ -128,35 +143,31 @@ __global__ void __launch_bounds__(XT) xline_kernel(const typename C2<T>::t* __re
   const T2* in7 = block_fft<T, true>(L0, (L0 == X) ? Y : X, 7, Px, pl);  // == X
   T2* prod = S + 7 * Px;   // five product lines
   T2* scr = S + 12 * Px;   // five scratch lines
-  for (int g0 = 0; g0 < 10; g0 += 5) {
-    // ---- 2. products for outputs g0 .. g0+4 (rows z0 in .x, z0+1 in .y)
+  for (int g0 = 0; g0 < 9; g0 += 5) {
+    const int cnt = (g0 == 0) ? 5 : 4;
+    // ---- 2. products for outputs g0 .. g0+cnt-1 (rows z0 in .x, z0+1 in .y)
     for (int x = threadIdx.x; x < Px; x += blockDim.x) {
       const T2 u = in7[x], v = in7[Px + x], w = in7[2 * Px + x], ph = in7[3 * Px + x];
       const T2 fx = in7[4 * Px + x], fy = in7[5 * Px + x], fz = in7[6 * Px + x];
-      const T g2x = fx.x * fx.x + fy.x * fy.x + fz.x * fz.x;
-      const T g2y = fx.y * fx.y + fy.y * fy.y + fz.y * fz.y;
-      T2 o[5];
       if (g0 == 0) {
-        o[0] = mk(-u.x * u.x + kappa * (g2x - fx.x * fx.x), -u.y * u.y + kappa * (g2y - fx.y * fx.y));
-        o[1] = mk(-v.x * v.x + kappa * (g2x - fy.x * fy.x), -v.y * v.y + kappa * (g2y - fy.y * fy.y));
-        o[2] = mk(-w.x * w.x + kappa * (g2x - fz.x * fz.x), -w.y * w.y + kappa * (g2y - fz.y * fz.y));
-        o[3] = mk(-u.x * v.x - kappa * fx.x * fy.x, -u.y * v.y - kappa * fx.y * fy.y);
-        o[4] = mk(-u.x * w.x - kappa * fx.x * fz.x, -u.y * w.y - kappa * fx.y * fz.y);
+        const T2 wz = mk(w.x * w.x + kappa * fz.x * fz.x, w.y * w.y + kappa * fz.y * fz.y);
+        prod[x] = mk(wz.x - u.x * u.x - kappa * fx.x * fx.x, wz.y - u.y * u.y - kappa * fx.y * fx.y);
+        prod[Px + x] = mk(wz.x - v.x * v.x - kappa * fy.x * fy.x, wz.y - v.y * v.y - kappa * fy.y * fy.y);
+        prod[2 * Px + x] = mk(-u.x * v.x - kappa * fx.x * fy.x, -u.y * v.y - kappa * fx.y * fy.y);
+        prod[3 * Px + x] = mk(-u.x * w.x - kappa * fx.x * fz.x, -u.y * w.y - kappa * fx.y * fz.y);
+        prod[4 * Px + x] = mk(-v.x * w.x - kappa * fy.x * fz.x, -v.y * w.y - kappa * fy.y * fz.y);
       } else {
-        o[0] = mk(-v.x * w.x - kappa * fy.x * fz.x, -v.y * w.y - kappa * fy.y * fz.y);
-        o[1] = mk(ph.x * ph.x * ph.x, ph.y * ph.y * ph.y);
-        o[2] = mk(u.x * ph.x, u.y * ph.y);
-        o[3] = mk(v.x * ph.x, v.y * ph.y);
-        o[4] = mk(w.x * ph.x, w.y * ph.y);
+        prod[x] = mk(ph.x * ph.x * ph.x, ph.y * ph.y * ph.y);
+        prod[Px + x] = mk(u.x * ph.x, u.y * ph.y);
+        prod[2 * Px + x] = mk(v.x * ph.x, v.y * ph.y);
+        prod[3 * Px + x] = mk(w.x * ph.x, w.y * ph.y);
       }
-#pragma unroll
-      for (int q = 0; q < 5; ++q) prod[q * Px + x] = o[q];
     }
     __syncthreads();
-    const T2* R = block_fft<T, false>(prod, scr, 5, Px, pl);
+    const T2* R = block_fft<T, false>(prod, scr, cnt, Px, pl);
     // ---- 3. unpack: A_k = (Z_k + conj Z_{-k}) / 2, B_k = (Z_k - conj Z_{-k}) / (2 i)
     const T hs = (T)0.5 * scale;
-    for (int idx = threadIdx.x; idx < 5 * Mx; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < cnt * Mx; idx += blockDim.x) {
       const int q = idx / Mx, m = idx - q * Mx;
       const T2 Zk = R[q * Px + m];
       const T2 Zm = R[q * Px + (m == 0 ? 0 : Px - m)];
@@ -236,7 +247,15 @@ int ytile(int P, size_t elem) {
 
 cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void* in, void* out,
                          int nf, long long fs_in, long long fs_out, double scale,
-                         const FftPlan& py, cudaStream_t s) {
+                         const FftPlan& py, cudaStream_t s, const YMap* mapp) {
+  YMap map;
+  if (mapp) {
+    map = *mapp;
+  } else {
+    for (int f = 0; f < YMap::kMax; ++f) map.src[f] = f;
+    map.dy_mask = 0;
+  }
+  map.kys = 6.283185307179586476925 / g.ly;
   const size_t elem = prec == 0 ? sizeof(double2) : sizeof(float2);
   const int TZ = ytile(P, elem);
   const size_t smem = (size_t)2 * TZ * P * elem;
@@ -250,7 +269,7 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
   if (e != cudaSuccess) return e;
 #define YL(T, INV)                                                                            \
   ypass_kernel<T, INV><<<grid, YT, smem, s>>>((const C2<T>::t*)in, (C2<T>::t*)out, g.Mx, g.ny, \
-                                              P, g.nz, TZ, fs_in, fs_out, (T)scale, py);
+                                              P, g.nz, TZ, fs_in, fs_out, (T)scale, py, map);
   if (prec == 0) {
     if (dir == 1) { YL(double, true) } else { YL(double, false) }
   } else {
@@ -271,10 +290,12 @@ cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out1
   if (e != cudaSuccess) return e;
   if (prec == 0) {
     xline_kernel<double><<<grid, XT, smem, s>>>((const double2*)in7, (double2*)out10, g.Mx, g.Px,
-                                                g.Py, g.nz, fs, g.kappa, scale, px);
+                                                g.Py, g.nz, fs, g.kappa, scale,
+                                                6.283185307179586476925 / g.lx, px);
   } else {
     xline_kernel<float><<<grid, XT, smem, s>>>((const float2*)in7, (float2*)out10, g.Mx, g.Px,
-                                               g.Py, g.nz, fs, (float)g.kappa, (float)scale, px);
+                                               g.Py, g.nz, fs, (float)g.kappa, (float)scale,
+                                               (float)(6.283185307179586476925 / g.lx), px);
   }
   return cudaGetLastError();
 }

@@ -222,64 +222,78 @@ __global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T
     LN(z, 11, Nz)[n] = st_w[off + n];
     LN(z, 12, Nz)[n] = st_phi[off + n];
   }
-  for (int idx = tid; idx < 10 * Nz; idx += blockDim.x) {
+  for (int idx = tid; idx < 9 * Nz; idx += blockDim.x) {
     const int f = idx / Nz, n = idx - f * Nz;
     LN(z, f, Nz)[n] = to_d2(nl[(long long)f * fs + off + n]);
   }
   __syncthreads();
-  for (int f0 = 0; f0 < 10; f0 += NBF) dct_forward_lines(z, f0, NBF, Nz, N, pz);
-  // lines: 0 Sxx 1 Syy 2 Szz 3 Sxy 4 Sxz 5 Syz 6 phi^3 7 u phi 8 v phi 9 w phi
-  {
-    double2* src[3] = {LN(z, 4, Nz), LN(z, 5, Nz), LN(z, 2, Nz)};
-    double2* dst[3] = {LN(z, 13, Nz), LN(z, 14, Nz), LN(z, 15, Nz)};
-    dz_tasks(src, dst, 3, N, z.tmp);
-  }
-  __syncthreads();
-  // S_i = i kx Sigma_ix + i ky Sigma_iy + D Sigma_iz
+  // Non-linear samples (lines): 0 Sxx-Szz 1 Syy-Szz 2 Sxy 3 Sxz 4 Syz 5 phi^3 6 u phi 7 v phi
+  // 8 w phi.  The Chebyshev transform commutes with multiplication by i kx, i ky, so the
+  // combinations the assembly needs are formed first and only seven lines are transformed:
+  //   A = i kx Sxx' + i ky Sxy,  B = i kx Sxy + i ky Syy'  (S_x = A + D Sxz, S_y = B + D Syz)
+  //   0: P = i kx B - i ky A   1: Q = i kx Syz - i ky Sxz   (h_omega = P + D Q)
+  //   2: C = i kx Sxz + i ky Syz  (S_z = C)   3: R = i kx A + i ky B  (i kx S_x + i ky S_y = R + D C)
+  //   4: F = -(i kx u phi + i ky v phi)   5: w phi   6: phi^3
+  // On the (0,0) line P = Q = 0; lines 0 and 1 carry Sxz and Syz instead (mean forcing).
   for (int n = tid; n < Nz; n += blockDim.x) {
-    const double2 sxx = LN(z, 0, Nz)[n], syy = LN(z, 1, Nz)[n];
-    const double2 sxy = LN(z, 3, Nz)[n], sxz = LN(z, 4, Nz)[n], syz = LN(z, 5, Nz)[n];
-    const double2 Sx = mul_i(kx * sxx + ky * sxy) + LN(z, 13, Nz)[n];
-    const double2 Sy = mul_i(kx * sxy + ky * syy) + LN(z, 14, Nz)[n];
-    const double2 Sz = mul_i(kx * sxz + ky * syz) + LN(z, 15, Nz)[n];
-    double2 hom;
-    if (is00) {  // mean flow: Sbar_x + i Sbar_y + (gx + i gy) delta_{n0}
-      hom = make_double2(Sx.x + (n == 0 ? g.gx : 0.0), Sy.x + (n == 0 ? g.gy : 0.0));
+    const double2 sxx = LN(z, 0, Nz)[n], syy = LN(z, 1, Nz)[n], sxy = LN(z, 2, Nz)[n];
+    const double2 sxz = LN(z, 3, Nz)[n], syz = LN(z, 4, Nz)[n], p3 = LN(z, 5, Nz)[n];
+    const double2 fu = LN(z, 6, Nz)[n], fv = LN(z, 7, Nz)[n], fw = LN(z, 8, Nz)[n];
+    const double2 A = mul_i(kx * sxx + ky * sxy);
+    const double2 B = mul_i(kx * sxy + ky * syy);
+    if (is00) {
+      LN(z, 0, Nz)[n] = sxz;
+      LN(z, 1, Nz)[n] = syz;
     } else {
-      hom = mul_i(kx * Sy - ky * Sx);  // i kx S_y - i ky S_x
+      LN(z, 0, Nz)[n] = mul_i(kx * B - ky * A);
+      LN(z, 1, Nz)[n] = mul_i(kx * syz - ky * sxz);
     }
-    LN(z, 2, Nz)[n] = Sz;
-    LN(z, 3, Nz)[n] = hom;
-    LN(z, 4, Nz)[n] = mul_i(kx * Sx + ky * Sy);  // i kx S_x + i ky S_y
-    const double2 ph = LN(z, 12, Nz)[n];
-    LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * ph;  // G = phi^3 - (1+shat) phi
-    LN(z, 7, Nz)[n] = -1.0 * mul_i(kx * LN(z, 7, Nz)[n] + ky * LN(z, 8, Nz)[n]);
+    LN(z, 2, Nz)[n] = mul_i(kx * sxz + ky * syz);
+    LN(z, 3, Nz)[n] = mul_i(kx * A + ky * B);
+    LN(z, 4, Nz)[n] = -1.0 * mul_i(kx * fu + ky * fv);
+    LN(z, 5, Nz)[n] = fw;
+    LN(z, 6, Nz)[n] = p3;
   }
+  __syncthreads();
+  for (int f0 = 0; f0 < 7; f0 += NBF) dct_forward_lines(z, f0, (7 - f0 < NBF) ? 7 - f0 : NBF, Nz, N, pz);
+  // G = phi^3 - (1 + shat) phi
+  for (int n = tid; n < Nz; n += blockDim.x)
+    LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * LN(z, 12, Nz)[n];
   __syncthreads();
   {
-    double2* src[4] = {LN(z, 9, Nz), LN(z, 4, Nz), LN(z, 6, Nz), LN(z, 11, Nz)};
-    double2* dst[4] = {LN(z, 13, Nz), LN(z, 14, Nz), LN(z, 15, Nz), LN(z, 5, Nz)};
-    dz_tasks(src, dst, 4, N, z.tmp);
+    double2* src[6] = {LN(z, 1, Nz), LN(z, 3, Nz), LN(z, 2, Nz), LN(z, 5, Nz), LN(z, 6, Nz),
+                       LN(z, 11, Nz)};
+    double2* dst[6] = {LN(z, 7, Nz), LN(z, 8, Nz), LN(z, 9, Nz), LN(z, 13, Nz), LN(z, 14, Nz),
+                       LN(z, 15, Nz)};
+    dz_tasks(src, dst, 6, N, z.tmp);   // DQ, DR, DC, D(w phi), DG, Dw
   }
+  __syncthreads();
+  const double rpe = 1.0 / g.pe;
+  for (int n = tid; n < Nz; n += blockDim.x)  // partial S_phi = F - D(w phi) - k^2 G / Pe
+    LN(z, 4, Nz)[n] = LN(z, 4, Nz)[n] - LN(z, 13, Nz)[n] - (k2 * rpe) * LN(z, 6, Nz)[n];
   __syncthreads();
   {
-    double2* src[2] = {LN(z, 15, Nz), LN(z, 5, Nz)};
-    double2* dst[2] = {LN(z, 8, Nz), LN(z, 9, Nz)};
-    dz_tasks(src, dst, 2, N, z.tmp);
+    double2* src[4] = {LN(z, 9, Nz), LN(z, 14, Nz), LN(z, 15, Nz), LN(z, 0, Nz)};
+    double2* dst[4] = {LN(z, 3, Nz), LN(z, 5, Nz), LN(z, 1, Nz), LN(z, 13, Nz)};
+    dz_tasks(src, dst, is00 ? 4 : 3, N, z.tmp);   // D^2 C, D^2 G, D^2 w (, D Sxz on (0,0))
   }
   __syncthreads();
-  // h_w, S_phi, theta^n = (D^2 - k^2) w^n; AB2; right-hand sides
+  // h_omega, h_w, S_phi, theta^n = (D^2 - k^2) w^n; AB2; right-hand sides
   const double twoRe = 2.0 * g.re;
   const double cphi = g.pe / (g.ch * g.ch);
   const double rdt = 1.0 / g.dt;
-  const double rpe = 1.0 / g.pe;
   for (int n = tid; n < Nz; n += blockDim.x) {
-    const double2 hw = is00 ? make_double2(0.0, 0.0)
-                            : (-k2) * LN(z, 2, Nz)[n] - LN(z, 14, Nz)[n];
-    const double2 sphi = LN(z, 7, Nz)[n] - LN(z, 13, Nz)[n] +
-                         rpe * (LN(z, 8, Nz)[n] - k2 * LN(z, 6, Nz)[n]);
-    const double2 hom = LN(z, 3, Nz)[n];
-    const double2 th = LN(z, 9, Nz)[n] - k2 * LN(z, 11, Nz)[n];
+    double2 hom, hw;
+    if (is00) {  // mean flow: Sbar_x + i Sbar_y + (gx + i gy) delta_{n0}
+      hom = make_double2(LN(z, 13, Nz)[n].x + (n == 0 ? g.gx : 0.0),
+                         LN(z, 7, Nz)[n].x + (n == 0 ? g.gy : 0.0));
+      hw = make_double2(0.0, 0.0);
+    } else {
+      hom = LN(z, 0, Nz)[n] + LN(z, 7, Nz)[n];                                  // P + D Q
+      hw = (-k2) * LN(z, 2, Nz)[n] - LN(z, 8, Nz)[n] - LN(z, 3, Nz)[n];        // -k^2 C - DR - D^2 C
+    }
+    const double2 sphi = LN(z, 4, Nz)[n] + rpe * LN(z, 5, Nz)[n];
+    const double2 th = LN(z, 1, Nz)[n] - k2 * LN(z, 11, Nz)[n];
     double2 Hom = hom, Hw = hw, Hphi = sphi;
     if (!first) {
       Hom = 1.5 * hom - 0.5 * h_om[off + n];
@@ -521,11 +535,12 @@ __global__ void homog_kernel(GridDev g, double* __restrict__ fac) {
   fac[(size_t)10 * Nz * NK + (size_t)6 * NK + (size_t)p * NK + K] = (sh != 0.0) ? 1.0 / sh : 0.0;
 }
 
-// ---- zbwd: update + the seven fields for the non-linear terms ------------------------------
+// ---- zbwd: update + the fields for the non-linear terms ------------------------------------
 // UPDATE = 1: new state = (solved sums - old state) for omega, w and phi from R; = 0: state as is.
-// Output: u, v (continuity + omega_z definition), w, phi, i kx phi, i ky phi, D phi, backward
-// DCT-I to samples in z.
-template <typename T, int UPDATE>
+// Output (backward DCT-I to samples in z): NOUT = 5: u, v (continuity + omega_z definition), w,
+// phi, D phi (the step: i kx phi and i ky phi are formed by the x and y passes); NOUT = 7:
+// u, v, w, phi, i kx phi, i ky phi, D phi.
+template <typename T, int UPDATE, int NOUT>
 __global__ void __launch_bounds__(ZT) zbwd_kernel(GridDev g, const double2* __restrict__ R,
                                                   double2* __restrict__ st_om,
                                                   double2* __restrict__ st_w,
@@ -542,7 +557,7 @@ __global__ void __launch_bounds__(ZT) zbwd_kernel(GridDev g, const double2* __re
   const size_t off = (size_t)line * Nz;
   const int tid = threadIdx.x;
   if (j == g.ny / 2) {
-    for (int idx = tid; idx < 7 * Nz; idx += blockDim.x) {
+    for (int idx = tid; idx < NOUT * Nz; idx += blockDim.x) {
       const int f = idx / Nz, n = idx - f * Nz;
       bw[(long long)f * fs + off + n] = from_d2<T2>(make_double2(0.0, 0.0));
     }
@@ -590,13 +605,17 @@ __global__ void __launch_bounds__(ZT) zbwd_kernel(GridDev g, const double2* __re
     LN(z, 1, Nz)[n] = v;
     LN(z, 2, Nz)[n] = LN(z, 11, Nz)[n];
     LN(z, 3, Nz)[n] = ph;
-    LN(z, 4, Nz)[n] = kx * mul_i(ph);
-    LN(z, 5, Nz)[n] = ky * mul_i(ph);
-    LN(z, 6, Nz)[n] = LN(z, 14, Nz)[n];
+    if (NOUT == 7) {
+      LN(z, 4, Nz)[n] = kx * mul_i(ph);
+      LN(z, 5, Nz)[n] = ky * mul_i(ph);
+      LN(z, 6, Nz)[n] = LN(z, 14, Nz)[n];
+    } else {
+      LN(z, 4, Nz)[n] = LN(z, 14, Nz)[n];
+    }
   }
   __syncthreads();
-  for (int f0 = 0; f0 < 7; f0 += NBF) {
-    const int cnt = (7 - f0 < NBF) ? 7 - f0 : NBF;
+  for (int f0 = 0; f0 < NOUT; f0 += NBF) {
+    const int cnt = (NOUT - f0 < NBF) ? NOUT - f0 : NBF;
     dct_backward_lines_store<T2>(z, f0, cnt, Nz, N, pz, bw, fs, off, f0);
   }
 }
@@ -779,27 +798,30 @@ cudaError_t launch_zsolve(const GridDev& g, double2* R, long long fs, cudaStream
   return cudaGetLastError();
 }
 
-template <typename T, int UPDATE>
+template <typename T, int UPDATE, int NOUT>
 static cudaError_t launch_zbwd_t(const GridDev& g, const double2* R, double2* st_om,
                                  double2* st_w, double2* st_phi, void* bw, long long fs,
                                  const FftPlan& pz, cudaStream_t s) {
   typedef typename C2<T>::t T2;
   const size_t smem = zline_smem(g);
   static int cur = 0;
-  cudaError_t e = ensure_smem(zbwd_kernel<T, UPDATE>, smem, &cur);
+  cudaError_t e = ensure_smem(zbwd_kernel<T, UPDATE, NOUT>, smem, &cur);
   if (e != cudaSuccess) return e;
-  zbwd_kernel<T, UPDATE><<<g.Mx * g.ny, ZT, smem, s>>>(g, R, st_om, st_w, st_phi, (T2*)bw, fs, pz);
+  zbwd_kernel<T, UPDATE, NOUT><<<g.Mx * g.ny, ZT, smem, s>>>(g, R, st_om, st_w, st_phi, (T2*)bw,
+                                                             fs, pz);
   return cudaGetLastError();
 }
 
-cudaError_t launch_zbwd(int update, int prec, const GridDev& g, const double2* R,
+cudaError_t launch_zbwd(int update, int prec, int nout, const GridDev& g, const double2* R,
                         double2* st_om, double2* st_w, double2* st_phi, void* bw, long long fs,
                         const FftPlan& pz, cudaStream_t s) {
+  if (nout == 7)  // auxiliary paths: fp64, from the state
+    return launch_zbwd_t<double, 0, 7>(g, R, st_om, st_w, st_phi, bw, fs, pz, s);
   if (prec == 0)
-    return update ? launch_zbwd_t<double, 1>(g, R, st_om, st_w, st_phi, bw, fs, pz, s)
-                  : launch_zbwd_t<double, 0>(g, R, st_om, st_w, st_phi, bw, fs, pz, s);
-  return update ? launch_zbwd_t<float, 1>(g, R, st_om, st_w, st_phi, bw, fs, pz, s)
-                : launch_zbwd_t<float, 0>(g, R, st_om, st_w, st_phi, bw, fs, pz, s);
+    return update ? launch_zbwd_t<double, 1, 5>(g, R, st_om, st_w, st_phi, bw, fs, pz, s)
+                  : launch_zbwd_t<double, 0, 5>(g, R, st_om, st_w, st_phi, bw, fs, pz, s);
+  return update ? launch_zbwd_t<float, 1, 5>(g, R, st_om, st_w, st_phi, bw, fs, pz, s)
+                : launch_zbwd_t<float, 0, 5>(g, R, st_om, st_w, st_phi, bw, fs, pz, s);
 }
 
 cudaError_t launch_project(const GridDev& g, const double2* uvwp, long long fs, double2* st_om,
