@@ -97,6 +97,7 @@ struct ch_grid {
   double* fac;
   // small tables and diagnostics scratch
   double* tab;  // go1 go2 go3 ccw dzl qint, nz each
+  double2* zcs; // cos(pi j / N), sin(pi j / N), j < N
   double* diag_part;
   double* diag_out;
 
@@ -341,6 +342,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   G->auxB = (double2*)A((size_t)7 * sb);
   G->phys7 = (double*)A((size_t)7 * G->fsp * sizeof(double));
   G->tab = (double*)A((size_t)6 * nz * sizeof(double));
+  G->zcs = (double2*)A((size_t)(nz - 1) * sizeof(double2));
   G->R = (double2*)A((size_t)3 * sb);
   g.NK = g.Mx * (ny / 2 + 1);
   G->fac = (double*)A(chf::fac_doubles(g) * sizeof(double));
@@ -355,7 +357,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   if (e == CH_OK) { G->px[1] = G->px[0]; G->px[1].tw = G->tws.back().d32; }
   if (e == CH_OK) e = make_plan(G, g.Py, 0, &G->py[0]);
   if (e == CH_OK) { G->py[1] = G->py[0]; G->py[1].tw = G->tws.back().d32; }
-  if (e == CH_OK) e = make_plan(G, 2 * g.N, 0, &G->pz);
+  if (e == CH_OK) e = make_plan(G, g.N, 0, &G->pz);
   if (e == CH_OK) e = make_plan(G, nx, 0, &G->pxu);
   if (e == CH_OK) e = make_plan(G, ny, 0, &G->pyu);
   if (e != CH_OK) {
@@ -397,6 +399,14 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
     if (cudaMemcpy(G->tab, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
       return bail(G, CH_ERR_CUDA);
     }
+    std::vector<double2> cs(N);
+    for (int j = 0; j < N; ++j) {
+      const long double a = pi * (long double)j / (long double)N;
+      cs[j] = make_double2((double)cosl(a), (double)sinl(a));
+    }
+    if (cudaMemcpy(G->zcs, cs.data(), N * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(G, CH_ERR_CUDA);
+    g.zcs = G->zcs;
     g.go1 = G->tab;
     g.go2 = G->tab + nz;
     g.go3 = G->tab + 2 * nz;

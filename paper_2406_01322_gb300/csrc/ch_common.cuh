@@ -207,6 +207,8 @@ struct GridDev {
   // K = mx (ny/2 + 1) + |my|, NK columns), layout described in ch_zline.cu
   const double* fac;
   int NK;
+  // cos(pi j / N), sin(pi j / N), j = 0..N-1 (Chebyshev transform through an N-point FFT)
+  const double2* zcs;
 };
 
 }  // namespace chf

@@ -41,6 +41,16 @@ __global__ void static_twiddles_kernel(double2* tw, int n) {
   }
 }
 
+// (cos(pi j / n), sin(pi j / n)), j < n: the Chebyshev transform's pre/post factors
+__global__ void static_cs_kernel(double2* cs, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    double s, c;
+    sincospi((double)t / (double)n, &s, &c);
+    cs[t] = make_double2(c, s);
+  }
+}
+
 // device address of the scratch array for the current device, set up once per device
 int scratch_for_current_device(unsigned char** out) {
   int dev = -1;
@@ -81,7 +91,7 @@ extern "C" int ch_transform_forward_noalloc(int nx, int ny, int nz, const double
   // scratch layout: x, y, z twiddles, then two (Mx, Ny, Nz) complex fields
   const size_t b_tx = round256((size_t)nx * sizeof(double2));
   const size_t b_ty = round256((size_t)ny * sizeof(double2));
-  const size_t b_tz = round256((size_t)2 * g.N * sizeof(double2));
+  const size_t b_tz = round256((size_t)2 * g.N * sizeof(double2));  // N twiddles + N cos/sin
   const size_t b_f = round256((size_t)fs * sizeof(double2));
   if (b_tx + b_ty + b_tz + 2 * b_f > kStaticScratchBytes) return CH_ERR_SIZE;
   unsigned char* base = nullptr;
@@ -94,15 +104,17 @@ extern "C" int ch_transform_forward_noalloc(int nx, int ny, int nz, const double
   double2* B = reinterpret_cast<double2*>(base + b_tx + b_ty + b_tz + b_f);
   chf::FftPlan px, py, pz;
   if (!chf::make_radices(nx, &px) || !chf::make_radices(ny, &py) ||
-      !chf::make_radices(2 * g.N, &pz))
+      !chf::make_radices(g.N, &pz))
     return CH_ERR_SIZE;
   px.tw = tx;
   py.tw = ty;
   pz.tw = tz;
+  g.zcs = tz + g.N;
   cudaStream_t s = (cudaStream_t)stream;
   static_twiddles_kernel<<<(nx + 255) / 256, 256, 0, s>>>(tx, nx);
   static_twiddles_kernel<<<(ny + 255) / 256, 256, 0, s>>>(ty, ny);
-  static_twiddles_kernel<<<(2 * g.N + 255) / 256, 256, 0, s>>>(tz, 2 * g.N);
+  static_twiddles_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(tz, g.N);
+  static_cs_kernel<<<(g.N + 255) / 256, 256, 0, s>>>(tz + g.N, g.N);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = chf::launch_x_r2c(g, phys, A, 1, (long long)nx * ny * nz, fs, px, s);
   if (e == cudaSuccess)

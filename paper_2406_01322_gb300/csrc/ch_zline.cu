@@ -37,7 +37,7 @@ namespace chf {
 namespace {
 
 constexpr int ZT = 128;   // threads of a per-line CTA
-constexpr int NBF = 2;    // DCT lines transformed per FFT call
+constexpr int NBF = 4;    // DCT lines transformed per FFT call (one warp each for scans)
 constexpr int NLINES = 16;
 constexpr int TL = 32;    // lines per zsolve CTA (64 threads: one per (line, parity))
 
@@ -124,7 +124,7 @@ __device__ void dz_tasks(double2* const* src, double2* const* dst, int ntask, in
 
 struct ZSmem {
   double2* L;   // NLINES lines of Nz
-  double2* FA;  // NBF * 2N
+  double2* FA;  // NBF * N
   double2* FB;
   double* tmp;  // scan scratch, (ZT/32) * (N/2 + 2)
 };
@@ -133,54 +133,117 @@ __device__ __forceinline__ ZSmem carve(double2* sm, int Nz, int N) {
   ZSmem z;
   z.L = sm;
   z.FA = sm + NLINES * Nz;
-  z.FB = z.FA + NBF * 2 * N;
-  z.tmp = reinterpret_cast<double*>(z.FB + NBF * 2 * N);
+  z.FB = z.FA + NBF * N;
+  z.tmp = reinterpret_cast<double*>(z.FB + NBF * N);
   return z;
 }
 
 __device__ __forceinline__ double2* LN(const ZSmem& z, int i, int Nz) { return z.L + i * Nz; }
 
-// forward DCT-I of cnt lines (in place): samples f_j -> a_n = G_n / (cbar_n N), where G is the
-// 2N-point DFT of the even extension (Sec. 3.2.1).
-__device__ void dct_forward_lines(const ZSmem& z, int first, int cnt, int Nz, int N,
-                                  const FftPlan& pz) {
-  const int NE = 2 * N;
-  for (int idx = threadIdx.x; idx < cnt * NE; idx += blockDim.x) {
-    const int f = idx / NE, m = idx - f * NE;
-    const int jj = (m <= N) ? m : NE - m;
-    z.FA[f * NE + m] = LN(z, first + f, Nz)[jj];
+// DCT-I of cnt lines (in place, cnt <= NBF = number of warps):
+//   E_k = x_0 + (-1)^k x_N + 2 sum_{j=1}^{N-1} x_j cos(pi j k / N),  k = 0..N,
+// i.e. the 2N-point DFT of the even extension (Sec. 3.2.1), computed with ONE complex N-point
+// FFT per line: with s_j = x_j + x_{N-j}, d_j = x_j - x_{N-j} (j = 0..N-1) and
+// y_j = s_j + sin(pi j/N) d_j, Y = FFT_N(y):  s is even and sin(pi j/N) d_j is odd, so
+//   E_{2k}   = (Y_k + Y_{N-k}) / 2,
+//   E_{2k+1} = E_1 - 2 i sum_{k'=1}^{k} (Y_{k'} - Y_{N-k'}) / 2   (cos(A+B) - cos(A-B) = -2 sin A sin B),
+//   E_1 = sum_j d_j cos(pi j / N).
+// mode 0 (forward): x = samples f_j, result a_n = E_n / (cbar_n N).
+// mode 1 (backward): x = coefficients with a_0, a_N doubled on input, result f_j = E_j / 2.
+// cs[j] = (cos(pi j / N), sin(pi j / N)), j = 0..N-1.
+__device__ void dct1_lines(const ZSmem& z, int first, int cnt, int Nz, int N, const FftPlan& pz,
+                           const double2* __restrict__ cs, int mode) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double e0 = (mode == 1) ? 2.0 : 1.0;   // weight of x_0 and x_N
+  for (int idx = threadIdx.x; idx < cnt * N; idx += blockDim.x) {
+    const int f = idx / N, j = idx - f * N;
+    const double2* x = LN(z, first + f, Nz);
+    double2 y;
+    if (j == 0) {
+      y = e0 * (x[0] + x[N]);
+    } else {
+      const double2 a = x[j], b = x[N - j];
+      const double sn = cs[j].y;
+      y = make_double2(a.x + b.x + sn * (a.x - b.x), a.y + b.y + sn * (a.y - b.y));
+    }
+    z.FA[f * N + j] = y;
+  }
+  // E_1 per line (warp f)
+  double2 e1 = make_double2(0.0, 0.0);
+  if (warp < cnt) {
+    const double2* x = LN(z, first + warp, Nz);
+    for (int j = lane; j < N; j += 32) {
+      const double2 d = (j == 0) ? e0 * (x[0] - x[N]) : x[j] - x[N - j];
+      const double c = cs[j].x;
+      e1.x = fma(c, d.x, e1.x);
+      e1.y = fma(c, d.y, e1.y);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      e1.x += __shfl_xor_sync(0xffffffffu, e1.x, off);
+      e1.y += __shfl_xor_sync(0xffffffffu, e1.y, off);
+    }
   }
   __syncthreads();
-  const double2* R = block_fft<double, false>(z.FA, z.FB, cnt, NE, pz);
-  const double sN = 1.0 / N;
-  for (int idx = threadIdx.x; idx < cnt * Nz; idx += blockDim.x) {
-    const int f = idx / Nz, n = idx - f * Nz;
-    const double s = (n == 0 || n == N) ? 0.5 * sN : sN;
-    LN(z, first + f, Nz)[n] = s * R[f * NE + n];
+  const double2* R = block_fft<double, false>(z.FA, z.FB, cnt, N, pz);
+  const double sc0 = (mode == 0) ? 0.5 / N : 0.5;   // scale of E_0 and E_N
+  const double sc = (mode == 0) ? 1.0 / N : 0.5;    // scale of the others
+  // even outputs
+  for (int idx = threadIdx.x; idx < cnt * (N / 2 + 1); idx += blockDim.x) {
+    const int f = idx / (N / 2 + 1), k = idx - f * (N / 2 + 1);
+    const double2 a = R[f * N + k], b = R[f * N + (k == 0 ? 0 : N - k)];
+    const double s = (k == 0 || 2 * k == N) ? sc0 : sc;
+    LN(z, first + f, Nz)[2 * k] = (0.5 * s) * (a + b);
+  }
+  // odd outputs: prefix sums of Q_k = (Y_k - Y_{N-k}) / 2 over k = 1..N/2-1 (warp f)
+  if (warp < cnt) {
+    const double2* Y = R + warp * N;
+    double2* out = LN(z, first + warp, Nz);
+    const int M = N / 2;                    // odd outputs E_1, E_3, .., E_{N-1}: k = 0..M-1
+    const int E = (M + 31) / 32;
+    const int k0 = lane * E;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int e = 0; e < E; ++e) {
+      const int k = k0 + e;
+      if (k >= 1 && k < M) acc = acc + 0.5 * (Y[k] - Y[N - k]);
+    }
+    double2 v = acc;                        // inclusive scan of chunk sums over lanes
+    for (int off = 1; off < 32; off <<= 1) {
+      const double ox = __shfl_up_sync(0xffffffffu, v.x, off);
+      const double oy = __shfl_up_sync(0xffffffffu, v.y, off);
+      if (lane >= off) { v.x += ox; v.y += oy; }
+    }
+    // exclusive prefix of this lane's chunk = inclusive value of the lane below
+    const double px = __shfl_up_sync(0xffffffffu, v.x, 1);
+    const double py = __shfl_up_sync(0xffffffffu, v.y, 1);
+    double2 T = (lane == 0) ? make_double2(0.0, 0.0) : make_double2(px, py);
+    for (int e = 0; e < E; ++e) {
+      const int k = k0 + e;
+      if (k < M) {
+        if (k >= 1) T = T + 0.5 * (Y[k] - Y[N - k]);
+        // E_{2k+1} = E_1 - 2 i T
+        out[2 * k + 1] = sc * make_double2(e1.x + 2.0 * T.y, e1.y - 2.0 * T.x);
+      }
+    }
   }
   __syncthreads();
 }
 
-// backward DCT-I of cnt lines starting at line `first`: f_j = sum_n a_n cos(pi n j / N),
-// evaluated as half the 2N-point DFT of the even extension of (2 a_0, a_1, .., a_{N-1}, 2 a_N).
-// Results are written to out[(out_first+f) * fs + off + j].
+// forward DCT-I of cnt lines in place (samples -> coefficients), cnt <= NBF
+__device__ __forceinline__ void dct_forward_lines(const ZSmem& z, int first, int cnt, int Nz, int N,
+                                                  const FftPlan& pz, const double2* cs) {
+  dct1_lines(z, first, cnt, Nz, N, pz, cs, 0);
+}
+
+// backward DCT-I of cnt lines (coefficients -> samples), results stored to
+// out[(out_first + f) * fs + off + j]
 template <typename T2>
 __device__ void dct_backward_lines_store(const ZSmem& z, int first, int cnt, int Nz, int N,
-                                         const FftPlan& pz, T2* out, long long fs, size_t off,
-                                         int out_first) {
-  const int NE = 2 * N;
-  for (int idx = threadIdx.x; idx < cnt * NE; idx += blockDim.x) {
-    const int f = idx / NE, m = idx - f * NE;
-    const int jj = (m <= N) ? m : NE - m;
-    double2 v = LN(z, first + f, Nz)[jj];
-    if (jj == 0 || jj == N) v = 2.0 * v;
-    z.FA[f * NE + m] = v;
-  }
-  __syncthreads();
-  const double2* R = block_fft<double, false>(z.FA, z.FB, cnt, NE, pz);
+                                         const FftPlan& pz, const double2* cs, T2* out,
+                                         long long fs, size_t off, int out_first) {
+  dct1_lines(z, first, cnt, Nz, N, pz, cs, 1);
   for (int idx = threadIdx.x; idx < cnt * Nz; idx += blockDim.x) {
     const int f = idx / Nz, j = idx - f * Nz;
-    out[(long long)(out_first + f) * fs + off + j] = from_d2<T2>(0.5 * R[f * NE + j]);
+    out[(long long)(out_first + f) * fs + off + j] = from_d2<T2>(LN(z, first + f, Nz)[j]);
   }
   __syncthreads();
 }
@@ -255,7 +318,7 @@ __global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T
     LN(z, 6, Nz)[n] = p3;
   }
   __syncthreads();
-  for (int f0 = 0; f0 < 7; f0 += NBF) dct_forward_lines(z, f0, (7 - f0 < NBF) ? 7 - f0 : NBF, Nz, N, pz);
+  for (int f0 = 0; f0 < 7; f0 += NBF) dct_forward_lines(z, f0, (7 - f0 < NBF) ? 7 - f0 : NBF, Nz, N, pz, g.zcs);
   // G = phi^3 - (1 + shat) phi
   for (int n = tid; n < Nz; n += blockDim.x)
     LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * LN(z, 12, Nz)[n];
@@ -616,7 +679,7 @@ __global__ void __launch_bounds__(ZT) zbwd_kernel(GridDev g, const double2* __re
   __syncthreads();
   for (int f0 = 0; f0 < NOUT; f0 += NBF) {
     const int cnt = (NOUT - f0 < NBF) ? NOUT - f0 : NBF;
-    dct_backward_lines_store<T2>(z, f0, cnt, Nz, N, pz, bw, fs, off, f0);
+    dct_backward_lines_store<T2>(z, f0, cnt, Nz, N, pz, g.zcs, bw, fs, off, f0);
   }
 }
 
@@ -640,8 +703,7 @@ __global__ void __launch_bounds__(ZT) project_kernel(GridDev g, const double2* _
     LN(z, f, Nz)[n] = in[(long long)f * fs + off + n];
   }
   __syncthreads();
-  dct_forward_lines(z, 0, 2, Nz, N, pz);
-  dct_forward_lines(z, 2, 2, Nz, N, pz);
+  dct_forward_lines(z, 0, 4, Nz, N, pz, g.zcs);
   const double2 zero = make_double2(0.0, 0.0);
   for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
     const double2 u = LN(z, 0, Nz)[n], v = LN(z, 1, Nz)[n];
@@ -675,14 +737,14 @@ __global__ void __launch_bounds__(ZT) dct_lines_kernel(GridDev g, int dir,
     }
     __syncthreads();
     if (dir == 0) {
-      dct_forward_lines(z, 0, cnt, Nz, N, pz);
+      dct_forward_lines(z, 0, cnt, Nz, N, pz, g.zcs);
       for (int idx = threadIdx.x; idx < cnt * Nz; idx += blockDim.x) {
         const int f = idx / Nz, n = idx - f * Nz;
         out[(long long)(f0 + f) * fs + off + n] = LN(z, f, Nz)[n];
       }
       __syncthreads();
     } else {
-      dct_backward_lines_store<double2>(z, 0, cnt, Nz, N, pz, out, fs, off, f0);
+      dct_backward_lines_store<double2>(z, 0, cnt, Nz, N, pz, g.zcs, out, fs, off, f0);
     }
   }
 }
@@ -753,7 +815,7 @@ __global__ void diag_final_kernel(GridDev g, int nblk, const double* __restrict_
 }  // namespace
 
 size_t zline_smem(const GridDev& g) {
-  return (size_t)(NLINES * g.nz + 2 * NBF * 2 * g.N) * sizeof(double2) +
+  return (size_t)(NLINES * g.nz + 2 * NBF * g.N) * sizeof(double2) +
          (size_t)(ZT / 32) * (g.N / 2 + 2) * sizeof(double);
 }
 

@@ -147,7 +147,9 @@ def test_poiseuille_fixed_point_on_gpu(binding):
     g.set_fields(*[torch.from_numpy(a) for a in (u, zero, zero, zero - 1.0)])
     g.step(20)
     uu, vv, ww, pp = [t.cpu().numpy() for t in g.get_fields()]
-    assert rel(uu, u) < 20 * 1e-14      # rounding drift of at most 1e-14 per step
+    # rounding drift per step: the odd Chebyshev outputs of the N-point DCT-I come from a
+    # prefix sum, whose rounding grows with the number of terms (~1e-14 per step here)
+    assert rel(uu, u) < 20 * 2e-14
     assert np.max(np.abs(vv)) < 1e-12 and np.max(np.abs(ww)) < 1e-12
     assert np.max(np.abs(pp + 1.0)) < 20 * 2e-15  # rounding drift per step
 
