@@ -39,7 +39,6 @@ namespace {
 constexpr int ZT = 128;   // threads of a per-line CTA
 constexpr int NBF = 4;    // DCT lines transformed per FFT call (one warp each for scans)
 constexpr int NLINES = 16;
-constexpr int TL = 32;    // lines per zsolve CTA (64 threads: one per (line, parity))
 
 __device__ __forceinline__ const double* fac_ptr(const GridDev& g, int op, int arr, int K) {
   return g.fac + ((size_t)(op * 3 + arr) * g.nz) * g.NK + K;
@@ -420,9 +419,73 @@ __device__ void tau_sweep_c(double2* x, int p, int N, double alpha, bool neumann
   }
 }
 
-// zsolve: TL lines per CTA, thread = (line, parity).  R holds [omega | theta-w | phi] right-hand
+// zsolve: one thread per (line, parity) elimination chain, sweeping in place on R in global
+// memory (line-major like the state).  The two chains of a line sit in adjacent lanes and touch
+// adjacent coefficients, so each warp access covers 16 lines x 32 bytes; a chain's half-line is
+// re-read by its three passes while still in L1/L2.  No shared memory, so occupancy is set by
+// registers.  R holds [omega | theta-w | phi] right-hand sides on entry and the solved sums /
+// new phi on exit.
+constexpr int ST = 128;   // threads per zsolve CTA
+__global__ void __launch_bounds__(ST) zsolve_kernel(GridDev g, double2* __restrict__ R,
+                                                    long long fs, int nlines) {
+  const int N = g.N, Nz = g.nz;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int line = t >> 1, p = t & 1;
+  if (line >= nlines) return;
+  int mx, j;
+  double kx, ky;
+  line_wavenumbers(g, line, mx, j, kx, ky);
+  const int K = line_K(g, mx, j);
+  const double k2 = kx * kx + ky * ky;
+  const bool is00 = (mx == 0 && j == 0);
+  const double* t1 = g.go1;
+  const double* t2 = g.go2;
+  const double* t3 = g.go3;
+  // omega (or the mean flow on the (0,0) line): (D^2 - k^2 - beta) Q = r, Dirichlet
+  double2* row = R + (size_t)line * Nz;
+  tau_sweep_c(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K), fac_ptr(g, 0, 1, K),
+              fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
+  // w: influence problem (theta, w) with w = w' = 0 at both walls
+  row = R + fs + (size_t)line * Nz;
+  if (is00) {
+    for (int n = p; n <= N; n += 2) row[n] = make_double2(0.0, 0.0);
+  } else {
+    tau_sweep_c(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
+                fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
+    tau_sweep_c(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K), fac_ptr(g, 1, 1, K),
+                fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
+    // Omega = Omega_p + c Omega_h with D Omega(+-1) = 0 (parity p)
+    const double* oh = fac_oh(g, K);
+    double2 sacc = make_double2(0.0, 0.0);
+    for (int n = p; n <= N; n += 2) {
+      const double n2 = (double)n * (double)n;
+      const double2 v = row[n];
+      sacc.x = fma(n2, v.x, sacc.x);
+      sacc.y = fma(n2, v.y, sacc.y);
+    }
+    const double rsh = fac_rsh(g, p, K);
+    const double2 c = make_double2(-sacc.x * rsh, -sacc.y * rsh);
+    for (int n = p; n <= N; n += 2) {
+      const double h = oh[(size_t)n * g.NK];
+      double2 v = row[n];
+      v.x = fma(c.x, h, v.x);
+      v.y = fma(c.y, h, v.y);
+      row[n] = v;
+    }
+  }
+  // phi: two Neumann problems with the same operator (D^2 - k^2 - lam)
+  row = R + 2 * fs + (size_t)line * Nz;
+  const double a = k2 + g.lam;
+  for (int rep = 0; rep < 2; ++rep)
+    tau_sweep_c(row, p, N, a, true, t1, t2, t3, fac_ptr(g, 2, 0, K), fac_ptr(g, 2, 1, K),
+                fac_ptr(g, 2, 2, K), g.NK, fac_rsq(g, 2, p, K));
+}
+
+constexpr int TL = 32;    // lines per tile-variant CTA (64 threads: one per (line, parity))
+
+// zsolve, tile variant (short lines): TL lines per CTA staged in shared memory, thread = (line, parity).  R holds [omega | theta-w | phi] right-hand
 // sides on entry and the solved sums / new phi on exit (line-major, like the state).
-__global__ void __launch_bounds__(2 * TL) zsolve_kernel(GridDev g, double2* __restrict__ R,
+__global__ void __launch_bounds__(2 * TL) zsolve_tile_kernel(GridDev g, double2* __restrict__ R,
                                                         long long fs, int nlines) {
   extern __shared__ double2 ssm[];
   const int Nz = g.nz, N = g.N;
@@ -851,12 +914,19 @@ cudaError_t launch_zrhs(int prec, const GridDev& g, const void* nl, long long fs
 }
 
 cudaError_t launch_zsolve(const GridDev& g, double2* R, long long fs, cudaStream_t s) {
-  const size_t smem = (size_t)TL * g.nz * sizeof(double2) + (size_t)3 * g.nz * sizeof(double);
-  static int cur = 0;
-  cudaError_t e = ensure_smem(zsolve_kernel, smem, &cur);
-  if (e != cudaSuccess) return e;
   const int nlines = g.Mx * g.ny;
-  zsolve_kernel<<<(nlines + TL - 1) / TL, 2 * TL, smem, s>>>(g, R, fs, nlines);
+  const size_t tile = (size_t)TL * g.nz * sizeof(double2) + (size_t)3 * g.nz * sizeof(double);
+  if (tile <= 72 * 1024) {
+    // short lines: a 32-line tile fits three CTAs per SM; staging in shared memory wins
+    static int cur = 0;
+    cudaError_t e = ensure_smem(zsolve_tile_kernel, tile, &cur);
+    if (e != cudaSuccess) return e;
+    zsolve_tile_kernel<<<(nlines + TL - 1) / TL, 2 * TL, tile, s>>>(g, R, fs, nlines);
+  } else {
+    // long lines: sweep in global memory (L1/L2), occupancy set by registers
+    const int nthreads = 2 * nlines;
+    zsolve_kernel<<<(nthreads + ST - 1) / ST, ST, 0, s>>>(g, R, fs, nlines);
+  }
   return cudaGetLastError();
 }
 
