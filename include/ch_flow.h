@@ -160,6 +160,29 @@ int ch_transform_forward(ch_grid* g, const double* phys, double* spec);
 int ch_transform_backward(ch_grid* g, const double* spec, double* phys);
 int ch_nonlinear(ch_grid* g, double* out9);
 
+/* ---- Ensemble of independent channels (uneven sizes) ---------------------------------------
+ * Not in the paper: a batching service of this library.  Each member is an ordinary ch_grid
+ * (created here with the given allocator and stream; all members share `precision`).  One
+ * ensemble step advances every member by one time step with six grouped persistent launches
+ * (one per stage; their CTAs walk a work list spanning all members), captured once into a CUDA
+ * graph and replayed.  Members are set, read and diagnosed through their ch_grid handles
+ * (ch_ensemble_member); ch_ensemble_step needs every member set.  ch_ensemble_autotune times the
+ * transforms' radix schedules and the persistent CTAs per SM of each stage on the live members
+ * (their states are saved and restored bit for bit) and keeps the fastest; the choice is cached
+ * per size signature for the process.  ch_ensemble_tuning writes the choice as a JSON object. */
+typedef struct ch_ensemble ch_ensemble;
+int ch_ensemble_init(const ch_params* members, int n, ch_alloc_fn alloc, ch_free_fn free_fn,
+                     void* alloc_ctx, void* stream, ch_ensemble** out);
+int ch_ensemble_size(const ch_ensemble* e);
+int ch_ensemble_member(ch_ensemble* e, int i, ch_grid** out);
+int ch_ensemble_step(ch_ensemble* e, int nsteps);
+/* as ch_ensemble_step with events between the six grouped launches (stream synchronised):
+ * stage_ms[0..CH_STEP_KERNELS-1] summed per stage, *total_ms over all steps */
+int ch_ensemble_step_timed(ch_ensemble* e, int nsteps, double* stage_ms, double* total_ms);
+int ch_ensemble_autotune(ch_ensemble* e, int reps);
+int ch_ensemble_tuning(const ch_ensemble* e, char* buf, size_t n);
+void ch_ensemble_destroy(ch_ensemble* e);
+
 /* Allocation-free variant of ch_transform_forward, for callers that must not allocate device
  * memory when they call it: code running while a stream is being captured into a CUDA graph
  * (allocation is not allowed inside a capture), plug-ins whose host application's memory pool

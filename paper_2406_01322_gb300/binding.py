@@ -72,6 +72,16 @@ _SIGS = {
     "ch_transform_forward_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     _P, _P, _P]),
     "ch_noalloc_scratch_bytes": (ctypes.c_size_t, []),
+    "ch_ensemble_init": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, ALLOC_FN, FREE_FN,
+                                        _P, _P, ctypes.POINTER(_P)]),
+    "ch_ensemble_size": (ctypes.c_int, [_P]),
+    "ch_ensemble_member": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "ch_ensemble_step": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ch_ensemble_step_timed": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]),
+    "ch_ensemble_autotune": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ch_ensemble_tuning": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    "ch_ensemble_destroy": (None, [_P]),
     "ch_destroy": (None, [_P]),
     "ch_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -171,10 +181,26 @@ class Grid:
                 None, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
         _ck("ch_init_grid", code)
         self.h = h
+        self._owned = True
+
+    @classmethod
+    def _view(cls, handle, params, device, stream):
+        """A Grid over a handle owned elsewhere (an ensemble member); close() does not free it."""
+        g = cls.__new__(cls)
+        g.device = torch.device(device)
+        g.shape = (params.nz, params.ny, params.nx)
+        g.spec_shape = (params.nx // 2, params.ny, params.nz)
+        g.params = params
+        g.stream = stream
+        g._alloc = None
+        g.h = handle
+        g._owned = False
+        return g
 
     def close(self):
         if getattr(self, "h", None):
-            lib().ch_destroy(self.h)
+            if getattr(self, "_owned", True):
+                lib().ch_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -272,3 +298,68 @@ class Grid:
         out = torch.empty((9,) + self.spec_shape, dtype=torch.complex128, device=self.device)
         _ck("ch_nonlinear", lib().ch_nonlinear(self.h, _ptr(out)))
         return out
+
+
+class Ensemble:
+    """Independent channels of uneven sizes advanced together by grouped persistent launches
+    (one per stage, replayed from a CUDA graph).  members: list of dicts with the Grid keyword
+    arguments (nx, ny, nz, re_tau, we, ch, pe, dt, ...); all members share `precision`.
+    ensemble.grids[i] is a Grid view of member i (set_fields, get_fields, diagnostics ...)."""
+
+    def __init__(self, members, precision=PREC_FP64, device="cuda:0", stream=None):
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        n = len(members)
+        arr = (Params * n)()
+        for i, m in enumerate(members):
+            arr[i] = Params(m["nx"], m["ny"], m["nz"], m.get("lx", 4 * math.pi),
+                            m.get("ly", 2 * math.pi), m.get("re_tau", 150.0), m.get("we", 1.0),
+                            m.get("ch", 0.05), m.get("pe", 20.0), m.get("dt", 1e-4),
+                            m.get("gx", 1.0), m.get("gy", 0.0), precision, 0, 0)
+        self._params = arr
+        self._alloc = TorchAllocator(self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            code = lib().ch_ensemble_init(arr, n, self._alloc.alloc_cb, self._alloc.free_cb, None,
+                                          ctypes.c_void_p(self.stream.cuda_stream),
+                                          ctypes.byref(h))
+        _ck("ch_ensemble_init", code)
+        self.h = h
+        self.grids = []
+        for i in range(n):
+            gh = ctypes.c_void_p()
+            _ck("ch_ensemble_member", lib().ch_ensemble_member(self.h, i, ctypes.byref(gh)))
+            self.grids.append(Grid._view(gh, arr[i], self.device, self.stream))
+
+    def step(self, n=1):
+        _ck("ch_ensemble_step", lib().ch_ensemble_step(self.h, int(n)))
+
+    def step_timed(self, n):
+        ks = (ctypes.c_double * len(Grid.KERNELS))()
+        tot = ctypes.c_double()
+        _ck("ch_ensemble_step_timed", lib().ch_ensemble_step_timed(self.h, int(n), ks,
+                                                                   ctypes.byref(tot)))
+        return tot.value, list(ks)
+
+    def autotune(self, reps=2):
+        _ck("ch_ensemble_autotune", lib().ch_ensemble_autotune(self.h, int(reps)))
+        return self.tuning()
+
+    def tuning(self):
+        import json
+        buf = ctypes.create_string_buffer(1024)
+        _ck("ch_ensemble_tuning", lib().ch_ensemble_tuning(self.h, buf, 1024))
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            for g in self.grids:
+                g.h = None
+            lib().ch_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

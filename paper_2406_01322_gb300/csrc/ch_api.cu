@@ -17,7 +17,14 @@
 #include <vector>
 
 #include "../../include/ch_flow.h"
+#include "ch_grid.h"
 #include "ch_internal.h"
+
+using chf::kBw;
+using chf::kMaxSmem;
+using chf::kNl;
+using chf::kYa;
+using chf::Tw;
 
 using chf::FftPlan;
 using chf::GridDev;
@@ -31,14 +38,22 @@ bool smooth23(int n) {
   return n == 1;
 }
 
-// radix schedule: 8 once if the power of two is odd (>= 3), 4s, a 2 if needed, then 3s
-bool make_radices(int n, FftPlan* pl) {
+bool make_radices(int n, FftPlan* pl) { return make_radices_style(n, 0, pl); }
+
+bool make_radices_style(int n, int style, FftPlan* pl) {
   int a = 0, b = 0, m = n;
   while (m % 2 == 0) { m /= 2; ++a; }
   while (m % 3 == 0) { m /= 3; ++b; }
   if (m != 1) return false;
   int k = 0;
-  if (a % 2 == 1 && a >= 3) { pl->rad[k++] = 8; a -= 3; }
+  if (style == 1)
+    while (b > 0) { pl->rad[k++] = 3; --b; }
+  if (style == 2) {
+    while (a >= 3 && a != 4) { pl->rad[k++] = 8; a -= 3; }
+  } else if (a % 2 == 1 && a >= 3) {
+    pl->rad[k++] = 8;
+    a -= 3;
+  }
   while (a >= 2) { pl->rad[k++] = 4; a -= 2; }
   if (a == 1) { pl->rad[k++] = 2; a = 0; }
   while (b > 0) { pl->rad[k++] = 3; --b; }
@@ -64,57 +79,6 @@ int check_sizes(int nx, int ny, int nz) {
 using chf::make_radices;
 using chf::smooth23;
 
-namespace {
-
-const int kMaxSmem = 227 * 1024 - 1024;  // opt-in limit less room for static shared memory
-
-struct Tw {
-  void* d64 = nullptr;  // double2[n]
-  void* d32 = nullptr;  // float2[n]
-};
-
-}  // namespace
-
-struct ch_grid {
-  ch_params p;
-  GridDev g;
-  int prec;
-  cudaStream_t stream;
-  ch_alloc_fn af;
-  ch_free_fn ff;
-  void* actx;
-  std::vector<void*> allocs;
-
-  // state and Adams-Bashforth history, (Mx, Ny, Nz) complex float64
-  double2 *om, *w, *phi, *hom, *hw, *hphi;
-  // step buffers in working precision
-  void *nl, *bw, *ya, *yb;
-  // auxiliary float64 buffers for set/get/diagnostics/stage entry points
-  double2 *auxA, *auxB;
-  double* phys7;
-  // right-hand sides / solved sums of the three implicit problems (3 fields), operator table
-  double2* R;
-  double* fac;
-  // small tables and diagnostics scratch
-  double* tab;  // go1 go2 go3 ccw dzl qint, nz each
-  double2* zcs; // cos(pi j / N), sin(pi j / N), j < N
-  double* diag_part;
-  double* diag_out;
-
-  FftPlan px[2], py[2], pz, pxu, pyu;
-  std::vector<Tw> tws;
-
-  long long fs;      // elements per (Mx, Ny, Nz) field
-  long long fsy;     // elements per (Mx, Py, Nz) field
-  long long fsp;     // elements per physical (Nz, Ny, Nx) field
-  int first;         // next step starts Adams-Bashforth
-  int fields_set;
-  long long nstep;
-  double t;
-  cudaGraphExec_t gexec;
-  int graph_ok;
-  cudaStream_t cap;  // private non-blocking stream used only to capture the step graph
-};
 
 namespace {
 
@@ -162,11 +126,9 @@ int make_plan(ch_grid* G, int n, int prec, FftPlan* pl) {
   return CH_OK;
 }
 
-// fields through the step: 5 backward (u v w phi Dphi) -> 6 y-padded (phi_y added by the y
-// pass) -> 9 products (Sxx-Szz Syy-Szz Sxy Sxz Syz phi^3 u phi v phi w phi)
-constexpr int kBw = 5, kYa = 6, kNl = 9;
+}  // namespace
 
-chf::YMap step_ymap() {
+chf::YMap chf::step_ymap() {
   chf::YMap m;
   const int src[kYa] = {0, 1, 2, 3, 3, 4};  // u v w phi (phi -> i ky phi) Dphi
   for (int f = 0; f < chf::YMap::kMax; ++f) m.src[f] = f < kYa ? src[f] : 0;
@@ -174,6 +136,10 @@ chf::YMap step_ymap() {
   m.kys = 0.0;
   return m;
 }
+
+using chf::step_ymap;
+
+namespace {
 
 #define CK(x)                                       \
   do {                                              \
@@ -186,7 +152,7 @@ chf::YMap step_ymap() {
 
 // non-linear terms of the current state: bw <- 7 fields; ya <- y backward; yb <- x line;
 // nl <- y forward (normalised)
-int eval_nonlinear(ch_grid* G) {
+int eval_nonlinear_impl(ch_grid* G) {
   const GridDev& g = G->g;
   cudaStream_t s = G->stream;
   const chf::YMap ym = step_ymap();
@@ -251,6 +217,11 @@ void drop_graph(ch_grid* G) {
 }
 
 }  // namespace
+
+int ch_launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev) {
+  return launch_step(G, first, s, ev);
+}
+int ch_eval_nonlinear(ch_grid* G) { return eval_nonlinear_impl(G); }
 
 extern "C" {
 
@@ -452,7 +423,7 @@ static int set_from_phys(ch_grid* G, const double* u, const double* v, const dou
   G->nstep = 0;
   G->t = 0.0;
   G->fields_set = 1;
-  return eval_nonlinear(G);
+  return eval_nonlinear_impl(G);
 }
 
 int ch_set_fields(ch_grid* G, const double* u, const double* v, const double* w,
@@ -643,7 +614,7 @@ int ch_set_state(ch_grid* G, const void* buf) {
   G->t = h.t;
   G->fields_set = h.fields_set;
   if (!G->fields_set) return CH_OK;
-  return eval_nonlinear(G);
+  return eval_nonlinear_impl(G);
 }
 
 int ch_get_spectral(ch_grid* G, double* om, double* w, double* phi) {
@@ -666,7 +637,7 @@ int ch_set_spectral(ch_grid* G, const double* om, const double* w, const double*
   G->nstep = 0;
   G->t = 0.0;
   G->fields_set = 1;
-  return eval_nonlinear(G);
+  return eval_nonlinear_impl(G);
 }
 
 int ch_transform_forward(ch_grid* G, const double* phys, double* spec) {

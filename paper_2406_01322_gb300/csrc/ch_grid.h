@@ -1,0 +1,74 @@
+// Host-side state of one channel handle (internal to libchflow).
+#pragma once
+
+#include <vector>
+
+#include "../../include/ch_flow.h"
+#include "ch_internal.h"
+
+namespace chf {
+
+const int kMaxSmem = 227 * 1024 - 1024;  // opt-in limit less room for static shared memory
+
+struct Tw {
+  void* d64 = nullptr;  // double2[n]
+  void* d32 = nullptr;  // float2[n]
+};
+
+// fields through the step: 5 backward (u v w phi Dphi) -> 6 y-padded (phi_y added by the y
+// pass) -> 9 products (Sxx-Szz Syy-Szz Sxy Sxz Syz phi^3 u phi v phi w phi)
+constexpr int kBw = 5, kYa = 6, kNl = 9;
+
+// backward y-pass map of the step: u v w phi (phi -> i ky phi) Dphi
+YMap step_ymap();
+
+// radix schedule with a style: 0 one radix-8 for an odd power of two then 4s, 2, 3s;
+// 1 the same with the radix-3 passes first; 2 as many radix-8 passes as possible
+bool make_radices_style(int n, int style, FftPlan* pl);
+
+}  // namespace chf
+
+struct ch_grid {
+  ch_params p;
+  chf::GridDev g;
+  int prec;
+  cudaStream_t stream;
+  ch_alloc_fn af;
+  ch_free_fn ff;
+  void* actx;
+  std::vector<void*> allocs;
+
+  // state and Adams-Bashforth history, (Mx, Ny, Nz) complex float64
+  double2 *om, *w, *phi, *hom, *hw, *hphi;
+  // step buffers in working precision
+  void *nl, *bw, *ya, *yb;
+  // auxiliary float64 buffers for set/get/diagnostics/stage entry points
+  double2 *auxA, *auxB;
+  double* phys7;
+  // right-hand sides / solved sums of the three implicit problems (3 fields), operator table
+  double2* R;
+  double* fac;
+  // small tables and diagnostics scratch
+  double* tab;  // go1 go2 go3 ccw dzl qint, nz each
+  double2* zcs; // cos(pi j / N), sin(pi j / N), j < N
+  double* diag_part;
+  double* diag_out;
+
+  chf::FftPlan px[2], py[2], pz, pxu, pyu;
+  std::vector<chf::Tw> tws;
+
+  long long fs;      // elements per (Mx, Ny, Nz) field
+  long long fsy;     // elements per (Mx, Py, Nz) field
+  long long fsp;     // elements per physical (Nz, Ny, Nx) field
+  int first;         // next step starts Adams-Bashforth
+  int fields_set;
+  long long nstep;
+  double t;
+  cudaGraphExec_t gexec;
+  int graph_ok;
+  cudaStream_t cap;  // private non-blocking stream used only to capture the step graph
+};
+
+// launch schedule of one step on stream s (events optional) and the non-linear evaluation
+int ch_launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev);
+int ch_eval_nonlinear(ch_grid* G);

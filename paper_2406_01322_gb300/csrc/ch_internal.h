@@ -79,6 +79,40 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
                          int nf, long long fs_in, long long fs_out, double scale,
                          const FftPlan& py, cudaStream_t s, const YMap* map = nullptr);
 
+// ---- ensemble: one member's everything the six step kernels need (device-resident array) ----
+struct Member {
+  GridDev g;
+  FftPlan px, py, pz;             // x (Px), y (Py), z (N) plans in the working precision
+  const void* nl;                 // 9 non-linear fields (Mx, Ny, Nz)
+  void* bw;                       // 5 backward fields (Mx, Ny, Nz)
+  void* ya;                       // 6 y-padded fields (Mx, Py, Nz)
+  void* yb;                       // 9 y-padded product fields (Mx, Py, Nz)
+  double2 *om, *w, *phi, *hom, *hw, *hphi, *R;
+  long long fs, fsy;
+  int first;                      // 1: this step starts Adams-Bashforth
+  int tzb, tzf;                   // y-pass z tiles (backward, forward)
+  int zsolve_tile;                // 1: shared-memory tile variant of the tau sweeps
+  YMap ym;                        // backward y-pass field map of the step
+  YMap yf;                        // forward y-pass field map (identity)
+  double yscale;                  // 1 / (Px Py)
+  double kxs;                     // 2 pi / lx
+};
+
+// Grouped persistent launches over all members: stage work items are numbered member by member,
+// begin[m] = first item of member m, begin[nmem] = total; `grid` CTAs loop over the items.
+// stage: 0 zrhs, 1 zsolve, 2 zbwd, 3 y backward, 4 x line, 5 y forward.
+cudaError_t launch_grouped(int stage, int prec, const Member* mem, const int* begin, int nmem,
+                           int grid, size_t smem, int zsolve_tile, cudaStream_t s);
+// work items of one member for a stage, and the dynamic shared memory one item needs
+int stage_items(int stage, const Member& m, int prec);
+size_t stage_smem(int stage, const Member& m, int prec);
+// CTAs per SM that the stage kernel can hold with `smem` bytes (occupancy API)
+int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile);
+// y-pass z tile for a padded length P (shared by single-grid and grouped launches)
+int ytile_for(int P, size_t elem);
+// x-line shared memory for a padded length Px
+size_t xline_smem(int Px, size_t elem);
+
 // fused x-line kernel: 6 fields u v w phi phi_y phi_z (Mx, Py, Nz) -> 7 c2r (Px, with
 // phi_x = i kx phi) -> 9 products -> r2c -> 9 fields.
 cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out10, long long fs,

@@ -21,18 +21,18 @@ constexpr int XT = 256;   // threads of an x-line CTA
 //   INV (backward): in (Mx, Ny, Nz) modes -> out (Mx, P, Nz) samples, modes |my| < Ny/2 placed,
 //   the rest zero.  Forward: in (Mx, P, Nz) samples -> out (Mx, Ny, Nz) kept modes * scale.
 template <typename T, bool INV>
-__global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __restrict__ in,
-                                                   typename C2<T>::t* __restrict__ out, int Mx,
-                                                   int Ny, int P, int Nz, int TZ, long long fs_in,
-                                                   long long fs_out, T scale, FftPlan pl,
-                                                   YMap map) {
+__device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__ in,
+                                           typename C2<T>::t* __restrict__ out, int Mx, int Ny,
+                                           int P, int Nz, int TZ, long long fs_in,
+                                           long long fs_out, T scale, const FftPlan& pl,
+                                           const YMap& map, int bx, int by, int bz) {
   typedef typename C2<T>::t T2;
   extern __shared__ unsigned char ysm_raw[];
   T2* A = reinterpret_cast<T2*>(ysm_raw);
   T2* B = A + TZ * P;
-  const int z0 = blockIdx.x * TZ;
-  const int mx = blockIdx.y;
-  const int f = blockIdx.z;          // output field
+  const int z0 = bx * TZ;
+  const int mx = by;
+  const int f = bz;                  // output field
   const int h = Ny / 2;
   const T2 zero = mk((T)0, (T)0);
   if (INV) {
@@ -83,6 +83,16 @@ __global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __re
   }
 }
 
+template <typename T, bool INV>
+__global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __restrict__ in,
+                                                   typename C2<T>::t* __restrict__ out, int Mx,
+                                                   int Ny, int P, int Nz, int TZ, long long fs_in,
+                                                   long long fs_out, T scale, FftPlan pl,
+                                                   YMap map) {
+  ypass_body<T, INV>(in, out, Mx, Ny, P, Nz, TZ, fs_in, fs_out, scale, pl, map, blockIdx.x,
+                     blockIdx.y, blockIdx.z);
+}
+
 // Fused x-line kernel.  One CTA per (pair of z rows, y).  The two rows z0, z0+1 of a field are
 // packed as one complex signal a + i b, so one complex FFT of length Px transforms both.
 //   1. six inputs u, v, w, phi, phi_y, phi_z (spectra kx < Mx); phi_x = i kx phi is formed from
@@ -94,15 +104,15 @@ __global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __re
 //   3. r2c, keep kx < Mx, times `scale`.
 // Shared memory: 7 + 5 + 5 lines of Px complex values.
 template <typename T>
-__global__ void __launch_bounds__(XT) xline_kernel(const typename C2<T>::t* __restrict__ in,
-                                                   typename C2<T>::t* __restrict__ out, int Mx,
-                                                   int Px, int Py, int Nz, long long fs, T kappa,
-                                                   T scale, T kxs, FftPlan pl) {
+__device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__ in,
+                                           typename C2<T>::t* __restrict__ out, int Mx, int Px,
+                                           int Py, int Nz, long long fs, T kappa, T scale, T kxs,
+                                           const FftPlan& pl, int bx, int by) {
   typedef typename C2<T>::t T2;
   extern __shared__ unsigned char xsm_raw[];
   T2* S = reinterpret_cast<T2*>(xsm_raw);
-  const int z0 = 2 * blockIdx.x;
-  const int y = blockIdx.y;
+  const int z0 = 2 * bx;
+  const int y = by;
   const bool two = (z0 + 1 < Nz);
   const T2 zero = mk((T)0, (T)0);
   const size_t base = (size_t)y * Nz + z0;
@@ -179,6 +189,14 @@ __global__ void __launch_bounds__(XT) xline_kernel(const typename C2<T>::t* __re
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(XT) xline_kernel(const typename C2<T>::t* __restrict__ in,
+                                                   typename C2<T>::t* __restrict__ out, int Mx,
+                                                   int Px, int Py, int Nz, long long fs, T kappa,
+                                                   T scale, T kxs, FftPlan pl) {
+  xline_body<T>(in, out, Mx, Px, Py, Nz, fs, kappa, scale, kxs, pl, blockIdx.x, blockIdx.y);
+}
+
 // plain r2c along x of physical rows (Nz, Ny, Nx) -> (Mx, Ny, Nz); two z rows per CTA
 __global__ void __launch_bounds__(128) x_r2c_kernel(const double* __restrict__ phys,
                                                     double2* __restrict__ out, int Nx, int Ny,
@@ -236,11 +254,57 @@ __global__ void __launch_bounds__(128) x_c2r_kernel(const double2* __restrict__ 
   }
 }
 
-int ytile(int P, size_t elem) {
+int ytile_local(int P, size_t elem) {
   // z tile: 8 columns (128 B of fp64 complex), fewer when the lines are long
   int tz = 8;
   while (tz > 1 && (size_t)2 * tz * P * elem > 160 * 1024) tz /= 2;
   return tz;
+}
+
+// ---- grouped persistent launches (ensemble) ---------------------------------------------
+__device__ __forceinline__ int member_of_xy(const int* __restrict__ begin, int nmem, int item) {
+  int m = 0;
+  while (m + 1 < nmem && begin[m + 1] <= item) ++m;
+  return m;
+}
+
+template <typename T, bool INV>
+__global__ void __launch_bounds__(YT) grouped_ypass_kernel(const Member* __restrict__ mem,
+                                                           const int* __restrict__ begin, int nmem) {
+  typedef typename C2<T>::t T2;
+  const int total = begin[nmem];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int m = member_of_xy(begin, nmem, item);
+    const Member& M = mem[m];
+    const int TZ = INV ? M.tzb : M.tzf;
+    const int nzt = (M.g.nz + TZ - 1) / TZ;
+    const int local = item - begin[m];
+    const int bx = local % nzt, rest = local / nzt;
+    const int by = rest % M.g.Mx, bz = rest / M.g.Mx;
+    if (INV)
+      ypass_body<T, true>((const T2*)M.bw, (T2*)M.ya, M.g.Mx, M.g.ny, M.g.Py, M.g.nz, TZ, M.fs,
+                          M.fsy, (T)1, M.py, M.ym, bx, by, bz);
+    else
+      ypass_body<T, false>((const T2*)M.yb, (T2*)M.nl, M.g.Mx, M.g.ny, M.g.Py, M.g.nz, TZ, M.fsy,
+                           M.fs, (T)M.yscale, M.py, M.yf, bx, by, bz);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(XT) grouped_xline_kernel(const Member* __restrict__ mem,
+                                                           const int* __restrict__ begin, int nmem) {
+  typedef typename C2<T>::t T2;
+  const int total = begin[nmem];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int m = member_of_xy(begin, nmem, item);
+    const Member& M = mem[m];
+    const int nzp = (M.g.nz + 1) / 2;
+    const int local = item - begin[m];
+    xline_body<T>((const T2*)M.ya, (T2*)M.yb, M.g.Mx, M.g.Px, M.g.Py, M.g.nz, M.fsy,
+                  (T)M.g.kappa, (T)1, (T)M.kxs, M.px, local % nzp, local / nzp);
+    __syncthreads();
+  }
 }
 
 }  // namespace
@@ -257,7 +321,7 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
   }
   map.kys = 6.283185307179586476925 / g.ly;
   const size_t elem = prec == 0 ? sizeof(double2) : sizeof(float2);
-  const int TZ = ytile(P, elem);
+  const int TZ = ytile_local(P, elem);
   const size_t smem = (size_t)2 * TZ * P * elem;
   dim3 grid((g.nz + TZ - 1) / TZ, g.Mx, nf);
   static int cur[4] = {0, 0, 0, 0};
@@ -316,6 +380,45 @@ cudaError_t launch_x_c2r(const GridDev& g, const double2* in, double* phys, int 
   x_c2r_kernel<<<grid, 128, 2 * g.nx * sizeof(double2), s>>>(in, phys, g.nx, g.ny, g.nz, fs_spec,
                                                              fs_phys, px);
   return cudaGetLastError();
+}
+
+}  // namespace chf
+
+namespace chf {
+
+int ytile_for(int P, size_t elem) { return ytile_local(P, elem); }
+size_t xline_smem(int Px, size_t elem) { return (size_t)17 * Px * elem; }
+
+cudaError_t launch_grouped_xy(int stage, int prec, const Member* mem, const int* begin, int nmem,
+                              int grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  static int cur[6] = {0, 0, 0, 0, 0, 0};
+#define GL(K, idx, T_)                                                   \
+  if ((e = ensure_smem(K, smem, &cur[idx])) != cudaSuccess) return e;    \
+  K<<<grid, (stage == 4 ? XT : YT), smem, s>>>(mem, begin, nmem);
+  if (stage == 3) {
+    if (prec == 0) { GL((grouped_ypass_kernel<double, true>), 0, double) }
+    else { GL((grouped_ypass_kernel<float, true>), 1, float) }
+  } else if (stage == 4) {
+    if (prec == 0) { GL(grouped_xline_kernel<double>, 2, double) }
+    else { GL(grouped_xline_kernel<float>, 3, float) }
+  } else {
+    if (prec == 0) { GL((grouped_ypass_kernel<double, false>), 4, double) }
+    else { GL((grouped_ypass_kernel<float, false>), 5, float) }
+  }
+#undef GL
+  return cudaGetLastError();
+}
+
+int occupancy_xy(int stage, int prec, size_t smem) {
+  int n = 0;
+  const void* k;
+  if (stage == 3) k = prec == 0 ? (const void*)grouped_ypass_kernel<double, true> : (const void*)grouped_ypass_kernel<float, true>;
+  else if (stage == 4) k = prec == 0 ? (const void*)grouped_xline_kernel<double> : (const void*)grouped_xline_kernel<float>;
+  else k = prec == 0 ? (const void*)grouped_ypass_kernel<double, false> : (const void*)grouped_ypass_kernel<float, false>;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, stage == 4 ? XT : YT, smem);
+  cudaGetLastError();
+  return n;
 }
 
 }  // namespace chf

@@ -249,17 +249,15 @@ __device__ void dct_backward_lines_store(const ZSmem& z, int first, int cnt, int
 
 // ---- zrhs: right-hand sides of the three implicit problems ---------------------------------
 template <typename T>
-__global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T>::t* __restrict__ nl,
-                                                  long long fs, const double2* __restrict__ st_om,
-                                                  const double2* __restrict__ st_w,
-                                                  const double2* __restrict__ st_phi,
-                                                  double2* __restrict__ h_om,
-                                                  double2* __restrict__ h_w,
-                                                  double2* __restrict__ h_phi,
-                                                  double2* __restrict__ R, int first, FftPlan pz) {
+__device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>::t* __restrict__ nl,
+                                          long long fs, const double2* __restrict__ st_om,
+                                          const double2* __restrict__ st_w,
+                                          const double2* __restrict__ st_phi,
+                                          double2* __restrict__ h_om, double2* __restrict__ h_w,
+                                          double2* __restrict__ h_phi, double2* __restrict__ R,
+                                          int first, const FftPlan& pz, int line) {
   extern __shared__ double2 zsm[];
   const int Nz = g.nz, N = g.N;
-  const int line = blockIdx.x;
   int mx, j;
   double kx, ky;
   line_wavenumbers(g, line, mx, j, kx, ky);
@@ -371,6 +369,18 @@ __global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T>::t* __restrict__ nl,
+                                                  long long fs, const double2* __restrict__ st_om,
+                                                  const double2* __restrict__ st_w,
+                                                  const double2* __restrict__ st_phi,
+                                                  double2* __restrict__ h_om,
+                                                  double2* __restrict__ h_w,
+                                                  double2* __restrict__ h_phi,
+                                                  double2* __restrict__ R, int first, FftPlan pz) {
+  zrhs_body<T>(g, nl, fs, st_om, st_w, st_phi, h_om, h_w, h_phi, R, first, pz, blockIdx.x);
+}
+
 // ---- tau elimination with tabulated factors -----------------------------------------------
 // Solve (D^2 - alpha) a = f (Gottlieb-Orszag rows n >= 2, homogeneous boundary row) for the
 // coefficients of parity p of one complex line, in place (x[n] = f_n on entry, a_n on exit).
@@ -426,10 +436,9 @@ __device__ void tau_sweep_c(double2* x, int p, int N, double alpha, bool neumann
 // registers.  R holds [omega | theta-w | phi] right-hand sides on entry and the solved sums /
 // new phi on exit.
 constexpr int ST = 128;   // threads per zsolve CTA
-__global__ void __launch_bounds__(ST) zsolve_kernel(GridDev g, double2* __restrict__ R,
-                                                    long long fs, int nlines) {
+__device__ __forceinline__ void zsolve_body(const GridDev& g, double2* __restrict__ R, long long fs,
+                                            int nlines, int t) {
   const int N = g.N, Nz = g.nz;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int line = t >> 1, p = t & 1;
   if (line >= nlines) return;
   int mx, j;
@@ -481,12 +490,17 @@ __global__ void __launch_bounds__(ST) zsolve_kernel(GridDev g, double2* __restri
                 fac_ptr(g, 2, 2, K), g.NK, fac_rsq(g, 2, p, K));
 }
 
+__global__ void __launch_bounds__(ST) zsolve_kernel(GridDev g, double2* __restrict__ R,
+                                                    long long fs, int nlines) {
+  zsolve_body(g, R, fs, nlines, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 constexpr int TL = 32;    // lines per tile-variant CTA (64 threads: one per (line, parity))
 
 // zsolve, tile variant (short lines): TL lines per CTA staged in shared memory, thread = (line, parity).  R holds [omega | theta-w | phi] right-hand
 // sides on entry and the solved sums / new phi on exit (line-major, like the state).
-__global__ void __launch_bounds__(2 * TL) zsolve_tile_kernel(GridDev g, double2* __restrict__ R,
-                                                        long long fs, int nlines) {
+__device__ __forceinline__ void zsolve_tile_body(const GridDev& g, double2* __restrict__ R,
+                                                 long long fs, int nlines, int bid) {
   extern __shared__ double2 ssm[];
   const int Nz = g.nz, N = g.N;
   double2* tile = ssm;
@@ -495,7 +509,7 @@ __global__ void __launch_bounds__(2 * TL) zsolve_tile_kernel(GridDev g, double2*
   double* t3 = t2 + Nz;
   const int tid = threadIdx.x;
   const int l = tid >> 1, p = tid & 1;
-  const int line0 = blockIdx.x * TL;
+  const int line0 = bid * TL;
   const int line = line0 + l;
   for (int n = tid; n < Nz; n += blockDim.x) {
     t1[n] = g.go1[n];
@@ -558,6 +572,11 @@ __global__ void __launch_bounds__(2 * TL) zsolve_tile_kernel(GridDev g, double2*
     for (int idx = tid; idx < ntile * Nz; idx += blockDim.x) Rp[idx] = tile[idx];
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(2 * TL) zsolve_tile_kernel(GridDev g, double2* __restrict__ R,
+                                                        long long fs, int nlines) {
+  zsolve_tile_body(g, R, fs, nlines, blockIdx.x);
 }
 
 // ---- operator table (init time) -------------------------------------------------------------
@@ -667,16 +686,14 @@ __global__ void homog_kernel(GridDev g, double* __restrict__ fac) {
 // phi, D phi (the step: i kx phi and i ky phi are formed by the x and y passes); NOUT = 7:
 // u, v, w, phi, i kx phi, i ky phi, D phi.
 template <typename T, int UPDATE, int NOUT>
-__global__ void __launch_bounds__(ZT) zbwd_kernel(GridDev g, const double2* __restrict__ R,
-                                                  double2* __restrict__ st_om,
-                                                  double2* __restrict__ st_w,
-                                                  double2* __restrict__ st_phi,
-                                                  typename C2<T>::t* __restrict__ bw,
-                                                  long long fs, FftPlan pz) {
+__device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __restrict__ R,
+                                          double2* __restrict__ st_om, double2* __restrict__ st_w,
+                                          double2* __restrict__ st_phi,
+                                          typename C2<T>::t* __restrict__ bw, long long fs,
+                                          const FftPlan& pz, int line) {
   typedef typename C2<T>::t T2;
   extern __shared__ double2 zsm[];
   const int Nz = g.nz, N = g.N;
-  const int line = blockIdx.x;
   int mx, j;
   double kx, ky;
   line_wavenumbers(g, line, mx, j, kx, ky);
@@ -744,6 +761,16 @@ __global__ void __launch_bounds__(ZT) zbwd_kernel(GridDev g, const double2* __re
     const int cnt = (NOUT - f0 < NBF) ? NOUT - f0 : NBF;
     dct_backward_lines_store<T2>(z, f0, cnt, Nz, N, pz, g.zcs, bw, fs, off, f0);
   }
+}
+
+template <typename T, int UPDATE, int NOUT>
+__global__ void __launch_bounds__(ZT) zbwd_kernel(GridDev g, const double2* __restrict__ R,
+                                                  double2* __restrict__ st_om,
+                                                  double2* __restrict__ st_w,
+                                                  double2* __restrict__ st_phi,
+                                                  typename C2<T>::t* __restrict__ bw,
+                                                  long long fs, FftPlan pz) {
+  zbwd_body<T, UPDATE, NOUT>(g, R, st_om, st_w, st_phi, bw, fs, pz, blockIdx.x);
 }
 
 // set_fields projection: u, v, w, phi samples (after the x/y transforms) -> state
@@ -875,6 +902,62 @@ __global__ void diag_final_kernel(GridDev g, int nblk, const double* __restrict_
   out[6] = m[2];
 }
 
+// ---- grouped persistent launches (ensemble) ---------------------------------------------
+__device__ __forceinline__ int member_of(const int* __restrict__ begin, int nmem, int item) {
+  int m = 0;
+  while (m + 1 < nmem && begin[m + 1] <= item) ++m;
+  return m;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(ZT) grouped_zrhs_kernel(const Member* __restrict__ mem,
+                                                          const int* __restrict__ begin, int nmem) {
+  typedef typename C2<T>::t T2;
+  const int total = begin[nmem];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int m = member_of(begin, nmem, item);
+    const Member& M = mem[m];
+    zrhs_body<T>(M.g, (const T2*)M.nl, M.fs, M.om, M.w, M.phi, M.hom, M.hw, M.hphi, M.R, M.first,
+                 M.pz, item - begin[m]);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(ZT) grouped_zbwd_kernel(const Member* __restrict__ mem,
+                                                          const int* __restrict__ begin, int nmem) {
+  typedef typename C2<T>::t T2;
+  const int total = begin[nmem];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int m = member_of(begin, nmem, item);
+    const Member& M = mem[m];
+    zbwd_body<T, 1, 5>(M.g, M.R, M.om, M.w, M.phi, (T2*)M.bw, M.fs, M.pz, item - begin[m]);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(2 * TL) grouped_zsolve_tile_kernel(const Member* __restrict__ mem,
+                                                                     const int* __restrict__ begin,
+                                                                     int nmem) {
+  const int total = begin[nmem];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int m = member_of(begin, nmem, item);
+    const Member& M = mem[m];
+    zsolve_tile_body(M.g, M.R, M.fs, M.g.Mx * M.g.ny, item - begin[m]);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(ST) grouped_zsolve_kernel(const Member* __restrict__ mem,
+                                                            const int* __restrict__ begin, int nmem) {
+  const int total = begin[nmem];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int m = member_of(begin, nmem, item);
+    const Member& M = mem[m];
+    zsolve_body(M.g, M.R, M.fs, M.g.Mx * M.g.ny, (item - begin[m]) * ST + threadIdx.x);
+  }
+}
+
 }  // namespace
 
 size_t zline_smem(const GridDev& g) {
@@ -911,6 +994,63 @@ cudaError_t launch_zrhs(int prec, const GridDev& g, const void* nl, long long fs
                                                      h_om, h_w, h_phi, R, first, pz);
   }
   return cudaGetLastError();
+}
+
+size_t zsolve_tile_smem(const GridDev& g) {
+  return (size_t)TL * g.nz * sizeof(double2) + (size_t)3 * g.nz * sizeof(double);
+}
+int zsolve_tile_lines() { return TL; }
+int zsolve_threads() { return ST; }
+
+cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* begin, int nmem,
+                             int grid, size_t smem, int zsolve_tile, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (stage == 0) {
+    if (prec == 0) {
+      static int cur = 0;
+      if ((e = ensure_smem(grouped_zrhs_kernel<double>, smem, &cur)) != cudaSuccess) return e;
+      grouped_zrhs_kernel<double><<<grid, ZT, smem, s>>>(mem, begin, nmem);
+    } else {
+      static int cur = 0;
+      if ((e = ensure_smem(grouped_zrhs_kernel<float>, smem, &cur)) != cudaSuccess) return e;
+      grouped_zrhs_kernel<float><<<grid, ZT, smem, s>>>(mem, begin, nmem);
+    }
+  } else if (stage == 1) {
+    if (zsolve_tile) {
+      static int cur = 0;
+      if ((e = ensure_smem(grouped_zsolve_tile_kernel, smem, &cur)) != cudaSuccess) return e;
+      grouped_zsolve_tile_kernel<<<grid, 2 * TL, smem, s>>>(mem, begin, nmem);
+    } else {
+      grouped_zsolve_kernel<<<grid, ST, 0, s>>>(mem, begin, nmem);
+    }
+  } else {
+    if (prec == 0) {
+      static int cur = 0;
+      if ((e = ensure_smem(grouped_zbwd_kernel<double>, smem, &cur)) != cudaSuccess) return e;
+      grouped_zbwd_kernel<double><<<grid, ZT, smem, s>>>(mem, begin, nmem);
+    } else {
+      static int cur = 0;
+      if ((e = ensure_smem(grouped_zbwd_kernel<float>, smem, &cur)) != cudaSuccess) return e;
+      grouped_zbwd_kernel<float><<<grid, ZT, smem, s>>>(mem, begin, nmem);
+    }
+  }
+  return cudaGetLastError();
+}
+
+int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile) {
+  int n = 0;
+  if (stage == 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prec == 0 ? (const void*)grouped_zrhs_kernel<double>
+                                                                : (const void*)grouped_zrhs_kernel<float>, ZT, smem);
+  else if (stage == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zsolve_tile ? (const void*)grouped_zsolve_tile_kernel
+                                                                  : (const void*)grouped_zsolve_kernel,
+                                                  zsolve_tile ? 2 * TL : ST, zsolve_tile ? smem : 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prec == 0 ? (const void*)grouped_zbwd_kernel<double>
+                                                                : (const void*)grouped_zbwd_kernel<float>, ZT, smem);
+  cudaGetLastError();
+  return n;
 }
 
 cudaError_t launch_zsolve(const GridDev& g, double2* R, long long fs, cudaStream_t s) {

@@ -1,0 +1,102 @@
+"""Ensemble of uneven channels advanced by grouped persistent launches (a CUDA graph per step).
+
+Each member must evolve exactly as the same channel stepped alone: with the default radix
+schedules the arithmetic is identical (bitwise); after autotuning the radix schedules may differ,
+so the members agree to rounding.  Autotuning leaves every member's state unchanged.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2406_01322_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+PHYS = dict(re_tau=150.0, we=1.0, ch=0.05, pe=20.0, dt=1e-4)
+SIZES = [(32, 32, 33), (24, 18, 17), (16, 36, 25), (48, 24, 33)]
+
+
+@pytest.fixture(scope="module")
+def binding():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_01322_gb300 import build
+    build.build_library()
+    from paper_2406_01322_gb300 import binding as b
+    b.lib()
+    return b
+
+
+def members():
+    return [dict(nx=nx, ny=ny, nz=nz, **PHYS) for nx, ny, nz in SIZES]
+
+
+def fields_of(m, seed):
+    return inputs.initial_fields(m["nx"], m["ny"], m["nz"], m["re_tau"], m["ch"], 1, 0.4, seed)
+
+
+def setup(binding, precision):
+    ms = members()
+    ens = binding.Ensemble(ms, precision=precision)
+    singles = [binding.Grid(precision=precision, **m) for m in ms]
+    for i, (g, s, m) in enumerate(zip(ens.grids, singles, ms)):
+        f = [torch.from_numpy(a) for a in fields_of(m, 1000 + i)]
+        g.set_fields(*f)
+        s.set_fields(*f)
+    return ens, singles
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ensemble_members_match_single_grids_bitwise(binding, precision):
+    ens, singles = setup(binding, precision)
+    ens.step(6)
+    for s in singles:
+        s.step(6)
+    for g, s in zip(ens.grids, singles):
+        for a, b in zip(g.get_fields(), s.get_fields()):
+            assert torch.equal(a, b)
+        assert g.diagnostics()["step"] == 6
+    ens.close()
+
+
+def test_ensemble_timed_steps_match_graph_steps(binding):
+    ens, singles = setup(binding, 0)
+    tot, ks = ens.step_timed(3)
+    assert len(ks) == 6 and tot > 0 and min(ks) >= 0
+    for s in singles:
+        s.step(3)
+    for g, s in zip(ens.grids, singles):
+        for a, b in zip(g.get_fields(), s.get_fields()):
+            assert torch.equal(a, b)
+    ens.close()
+
+
+def test_autotune_keeps_state_and_results(binding):
+    ens, singles = setup(binding, 0)
+    ens.step(2)
+    for s in singles:
+        s.step(2)
+    before = [[t.clone() for t in g.get_fields()] for g in ens.grids]
+    tuning = ens.autotune(reps=1)
+    assert tuning["tuned"] == 1
+    after = [g.get_fields() for g in ens.grids]
+    for x, y in zip(before, after):
+        for a, b in zip(x, y):
+            assert torch.equal(a, b)
+    ens.step(4)
+    for s in singles:
+        s.step(4)
+    for g, s in zip(ens.grids, singles):
+        for a, b in zip(g.get_fields(), s.get_fields()):
+            rel = float((a - b).abs().max() / b.abs().max())
+            assert rel < 1e-12
+    ens.close()
+
+
+def test_ensemble_requires_every_member_set(binding):
+    ens = binding.Ensemble(members()[:2], precision=0)
+    with pytest.raises(binding.ChError) as e:
+        ens.step(1)
+    assert e.value.code == -7
+    ens.close()
