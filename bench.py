@@ -199,6 +199,51 @@ def run_reference(args, w):
     print(json.dumps(out))
 
 
+def run_ensemble(args):
+    """32 uneven channels (mixed precision) advanced by grouped persistent launches, after the
+    autotuner; the same members stepped one by one with their own graphs are timed beside it."""
+    import torch
+    from paper_2406_01322_gb300 import binding, build, inputs
+    build.build_library()
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ms = inputs.ensemble_members()
+    ens = binding.Ensemble(ms, precision=1, device=f"cuda:{local}")
+    for i, (g, m) in enumerate(zip(ens.grids, ms)):
+        g.set_fields(*[torch.from_numpy(a) for a in inputs.initial_fields(**m)])
+    ens.step(1)
+    tuning = ens.autotune(reps=2)
+    ens.step(args.warmup)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        tot_ms, kms = ens.step_timed(args.steps)
+    torch.cuda.synchronize()
+    # the same members, one ch_step per member per step (graph replays, no grouping)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        for g in ens.grids:
+            g.step(1)
+    t1.record()
+    torch.cuda.synchronize()
+    seq_ms = t0.elapsed_time(t1)
+    pts = sum(m["nx"] * m["ny"] * m["nz"] for m in ms)
+    names = list(binding.Grid.KERNELS)
+    out = {"metric": METRIC, "value": pts * args.steps / (tot_ms * 1e-3) / 1e6, "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 transforms/products + f64 solves",
+           "data": "synthetic",
+           "config": {"workload": "ensemble_32_uneven", "members": len(ms),
+                      "points": pts, "precision": "mixed"},
+           "sequential_members_ms_per_step": seq_ms / args.steps,
+           "stage_ms_per_step": {n: kms[i] / args.steps for i, n in enumerate(names)},
+           "tuning": tuning, "gpu_launches": 6 * args.steps, "clocks": clk.summary()}
+    ens.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +256,9 @@ def main():
     args = ap.parse_args()
 
     from paper_2406_01322_gb300 import inputs
+    if args.workload == "ensemble_32_uneven":
+        run_ensemble(args)
+        return
     w = dict(inputs.WORKLOADS[args.workload])
     prec = w["precision"] if args.precision is None else args.precision
     if args.impl == "reference":

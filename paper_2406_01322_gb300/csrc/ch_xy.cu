@@ -416,6 +416,10 @@ int occupancy_xy(int stage, int prec, size_t smem) {
   if (stage == 3) k = prec == 0 ? (const void*)grouped_ypass_kernel<double, true> : (const void*)grouped_ypass_kernel<float, true>;
   else if (stage == 4) k = prec == 0 ? (const void*)grouped_xline_kernel<double> : (const void*)grouped_xline_kernel<float>;
   else k = prec == 0 ? (const void*)grouped_ypass_kernel<double, false> : (const void*)grouped_ypass_kernel<float, false>;
+  if (smem > 48 * 1024) {  // opt-in first (init time, never during capture)
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaGetLastError();
+  }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, stage == 4 ? XT : YT, smem);
   cudaGetLastError();
   return n;

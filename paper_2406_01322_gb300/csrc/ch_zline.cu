@@ -1039,6 +1039,15 @@ cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* 
 
 int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile) {
   int n = 0;
+  // the opt-in above 48 KB must be in place before the query (init time, never during capture)
+  if (smem > 48 * 1024) {
+    const void* k = stage == 0 ? (prec == 0 ? (const void*)grouped_zrhs_kernel<double> : (const void*)grouped_zrhs_kernel<float>)
+                  : stage == 1 ? (const void*)grouped_zsolve_tile_kernel
+                               : (prec == 0 ? (const void*)grouped_zbwd_kernel<double> : (const void*)grouped_zbwd_kernel<float>);
+    if (stage != 1 || zsolve_tile)
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaGetLastError();
+  }
   if (stage == 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prec == 0 ? (const void*)grouped_zrhs_kernel<double>
                                                                 : (const void*)grouped_zrhs_kernel<float>, ZT, smem);

@@ -42,6 +42,20 @@ WORKLOADS = {
 }
 
 
+def ensemble_members(n=32, seed=4):
+    """Uneven ensemble: n channels with seeded sizes nx in {64, 96, 128}, ny in {64, 128},
+    nz in {65, 97, 129}; Re_tau = 150, one drop R = 0.3, Ch = 0.03, Pe = 1/Ch, We = 1, dt = 5e-5;
+    member m's initial field uses seed 1000 + m.  Transforms in float32, solves in float64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for m in range(n):
+        out.append(dict(nx=int(rng.choice([64, 96, 128])), ny=int(rng.choice([64, 128])),
+                        nz=int(rng.choice([65, 97, 129])), re_tau=150.0, ch=0.03,
+                        pe=1.0 / 0.03, we=1.0, dt=5e-5, steps=100, ndrops=1, radius=0.3,
+                        seed=1000 + m, precision=1))
+    return out
+
+
 def grid(nx, ny, nz, lx=4.0 * math.pi, ly=2.0 * math.pi):
     """Collocation coordinates x (nx,), y (ny,), z (nz,)."""
     x = np.arange(nx) * (lx / nx)
