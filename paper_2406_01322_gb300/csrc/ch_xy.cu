@@ -44,7 +44,7 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
       T2 v = zero;
       if (z < Nz && jj != h) v = src[(size_t)jj * Nz + z];
       if (dy) {
-        const T ky = (T)(map.kys * (double)((jj < h) ? jj : jj - Ny));
+        const T ky = (T)map.kys * (T)((jj < h) ? jj : jj - Ny);
         v = mk(-ky * v.y, ky * v.x);
       }
       const int p = (jj < h) ? jj : P - Ny + jj;
