@@ -160,6 +160,34 @@ int ch_transform_forward(ch_grid* g, const double* phys, double* spec);
 int ch_transform_backward(ch_grid* g, const double* spec, double* phys);
 int ch_nonlinear(ch_grid* g, double* out9);
 
+/* ---- Discrete adjoint (float64 grids) ---------------------------------------------------------
+ * Reverse-mode derivative of the discrete step map (Sec. 2.2, steps i)-v); not in the paper: a
+ * service of this library for optimisation / sensitivity studies) for the objective of the
+ * final state
+ *   J = 1/2 int |u|^2 dV + int |grad phi|^2 dV   (exact integrals of the interpolants)
+ * with respect to the physical initial fields u, v, w, phi given to ch_set_fields.
+ * ch_objective: J of the current state (host double; synchronises the stream).
+ * ch_adjoint_begin: allocates the reverse-sweep workspace (24 spectral fields plus six y-padded
+ *   fields, with the grid's allocator) and seeds the sweep with dJ/ds of the CURRENT state (the
+ *   final state of the forward run); *J receives J (may be NULL).
+ * ch_adjoint_step: reverses ONE forward step.  `state` is a device buffer written by
+ *   ch_get_state just before that forward step; steps are reversed last to first.  The handle's
+ *   state becomes the saved one but its non-linear terms are not recomputed: ch_step,
+ *   ch_step_timed and ch_nonlinear answer CH_ERR_STATE until ch_set_state / ch_set_fields /
+ *   ch_set_spectral.
+ * ch_adjoint_gradient: after the step reversed last (the first forward step), writes
+ *   dJ/du0, dJ/dv0, dJ/dw0, dJ/dphi0 into four device (nz,ny,nx) float64 arrays.
+ * ch_adjoint_end: frees the workspace (ch_destroy does too).
+ * Mixed-precision grids: CH_ERR_ARG.  Grids whose padded x length Px = 3 nx / 2 exceeds 602
+ * (the transposed x line keeps 24 lines of Px complex float64, 384 Px bytes, in the 226 KiB of
+ * shared memory a block may use): CH_ERR_SIZE (nx <= 384 among the supported sizes).
+ * Calls out of order (step/gradient before begin; J of an unset grid): CH_ERR_STATE. */
+int ch_objective(ch_grid* g, double* J);
+int ch_adjoint_begin(ch_grid* g, double* J);
+int ch_adjoint_step(ch_grid* g, const void* state);
+int ch_adjoint_gradient(ch_grid* g, double* gu, double* gv, double* gw, double* gphi);
+int ch_adjoint_end(ch_grid* g);
+
 /* ---- Ensemble of independent channels (uneven sizes) ---------------------------------------
  * Not in the paper: a batching service of this library.  Each member is an ordinary ch_grid
  * (created here with the given allocator and stream; all members share `precision`).  One

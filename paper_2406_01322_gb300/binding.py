@@ -72,6 +72,11 @@ _SIGS = {
     "ch_transform_forward_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     _P, _P, _P]),
     "ch_noalloc_scratch_bytes": (ctypes.c_size_t, []),
+    "ch_objective": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "ch_adjoint_begin": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "ch_adjoint_step": (ctypes.c_int, [_P, _P]),
+    "ch_adjoint_gradient": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "ch_adjoint_end": (ctypes.c_int, [_P]),
     "ch_ensemble_init": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, ALLOC_FN, FREE_FN,
                                         _P, _P, ctypes.POINTER(_P)]),
     "ch_ensemble_size": (ctypes.c_int, [_P]),
@@ -298,6 +303,85 @@ class Grid:
         out = torch.empty((9,) + self.spec_shape, dtype=torch.complex128, device=self.device)
         _ck("ch_nonlinear", lib().ch_nonlinear(self.h, _ptr(out)))
         return out
+
+    # ---- discrete adjoint (float64 grids) ----
+    def objective(self):
+        """J = 1/2 int |u|^2 + int |grad phi|^2 of the current state (a Python float)."""
+        J = ctypes.c_double()
+        _ck("ch_objective", lib().ch_objective(self.h, ctypes.byref(J)))
+        return J.value
+
+    def adjoint_begin(self):
+        """Seed the reverse sweep with dJ/ds of the current (final) state; returns J."""
+        J = ctypes.c_double()
+        _ck("ch_adjoint_begin", lib().ch_adjoint_begin(self.h, ctypes.byref(J)))
+        return J.value
+
+    def adjoint_step(self, state):
+        """Reverse the forward step that started from `state` (a get_state() buffer)."""
+        _ck("ch_adjoint_step", lib().ch_adjoint_step(self.h, _ptr(state)))
+
+    def adjoint_gradient(self):
+        """dJ/d(u0, v0, w0, phi0) after the first forward step was reversed."""
+        outs = [torch.empty(self.shape, dtype=torch.float64, device=self.device) for _ in range(4)]
+        _ck("ch_adjoint_gradient", lib().ch_adjoint_gradient(self.h, *[_ptr(t) for t in outs]))
+        return outs
+
+    def adjoint_end(self):
+        _ck("ch_adjoint_end", lib().ch_adjoint_end(self.h))
+
+
+class ChannelObjective(torch.autograd.Function):
+    """J(s_K) after K steps from the physical initial fields, differentiable in (u, v, w, phi).
+
+    Forward: set_fields, K steps, J.  Saved: the state every `every` steps (checkpoints) and the
+    final state.  Backward: segment by segment from the last, the segment is recomputed from its
+    checkpoint with every intermediate state saved, then reversed step by step by the library's
+    adjoint kernels; the gradient of the first state maps back to the physical fields."""
+
+    @staticmethod
+    def forward(ctx, u, v, w, phi, grid, nsteps, every):
+        every = max(1, int(every))
+        grid.set_fields(u, v, w, phi)
+        ckpts = []
+        for n in range(nsteps):
+            if n % every == 0:
+                ckpts.append(grid.get_state())
+            grid.step(1)
+        final = grid.get_state()
+        J = grid.objective()
+        ctx.grid, ctx.nsteps, ctx.every = grid, nsteps, every
+        ctx.ckpts, ctx.final = ckpts, final
+        ctx.devices = [(t.device, t.dtype) for t in (u, v, w, phi)]
+        return torch.tensor(J, dtype=torch.float64, device=u.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        g, K, every = ctx.grid, ctx.nsteps, ctx.every
+        g.set_state(ctx.final)
+        g.adjoint_begin()
+        try:
+            for c in range(len(ctx.ckpts) - 1, -1, -1):
+                n0 = c * every
+                n1 = min(K, n0 + every)
+                g.set_state(ctx.ckpts[c])
+                states = [ctx.ckpts[c]]
+                for _ in range(n0 + 1, n1):
+                    g.step(1)
+                    states.append(g.get_state())
+                for st in reversed(states):
+                    g.adjoint_step(st)
+            grads = g.adjoint_gradient()
+        finally:
+            g.adjoint_end()
+        scale = gJ.to(dtype=torch.float64, device=grads[0].device)
+        out = [(gr * scale).to(device=d, dtype=dt) for gr, (d, dt) in zip(grads, ctx.devices)]
+        return out[0], out[1], out[2], out[3], None, None, None
+
+
+def objective_after(grid, u, v, w, phi, nsteps, checkpoint_every=10):
+    """J after `nsteps` steps of `grid` from (u, v, w, phi); differentiable through autograd."""
+    return ChannelObjective.apply(u, v, w, phi, grid, int(nsteps), int(checkpoint_every))
 
 
 class Ensemble:

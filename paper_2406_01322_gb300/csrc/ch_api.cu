@@ -318,6 +318,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   g.NK = g.Mx * (ny / 2 + 1);
   G->fac = (double*)A(chf::fac_doubles(g) * sizeof(double));
   G->diag_part = (double*)A((size_t)(304 * 6 + 16) * sizeof(double));
+  G->obj_part = (double*)A(((size_t)g.Mx * ny + 8) * sizeof(double));
   G->diag_out = G->diag_part + 304 * 6;
   if (st != CH_OK) {
     return bail(G, st);
@@ -423,6 +424,7 @@ static int set_from_phys(ch_grid* G, const double* u, const double* v, const dou
   G->nstep = 0;
   G->t = 0.0;
   G->fields_set = 1;
+  G->nl_stale = 0;
   return eval_nonlinear_impl(G);
 }
 
@@ -445,7 +447,7 @@ int ch_set_fields_host(ch_grid* G, const double* u, const double* v, const doubl
 
 int ch_step(ch_grid* G, int nsteps) {
   if (!G || nsteps < 0) return CH_ERR_ARG;
-  if (!G->fields_set) return CH_ERR_STATE;
+  if (!G->fields_set || G->nl_stale) return CH_ERR_STATE;
   for (int i = 0; i < nsteps; ++i) {
     if (G->first) {
       int r = launch_step(G, 1, G->stream);
@@ -480,7 +482,7 @@ int ch_launches_per_step(const ch_grid* G) { return G ? CH_STEP_KERNELS : 0; }
 
 int ch_step_timed(ch_grid* G, int nsteps, double* kernel_ms, double* total_ms) {
   if (!G || nsteps < 0 || !total_ms) return CH_ERR_ARG;
-  if (!G->fields_set) return CH_ERR_STATE;
+  if (!G->fields_set || G->nl_stale) return CH_ERR_STATE;
   const int NKER = CH_STEP_KERNELS;
   const int nev = NKER * nsteps + 1;
   std::vector<cudaEvent_t> ev(nev);
@@ -560,15 +562,7 @@ int ch_diagnostics(ch_grid* G, ch_diag* out) {
 }
 
 // checkpoint layout: 64-byte header, then om w phi hom hw hphi
-struct StateHeader {
-  uint64_t magic;
-  int32_t nx, ny, nz, first;
-  int64_t nstep;
-  double t;
-  int32_t fields_set, pad0;
-  uint64_t pad[2];
-};
-static_assert(sizeof(StateHeader) == 64, "header size");
+using chf::StateHeader;
 
 size_t ch_state_bytes(const ch_grid* G) {
   if (!G) return 0;
@@ -579,7 +573,7 @@ int ch_get_state(ch_grid* G, void* buf) {
   if (!G || !buf) return CH_ERR_ARG;
   StateHeader h;
   memset(&h, 0, sizeof(h));
-  h.magic = 0x3130333234303632ULL;
+  h.magic = chf::kStateMagic;
   h.nx = G->g.nx;
   h.ny = G->g.ny;
   h.nz = G->g.nz;
@@ -603,7 +597,7 @@ int ch_set_state(ch_grid* G, const void* buf) {
   const char* b = (const char*)buf;
   CK(cudaMemcpyAsync(&h, b, sizeof(h), cudaMemcpyDeviceToHost, G->stream));
   CK(cudaStreamSynchronize(G->stream));
-  if (h.magic != 0x3130333234303632ULL || h.nx != G->g.nx || h.ny != G->g.ny || h.nz != G->g.nz)
+  if (h.magic != chf::kStateMagic || h.nx != G->g.nx || h.ny != G->g.ny || h.nz != G->g.nz)
     return CH_ERR_ARG;
   const size_t sb = (size_t)G->fs * sizeof(double2);
   double2* dst[6] = {G->om, G->w, G->phi, G->hom, G->hw, G->hphi};
@@ -613,6 +607,7 @@ int ch_set_state(ch_grid* G, const void* buf) {
   G->nstep = h.nstep;
   G->t = h.t;
   G->fields_set = h.fields_set;
+  G->nl_stale = 0;
   if (!G->fields_set) return CH_OK;
   return eval_nonlinear_impl(G);
 }
@@ -637,6 +632,7 @@ int ch_set_spectral(ch_grid* G, const double* om, const double* w, const double*
   G->nstep = 0;
   G->t = 0.0;
   G->fields_set = 1;
+  G->nl_stale = 0;
   return eval_nonlinear_impl(G);
 }
 
@@ -663,7 +659,7 @@ int ch_transform_backward(ch_grid* G, const double* spec, double* phys) {
 
 int ch_nonlinear(ch_grid* G, double* out10) {
   if (!G || !out10) return CH_ERR_ARG;
-  if (!G->fields_set) return CH_ERR_STATE;
+  if (!G->fields_set || G->nl_stale) return CH_ERR_STATE;
   CK(chf::launch_dct_lines(0, G->prec, G->g, G->nl, (double2*)out10, kNl, G->fs, G->pz, G->stream));
   return CH_OK;
 }
@@ -672,6 +668,7 @@ void ch_destroy(ch_grid* G) {
   if (!G) return;
   cudaStreamSynchronize(G->stream);
   drop_graph(G);
+  ch_adjoint_release(G);
   release_all(G);
   cudaStreamDestroy(G->cap);
   delete G;

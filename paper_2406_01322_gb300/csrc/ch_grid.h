@@ -1,6 +1,8 @@
 // Host-side state of one channel handle (internal to libchflow).
 #pragma once
 
+#include <stdint.h>
+
 #include <vector>
 
 #include "../../include/ch_flow.h"
@@ -25,6 +27,18 @@ YMap step_ymap();
 // radix schedule with a style: 0 one radix-8 for an odd power of two then 4s, 2, 3s;
 // 1 the same with the radix-3 passes first; 2 as many radix-8 passes as possible
 bool make_radices_style(int n, int style, FftPlan* pl);
+
+// header of a ch_get_state buffer (followed by om, w, phi, h_om, h_w, h_phi)
+struct StateHeader {
+  uint64_t magic;
+  int32_t nx, ny, nz, first;
+  int64_t nstep;
+  double t;
+  int32_t fields_set, pad0;
+  uint64_t pad[2];
+};
+static_assert(sizeof(StateHeader) == 64, "header size");
+const uint64_t kStateMagic = 0x3130333234303632ULL;
 
 }  // namespace chf
 
@@ -67,8 +81,18 @@ struct ch_grid {
   cudaGraphExec_t gexec;
   int graph_ok;
   cudaStream_t cap;  // private non-blocking stream used only to capture the step graph
+
+  // discrete adjoint: per-line objective partial sums and the reduced value (allocated with the
+  // grid), the reverse-sweep workspace (one block, ch_adjoint_begin .. ch_adjoint_end)
+  double* obj_part = nullptr;
+  void* adj_block = nullptr;
+  double2 *a_lam = nullptr, *a_L = nullptr, *a_Rb = nullptr, *a_mu = nullptr, *a_mu2 = nullptr;
+  double2 *a_nlb = nullptr, *a_x6 = nullptr, *a_bb = nullptr;
+  int nl_stale = 0;  // 1: the state was replaced by a reverse step; products not recomputed
 };
 
 // launch schedule of one step on stream s (events optional) and the non-linear evaluation
 int ch_launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev);
 int ch_eval_nonlinear(ch_grid* G);
+// frees the reverse-sweep workspace if allocated
+void ch_adjoint_release(ch_grid* G);

@@ -126,6 +126,37 @@ cudaError_t launch_x_c2r(const GridDev& g, const double2* in, double* phys, int 
                          long long fs_spec, long long fs_phys, const FftPlan& px,
                          cudaStream_t s);
 
+// ---- discrete adjoint of the step (float64; transposes under the real inner product) ----
+// adj_zsolve: Rb = transposed tau solves of L (adjoint of the new state, 3 fields); bb receives
+//   per (line, parity) the adjoints of the omega, w and D w wall values of s_n (3 complex).
+// adj_zrhs: from Rb, L, bb and mu (adjoint of this step's AB2 history h_n): lam = adjoint of the
+//   state s_n except its non-linear dependence, mu_prev = adjoint of h_{n-1}, nlb = adjoint of
+//   the 9 spectral non-linear fields times 1/(Px Py).
+// adj_xline: transposed x-line (in6 = the forward y-padded fields of s_n, pb9 = adjoints of the
+//   9 products after the transposed forward y pass) -> out6 adjoints of u v w phi phi_y phi_z.
+// fold_dy: f6[3] += -i ky f6[4]; f6[4] = f6[5].
+// adj_zbwd: transposed backward fields (5 inputs u v w phi D phi) accumulated into lam.
+// objective: J = 1/2 int |u|^2 + int |grad phi|^2 per line into part[Mx*Ny], lam = dJ/ds.
+// adj_project: transposed set_fields projection -> 4 fields scaled for the x/y transposes.
+cudaError_t launch_adj_zsolve(const GridDev& g, const double2* L, double2* Rb, long long fs,
+                              double2* bb, cudaStream_t s);
+cudaError_t launch_adj_zrhs(const GridDev& g, const double2* Rb, const double2* L,
+                            const double2* mu, double2* lam, double2* mu_prev, double2* nlb,
+                            long long fs, int first, const double2* bb, const FftPlan& pz,
+                            cudaStream_t s);
+cudaError_t launch_adj_zbwd(const GridDev& g, const double2* in5, long long fs_in, double2* lam,
+                            long long fs, const FftPlan& pz, cudaStream_t s);
+cudaError_t launch_objective(const GridDev& g, const double2* om, const double2* w,
+                             const double2* phi, double2* lam, long long fs, double* part,
+                             cudaStream_t s);
+cudaError_t launch_adj_project(const GridDev& g, const double2* lam, long long fs, double2* out4,
+                               const FftPlan& pz, cudaStream_t s);
+cudaError_t launch_fold_dy(const GridDev& g, double2* f6, long long fs, cudaStream_t s);
+cudaError_t launch_sum(const double* a, int n, double* out, cudaStream_t s);
+size_t adj_xline_smem(int Px);
+cudaError_t launch_adj_xline(const GridDev& g, const double2* in6, const double2* pb9,
+                             double2* out6, long long fs, const FftPlan& px, cudaStream_t s);
+
 // diagnostics reduction over the 7 physical unpadded fields u v w phi phix phiy phiz
 // (each (Nz, Ny, Nx)); out[0..8] as in ch_diag (t and step filled by the host).
 cudaError_t launch_diag(const GridDev& g, const double* phys7, long long fs,

@@ -254,6 +254,151 @@ __global__ void __launch_bounds__(128) x_c2r_kernel(const double2* __restrict__ 
   }
 }
 
+// Transposed x-line kernel (float64, discrete adjoint of xline_kernel with scale 1).
+// Per (pair of z rows, y): the seven forward inputs are re-synthesised from `in` (as in the
+// forward kernel); the nine product adjoints `pb` (kept modes kx < Mx) go to physical space by
+// the transpose of the truncated r2c, i.e. a c2r of the half spectrum with modes kx >= 1 halved;
+// the pointwise Jacobian of the nine products is applied transposed, accumulating the adjoints
+// of u, v, w, phi, phi_x, phi_y, phi_z; those go back by the transpose of the zero-padded c2r,
+// an r2c with modes kx >= 1 doubled; phi_x = i kx phi folds into phi with -i kx.
+// Outputs (spectra kx < Mx, layout of `in`): u, v, w, phi, phi_y, phi_z adjoints.
+// Shared memory: 24 lines of Px complex values (7 forward, 7 accumulators, 5 + 5 product/scratch).
+__global__ void __launch_bounds__(XT) adj_xline_kernel(const double2* __restrict__ in,
+                                                       const double2* __restrict__ pb,
+                                                       double2* __restrict__ out, int Mx, int Px,
+                                                       int Py, int Nz, long long fs, double kappa,
+                                                       double kxs, FftPlan pl) {
+  extern __shared__ double2 axs[];
+  double2* S = axs;
+  const int z0 = 2 * blockIdx.x;
+  const int y = blockIdx.y;
+  const bool two = (z0 + 1 < Nz);
+  const double2 zero = make_double2(0.0, 0.0);
+  const size_t base = (size_t)y * Nz + z0;
+  const size_t mstride = (size_t)Py * Nz;
+  const bool odd = (pl.nst & 1);
+  // ---- forward inputs: start so that the result lands in S[0..6]
+  double2* F0 = odd ? S + 7 * Px : S;
+  for (int idx = threadIdx.x; idx < 7 * Mx; idx += blockDim.x) {
+    const int f = idx / Mx, m = idx - f * Mx;
+    const int src_f = (f < 4) ? f : f - 1;
+    const double2* src = in + src_f * fs + (size_t)m * mstride + base;
+    double2 a = src[0];
+    double2 b = two ? src[1] : zero;
+    if (f == 4) {
+      const double kx = kxs * m;
+      a = make_double2(-kx * a.y, kx * a.x);
+      b = make_double2(-kx * b.y, kx * b.x);
+    }
+    double2* L = F0 + f * Px;
+    if (m == 0) {
+      L[0] = make_double2(a.x, b.x);
+    } else {
+      L[m] = make_double2(a.x - b.y, a.y + b.x);
+      L[Px - m] = make_double2(a.x + b.y, b.x - a.y);
+    }
+  }
+  {
+    const int w = Px - 2 * Mx + 1;
+    for (int idx = threadIdx.x; idx < 7 * w; idx += blockDim.x) {
+      const int f = idx / w, q = idx - f * w;
+      F0[f * Px + Mx + q] = zero;
+    }
+  }
+  __syncthreads();
+  const double2* in7 = block_fft<double, true>(F0, odd ? S : S + 7 * Px, 7, Px, pl);  // == S
+  double2* acc = S + 7 * Px;       // seven accumulator lines
+  double2* P0 = S + 14 * Px;       // five product-adjoint lines (result position)
+  double2* P1 = S + 19 * Px;       // five scratch lines
+  for (int g0 = 0; g0 < 9; g0 += 5) {
+    const int cnt = (g0 == 0) ? 5 : 4;
+    double2* L0 = odd ? P1 : P0;
+    for (int idx = threadIdx.x; idx < cnt * Mx; idx += blockDim.x) {
+      const int q = idx / Mx, m = idx - q * Mx;
+      const double2* src = pb + (g0 + q) * fs + (size_t)m * mstride + base;
+      double2 a = src[0];
+      double2 b = two ? src[1] : zero;
+      double2* L = L0 + q * Px;
+      if (m == 0) {
+        L[0] = make_double2(a.x, b.x);
+      } else {
+        a = 0.5 * a;
+        b = 0.5 * b;
+        L[m] = make_double2(a.x - b.y, a.y + b.x);
+        L[Px - m] = make_double2(a.x + b.y, b.x - a.y);
+      }
+    }
+    {
+      const int w = Px - 2 * Mx + 1;
+      for (int idx = threadIdx.x; idx < cnt * w; idx += blockDim.x) {
+        const int q = idx / w, r = idx - q * w;
+        L0[q * Px + Mx + r] = zero;
+      }
+    }
+    __syncthreads();
+    const double2* pr = block_fft<double, true>(L0, odd ? P0 : P1, cnt, Px, pl);  // == P0
+    for (int x = threadIdx.x; x < Px; x += blockDim.x) {
+      const double2 u = in7[x], v = in7[Px + x], w = in7[2 * Px + x], ph = in7[3 * Px + x];
+      const double2 fx = in7[4 * Px + x], fy = in7[5 * Px + x], fz = in7[6 * Px + x];
+      if (g0 == 0) {
+        const double2 b0 = pr[x], b1 = pr[Px + x], b2 = pr[2 * Px + x], b3 = pr[3 * Px + x],
+                      b4 = pr[4 * Px + x];
+        double2 r;
+#define ADJ0(C)                                                                             \
+        r.C = -2.0 * u.C * b0.C - v.C * b2.C - w.C * b3.C;                                  \
+        acc[x].C = r.C;                                                                     \
+        r.C = -2.0 * v.C * b1.C - u.C * b2.C - w.C * b4.C;                                  \
+        acc[Px + x].C = r.C;                                                                \
+        r.C = 2.0 * w.C * (b0.C + b1.C) - u.C * b3.C - v.C * b4.C;                          \
+        acc[2 * Px + x].C = r.C;                                                            \
+        acc[3 * Px + x].C = 0.0;                                                            \
+        r.C = kappa * (-2.0 * fx.C * b0.C - fy.C * b2.C - fz.C * b3.C);                     \
+        acc[4 * Px + x].C = r.C;                                                            \
+        r.C = kappa * (-2.0 * fy.C * b1.C - fx.C * b2.C - fz.C * b4.C);                     \
+        acc[5 * Px + x].C = r.C;                                                            \
+        r.C = kappa * (2.0 * fz.C * (b0.C + b1.C) - fx.C * b3.C - fy.C * b4.C);             \
+        acc[6 * Px + x].C = r.C;
+        ADJ0(x)
+        ADJ0(y)
+#undef ADJ0
+      } else {
+        const double2 b5 = pr[x], b6 = pr[Px + x], b7 = pr[2 * Px + x], b8 = pr[3 * Px + x];
+#define ADJ1(C)                                                                             \
+        acc[x].C += ph.C * b6.C;                                                            \
+        acc[Px + x].C += ph.C * b7.C;                                                       \
+        acc[2 * Px + x].C += ph.C * b8.C;                                                   \
+        acc[3 * Px + x].C = 3.0 * ph.C * ph.C * b5.C + u.C * b6.C + v.C * b7.C + w.C * b8.C;
+        ADJ1(x)
+        ADJ1(y)
+#undef ADJ1
+      }
+    }
+    __syncthreads();
+  }
+  // ---- r2c of the seven accumulators (kx >= 1 doubled), fold phi_x into phi
+  const double2* R = block_fft<double, false>(acc, P0, 7, Px, pl);
+  for (int idx = threadIdx.x; idx < 6 * Mx; idx += blockDim.x) {
+    const int q = idx / Mx, m = idx - q * Mx;
+    const int line = (q < 4) ? q : q + 1;           // skip phi_x (line 4)
+    const double hs = (m == 0) ? 0.5 : 1.0;
+    const int mm = (m == 0) ? 0 : Px - m;
+    double2 Zk = R[line * Px + m], Zm = R[line * Px + mm];
+    double2 A = make_double2(hs * (Zk.x + Zm.x), hs * (Zk.y - Zm.y));
+    double2 B = make_double2(hs * (Zk.y + Zm.y), hs * (Zm.x - Zk.x));
+    if (q == 3) {  // + (-i kx) phi_x adjoint
+      const double2 Xk = R[4 * Px + m], Xm = R[4 * Px + mm];
+      const double2 Ax = make_double2(hs * (Xk.x + Xm.x), hs * (Xk.y - Xm.y));
+      const double2 Bx = make_double2(hs * (Xk.y + Xm.y), hs * (Xm.x - Xk.x));
+      const double kx = kxs * m;
+      A = make_double2(A.x + kx * Ax.y, A.y - kx * Ax.x);
+      B = make_double2(B.x + kx * Bx.y, B.y - kx * Bx.x);
+    }
+    double2* dst = out + q * fs + (size_t)m * mstride + base;
+    dst[0] = A;
+    if (two) dst[1] = B;
+  }
+}
+
 int ytile_local(int P, size_t elem) {
   // z tile: 8 columns (128 B of fp64 complex), fewer when the lines are long
   int tz = 8;
@@ -361,6 +506,20 @@ cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out1
                                                g.Py, g.nz, fs, (float)g.kappa, (float)scale,
                                                (float)(6.283185307179586476925 / g.lx), px);
   }
+  return cudaGetLastError();
+}
+
+size_t adj_xline_smem(int Px) { return (size_t)24 * Px * sizeof(double2); }
+
+cudaError_t launch_adj_xline(const GridDev& g, const double2* in6, const double2* pb9,
+                             double2* out6, long long fs, const FftPlan& px, cudaStream_t s) {
+  const size_t smem = adj_xline_smem(g.Px);
+  dim3 grid((g.nz + 1) / 2, g.Py);
+  static int cur = 0;
+  cudaError_t e = ensure_smem(adj_xline_kernel, smem, &cur);
+  if (e != cudaSuccess) return e;
+  adj_xline_kernel<<<grid, XT, smem, s>>>(in6, pb9, out6, g.Mx, g.Px, g.Py, g.nz, fs, g.kappa,
+                                          6.283185307179586476925 / g.lx, px);
   return cudaGetLastError();
 }
 

@@ -902,6 +902,618 @@ __global__ void diag_final_kernel(GridDev g, int nblk, const double* __restrict_
   out[6] = m[2];
 }
 
+// ---- discrete adjoint of the step (float64) ----------------------------------------------
+// Transposes are taken with respect to the real inner product <a, b> = sum Re(conj(a) b) over
+// the stored components, so multiplication by a complex constant c transposes to conj(c).
+
+// D^T in coefficient space as warp prefix sums: (D^T l)_p = 2 p sum_{n < p, n + p odd} l_n / c_n.
+// For output parity q the source class is n = (1-q) + 2m; output p = q + 2i collects m <= i - 1
+// (q = 0) or m <= i (q = 1).
+__device__ void dzT_scan(const double2* src, double2* dst, int comp, int q, int N, double* tmp) {
+  const double* s = reinterpret_cast<const double*>(src) + comp;
+  double* d = reinterpret_cast<double*>(dst) + comp;
+  const int lane = threadIdx.x & 31;
+  const int ps = 1 - q;
+  const int cnt = (N - ps) / 2 + 1;
+  const int E = (cnt + 31) / 32;
+  const int m0 = lane * E;
+  double acc = 0.0;
+  for (int e = 0; e < E; ++e) {
+    const int m = m0 + e;
+    if (m < cnt) {
+      const int n = ps + 2 * m;
+      acc += (n == 0 ? 0.5 : 1.0) * s[2 * n];
+      tmp[m] = acc;
+    }
+  }
+  double v = acc;  // inclusive scan of chunk totals
+  for (int off = 1; off < 32; off <<= 1) {
+    const double o = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane >= off) v += o;
+  }
+  const double prv = __shfl_up_sync(0xffffffffu, v, 1);
+  const double excl = (lane == 0) ? 0.0 : prv;
+  for (int e = 0; e < E; ++e) {
+    const int m = m0 + e;
+    if (m < cnt) tmp[m] += excl;
+  }
+  __syncwarp();
+  const int nout = (N - q) / 2 + 1;
+  for (int i = lane; i < nout; i += 32) {
+    const int pp = q + 2 * i;
+    int m = (q == 0) ? i - 1 : i;
+    if (m > cnt - 1) m = cnt - 1;
+    const double T = (m >= 0) ? tmp[m] : 0.0;
+    d[2 * pp] = 2.0 * pp * T;
+  }
+  __syncwarp();
+}
+
+__device__ void dzT_tasks(double2* const* src, double2* const* dst, int ntask, int N, double* tmp) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* mytmp = tmp + warp * (N / 2 + 2);
+  for (int s = warp; s < 4 * ntask; s += nw) {
+    const int t = s >> 2, comp = (s >> 1) & 1, q = s & 1;
+    dzT_scan(src[t], dst[t], comp, q, N, mytmp);
+  }
+}
+
+// transpose of tau_sweep_c for parity p of one complex line, in place (x: solution adjoint in,
+// right-hand-side adjoint out).  Reverses: a_i = P_i + Q_i a_0; a_0 = -rsq sum beta_i P_i;
+// P_i = X_i + Y_i P_{i-1}; X_i = (g_i - U_i X_{i+1}) rd_i; g_i = t1 f_{n-2} - t2 f_n + t3 f_{n+2}.
+// Returns rsq times the adjoint of a_0, which is the adjoint of the boundary-row value b when the
+// row reads sum_n wb_n a_n = b (a_0 = (b - sum wb P) rsq; the forward sweep has b = 0).
+__device__ double2 tau_sweep_ct(double2* x, int p, int N, double alpha, bool neumann,
+                                const double* t1, const double* t2, const double* t3,
+                                const double* Y, const double* RD, const double* Q, int NK,
+                                double rsq) {
+  const int I = (N - p) / 2;
+  // a_0 collects the Q-weighted adjoints of a_1..a_I
+  double2 a0 = x[p];
+  for (int i = 1; i <= I; ++i) {
+    const int n = p + 2 * i;
+    const double q = Q[(size_t)n * NK];
+    a0.x = fma(q, x[n].x, a0.x);
+    a0.y = fma(q, x[n].y, a0.y);
+  }
+  // P_i adjoint = a_i adjoint - rsq beta_i a_0 adjoint
+  for (int i = 1; i <= I; ++i) {
+    const int n = p + 2 * i;
+    const double wb = neumann ? (double)n * (double)n : 1.0;
+    const double c = -rsq * wb;
+    double2 v = x[n];
+    v.x = fma(c, a0.x, v.x);
+    v.y = fma(c, a0.y, v.y);
+    x[n] = v;
+  }
+  // X adjoint: X_i = P_i + Y_{i+1} X_{i+1} (from the top)
+  double2 xn = make_double2(0.0, 0.0);
+  for (int i = I; i >= 1; --i) {
+    const int n = p + 2 * i;
+    double2 v = x[n];
+    if (i < I) {
+      const double y = Y[(size_t)(n + 2) * NK];
+      v.x = fma(y, xn.x, v.x);
+      v.y = fma(y, xn.y, v.y);
+    }
+    x[n] = v;
+    xn = v;
+  }
+  // g adjoint: g_1 = X_1 rd_1, g_i = (X_i - U_{i-1} g_{i-1}) rd_i
+  double2 gp = make_double2(0.0, 0.0);
+  for (int i = 1; i <= I; ++i) {
+    const int n = p + 2 * i;
+    const double rd = RD[(size_t)n * NK];
+    double2 v = x[n];
+    if (i > 1) {
+      const double U = -alpha * t3[n - 2];
+      v.x = fma(-U, gp.x, v.x);
+      v.y = fma(-U, gp.y, v.y);
+    }
+    v.x *= rd;
+    v.y *= rd;
+    x[n] = v;
+    gp = v;
+  }
+  // f adjoint from the stencil: f_{n_k} = t1[n_{k+1}] g_{k+1} - t2[n_k] g_k + t3[n_{k-1}] g_{k-1}
+  double2 gprev = make_double2(0.0, 0.0);  // g_{k-1}
+  for (int k = 0; k <= I; ++k) {
+    const int n = p + 2 * k;
+    const double2 gk = (k >= 1) ? x[n] : make_double2(0.0, 0.0);
+    const double2 gn = (k + 1 <= I) ? x[n + 2] : make_double2(0.0, 0.0);
+    double2 f = make_double2(0.0, 0.0);
+    if (k + 1 <= I) {
+      f.x = t1[n + 2] * gn.x;
+      f.y = t1[n + 2] * gn.y;
+    }
+    if (k >= 1) {
+      f.x = fma(-t2[n], gk.x, f.x);
+      f.y = fma(-t2[n], gk.y, f.y);
+    }
+    if (k >= 2) {
+      f.x = fma(t3[n - 2], gprev.x, f.x);
+      f.y = fma(t3[n - 2], gprev.y, f.y);
+    }
+    x[n] = f;
+    gprev = gk;
+  }
+  return make_double2(rsq * a0.x, rsq * a0.y);
+}
+
+// adjoint of zsolve + state update: one thread per (line, parity); L = adjoint of the new
+// state (3 fields), Rb = adjoint of the right-hand sides (3 fields, written).
+// The adjoint differentiates the literal Crank-Nicolson map, whose solves impose the wall
+// conditions on q^{n+1}.  The forward sweeps solve for S = q^{n+1} + q^n with homogeneous wall
+// rows; on states that meet the wall conditions that is the same as imposing S's wall values =
+// q^n's, and the adjoint of those values goes back to q^n: bb[(line, p)] = (omega wall value,
+// w wall value, D w wall value) adjoints of parity p, added to the state adjoint by adj_zrhs.
+__global__ void __launch_bounds__(ST) adj_zsolve_kernel(GridDev g, const double2* __restrict__ L,
+                                                        double2* __restrict__ Rb, long long fs,
+                                                        int nlines, double2* __restrict__ bb) {
+  const int N = g.N, Nz = g.nz;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int line = t >> 1, p = t & 1;
+  if (line >= nlines) return;
+  int mx, j;
+  double kx, ky;
+  line_wavenumbers(g, line, mx, j, kx, ky);
+  const int K = line_K(g, mx, j);
+  const double k2 = kx * kx + ky * ky;
+  const bool is00 = (mx == 0 && j == 0);
+  const bool nyq = (j == g.ny / 2);
+  const double *t1 = g.go1, *t2 = g.go2, *t3 = g.go3;
+  const double2 zero = make_double2(0.0, 0.0);
+  double2* bl = bb + (size_t)t * 3;
+  for (int f = 0; f < 3; ++f) {
+    const double2* in = L + f * fs + (size_t)line * Nz;
+    double2* row = Rb + f * fs + (size_t)line * Nz;
+    for (int n = p; n <= N; n += 2) row[n] = nyq ? zero : in[n];
+  }
+  if (nyq) {
+    bl[0] = zero;
+    bl[1] = zero;
+    bl[2] = zero;
+    return;
+  }
+  // omega (and the mean flow): S = Sol_beta(r; wall value of omega^n)
+  double2* row = Rb + (size_t)line * Nz;
+  bl[0] = tau_sweep_ct(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
+                       fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
+  // w: S_w = Omega_p + c Omega_h, Omega_p = Sol_0(Sol_beta r; wall value of w^n),
+  //    c = (D w^n wall value - sum n^2 Omega_p) rsh
+  row = Rb + fs + (size_t)line * Nz;
+  if (is00) {
+    for (int n = p; n <= N; n += 2) row[n] = zero;
+    bl[1] = zero;
+    bl[2] = zero;
+  } else {
+    const double* oh = fac_oh(g, K);
+    const double rsh = fac_rsh(g, p, K);
+    double2 sacc = zero;
+    for (int n = p; n <= N; n += 2) {
+      const double h = oh[(size_t)n * g.NK];
+      sacc.x = fma(h, row[n].x, sacc.x);
+      sacc.y = fma(h, row[n].y, sacc.y);
+    }
+    const double2 bD = make_double2(rsh * sacc.x, rsh * sacc.y);
+    for (int n = p; n <= N; n += 2) {
+      const double c = -(double)n * (double)n;
+      double2 v = row[n];
+      v.x = fma(c, bD.x, v.x);
+      v.y = fma(c, bD.y, v.y);
+      row[n] = v;
+    }
+    bl[2] = bD;
+    bl[1] = tau_sweep_ct(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K),
+                         fac_ptr(g, 1, 1, K), fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
+    tau_sweep_ct(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
+                 fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
+  }
+  // phi: two Neumann solves with the same operator (implicit Euler: no wall-value term)
+  row = Rb + 2 * fs + (size_t)line * Nz;
+  for (int rep = 0; rep < 2; ++rep)
+    tau_sweep_ct(row, p, N, k2 + g.lam, true, t1, t2, t3, fac_ptr(g, 2, 0, K), fac_ptr(g, 2, 1, K),
+                 fac_ptr(g, 2, 2, K), g.NK, fac_rsq(g, 2, p, K));
+}
+
+// transpose of the forward DCT on lines [first, first+cnt): a = F x with F[n][j] =
+// scale_n w_j cos(pi n j / N)  ->  x_bar = w (.) C (scale (.) a_bar), C the backward transform
+__device__ void dct_forward_transpose_lines(const ZSmem& z, int first, int cnt, int Nz, int N,
+                                            const FftPlan& pz, const double2* cs) {
+  for (int idx = threadIdx.x; idx < cnt * Nz; idx += blockDim.x) {
+    const int f = idx / Nz, n = idx - f * Nz;
+    const double sc = (n == 0 || n == N) ? 0.5 / N : 1.0 / N;
+    LN(z, first + f, Nz)[n] = sc * LN(z, first + f, Nz)[n];
+  }
+  __syncthreads();
+  dct1_lines(z, first, cnt, Nz, N, pz, cs, 1);
+  for (int idx = threadIdx.x; idx < cnt * Nz; idx += blockDim.x) {
+    const int f = idx / Nz, j = idx - f * Nz;
+    if (j != 0 && j != N) LN(z, first + f, Nz)[j] = 2.0 * LN(z, first + f, Nz)[j];
+  }
+  __syncthreads();
+}
+
+// adjoint of zrhs (right-hand sides, AB2, assembly, forward DCT and combinations):
+// inputs Rb (rhs adjoints), L (new-state adjoint), mu (adjoint of h_n), state s_n;
+// outputs lam (adjoint of s_n, partial: update + rhs + phi in G), mu_prev (adjoint of h_{n-1}),
+// nlb (9 non-linear sample adjoints, fp64)
+__global__ void __launch_bounds__(ZT) adj_zrhs_kernel(GridDev g, const double2* __restrict__ Rb,
+                                                      const double2* __restrict__ L,
+                                                      const double2* __restrict__ mu,
+                                                      double2* __restrict__ lam,
+                                                      double2* __restrict__ mu_prev,
+                                                      double2* __restrict__ nlb, long long fs,
+                                                      int first, double nls,
+                                                      const double2* __restrict__ bb, FftPlan pz) {
+  extern __shared__ double2 zsm[];
+  const int Nz = g.nz, N = g.N;
+  const int line = blockIdx.x;
+  int mx, j;
+  double kx, ky;
+  line_wavenumbers(g, line, mx, j, kx, ky);
+  const size_t off = (size_t)line * Nz;
+  const int tid = threadIdx.x;
+  const double2 zero = make_double2(0.0, 0.0);
+  if (j == g.ny / 2) {
+    for (int n = tid; n < Nz; n += blockDim.x) {
+      for (int f = 0; f < 3; ++f) {
+        lam[f * fs + off + n] = zero;
+        mu_prev[f * fs + off + n] = zero;
+      }
+      for (int f = 0; f < 9; ++f) nlb[f * fs + off + n] = zero;
+    }
+    return;
+  }
+  const ZSmem z = carve(zsm, Nz, N);
+  const bool is00 = (mx == 0 && j == 0);
+  const double k2 = kx * kx + ky * ky;
+  const double a = first ? 1.0 : 1.5, b = first ? 0.0 : -0.5;
+  const double twoRe = 2.0 * g.re, cphi = g.pe / (g.ch * g.ch), rdt = 1.0 / g.dt, rpe = 1.0 / g.pe;
+  // lines: 10 hbar_om, 11 hbar_w, 12 hbar_phi, 13 -2 beta Rb_theta (for (D^2 - k^2)^T)
+  for (int n = tid; n < Nz; n += blockDim.x) {
+    const double2 ro = Rb[off + n], rt = Rb[fs + off + n], rp = Rb[2 * fs + off + n];
+    const double2 Ho = (-twoRe) * ro, Hw = (-twoRe) * rt, Hp = cphi * rp;
+    LN(z, 10, Nz)[n] = a * Ho + mu[off + n];
+    LN(z, 11, Nz)[n] = a * Hw + mu[fs + off + n];
+    LN(z, 12, Nz)[n] = a * Hp + mu[2 * fs + off + n];
+    mu_prev[off + n] = b * Ho;
+    mu_prev[fs + off + n] = b * Hw;
+    mu_prev[2 * fs + off + n] = b * Hp;
+    LN(z, 13, Nz)[n] = (-2.0 * g.beta) * rt;
+    // state adjoint from the update, the right-hand sides (D^2 part of w added below) and the
+    // wall values (bb, parity of n)
+    const double2* bl = bb + ((size_t)line * 2 + (n & 1)) * 3;
+    const double n2 = (double)n * (double)n;
+    lam[off + n] = (-1.0) * L[off + n] + (-2.0 * g.beta) * ro + bl[0];
+    lam[fs + off + n] = (-1.0) * L[fs + off + n] + (-k2) * LN(z, 13, Nz)[n] + bl[1] + n2 * bl[2];
+    lam[2 * fs + off + n] = (cphi * rdt) * rp;
+  }
+  __syncthreads();
+  // first derivatives transposed: D^T hbar_om -> 7 (Q), D^T hbar_w -> 8 (R), D^T hbar_phi -> 9
+  // (w phi), D^T line13 -> 14, and on (0,0) D^T of the real parts of hbar_om
+  if (is00) {
+    for (int n = tid; n < Nz; n += blockDim.x) {
+      const double2 h = LN(z, 10, Nz)[n];
+      LN(z, 0, Nz)[n] = make_double2(h.x, 0.0);
+      LN(z, 1, Nz)[n] = make_double2(h.y, 0.0);
+    }
+    __syncthreads();
+  }
+  {
+    double2* src[6] = {LN(z, 10, Nz), LN(z, 11, Nz), LN(z, 12, Nz), LN(z, 13, Nz), LN(z, 0, Nz),
+                       LN(z, 1, Nz)};
+    double2* dst[6] = {LN(z, 7, Nz), LN(z, 8, Nz), LN(z, 9, Nz), LN(z, 14, Nz), LN(z, 2, Nz),
+                       LN(z, 3, Nz)};
+    dzT_tasks(src, dst, is00 ? 6 : 4, N, z.tmp);
+  }
+  __syncthreads();
+  // second derivatives transposed: D^T(D^T hbar_w) -> 4, D^T(D^T hbar_phi) -> 5, D^T line14 -> 6
+  {
+    double2* src[3] = {LN(z, 8, Nz), LN(z, 9, Nz), LN(z, 14, Nz)};
+    double2* dst[3] = {LN(z, 4, Nz), LN(z, 5, Nz), LN(z, 6, Nz)};
+    dzT_tasks(src, dst, 3, N, z.tmp);
+  }
+  __syncthreads();
+  // coefficient adjoints of the seven transformed lines c0..c6 into lines 0..6
+  for (int n = tid; n < Nz; n += blockDim.x) {
+    const double2 ho = LN(z, 10, Nz)[n], hw = LN(z, 11, Nz)[n], hp = LN(z, 12, Nz)[n];
+    const double2 Gb = (-k2 * rpe) * hp + rpe * LN(z, 5, Nz)[n];      // G adjoint
+    lam[fs + off + n] = lam[fs + off + n] + LN(z, 6, Nz)[n];           // (D^2)^T part of theta
+    lam[2 * fs + off + n] = lam[2 * fs + off + n] - (1.0 + g.shat) * Gb;
+    double2 c0, c1, c2, c3;
+    if (is00) {
+      c0 = LN(z, 2, Nz)[n];             // D^T of Re(hbar_om.x): Sxz
+      c1 = LN(z, 3, Nz)[n];             // Syz
+      c2 = zero;
+      c3 = zero;
+    } else {
+      c0 = ho;                                          // P
+      c1 = LN(z, 7, Nz)[n];                             // Q: D^T hbar_om
+      c2 = (-k2) * hw - LN(z, 4, Nz)[n];                // C: -k^2 hbar_w - (D^2)^T hbar_w
+      c3 = (-1.0) * LN(z, 8, Nz)[n];                    // R: -D^T hbar_w
+    }
+    const double2 c4 = hp;                              // F
+    const double2 c5 = (-1.0) * LN(z, 9, Nz)[n];        // w phi: -D^T hbar_phi
+    LN(z, 0, Nz)[n] = c0;
+    LN(z, 1, Nz)[n] = c1;
+    LN(z, 2, Nz)[n] = c2;
+    LN(z, 3, Nz)[n] = c3;
+    LN(z, 4, Nz)[n] = c4;
+    LN(z, 5, Nz)[n] = c5;
+    LN(z, 6, Nz)[n] = Gb;                               // phi^3 line
+  }
+  __syncthreads();
+  for (int f0 = 0; f0 < 7; f0 += NBF)
+    dct_forward_transpose_lines(z, f0, (7 - f0 < NBF) ? 7 - f0 : NBF, Nz, N, pz, g.zcs);
+  // combinations transposed: samples of the nine non-linear fields
+  for (int n = tid; n < Nz; n += blockDim.x) {
+    const double2 c0 = LN(z, 0, Nz)[n], c1 = LN(z, 1, Nz)[n], c2 = LN(z, 2, Nz)[n];
+    const double2 c3 = LN(z, 3, Nz)[n], c4 = LN(z, 4, Nz)[n], c5 = LN(z, 5, Nz)[n];
+    const double2 c6 = LN(z, 6, Nz)[n];
+    double2 s[9];
+    for (int q = 0; q < 9; ++q) s[q] = zero;
+    if (is00) {
+      s[3] = c0;
+      s[4] = c1;
+    } else {
+      // P = i kx B - i ky A, R = i kx A + i ky B  ->  A, B adjoints
+      const double2 Ab = mul_i(ky * c0) + (-1.0) * mul_i(kx * c3);
+      const double2 Bb = (-1.0) * mul_i(kx * c0) + (-1.0) * mul_i(ky * c3);
+      s[0] = (-1.0) * mul_i(kx * Ab);                         // A = i kx s0 + i ky s2
+      s[2] = (-1.0) * mul_i(ky * Ab) + (-1.0) * mul_i(kx * Bb);
+      s[1] = (-1.0) * mul_i(ky * Bb);                         // B = i kx s2 + i ky s1
+      s[4] = (-1.0) * mul_i(kx * c1) + (-1.0) * mul_i(ky * c2);   // Q = i kx s4 - i ky s3
+      s[3] = mul_i(ky * c1) + (-1.0) * mul_i(kx * c2);            // C = i kx s3 + i ky s4
+      s[6] = mul_i(kx * c4);                                      // F = -(i kx s6 + i ky s7)
+      s[7] = mul_i(ky * c4);
+    }
+    s[8] = c5;
+    s[5] = c6;
+    // nls: the forward y pass's 1/(Px Py), moved here from the transposed (backward) y pass
+    for (int q = 0; q < 9; ++q) nlb[q * fs + off + n] = nls * s[q];
+  }
+}
+
+// adjoint of the backward fields of s_n (u, v, w, phi, D phi -> backward DCT): in = 5 sample
+// adjoint fields; adds the state adjoint into lam
+__global__ void __launch_bounds__(ZT) adj_zbwd_kernel(GridDev g, const double2* __restrict__ in5,
+                                                      long long fs_in, double2* __restrict__ lam,
+                                                      long long fs, FftPlan pz) {
+  extern __shared__ double2 zsm[];
+  const int Nz = g.nz, N = g.N;
+  const int line = blockIdx.x;
+  int mx, j;
+  double kx, ky;
+  line_wavenumbers(g, line, mx, j, kx, ky);
+  const size_t off = (size_t)line * Nz;
+  if (j == g.ny / 2) return;
+  const ZSmem z = carve(zsm, Nz, N);
+  const bool is00 = (mx == 0 && j == 0);
+  for (int idx = threadIdx.x; idx < 5 * Nz; idx += blockDim.x) {
+    const int f = idx / Nz, n = idx - f * Nz;
+    LN(z, f, Nz)[n] = in5[(long long)f * fs_in + off + n];
+  }
+  __syncthreads();
+  // the backward DCT matrix C[j][n] = cos(pi n j / N) is symmetric: its transpose is itself
+  dct1_lines(z, 0, 4, Nz, N, pz, g.zcs, 1);
+  dct1_lines(z, 4, 1, Nz, N, pz, g.zcs, 1);
+  const double k2 = kx * kx + ky * ky;
+  const double rk2 = is00 ? 0.0 : 1.0 / k2;
+  for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
+    const double2 ub = LN(z, 0, Nz)[n], vb = LN(z, 1, Nz)[n];
+    double2 omb, dwb;
+    if (is00) {
+      omb = make_double2(ub.x, vb.x);
+      dwb = make_double2(0.0, 0.0);
+    } else {
+      // u = (i kx Dw + i ky om)/k^2, v = (i ky Dw - i kx om)/k^2
+      omb = rk2 * ((-1.0) * mul_i(ky * ub) + mul_i(kx * vb));
+      dwb = rk2 * ((-1.0) * mul_i(kx * ub) + (-1.0) * mul_i(ky * vb));
+    }
+    LN(z, 10, Nz)[n] = omb;
+    LN(z, 11, Nz)[n] = dwb;
+  }
+  __syncthreads();
+  {
+    double2* src[2] = {LN(z, 11, Nz), LN(z, 4, Nz)};
+    double2* dst[2] = {LN(z, 12, Nz), LN(z, 13, Nz)};
+    dzT_tasks(src, dst, 2, N, z.tmp);
+  }
+  __syncthreads();
+  for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
+    lam[off + n] = lam[off + n] + LN(z, 10, Nz)[n];
+    lam[fs + off + n] = lam[fs + off + n] + LN(z, 2, Nz)[n] + LN(z, 12, Nz)[n];
+    lam[2 * fs + off + n] = lam[2 * fs + off + n] + LN(z, 3, Nz)[n] + LN(z, 13, Nz)[n];
+  }
+}
+
+// G a with G[n][m] = (q_{n+m} + q_{|n-m|}) / 2, q_k = 2/(1-k^2) (k even), 0 (k odd)
+__device__ __forceinline__ double gram_q(int k) { return (k & 1) ? 0.0 : 2.0 / (1.0 - (double)k * k); }
+
+// objective J = 1/2 int |u|^2 + int |grad phi|^2 (exact) per line: partial sums and gradient
+__global__ void __launch_bounds__(ZT) objective_kernel(GridDev g, const double2* __restrict__ st_om,
+                                                       const double2* __restrict__ st_w,
+                                                       const double2* __restrict__ st_phi,
+                                                       double2* __restrict__ lam, long long fs,
+                                                       double* __restrict__ part) {
+  extern __shared__ double2 zsm[];
+  const int Nz = g.nz, N = g.N;
+  const int line = blockIdx.x;
+  int mx, j;
+  double kx, ky;
+  line_wavenumbers(g, line, mx, j, kx, ky);
+  const size_t off = (size_t)line * Nz;
+  const ZSmem z = carve(zsm, Nz, N);
+  __shared__ double red[ZT];
+  const bool nyq = (j == g.ny / 2);
+  const bool is00 = (mx == 0 && j == 0);
+  const double k2 = kx * kx + ky * ky;
+  const double rk2 = is00 ? 0.0 : 1.0 / k2;
+  const double wts = (mx == 0 ? 1.0 : 2.0) * g.lx * g.ly;
+  for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
+    LN(z, 10, Nz)[n] = nyq ? make_double2(0.0, 0.0) : st_om[off + n];
+    LN(z, 11, Nz)[n] = nyq ? make_double2(0.0, 0.0) : st_w[off + n];
+    LN(z, 12, Nz)[n] = nyq ? make_double2(0.0, 0.0) : st_phi[off + n];
+  }
+  __syncthreads();
+  {
+    double2* src[2] = {LN(z, 11, Nz), LN(z, 12, Nz)};
+    double2* dst[2] = {LN(z, 13, Nz), LN(z, 14, Nz)};
+    dz_tasks(src, dst, 2, N, z.tmp);
+  }
+  __syncthreads();
+  // lines 0 u, 1 v, 2 w, 3 D phi (coefficients)
+  for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
+    const double2 om = LN(z, 10, Nz)[n], dw = LN(z, 13, Nz)[n];
+    double2 u, v;
+    if (is00) {
+      u = make_double2(om.x, 0.0);
+      v = make_double2(om.y, 0.0);
+    } else {
+      u = rk2 * mul_i(kx * dw + ky * om);
+      v = rk2 * mul_i(ky * dw - kx * om);
+    }
+    LN(z, 0, Nz)[n] = u;
+    LN(z, 1, Nz)[n] = v;
+    LN(z, 2, Nz)[n] = LN(z, 11, Nz)[n];
+    LN(z, 3, Nz)[n] = LN(z, 14, Nz)[n];
+  }
+  __syncthreads();
+  // G times lines 0..3 and phi (line 12) into lines 4..8; partial J
+  double jp = 0.0;
+  for (int idx = threadIdx.x; idx < 5 * Nz; idx += blockDim.x) {
+    const int f = idx / Nz, n = idx - f * Nz;
+    const double2* a = (f < 4) ? LN(z, f, Nz) : LN(z, 12, Nz);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int m = 0; m <= N; ++m) {
+      const double gnm = 0.5 * (gram_q(n + m) + gram_q(n > m ? n - m : m - n));
+      acc.x = fma(gnm, a[m].x, acc.x);
+      acc.y = fma(gnm, a[m].y, acc.y);
+    }
+    LN(z, 4 + f, Nz)[n] = acc;
+    const double2 an = a[n];
+    const double wq = (f < 3) ? 0.5 : (f == 3 ? 1.0 : k2);  // u v w: 1/2; D phi: 1; phi: k^2
+    jp += wq * (an.x * acc.x + an.y * acc.y);
+  }
+  red[threadIdx.x] = jp;
+  __syncthreads();
+  for (int s2 = ZT / 2; s2 > 0; s2 >>= 1) {
+    if (threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[line] = wts * red[0];
+  // gradient: d/da Re(a^H G a) = 2 G a
+  for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
+    const double2 ub = wts * LN(z, 4, Nz)[n], vb = wts * LN(z, 5, Nz)[n];
+    double2 omb, dwb;
+    if (is00) {
+      omb = make_double2(ub.x, vb.x);
+      dwb = make_double2(0.0, 0.0);
+    } else {
+      omb = rk2 * ((-1.0) * mul_i(ky * ub) + mul_i(kx * vb));
+      dwb = rk2 * ((-1.0) * mul_i(kx * ub) + (-1.0) * mul_i(ky * vb));
+    }
+    LN(z, 0, Nz)[n] = omb;
+    LN(z, 1, Nz)[n] = dwb;
+    LN(z, 2, Nz)[n] = (2.0 * wts) * LN(z, 7, Nz)[n];   // D phi adjoint
+  }
+  __syncthreads();
+  {
+    double2* src[2] = {LN(z, 1, Nz), LN(z, 2, Nz)};
+    double2* dst[2] = {LN(z, 9, Nz), LN(z, 13, Nz)};
+    dzT_tasks(src, dst, 2, N, z.tmp);
+  }
+  __syncthreads();
+  for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
+    if (nyq) {
+      lam[off + n] = make_double2(0.0, 0.0);
+      lam[fs + off + n] = make_double2(0.0, 0.0);
+      lam[2 * fs + off + n] = make_double2(0.0, 0.0);
+      continue;
+    }
+    lam[off + n] = LN(z, 0, Nz)[n];
+    lam[fs + off + n] = is00 ? make_double2(0.0, 0.0)
+                             : wts * LN(z, 6, Nz)[n] + LN(z, 9, Nz)[n];
+    lam[2 * fs + off + n] = (2.0 * wts * k2) * LN(z, 8, Nz)[n] + LN(z, 13, Nz)[n];
+  }
+}
+
+// adjoint of set_fields' projection and forward DCT: lam (3 state fields) -> four (Mx, Ny, Nz)
+// sample-adjoint fields of u, v, w, phi, scaled for the transposed x/y transforms that follow:
+// 1/(nx ny) (the forward normalisation) and 1/2 for kx >= 1 (a c2r then transposes the r2c)
+__global__ void __launch_bounds__(ZT) adj_project_kernel(GridDev g, const double2* __restrict__ lam,
+                                                         long long fs, double2* __restrict__ out4,
+                                                         FftPlan pz) {
+  extern __shared__ double2 zsm[];
+  const int Nz = g.nz, N = g.N;
+  const int line = blockIdx.x;
+  int mx, j;
+  double kx, ky;
+  line_wavenumbers(g, line, mx, j, kx, ky);
+  const size_t off = (size_t)line * Nz;
+  const ZSmem z = carve(zsm, Nz, N);
+  const bool nyq = (j == g.ny / 2);
+  const bool is00 = (mx == 0 && j == 0);
+  for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
+    const double2 ob = nyq ? make_double2(0.0, 0.0) : lam[off + n];
+    const double2 wb = (nyq || is00) ? make_double2(0.0, 0.0) : lam[fs + off + n];
+    const double2 pb = nyq ? make_double2(0.0, 0.0) : lam[2 * fs + off + n];
+    double2 ub, vb;
+    if (is00) {
+      ub = make_double2(ob.x, 0.0);
+      vb = make_double2(ob.y, 0.0);
+    } else {
+      ub = mul_i(ky * ob);              // om = i kx v - i ky u
+      vb = (-1.0) * mul_i(kx * ob);
+    }
+    if (nyq) {
+      ub = make_double2(0.0, 0.0);
+      vb = make_double2(0.0, 0.0);
+    }
+    LN(z, 0, Nz)[n] = ub;
+    LN(z, 1, Nz)[n] = vb;
+    LN(z, 2, Nz)[n] = wb;
+    LN(z, 3, Nz)[n] = pb;
+  }
+  __syncthreads();
+  dct_forward_transpose_lines(z, 0, 4, Nz, N, pz, g.zcs);
+  const double sc = (mx >= 1 ? 0.5 : 1.0) / ((double)g.nx * (double)g.ny);
+  for (int idx = threadIdx.x; idx < 4 * Nz; idx += blockDim.x) {
+    const int f = idx / Nz, n = idx - f * Nz;
+    out4[(long long)f * fs + off + n] = sc * LN(z, f, Nz)[n];
+  }
+}
+
+// transpose of the backward y pass's field map: field 3 (phi) += -i ky field 4 (i ky phi), then
+// field 4 <- field 5 (D phi), leaving u v w phi D phi adjoints in fields 0..4
+__global__ void fold_dy_kernel(GridDev g, double2* __restrict__ f6, long long fs) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)g.Mx * g.ny * g.nz;
+  if (i >= total) return;
+  const int j = (int)((i / g.nz) % g.ny);
+  const int my = (j < g.ny / 2) ? j : j - g.ny;
+  const double ky = 6.283185307179586476925 * my / g.ly;
+  const double2 d = f6[4 * fs + i];
+  f6[3 * fs + i] = f6[3 * fs + i] + (-1.0) * mul_i(ky * d);
+  f6[4 * fs + i] = f6[5 * fs + i];
+}
+
+// sum of n doubles in a fixed order (one CTA of 256 threads)
+__global__ void __launch_bounds__(256) sum_kernel(const double* __restrict__ a, int n,
+                                                  double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) acc += a[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s2 = 128; s2 > 0; s2 >>= 1) {
+    if (threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
 // ---- grouped persistent launches (ensemble) ---------------------------------------------
 __device__ __forceinline__ int member_of(const int* __restrict__ begin, int nmem, int item) {
   int m = 0;
@@ -1060,6 +1672,68 @@ int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile) {
                                                                 : (const void*)grouped_zbwd_kernel<float>, ZT, smem);
   cudaGetLastError();
   return n;
+}
+
+cudaError_t launch_adj_zsolve(const GridDev& g, const double2* L, double2* Rb, long long fs,
+                              double2* bb, cudaStream_t s) {
+  const int nlines = g.Mx * g.ny;
+  adj_zsolve_kernel<<<(2 * nlines + ST - 1) / ST, ST, 0, s>>>(g, L, Rb, fs, nlines, bb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_zrhs(const GridDev& g, const double2* Rb, const double2* L,
+                            const double2* mu, double2* lam, double2* mu_prev, double2* nlb,
+                            long long fs, int first, const double2* bb, const FftPlan& pz,
+                            cudaStream_t s) {
+  const size_t smem = zline_smem(g);
+  static int cur = 0;
+  cudaError_t e = ensure_smem(adj_zrhs_kernel, smem, &cur);
+  if (e != cudaSuccess) return e;
+  adj_zrhs_kernel<<<g.Mx * g.ny, ZT, smem, s>>>(g, Rb, L, mu, lam, mu_prev, nlb, fs, first,
+                                                 1.0 / ((double)g.Px * (double)g.Py), bb, pz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_zbwd(const GridDev& g, const double2* in5, long long fs_in, double2* lam,
+                            long long fs, const FftPlan& pz, cudaStream_t s) {
+  const size_t smem = zline_smem(g);
+  static int cur = 0;
+  cudaError_t e = ensure_smem(adj_zbwd_kernel, smem, &cur);
+  if (e != cudaSuccess) return e;
+  adj_zbwd_kernel<<<g.Mx * g.ny, ZT, smem, s>>>(g, in5, fs_in, lam, fs, pz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const GridDev& g, const double2* om, const double2* w,
+                             const double2* phi, double2* lam, long long fs, double* part,
+                             cudaStream_t s) {
+  const size_t smem = zline_smem(g);
+  static int cur = 0;
+  cudaError_t e = ensure_smem(objective_kernel, smem, &cur);
+  if (e != cudaSuccess) return e;
+  objective_kernel<<<g.Mx * g.ny, ZT, smem, s>>>(g, om, w, phi, lam, fs, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_project(const GridDev& g, const double2* lam, long long fs, double2* out4,
+                               const FftPlan& pz, cudaStream_t s) {
+  const size_t smem = zline_smem(g);
+  static int cur = 0;
+  cudaError_t e = ensure_smem(adj_project_kernel, smem, &cur);
+  if (e != cudaSuccess) return e;
+  adj_project_kernel<<<g.Mx * g.ny, ZT, smem, s>>>(g, lam, fs, out4, pz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum(const double* a, int n, double* out, cudaStream_t s) {
+  sum_kernel<<<1, 256, 0, s>>>(a, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_dy(const GridDev& g, double2* f6, long long fs, cudaStream_t s) {
+  const long long total = (long long)g.Mx * g.ny * g.nz;
+  fold_dy_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, f6, fs);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_zsolve(const GridDev& g, double2* R, long long fs, cudaStream_t s) {
