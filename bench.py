@@ -61,8 +61,10 @@ def kernel_work(w, prec):
     S = Mx * ny * nz           # spectral points per field
     Y = Mx * Py * nz           # y-padded points per field
     lines = Mx * ny
-    # complex DCT-I of a line = complex FFT of 2N points; a derivative = 4 flops per coefficient
-    dct = fft_flops(2 * N)
+    # complex DCT-I of a line: 5 N log2 N (an N-point complex FFT per complex line, the count of
+    # the scope table; the paper's 2N-point even extension would be twice that); a derivative =
+    # 4 flops per coefficient
+    dct = fft_flops(N)
     # zrhs: 9 non-linear fields in, combined to 7 lines, 7 DCTs, 9 derivatives, assembly
     zrhs_fl = lines * (7 * dct + 9 * 4 * nz + 150 * nz)
     zrhs_by = S * (b * 9 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)   # NL, state, hist in/out, R out
@@ -79,6 +81,112 @@ def kernel_work(w, prec):
     return {"zrhs": (zrhs_fl, zrhs_by), "zsolve": (zsolve_fl, zsolve_by),
             "zbwd": (zbwd_fl, zbwd_by), "ybwd": (yb_fl, yb_by), "xline": (x_fl, x_by),
             "yfwd": (yf_fl, yf_by)}
+
+
+def cufft_transforms_ms(w, prec, reps=5, warmup=2, dev="cuda"):
+    """Timed comparison only: the transforms of one step done with cuFFT through torch.fft, as a
+    library user would write them (zero padding / truncation by copies, layouts as stored):
+    12 Chebyshev DCT-I (5 backward + 7 forward, each a 2N-point FFT of the even extension),
+    6 y inverse FFTs and 9 y forward FFTs of length Py, 7 x c2r and 9 x r2c of length Px.
+    The products, assembly and solves are not included.  Returns (z ms, x-y ms) per step."""
+    import torch
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    Mx, Px, Py, N = nx // 2, 3 * nx // 2, 3 * ny // 2, nz - 1
+    h = ny // 2
+    cd = torch.complex128 if prec == 0 else torch.complex64
+    rd = torch.float64 if prec == 0 else torch.float32
+    spec = torch.randn(12, Mx, ny, nz, dtype=torch.complex128, device=dev)
+    ymod = torch.randn(6, Mx, ny, nz, dtype=cd, device=dev)
+    prod = torch.randn(9, Px, Py, nz, dtype=rd, device=dev)
+
+    def zpart():
+        ext = torch.cat([spec, spec.flip(-1)[..., 1:-1]], dim=-1)      # even extension, 2N
+        return torch.fft.fft(ext, dim=-1)
+
+    def xypart():
+        pad = torch.zeros(6, Mx, Py, nz, dtype=cd, device=dev)
+        pad[:, :, :h] = ymod[:, :, :h]
+        pad[:, :, Py - h + 1:] = ymod[:, :, h + 1:]
+        yb = torch.fft.ifft(pad, dim=2)
+        xin = torch.cat([yb, yb[3:4]], dim=0)                          # 7 fields (phi_x from phi)
+        phys = torch.fft.irfft(xin, n=Px, dim=1)                       # (7, Px, Py, nz)
+        xf = torch.fft.rfft(prod, dim=1)[:, :Mx]                       # (9, Mx, Py, nz)
+        yf = torch.fft.fft(xf, dim=2)
+        out = torch.cat([yf[:, :, :h], yf[:, :, Py - h:]], dim=2)
+        return phys, out
+
+    res = []
+    for fn in (zpart, xypart):
+        for _ in range(warmup):
+            fn()
+        if dev == "cpu":                 # shape check of the comparison (no timing meaning)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            res.append((time.perf_counter() - t0) * 1e3 / reps)
+            continue
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        res.append(a.elapsed_time(b) / reps)
+    del spec, ymod, prod
+    if dev != "cpu":
+        torch.cuda.empty_cache()
+    return res[0], res[1]
+
+
+def mixed_accuracy(binding, w, fields, steps, device):
+    """Mixed-precision step against the FP64 step from the same fields after `steps` steps:
+    per-field max relative difference (max |a - b| / max |b|), phi mass drift of each path
+    relative to the initial mass, and relative differences of kinetic energy, int |grad phi|^2
+    and free energy."""
+    import torch
+    kw = dict(re_tau=w["re_tau"], we=w["we"], ch=w["ch"], pe=w["pe"], dt=w["dt"])
+    out = {}
+    res = {}
+    for prec in (0, 1):
+        g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=prec, device=device, **kw)
+        g.set_fields(*[torch.from_numpy(f) for f in fields])
+        m0 = g.diagnostics()["mass"]
+        g.step(steps)
+        d = g.diagnostics()
+        res[prec] = ([f.cpu() for f in g.get_fields()], d, m0)
+        g.close()
+        torch.cuda.empty_cache()
+    (f64, d64, m64), (f32, d32, m32) = res[0], res[1]
+    out["rel_err"] = {n: float((a - b).abs().max() / b.abs().max())
+                      for n, a, b in zip(("u", "v", "w", "phi"), f32, f64)}
+    out["mass_drift_fp64"] = (d64["mass"] - m64) / abs(m64)
+    out["mass_drift_mixed"] = (d32["mass"] - m32) / abs(m32)
+    for k in ("kinetic", "grad2", "free_energy"):
+        out[k + "_rel_diff"] = (d32[k] - d64[k]) / abs(d64[k])
+    out["steps"] = steps
+    return out
+
+
+def adjoint_work(w):
+    """Algorithmic flops and bytes per launch of the reverse step's kernels (FP64)."""
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    Mx, Px, Py, N = nx // 2, 3 * nx // 2, 3 * ny // 2, nz - 1
+    S, Y, lines = Mx * ny * nz, Mx * Py * nz, Mx * ny
+    dct = fft_flops(N)
+    f = kernel_work(w, 0)
+    return {
+        "zbwd": (lines * (5 * dct + 2 * 4 * nz + 40 * nz), S * 16 * (3 + 5)),
+        "ybwd": f["ybwd"],
+        "adj_zsolve": (lines * nz * (5 * 30 + 12), S * 16 * 3 * 3),
+        "adj_zrhs": (lines * (7 * dct + 7 * 4 * nz + 150 * nz), S * 16 * (3 + 3 + 3 + 3 + 3 + 9)),
+        "adj_ybwd": (9 * Mx * nz * fft_flops(Py), 9 * (S + Y) * 16),
+        "adj_xline": (Py * nz * (23 * 0.5 * fft_flops(Px) + 60 * Px), (6 + 9 + 6) * Y * 16),
+        "adj_yfwd": (6 * Mx * nz * fft_flops(Py), 6 * (S + Y) * 16),
+        "fold_dy": (8 * S, 4 * S * 16),
+        "adj_zbwd": (lines * (5 * dct + 2 * 4 * nz + 30 * nz), S * 16 * (5 + 3 + 3)),
+    }
 
 
 class ClockSampler:
@@ -142,6 +250,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device):
+    """Largest x over the ranks of the default process group (x itself when world == 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(points, steps, world, seconds):
+    """Whole-job Mpoints*step/s of `world` independent replicas, each advancing `points` for
+    `steps` steps, timed by the slowest rank (`seconds`)."""
+    return world * points * steps / seconds / 1e6
+
+
 def oracle_sample(w, nsample_lines=None, steps=1):
     """Time the CPU oracle on one step of the workload: the full non-linear evaluation plus the
     implicit solves of a sample of wavenumber lines, scaled to all lines."""
@@ -176,15 +301,67 @@ def oracle_sample(w, nsample_lines=None, steps=1):
     return pts * steps / total / 1e6, total / steps, len(sample), len(lines)
 
 
+def oracle_step_sample(c, nplanes, nlines, rng):
+    """One oracle step on a bounded sample, timed per part and scaled to the whole step.
+
+    Non-linear terms: the oracle's own nonlinear_spectral on a copy of the channel whose
+    Chebyshev transform matrices keep `nplanes` random z-planes (rows of the backward matrix,
+    columns of the forward one), so the x-y transforms and products run on those planes only;
+    the parts that do not shrink with the planes (velocity recovery, d/dz) are timed on their own
+    and not scaled.  Assembly and right-hand sides: all lines.  Implicit solves: `nlines` random
+    lines, scaled to all lines.  Returns the estimated seconds of one full oracle step."""
+    import copy
+    import numpy as np
+    Nz = c.p.nz
+    planes = np.sort(rng.choice(Nz, size=min(nplanes, Nz), replace=False))
+    s = copy.copy(c)
+    s.Bm = c.Bm[planes]
+    s.Fm = c.Fm[:, planes]
+    t0 = time.perf_counter()
+    uh, vh, wh = c.velocity_spectral()
+    c.dz(c.phi)
+    t1 = time.perf_counter()
+    s.nonlinear_spectral()
+    t2 = time.perf_counter()
+    nl = [np.zeros_like(c.phi) for _ in range(10)]     # shapes only: the values are not used
+    h = c.assemble(nl)
+    prev = h if c.hist is None else c.hist
+    H = tuple(1.5 * a - 0.5 * b for a, b in zip(h, prev))
+    r = c.rhs(H)
+    t3 = time.perf_counter()
+    lines = c.all_lines()
+    idx = rng.choice(len(lines), size=min(nlines, len(lines)), replace=False)
+    for i in idx:
+        j, m = lines[i]
+        c.solve_line(j, m, r[0][:, j, m], r[1][:, j, m], r[2][:, j, m])
+    t4 = time.perf_counter()
+    fixed = t1 - t0
+    nl_scaled = fixed + max(t2 - t1 - fixed, 0.0) * Nz / len(planes)
+    return nl_scaled + (t3 - t2) + (t4 - t3) * len(lines) / len(idx)
+
+
 def run_reference(args, w):
+    """The CPU oracle (the reference arm) on the machine's host cores: each timed step is one oracle
+    step on a bounded sample (oracle_step_sample), so K steps stay within minutes."""
+    import numpy as np
+    from oracle.channel import Channel, Params
+    from paper_2406_01322_gb300 import inputs
     rank, world, _ = dist_env()
     if rank != 0:
         return
     cores = os.cpu_count()
-    nsample = max(64, (w["nx"] // 2) * w["ny"] // 64)
-    if args.warmup:
-        oracle_sample(w, nsample_lines=8, steps=1)
-    val, t_step, ns, nl = oracle_sample(w, nsample_lines=nsample, steps=max(1, args.steps))
+    p = Params(nx=w["nx"], ny=w["ny"], nz=w["nz"], re_tau=w["re_tau"], we=w["we"], ch=w["ch"],
+               pe=w["pe"], dt=w["dt"])
+    c = Channel(p)
+    c.set_fields(*inputs.initial_fields(**w))
+    rng = np.random.default_rng(0)
+    nplanes, nlines = 4, 32
+    for _ in range(args.warmup):
+        oracle_step_sample(c, nplanes, nlines, rng)
+    total = sum(oracle_step_sample(c, nplanes, nlines, rng) for _ in range(args.steps))
+    pts = w["nx"] * w["ny"] * w["nz"]
+    t_step = total / max(1, args.steps)
+    val = pts / t_step / 1e6
     out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -192,9 +369,10 @@ def run_reference(args, w):
            "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]],
                       "precision": "fp64"},
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"full non-linear evaluation + implicit solves of {ns} of "
-                                      f"{nl} wavenumber lines per step, solve time scaled to "
-                                      f"all lines; numpy FP64 oracle, {args.steps} step(s)"},
+                            "sample": f"per step: the oracle's non-linear evaluation on "
+                                      f"{nplanes} of {w['nz']} z-planes (scaled), assembly and "
+                                      f"right-hand sides of all lines, implicit solves of "
+                                      f"{nlines} lines (scaled to all); numpy FP64 oracle"},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -244,20 +422,130 @@ def run_ensemble(args):
     print(json.dumps(out))
 
 
+def run_adjoint(args):
+    """Gradient of J = 1/2 int |u|^2 + int |grad phi|^2 after the workload's steps with respect to
+    the initial fields: forward run with checkpoints every 10 steps, then segment recomputation
+    and the reverse sweep (torch.autograd through the library's adjoint kernels).  A bench step
+    is one gradient; value = points x differentiated steps x gradients / device time."""
+    import torch
+    from paper_2406_01322_gb300 import binding, build, inputs
+    build.build_library()
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    w = dict(inputs.WORKLOADS[args.workload])
+    nsteps = w["steps"]
+    fields = inputs.initial_fields(**dict(w, seed=w["seed"] + rank))
+    kw = dict(re_tau=w["re_tau"], we=w["we"], ch=w["ch"], pe=w["pe"], dt=w["dt"])
+    g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=0, device=f"cuda:{local}", **kw)
+    dev = [torch.from_numpy(f).cuda() for f in fields]
+
+    def gradient(ts):
+        ts = [t.detach().requires_grad_(True) for t in ts]
+        J = binding.objective_after(g, *ts, nsteps, checkpoint_every=10)
+        J.backward()
+        return J, [t.grad for t in ts]
+
+    for _ in range(args.warmup):
+        gradient(dev)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            gradient(dev)
+        e1.record()
+        torch.cuda.synchronize()
+    tot_ms = e0.elapsed_time(e1)
+    pts = w["nx"] * w["ny"] * w["nz"]
+    value = pts * nsteps * args.steps / (tot_ms * 1e-3) / 1e6
+    # forward-only reference on the same grid: nsteps plain steps
+    g.set_fields(*dev)
+    e0.record()
+    g.step(nsteps)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    # e2e: pinned host fields in, gradients out to pinned host memory, per gradient
+    host = [torch.from_numpy(f).pin_memory() for f in fields]
+    outs = [torch.empty_like(h).pin_memory() for h in host]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ts = [h.to("cuda", non_blocking=True) for h in host]
+        _, gr = gradient(ts)
+        for o, a in zip(outs, gr):
+            o.copy_(a, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    # per-kernel times of one instrumented reverse sweep (states recomputed and saved first)
+    g.set_fields(*dev)
+    states = []
+    for _ in range(nsteps):
+        states.append(g.get_state())
+        g.step(1)
+    g.adjoint_begin()
+    kms = [0.0] * len(binding.Grid.ADJ_KERNELS)
+    for st in reversed(states):
+        for i, v in enumerate(g.adjoint_step_timed(st)):
+            kms[i] += v
+    g.adjoint_end()
+    names = list(binding.Grid.ADJ_KERNELS)
+    work = adjoint_work(w)
+    k = max(range(len(names)), key=lambda i: kms[i])
+    per_launch_ms = kms[k] / nsteps
+    fl, by = work[names[k]]
+    ach = fl / (per_launch_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": names[k],
+            "peak_kind": "float64 FMA pipe: 152 SMs x 2.07 GHz x 4 flop/clk (nominal)",
+            "kernel_share": {n: kms[i] / sum(kms) for i, n in enumerate(names)},
+            "kernel_ms_per_reverse_step": {n: kms[i] / nsteps for i, n in enumerate(names)}}
+    nbytes = 4 * pts * 8
+    # launches of this library per gradient: set_fields 10 (4 x r2c, y pass, projection, four
+    # for the products), 6 per forward step, objective 2, restore of the final state 4,
+    # adjoint seed 2, per segment a restore (4) and 6 per recomputed step, 9 per reverse step,
+    # gradient 6 (projection transpose, y pass, 4 x c2r)
+    nseg = -(-nsteps // 10)
+    launches = 10 + 6 * nsteps + 2 + 4 + 2 + 4 * nseg + 6 * (nsteps - nseg) + 9 * nsteps + 6
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]],
+                      "differentiated_steps": nsteps, "checkpoint_every": 10,
+                      "precision": "fp64", "l2": "working set larger than L2 (no flush)",
+                      "step": "one gradient: forward with checkpoints, recomputation, reverse"},
+           "forward_only_ms": fwd_ms, "gradient_over_forward": (tot_ms / args.steps) / fwd_ms,
+           "e2e": {"value": pts * nsteps * args.steps / e2e_s / 1e6, "unit": UNIT,
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+           "gpu_launches": launches * args.steps, "roofline": roof, "clocks": clk.summary()}
+    g.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 100; adjoint workload: gradients, default 5)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="channel_128x128x129")
     ap.add_argument("--precision", type=int, default=None, help="0 fp64, 1 mixed")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the mixed-vs-FP64 comparison of mixed-precision workloads")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 5 if args.workload == "channel_128x128x129_adjoint" else 100
 
     from paper_2406_01322_gb300 import inputs
     if args.workload == "ensemble_32_uneven":
         run_ensemble(args)
+        return
+    if args.workload == "channel_128x128x129_adjoint" and args.impl == "native":
+        run_adjoint(args)
         return
     w = dict(inputs.WORKLOADS[args.workload])
     prec = w["precision"] if args.precision is None else args.precision
@@ -295,12 +583,9 @@ def main():
     with ClockSampler(local) as clk:
         tot_ms, kms = g.step_timed(args.steps)
     barrier()
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(tot_ms, world, "cuda")
     pts = w["nx"] * w["ny"] * w["nz"]
-    value = world * pts * args.steps / (tot_ms * 1e-3) / 1e6
+    value = replica_throughput(pts, args.steps, world, tot_ms * 1e-3)
     ms_step = tot_ms / args.steps
 
     # ---- e2e through the C ABI with host buffers
@@ -312,12 +597,8 @@ def main():
     g.step(args.steps)
     g.get_fields_host(outs)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = world * pts * args.steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e_val = replica_throughput(pts, args.steps, world, e2e_s)
     nbytes = 4 * pts * 8
 
     # ---- roofline of the dominant kernel
@@ -363,6 +644,17 @@ def main():
            "roofline": roof,
            "clocks": clk.summary()}
     g.close()
+    if world == 1 and prec == 1 and not args.no_accuracy:
+        out["mixed_vs_fp64"] = mixed_accuracy(binding, w, fields, w["steps"], f"cuda:{local}")
+    if world == 1:
+        zc, xyc = cufft_transforms_ms(w, prec)
+        ours_xy = sum(roof["kernel_ms_per_step"][n] for n in ("ybwd", "xline", "yfwd"))
+        out["cufft_comparison"] = {
+            "cufft_z_dct_ms_per_step": zc, "cufft_xy_ms_per_step": xyc,
+            "cufft_transforms_ms_per_step": zc + xyc,
+            "ours_step_ms": ms_step, "ours_ybwd_xline_yfwd_ms": ours_xy,
+            "note": "cuFFT (torch.fft) timed on the transforms of one step only (no products, "
+                    "assembly or solves); ours_ybwd_xline_yfwd_ms also includes the products"}
     if world == 1 and not args.no_cpu_baseline:
         nsample = max(64, (w["nx"] // 2) * w["ny"] // 64)
         val, t_step, ns, nl = oracle_sample(w, nsample_lines=nsample, steps=1)

@@ -185,6 +185,12 @@ int ch_nonlinear(ch_grid* g, double* out9);
 int ch_objective(ch_grid* g, double* J);
 int ch_adjoint_begin(ch_grid* g, double* J);
 int ch_adjoint_step(ch_grid* g, const void* state);
+/* as ch_adjoint_step with events around its launches (synchronises the stream):
+ * kernel_ms[0..CH_ADJ_KERNELS-1] = field recomputation (z backward, y backward), transposed
+ * tau solves, transposed right-hand sides, transposed y forward pass, transposed x line,
+ * transposed y backward pass, i ky fold, transposed z backward. */
+#define CH_ADJ_KERNELS 9
+int ch_adjoint_step_timed(ch_grid* g, const void* state, double* kernel_ms);
 int ch_adjoint_gradient(ch_grid* g, double* gu, double* gv, double* gw, double* gphi);
 int ch_adjoint_end(ch_grid* g);
 

@@ -75,6 +75,7 @@ _SIGS = {
     "ch_objective": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "ch_adjoint_begin": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "ch_adjoint_step": (ctypes.c_int, [_P, _P]),
+    "ch_adjoint_step_timed": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
     "ch_adjoint_gradient": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "ch_adjoint_end": (ctypes.c_int, [_P]),
     "ch_ensemble_init": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, ALLOC_FN, FREE_FN,
@@ -320,6 +321,16 @@ class Grid:
     def adjoint_step(self, state):
         """Reverse the forward step that started from `state` (a get_state() buffer)."""
         _ck("ch_adjoint_step", lib().ch_adjoint_step(self.h, _ptr(state)))
+
+    ADJ_KERNELS = ("zbwd", "ybwd", "adj_zsolve", "adj_zrhs", "adj_ybwd", "adj_xline",
+                   "adj_yfwd", "fold_dy", "adj_zbwd")
+
+    def adjoint_step_timed(self, state):
+        """adjoint_step with CUDA events between its launches; returns per-kernel ms in the
+        order of Grid.ADJ_KERNELS (synchronises the stream)."""
+        ks = (ctypes.c_double * len(self.ADJ_KERNELS))()
+        _ck("ch_adjoint_step_timed", lib().ch_adjoint_step_timed(self.h, _ptr(state), ks))
+        return list(ks)
 
     def adjoint_gradient(self):
         """dJ/d(u0, v0, w0, phi0) after the first forward step was reversed."""

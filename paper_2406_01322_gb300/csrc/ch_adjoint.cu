@@ -107,7 +107,13 @@ int ch_adjoint_begin(ch_grid* G, double* J) {
   return CH_OK;
 }
 
-int ch_adjoint_step(ch_grid* G, const void* state) {
+}  // extern "C"
+
+namespace {
+
+// one reverse step; ev (optional) holds CH_ADJ_KERNELS + 1 events: ev[0] before the first launch,
+// ev[k + 1] after launch k
+int adjoint_step_impl(ch_grid* G, const void* state, cudaEvent_t* ev) {
   if (!G || !state) return CH_ERR_ARG;
   if (!G->adj_block) return CH_ERR_STATE;
   const GridDev& g = G->g;
@@ -127,20 +133,37 @@ int ch_adjoint_step(ch_grid* G, const void* state) {
   G->nstep = h.nstep;
   G->t = h.t;
   G->nl_stale = 1;
-  // forward fields of s_n on the y-padded grid (the x line's linearisation point)
   const chf::YMap ym = chf::step_ymap();
-  CK(chf::launch_zbwd(0, 0, kBw, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s));
-  CK(chf::launch_ypass(1, 0, g, g.Py, G->bw, G->ya, kYa, G->fs, G->fsy, 1.0, G->py[0], s, &ym));
+  cudaError_t e[CH_ADJ_KERNELS];
+  if (ev) cudaEventRecord(ev[0], s);
+  // forward fields of s_n on the y-padded grid (the x line's linearisation point)
+  e[0] = chf::launch_zbwd(0, 0, kBw, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  e[1] = chf::launch_ypass(1, 0, g, g.Py, G->bw, G->ya, kYa, G->fs, G->fsy, 1.0, G->py[0], s,
+                           &ym);
+  if (ev) cudaEventRecord(ev[2], s);
   // reverse step
-  CK(chf::launch_adj_zsolve(g, G->a_L, G->a_Rb, G->fs, G->a_bb, s));
-  CK(chf::launch_adj_zrhs(g, G->a_Rb, G->a_L, G->a_mu, G->a_lam, G->a_mu2, G->a_nlb, G->fs,
-                          h.first, G->a_bb, G->pz, s));
-  CK(chf::launch_ypass(1, 0, g, g.Py, G->a_nlb, G->yb, kNl, G->fs, G->fsy, 1.0, G->py[0], s));
-  CK(chf::launch_adj_xline(g, (const double2*)G->ya, (const double2*)G->yb, G->a_x6, G->fsy,
-                           G->px[0], s));
-  CK(chf::launch_ypass(0, 0, g, g.Py, G->a_x6, G->auxA, kYa, G->fsy, G->fs, 1.0, G->py[0], s));
-  CK(chf::launch_fold_dy(g, G->auxA, G->fs, s));
-  CK(chf::launch_adj_zbwd(g, G->auxA, G->fs, G->a_lam, G->fs, G->pz, s));
+  e[2] = chf::launch_adj_zsolve(g, G->a_L, G->a_Rb, G->fs, G->a_bb, s);
+  if (ev) cudaEventRecord(ev[3], s);
+  e[3] = chf::launch_adj_zrhs(g, G->a_Rb, G->a_L, G->a_mu, G->a_lam, G->a_mu2, G->a_nlb, G->fs,
+                              h.first, G->a_bb, G->pz, s);
+  if (ev) cudaEventRecord(ev[4], s);
+  e[4] = chf::launch_ypass(1, 0, g, g.Py, G->a_nlb, G->yb, kNl, G->fs, G->fsy, 1.0, G->py[0], s);
+  if (ev) cudaEventRecord(ev[5], s);
+  e[5] = chf::launch_adj_xline(g, (const double2*)G->ya, (const double2*)G->yb, G->a_x6, G->fsy,
+                               G->px[0], s);
+  if (ev) cudaEventRecord(ev[6], s);
+  e[6] = chf::launch_ypass(0, 0, g, g.Py, G->a_x6, G->auxA, kYa, G->fsy, G->fs, 1.0, G->py[0], s);
+  if (ev) cudaEventRecord(ev[7], s);
+  e[7] = chf::launch_fold_dy(g, G->auxA, G->fs, s);
+  if (ev) cudaEventRecord(ev[8], s);
+  e[8] = chf::launch_adj_zbwd(g, G->auxA, G->fs, G->a_lam, G->fs, G->pz, s);
+  if (ev) cudaEventRecord(ev[9], s);
+  for (int k = 0; k < CH_ADJ_KERNELS; ++k)
+    if (e[k] != cudaSuccess) {
+      cudaGetLastError();
+      return CH_ERR_CUDA;
+    }
   double2* t = G->a_L;
   G->a_L = G->a_lam;
   G->a_lam = t;
@@ -148,6 +171,33 @@ int ch_adjoint_step(ch_grid* G, const void* state) {
   G->a_mu = G->a_mu2;
   G->a_mu2 = t;
   return CH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ch_adjoint_step(ch_grid* G, const void* state) { return adjoint_step_impl(G, state, nullptr); }
+
+int ch_adjoint_step_timed(ch_grid* G, const void* state, double* kernel_ms) {
+  if (!kernel_ms) return CH_ERR_ARG;
+  cudaEvent_t ev[CH_ADJ_KERNELS + 1];
+  for (int i = 0; i <= CH_ADJ_KERNELS; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaEventDestroy(ev[k]);
+      cudaGetLastError();
+      return CH_ERR_CUDA;
+    }
+  int st = adjoint_step_impl(G, state, ev);
+  if (st == CH_OK && cudaEventSynchronize(ev[CH_ADJ_KERNELS]) != cudaSuccess) st = CH_ERR_CUDA;
+  for (int k = 0; k < CH_ADJ_KERNELS && st == CH_OK; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) st = CH_ERR_CUDA;
+    kernel_ms[k] = ms;
+  }
+  for (int i = 0; i <= CH_ADJ_KERNELS; ++i) cudaEventDestroy(ev[i]);
+  if (st == CH_ERR_CUDA) cudaGetLastError();
+  return st;
 }
 
 int ch_adjoint_gradient(ch_grid* G, double* gu, double* gv, double* gw, double* gphi) {

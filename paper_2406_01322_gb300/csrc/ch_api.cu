@@ -1,12 +1,15 @@
 // C-ABI of the channel solver (declared in include/ch_flow.h): validation, plans, twiddle
 // tables, internal buffers, the per-step launch schedule and its CUDA-graph replay.
 //
-// One time step (paper Sec. 2.2, steps i)-v)) is four launches on the handle's stream:
-//   zline (mode 0)  : Chebyshev DCT of the 10 non-linear fields, assembly, AB2/CN/IE, tau
-//                     solves, state update, backward DCT of the 7 fields the next products need;
-//   ypass backward  : 7 fields, ky -> y with 3/2 zero padding;
-//   xline           : 7 fields kx -> x (padded), 10 products, x -> kx (truncated);
-//   ypass forward   : 10 fields, y -> ky, truncation and the 1/(Px Py) normalisation.
+// One time step (paper Sec. 2.2, steps i)-v)) is six launches on the handle's stream:
+//   zrhs    : Chebyshev DCT-I of the nine non-linear fields (as seven combinations), assembly,
+//             AB2 / CN / IE right-hand sides;
+//   zsolve  : the Chebyshev-tau solves of every wavenumber line;
+//   zbwd    : state update, velocity from continuity, backward DCT-I of the five fields the next
+//             products need;
+//   ybwd    : ky -> y with 3/2 zero padding (i ky phi formed here: six fields);
+//   xline   : kx -> x (padded), the nine products, x -> kx (truncated);
+//   yfwd    : y -> ky, truncation and the 1/(Px Py) normalisation.
 // The non-linear buffer therefore always holds the products of the current state.
 #include <math.h>
 #include <stdint.h>

@@ -1380,14 +1380,18 @@ __global__ void __launch_bounds__(ZT) objective_kernel(GridDev g, const double2*
     LN(z, 3, Nz)[n] = LN(z, 14, Nz)[n];
   }
   __syncthreads();
-  // G times lines 0..3 and phi (line 12) into lines 4..8; partial J
+  // G times lines 0..3 and phi (line 12) into lines 4..8; partial J.  q_k (k = 0..2N) is
+  // tabulated in line 15 (2 Nz >= 2N + 1 doubles)
   double jp = 0.0;
+  double* qt = reinterpret_cast<double*>(LN(z, 15, Nz));
+  for (int k = threadIdx.x; k <= 2 * N; k += blockDim.x) qt[k] = gram_q(k);
+  __syncthreads();
   for (int idx = threadIdx.x; idx < 5 * Nz; idx += blockDim.x) {
     const int f = idx / Nz, n = idx - f * Nz;
     const double2* a = (f < 4) ? LN(z, f, Nz) : LN(z, 12, Nz);
     double2 acc = make_double2(0.0, 0.0);
     for (int m = 0; m <= N; ++m) {
-      const double gnm = 0.5 * (gram_q(n + m) + gram_q(n > m ? n - m : m - n));
+      const double gnm = 0.5 * (qt[n + m] + qt[n > m ? n - m : m - n]);
       acc.x = fma(gnm, a[m].x, acc.x);
       acc.y = fma(gnm, a[m].y, acc.y);
     }
