@@ -57,7 +57,7 @@ def kernel_work(w, prec):
     """Algorithmic flops (an FMA counts 2) and bytes per launch of the six step kernels."""
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     Mx, Px, Py, N = nx // 2, 3 * nx // 2, 3 * ny // 2, nz - 1
-    b = 16 if prec == 0 else 8
+    b = 8 if prec == 1 else 16
     S = Mx * ny * nz           # spectral points per field
     Y = Mx * Py * nz           # y-padded points per field
     lines = Mx * ny
@@ -93,8 +93,8 @@ def cufft_transforms_ms(w, prec, reps=5, warmup=2, dev="cuda"):
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     Mx, Px, Py, N = nx // 2, 3 * nx // 2, 3 * ny // 2, nz - 1
     h = ny // 2
-    cd = torch.complex128 if prec == 0 else torch.complex64
-    rd = torch.float64 if prec == 0 else torch.float32
+    cd = torch.complex64 if prec == 1 else torch.complex128
+    rd = torch.float32 if prec == 1 else torch.float64
     spec = torch.randn(12, Mx, ny, nz, dtype=torch.complex128, device=dev)
     ymod = torch.randn(6, Mx, ny, nz, dtype=cd, device=dev)
     prod = torch.randn(9, Px, Py, nz, dtype=rd, device=dev)
@@ -140,8 +140,13 @@ def cufft_transforms_ms(w, prec, reps=5, warmup=2, dev="cuda"):
     return res[0], res[1]
 
 
-def mixed_accuracy(binding, w, fields, steps, device):
-    """Mixed-precision step against the FP64 step from the same fields after `steps` steps:
+PREC_NAMES = {0: "fp64", 1: "mixed", 2: "dfloat"}
+DTYPES = {0: "f64", 1: "f32 transforms/products + f64 solves",
+          2: "double-float (float pair, ~48-bit) transforms/products + f64 solves"}
+
+
+def precision_accuracy(binding, w, fields, steps, device, prec=1):
+    """Step of precision `prec` against the FP64 step from the same fields after `steps` steps:
     per-field max relative difference (max |a - b| / max |b|), phi mass drift of each path
     relative to the initial mass, and relative differences of kinetic energy, int |grad phi|^2
     and free energy."""
@@ -149,20 +154,20 @@ def mixed_accuracy(binding, w, fields, steps, device):
     kw = dict(re_tau=w["re_tau"], we=w["we"], ch=w["ch"], pe=w["pe"], dt=w["dt"])
     out = {}
     res = {}
-    for prec in (0, 1):
-        g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=prec, device=device, **kw)
+    for pr in (0, prec):
+        g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=pr, device=device, **kw)
         g.set_fields(*[torch.from_numpy(f) for f in fields])
         m0 = g.diagnostics()["mass"]
         g.step(steps)
         d = g.diagnostics()
-        res[prec] = ([f.cpu() for f in g.get_fields()], d, m0)
+        res[pr] = ([f.cpu() for f in g.get_fields()], d, m0)
         g.close()
         torch.cuda.empty_cache()
-    (f64, d64, m64), (f32, d32, m32) = res[0], res[1]
+    (f64, d64, m64), (f32, d32, m32) = res[0], res[prec]
     out["rel_err"] = {n: float((a - b).abs().max() / b.abs().max())
                       for n, a, b in zip(("u", "v", "w", "phi"), f32, f64)}
     out["mass_drift_fp64"] = (d64["mass"] - m64) / abs(m64)
-    out["mass_drift_mixed"] = (d32["mass"] - m32) / abs(m32)
+    out["mass_drift_" + PREC_NAMES[prec]] = (d32["mass"] - m32) / abs(m32)
     for k in ("kinetic", "grad2", "free_energy"):
         out[k + "_rel_diff"] = (d32[k] - d64[k]) / abs(d64[k])
     out["steps"] = steps
@@ -531,11 +536,12 @@ def main():
                     help="timed steps (default 100; adjoint workload: gradients, default 5)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="channel_128x128x129")
-    ap.add_argument("--precision", type=int, default=None, help="0 fp64, 1 mixed")
+    ap.add_argument("--precision", type=int, default=None,
+                    help="0 fp64, 1 mixed (fp32 x/y), 2 double-float x/y")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
-                    help="skip the mixed-vs-FP64 comparison of mixed-precision workloads")
+                    help="skip the comparison against the FP64 path (precision 1 and 2)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 5 if args.workload == "channel_128x128x129_adjoint" else 100
@@ -609,7 +615,10 @@ def main():
     per_launch_ms = kms[k] / args.steps
     fl, by = work[name]
     hbm, hbm_kind = peaks()
-    fp64_like = (prec == 0) or name.startswith("z")
+    # float64 kernels (all of precision 0, the z kernels of every precision) and the
+    # double-float kernels (float64-accurate work on the float32 pipe) are ALU-bound and are
+    # measured against the float64 peak; float32 kernels against HBM
+    fp64_like = (prec != 1) or name.startswith("z")
     if fp64_like:
         ach = fl / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -631,10 +640,10 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "steps_per_s": 1e3 / ms_step,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if prec == 0 else "f32 transforms/products + f64 solves",
+           "dtype": DTYPES[prec],
            "data": "synthetic",
            "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]],
-                      "precision": "fp64" if prec == 0 else "mixed",
+                      "precision": PREC_NAMES[prec],
                       "parallelism": "replicas" if world > 1 else "single",
                       "l2": "step working set larger than L2 (no flush)"},
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes / args.steps,
@@ -644,8 +653,9 @@ def main():
            "roofline": roof,
            "clocks": clk.summary()}
     g.close()
-    if world == 1 and prec == 1 and not args.no_accuracy:
-        out["mixed_vs_fp64"] = mixed_accuracy(binding, w, fields, w["steps"], f"cuda:{local}")
+    if world == 1 and prec != 0 and not args.no_accuracy:
+        out[PREC_NAMES[prec] + "_vs_fp64"] = precision_accuracy(binding, w, fields, w["steps"],
+                                                                f"cuda:{local}", prec)
     if world == 1:
         zc, xyc = cufft_transforms_ms(w, prec)
         ours_xy = sum(roof["kernel_ms_per_step"][n] for n in ("ybwd", "xline", "yfwd"))

@@ -53,6 +53,10 @@ extern "C" {
 #define CH_PREC_FP64 0  /* every stage in float64                                         */
 #define CH_PREC_MIXED 1 /* x/y transforms and physical-space products in float32; the
                            Chebyshev transform, tau solves, state and mass stay float64      */
+#define CH_PREC_DFLOAT 2 /* x/y transforms and physical-space products in double-float (the
+                           unevaluated sum of two floats, ~48-bit significand, on the float32
+                           pipe); the rest as in CH_PREC_FP64.  Not a precision of the paper:
+                           an FP64-accurate variant for GPUs whose float64 rate is low       */
 
 typedef struct ch_grid ch_grid; /* opaque, owned by the library */
 
@@ -66,7 +70,7 @@ typedef struct {
   double pe;          /* Peclet number                                                     */
   double dt;          /* time step (> 0)                                                   */
   double gx, gy;      /* mean pressure gradient -dp/dx, -dp/dy driving the mean flow       */
-  int precision;      /* CH_PREC_FP64 or CH_PREC_MIXED                                     */
+  int precision;      /* CH_PREC_FP64, CH_PREC_MIXED or CH_PREC_DFLOAT (single grids only)   */
   int dealias_z;      /* must be 0: no padding of the Chebyshev direction                  */
   int bc;             /* must be 0: no-slip walls for velocity, no-flux for phi            */
 } ch_params;
@@ -178,7 +182,7 @@ int ch_nonlinear(ch_grid* g, double* out9);
  * ch_adjoint_gradient: after the step reversed last (the first forward step), writes
  *   dJ/du0, dJ/dv0, dJ/dw0, dJ/dphi0 into four device (nz,ny,nx) float64 arrays.
  * ch_adjoint_end: frees the workspace (ch_destroy does too).
- * Mixed-precision grids: CH_ERR_ARG.  Grids whose padded x length Px = 3 nx / 2 exceeds 602
+ * Mixed-precision and double-float grids: CH_ERR_ARG.  Grids whose padded x length Px = 3 nx / 2 exceeds 602
  * (the transposed x line keeps 24 lines of Px complex float64, 384 Px bytes, in the 226 KiB of
  * shared memory a block may use): CH_ERR_SIZE (nx <= 384 among the supported sizes).
  * Calls out of order (step/gradient before begin; J of an unset grid): CH_ERR_STATE. */

@@ -19,6 +19,7 @@ STATUS = {0: "ok", -1: "CH_ERR_ARG", -2: "CH_ERR_SIZE", -3: "CH_ERR_ALLOC", -4: 
           -5: "CH_ERR_DIVERGED", -6: "CH_ERR_TIMEOUT", -7: "CH_ERR_STATE"}
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_DFLOAT = 2
 
 
 class ChError(RuntimeError):

@@ -110,22 +110,31 @@ int make_plan(ch_grid* G, int n, int prec, FftPlan* pl) {
   if (!make_radices(n, pl)) return CH_ERR_SIZE;
   std::vector<double2> h64(n);
   std::vector<float2> h32(n);
+  std::vector<float> hdf(4 * (size_t)n);  // double-float pairs (h, l) of re and im
   const long double pi2 = 6.283185307179586476925286766559L;
   for (int t = 0; t < n; ++t) {
     const long double a = pi2 * (long double)t / (long double)n;
     const long double c = cosl(a), s = -sinl(a);
     h64[t] = make_double2((double)c, (double)s);
     h32[t] = make_float2((float)c, (float)s);
+    const float ch = (float)c, sh = (float)s;
+    hdf[4 * (size_t)t + 0] = ch;
+    hdf[4 * (size_t)t + 1] = (float)(c - (long double)ch);
+    hdf[4 * (size_t)t + 2] = sh;
+    hdf[4 * (size_t)t + 3] = (float)(s - (long double)sh);
   }
   Tw tw;
   tw.d64 = galloc(G, n * sizeof(double2));
   tw.d32 = galloc(G, n * sizeof(float2));
-  if (!tw.d64 || !tw.d32) return CH_ERR_ALLOC;
+  tw.ddf = galloc(G, 4 * (size_t)n * sizeof(float));
+  if (!tw.d64 || !tw.d32 || !tw.ddf) return CH_ERR_ALLOC;
   if (cudaMemcpy(tw.d64, h64.data(), n * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(tw.d32, h32.data(), n * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(tw.d32, h32.data(), n * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(tw.ddf, hdf.data(), 4 * (size_t)n * sizeof(float), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
     return CH_ERR_CUDA;
   G->tws.push_back(tw);
-  pl->tw = prec == 0 ? tw.d64 : tw.d32;
+  pl->tw = prec == 0 ? tw.d64 : prec == 1 ? tw.d32 : tw.ddf;
   return CH_OK;
 }
 
@@ -249,7 +258,9 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   if (!(p->dt > 0) || !(p->lx > 0) || !(p->ly > 0) || !(p->re_tau > 0) || !(p->we > 0) ||
       !(p->ch > 0) || !(p->pe > 0))
     return CH_ERR_ARG;
-  if (p->precision != CH_PREC_FP64 && p->precision != CH_PREC_MIXED) return CH_ERR_ARG;
+  if (p->precision != CH_PREC_FP64 && p->precision != CH_PREC_MIXED &&
+      p->precision != CH_PREC_DFLOAT)
+    return CH_ERR_ARG;
   if (p->dealias_z != 0 || p->bc != 0) return CH_ERR_ARG;
   if ((alloc == nullptr) != (free_fn == nullptr)) return CH_ERR_ARG;
   const int nx = p->nx, ny = p->ny, nz = p->nz;
@@ -291,7 +302,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   g.shat = 2.0 * g.lam * p->ch * p->ch;
   g.kappa = 3.0 / sqrt(8.0) * p->ch / p->we;
 
-  const size_t esz = G->prec == 0 ? sizeof(double2) : sizeof(float2);
+  const size_t esz = G->prec == CH_PREC_MIXED ? sizeof(float2) : sizeof(double2);
   G->fs = (long long)g.Mx * ny * nz;
   G->fsy = (long long)g.Mx * g.Py * nz;
   G->fsp = (long long)nx * ny * nz;
@@ -329,9 +340,19 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   // plans
   int e = CH_OK;
   if (e == CH_OK) e = make_plan(G, g.Px, 0, &G->px[0]);
-  if (e == CH_OK) { G->px[1] = G->px[0]; G->px[1].tw = G->tws.back().d32; }
+  if (e == CH_OK) {
+    G->px[1] = G->px[0];
+    G->px[1].tw = G->tws.back().d32;
+    G->px[2] = G->px[0];
+    G->px[2].tw = G->tws.back().ddf;
+  }
   if (e == CH_OK) e = make_plan(G, g.Py, 0, &G->py[0]);
-  if (e == CH_OK) { G->py[1] = G->py[0]; G->py[1].tw = G->tws.back().d32; }
+  if (e == CH_OK) {
+    G->py[1] = G->py[0];
+    G->py[1].tw = G->tws.back().d32;
+    G->py[2] = G->py[0];
+    G->py[2].tw = G->tws.back().ddf;
+  }
   if (e == CH_OK) e = make_plan(G, g.N, 0, &G->pz);
   if (e == CH_OK) e = make_plan(G, nx, 0, &G->pxu);
   if (e == CH_OK) e = make_plan(G, ny, 0, &G->pyu);

@@ -53,8 +53,72 @@ template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// double-float: the unevaluated sum h + l of two floats with |l| <= ulp(h) / 2 (about 48
+// significant bits), so that FP64-accurate transforms run on the FP32 pipe.  Built from the
+// error-free transformations of Knuth (TwoSum: s + e = a + b exactly) and of Dekker with a fused
+// multiply-add (TwoProduct: p + e = a * b exactly); the sum adds the low parts after TwoSum of
+// the high parts and renormalises (the "sloppy" double-float addition: relative error about
+// 2^-47 of max(|a|, |b|), enough for the norm-wise error bounds of FFTs and products); the
+// product drops the l * l term.  Range is that of float.
+struct df {
+  float h, l;
+  df() = default;
+  __host__ __device__ __forceinline__ df(float hi, float lo) : h(hi), l(lo) {}
+  __host__ __device__ __forceinline__ df(double v) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+  }
+};
+struct __align__(16) df2 {
+  df x, y;
+};
+template <> struct C2<df> { typedef df2 t; };
+
+__device__ __forceinline__ df df_quick(float s, float e) {   // |s| >= |e|
+  const float h = s + e;
+  return df(h, e - (h - s));
+}
+__device__ __forceinline__ df operator+(df a, df b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  return df_quick(s, e);
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.h, -a.l); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ df2 mk(df x, df y) {
+  df2 r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+__device__ __forceinline__ df2 operator+(df2 a, df2 b) { return mk(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ df2 operator-(df2 a, df2 b) { return mk(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ df2 operator*(df s, df2 a) { return mk(s * a.x, s * a.y); }
+__device__ __forceinline__ df2 cmul(df2 a, df2 b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ df2 cmulc(df2 a, df2 b) {
+  return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ double2 to_d2(df2 a) {
+  return make_double2((double)a.x.h + (double)a.x.l, (double)a.y.h + (double)a.y.l);
+}
+template <> __device__ __forceinline__ df2 from_d2<df2>(double2 a) {
+  return mk(df(a.x), df(a.y));
+}
+
+// ---------------------------------------------------------------------------------------------
 // FFT plan: length n = product of radices (each 2, 3, 4 or 8), twiddle table
-// tw[t] = exp(-2 pi i t / n), t = 0..n-1, in the working precision.
+// tw[t] = exp(-2 pi i t / n), t = 0..n-1, in the working precision (double2, float2 or df2).
 #define CHF_MAX_STAGES 16
 struct FftPlan {
   int n;

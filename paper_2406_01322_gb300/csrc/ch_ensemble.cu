@@ -315,6 +315,7 @@ int ch_ensemble_init(const ch_params* members, int n, ch_alloc_fn alloc, ch_free
   *out = nullptr;
   for (int i = 0; i < n; ++i)
     if (members[i].precision != members[0].precision) return CH_ERR_ARG;
+  if (members[0].precision == CH_PREC_DFLOAT) return CH_ERR_ARG;  // grouped kernels: fp64/fp32
   ch_ensemble* E = new (std::nothrow) ch_ensemble();
   if (!E) return CH_ERR_ALLOC;
   E->prec = members[0].precision;

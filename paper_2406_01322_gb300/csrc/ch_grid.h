@@ -15,6 +15,7 @@ const int kMaxSmem = 227 * 1024 - 1024;  // opt-in limit less room for static sh
 struct Tw {
   void* d64 = nullptr;  // double2[n]
   void* d32 = nullptr;  // float2[n]
+  void* ddf = nullptr;  // df2[n] (double-float pairs)
 };
 
 // fields through the step: 5 backward (u v w phi Dphi) -> 6 y-padded (phi_y added by the y
@@ -68,7 +69,7 @@ struct ch_grid {
   double* diag_part;
   double* diag_out;
 
-  chf::FftPlan px[2], py[2], pz, pxu, pyu;
+  chf::FftPlan px[3], py[3], pz, pxu, pyu;  // px, py indexed by precision
   std::vector<chf::Tw> tws;
 
   long long fs;      // elements per (Mx, Ny, Nz) field

@@ -465,24 +465,28 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
     map.dy_mask = 0;
   }
   map.kys = 6.283185307179586476925 / g.ly;
-  const size_t elem = prec == 0 ? sizeof(double2) : sizeof(float2);
+  const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);
   const int TZ = ytile_local(P, elem);
   const size_t smem = (size_t)2 * TZ * P * elem;
   dim3 grid((g.nz + TZ - 1) / TZ, g.Mx, nf);
-  static int cur[4] = {0, 0, 0, 0};
+  static int cur[6] = {0, 0, 0, 0, 0, 0};
   cudaError_t e = cudaSuccess;
   if (prec == 0) e = dir == 1 ? ensure_smem(ypass_kernel<double, true>, smem, &cur[0])
                               : ensure_smem(ypass_kernel<double, false>, smem, &cur[1]);
-  else e = dir == 1 ? ensure_smem(ypass_kernel<float, true>, smem, &cur[2])
-                    : ensure_smem(ypass_kernel<float, false>, smem, &cur[3]);
+  else if (prec == 1) e = dir == 1 ? ensure_smem(ypass_kernel<float, true>, smem, &cur[2])
+                                   : ensure_smem(ypass_kernel<float, false>, smem, &cur[3]);
+  else e = dir == 1 ? ensure_smem(ypass_kernel<df, true>, smem, &cur[4])
+                    : ensure_smem(ypass_kernel<df, false>, smem, &cur[5]);
   if (e != cudaSuccess) return e;
 #define YL(T, INV)                                                                            \
   ypass_kernel<T, INV><<<grid, YT, smem, s>>>((const C2<T>::t*)in, (C2<T>::t*)out, g.Mx, g.ny, \
-                                              P, g.nz, TZ, fs_in, fs_out, (T)scale, py, map);
+                                              P, g.nz, TZ, fs_in, fs_out, T(scale), py, map);
   if (prec == 0) {
     if (dir == 1) { YL(double, true) } else { YL(double, false) }
-  } else {
+  } else if (prec == 1) {
     if (dir == 1) { YL(float, true) } else { YL(float, false) }
+  } else {
+    if (dir == 1) { YL(df, true) } else { YL(df, false) }
   }
 #undef YL
   return cudaGetLastError();
@@ -490,21 +494,25 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
 
 cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out10, long long fs,
                          double scale, const FftPlan& px, cudaStream_t s) {
-  const size_t elem = prec == 0 ? sizeof(double2) : sizeof(float2);
+  const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);
   const size_t smem = (size_t)17 * g.Px * elem;
   dim3 grid((g.nz + 1) / 2, g.Py);
-  static int cur64 = 0, cur32 = 0;
+  static int cur64 = 0, cur32 = 0, curdf = 0;
   cudaError_t e = prec == 0 ? ensure_smem(xline_kernel<double>, smem, &cur64)
-                            : ensure_smem(xline_kernel<float>, smem, &cur32);
+                  : prec == 1 ? ensure_smem(xline_kernel<float>, smem, &cur32)
+                              : ensure_smem(xline_kernel<df>, smem, &curdf);
   if (e != cudaSuccess) return e;
+  const double kxs = 6.283185307179586476925 / g.lx;
   if (prec == 0) {
     xline_kernel<double><<<grid, XT, smem, s>>>((const double2*)in7, (double2*)out10, g.Mx, g.Px,
-                                                g.Py, g.nz, fs, g.kappa, scale,
-                                                6.283185307179586476925 / g.lx, px);
-  } else {
+                                                g.Py, g.nz, fs, g.kappa, scale, kxs, px);
+  } else if (prec == 1) {
     xline_kernel<float><<<grid, XT, smem, s>>>((const float2*)in7, (float2*)out10, g.Mx, g.Px,
                                                g.Py, g.nz, fs, (float)g.kappa, (float)scale,
-                                               (float)(6.283185307179586476925 / g.lx), px);
+                                               (float)kxs, px);
+  } else {
+    xline_kernel<df><<<grid, XT, smem, s>>>((const df2*)in7, (df2*)out10, g.Mx, g.Px, g.Py, g.nz,
+                                            fs, df(g.kappa), df(scale), df(kxs), px);
   }
   return cudaGetLastError();
 }

@@ -1603,11 +1603,16 @@ cudaError_t launch_zrhs(int prec, const GridDev& g, const void* nl, long long fs
     if ((e = ensure_smem(zrhs_kernel<double>, smem, &cur)) != cudaSuccess) return e;
     zrhs_kernel<double><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const double2*)nl, fs, st_om, st_w, st_phi,
                                                       h_om, h_w, h_phi, R, first, pz);
-  } else {
+  } else if (prec == 1) {
     static int cur = 0;
     if ((e = ensure_smem(zrhs_kernel<float>, smem, &cur)) != cudaSuccess) return e;
     zrhs_kernel<float><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const float2*)nl, fs, st_om, st_w, st_phi,
                                                      h_om, h_w, h_phi, R, first, pz);
+  } else {
+    static int cur = 0;
+    if ((e = ensure_smem(zrhs_kernel<df>, smem, &cur)) != cudaSuccess) return e;
+    zrhs_kernel<df><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const df2*)nl, fs, st_om, st_w, st_phi,
+                                                  h_om, h_w, h_phi, R, first, pz);
   }
   return cudaGetLastError();
 }
@@ -1779,6 +1784,9 @@ cudaError_t launch_zbwd(int update, int prec, int nout, const GridDev& g, const 
   if (prec == 0)
     return update ? launch_zbwd_t<double, 1, 5>(g, R, st_om, st_w, st_phi, bw, fs, pz, s)
                   : launch_zbwd_t<double, 0, 5>(g, R, st_om, st_w, st_phi, bw, fs, pz, s);
+  if (prec == 2)
+    return update ? launch_zbwd_t<df, 1, 5>(g, R, st_om, st_w, st_phi, bw, fs, pz, s)
+                  : launch_zbwd_t<df, 0, 5>(g, R, st_om, st_w, st_phi, bw, fs, pz, s);
   return update ? launch_zbwd_t<float, 1, 5>(g, R, st_om, st_w, st_phi, bw, fs, pz, s)
                 : launch_zbwd_t<float, 0, 5>(g, R, st_om, st_w, st_phi, bw, fs, pz, s);
 }
@@ -1797,14 +1805,17 @@ cudaError_t launch_project(const GridDev& g, const double2* uvwp, long long fs, 
 cudaError_t launch_dct_lines(int dir, int prec, const GridDev& g, const void* in, double2* out,
                              int nf, long long fs, const FftPlan& pz, cudaStream_t s) {
   const size_t smem = zline_smem(g);
-  static int cur64 = 0, cur32 = 0;
+  static int cur64 = 0, cur32 = 0, curdf = 0;
   cudaError_t e = ensure_smem(dct_lines_kernel<double>, smem, &cur64);
   if (e == cudaSuccess) e = ensure_smem(dct_lines_kernel<float>, smem, &cur32);
+  if (e == cudaSuccess) e = ensure_smem(dct_lines_kernel<df>, smem, &curdf);
   if (e != cudaSuccess) return e;
   if (prec == 0) {
     dct_lines_kernel<double><<<g.Mx * g.ny, ZT, smem, s>>>(g, dir, (const double2*)in, out, nf, fs, pz);
-  } else {
+  } else if (prec == 1) {
     dct_lines_kernel<float><<<g.Mx * g.ny, ZT, smem, s>>>(g, dir, (const float2*)in, out, nf, fs, pz);
+  } else {
+    dct_lines_kernel<df><<<g.Mx * g.ny, ZT, smem, s>>>(g, dir, (const df2*)in, out, nf, fs, pz);
   }
   return cudaGetLastError();
 }

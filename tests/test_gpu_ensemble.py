@@ -100,3 +100,10 @@ def test_ensemble_requires_every_member_set(binding):
         ens.step(1)
     assert e.value.code == -7
     ens.close()
+
+
+def test_ensemble_rejects_double_float(binding):
+    """The grouped kernels exist in float64 and float32 only."""
+    with pytest.raises(binding.ChError) as e:
+        binding.Ensemble(members()[:2], precision=binding.PREC_DFLOAT)
+    assert e.value.code == -1

@@ -196,6 +196,31 @@ def test_host_entry_points_match_device(binding):
         assert torch.equal(x, y.cpu())
 
 
+@pytest.mark.parametrize("name,over", SIZES)
+def test_dfloat_nonlinear_terms(binding, name, over):
+    """Double-float x/y transforms and products (CH_PREC_DFLOAT) against the FP64 oracle."""
+    w = workload(name, **over)
+    g, o = make_pair(binding, w, precision=binding.PREC_DFLOAT)
+    got = g.nonlinear()
+    r = o.nonlinear_spectral()
+    ref = [r[0] - r[2], r[1] - r[2], r[3], r[4], r[5], r[6], r[7], r[8], r[9]]
+    for k in range(9):
+        assert rel(spec_to_oracle(got[k]), ref[k]) < 1e-11, k
+
+
+@pytest.mark.parametrize("name,over", SIZES)
+def test_dfloat_ten_steps_within_1e_10(binding, name, over):
+    """The double-float path meets the FP64 path's bar: max relative field error <= 1e-10
+    against the FP64 oracle after 10 steps."""
+    w = workload(name, **over)
+    g, o = make_pair(binding, w, precision=binding.PREC_DFLOAT)
+    g.step(10)
+    for _ in range(10):
+        o.step()
+    for a, b, f in zip(g.get_fields(), o.get_fields(), "uvwp"):
+        assert rel(a.cpu().numpy(), b) <= 1e-10, f
+
+
 def test_mixed_precision_error_bounds(binding):
     w = workload("channel_32x32x33")
     fields = inputs.initial_fields(**w)
@@ -229,11 +254,12 @@ def test_error_codes(binding):
     assert e.value.code == -7
 
 
-def test_medium_channel_one_step_sampled_lines(binding):
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "dfloat"])
+def test_medium_channel_one_step_sampled_lines(binding, precision):
     """128x128x129 workload: one GPU step against the oracle on a sample of wavenumber lines
     (the oracle forms every non-linear term but solves only the sampled lines)."""
     w = workload("channel_128x128x129")
-    g, o = make_pair(binding, w)
+    g, o = make_pair(binding, w, precision)
     g.step(1)
     rng = np.random.default_rng(3)
     lines = [(0, 0), (1, 0), (0, 1), (w["ny"] - 1, 0), (5, 7), (w["ny"] // 2 + 3, 63)]
