@@ -72,7 +72,9 @@ typedef struct {
   double gx, gy;      /* mean pressure gradient -dp/dx, -dp/dy driving the mean flow       */
   int precision;      /* CH_PREC_FP64, CH_PREC_MIXED or CH_PREC_DFLOAT (single grids only)   */
   int dealias_z;      /* must be 0: no padding of the Chebyshev direction                  */
-  int bc;             /* must be 0: no-slip walls for velocity, no-flux for phi            */
+  int bc;             /* walls (Sec. 2.1: no-slip or free-slip): 0 no-slip (u = v = w =
+                         dw/dz = 0), 1 free-slip (du/dz = dv/dz = 0, w = 0, d2w/dz2 = 0) at both
+                         walls; phi no-flux in both.  Other values: CH_ERR_ARG             */
 } ch_params;
 
 typedef void* (*ch_alloc_fn)(size_t bytes, void* ctx);
@@ -182,7 +184,7 @@ int ch_nonlinear(ch_grid* g, double* out9);
  * ch_adjoint_gradient: after the step reversed last (the first forward step), writes
  *   dJ/du0, dJ/dv0, dJ/dw0, dJ/dphi0 into four device (nz,ny,nx) float64 arrays.
  * ch_adjoint_end: frees the workspace (ch_destroy does too).
- * Mixed-precision and double-float grids: CH_ERR_ARG.  Grids whose padded x length Px = 3 nx / 2 exceeds 602
+ * Mixed-precision, double-float and free-slip grids: CH_ERR_ARG.  Grids whose padded x length Px = 3 nx / 2 exceeds 602
  * (the transposed x line keeps 24 lines of Px complex float64, 384 Px bytes, in the 226 KiB of
  * shared memory a block may use): CH_ERR_SIZE (nx <= 384 among the supported sizes).
  * Calls out of order (step/gradient before begin; J of an unset grid): CH_ERR_STATE. */

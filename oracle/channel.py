@@ -38,6 +38,11 @@ R7  phi boundary conditions: d phi/dz = 0 for both split problems (no flux); vel
 R8  Both S and S_phi are evaluated from (u^n, phi^n).
 R9  Mass of phi = Lx Ly sum_{n even} 2 Re(phihat_00,n) / (1 - n^2) (exact integral).
 R10 Chebyshev-tau with the Gottlieb-Orszag rows (``oracle.chebyshev``).
+R13 Free-slip walls (Params.bc = 1; Sec. 2.1 allows no-slip or free-slip at the walls; the same
+    condition at both walls): du/dz = dv/dz = 0 and w = 0, so d omega_z/dz = 0 and the mean flow
+    takes Neumann rows; continuity then gives d2w/dz2 = 0, and the (theta, w) pair takes its four
+    wall rows on w (w = w'' = 0), as for no-slip (w = w' = 0).  A different condition on each
+    wall is not built.
 
 State: omega (Nz, Ny, Mx), w, phi complex Chebyshev x Fourier coefficients, [n, j(my), mx].
 """
@@ -64,6 +69,7 @@ class Params:
     dt: float = 1e-4
     gx: float = 1.0
     gy: float = 0.0
+    bc: int = 0          # walls (Sec. 2.1): 0 no-slip, 1 free-slip (both walls)
 
 
 class Channel:
@@ -224,11 +230,13 @@ class Channel:
     def solve_line(self, j, m, r_om, r_th, r_psi):
         """Solve the implicit problems of one (my, mx) line; returns (omega, w, phi)^{n+1}."""
         k2 = self.k2[j, m]
-        om = cheb.solve_helmholtz(r_om, k2 + self.beta, "dirichlet")
+        free = self.p.bc == 1
+        # omega_z and the mean flow: Dirichlet (no-slip) or Neumann (free-slip: du/dz = dv/dz = 0)
+        om = cheb.solve_helmholtz(r_om, k2 + self.beta, "neumann" if free else "dirichlet")
         if j == 0 and m == 0:
             w = np.zeros_like(r_th)
         else:
-            _, w = cheb.solve_coupled_w(r_th, k2, self.beta)
+            _, w = cheb.solve_coupled_w(r_th, k2, self.beta, "free-slip" if free else "no-slip")
         psi = cheb.solve_helmholtz(r_psi, k2 + self.lam, "neumann")
         ph = cheb.solve_helmholtz(psi, k2 + self.lam, "neumann")
         return om, w, ph

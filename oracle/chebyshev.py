@@ -100,15 +100,20 @@ def go_matrix(N):
 
 
 def bc_rows(N, bc):
-    """Two boundary rows: values at z = +1 and z = -1 (bc='dirichlet'), or of d/dz (bc='neumann').
+    """Two boundary rows: values at z = +1 and z = -1 (bc='dirichlet'), of d/dz (bc='neumann')
+    or of d2/dz2 (bc='second').
 
-    T_n(+1) = 1, T_n(-1) = (-1)^n, T_n'(+1) = n^2, T_n'(-1) = (-1)^(n+1) n^2."""
+    T_n(+1) = 1, T_n(-1) = (-1)^n, T_n'(+1) = n^2, T_n'(-1) = (-1)^(n+1) n^2,
+    T_n''(+1) = n^2 (n^2 - 1) / 3, T_n''(-1) = (-1)^n n^2 (n^2 - 1) / 3."""
     n = np.arange(N + 1, dtype=float)
     sgn = (-1.0) ** np.arange(N + 1)
     if bc == "dirichlet":
         return np.stack([np.ones(N + 1), sgn])
     if bc == "neumann":
         return np.stack([n * n, -sgn * n * n])
+    if bc == "second":
+        t2 = n * n * (n * n - 1.0) / 3.0
+        return np.stack([t2, sgn * t2])
     raise ValueError(bc)
 
 
@@ -138,14 +143,15 @@ def solve_helmholtz(f, alpha, bc, g_plus=0.0, g_minus=0.0):
     return _solve_real(M, r)
 
 
-def coupled_w_matrix(N, k2, beta):
+def coupled_w_matrix(N, k2, beta, walls="no-slip"):
     """Dense matrix of the influence-matrix pair for (theta, w), 2(N+1) unknowns.
 
     (D^2 - k^2 - beta) theta = r   (tau rows 0..N-2)
     (D^2 - k^2) w = theta          (tau rows 0..N-2)
-    w(+1) = w(-1) = 0, w'(+1) = w'(-1) = 0.
-    Both second-order problems are written in Gottlieb-Orszag form; the four wall conditions
-    all fall on w (no-slip, Sec. 2.1 / Eq. (ww)).  Unknown vector = [theta_0..N, w_0..N]."""
+    no-slip:   w(+1) = w(-1) = 0, w'(+1) = w'(-1) = 0 (all four wall rows on w, Eq. (ww));
+    free-slip: w(+1) = w(-1) = 0, w''(+1) = w''(-1) = 0 (again all four on w).
+    Both second-order problems are written in Gottlieb-Orszag form.  The walls are those of
+    Sec. 2.1 (no-slip or free-slip).  Unknown vector = [theta_0..N, w_0..N]."""
     G = go_matrix(N)
     n1 = N + 1
     M = np.zeros((2 * n1, 2 * n1))
@@ -156,19 +162,24 @@ def coupled_w_matrix(N, k2, beta):
     # w rows n = 2..N:  w_n - k^2 (G w)_n - (G theta)_n = 0
     M[n1 + 2:2 * n1, n1:2 * n1] = (I - k2 * G)[rows]
     M[n1 + 2:2 * n1, 0:n1] = -G[rows]
-    # four wall rows on w
-    M[0:2, n1:2 * n1] = bc_rows(N, "dirichlet")
-    M[n1:n1 + 2, n1:2 * n1] = bc_rows(N, "neumann")
+    if walls == "no-slip":                      # four wall rows on w
+        M[0:2, n1:2 * n1] = bc_rows(N, "dirichlet")
+        M[n1:n1 + 2, n1:2 * n1] = bc_rows(N, "neumann")
+    elif walls == "free-slip":                  # w and w'' vanish at both walls
+        M[0:2, n1:2 * n1] = bc_rows(N, "dirichlet")
+        M[n1:n1 + 2, n1:2 * n1] = bc_rows(N, "second")
+    else:
+        raise ValueError(walls)
     return M
 
 
-def solve_coupled_w(r, k2, beta):
-    """Solve the (theta, w) influence problem of ``coupled_w_matrix`` for one right-hand side r.
+def solve_coupled_w(r, k2, beta, walls="no-slip"):
+    """Solve the (theta, w) problem of ``coupled_w_matrix`` for one right-hand side r.
 
     Returns (theta, w)."""
     N = len(r) - 1
     n1 = N + 1
-    M = coupled_w_matrix(N, k2, beta)
+    M = coupled_w_matrix(N, k2, beta, walls)
     rhs = np.zeros(2 * n1, dtype=np.result_type(r, float))
     rhs[0:n1] = go_matrix(N) @ r
     rhs[0:2] = 0.0

@@ -20,6 +20,8 @@ STATUS = {0: "ok", -1: "CH_ERR_ARG", -2: "CH_ERR_SIZE", -3: "CH_ERR_ALLOC", -4: 
 PREC_FP64 = 0
 PREC_MIXED = 1
 PREC_DFLOAT = 2
+BC_NO_SLIP = 0
+BC_FREE_SLIP = 1
 
 
 class ChError(RuntimeError):
@@ -172,11 +174,11 @@ class Grid:
 
     def __init__(self, nx, ny, nz, re_tau=150.0, we=1.0, ch=0.05, pe=20.0, dt=1e-4,
                  lx=4 * math.pi, ly=2 * math.pi, gx=1.0, gy=0.0, precision=PREC_FP64,
-                 device="cuda:0", stream=None, use_torch_allocator=True):
+                 device="cuda:0", stream=None, use_torch_allocator=True, bc=BC_NO_SLIP):
         self.device = torch.device(device)
         self.shape = (nz, ny, nx)
         self.spec_shape = (nx // 2, ny, nz)
-        self.params = Params(nx, ny, nz, lx, ly, re_tau, we, ch, pe, dt, gx, gy, precision, 0, 0)
+        self.params = Params(nx, ny, nz, lx, ly, re_tau, we, ch, pe, dt, gx, gy, precision, 0, bc)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._alloc = TorchAllocator(self.device) if use_torch_allocator else None
         h = ctypes.c_void_p()
@@ -411,7 +413,8 @@ class Ensemble:
             arr[i] = Params(m["nx"], m["ny"], m["nz"], m.get("lx", 4 * math.pi),
                             m.get("ly", 2 * math.pi), m.get("re_tau", 150.0), m.get("we", 1.0),
                             m.get("ch", 0.05), m.get("pe", 20.0), m.get("dt", 1e-4),
-                            m.get("gx", 1.0), m.get("gy", 0.0), precision, 0, 0)
+                            m.get("gx", 1.0), m.get("gy", 0.0), precision, 0,
+                            m.get("bc", BC_NO_SLIP))
         self._params = arr
         self._alloc = TorchAllocator(self.device)
         h = ctypes.c_void_p()

@@ -261,7 +261,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   if (p->precision != CH_PREC_FP64 && p->precision != CH_PREC_MIXED &&
       p->precision != CH_PREC_DFLOAT)
     return CH_ERR_ARG;
-  if (p->dealias_z != 0 || p->bc != 0) return CH_ERR_ARG;
+  if (p->dealias_z != 0 || (p->bc != 0 && p->bc != 1)) return CH_ERR_ARG;
   if ((alloc == nullptr) != (free_fn == nullptr)) return CH_ERR_ARG;
   const int nx = p->nx, ny = p->ny, nz = p->nz;
   if (chf::check_sizes(nx, ny, nz) != CH_OK) return CH_ERR_SIZE;
@@ -301,6 +301,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   g.lam = sqrt(p->pe / (p->ch * p->ch * p->dt));
   g.shat = 2.0 * g.lam * p->ch * p->ch;
   g.kappa = 3.0 / sqrt(8.0) * p->ch / p->we;
+  g.bc = p->bc;
 
   const size_t esz = G->prec == CH_PREC_MIXED ? sizeof(float2) : sizeof(double2);
   G->fs = (long long)g.Mx * ny * nz;

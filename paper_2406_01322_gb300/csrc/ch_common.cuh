@@ -273,6 +273,9 @@ struct GridDev {
   int NK;
   // cos(pi j / N), sin(pi j / N), j = 0..N-1 (Chebyshev transform through an N-point FFT)
   const double2* zcs;
+  // wall conditions: 0 no-slip (u = v = w = dw/dz = 0), 1 free-slip (du/dz = dv/dz = 0, w = 0,
+  // d2w/dz2 = 0) at both walls
+  int bc;
 };
 
 }  // namespace chf

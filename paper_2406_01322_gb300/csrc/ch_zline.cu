@@ -27,7 +27,13 @@
 //   for op in {0: D^2-(k^2+beta) Dirichlet, 1: D^2-k^2 Dirichlet, 2: D^2-(k^2+lam) Neumann}
 //     Y[op][n][K], RD[op][n][K] (1/pivot), Q[op][n][K]  (n = 0..N, both parities interleaved)
 //     rsq[op][p][K] = 1 / (boundary-row sum of Q for parity p)
-//   Oh[n][K]  homogeneous Omega_h of the w problem, rsh[p][K] = 1 / sum_n n^2 Oh (parity p).
+//   Oh[n][K]  homogeneous Omega_h of the w problem, rsh[p][K] = 1 / sum_n n^2 Oh (parity p);
+//   then op 3: D^2-(k^2+beta) Neumann (omega_z and the mean flow between free-slip walls), its
+//   Y, RD, Q and rsq, and rsh2[p][K] = 1 / sum_n T_n''(1) Oh (parity p), appended after rsh so
+//   that the offsets above do not depend on them.
+// Free-slip walls (g.bc = 1): omega_z and the mean flow take Neumann rows (op 3); the w problem
+// keeps its influence-matrix form with the wall rows w = w'' = 0 (the correction fixes w''
+// instead of w', weights T_n''(1) = n^2 (n^2 - 1) / 3 and rsh2).
 //
 // All arithmetic in this file is float64.
 #include "ch_internal.h"
@@ -40,14 +46,32 @@ constexpr int ZT = 128;   // threads of a per-line CTA
 constexpr int NBF = 4;    // DCT lines transformed per FFT call (one warp each for scans)
 constexpr int NLINES = 16;
 
+// offsets of the table parts (op 3 sits after the influence-matrix columns)
+__host__ __device__ __forceinline__ size_t fac_arr_off(const GridDev& g, int op, int arr) {
+  return op < 3 ? (size_t)(op * 3 + arr) * g.nz * g.NK
+                : ((size_t)10 * g.nz + 8) * g.NK + (size_t)arr * g.nz * g.NK;
+}
+__host__ __device__ __forceinline__ size_t fac_rsq_off(const GridDev& g, int op, int p) {
+  return op < 3 ? (size_t)9 * g.nz * g.NK + (size_t)(op * 2 + p) * g.NK
+                : ((size_t)13 * g.nz + 8) * g.NK + (size_t)p * g.NK;
+}
 __device__ __forceinline__ const double* fac_ptr(const GridDev& g, int op, int arr, int K) {
-  return g.fac + ((size_t)(op * 3 + arr) * g.nz) * g.NK + K;
+  return g.fac + fac_arr_off(g, op, arr) + K;
 }
 __device__ __forceinline__ double fac_rsq(const GridDev& g, int op, int p, int K) {
-  return g.fac[(size_t)9 * g.nz * g.NK + (size_t)(op * 2 + p) * g.NK + K];
+  return g.fac[fac_rsq_off(g, op, p) + K];
 }
 __device__ __forceinline__ const double* fac_oh(const GridDev& g, int K) {
   return g.fac + (size_t)9 * g.nz * g.NK + (size_t)6 * g.NK + K;
+}
+// 1 / sum_n T_n''(1) Oh_n over parity p (free-slip: the correction fixes w'' at the walls)
+__device__ __forceinline__ double fac_rsh2(const GridDev& g, int p, int K) {
+  return g.fac[((size_t)13 * g.nz + 10) * g.NK + (size_t)p * g.NK + K];
+}
+// influence-correction weight of coefficient n: T_n'(1) = n^2 (no-slip), T_n''(1) (free-slip)
+__device__ __forceinline__ double infl_weight(int bc, int n) {
+  const double n2 = (double)n * (double)n;
+  return bc == 1 ? n2 * (n2 - 1.0) * (1.0 / 3.0) : n2;
 }
 __device__ __forceinline__ double fac_rsh(const GridDev& g, int p, int K) {
   return g.fac[(size_t)10 * g.nz * g.NK + (size_t)6 * g.NK + (size_t)p * g.NK + K];
@@ -450,11 +474,15 @@ __device__ __forceinline__ void zsolve_body(const GridDev& g, double2* __restric
   const double* t1 = g.go1;
   const double* t2 = g.go2;
   const double* t3 = g.go3;
-  // omega (or the mean flow on the (0,0) line): (D^2 - k^2 - beta) Q = r, Dirichlet
+  // omega (or the mean flow on the (0,0) line): (D^2 - k^2 - beta) Q = r, Dirichlet rows
+  // (no-slip) or Neumann rows (free-slip, op 3)
+  const bool fsl = (g.bc == 1);
+  const int oo = fsl ? 3 : 0;
   double2* row = R + (size_t)line * Nz;
-  tau_sweep_c(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K), fac_ptr(g, 0, 1, K),
-              fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
-  // w: influence problem (theta, w) with w = w' = 0 at both walls
+  tau_sweep_c(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K), fac_ptr(g, oo, 1, K),
+              fac_ptr(g, oo, 2, K), g.NK, fac_rsq(g, oo, p, K));
+  // w: influence problem (theta, w) with w = w' = 0 at both walls, or (free-slip) theta and w
+  // each with Dirichlet rows
   row = R + fs + (size_t)line * Nz;
   if (is00) {
     for (int n = p; n <= N; n += 2) row[n] = make_double2(0.0, 0.0);
@@ -463,16 +491,19 @@ __device__ __forceinline__ void zsolve_body(const GridDev& g, double2* __restric
                 fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
     tau_sweep_c(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K), fac_ptr(g, 1, 1, K),
                 fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
-    // Omega = Omega_p + c Omega_h with D Omega(+-1) = 0 (parity p)
+  }
+  if (!is00) {
+    // Omega = Omega_p + c Omega_h with D Omega(+-1) = 0 (no-slip) or D^2 Omega(+-1) = 0
+    // (free-slip), parity p
     const double* oh = fac_oh(g, K);
     double2 sacc = make_double2(0.0, 0.0);
     for (int n = p; n <= N; n += 2) {
-      const double n2 = (double)n * (double)n;
+      const double n2 = infl_weight(g.bc, n);
       const double2 v = row[n];
       sacc.x = fma(n2, v.x, sacc.x);
       sacc.y = fma(n2, v.y, sacc.y);
     }
-    const double rsh = fac_rsh(g, p, K);
+    const double rsh = fsl ? fac_rsh2(g, p, K) : fac_rsh(g, p, K);
     const double2 c = make_double2(-sacc.x * rsh, -sacc.y * rsh);
     for (int n = p; n <= N; n += 2) {
       const double h = oh[(size_t)n * g.NK];
@@ -533,8 +564,10 @@ __device__ __forceinline__ void zsolve_tile_body(const GridDev& g, double2* __re
     if (valid) {
       double2* row = tile + l * Nz;
       if (prob == 0) {
-        tau_sweep_c(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
-                    fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
+        const bool fsl = (g.bc == 1);     // free-slip: Neumann rows (op 3)
+        const int oo = fsl ? 3 : 0;
+        tau_sweep_c(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K),
+                    fac_ptr(g, oo, 1, K), fac_ptr(g, oo, 2, K), g.NK, fac_rsq(g, oo, p, K));
       } else if (prob == 1) {
         if (is00) {
           for (int n = p; n <= N; n += 2) row[n] = make_double2(0.0, 0.0);
@@ -543,15 +576,18 @@ __device__ __forceinline__ void zsolve_tile_body(const GridDev& g, double2* __re
                       fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
           tau_sweep_c(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K),
                       fac_ptr(g, 1, 1, K), fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
-          // influence matrix: Omega = Omega_p + c Omega_h with D Omega(+-1) = 0 (parity p)
+        }
+        if (!is00) {
+          // influence matrix: Omega = Omega_p + c Omega_h with D Omega(+-1) = 0 (no-slip) or
+          // D^2 Omega(+-1) = 0 (free-slip), parity p
           const double* oh = fac_oh(g, K);
           double2 s = make_double2(0.0, 0.0);
           for (int n = p; n <= N; n += 2) {
-            const double n2 = (double)n * (double)n;
+            const double n2 = infl_weight(g.bc, n);
             s.x = fma(n2, row[n].x, s.x);
             s.y = fma(n2, row[n].y, s.y);
           }
-          const double rsh = fac_rsh(g, p, K);
+          const double rsh = g.bc == 1 ? fac_rsh2(g, p, K) : fac_rsh(g, p, K);
           const double2 c = make_double2(-s.x * rsh, -s.y * rsh);
           for (int n = p; n <= N; n += 2) {
             const double h = oh[(size_t)n * g.NK];
@@ -592,16 +628,16 @@ __device__ __forceinline__ void K_wavenumbers(const GridDev& g, int K, double& k
 // closes the system at n = p
 __global__ void factor_kernel(GridDev g, double* __restrict__ fac) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.NK * 6) return;
-  const int K = t / 6, op = (t % 6) >> 1, p = t & 1;
+  if (t >= g.NK * 8) return;
+  const int K = t / 8, op = (t % 8) >> 1, p = t & 1;
   double k2;
   K_wavenumbers(g, K, k2);
-  const double alpha = (op == 0) ? k2 + g.beta : (op == 1) ? k2 : k2 + g.lam;
-  const bool neumann = (op == 2);
-  const int N = g.N, NK = g.NK, Nz = g.nz;
-  double* Y = fac + ((size_t)(op * 3 + 0) * Nz) * NK + K;
-  double* RD = fac + ((size_t)(op * 3 + 1) * Nz) * NK + K;
-  double* Q = fac + ((size_t)(op * 3 + 2) * Nz) * NK + K;
+  const double alpha = (op == 0 || op == 3) ? k2 + g.beta : (op == 1) ? k2 : k2 + g.lam;
+  const bool neumann = (op >= 2);
+  const int N = g.N, NK = g.NK;
+  double* Y = fac + fac_arr_off(g, op, 0) + K;
+  double* RD = fac + fac_arr_off(g, op, 1) + K;
+  double* Q = fac + fac_arr_off(g, op, 2) + K;
   const int I = (N - p) / 2;
   double ynext = 0.0;
   for (int i = I; i >= 1; --i) {
@@ -626,7 +662,7 @@ __global__ void factor_kernel(GridDev g, double* __restrict__ fac) {
     Q[(size_t)n * NK] = q;
     sq = fma(neumann ? (double)n * (double)n : 1.0, q, sq);
   }
-  fac[(size_t)9 * Nz * NK + (size_t)(op * 2 + p) * NK + K] = 1.0 / sq;
+  fac[fac_rsq_off(g, op, p) + K] = 1.0 / sq;
 }
 
 // thread = (K, parity): Psi_h = Q_0 / SQ_0 (operator 0 with unit wall value), then
@@ -669,15 +705,18 @@ __global__ void homog_kernel(GridDev g, double* __restrict__ fac) {
   }
   const double a0 = -sp * rsq;
   oh[(size_t)p * NK] = a0;
-  double sh = 0.0;
+  double sh = 0.0, sh2 = 0.0;
   for (int i = 0; i <= I; ++i) {
     const int n = p + 2 * i;
     double v = oh[(size_t)n * NK];
     if (i > 0) v = fma(Q[(size_t)n * NK], a0, v);
     oh[(size_t)n * NK] = v;
-    sh = fma((double)n * (double)n, v, sh);
+    const double n2 = (double)n * (double)n;
+    sh = fma(n2, v, sh);
+    sh2 = fma(n2 * (n2 - 1.0) * (1.0 / 3.0), v, sh2);
   }
   fac[(size_t)10 * Nz * NK + (size_t)6 * NK + (size_t)p * NK + K] = (sh != 0.0) ? 1.0 / sh : 0.0;
+  fac[((size_t)13 * Nz + 10) * NK + (size_t)p * NK + K] = (sh2 != 0.0) ? 1.0 / sh2 : 0.0;
 }
 
 // ---- zbwd: update + the fields for the non-linear terms ------------------------------------
@@ -1581,10 +1620,10 @@ size_t zline_smem(const GridDev& g) {
          (size_t)(ZT / 32) * (g.N / 2 + 2) * sizeof(double);
 }
 
-size_t fac_doubles(const GridDev& g) { return ((size_t)10 * g.nz + 8) * g.NK; }
+size_t fac_doubles(const GridDev& g) { return ((size_t)13 * g.nz + 12) * g.NK; }
 
 cudaError_t build_factor_table(const GridDev& g, double* fac, cudaStream_t s) {
-  const int n1 = g.NK * 6, n2 = g.NK * 2;
+  const int n1 = g.NK * 8, n2 = g.NK * 2;
   factor_kernel<<<(n1 + 127) / 128, 128, 0, s>>>(g, fac);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -64,14 +64,21 @@ def grid(nx, ny, nz, lx=4.0 * math.pi, ly=2.0 * math.pi):
     return x, y, z
 
 
-def perturbation(nx, ny, nz, seed, amp=0.1, kmax=4, lx=4.0 * math.pi, ly=2.0 * math.pi):
-    """Divergence-free, no-slip velocity perturbation (u, v, w), each (nz, ny, nx)."""
+def perturbation(nx, ny, nz, seed, amp=0.1, kmax=4, lx=4.0 * math.pi, ly=2.0 * math.pi, bc=0):
+    """Divergence-free velocity perturbation (u, v, w), each (nz, ny, nx), meeting the wall
+    conditions: no-slip (bc = 0) or free-slip (bc = 1: w profile (1-z^2)^3, whose value and
+    second derivative vanish at the walls; vortical profile (1-z^2)^2, zero wall derivative)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     x, y, z = grid(nx, ny, nz, lx, ly)
     Z = z[:, None, None]
-    f = (1.0 - Z * Z) ** 2              # w profile: f(+-1) = f'(+-1) = 0
-    fp = -4.0 * Z * (1.0 - Z * Z)       # f'
-    g = 1.0 - Z * Z                     # vortical profile: g(+-1) = 0
+    if bc == 1:
+        f = (1.0 - Z * Z) ** 3          # w profile: f(+-1) = f''(+-1) = 0
+        fp = -6.0 * Z * (1.0 - Z * Z) ** 2
+        g = (1.0 - Z * Z) ** 2          # vortical profile: g'(+-1) = 0
+    else:
+        f = (1.0 - Z * Z) ** 2          # w profile: f(+-1) = f'(+-1) = 0
+        fp = -4.0 * Z * (1.0 - Z * Z)   # f'
+        g = 1.0 - Z * Z                 # vortical profile: g(+-1) = 0
     u = np.zeros((nz, ny, nx))
     v = np.zeros((nz, ny, nx))
     w = np.zeros((nz, ny, nx))
@@ -147,11 +154,13 @@ def drops(nx, ny, nz, ndrops, radius, ch, seed, lx=4.0 * math.pi, ly=2.0 * math.
 
 
 def initial_fields(nx, ny, nz, re_tau, ch, ndrops, radius, seed, amp=0.1,
-                   lx=4.0 * math.pi, ly=2.0 * math.pi, **_):
-    """(u, v, w, phi) initial condition of the recipe above, each (nz, ny, nx) float64."""
+                   lx=4.0 * math.pi, ly=2.0 * math.pi, bc=0, **_):
+    """(u, v, w, phi) initial condition of the recipe above, each (nz, ny, nx) float64.  With
+    free-slip walls (bc = 1) the mean profile is (Re/2)(1 - z^2)^2 (zero wall derivative)."""
     _, _, z = grid(nx, ny, nz, lx, ly)
-    u, v, w = perturbation(nx, ny, nz, seed, amp=amp, lx=lx, ly=ly)
-    u = u + (0.5 * re_tau * (1.0 - z * z))[:, None, None]
+    u, v, w = perturbation(nx, ny, nz, seed, amp=amp, lx=lx, ly=ly, bc=bc)
+    base = (1.0 - z * z) ** 2 if bc == 1 else 1.0 - z * z
+    u = u + (0.5 * re_tau * base)[:, None, None]
     phi = drops(nx, ny, nz, ndrops, radius, ch, seed, lx, ly)
     return u, v, w, phi
 

@@ -41,9 +41,10 @@ def phys_kw(w):
 def make_pair(binding, w, precision=0, fields=None):
     if fields is None:
         fields = inputs.initial_fields(**w)
-    g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=precision, **phys_kw(w))
+    bc = w.get("bc", 0)
+    g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=precision, bc=bc, **phys_kw(w))
     g.set_fields(*[torch.from_numpy(f) for f in fields])
-    o = Channel(Params(nx=w["nx"], ny=w["ny"], nz=w["nz"], **phys_kw(w)))
+    o = Channel(Params(nx=w["nx"], ny=w["ny"], nz=w["nz"], bc=bc, **phys_kw(w)))
     o.set_fields(*fields)
     return g, o
 
@@ -219,6 +220,43 @@ def test_dfloat_ten_steps_within_1e_10(binding, name, over):
         o.step()
     for a, b, f in zip(g.get_fields(), o.get_fields(), "uvwp"):
         assert rel(a.cpu().numpy(), b) <= 1e-10, f
+
+
+FREE_SLIP = [("channel_32x32x33", dict(bc=1)),
+             ("channel_32x32x33", dict(nx=24, ny=18, nz=17, bc=1))]
+
+
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "dfloat"])
+@pytest.mark.parametrize("name,over", FREE_SLIP)
+def test_free_slip_ten_steps_within_1e_10(binding, name, over, precision):
+    """Free-slip walls (bc = 1) from admissible free-slip fields: 10 steps against the oracle."""
+    w = workload(name, **over)
+    g, o = make_pair(binding, w, precision)
+    g.step(10)
+    for _ in range(10):
+        o.step()
+    for a, b, f in zip(g.get_fields(), o.get_fields(), "uvwp"):
+        assert rel(a.cpu().numpy(), b) <= 1e-10, f
+
+
+def test_free_slip_uniform_flow_accelerates_by_gx_dt(binding):
+    nx, ny, nz = 16, 8, 17
+    dt, U0, n = 2e-3, 3.0, 10
+    g = binding.Grid(nx, ny, nz, re_tau=50.0, dt=dt, gx=1.0, bc=binding.BC_FREE_SLIP)
+    zero = torch.zeros((nz, ny, nx), dtype=torch.float64)
+    g.set_fields(zero + U0, zero, zero, zero - 1.0)
+    g.step(n)
+    u, v, ww, _ = [t.cpu() for t in g.get_fields()]
+    assert float((u - (U0 + n * dt)).abs().max()) < 1e-12
+    assert float(v.abs().max()) < 1e-14 and float(ww.abs().max()) < 1e-14
+
+
+def test_free_slip_rejected_by_the_adjoint(binding):
+    w = workload("channel_32x32x33", nx=16, ny=8, nz=17, bc=1)
+    g, _ = make_pair(binding, w)
+    with pytest.raises(binding.ChError) as e:
+        g.adjoint_begin()
+    assert e.value.code == -1
 
 
 def test_mixed_precision_error_bounds(binding):

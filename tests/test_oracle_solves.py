@@ -113,3 +113,40 @@ def test_influence_pair_wall_conditions():
     scale = np.max(np.abs(w))
     assert abs(np.sum(w)) < 1e-13 * scale and abs(np.sum(sgn * w)) < 1e-13 * scale
     assert abs(np.sum(n * n * w)) < 1e-11 * scale and abs(np.sum(sgn * n * n * w)) < 1e-11 * scale
+
+
+@pytest.mark.parametrize("N,k2,beta", [(16, 0.25, 10.0), (32, 1.25, 3.0e6), (128, 4.0, 6.0e6)])
+def test_free_slip_pair_manufactured(N, k2, beta):
+    """Free-slip walls (Sec. 2.1): w = (1 - z^2)^3 q has w = w'' = 0 at both walls; the
+    (theta, w) solve must return it exactly."""
+    rng = np.random.default_rng(N + 5)
+    q = rng.standard_normal(N - 5) / np.arange(1, N - 4) ** 2       # degree N-6
+    w = pad(npc.chebmul(npc.chebpow(one_minus_z2(), 3), q), N)
+    theta = pad(npc.chebder(w, 2), N) - k2 * w
+    r = pad(npc.chebder(theta, 2), N) - (k2 + beta) * theta
+    th_got, w_got = cheb.solve_coupled_w(r, k2, beta, "free-slip")
+    # the w'' wall rows carry entries up to N^4 / 3 (the no-slip w' rows: N^2), a factor ~N^2
+    # more rounding in the dense solve
+    assert np.max(np.abs(w_got - w)) < 1e-13 * np.max(np.abs(w)) * max(1, N * N / 64)
+    # theta is fixed only through the wall curvature of the thin homogeneous solutions (width
+    # 1/sqrt(beta)), seen through rows of size N^4/3: rounding O(eps N^4 sqrt(beta)); w stays exact
+    bound = 4 * np.finfo(float).eps * N ** 4 / 3 * math.sqrt(beta) * np.max(np.abs(theta))
+    assert np.max(np.abs(th_got - theta)) < max(bound, 1e-12 * np.max(np.abs(theta)))
+
+
+def test_free_slip_pair_wall_conditions():
+    # Arbitrary forcing: w(+-1) = 0 and w''(+-1) = 0 (T_n''(+-1) = (+-1)^n n^2 (n^2 - 1) / 3).
+    N = 48
+    r = np.random.default_rng(19).standard_normal(N + 1)
+    _, w = cheb.solve_coupled_w(r, 2.0, 1.0e4, "free-slip")
+    n = np.arange(N + 1, dtype=float)
+    sgn = (-1.0) ** n
+    t2 = n * n * (n * n - 1) / 3
+    scale = np.max(np.abs(w))
+    assert abs(np.sum(w)) < 1e-13 * scale and abs(np.sum(sgn * w)) < 1e-13 * scale
+    assert abs(np.sum(t2 * w)) < 1e-9 * scale and abs(np.sum(sgn * t2 * w)) < 1e-9 * scale
+    # the second derivative at the walls from the coefficients directly (numpy.polynomial)
+    d2 = npc.chebder(w, 2)
+    assert abs(npc.chebval(1.0, d2)) < 1e-9 * scale and abs(npc.chebval(-1.0, d2)) < 1e-9 * scale
+    # the no-slip rows would leave w' nonzero here: the two wall sets differ
+    assert abs(np.sum(n * n * w)) > 1e-6 * scale

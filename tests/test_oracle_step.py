@@ -329,3 +329,73 @@ def test_diagnostics_closed_forms():
     assert math.isclose(d["kinetic"], 0.5 * area * (p.re_tau / 2) ** 2 * 16 / 15, rel_tol=1e-13)
     assert d["grad2"] < 1e-20 and d["nan"] == 0
     assert math.isclose(d["free_energy"], 0.25 * (0.25 ** 2 - 1) ** 2 * 2 * area, rel_tol=1e-13)
+
+
+def test_free_slip_vorticity_mode_decays_at_crank_nicolson_rate():
+    # free-slip walls (d omega_z / dz = 0): omega_z = eps sin(pi z / 2) cos(kx x) is a Stokes
+    # eigenmode with sigma = (kx^2 + pi^2/4) / Re.
+    p = Params(nx=8, ny=4, nz=33, re_tau=50.0, dt=2e-3, gx=0.0, bc=1)
+    c = Channel(p)
+    X, Y, Z = grid(p)
+    kx = 2 * math.pi / p.lx
+    eps = 1e-9
+    v = eps * np.sin(0.5 * math.pi * Z) * np.sin(kx * X) / kx + zeros(p)
+    c.set_fields(zeros(p), v, zeros(p), zeros(p) - 1.0)
+    a0 = c.omega[:, 0, 1].copy()
+    sigma = (kx * kx + 0.25 * math.pi ** 2) / p.re_tau
+    g = (1 - 0.5 * p.dt * sigma) / (1 + 0.5 * p.dt * sigma)
+    n = 20
+    for _ in range(n):
+        c.step()
+    assert np.max(np.abs(c.omega[:, 0, 1] - g ** n * a0)) < 1e-7 * np.max(np.abs(a0))
+
+
+def test_free_slip_wall_normal_mode_decays_at_crank_nicolson_rate():
+    # free-slip walls (w = w'' = 0): w = eps cos(pi z / 2) cos(kx x) is a Stokes eigenmode of
+    # lap(w) with sigma = (kx^2 + pi^2/4) / Re (no boundary layer, unlike the no-slip mode).
+    p = Params(nx=8, ny=4, nz=33, re_tau=50.0, dt=2e-3, gx=0.0, bc=1)
+    c = Channel(p)
+    X, Y, Z = grid(p)
+    k = 2 * math.pi / p.lx
+    eps = 1e-9
+    w = eps * np.cos(0.5 * math.pi * Z) * np.cos(k * X) + zeros(p)
+    u = eps * 0.5 * math.pi * np.sin(0.5 * math.pi * Z) * np.sin(k * X) / k + zeros(p)
+    c.set_fields(u, zeros(p), w, zeros(p) - 1.0)
+    a0 = c.w[:, 0, 1].copy()
+    sigma = (k * k + 0.25 * math.pi ** 2) / p.re_tau
+    g = (1 - 0.5 * p.dt * sigma) / (1 + 0.5 * p.dt * sigma)
+    n = 20
+    for _ in range(n):
+        c.step()
+    assert np.max(np.abs(c.w[:, 0, 1] - g ** n * a0)) < 1e-7 * np.max(np.abs(a0))
+
+
+def test_free_slip_uniform_flow_accelerates_by_gx_dt():
+    # no wall stress: a uniform streamwise flow gains exactly gx dt per step (the CN step of
+    # dU/dt = gx + U''/Re with U'' = 0 and U' = 0 at the walls)
+    p = Params(nx=8, ny=4, nz=17, re_tau=50.0, dt=2e-3, gx=1.0, bc=1)
+    c = Channel(p)
+    U0 = 3.0
+    c.set_fields(zeros(p) + U0, zeros(p), zeros(p), zeros(p) - 1.0)
+    n = 10
+    for _ in range(n):
+        c.step()
+    u, v, w, _ = c.get_fields()
+    assert np.max(np.abs(u - (U0 + n * p.dt * p.gx))) < 1e-12
+    assert np.max(np.abs(v)) < 1e-14 and np.max(np.abs(w)) < 1e-14
+
+
+def test_free_slip_mean_shear_decays_at_crank_nicolson_rate():
+    # U = eps cos(pi z) (U' = 0 at the walls) decays with sigma = pi^2 / Re
+    p = Params(nx=8, ny=4, nz=33, re_tau=50.0, dt=2e-3, gx=0.0, bc=1)
+    c = Channel(p)
+    X, Y, Z = grid(p)
+    eps = 1e-9
+    c.set_fields(eps * np.cos(math.pi * Z) + zeros(p), zeros(p), zeros(p), zeros(p) - 1.0)
+    a0 = c.omega[:, 0, 0].real.copy()
+    sigma = math.pi ** 2 / p.re_tau
+    g = (1 - 0.5 * p.dt * sigma) / (1 + 0.5 * p.dt * sigma)
+    n = 20
+    for _ in range(n):
+        c.step()
+    assert np.max(np.abs(c.omega[:, 0, 0].real - g ** n * a0)) < 1e-7 * np.max(np.abs(a0))
