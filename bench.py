@@ -38,6 +38,36 @@ UNIT = "Mpoints*step/s"
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 DFMA per clock per SM (recipe: 1.25 TF/s)
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, MB) of kernels of the
+# current build from one ncu capture each (128 x 128 x 129 workloads, steady-state launches);
+# absent entries report null.  Re-capture when a kernel changes.
+TRAFFIC_MB = {
+    ("channel_128x128x129", 0, "xline"): 153.0 + 186.1,
+    ("channel_128x128x129", 0, "zrhs"): 251.7 + 75.9,
+    ("channel_128x128x129", 0, "yfwd"): 228.4 + 128.6,
+    ("channel_128x128x129", 0, "ybwd"): 84.7 + 135.0,
+    ("channel_128x128x129", 0, "zsolve"): 93.4 + 8.5,
+    ("channel_128x128x129", 1, "zrhs"): 176.2 + 69.6,
+    ("channel_128x128x129", 1, "xline"): 76.6 + 75.6,
+    ("channel_128x128x129", 1, "yfwd"): 114.2 + 80.1,
+    ("channel_128x128x129", 1, "ybwd"): 42.1 + 90.8,
+    ("channel_128x128x129", 1, "zsolve"): 93.4 + 8.5,
+    ("channel_128x128x129", 2, "zrhs"): 251.7 + 75.8,
+    ("channel_128x128x129", 2, "xline"): 153.3 + 192.1,
+    ("channel_128x128x129", 2, "yfwd"): 228.4 + 129.0,
+    ("channel_128x128x129", 2, "ybwd"): 84.7 + 134.8,
+    ("channel_128x128x129", 2, "zsolve"): 93.5 + 8.8,
+    ("channel_128x128x129_adjoint", 0, "adj_xline"): 380.8 + 134.1,
+    ("channel_128x128x129_adjoint", 0, "adj_zrhs"): 135.1 + 241.3,
+    ("channel_128x128x129_adjoint", 0, "adj_zsolve"): 102.7 + 29.1,
+}
+
+
+def traffic_bytes(workload, prec, kernel):
+    v = TRAFFIC_MB.get((workload, prec, kernel))
+    return None if v is None else v * 1e6
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -502,7 +532,8 @@ def run_adjoint(args):
     fl, by = work[names[k]]
     ach = fl / (per_launch_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": names[k],
+            "frac": ach / FP64_PEAK_TFLOPS,
+            "traffic": traffic_bytes(args.workload, 0, names[k]), "kernel": names[k],
             "peak_kind": "float64 FMA pipe: 152 SMs x 2.07 GHz x 4 flop/clk (nominal)",
             "kernel_share": {n: kms[i] / sum(kms) for i, n in enumerate(names)},
             "kernel_ms_per_reverse_step": {n: kms[i] / nsteps for i, n in enumerate(names)}}
@@ -622,12 +653,14 @@ def main():
     if fp64_like:
         ach = fl / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": name,
+                "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": traffic_bytes(args.workload, prec, name), "kernel": name,
                 "peak_kind": "float64 FMA pipe: 152 SMs x 2.07 GHz x 4 flop/clk (nominal)"}
     else:
         ach = by / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": name, "peak_kind": f"{hbm_kind} copy bandwidth"}
+                "traffic": traffic_bytes(args.workload, prec, name), "kernel": name,
+                "peak_kind": f"{hbm_kind} copy bandwidth"}
     roof["kernel_share"] = {n: kms[i] / sum(kms) for i, n in enumerate(names)}
     roof["kernel_ms_per_step"] = {n: kms[i] / args.steps for i, n in enumerate(names)}
     roof["hbm_frac_step"] = (sum(v[1] for v in work.values()) / (ms_step * 1e-3) / 1e9) / hbm
