@@ -72,9 +72,11 @@ typedef struct {
   double gx, gy;      /* mean pressure gradient -dp/dx, -dp/dy driving the mean flow       */
   int precision;      /* CH_PREC_FP64, CH_PREC_MIXED or CH_PREC_DFLOAT (single grids only)   */
   int dealias_z;      /* must be 0: no padding of the Chebyshev direction                  */
-  int bc;             /* walls (Sec. 2.1: no-slip or free-slip): 0 no-slip (u = v = w =
-                         dw/dz = 0), 1 free-slip (du/dz = dv/dz = 0, w = 0, d2w/dz2 = 0) at both
-                         walls; phi no-flux in both.  Other values: CH_ERR_ARG             */
+  int bc;             /* walls (Sec. 2.1: no-slip, free-slip or a combination): 0 no-slip
+                         (u = v = w = dw/dz = 0) at both walls, 1 free-slip (du/dz = dv/dz = 0,
+                         w = 0, d2w/dz2 = 0) at both, 2 no-slip at z = -1 and free-slip at
+                         z = +1, 3 free-slip at z = -1 and no-slip at z = +1; phi no-flux at
+                         both.  Other values: CH_ERR_ARG                                  */
 } ch_params;
 
 typedef void* (*ch_alloc_fn)(size_t bytes, void* ctx);

@@ -41,8 +41,8 @@ R10 Chebyshev-tau with the Gottlieb-Orszag rows (``oracle.chebyshev``).
 R13 Free-slip walls (Params.bc = 1; Sec. 2.1 allows no-slip or free-slip at the walls; the same
     condition at both walls): du/dz = dv/dz = 0 and w = 0, so d omega_z/dz = 0 and the mean flow
     takes Neumann rows; continuity then gives d2w/dz2 = 0, and the (theta, w) pair takes its four
-    wall rows on w (w = w'' = 0), as for no-slip (w = w' = 0).  A different condition on each
-    wall is not built.
+    wall rows on w (w = w'' = 0), as for no-slip (w = w' = 0).  Params.bc = 2 / 3 combine the two
+    (no-slip at z = -1 and free-slip at z = +1, or the reverse), each wall with its own rows.
 
 State: omega (Nz, Ny, Mx), w, phi complex Chebyshev x Fourier coefficients, [n, j(my), mx].
 """
@@ -53,6 +53,11 @@ import numpy as np
 
 from . import chebyshev as cheb
 from . import fourier
+
+
+# wall conditions by Params.bc: (z = +1, z = -1)
+WALLS = {0: ("no-slip", "no-slip"), 1: ("free-slip", "free-slip"),
+         2: ("free-slip", "no-slip"), 3: ("no-slip", "free-slip")}
 
 
 @dataclass
@@ -69,7 +74,8 @@ class Params:
     dt: float = 1e-4
     gx: float = 1.0
     gy: float = 0.0
-    bc: int = 0          # walls (Sec. 2.1): 0 no-slip, 1 free-slip (both walls)
+    bc: int = 0          # walls (Sec. 2.1): 0 no-slip, 1 free-slip (both walls), 2 no-slip at
+                         # z = -1 and free-slip at z = +1, 3 free-slip at z = -1, no-slip at +1
 
 
 class Channel:
@@ -230,13 +236,15 @@ class Channel:
     def solve_line(self, j, m, r_om, r_th, r_psi):
         """Solve the implicit problems of one (my, mx) line; returns (omega, w, phi)^{n+1}."""
         k2 = self.k2[j, m]
-        free = self.p.bc == 1
-        # omega_z and the mean flow: Dirichlet (no-slip) or Neumann (free-slip: du/dz = dv/dz = 0)
-        om = cheb.solve_helmholtz(r_om, k2 + self.beta, "neumann" if free else "dirichlet")
+        top, bottom = WALLS[self.p.bc]
+        # omega_z and the mean flow: Dirichlet at a no-slip wall, Neumann at a free-slip wall
+        # (du/dz = dv/dz = 0)
+        kind = {"no-slip": "dirichlet", "free-slip": "neumann"}
+        om = cheb.solve_helmholtz(r_om, k2 + self.beta, (kind[top], kind[bottom]))
         if j == 0 and m == 0:
             w = np.zeros_like(r_th)
         else:
-            _, w = cheb.solve_coupled_w(r_th, k2, self.beta, "free-slip" if free else "no-slip")
+            _, w = cheb.solve_coupled_w(r_th, k2, self.beta, (top, bottom))
         psi = cheb.solve_helmholtz(r_psi, k2 + self.lam, "neumann")
         ph = cheb.solve_helmholtz(psi, k2 + self.lam, "neumann")
         return om, w, ph

@@ -117,12 +117,19 @@ def bc_rows(N, bc):
     raise ValueError(bc)
 
 
+def wall_rows(N, top, bottom):
+    """Row 0: condition `top` at z = +1; row 1: condition `bottom` at z = -1; each one of
+    'dirichlet', 'neumann', 'second' (value, first or second derivative), as in ``bc_rows``."""
+    return np.stack([bc_rows(N, top)[0], bc_rows(N, bottom)[1]])
+
+
 def helmholtz_matrix(N, alpha, bc):
     """Dense tau matrix of (D^2 - alpha) a = f in Gottlieb-Orszag form.
 
-    Rows 0, 1: boundary conditions.  Rows n = 2..N: a_n - alpha (G a)_n = (G f)_n."""
+    Rows 0, 1: boundary conditions (bc: one kind for both walls, or a (top, bottom) pair).
+    Rows n = 2..N: a_n - alpha (G a)_n = (G f)_n."""
     M = np.eye(N + 1) - alpha * go_matrix(N)
-    M[0:2, :] = bc_rows(N, bc)
+    M[0:2, :] = wall_rows(N, *bc) if isinstance(bc, tuple) else bc_rows(N, bc)
     return M
 
 
@@ -149,7 +156,9 @@ def coupled_w_matrix(N, k2, beta, walls="no-slip"):
     (D^2 - k^2 - beta) theta = r   (tau rows 0..N-2)
     (D^2 - k^2) w = theta          (tau rows 0..N-2)
     no-slip:   w(+1) = w(-1) = 0, w'(+1) = w'(-1) = 0 (all four wall rows on w, Eq. (ww));
-    free-slip: w(+1) = w(-1) = 0, w''(+1) = w''(-1) = 0 (again all four on w).
+    free-slip: w(+1) = w(-1) = 0, w''(+1) = w''(-1) = 0 (again all four on w);
+    (top, bottom) pair of 'no-slip' / 'free-slip': w(+-1) = 0 and, at each wall, w' = 0
+    (no-slip) or w'' = 0 (free-slip).
     Both second-order problems are written in Gottlieb-Orszag form.  The walls are those of
     Sec. 2.1 (no-slip or free-slip).  Unknown vector = [theta_0..N, w_0..N]."""
     G = go_matrix(N)
@@ -162,14 +171,10 @@ def coupled_w_matrix(N, k2, beta, walls="no-slip"):
     # w rows n = 2..N:  w_n - k^2 (G w)_n - (G theta)_n = 0
     M[n1 + 2:2 * n1, n1:2 * n1] = (I - k2 * G)[rows]
     M[n1 + 2:2 * n1, 0:n1] = -G[rows]
-    if walls == "no-slip":                      # four wall rows on w
-        M[0:2, n1:2 * n1] = bc_rows(N, "dirichlet")
-        M[n1:n1 + 2, n1:2 * n1] = bc_rows(N, "neumann")
-    elif walls == "free-slip":                  # w and w'' vanish at both walls
-        M[0:2, n1:2 * n1] = bc_rows(N, "dirichlet")
-        M[n1:n1 + 2, n1:2 * n1] = bc_rows(N, "second")
-    else:
-        raise ValueError(walls)
+    kind = {"no-slip": "neumann", "free-slip": "second"}
+    top, bottom = walls if isinstance(walls, tuple) else (walls, walls)
+    M[0:2, n1:2 * n1] = bc_rows(N, "dirichlet")                 # w = 0 at both walls
+    M[n1:n1 + 2, n1:2 * n1] = wall_rows(N, kind[top], kind[bottom])
     return M
 
 

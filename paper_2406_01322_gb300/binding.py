@@ -22,6 +22,8 @@ PREC_MIXED = 1
 PREC_DFLOAT = 2
 BC_NO_SLIP = 0
 BC_FREE_SLIP = 1
+BC_NO_SLIP_BOTTOM_FREE_SLIP_TOP = 2
+BC_FREE_SLIP_BOTTOM_NO_SLIP_TOP = 3
 
 
 class ChError(RuntimeError):

@@ -261,7 +261,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
   if (p->precision != CH_PREC_FP64 && p->precision != CH_PREC_MIXED &&
       p->precision != CH_PREC_DFLOAT)
     return CH_ERR_ARG;
-  if (p->dealias_z != 0 || (p->bc != 0 && p->bc != 1)) return CH_ERR_ARG;
+  if (p->dealias_z != 0 || p->bc < 0 || p->bc > 3) return CH_ERR_ARG;
   if ((alloc == nullptr) != (free_fn == nullptr)) return CH_ERR_ARG;
   const int nx = p->nx, ny = p->ny, nz = p->nz;
   if (chf::check_sizes(nx, ny, nz) != CH_OK) return CH_ERR_SIZE;

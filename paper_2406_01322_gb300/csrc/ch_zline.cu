@@ -73,6 +73,39 @@ __device__ __forceinline__ double infl_weight(int bc, int n) {
   const double n2 = (double)n * (double)n;
   return bc == 1 ? n2 * (n2 - 1.0) * (1.0 / 3.0) : n2;
 }
+// Different walls (g.bc = 2: no-slip at z = -1, free-slip at z = +1; 3: the mirror).  The wall
+// rows no longer split into an even and an odd sum, so each parity chain leaves its lowest
+// coefficient a_p free and the two rows (top, bottom) close the line with a 2x2 system in
+// (a_0, a_1), exchanged between the two lanes of the line.  Tables per K (after rsh2):
+// mo[4] = inverse of [[sum_even top_n Q_n, sum_odd top_n Q_n], [.. bottom ..]] (omega_z and the
+// mean flow, op 0 factors), mw[4] = inverse of the same with the w-wall rows and Oh (w problem).
+__host__ __device__ __forceinline__ size_t fac_mixed_off(const GridDev& g, int i) {
+  return ((size_t)13 * g.nz + 12) * g.NK + (size_t)i * g.NK;
+}
+// wall rows at z = +1 (top) and z = -1 (bottom) of coefficient n for the mixed cases:
+// omega_z rows (value at a no-slip wall, slope at a free-slip wall)
+__device__ __forceinline__ double om_row(int bc, bool top, int n) {
+  const double n2 = (double)n * (double)n;
+  const double sgn = (n & 1) ? -1.0 : 1.0;            // T_n(-1)
+  const bool free_wall = top ? (bc == 2) : (bc == 3);
+  if (top) return free_wall ? n2 : 1.0;
+  return free_wall ? -sgn * n2 : sgn;                 // T_n'(-1) = (-1)^(n+1) n^2
+}
+// w rows (slope at a no-slip wall, curvature at a free-slip wall; w = 0 is in the sweeps)
+__device__ __forceinline__ double w_row(int bc, bool top, int n) {
+  const double n2 = (double)n * (double)n;
+  const double sgn = (n & 1) ? -1.0 : 1.0;
+  const bool free_wall = top ? (bc == 2) : (bc == 3);
+  const double d1 = top ? n2 : -sgn * n2;             // T_n'(+-1)
+  const double d2 = (top ? 1.0 : sgn) * n2 * (n2 - 1.0) * (1.0 / 3.0);   // T_n''(+-1)
+  return free_wall ? d2 : d1;
+}
+// sum of v over the two lanes (parities) of one line; pm = the pair's lane mask
+__device__ __forceinline__ double2 pair_sum(double2 v, unsigned pm) {
+  v.x += __shfl_xor_sync(pm, v.x, 1);
+  v.y += __shfl_xor_sync(pm, v.y, 1);
+  return v;
+}
 __device__ __forceinline__ double fac_rsh(const GridDev& g, int p, int K) {
   return g.fac[(size_t)10 * g.nz * g.NK + (size_t)6 * g.NK + (size_t)p * g.NK + K];
 }
@@ -453,6 +486,87 @@ __device__ void tau_sweep_c(double2* x, int p, int N, double alpha, bool neumann
   }
 }
 
+// Different walls: as tau_sweep_c (Dirichlet/Neumann flag unused) but closed by the two wall
+// rows of g.bc together with the partner lane's chain: a_p = -row p of minv . (top, bottom row
+// sums of P over both parities); minv points at the four inverse entries (stride NK).
+__device__ void tau_sweep_mixed(double2* __restrict__ x, int p, int N, double alpha, int bc,
+                                const double* __restrict__ t1, const double* __restrict__ t2,
+                                const double* __restrict__ t3, const double* __restrict__ Y,
+                                const double* __restrict__ RD, const double* __restrict__ Q,
+                                int NK, const double* __restrict__ minv, unsigned pm) {
+  const int I = (N - p) / 2;
+  double2 xn = make_double2(0.0, 0.0), fnp2 = make_double2(0.0, 0.0);
+  for (int i = I; i >= 1; --i) {
+    const int n = p + 2 * i;
+    const double2 fn = x[n];
+    const double2 fnm2 = x[n - 2];
+    const double a1 = t1[n], a2 = t2[n], a3 = t3[n];
+    const double U = -alpha * a3;
+    const double rd = RD[(size_t)n * NK];
+    double2 xi;
+    xi.x = fma(-U, xn.x, fma(a1, fnm2.x, fma(-a2, fn.x, a3 * fnp2.x))) * rd;
+    xi.y = fma(-U, xn.y, fma(a1, fnm2.y, fma(-a2, fn.y, a3 * fnp2.y))) * rd;
+    x[n] = xi;
+    fnp2 = fn;
+    xn = xi;
+  }
+  double2 P = make_double2(0.0, 0.0), st = P, sb = P;
+  for (int i = 1; i <= I; ++i) {
+    const int n = p + 2 * i;
+    const double y = Y[(size_t)n * NK];
+    const double2 xv = x[n];
+    P.x = fma(y, P.x, xv.x);
+    P.y = fma(y, P.y, xv.y);
+    x[n] = P;
+    const double bt = om_row(bc, true, n), bb = om_row(bc, false, n);
+    st.x = fma(bt, P.x, st.x);
+    st.y = fma(bt, P.y, st.y);
+    sb.x = fma(bb, P.x, sb.x);
+    sb.y = fma(bb, P.y, sb.y);
+  }
+  st = pair_sum(st, pm);
+  sb = pair_sum(sb, pm);
+  const double m0 = minv[(size_t)(2 * p) * NK], m1 = minv[(size_t)(2 * p + 1) * NK];
+  const double2 a0 = make_double2(-(m0 * st.x + m1 * sb.x), -(m0 * st.y + m1 * sb.y));
+  x[p] = a0;
+  for (int i = 1; i <= I; ++i) {
+    const int n = p + 2 * i;
+    const double q = Q[(size_t)n * NK];
+    double2 v = x[n];
+    v.x = fma(q, a0.x, v.x);
+    v.y = fma(q, a0.y, v.y);
+    x[n] = v;
+  }
+}
+
+// Different walls, w problem: Omega = Omega_p + c_0 Oh_even + c_1 Oh_odd with the top and bottom
+// w-wall rows zero (Omega_p holds w = 0 at both walls already); c from the 2x2 inverse mw.
+__device__ void w_correct_mixed(const GridDev& g, double2* __restrict__ row, int p, int K,
+                                unsigned pm) {
+  const int N = g.N;
+  const double* oh = fac_oh(g, K);
+  double2 rt = make_double2(0.0, 0.0), rb = rt;
+  for (int n = p; n <= N; n += 2) {
+    const double bt = w_row(g.bc, true, n), bb = w_row(g.bc, false, n);
+    rt.x = fma(bt, row[n].x, rt.x);
+    rt.y = fma(bt, row[n].y, rt.y);
+    rb.x = fma(bb, row[n].x, rb.x);
+    rb.y = fma(bb, row[n].y, rb.y);
+  }
+  rt = pair_sum(rt, pm);
+  rb = pair_sum(rb, pm);
+  const double* mw = g.fac + fac_mixed_off(g, 4) + K;
+  const double m0 = mw[(size_t)(2 * p) * g.NK], m1 = mw[(size_t)(2 * p + 1) * g.NK];
+  const double2 c = make_double2(-(m0 * rt.x + m1 * rb.x), -(m0 * rt.y + m1 * rb.y));
+  for (int n = p; n <= N; n += 2) {
+    const double h = oh[(size_t)n * g.NK];
+    double2 v = row[n];
+    v.x = fma(c.x, h, v.x);
+    v.y = fma(c.y, h, v.y);
+    row[n] = v;
+  }
+}
+
 // zsolve: one thread per (line, parity) elimination chain, sweeping in place on R in global
 // memory (line-major like the state).  The two chains of a line sit in adjacent lanes and touch
 // adjacent coefficients, so each warp access covers 16 lines x 32 bytes; a chain's half-line is
@@ -477,10 +591,17 @@ __device__ __forceinline__ void zsolve_body(const GridDev& g, double2* __restric
   // omega (or the mean flow on the (0,0) line): (D^2 - k^2 - beta) Q = r, Dirichlet rows
   // (no-slip) or Neumann rows (free-slip, op 3)
   const bool fsl = (g.bc == 1);
+  const bool mixed = (g.bc >= 2);                 // a different condition on each wall
+  const unsigned pm = 0x3u << (threadIdx.x & 30);  // the two lanes (parities) of this line
   const int oo = fsl ? 3 : 0;
   double2* row = R + (size_t)line * Nz;
-  tau_sweep_c(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K), fac_ptr(g, oo, 1, K),
-              fac_ptr(g, oo, 2, K), g.NK, fac_rsq(g, oo, p, K));
+  if (mixed)
+    tau_sweep_mixed(row, p, N, k2 + g.beta, g.bc, t1, t2, t3, fac_ptr(g, 0, 0, K),
+                    fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK,
+                    g.fac + fac_mixed_off(g, 0) + K, pm);
+  else
+    tau_sweep_c(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K),
+                fac_ptr(g, oo, 1, K), fac_ptr(g, oo, 2, K), g.NK, fac_rsq(g, oo, p, K));
   // w: influence problem (theta, w) with w = w' = 0 at both walls, or (free-slip) theta and w
   // each with Dirichlet rows
   row = R + fs + (size_t)line * Nz;
@@ -492,7 +613,9 @@ __device__ __forceinline__ void zsolve_body(const GridDev& g, double2* __restric
     tau_sweep_c(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K), fac_ptr(g, 1, 1, K),
                 fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
   }
-  if (!is00) {
+  if (!is00 && mixed) {
+    w_correct_mixed(g, row, p, K, pm);
+  } else if (!is00) {
     // Omega = Omega_p + c Omega_h with D Omega(+-1) = 0 (no-slip) or D^2 Omega(+-1) = 0
     // (free-slip), parity p
     const double* oh = fac_oh(g, K);
@@ -563,11 +686,17 @@ __device__ __forceinline__ void zsolve_tile_body(const GridDev& g, double2* __re
     __syncthreads();
     if (valid) {
       double2* row = tile + l * Nz;
+      const unsigned pm = 0x3u << (threadIdx.x & 30);  // the two lanes of this line
       if (prob == 0) {
         const bool fsl = (g.bc == 1);     // free-slip: Neumann rows (op 3)
         const int oo = fsl ? 3 : 0;
-        tau_sweep_c(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K),
-                    fac_ptr(g, oo, 1, K), fac_ptr(g, oo, 2, K), g.NK, fac_rsq(g, oo, p, K));
+        if (g.bc >= 2)                    // a different condition on each wall
+          tau_sweep_mixed(row, p, N, k2 + g.beta, g.bc, t1, t2, t3, fac_ptr(g, 0, 0, K),
+                          fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK,
+                          g.fac + fac_mixed_off(g, 0) + K, pm);
+        else
+          tau_sweep_c(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K),
+                      fac_ptr(g, oo, 1, K), fac_ptr(g, oo, 2, K), g.NK, fac_rsq(g, oo, p, K));
       } else if (prob == 1) {
         if (is00) {
           for (int n = p; n <= N; n += 2) row[n] = make_double2(0.0, 0.0);
@@ -577,7 +706,9 @@ __device__ __forceinline__ void zsolve_tile_body(const GridDev& g, double2* __re
           tau_sweep_c(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K),
                       fac_ptr(g, 1, 1, K), fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
         }
-        if (!is00) {
+        if (!is00 && g.bc >= 2) {
+          w_correct_mixed(g, row, p, K, pm);
+        } else if (!is00) {
           // influence matrix: Omega = Omega_p + c Omega_h with D Omega(+-1) = 0 (no-slip) or
           // D^2 Omega(+-1) = 0 (free-slip), parity p
           const double* oh = fac_oh(g, K);
@@ -717,6 +848,36 @@ __global__ void homog_kernel(GridDev g, double* __restrict__ fac) {
   }
   fac[(size_t)10 * Nz * NK + (size_t)6 * NK + (size_t)p * NK + K] = (sh != 0.0) ? 1.0 / sh : 0.0;
   fac[((size_t)13 * Nz + 10) * NK + (size_t)p * NK + K] = (sh2 != 0.0) ? 1.0 / sh2 : 0.0;
+}
+
+// thread = K: the 2x2 wall closures of the different-walls cases (inverses stored row-major)
+__device__ void store_inverse(double* out, size_t NK, double a, double b, double c, double d) {
+  const double det = a * d - b * c;
+  const double r = (det != 0.0) ? 1.0 / det : 0.0;
+  out[0] = d * r;
+  out[NK] = -b * r;
+  out[2 * NK] = -c * r;
+  out[3 * NK] = a * r;
+}
+
+__global__ void mixed_kernel(GridDev g, double* __restrict__ fac) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= g.NK) return;
+  const int N = g.N;
+  const size_t NK = g.NK;
+  const double* Q0 = fac + fac_arr_off(g, 0, 2) + K;       // Q_p = 1 at n = p
+  const double* oh = fac + (size_t)9 * g.nz * NK + (size_t)6 * NK + K;
+  double so[2][2] = {{0.0, 0.0}, {0.0, 0.0}}, sw[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int n = 0; n <= N; ++n) {
+    const int c = n & 1;
+    const double q = Q0[(size_t)n * NK], h = oh[(size_t)n * NK];
+    so[0][c] += om_row(g.bc, true, n) * q;
+    so[1][c] += om_row(g.bc, false, n) * q;
+    sw[0][c] += w_row(g.bc, true, n) * h;
+    sw[1][c] += w_row(g.bc, false, n) * h;
+  }
+  store_inverse(fac + fac_mixed_off(g, 0) + K, NK, so[0][0], so[0][1], so[1][0], so[1][1]);
+  store_inverse(fac + fac_mixed_off(g, 4) + K, NK, sw[0][0], sw[0][1], sw[1][0], sw[1][1]);
 }
 
 // ---- zbwd: update + the fields for the non-linear terms ------------------------------------
@@ -1620,14 +1781,18 @@ size_t zline_smem(const GridDev& g) {
          (size_t)(ZT / 32) * (g.N / 2 + 2) * sizeof(double);
 }
 
-size_t fac_doubles(const GridDev& g) { return ((size_t)13 * g.nz + 12) * g.NK; }
+size_t fac_doubles(const GridDev& g) { return ((size_t)13 * g.nz + 20) * g.NK; }
 
 cudaError_t build_factor_table(const GridDev& g, double* fac, cudaStream_t s) {
+  const int n3 = g.NK;
   const int n1 = g.NK * 8, n2 = g.NK * 2;
   factor_kernel<<<(n1 + 127) / 128, 128, 0, s>>>(g, fac);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   homog_kernel<<<(n2 + 127) / 128, 128, 0, s>>>(g, fac);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || g.bc < 2) return e;
+  mixed_kernel<<<(n3 + 127) / 128, 128, 0, s>>>(g, fac);
   return cudaGetLastError();
 }
 

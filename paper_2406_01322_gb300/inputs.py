@@ -64,21 +64,42 @@ def grid(nx, ny, nz, lx=4.0 * math.pi, ly=2.0 * math.pi):
     return x, y, z
 
 
+def wall_profiles(bc):
+    """(w profile f, vortical profile g) as polynomials in z meeting the wall conditions exactly:
+    w = 0 at both walls and w' = 0 at a no-slip wall, w'' = 0 at a free-slip wall (then u, v from
+    continuity, proportional to f', vanish at a no-slip wall and have zero slope at a free-slip
+    one); g = 0 at a no-slip wall, g' = 0 at a free-slip wall.  bc: 0 no-slip, 1 free-slip,
+    2 no-slip at z = -1 and free-slip at z = +1, 3 the mirror."""
+    P = np.polynomial.Polynomial
+    one_m, one_p = P([1.0, -1.0]), P([1.0, 1.0])       # 1 - z, 1 + z
+    if bc == 0:
+        return (one_m * one_p) ** 2, one_m * one_p
+    if bc == 1:
+        return (one_m * one_p) ** 3, (one_m * one_p) ** 2
+    if bc == 2:
+        return one_p ** 2 * one_m ** 3, one_p * P([3.0, -1.0])
+    if bc == 3:
+        return one_m ** 2 * one_p ** 3, one_m * P([3.0, 1.0])
+    raise ValueError(bc)
+
+
+def mean_profile(bc):
+    """Laminar-like mean profile with max 1: zero at no-slip walls, zero slope at free-slip ones."""
+    P = np.polynomial.Polynomial
+    return {0: P([1.0, 0.0, -1.0]), 1: P([1.0, 0.0, -2.0, 0.0, 1.0]),
+            2: P([3.0, 2.0, -1.0]) / 4.0, 3: P([3.0, -2.0, -1.0]) / 4.0}[bc]
+
+
 def perturbation(nx, ny, nz, seed, amp=0.1, kmax=4, lx=4.0 * math.pi, ly=2.0 * math.pi, bc=0):
     """Divergence-free velocity perturbation (u, v, w), each (nz, ny, nx), meeting the wall
-    conditions: no-slip (bc = 0) or free-slip (bc = 1: w profile (1-z^2)^3, whose value and
-    second derivative vanish at the walls; vortical profile (1-z^2)^2, zero wall derivative)."""
+    conditions of `bc` (see wall_profiles)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     x, y, z = grid(nx, ny, nz, lx, ly)
     Z = z[:, None, None]
-    if bc == 1:
-        f = (1.0 - Z * Z) ** 3          # w profile: f(+-1) = f''(+-1) = 0
-        fp = -6.0 * Z * (1.0 - Z * Z) ** 2
-        g = (1.0 - Z * Z) ** 2          # vortical profile: g'(+-1) = 0
-    else:
-        f = (1.0 - Z * Z) ** 2          # w profile: f(+-1) = f'(+-1) = 0
-        fp = -4.0 * Z * (1.0 - Z * Z)   # f'
-        g = 1.0 - Z * Z                 # vortical profile: g(+-1) = 0
+    fpoly, gpoly = wall_profiles(bc)
+    f = fpoly(Z)                        # w profile
+    fp = fpoly.deriv()(Z)               # f'
+    g = gpoly(Z)                        # vortical (u, v) profile
     u = np.zeros((nz, ny, nx))
     v = np.zeros((nz, ny, nx))
     w = np.zeros((nz, ny, nx))
@@ -155,12 +176,11 @@ def drops(nx, ny, nz, ndrops, radius, ch, seed, lx=4.0 * math.pi, ly=2.0 * math.
 
 def initial_fields(nx, ny, nz, re_tau, ch, ndrops, radius, seed, amp=0.1,
                    lx=4.0 * math.pi, ly=2.0 * math.pi, bc=0, **_):
-    """(u, v, w, phi) initial condition of the recipe above, each (nz, ny, nx) float64.  With
-    free-slip walls (bc = 1) the mean profile is (Re/2)(1 - z^2)^2 (zero wall derivative)."""
+    """(u, v, w, phi) initial condition of the recipe above, each (nz, ny, nx) float64.  Other
+    walls than no-slip (bc = 1, 2, 3) take the profiles of wall_profiles and mean_profile."""
     _, _, z = grid(nx, ny, nz, lx, ly)
     u, v, w = perturbation(nx, ny, nz, seed, amp=amp, lx=lx, ly=ly, bc=bc)
-    base = (1.0 - z * z) ** 2 if bc == 1 else 1.0 - z * z
-    u = u + (0.5 * re_tau * base)[:, None, None]
+    u = u + (0.5 * re_tau * mean_profile(bc)(z))[:, None, None]
     phi = drops(nx, ny, nz, ndrops, radius, ch, seed, lx, ly)
     return u, v, w, phi
 

@@ -110,11 +110,12 @@ def test_ensemble_rejects_double_float(binding):
 
 
 def test_ensemble_of_mixed_wall_conditions_matches_single_grids(binding):
-    """Members with no-slip and free-slip walls in one ensemble: each member's grouped solve
-    takes its own wall rows and matches the member stepped alone bitwise."""
+    """Members with the four wall cases (no-slip, free-slip, and the two combinations) in one
+    ensemble: each member's grouped solve takes its own wall rows and matches the member stepped
+    alone bitwise."""
     ms = members()
     for i, m in enumerate(ms):
-        m["bc"] = i % 2
+        m["bc"] = i % 4
     ens = binding.Ensemble(ms, precision=0)
     singles = [binding.Grid(precision=0, **m) for m in ms]
     for i, (g, s, m) in enumerate(zip(ens.grids, singles, ms)):

@@ -222,14 +222,15 @@ def test_dfloat_ten_steps_within_1e_10(binding, name, over):
         assert rel(a.cpu().numpy(), b) <= 1e-10, f
 
 
-FREE_SLIP = [("channel_32x32x33", dict(bc=1)),
-             ("channel_32x32x33", dict(nx=24, ny=18, nz=17, bc=1))]
+FREE_SLIP = [("channel_32x32x33", dict(bc=b)) for b in (1, 2, 3)] + \
+            [("channel_32x32x33", dict(nx=24, ny=18, nz=17, bc=b)) for b in (1, 2, 3)]
 
 
 @pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "dfloat"])
 @pytest.mark.parametrize("name,over", FREE_SLIP)
 def test_free_slip_ten_steps_within_1e_10(binding, name, over, precision):
-    """Free-slip walls (bc = 1) from admissible free-slip fields: 10 steps against the oracle."""
+    """Free-slip walls (bc = 1) and the two combinations (bc = 2, 3: no-slip at one wall,
+    free-slip at the other) from fields meeting those walls: 10 steps against the oracle."""
     w = workload(name, **over)
     g, o = make_pair(binding, w, precision)
     g.step(10)
@@ -249,6 +250,21 @@ def test_free_slip_uniform_flow_accelerates_by_gx_dt(binding):
     u, v, ww, _ = [t.cpu() for t in g.get_fields()]
     assert float((u - (U0 + n * dt)).abs().max()) < 1e-12
     assert float(v.abs().max()) < 1e-14 and float(ww.abs().max()) < 1e-14
+
+
+@pytest.mark.parametrize("bc", [2, 3])
+def test_open_channel_laminar_profile_is_a_fixed_point_on_gpu(binding, bc):
+    nx, ny, nz, re = 16, 8, 17, 50.0
+    g = binding.Grid(nx, ny, nz, re_tau=re, dt=2e-3, gx=1.0, bc=bc)
+    z = np.cos(np.pi * np.arange(nz) / (nz - 1))
+    sz = z if bc == 2 else -z
+    U = np.broadcast_to((0.5 * re * (3.0 - sz) * (1.0 + sz))[:, None, None], (nz, ny, nx)).copy()
+    zero = np.zeros((nz, ny, nx))
+    g.set_fields(*[torch.from_numpy(a) for a in (U, zero, zero, zero - 1.0)])
+    g.step(10)
+    u, v, ww, _ = [t.cpu().numpy() for t in g.get_fields()]
+    assert rel(u, U) < 1e-12
+    assert np.max(np.abs(v)) < 1e-14 and np.max(np.abs(ww)) < 1e-14
 
 
 def test_free_slip_rejected_by_the_adjoint(binding):

@@ -150,3 +150,34 @@ def test_free_slip_pair_wall_conditions():
     assert abs(npc.chebval(1.0, d2)) < 1e-9 * scale and abs(npc.chebval(-1.0, d2)) < 1e-9 * scale
     # the no-slip rows would leave w' nonzero here: the two wall sets differ
     assert abs(np.sum(n * n * w)) > 1e-6 * scale
+
+
+@pytest.mark.parametrize("walls", [("neumann", "dirichlet"), ("dirichlet", "neumann")])
+def test_mixed_wall_helmholtz_manufactured(walls):
+    """Different rows on each wall (Sec. 2.1 allows a combination of no-slip and free-slip):
+    any polynomial a solves (D^2 - alpha) a = f with its own wall values."""
+    N, alpha = 32, 7.5e3
+    a = np.random.default_rng(4).standard_normal(N + 1) / np.arange(1, N + 2) ** 2
+    f = pad(npc.chebder(a, 2), N) - alpha * a
+    val = {"dirichlet": lambda z: npc.chebval(z, a),
+           "neumann": lambda z: npc.chebval(z, npc.chebder(a))}
+    got = cheb.solve_helmholtz(f, alpha, walls, val[walls[0]](1.0), val[walls[1]](-1.0))
+    assert np.max(np.abs(got - a)) < 1e-13 * np.max(np.abs(a))
+
+
+@pytest.mark.parametrize("N", [16, 64])
+def test_mixed_wall_pair_manufactured(N):
+    """Free-slip at z = +1, no-slip at z = -1: w = (1+z)^2 (1-z)^3 q has w(+-1) = 0, w'(-1) = 0
+    and w''(+1) = 0; the mirrored case uses w(-z)."""
+    rng = np.random.default_rng(N + 7)
+    q = rng.standard_normal(N - 4) / np.arange(1, N - 3) ** 2          # degree N-5
+    base = npc.chebmul(npc.chebpow(npc.poly2cheb([1.0, 1.0]), 2), npc.chebpow(npc.poly2cheb([1.0, -1.0]), 3))
+    w = pad(npc.chebmul(base, q), N)
+    k2, beta = 1.5, 4.0e4
+    for walls, ww in ((("free-slip", "no-slip"), w), (("no-slip", "free-slip"), w * (-1.0) ** np.arange(N + 1))):
+        theta = pad(npc.chebder(ww, 2), N) - k2 * ww
+        r = pad(npc.chebder(theta, 2), N) - (k2 + beta) * theta
+        _, w_got = cheb.solve_coupled_w(r, k2, beta, walls)
+        # one w'' row (entries up to N^4 / 3): rounding grows like N^2 as for free-slip walls
+        tol = 1e-13 * max(1, N * N / 64)
+        assert np.max(np.abs(w_got - ww)) < tol * np.max(np.abs(ww)), walls

@@ -399,3 +399,25 @@ def test_free_slip_mean_shear_decays_at_crank_nicolson_rate():
     for _ in range(n):
         c.step()
     assert np.max(np.abs(c.omega[:, 0, 0].real - g ** n * a0)) < 1e-7 * np.max(np.abs(a0))
+
+
+@pytest.mark.parametrize("bc", [2, 3])
+def test_open_channel_laminar_profile_is_a_fixed_point(bc):
+    # no-slip at one wall, free-slip at the other: U'' = -Re gx with U = 0 at the no-slip wall
+    # and U' = 0 at the free-slip wall gives U = (Re gx / 2)(3 - s z)(1 + s z), s = +1 for a
+    # no-slip wall at z = -1 (bc = 2), s = -1 for the mirror (bc = 3)
+    p = Params(nx=8, ny=4, nz=17, re_tau=50.0, dt=2e-3, gx=1.0, bc=bc)
+    c = Channel(p)
+    X, Y, Z = grid(p)
+    sz = Z if bc == 2 else -Z
+    U = 0.5 * p.re_tau * p.gx * (3.0 - sz) * (1.0 + sz) + zeros(p)
+    c.set_fields(U, zeros(p), zeros(p), zeros(p) - 1.0)
+    for _ in range(10):
+        c.step()
+    u, v, w, _ = c.get_fields()
+    assert np.max(np.abs(u - U)) < 1e-12 * np.max(np.abs(U))
+    assert np.max(np.abs(v)) < 1e-14 and np.max(np.abs(w)) < 1e-14
+    # and the symmetric no-slip profile is not a fixed point of these walls
+    c.set_fields(0.5 * p.re_tau * (1.0 - Z * Z) + zeros(p), zeros(p), zeros(p), zeros(p) - 1.0)
+    c.step()
+    assert np.max(np.abs(c.get_fields()[0] - 0.5 * p.re_tau * (1.0 - Z * Z))) > 1e-6
