@@ -202,6 +202,21 @@ int ch_adjoint_step_timed(ch_grid* g, const void* state, double* kernel_ms);
 int ch_adjoint_gradient(ch_grid* g, double* gu, double* gv, double* gw, double* gphi);
 int ch_adjoint_end(ch_grid* g);
 
+/* ---- Interface rendering (headless) ----------------------------------------------------------
+ * ch_render_interface: an image of the interface phi = 0 of the current state (the surface shown
+ * for the drop simulation in Sec. 4) for visual checks, without any graphics API.  camera =
+ * {eye x, y, z, target x, y, z, up x, y, z} in box coordinates (x in [0, lx], y in [0, ly],
+ * z in [-1, 1]); fov_deg = vertical field of view in (0, 180); step = ray-march step (<= 0: half
+ * the smallest of dx, dy and pi/N).  Per pixel: a perspective ray through the box, phi sampled
+ * trilinearly on the collocation grid (periodic in x, y; between Gauss-Lobatto nodes in z) every
+ * `step`, the first sign change refined by 40 bisections, a headlight shade from the spectral
+ * gradient of phi.  rgb: device array height x width x 3 (row-major, top row first); depth
+ * (device, height x width doubles, may be NULL): ray parameter of the hit, -1 for no hit.
+ * Enqueued on the handle's stream.  CH_ERR_ARG for null pointers, sizes < 1, a degenerate camera;
+ * CH_ERR_STATE before the fields are set. */
+int ch_render_interface(ch_grid* g, unsigned char* rgb, double* depth, int width, int height,
+                        const double* camera, double fov_deg, double step);
+
 /* ---- Ensemble of independent channels (uneven sizes) ---------------------------------------
  * Not in the paper: a batching service of this library.  Each member is an ordinary ch_grid
  * (created here with the given allocator and stream; all members share `precision`).  One

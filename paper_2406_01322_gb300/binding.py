@@ -77,6 +77,9 @@ _SIGS = {
     "ch_transform_forward_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     _P, _P, _P]),
     "ch_noalloc_scratch_bytes": (ctypes.c_size_t, []),
+    "ch_render_interface": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                           ctypes.c_double]),
     "ch_objective": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "ch_adjoint_begin": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "ch_adjoint_step": (ctypes.c_int, [_P, _P]),
@@ -310,6 +313,18 @@ class Grid:
         _ck("ch_nonlinear", lib().ch_nonlinear(self.h, _ptr(out)))
         return out
 
+    def render_interface(self, width, height, eye, target, up=(0.0, 0.0, 1.0), fov_deg=40.0,
+                         step=0.0):
+        """Image of the interface phi = 0: (rgb uint8 (height, width, 3), depth float64
+        (height, width), -1 where the ray misses), both CUDA tensors."""
+        rgb = torch.empty((height, width, 3), dtype=torch.uint8, device=self.device)
+        depth = torch.empty((height, width), dtype=torch.float64, device=self.device)
+        cam = (ctypes.c_double * 9)(*(list(eye) + list(target) + list(up)))
+        _ck("ch_render_interface", lib().ch_render_interface(
+            self.h, _ptr(rgb), _ptr(depth), int(width), int(height), cam, float(fov_deg),
+            float(step)))
+        return rgb, depth
+
     # ---- discrete adjoint (float64 grids) ----
     def objective(self):
         """J = 1/2 int |u|^2 + int |grad phi|^2 of the current state (a Python float)."""
@@ -393,6 +408,15 @@ class ChannelObjective(torch.autograd.Function):
         scale = gJ.to(dtype=torch.float64, device=grads[0].device)
         out = [(gr * scale).to(device=d, dtype=dt) for gr, (d, dt) in zip(grads, ctx.devices)]
         return out[0], out[1], out[2], out[3], None, None, None
+
+
+def write_ppm(path, rgb):
+    """Write an (height, width, 3) uint8 image (tensor or array) as a binary PPM file."""
+    import numpy as np
+    a = np.ascontiguousarray(rgb.cpu().numpy() if hasattr(rgb, "cpu") else rgb, dtype=np.uint8)
+    with open(path, "wb") as f:
+        f.write(b"P6\n%d %d\n255\n" % (a.shape[1], a.shape[0]))
+        f.write(a.tobytes())
 
 
 def objective_after(grid, u, v, w, phi, nsteps, checkpoint_every=10):

@@ -233,6 +233,7 @@ void drop_graph(ch_grid* G) {
 int ch_launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev) {
   return launch_step(G, first, s, ev);
 }
+int ch_state_phys7(ch_grid* G) { return state_to_phys7(G, 7); }
 int ch_eval_nonlinear(ch_grid* G) { return eval_nonlinear_impl(G); }
 
 extern "C" {

@@ -95,5 +95,7 @@ struct ch_grid {
 // launch schedule of one step on stream s (events optional) and the non-linear evaluation
 int ch_launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev);
 int ch_eval_nonlinear(ch_grid* G);
+// u v w phi phi_x phi_y phi_z of the state on the unpadded grid into phys7 ((nz, ny, nx) each)
+int ch_state_phys7(ch_grid* G);
 // frees the reverse-sweep workspace if allocated
 void ch_adjoint_release(ch_grid* G);
