@@ -204,6 +204,36 @@ def precision_accuracy(binding, w, fields, steps, device, prec=1):
     return out
 
 
+def dct_gemm_ms(w, reps=5, warmup=2, dev="cuda"):
+    """Timed comparison only: the seven forward Chebyshev transforms of one step as one dense
+    float64 matrix product (cuBLAS through torch.matmul): the (N+1) x (N+1) DCT-I matrix times
+    the real and imaginary parts of 7 x Mx x Ny lines.  Returns (ms, TFLOP/s)."""
+    import torch
+    nz = w["nz"]
+    ncols = 7 * (w["nx"] // 2) * w["ny"] * 2
+    C = torch.randn(nz, nz, dtype=torch.float64, device=dev)
+    X = torch.randn(nz, ncols, dtype=torch.float64, device=dev)
+    for _ in range(warmup):
+        torch.matmul(C, X)
+    if dev == "cpu":
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            torch.matmul(C, X)
+        ms = (time.perf_counter() - t0) * 1e3 / reps
+    else:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            torch.matmul(C, X)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+    del C, X
+    return ms, 2.0 * nz * nz * ncols / (ms * 1e-3) / 1e12
+
+
 def adjoint_work(w):
     """Algorithmic flops and bytes per launch of the reverse step's kernels (FP64)."""
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
@@ -692,6 +722,12 @@ def main():
     if world == 1:
         zc, xyc = cufft_transforms_ms(w, prec)
         ours_xy = sum(roof["kernel_ms_per_step"][n] for n in ("ybwd", "xline", "yfwd"))
+        gm, gtf = dct_gemm_ms(w)
+        out["dct_as_gemm_comparison"] = {
+            "fp64_gemm_ms_for_7_forward_dcts": gm, "fp64_gemm_tflops": gtf,
+            "ours_zrhs_ms": roof["kernel_ms_per_step"]["zrhs"],
+            "note": "the 7 forward DCTs of one step as one cuBLAS float64 GEMM, against our whole "
+                    "zrhs kernel (7 DCTs + derivatives + assembly)"}
         out["cufft_comparison"] = {
             "cufft_z_dct_ms_per_step": zc, "cufft_xy_ms_per_step": xyc,
             "cufft_transforms_ms_per_step": zc + xyc,
