@@ -566,14 +566,17 @@ def run_adjoint(args):
             "traffic": traffic_bytes(args.workload, 0, names[k]), "kernel": names[k],
             "peak_kind": "float64 FMA pipe: 152 SMs x 2.07 GHz x 4 flop/clk (nominal)",
             "kernel_share": {n: kms[i] / sum(kms) for i, n in enumerate(names)},
-            "kernel_ms_per_reverse_step": {n: kms[i] / nsteps for i, n in enumerate(names)}}
+            "kernel_ms_per_reverse_step": {n: kms[i] / nsteps for i, n in enumerate(names)},
+            "note": "kernel times from an instrumented step-by-step reverse sweep, which "
+                    "recomputes each state's fields (zbwd, ybwd); the timed gradients reverse "
+                    "whole segments that keep them"}
     nbytes = 4 * pts * 8
     # launches of this library per gradient: set_fields 10 (4 x r2c, y pass, projection, four
     # for the products), 6 per forward step, objective 2, restore of the final state 4,
-    # adjoint seed 2, per segment a restore (4) and 6 per recomputed step, 9 per reverse step,
-    # gradient 6 (projection transpose, y pass, 4 x c2r)
+    # adjoint seed 2, per segment a restore (4) and 6 per recomputed step, 7 per reverse step
+    # (the segment keeps the y-padded fields), gradient 6 (projection transpose, y pass, 4 c2r)
     nseg = -(-nsteps // 10)
-    launches = 10 + 6 * nsteps + 2 + 4 + 2 + 4 * nseg + 6 * (nsteps - nseg) + 9 * nsteps + 6
+    launches = 10 + 6 * nsteps + 2 + 4 + 2 + 4 * nseg + 6 * (nsteps - nseg) + 7 * nsteps + 6
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

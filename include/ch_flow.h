@@ -199,6 +199,15 @@ int ch_adjoint_step(ch_grid* g, const void* state);
  * transposed y backward pass, i ky fold, transposed z backward. */
 #define CH_ADJ_KERNELS 9
 int ch_adjoint_step_timed(ch_grid* g, const void* state, double* kernel_ms);
+/* ch_adjoint_segment: reverses the `nsteps` forward steps that follow `checkpoint` (a
+ * ch_get_state buffer) in one call: restores the checkpoint, recomputes nsteps - 1 steps while
+ * keeping each state's y-padded forward fields (the only values of a state the reverse step
+ * uses: the linearisation point of the x line), then reverses the steps last to first.  Needs
+ * nsteps x 6 y-padded fields of device memory (6 * 16 * nx/2 * 3ny/2 * nz bytes per step, from
+ * the grid's allocator, kept until ch_adjoint_end).  Afterwards the handle holds the last
+ * recomputed state with its non-linear terms (it may step on).  Same reverse arithmetic as
+ * ch_adjoint_step: the gradient is bitwise the same. */
+int ch_adjoint_segment(ch_grid* g, const void* checkpoint, int nsteps);
 int ch_adjoint_gradient(ch_grid* g, double* gu, double* gv, double* gw, double* gphi);
 int ch_adjoint_end(ch_grid* g);
 

@@ -83,6 +83,7 @@ _SIGS = {
     "ch_objective": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "ch_adjoint_begin": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "ch_adjoint_step": (ctypes.c_int, [_P, _P]),
+    "ch_adjoint_segment": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "ch_adjoint_step_timed": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
     "ch_adjoint_gradient": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "ch_adjoint_end": (ctypes.c_int, [_P]),
@@ -342,6 +343,11 @@ class Grid:
         """Reverse the forward step that started from `state` (a get_state() buffer)."""
         _ck("ch_adjoint_step", lib().ch_adjoint_step(self.h, _ptr(state)))
 
+    def adjoint_segment(self, checkpoint, nsteps):
+        """Reverse the nsteps forward steps that follow `checkpoint` (a get_state() buffer):
+        recomputation and reverse sweep in one library call."""
+        _ck("ch_adjoint_segment", lib().ch_adjoint_segment(self.h, _ptr(checkpoint), int(nsteps)))
+
     ADJ_KERNELS = ("zbwd", "ybwd", "adj_zsolve", "adj_zrhs", "adj_ybwd", "adj_xline",
                    "adj_yfwd", "fold_dy", "adj_zbwd")
 
@@ -366,9 +372,9 @@ class ChannelObjective(torch.autograd.Function):
     """J(s_K) after K steps from the physical initial fields, differentiable in (u, v, w, phi).
 
     Forward: set_fields, K steps, J.  Saved: the state every `every` steps (checkpoints) and the
-    final state.  Backward: segment by segment from the last, the segment is recomputed from its
-    checkpoint with every intermediate state saved, then reversed step by step by the library's
-    adjoint kernels; the gradient of the first state maps back to the physical fields."""
+    final state.  Backward: segment by segment from the last, the library recomputes the segment
+    from its checkpoint and reverses it (ch_adjoint_segment); the gradient of the first state
+    maps back to the physical fields."""
 
     @staticmethod
     def forward(ctx, u, v, w, phi, grid, nsteps, every):
@@ -395,13 +401,7 @@ class ChannelObjective(torch.autograd.Function):
             for c in range(len(ctx.ckpts) - 1, -1, -1):
                 n0 = c * every
                 n1 = min(K, n0 + every)
-                g.set_state(ctx.ckpts[c])
-                states = [ctx.ckpts[c]]
-                for _ in range(n0 + 1, n1):
-                    g.step(1)
-                    states.append(g.get_state())
-                for st in reversed(states):
-                    g.adjoint_step(st)
+                g.adjoint_segment(ctx.ckpts[c], n1 - n0)
             grads = g.adjoint_gradient()
         finally:
             g.adjoint_end()

@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "../../include/ch_flow.h"
 #include "ch_grid.h"
@@ -64,6 +65,12 @@ void ch_adjoint_release(ch_grid* G) {
   else if (!G->af) cudaFree(G->adj_block);
   G->adj_block = nullptr;
   G->a_lam = G->a_L = G->a_Rb = G->a_mu = G->a_mu2 = G->a_nlb = G->a_x6 = G->a_bb = nullptr;
+  if (G->seg_block) {
+    if (G->ff) G->ff(G->seg_block, G->actx);
+    else if (!G->af) cudaFree(G->seg_block);
+    G->seg_block = nullptr;
+    G->seg_cap = 0;
+  }
 }
 
 extern "C" {
@@ -111,8 +118,44 @@ int ch_adjoint_begin(ch_grid* G, double* J) {
 
 namespace {
 
-// one reverse step; ev (optional) holds CH_ADJ_KERNELS + 1 events: ev[0] before the first launch,
-// ev[k + 1] after launch k
+// the linear part of one reverse step, given the forward y-padded fields ya of s_n (the x line's
+// linearisation point) and whether step n started Adams-Bashforth; ev (optional): 8 events,
+// ev[0] already recorded before, ev[k + 1] recorded after launch k of the 7 launches
+int reverse_core(ch_grid* G, const double2* ya, int first, cudaEvent_t* ev) {
+  const GridDev& g = G->g;
+  cudaStream_t s = G->stream;
+  cudaError_t e[7];
+  e[0] = chf::launch_adj_zsolve(g, G->a_L, G->a_Rb, G->fs, G->a_bb, s);
+  if (ev) cudaEventRecord(ev[1], s);
+  e[1] = chf::launch_adj_zrhs(g, G->a_Rb, G->a_L, G->a_mu, G->a_lam, G->a_mu2, G->a_nlb, G->fs,
+                              first, G->a_bb, G->pz, s);
+  if (ev) cudaEventRecord(ev[2], s);
+  e[2] = chf::launch_ypass(1, 0, g, g.Py, G->a_nlb, G->yb, kNl, G->fs, G->fsy, 1.0, G->py[0], s);
+  if (ev) cudaEventRecord(ev[3], s);
+  e[3] = chf::launch_adj_xline(g, ya, (const double2*)G->yb, G->a_x6, G->fsy, G->px[0], s);
+  if (ev) cudaEventRecord(ev[4], s);
+  e[4] = chf::launch_ypass(0, 0, g, g.Py, G->a_x6, G->auxA, kYa, G->fsy, G->fs, 1.0, G->py[0], s);
+  if (ev) cudaEventRecord(ev[5], s);
+  e[5] = chf::launch_fold_dy(g, G->auxA, G->fs, s);
+  if (ev) cudaEventRecord(ev[6], s);
+  e[6] = chf::launch_adj_zbwd(g, G->auxA, G->fs, G->a_lam, G->fs, G->pz, s);
+  if (ev) cudaEventRecord(ev[7], s);
+  for (int k = 0; k < 7; ++k)
+    if (e[k] != cudaSuccess) {
+      cudaGetLastError();
+      return CH_ERR_CUDA;
+    }
+  double2* t = G->a_L;
+  G->a_L = G->a_lam;
+  G->a_lam = t;
+  t = G->a_mu;
+  G->a_mu = G->a_mu2;
+  G->a_mu2 = t;
+  return CH_OK;
+}
+
+// one reverse step from a saved state; ev (optional) holds CH_ADJ_KERNELS + 1 events: ev[0]
+// before the first launch, ev[k + 1] after launch k
 int adjoint_step_impl(ch_grid* G, const void* state, cudaEvent_t* ev) {
   if (!G || !state) return CH_ERR_ARG;
   if (!G->adj_block) return CH_ERR_STATE;
@@ -134,43 +177,18 @@ int adjoint_step_impl(ch_grid* G, const void* state, cudaEvent_t* ev) {
   G->t = h.t;
   G->nl_stale = 1;
   const chf::YMap ym = chf::step_ymap();
-  cudaError_t e[CH_ADJ_KERNELS];
   if (ev) cudaEventRecord(ev[0], s);
   // forward fields of s_n on the y-padded grid (the x line's linearisation point)
-  e[0] = chf::launch_zbwd(0, 0, kBw, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s);
+  cudaError_t e0 = chf::launch_zbwd(0, 0, kBw, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s);
   if (ev) cudaEventRecord(ev[1], s);
-  e[1] = chf::launch_ypass(1, 0, g, g.Py, G->bw, G->ya, kYa, G->fs, G->fsy, 1.0, G->py[0], s,
-                           &ym);
+  cudaError_t e1 = chf::launch_ypass(1, 0, g, g.Py, G->bw, G->ya, kYa, G->fs, G->fsy, 1.0,
+                                     G->py[0], s, &ym);
   if (ev) cudaEventRecord(ev[2], s);
-  // reverse step
-  e[2] = chf::launch_adj_zsolve(g, G->a_L, G->a_Rb, G->fs, G->a_bb, s);
-  if (ev) cudaEventRecord(ev[3], s);
-  e[3] = chf::launch_adj_zrhs(g, G->a_Rb, G->a_L, G->a_mu, G->a_lam, G->a_mu2, G->a_nlb, G->fs,
-                              h.first, G->a_bb, G->pz, s);
-  if (ev) cudaEventRecord(ev[4], s);
-  e[4] = chf::launch_ypass(1, 0, g, g.Py, G->a_nlb, G->yb, kNl, G->fs, G->fsy, 1.0, G->py[0], s);
-  if (ev) cudaEventRecord(ev[5], s);
-  e[5] = chf::launch_adj_xline(g, (const double2*)G->ya, (const double2*)G->yb, G->a_x6, G->fsy,
-                               G->px[0], s);
-  if (ev) cudaEventRecord(ev[6], s);
-  e[6] = chf::launch_ypass(0, 0, g, g.Py, G->a_x6, G->auxA, kYa, G->fsy, G->fs, 1.0, G->py[0], s);
-  if (ev) cudaEventRecord(ev[7], s);
-  e[7] = chf::launch_fold_dy(g, G->auxA, G->fs, s);
-  if (ev) cudaEventRecord(ev[8], s);
-  e[8] = chf::launch_adj_zbwd(g, G->auxA, G->fs, G->a_lam, G->fs, G->pz, s);
-  if (ev) cudaEventRecord(ev[9], s);
-  for (int k = 0; k < CH_ADJ_KERNELS; ++k)
-    if (e[k] != cudaSuccess) {
-      cudaGetLastError();
-      return CH_ERR_CUDA;
-    }
-  double2* t = G->a_L;
-  G->a_L = G->a_lam;
-  G->a_lam = t;
-  t = G->a_mu;
-  G->a_mu = G->a_mu2;
-  G->a_mu2 = t;
-  return CH_OK;
+  if (e0 != cudaSuccess || e1 != cudaSuccess) {
+    cudaGetLastError();
+    return CH_ERR_CUDA;
+  }
+  return reverse_core(G, (const double2*)G->ya, h.first, ev ? ev + 2 : nullptr);
 }
 
 }  // namespace
@@ -198,6 +216,46 @@ int ch_adjoint_step_timed(ch_grid* G, const void* state, double* kernel_ms) {
   for (int i = 0; i <= CH_ADJ_KERNELS; ++i) cudaEventDestroy(ev[i]);
   if (st == CH_ERR_CUDA) cudaGetLastError();
   return st;
+}
+
+int ch_adjoint_segment(ch_grid* G, const void* checkpoint, int nsteps) {
+  if (!G || !checkpoint || nsteps < 1) return CH_ERR_ARG;
+  if (!G->adj_block) return CH_ERR_STATE;
+  cudaStream_t s = G->stream;
+  const size_t yab = (size_t)kYa * G->fsy * sizeof(double2);
+  if (G->seg_cap < nsteps) {                 // storage for the y-padded fields of the segment
+    if (G->seg_block) {
+      cudaStreamSynchronize(s);
+      if (G->ff) G->ff(G->seg_block, G->actx);
+      else if (!G->af) cudaFree(G->seg_block);
+      G->seg_block = nullptr;
+      G->seg_cap = 0;
+    }
+    void* p = nullptr;
+    if (G->af) p = G->af((size_t)nsteps * yab, G->actx);
+    else if (cudaMalloc(&p, (size_t)nsteps * yab) != cudaSuccess) { cudaGetLastError(); p = nullptr; }
+    if (!p) return CH_ERR_ALLOC;
+    G->seg_block = p;
+    G->seg_cap = nsteps;
+  }
+  char* seg = (char*)G->seg_block;
+  // recompute the segment from its checkpoint, keeping each state's y-padded fields
+  int r = ch_set_state(G, checkpoint);       // also evaluates the fields of the first state
+  if (r != CH_OK) return r;
+  std::vector<int> first((size_t)nsteps);
+  for (int k = 0; k < nsteps; ++k) {
+    first[k] = G->first;
+    CK(cudaMemcpyAsync(seg + (size_t)k * yab, G->ya, yab, cudaMemcpyDeviceToDevice, s));
+    if (k + 1 < nsteps) {
+      r = ch_step(G, 1);                     // ends with the y-padded fields of the next state
+      if (r != CH_OK) return r;
+    }
+  }
+  for (int k = nsteps - 1; k >= 0; --k) {
+    r = reverse_core(G, (const double2*)(seg + (size_t)k * yab), first[k], nullptr);
+    if (r != CH_OK) return r;
+  }
+  return CH_OK;
 }
 
 int ch_adjoint_gradient(ch_grid* G, double* gu, double* gv, double* gw, double* gphi) {

@@ -89,6 +89,8 @@ struct ch_grid {
   void* adj_block = nullptr;
   double2 *a_lam = nullptr, *a_L = nullptr, *a_Rb = nullptr, *a_mu = nullptr, *a_mu2 = nullptr;
   double2 *a_nlb = nullptr, *a_x6 = nullptr, *a_bb = nullptr;
+  void* seg_block = nullptr;  // y-padded fields of the states of one recomputed segment
+  int seg_cap = 0;            // states that seg_block holds
   int nl_stale = 0;  // 1: the state was replaced by a reverse step; products not recomputed
 };
 

@@ -181,6 +181,33 @@ def test_full_size_directional_derivative(binding):
     g.close()
 
 
+def test_segment_reversal_equals_step_by_step_bitwise(binding):
+    """ch_adjoint_segment (recompute keeping the y-padded fields, reverse) against reversing the
+    same steps one by one from saved states (ch_adjoint_step recomputes those fields)."""
+    c = dict(CASES[2], steps=6)
+    f = fields(c, seed=9)
+    grads = []
+    for mode in ("segment", "steps"):
+        g = grid(binding, c)
+        g.set_fields(*dev(f))
+        states = []
+        for _ in range(c["steps"]):
+            states.append(g.get_state())
+            g.step(1)
+        g.adjoint_begin()
+        if mode == "segment":
+            g.adjoint_segment(states[3], 3)
+            g.adjoint_segment(states[0], 3)
+        else:
+            for st in reversed(states):
+                g.adjoint_step(st)
+        grads.append([t.cpu() for t in g.adjoint_gradient()])
+        g.adjoint_end()
+        g.close()
+    for a, b in zip(*grads):
+        assert torch.equal(a, b)
+
+
 def test_adjoint_call_order_and_precision(binding):
     c = CASES[0]
     f = fields(c)
