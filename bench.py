@@ -77,7 +77,7 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# ---- algorithmic work per launch (see the module docstring of DESIGN notes in this file) ----
+# ---- algorithmic work per launch --------------------------------------------------------------
 def fft_flops(n):
     """5 n log2 n: the conventional flop count of a complex FFT of length n."""
     return 5.0 * n * math.log2(n)
@@ -420,7 +420,7 @@ def run_reference(args, w):
     c = Channel(p)
     c.set_fields(*inputs.initial_fields(**w))
     rng = np.random.default_rng(0)
-    nplanes, nlines = 4, 32
+    nplanes, nlines = 3, 24
     for _ in range(args.warmup):
         oracle_step_sample(c, nplanes, nlines, rng)
     total = sum(oracle_step_sample(c, nplanes, nlines, rng) for _ in range(args.steps))
