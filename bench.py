@@ -204,6 +204,31 @@ def precision_accuracy(binding, w, fields, steps, device, prec=1):
     return out
 
 
+def precision_variants(binding, w, fields, kw, steps, device):
+    """The same workload in the other precision modes: device time per step over `steps` steps
+    (after 3 warm-up steps) and, for double-float, the max relative field difference from the
+    float64 path after 3 + `steps` steps from the same fields."""
+    import torch
+    out, final = {}, {}
+    for pr in (0, 2, 1):
+        g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=pr, device=device, **kw)
+        g.set_fields(*[torch.from_numpy(f) for f in fields])
+        g.step(3)
+        tot, _ = g.step_timed(steps)
+        final[pr] = [f.cpu() for f in g.get_fields()]
+        g.close()
+        torch.cuda.empty_cache()
+        if pr:
+            pts = w["nx"] * w["ny"] * w["nz"]
+            out[PREC_NAMES[pr]] = {"ms_per_step": tot / steps, "dtype": DTYPES[pr],
+                                   "value": pts * steps / (tot * 1e-3) / 1e6}
+    out["dfloat"]["max_rel_field_diff_vs_fp64"] = max(
+        float((a - b).abs().max() / b.abs().max()) for a, b in zip(final[2], final[0]))
+    out["mixed"]["max_rel_field_diff_vs_fp64"] = max(
+        float((a - b).abs().max() / b.abs().max()) for a, b in zip(final[1], final[0]))
+    return out
+
+
 def dct_gemm_ms(w, reps=5, warmup=2, dev="cuda"):
     """Timed comparison only: the seven forward Chebyshev transforms of one step as one dense
     float64 matrix product (cuBLAS through torch.matmul): the (N+1) x (N+1) DCT-I matrix times
@@ -719,6 +744,8 @@ def main():
            "roofline": roof,
            "clocks": clk.summary()}
     g.close()
+    if world == 1 and prec == 0 and args.precision is None and not args.no_accuracy:
+        out["variants"] = precision_variants(binding, w, fields, kw, args.steps, f"cuda:{local}")
     if world == 1 and prec != 0 and not args.no_accuracy:
         out[PREC_NAMES[prec] + "_vs_fp64"] = precision_accuracy(binding, w, fields, w["steps"],
                                                                 f"cuda:{local}", prec)
