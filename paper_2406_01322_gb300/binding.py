@@ -180,13 +180,19 @@ class Grid:
 
     def __init__(self, nx, ny, nz, re_tau=150.0, we=1.0, ch=0.05, pe=20.0, dt=1e-4,
                  lx=4 * math.pi, ly=2 * math.pi, gx=1.0, gy=0.0, precision=PREC_FP64,
-                 device="cuda:0", stream=None, use_torch_allocator=True, bc=BC_NO_SLIP):
+                 device="cuda:0", stream=None, use_torch_allocator=True, bc=BC_NO_SLIP,
+                 allocator=None):
         self.device = torch.device(device)
         self.shape = (nz, ny, nx)
         self.spec_shape = (nx // 2, ny, nz)
         self.params = Params(nx, ny, nz, lx, ly, re_tau, we, ch, pe, dt, gx, gy, precision, 0, bc)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self._alloc = TorchAllocator(self.device) if use_torch_allocator else None
+        # allocator: an object with alloc_cb / free_cb (e.g. TorchAllocator); default: torch's
+        # caching allocator, or the library's cudaMalloc when use_torch_allocator is False
+        if allocator is not None:
+            self._alloc = allocator
+        else:
+            self._alloc = TorchAllocator(self.device) if use_torch_allocator else None
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             code = lib().ch_init_grid(

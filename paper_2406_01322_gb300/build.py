@@ -71,7 +71,7 @@ def build_library(force=False, verbose=False, extra_flags=()):
     if any(codes):
         raise RuntimeError("nvcc failed; see the messages above")
     tmp = LIB + ".tmp"
-    link = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    link = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"]
     if run(link) != 0:
         raise RuntimeError("link of libchflow.so failed")
     os.replace(tmp, LIB)

@@ -19,6 +19,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ch_flow.h"
 #include "ch_grid.h"
 #include "ch_internal.h"
@@ -182,20 +184,35 @@ int launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev = nullptr
   const GridDev& g = G->g;
   const chf::YMap ym = step_ymap();
   cudaError_t e[CH_STEP_KERNELS];
+  // NVTX ranges (host side, for profilers) around the six stages
+  nvtxRangePushA("ch step");
+  nvtxRangePushA("zrhs");
   e[0] = chf::launch_zrhs(G->prec, g, G->nl, G->fs, G->om, G->w, G->phi, G->hom, G->hw, G->hphi,
                           G->R, first, G->pz, s);
+  nvtxRangePop();
   if (ev) cudaEventRecord(ev[0], s);
+  nvtxRangePushA("zsolve");
   e[1] = chf::launch_zsolve(g, G->R, G->fs, s);
+  nvtxRangePop();
   if (ev) cudaEventRecord(ev[1], s);
+  nvtxRangePushA("zbwd");
   e[2] = chf::launch_zbwd(1, G->prec, kBw, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s);
+  nvtxRangePop();
   if (ev) cudaEventRecord(ev[2], s);
+  nvtxRangePushA("ybwd");
   e[3] = chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, kYa, G->fs, G->fsy, 1.0,
                            G->py[G->prec], s, &ym);
+  nvtxRangePop();
   if (ev) cudaEventRecord(ev[3], s);
+  nvtxRangePushA("xline");
   e[4] = chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s);
+  nvtxRangePop();
   if (ev) cudaEventRecord(ev[4], s);
+  nvtxRangePushA("yfwd");
   e[5] = chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, kNl, G->fsy, G->fs,
                            1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s);
+  nvtxRangePop();
+  nvtxRangePop();
   if (ev) cudaEventRecord(ev[5], s);
   for (int k = 0; k < CH_STEP_KERNELS; ++k)
     if (e[k] != cudaSuccess) {
@@ -501,7 +518,10 @@ int ch_step(ch_grid* G, int nsteps) {
         if (e != cudaSuccess) return CH_ERR_CUDA;
         G->graph_ok = 1;
       }
-      CK(cudaGraphLaunch(G->gexec, G->stream));
+      nvtxRangePushA("ch step (graph)");
+      cudaError_t eg = cudaGraphLaunch(G->gexec, G->stream);
+      nvtxRangePop();
+      CK(eg);
     }
     G->nstep += 1;
     G->t += G->p.dt;
