@@ -497,6 +497,20 @@ def run_ensemble(args):
     torch.cuda.synchronize()
     seq_ms = t0.elapsed_time(t1)
     pts = sum(m["nx"] * m["ny"] * m["nz"] for m in ms)
+    # e2e: every member's fields from pinned host memory, K grouped steps, fields back to pinned
+    # host memory, on the host clock
+    host = [[torch.from_numpy(a).pin_memory() for a in inputs.initial_fields(**m)] for m in ms]
+    outs = [[torch.empty_like(h).pin_memory() for h in hs] for hs in host]
+    torch.cuda.synchronize()
+    t_e = time.perf_counter()
+    for g, hs in zip(ens.grids, host):
+        g.set_fields_host(*hs)
+    ens.step(args.steps)
+    for g, os_ in zip(ens.grids, outs):
+        g.get_fields_host(os_)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t_e
+    nbytes = sum(4 * m["nx"] * m["ny"] * m["nz"] * 8 for m in ms)
     names = list(binding.Grid.KERNELS)
     out = {"metric": METRIC, "value": pts * args.steps / (tot_ms * 1e-3) / 1e6, "unit": UNIT,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -506,6 +520,10 @@ def run_ensemble(args):
            "config": {"workload": "ensemble_32_uneven", "members": len(ms),
                       "points": pts, "precision": "mixed"},
            "sequential_members_ms_per_step": seq_ms / args.steps,
+           "e2e": {"value": pts * args.steps / e2e_s / 1e6, "unit": UNIT,
+                   "h2d_bytes_per_step": nbytes / args.steps,
+                   "d2h_bytes_per_step": nbytes / args.steps,
+                   "note": "set_fields_host of every member + K grouped steps + get_fields_host"},
            "stage_ms_per_step": {n: kms[i] / args.steps for i, n in enumerate(names)},
            "tuning": tuning, "gpu_launches": 6 * args.steps, "clocks": clk.summary()}
     ens.close()
