@@ -68,6 +68,17 @@ def traffic_bytes(workload, prec, kernel):
     return None if v is None else v * 1e6
 
 
+def tensor_peak():
+    """Measured bf16 dense tensor peak (burst: the kernel is timed inside a short step)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured bf16 dense (cuBLAS burst)"
+    return 1900.0, "fallback bf16 dense"
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -108,9 +119,27 @@ def kernel_work(w, prec):
     x_by = 15 * Y * b
     yf_fl = 9 * Mx * nz * fft_flops(Py)
     yf_by = 9 * (S + Y) * b
+    # Chebyshev transforms on the tensor cores (CH_CHEB_TC): tensor-pipe flops issued (36 digit
+    # products of 2 M Nout K each, M = real rows, Nout and K padded as the kernel pads them) and
+    # the bytes of the fields read and written once
+    Kp, NT, nNt = tc_tiles(nz)
+    rows = 2 * lines
+    tcf_fl = 36 * 2.0 * (9 * rows) * (NT * nNt) * Kp
+    tcf_by = 9 * S * (b + 16)
+    tcb_fl = 36 * 2.0 * (5 * rows) * (NT * nNt) * Kp
+    tcb_by = 5 * S * (16 + b)
     return {"zrhs": (zrhs_fl, zrhs_by), "zsolve": (zsolve_fl, zsolve_by),
             "zbwd": (zbwd_fl, zbwd_by), "ybwd": (yb_fl, yb_by), "xline": (x_fl, x_by),
-            "yfwd": (yf_fl, yf_by)}
+            "yfwd": (yf_fl, yf_by), "cheb_fwd": (tcf_fl, tcf_by), "cheb_bwd": (tcb_fl, tcb_by)}
+
+
+def tc_tiles(nz):
+    """K padding, output slice width and slice count of the tensor-core Chebyshev kernel (the
+    library's rule: 48-wide slices unless 64-wide ones pad 20 % less)."""
+    Kp = (nz + 15) // 16 * 16
+    c48, c64 = (nz + 47) // 48 * 48, (nz + 63) // 64 * 64
+    NT = 48 if 5 * c48 <= 4 * c64 else 64
+    return Kp, NT, (nz + NT - 1) // NT
 
 
 def cufft_transforms_ms(w, prec, reps=5, warmup=2, dev="cuda"):
@@ -511,7 +540,7 @@ def run_ensemble(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t_e
     nbytes = sum(4 * m["nx"] * m["ny"] * m["nz"] * 8 for m in ms)
-    names = list(binding.Grid.KERNELS)
+    names = list(binding.Ensemble.STAGES)
     out = {"metric": METRIC, "value": pts * args.steps / (tot_ms * 1e-3) / 1e6, "unit": UNIT,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -649,6 +678,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the comparison against the FP64 path (precision 1 and 2)")
+    ap.add_argument("--cheb", default="fft", choices=["fft", "tc"],
+                    help="Chebyshev transforms of the step: N-point DCT-I in float64 (fft) or "
+                         "the exact-split matrix product on the tensor cores (tc)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 5 if args.workload == "channel_128x128x129_adjoint" else 100
@@ -682,6 +714,7 @@ def main():
     fields = inputs.initial_fields(**dict(w, seed=w["seed"] + rank))
     kw = dict(re_tau=w["re_tau"], we=w["we"], ch=w["ch"], pe=w["pe"], dt=w["dt"])
     g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=prec, device=f"cuda:{local}", **kw)
+    g.set_chebyshev(binding.CHEB_TC if args.cheb == "tc" else binding.CHEB_FFT)
     g.set_fields(*[torch.from_numpy(f) for f in fields])
     g.step(args.warmup)
     torch.cuda.synchronize()
@@ -726,7 +759,12 @@ def main():
     # double-float kernels (float64-accurate work on the float32 pipe) are ALU-bound and are
     # measured against the float64 peak; float32 kernels against HBM
     fp64_like = (prec != 1) or name.startswith("z")
-    if fp64_like:
+    if name.startswith("cheb"):
+        tpk, tpk_kind = tensor_peak()
+        ach = fl / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": tpk, "unit": "TFLOP/s",
+                "frac": ach / tpk, "traffic": None, "kernel": name, "peak_kind": tpk_kind}
+    elif fp64_like:
         ach = fl / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS,
@@ -752,7 +790,7 @@ def main():
            "dtype": DTYPES[prec],
            "data": "synthetic",
            "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]],
-                      "precision": PREC_NAMES[prec],
+                      "precision": PREC_NAMES[prec], "chebyshev": args.cheb,
                       "parallelism": "replicas" if world > 1 else "single",
                       "l2": "step working set larger than L2 (no flush)"},
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes / args.steps,

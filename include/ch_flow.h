@@ -119,10 +119,41 @@ int ch_set_fields_host(ch_grid* g, const double* u, const double* v, const doubl
  * the first step the per-step launch sequence is replayed from a captured CUDA graph. */
 int ch_step(ch_grid* g, int nsteps);
 
-/* Number of kernels in one time step and the order ch_step_timed reports them in:
- * zrhs (DCT, assembly, AB2, right-hand sides), zsolve (tau solves), zbwd (update, velocity,
- * backward DCT), y backward, x line, y forward. */
-#define CH_STEP_KERNELS 6
+/* The kernels of one time step in the order ch_step_timed reports them in: zrhs (DCT,
+ * assembly, AB2, right-hand sides), zsolve (tau solves), zbwd (update, velocity, backward DCT),
+ * y backward, x line, y forward, then the two Chebyshev transforms on the tensor cores
+ * (forward of the nine products before zrhs, backward of the five fields after zbwd), which run
+ * only under CH_CHEB_TC (zero time otherwise; zrhs and zbwd then skip their DCTs). */
+#define CH_STEP_KERNELS 8
+
+/* Method of the Chebyshev transforms (Sec. 3.2.1) inside the step:
+ * CH_CHEB_FFT: DCT-I through one N-point complex FFT per line, in float64, fused into zrhs/zbwd
+ *   (the default);
+ * CH_CHEB_TC: the transform as a product with the fixed Nz x Nz Chebyshev matrix on the tensor
+ *   cores, float64-accurate by an exact split of both operands into eight signed 7-bit digits
+ *   (bf16, Ozaki scheme; fp32 accumulation is exact for these integers) and a recombination in
+ *   64-bit integers; error a few units of 2^-53 of max|row| x max_n sum_k |B_nk| per line, the
+ *   accuracy of a float64 transform.  Two extra launches per step and a 9-field float64 coefficient buffer.
+ *   Single grids in CH_PREC_FP64 or CH_PREC_MIXED with nz <= 496; not with the adjoint. */
+#define CH_CHEB_FFT 0
+#define CH_CHEB_TC 1
+
+/* Select the step's Chebyshev method; allocates the tensor-core tables and buffer on the first
+ * CH_CHEB_TC (synchronous).  CH_ERR_ARG: bad method or CH_PREC_DFLOAT; CH_ERR_SIZE: nz > 496.
+ * The captured step graph is rebuilt at the next ch_step. */
+int ch_set_chebyshev(ch_grid* g, int method);
+int ch_get_chebyshev(const ch_grid* g);
+
+/* Chebyshev transform along z of nf fields of complex lines (device, float64 (re, im) pairs,
+ * layout [field][mx * ny + j][n], field stride (nx/2) ny nz, the layout of ch_get_spectral) with
+ * the selected method: dir 0 samples at z_k = cos(pi k / N) -> coefficients a_n, dir 1 the
+ * inverse.  in and out must not overlap.  Asynchronous on the handle's stream. */
+int ch_chebyshev_lines(ch_grid* g, int dir, const double* in, double* out, int nf);
+
+/* Synchronise the handle's stream; CH_ERR_TIMEOUT (and the flag cleared) if a bounded device
+ * wait of the tensor-core kernels gave up since the last check (its outputs are then invalid),
+ * else CH_OK.  ch_diagnostics reports the same condition. */
+int ch_device_status(ch_grid* g);
 
 /* As ch_step, but launched without the graph and bracketed by CUDA events on the stream: on
  * return (the stream is synchronised) kernel_ms[0..CH_STEP_KERNELS-1] hold the summed device
@@ -186,9 +217,10 @@ int ch_nonlinear(ch_grid* g, double* out9);
  * ch_adjoint_gradient: after the step reversed last (the first forward step), writes
  *   dJ/du0, dJ/dv0, dJ/dw0, dJ/dphi0 into four device (nz,ny,nx) float64 arrays.
  * ch_adjoint_end: frees the workspace (ch_destroy does too).
- * Mixed-precision, double-float and free-slip grids: CH_ERR_ARG.  Grids whose padded x length Px = 3 nx / 2 exceeds 602
- * (the transposed x line keeps 24 lines of Px complex float64, 384 Px bytes, in the 226 KiB of
- * shared memory a block may use): CH_ERR_SIZE (nx <= 384 among the supported sizes).
+ * Mixed-precision, double-float, free-slip and CH_CHEB_TC grids: CH_ERR_ARG.  Grids whose padded
+ * x length Px = 3 nx / 2 exceeds 602 (the transposed x line keeps 24 lines of Px complex
+ * float64, 384 Px bytes, in the 226 KiB of shared memory a block may use): CH_ERR_SIZE
+ * (nx <= 384 among the supported sizes).
  * Calls out of order (step/gradient before begin; J of an unset grid): CH_ERR_STATE. */
 int ch_objective(ch_grid* g, double* J);
 int ch_adjoint_begin(ch_grid* g, double* J);
@@ -243,7 +275,9 @@ int ch_ensemble_size(const ch_ensemble* e);
 int ch_ensemble_member(ch_ensemble* e, int i, ch_grid** out);
 int ch_ensemble_step(ch_ensemble* e, int nsteps);
 /* as ch_ensemble_step with events between the six grouped launches (stream synchronised):
- * stage_ms[0..CH_STEP_KERNELS-1] summed per stage, *total_ms over all steps */
+ * stage_ms[0..CH_ENSEMBLE_STAGES-1] summed per stage (zrhs zsolve zbwd y backward x line
+ * y forward), *total_ms over all steps */
+#define CH_ENSEMBLE_STAGES 6
 int ch_ensemble_step_timed(ch_ensemble* e, int nsteps, double* stage_ms, double* total_ms);
 int ch_ensemble_autotune(ch_ensemble* e, int reps);
 int ch_ensemble_tuning(const ch_ensemble* e, char* buf, size_t n);

@@ -24,6 +24,8 @@ BC_NO_SLIP = 0
 BC_FREE_SLIP = 1
 BC_NO_SLIP_BOTTOM_FREE_SLIP_TOP = 2
 BC_FREE_SLIP_BOTTOM_NO_SLIP_TOP = 3
+CHEB_FFT = 0
+CHEB_TC = 1
 
 
 class ChError(RuntimeError):
@@ -99,6 +101,10 @@ _SIGS = {
     "ch_ensemble_destroy": (None, [_P]),
     "ch_destroy": (None, [_P]),
     "ch_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ch_set_chebyshev": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ch_get_chebyshev": (ctypes.c_int, [_P]),
+    "ch_chebyshev_lines": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
+    "ch_device_status": (ctypes.c_int, [_P]),
 }
 
 
@@ -249,7 +255,28 @@ class Grid:
     def step(self, n=1):
         _ck("ch_step", lib().ch_step(self.h, int(n)))
 
-    KERNELS = ("zrhs", "zsolve", "zbwd", "ybwd", "xline", "yfwd")
+    KERNELS = ("zrhs", "zsolve", "zbwd", "ybwd", "xline", "yfwd", "cheb_fwd", "cheb_bwd")
+
+    def set_chebyshev(self, method):
+        """CHEB_FFT (default) or CHEB_TC: how the step does its Chebyshev transforms."""
+        _ck("ch_set_chebyshev", lib().ch_set_chebyshev(self.h, int(method)))
+
+    def chebyshev(self):
+        return int(lib().ch_get_chebyshev(self.h))
+
+    def chebyshev_lines(self, x, direction):
+        """Chebyshev transform along z of complex lines x (nf, nx/2, ny, nz) complex128 on the
+        device with the selected method: direction 0 samples -> coefficients, 1 the inverse."""
+        x = x.contiguous()
+        assert x.dtype == torch.complex128 and tuple(x.shape[1:]) == tuple(self.spec_shape)
+        out = torch.empty_like(x)
+        _ck("ch_chebyshev_lines", lib().ch_chebyshev_lines(self.h, int(direction), _ptr(x),
+                                                           _ptr(out), int(x.shape[0])))
+        return out
+
+    def device_status(self):
+        """Synchronise; raises ChError(CH_ERR_TIMEOUT) if a bounded device wait gave up."""
+        _ck("ch_device_status", lib().ch_device_status(self.h))
 
     def step_timed(self, n):
         """n steps with CUDA events between launches; returns (total_ms, per-kernel summed ms in
@@ -465,8 +492,10 @@ class Ensemble:
     def step(self, n=1):
         _ck("ch_ensemble_step", lib().ch_ensemble_step(self.h, int(n)))
 
+    STAGES = ("zrhs", "zsolve", "zbwd", "ybwd", "xline", "yfwd")
+
     def step_timed(self, n):
-        ks = (ctypes.c_double * len(Grid.KERNELS))()
+        ks = (ctypes.c_double * len(self.STAGES))()
         tot = ctypes.c_double()
         _ck("ch_ensemble_step_timed", lib().ch_ensemble_step_timed(self.h, int(n), ks,
                                                                    ctypes.byref(tot)))

@@ -85,7 +85,8 @@ int ch_objective(ch_grid* G, double* J) {
 int ch_adjoint_begin(ch_grid* G, double* J) {
   if (!G) return CH_ERR_ARG;
   if (!G->fields_set) return CH_ERR_STATE;
-  if (G->prec != CH_PREC_FP64 || G->g.bc != 0) return CH_ERR_ARG;  // no-slip walls only
+  // float64, no-slip walls, FFT Chebyshev transforms only
+  if (G->prec != CH_PREC_FP64 || G->g.bc != 0 || G->cheb != CH_CHEB_FFT) return CH_ERR_ARG;
   if (chf::adj_xline_smem(G->g.Px) > (size_t)chf::kMaxSmem) return CH_ERR_SIZE;
   if (!G->adj_block) {
     const size_t sb = (size_t)G->fs * sizeof(double2);

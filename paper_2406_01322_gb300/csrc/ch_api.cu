@@ -178,42 +178,65 @@ int eval_nonlinear_impl(ch_grid* G) {
   return CH_OK;
 }
 
-// The step's launch schedule (the only copy): zrhs, zsolve, zbwd, y backward, x line, y forward.
-// ev, when given, holds CH_STEP_KERNELS events recorded after each launch.
+// The step's launch schedule (the only copy).  Launch positions: 0 Chebyshev forward transform
+// on the tensor cores (CH_CHEB_TC only), 1 zrhs, 2 zsolve, 3 zbwd, 4 Chebyshev backward
+// transform (CH_CHEB_TC only), 5 y backward, 6 x line, 7 y forward.  ev, when given, holds
+// CH_STEP_KERNELS events: ev[p] is recorded after position p (right away for an empty position).
 int launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   const GridDev& g = G->g;
   const chf::YMap ym = step_ymap();
+  const bool tc = G->cheb == CH_CHEB_TC;
+  const int nlines = g.Mx * g.ny;
   cudaError_t e[CH_STEP_KERNELS];
-  // NVTX ranges (host side, for profilers) around the six stages
+  for (int k = 0; k < CH_STEP_KERNELS; ++k) e[k] = cudaSuccess;
+  // NVTX ranges (host side, for profilers) around the stages
   nvtxRangePushA("ch step");
-  nvtxRangePushA("zrhs");
-  e[0] = chf::launch_zrhs(G->prec, g, G->nl, G->fs, G->om, G->w, G->phi, G->hom, G->hw, G->hphi,
-                          G->R, first, G->pz, s);
-  nvtxRangePop();
+  if (tc) {
+    nvtxRangePushA("cheb fwd (tensor cores)");
+    e[6] = chf::launch_cheb_tc(G->prec == 1 ? 1 : 0, 0, G->nl, G->fs, G->cf, G->fs, kNl, nlines,
+                               g.nz, G->tcf, G->tc_err, s);
+    nvtxRangePop();
+  }
   if (ev) cudaEventRecord(ev[0], s);
+  nvtxRangePushA("zrhs");
+  e[0] = tc ? chf::launch_zrhs_coef(g, G->cf, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
+                                    G->hphi, G->R, first, G->pz, s)
+            : chf::launch_zrhs(G->prec, g, G->nl, G->fs, G->om, G->w, G->phi, G->hom, G->hw,
+                               G->hphi, G->R, first, G->pz, s);
+  nvtxRangePop();
+  if (ev) cudaEventRecord(ev[1], s);
   nvtxRangePushA("zsolve");
   e[1] = chf::launch_zsolve(g, G->R, G->fs, s);
   nvtxRangePop();
-  if (ev) cudaEventRecord(ev[1], s);
-  nvtxRangePushA("zbwd");
-  e[2] = chf::launch_zbwd(1, G->prec, kBw, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s);
-  nvtxRangePop();
   if (ev) cudaEventRecord(ev[2], s);
+  nvtxRangePushA("zbwd");
+  e[2] = tc ? chf::launch_zbwd_coef(g, G->R, G->om, G->w, G->phi, G->cf, G->fs, G->pz, s)
+            : chf::launch_zbwd(1, G->prec, kBw, g, G->R, G->om, G->w, G->phi, G->bw, G->fs,
+                               G->pz, s);
+  nvtxRangePop();
+  if (ev) cudaEventRecord(ev[3], s);
+  if (tc) {
+    nvtxRangePushA("cheb bwd (tensor cores)");
+    e[7] = chf::launch_cheb_tc(0, G->prec == 1 ? 1 : 0, G->cf, G->fs, G->bw, G->fs, kBw, nlines,
+                               g.nz, G->tcb, G->tc_err, s);
+    nvtxRangePop();
+  }
+  if (ev) cudaEventRecord(ev[4], s);
   nvtxRangePushA("ybwd");
   e[3] = chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, kYa, G->fs, G->fsy, 1.0,
                            G->py[G->prec], s, &ym);
   nvtxRangePop();
-  if (ev) cudaEventRecord(ev[3], s);
+  if (ev) cudaEventRecord(ev[5], s);
   nvtxRangePushA("xline");
   e[4] = chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s);
   nvtxRangePop();
-  if (ev) cudaEventRecord(ev[4], s);
+  if (ev) cudaEventRecord(ev[6], s);
   nvtxRangePushA("yfwd");
   e[5] = chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, kNl, G->fsy, G->fs,
                            1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s);
   nvtxRangePop();
   nvtxRangePop();
-  if (ev) cudaEventRecord(ev[5], s);
+  if (ev) cudaEventRecord(ev[7], s);
   for (int k = 0; k < CH_STEP_KERNELS; ++k)
     if (e[k] != cudaSuccess) {
       cudaGetLastError();
@@ -221,6 +244,10 @@ int launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev = nullptr
     }
   return CH_OK;
 }
+
+// launch position of each entry of ch_step_timed's kernel_ms (zrhs zsolve zbwd ybwd xline yfwd
+// cheb_fwd cheb_bwd)
+const int kStepPos[CH_STEP_KERNELS] = {1, 2, 3, 5, 6, 7, 0, 4};
 
 // the 7 backward fields of the state, evaluated on the unpadded grid, into phys7
 int state_to_phys7(ch_grid* G, int nf) {
@@ -529,7 +556,9 @@ int ch_step(ch_grid* G, int nsteps) {
   return CH_OK;
 }
 
-int ch_launches_per_step(const ch_grid* G) { return G ? CH_STEP_KERNELS : 0; }
+int ch_launches_per_step(const ch_grid* G) {
+  return G ? (G->cheb == CH_CHEB_TC ? 8 : 6) : 0;
+}
 
 int ch_step_timed(ch_grid* G, int nsteps, double* kernel_ms, double* total_ms) {
   if (!G || nsteps < 0 || !total_ms) return CH_ERR_ARG;
@@ -550,8 +579,9 @@ int ch_step_timed(ch_grid* G, int nsteps, double* kernel_ms, double* total_ms) {
   double ks[CH_STEP_KERNELS] = {0};
   for (int i = 0; i < nsteps; ++i)
     for (int k = 0; k < NKER; ++k) {
+      const int p = kStepPos[k];
       float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, ev[NKER * i + k], ev[NKER * i + k + 1]));
+      CK(cudaEventElapsedTime(&ms, ev[NKER * i + p], ev[NKER * i + p + 1]));
       ks[k] += ms;
     }
   float tot = 0.f;
@@ -599,6 +629,11 @@ int ch_diagnostics(ch_grid* G, ch_diag* out) {
   double h[8];
   CK(cudaMemcpyAsync(h, G->diag_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, G->stream));
   CK(cudaStreamSynchronize(G->stream));
+  if (G->tc_err) {
+    int te = 0;
+    CK(cudaMemcpy(&te, G->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (te) return CH_ERR_TIMEOUT;
+  }
   out->t = G->t;
   out->step = G->nstep;
   out->mass = h[0];
@@ -723,6 +758,76 @@ void ch_destroy(ch_grid* G) {
   release_all(G);
   cudaStreamDestroy(G->cap);
   delete G;
+}
+
+int ch_set_chebyshev(ch_grid* G, int method) {
+  if (!G || (method != CH_CHEB_FFT && method != CH_CHEB_TC)) return CH_ERR_ARG;
+  if (G->adj_block) return CH_ERR_STATE;   // not while a reverse sweep is open
+  if (method == CH_CHEB_TC) {
+    if (G->prec == CH_PREC_DFLOAT) return CH_ERR_ARG;
+    if (!G->cf) {
+      const GridDev& g = G->g;
+      std::vector<uint16_t> dig[2];
+      std::vector<int> fe[2];
+      chf::ChebTc t[2];
+      for (int dir = 0; dir < 2; ++dir) {
+        int NT, nNt, Kp;
+        if (chf::cheb_tc_tables(g.N, dir, dig[dir], fe[dir], NT, nNt, Kp) != 0) return CH_ERR_SIZE;
+        t[dir].NT = NT;
+        t[dir].nNt = nNt;
+        t[dir].Kp = Kp;
+        void* dd = galloc(G, dig[dir].size() * sizeof(uint16_t));
+        void* df = galloc(G, fe[dir].size() * sizeof(int));
+        if (!dd || !df) return CH_ERR_ALLOC;
+        CK(cudaMemcpy(dd, dig[dir].data(), dig[dir].size() * sizeof(uint16_t),
+                      cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(df, fe[dir].data(), fe[dir].size() * sizeof(int), cudaMemcpyHostToDevice));
+        t[dir].dig = (const uint16_t*)dd;
+        t[dir].fexp = (const int*)df;
+        CK(chf::cheb_tc_prepare(NT));
+      }
+      CK(chf::zline_coef_prepare(g));
+      int* err = (int*)galloc(G, sizeof(int));
+      double2* cf = (double2*)galloc(G, (size_t)kNl * G->fs * sizeof(double2));
+      if (!err || !cf) return CH_ERR_ALLOC;
+      CK(cudaMemset(err, 0, sizeof(int)));
+      G->tcf = t[0];
+      G->tcb = t[1];
+      G->tc_err = err;
+      G->cf = cf;
+    }
+  }
+  drop_graph(G);
+  G->cheb = method;
+  return CH_OK;
+}
+
+int ch_get_chebyshev(const ch_grid* G) { return G ? G->cheb : CH_ERR_ARG; }
+
+int ch_chebyshev_lines(ch_grid* G, int dir, const double* in, double* out, int nf) {
+  if (!G || !in || !out || nf < 1 || (dir != 0 && dir != 1)) return CH_ERR_ARG;
+  const GridDev& g = G->g;
+  if (G->cheb == CH_CHEB_TC) {
+    CK(chf::launch_cheb_tc(0, 0, in, G->fs, out, G->fs, nf, g.Mx * g.ny, g.nz,
+                           dir == 0 ? G->tcf : G->tcb, G->tc_err, G->stream));
+  } else {
+    CK(chf::launch_dct_lines(dir, 0, g, in, (double2*)out, nf, G->fs, G->pz, G->stream));
+  }
+  return CH_OK;
+}
+
+int ch_device_status(ch_grid* G) {
+  if (!G) return CH_ERR_ARG;
+  CK(cudaStreamSynchronize(G->stream));
+  if (G->tc_err) {
+    int te = 0;
+    CK(cudaMemcpy(&te, G->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (te) {
+      CK(cudaMemset(G->tc_err, 0, sizeof(int)));
+      return CH_ERR_TIMEOUT;
+    }
+  }
+  return CH_OK;
 }
 
 }  // extern "C"

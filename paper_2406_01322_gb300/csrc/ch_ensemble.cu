@@ -77,7 +77,7 @@ using chf::Member;
 
 namespace {
 
-constexpr int kStages = CH_STEP_KERNELS;
+constexpr int kStages = CH_ENSEMBLE_STAGES;
 
 struct Tuning {
   int style[3] = {0, 0, 0};        // radix style of x, y, z transforms

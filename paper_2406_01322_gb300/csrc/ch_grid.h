@@ -92,6 +92,14 @@ struct ch_grid {
   void* seg_block = nullptr;  // y-padded fields of the states of one recomputed segment
   int seg_cap = 0;            // states that seg_block holds
   int nl_stale = 0;  // 1: the state was replaced by a reverse step; products not recomputed
+
+  // Chebyshev transform of the step: CH_CHEB_FFT (inside zrhs / zbwd) or CH_CHEB_TC (tensor
+  // cores, two extra launches); the tables, the coefficient buffer (9 fields) and the error flag
+  // of the bounded device waits exist once CH_CHEB_TC was selected
+  int cheb = 0;
+  chf::ChebTc tcf, tcb;
+  double2* cf = nullptr;
+  int* tc_err = nullptr;
 };
 
 // launch schedule of one step on stream s (events optional) and the non-linear evaluation

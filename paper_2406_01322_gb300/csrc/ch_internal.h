@@ -2,6 +2,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
 
 #include "ch_common.cuh"
 
@@ -48,6 +51,16 @@ cudaError_t launch_zbwd(int update, int prec, int nout, const GridDev& g, const 
                         double2* st_om, double2* st_w, double2* st_phi, void* bw, long long fs,
                         const FftPlan& pz, cudaStream_t s);
 size_t zline_smem(const GridDev& g);
+// the same two kernels around the tensor-core Chebyshev transform: zrhs reading the nine
+// products' coefficients cf (float64), zbwd (update, 5 outputs) writing coefficients to cf
+cudaError_t launch_zrhs_coef(const GridDev& g, const double2* cf, long long fs,
+                             const double2* st_om, const double2* st_w, const double2* st_phi,
+                             double2* h_om, double2* h_w, double2* h_phi, double2* R, int first,
+                             const FftPlan& pz, cudaStream_t s);
+cudaError_t zline_coef_prepare(const GridDev& g);   // shared-memory limits of the two, eagerly
+cudaError_t launch_zbwd_coef(const GridDev& g, const double2* R, double2* st_om, double2* st_w,
+                             double2* st_phi, double2* cf, long long fs, const FftPlan& pz,
+                             cudaStream_t s);
 // time-independent tau-operator table (g.fac, fac_doubles(g) doubles), built once
 size_t fac_doubles(const GridDev& g);
 cudaError_t build_factor_table(const GridDev& g, double* fac, cudaStream_t s);
@@ -162,5 +175,25 @@ cudaError_t launch_adj_xline(const GridDev& g, const double2* in6, const double2
 cudaError_t launch_diag(const GridDev& g, const double* phys7, long long fs,
                         const double2* st_phi, const double* ccw, const double* dzl,
                         const double* qint, double* part, double* out, cudaStream_t s);
+
+// Chebyshev transform along z as an exact-split (Ozaki) bf16 matrix product on the tensor cores
+// (ch_tc.cu).  Tables of one direction (dir 0 forward: samples -> coefficients; 1 backward):
+// nNt output slices of NT columns, K padded to Kp (a multiple of 16, < 512).
+struct ChebTc {
+  const uint16_t* dig = nullptr;   // device: per slice, per K chunk, eight NT x KC digit planes
+  const int* fexp = nullptr;       // device: output-row scale exponents F_n (nNt NT entries)
+  int NT = 0, nNt = 0, Kp = 0;
+};
+// host tables; 0 or -1 (size not supported)
+int cheb_tc_tables(int N, int dir, std::vector<uint16_t>& dig, std::vector<int>& fexp, int& NT,
+                   int& nNt, int& Kp);
+size_t cheb_tc_smem(int NT);
+// raise the shared-memory limit of every instantiation for slice width NT (before any capture)
+cudaError_t cheb_tc_prepare(int NT);
+// nf fields of complex lines, element type tin / tout (0 float64, 1 float32), field strides
+// fsi / fso (complex elements), nlines lines of Nz; *err |= 1 if a bounded wait gave up
+cudaError_t launch_cheb_tc(int tin, int tout, const void* in, long long fsi, void* out,
+                           long long fso, int nf, int nlines, int Nz, const ChebTc& t, int* err,
+                           cudaStream_t s);
 
 }  // namespace chf

@@ -305,7 +305,10 @@ __device__ void dct_backward_lines_store(const ZSmem& z, int first, int cnt, int
 }
 
 // ---- zrhs: right-hand sides of the three implicit problems ---------------------------------
-template <typename T>
+// PRE = 1: nl holds the Chebyshev coefficients of the nine products (float64, transformed by
+// the tensor-core kernel), so the forward DCTs are skipped; the combinations below are linear
+// with z-independent factors and are formed the same way in coefficient space.
+template <typename T, int PRE = 0>
 __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>::t* __restrict__ nl,
                                           long long fs, const double2* __restrict__ st_om,
                                           const double2* __restrict__ st_w,
@@ -372,7 +375,9 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
     LN(z, 6, Nz)[n] = p3;
   }
   __syncthreads();
-  for (int f0 = 0; f0 < 7; f0 += NBF) dct_forward_lines(z, f0, (7 - f0 < NBF) ? 7 - f0 : NBF, Nz, N, pz, g.zcs);
+  if (!PRE)
+    for (int f0 = 0; f0 < 7; f0 += NBF)
+      dct_forward_lines(z, f0, (7 - f0 < NBF) ? 7 - f0 : NBF, Nz, N, pz, g.zcs);
   // G = phi^3 - (1 + shat) phi
   for (int n = tid; n < Nz; n += blockDim.x)
     LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * LN(z, 12, Nz)[n];
@@ -426,7 +431,7 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   }
 }
 
-template <typename T>
+template <typename T, int PRE = 0>
 __global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T>::t* __restrict__ nl,
                                                   long long fs, const double2* __restrict__ st_om,
                                                   const double2* __restrict__ st_w,
@@ -435,7 +440,7 @@ __global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T
                                                   double2* __restrict__ h_w,
                                                   double2* __restrict__ h_phi,
                                                   double2* __restrict__ R, int first, FftPlan pz) {
-  zrhs_body<T>(g, nl, fs, st_om, st_w, st_phi, h_om, h_w, h_phi, R, first, pz, blockIdx.x);
+  zrhs_body<T, PRE>(g, nl, fs, st_om, st_w, st_phi, h_om, h_w, h_phi, R, first, pz, blockIdx.x);
 }
 
 // ---- tau elimination with tabulated factors -----------------------------------------------
@@ -885,7 +890,9 @@ __global__ void mixed_kernel(GridDev g, double* __restrict__ fac) {
 // Output (backward DCT-I to samples in z): NOUT = 5: u, v (continuity + omega_z definition), w,
 // phi, D phi (the step: i kx phi and i ky phi are formed by the x and y passes); NOUT = 7:
 // u, v, w, phi, i kx phi, i ky phi, D phi.
-template <typename T, int UPDATE, int NOUT>
+// COEF = 1: the NOUT lines are stored as Chebyshev coefficients (float64, bw typed double2) for
+// the tensor-core backward transform instead of being transformed here.
+template <typename T, int UPDATE, int NOUT, int COEF = 0>
 __device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __restrict__ R,
                                           double2* __restrict__ st_om, double2* __restrict__ st_w,
                                           double2* __restrict__ st_phi,
@@ -957,20 +964,27 @@ __device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __res
     }
   }
   __syncthreads();
+  if (COEF) {
+    for (int idx = tid; idx < NOUT * Nz; idx += blockDim.x) {
+      const int f = idx / Nz, n = idx - f * Nz;
+      bw[(long long)f * fs + off + n] = from_d2<T2>(LN(z, f, Nz)[n]);
+    }
+    return;
+  }
   for (int f0 = 0; f0 < NOUT; f0 += NBF) {
     const int cnt = (NOUT - f0 < NBF) ? NOUT - f0 : NBF;
     dct_backward_lines_store<T2>(z, f0, cnt, Nz, N, pz, g.zcs, bw, fs, off, f0);
   }
 }
 
-template <typename T, int UPDATE, int NOUT>
+template <typename T, int UPDATE, int NOUT, int COEF = 0>
 __global__ void __launch_bounds__(ZT) zbwd_kernel(GridDev g, const double2* __restrict__ R,
                                                   double2* __restrict__ st_om,
                                                   double2* __restrict__ st_w,
                                                   double2* __restrict__ st_phi,
                                                   typename C2<T>::t* __restrict__ bw,
                                                   long long fs, FftPlan pz) {
-  zbwd_body<T, UPDATE, NOUT>(g, R, st_om, st_w, st_phi, bw, fs, pz, blockIdx.x);
+  zbwd_body<T, UPDATE, NOUT, COEF>(g, R, st_om, st_w, st_phi, bw, fs, pz, blockIdx.x);
 }
 
 // set_fields projection: u, v, w, phi samples (after the x/y transforms) -> state
@@ -1818,6 +1832,38 @@ cudaError_t launch_zrhs(int prec, const GridDev& g, const void* nl, long long fs
     zrhs_kernel<df><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const df2*)nl, fs, st_om, st_w, st_phi,
                                                   h_om, h_w, h_phi, R, first, pz);
   }
+  return cudaGetLastError();
+}
+
+static int cur_zrhs_coef = 0, cur_zbwd_coef = 0;
+
+cudaError_t zline_coef_prepare(const GridDev& g) {
+  const size_t smem = zline_smem(g);
+  cudaError_t e = ensure_smem(zrhs_kernel<double, 1>, smem, &cur_zrhs_coef);
+  if (e == cudaSuccess) e = ensure_smem(zbwd_kernel<double, 1, 5, 1>, smem, &cur_zbwd_coef);
+  return e;
+}
+
+cudaError_t launch_zrhs_coef(const GridDev& g, const double2* cf, long long fs,
+                             const double2* st_om, const double2* st_w, const double2* st_phi,
+                             double2* h_om, double2* h_w, double2* h_phi, double2* R, int first,
+                             const FftPlan& pz, cudaStream_t s) {
+  const size_t smem = zline_smem(g);
+  cudaError_t e = ensure_smem(zrhs_kernel<double, 1>, smem, &cur_zrhs_coef);
+  if (e != cudaSuccess) return e;
+  zrhs_kernel<double, 1><<<g.Mx * g.ny, ZT, smem, s>>>(g, cf, fs, st_om, st_w, st_phi, h_om, h_w,
+                                                       h_phi, R, first, pz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zbwd_coef(const GridDev& g, const double2* R, double2* st_om, double2* st_w,
+                             double2* st_phi, double2* cf, long long fs, const FftPlan& pz,
+                             cudaStream_t s) {
+  const size_t smem = zline_smem(g);
+  cudaError_t e = ensure_smem(zbwd_kernel<double, 1, 5, 1>, smem, &cur_zbwd_coef);
+  if (e != cudaSuccess) return e;
+  zbwd_kernel<double, 1, 5, 1><<<g.Mx * g.ny, ZT, smem, s>>>(g, R, st_om, st_w, st_phi, cf, fs,
+                                                             pz);
   return cudaGetLastError();
 }
 
