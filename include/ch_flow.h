@@ -306,6 +306,8 @@ void ch_destroy(ch_grid* g);
 
 /* Static string for a status code. */
 const char* ch_status_string(int status);
+/* Text of the CUDA error behind the calling thread's last CH_ERR_CUDA ("no error" if none). */
+const char* ch_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

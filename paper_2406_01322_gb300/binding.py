@@ -29,8 +29,11 @@ CHEB_TC = 1
 
 
 class ChError(RuntimeError):
-    def __init__(self, fn, code):
-        super().__init__(f"{fn} failed: {STATUS.get(code, code)} ({code})")
+    def __init__(self, fn, code, detail=None):
+        msg = f"{fn} failed: {STATUS.get(code, code)} ({code})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
         self.code = code
 
 
@@ -101,6 +104,7 @@ _SIGS = {
     "ch_ensemble_destroy": (None, [_P]),
     "ch_destroy": (None, [_P]),
     "ch_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ch_last_cuda_error": (ctypes.c_char_p, []),
     "ch_set_chebyshev": (ctypes.c_int, [_P, ctypes.c_int]),
     "ch_get_chebyshev": (ctypes.c_int, [_P]),
     "ch_chebyshev_lines": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
@@ -131,7 +135,10 @@ def lib():
 
 def _ck(name, code):
     if code != CH_OK:
-        raise ChError(name, code)
+        detail = None
+        if code == -4:
+            detail = lib().ch_last_cuda_error().decode()
+        raise ChError(name, code, detail)
 
 
 def _ptr(t):

@@ -155,10 +155,14 @@ using chf::step_ymap;
 
 namespace {
 
+// the CUDA error behind the last CH_ERR_CUDA of this thread (ch_last_cuda_error)
+thread_local cudaError_t t_last_cuda = cudaSuccess;
+
 #define CK(x)                                       \
   do {                                              \
     cudaError_t e__ = (x);                          \
     if (e__ != cudaSuccess) {                       \
+      t_last_cuda = e__;                            \
       cudaGetLastError();                           \
       return CH_ERR_CUDA;                           \
     }                                               \
@@ -281,6 +285,8 @@ int ch_state_phys7(ch_grid* G) { return state_to_phys7(G, 7); }
 int ch_eval_nonlinear(ch_grid* G) { return eval_nonlinear_impl(G); }
 
 extern "C" {
+
+const char* ch_last_cuda_error(void) { return cudaGetErrorString(t_last_cuda); }
 
 const char* ch_status_string(int st) {
   switch (st) {
@@ -787,6 +793,17 @@ int ch_set_chebyshev(ch_grid* G, int method) {
         CK(chf::cheb_tc_prepare(NT));
       }
       CK(chf::zline_coef_prepare(g));
+      // one persistent CTA per SM, each with a plane cache for one tile of rows
+      int dev = 0, nsm = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      if (nsm < 1) nsm = 1;
+      void* cache = galloc(G, (size_t)nsm * chf::cheb_tc_cache_bytes(t[0].Kp));
+      if (!cache) return CH_ERR_ALLOC;
+      for (int dir = 0; dir < 2; ++dir) {
+        t[dir].cache = (uint32_t*)cache;
+        t[dir].ctas = nsm;
+      }
       int* err = (int*)galloc(G, sizeof(int));
       double2* cf = (double2*)galloc(G, (size_t)kNl * G->fs * sizeof(double2));
       if (!err || !cf) return CH_ERR_ALLOC;

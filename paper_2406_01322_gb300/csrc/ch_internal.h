@@ -182,8 +182,12 @@ cudaError_t launch_diag(const GridDev& g, const double* phys7, long long fs,
 struct ChebTc {
   const uint16_t* dig = nullptr;   // device: per slice, per K chunk, eight NT x KC digit planes
   const int* fexp = nullptr;       // device: output-row scale exponents F_n (nNt NT entries)
+  uint32_t* cache = nullptr;       // device: A digit planes of one tile per persistent CTA
   int NT = 0, nNt = 0, Kp = 0;
+  int ctas = 0;                    // persistent CTAs (the cache holds ctas cheb_tc_cache_bytes)
 };
+// bytes of plane cache one persistent CTA needs for rows of padded length Kp
+size_t cheb_tc_cache_bytes(int Kp);
 // host tables; 0 or -1 (size not supported)
 int cheb_tc_tables(int N, int dir, std::vector<uint16_t>& dig, std::vector<int>& fexp, int& NT,
                    int& nNt, int& Kp);

@@ -45,7 +45,7 @@ namespace chf {
 
 namespace {
 
-constexpr int TCT = 512;          // producer threads per CTA (plus one issuer warp)
+constexpr int TCT = 512;          // threads per CTA
 constexpr int TCM = 128;          // rows per tile = tensor-memory lanes
 constexpr int TCKC = 144;         // K per chunk
 constexpr int TCG = TCKC / 8;     // 8-element core-matrix groups per chunk
@@ -68,7 +68,18 @@ __device__ __forceinline__ uint64_t gtime() {
   return t;
 }
 // bounded wait for the phase with the given parity; false if it did not complete in time
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;   // the common case: no clock read
   const uint64_t t0 = gtime();
   while (true) {
     uint32_t done;
@@ -122,7 +133,6 @@ __device__ __forceinline__ void tmem_ld8x4(uint32_t addr, int stride, uint32_t (
                :
                : "memory");
 }
-
 // ---- float bits -> biased fixed point, digits, and back ---------------------------------------
 template <typename T> struct FBits;
 template <> struct FBits<double> {
@@ -158,16 +168,20 @@ __device__ __forceinline__ unsigned long long to_biased(typename FBits<T>::U b, 
   return neg ? kBias - X : kBias + X;
 }
 
-// digits at bit offset sh of two elements, as two bf16 packed in one word (first in the low half)
-__device__ __forceinline__ uint32_t digit_pair(unsigned long long y0, unsigned long long y1,
-                                               int sh) {
-  const uint32_t u0 = (uint32_t)(y0 >> sh) & 127u, u1 = (uint32_t)(y1 >> sh) & 127u;
-  const float f0 = __uint_as_float(0x4B000000u | u0) - 8388672.0f;   // u - 64, exact
-  const float f1 = __uint_as_float(0x4B000000u | u1) - 8388672.0f;
+// digits at bit offset sh (< 28) of two elements' 28-bit halves, as two bf16 packed in one word
+// (first in the low half): u = 7-bit group, value u - 64 through the float 2^23 + u
+__device__ __forceinline__ uint32_t digit_pair(uint32_t w0, uint32_t w1, int sh) {
+  const float f0 = __uint_as_float(0x4B000000u | ((w0 >> sh) & 127u)) - 8388672.0f;
+  const float f1 = __uint_as_float(0x4B000000u | ((w1 >> sh) & 127u)) - 8388672.0f;
   return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
 }
 
-// integer value of an fp32 accumulator (integer-valued, |v| < 2^24)
+// integer value of an fp32 accumulator: exact for integer values of magnitude <= 2^22 through
+// the float 1.5 2^23 + v (small K) ...
+__device__ __forceinline__ int acc_int_small(uint32_t b) {
+  return __float_as_int(__uint_as_float(b) + 12582912.0f) - 0x4B400000;
+}
+// ... and by the bit pattern for any integer value below 2^24 (larger K)
 __device__ __forceinline__ int acc_int(uint32_t b) {
   int e = (int)((b >> 23) & 0xFF);
   if (e < 127) return 0;
@@ -180,45 +194,30 @@ __device__ __forceinline__ int acc_int(uint32_t b) {
 template <typename TO> __device__ TO scaled(long long T, int e);
 template <> __device__ __forceinline__ double scaled<double>(long long T, int e) {
   if (T == 0) return 0.0;
-  const bool neg = T < 0;
-  unsigned long long a = neg ? 0ull - (unsigned long long)T : (unsigned long long)T;
+  const unsigned long long sg = (unsigned long long)T & 0x8000000000000000ull;
+  unsigned long long a = sg ? 0ull - (unsigned long long)T : (unsigned long long)T;
   const int lz = __clzll((long long)a);
-  a <<= lz;
-  unsigned long long mant = a >> 11;
-  const unsigned long long rem = a & 0x7FFull;
-  int ex = 63 - lz + e;
-  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
-    ++mant;
-    if (mant >> 53) {
-      mant >>= 1;
-      ++ex;
-    }
-  }
-  const int be = ex + 1023;
+  a <<= lz;                                     // leading one at bit 63
+  unsigned long long mant = a >> 11;            // 53 bits
+  const unsigned rem = (unsigned)(a & 0x7FFull);
+  mant += (rem + (unsigned)(mant & 1ull)) > 0x400u ? 1ull : 0ull;   // to nearest, ties to even
+  const int be = 63 - lz + e + 1023 + (int)(mant >> 53);
   if (be <= 0 || be >= 2047) return ldexp((double)T, e);
-  return __longlong_as_double((long long)(((unsigned long long)neg << 63) |
-                                          ((unsigned long long)be << 52) |
+  return __longlong_as_double((long long)(sg | ((unsigned long long)be << 52) |
                                           (mant & 0xFFFFFFFFFFFFFull)));
 }
 template <> __device__ __forceinline__ float scaled<float>(long long T, int e) {
   if (T == 0) return 0.0f;
-  const bool neg = T < 0;
-  unsigned long long a = neg ? 0ull - (unsigned long long)T : (unsigned long long)T;
+  const unsigned long long sg = (unsigned long long)T & 0x8000000000000000ull;
+  unsigned long long a = sg ? 0ull - (unsigned long long)T : (unsigned long long)T;
   const int lz = __clzll((long long)a);
   a <<= lz;
-  unsigned long long mant = a >> 40;
-  const unsigned long long rem = a & 0xFFFFFFFFFFull, half = 1ull << 39;
-  int ex = 63 - lz + e;
-  if (rem > half || (rem == half && (mant & 1ull))) {
-    ++mant;
-    if (mant >> 24) {
-      mant >>= 1;
-      ++ex;
-    }
-  }
-  const int be = ex + 127;
+  unsigned long long mant = a >> 40;            // 24 bits
+  const unsigned long long rem = a & 0xFFFFFFFFFFull;
+  mant += (rem + (mant & 1ull)) > (1ull << 39) ? 1ull : 0ull;
+  const int be = 63 - lz + e + 127 + (int)(mant >> 24);
   if (be <= 0 || be >= 255) return ldexpf((float)T, e);
-  return __uint_as_float(((unsigned)neg << 31) | ((unsigned)be << 23) |
+  return __uint_as_float((unsigned)(sg >> 32) | ((unsigned)be << 23) |
                          (unsigned)(mant & 0x7FFFFFull));
 }
 template <typename TO> __device__ __forceinline__ TO qnan();
@@ -228,25 +227,36 @@ template <> __device__ __forceinline__ double qnan<double>() {
 template <> __device__ __forceinline__ float qnan<float>() { return __uint_as_float(0x7FC00000u); }
 
 __host__ __device__ constexpr size_t tc_smem_bytes(int NT) {
-  return (size_t)8 * NT * TCKC * 2 + (size_t)2 * TCM * TCKC * 2 + TCM * sizeof(int) + 64;
+  // B planes, two A planes, row exponents, eight barriers and the tensor-memory address
+  // (80 bytes), output-column exponents (at most 512)
+  return (size_t)8 * NT * TCKC * 2 + (size_t)2 * TCM * TCKC * 2 + TCM * sizeof(int) + 80 +
+         512 * sizeof(int);
 }
 
 // ---- the transform kernel ---------------------------------------------------------------------
 // in / out: nf fields of complex lines (re, im interleaved), field stride fsi / fso complex
-// elements, line stride Nz; bdig: nNt output slices of 8 NT Kp bf16 digits (per slice: per chunk
-// of K, the eight digit planes, each NT x KC in the canonical core-matrix layout); fexp: F_n.
+// elements, line stride Nz; bdig: nNt output slices of 8 NT Kp bf16 digits (per slice and chunk
+// of K: the eight digit planes stacked as one 8 NT x KC matrix in the canonical no-swizzle
+// K-major core-matrix layout, plane j in rows j NT ..); fexp: F_n; cache: per CTA, nchunk x 8
+// A digit planes of one tile (TCM x TCKC bf16 each, the shared-memory layout).
 //
-// Warps 0..15 produce (row exponents, digit planes) and run the epilogue; warp 16 allocates the
-// tensor memory and one of its lanes issues the bulk copies and the MMAs.  Plane t goes to
-// shared buffer t % 2: the producers wait for `empty` of that buffer (the MMAs of plane t - 2
-// completed, signalled by tcgen05.commit), write the plane and arrive on `full` (one arrival
-// per warp); the issuer waits for `full`, issues the plane's MMAs and commits to `empty`.
+// Persistent CTAs (17 warps) walk the tiles of 128 rows; per tile they loop over the nNt output
+// slices.  Warps 0..15 turn the rows into fixed-point values and, for the first slice, write the
+// eight digit planes into a double-buffered shared tile (and the CTA's plane cache in global
+// memory, which stays in L2); they drain the accumulators of every slice.  Lane 0 of warp 16
+// allocates the tensor memory and issues the bulk copies and the MMAs; for the later slices it
+// copies the cached planes back itself, one plane ahead of the MMAs.  Plane t (counted over
+// tiles, slices and chunks) uses shared buffer t % 2: whoever fills it first waits for `empty`
+// of that buffer (the MMAs of plane t - 2 completed, signalled by tcgen05.commit); generated
+// planes are announced on `full` (one arrival per producer warp), copied ones on `loaded`
+// (transaction count).  The next slice's digits of B are copied while the accumulators drain;
+// its MMAs start once every producer warp has arrived on `drained`.
 template <typename TI, typename TO, int NT>
 __global__ void __launch_bounds__(TCT + 32, 1)
     cheb_tc_kernel(const TI* __restrict__ in, long long fsi, TO* __restrict__ out, long long fso,
-                   int nlines, int Nz, int Kp, int tpf, int nNt,
+                   int nlines, int Nz, int Kp, int tpf, int ntiles, int nNt,
                    const uint16_t* __restrict__ bdig, const int* __restrict__ fexp,
-                   int* __restrict__ err) {
+                   uint32_t* __restrict__ cache, int* __restrict__ err) {
   typedef FBits<TI> F;
   typedef typename F::U U;
   extern __shared__ __align__(1024) unsigned char tsm[];
@@ -254,66 +264,108 @@ __global__ void __launch_bounds__(TCT + 32, 1)
   unsigned char* sA = sB + (size_t)8 * NT * TCKC * 2;
   int* sE = reinterpret_cast<int*>(sA + (size_t)2 * TCM * TCKC * 2);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(sE + TCM);
-  uint32_t* sT = reinterpret_cast<uint32_t*>(bars + 5);
+  uint32_t* sT = reinterpret_cast<uint32_t*>(bars + 9);
+  int* sF = reinterpret_cast<int*>(bars + 10);   // F_n of every output column (nNt NT <= 512)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nt = blockIdx.x % nNt, tile = blockIdx.x / nNt;
-  const int fld = tile / tpf;
-  const int line0 = (tile - fld * tpf) * (TCM / 2);
   const int nchunk = (Kp + TCKC - 1) / TCKC;
-  // barriers: B loaded; full[b] (16 producer warps arrived); empty[b] (MMAs of the plane done)
-  const uint32_t barB = su32(&bars[0]), barFull = su32(&bars[1]), barEmpty = su32(&bars[3]);
+  constexpr uint32_t kPlaneBytes = TCM * TCKC * 2;
+  // barriers: B loaded; full[b] (16 producer warps); loaded[b] (a cached plane copied);
+  // empty[b] (MMAs of the plane done); drained (16 producer warps read the accumulators);
+  // sliced (every MMA of a slice done: one phase per slice, so the producers, which skip the
+  // planes of the later slices, never wait on a phase more than one ahead)
+  const uint32_t barB = su32(&bars[0]), barFull = su32(&bars[1]), barLoad = su32(&bars[3]);
+  const uint32_t barEmpty = su32(&bars[5]), barDrain = su32(&bars[7]);
+  const uint32_t barSlice = su32(&bars[8]);
   const size_t bslice = (size_t)8 * NT * Kp;
-  const bool issuer = (warp == TCT / 32);
-  if (issuer && lane == 0) {
+  uint32_t* ccta = cache + (size_t)blockIdx.x * nchunk * 8 * (kPlaneBytes / 4);
+  const bool issuer_warp = (warp == TCT / 32);
+  const bool issuer = issuer_warp && lane == 0;
+  if (issuer) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barB));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(barFull));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(barFull + 8));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barLoad));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barLoad + 8));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barEmpty));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barEmpty + 8));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(barDrain));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barSlice));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    bulk_load(su32(sB), bdig + (size_t)nt * bslice, (uint32_t)(8 * NT * min(TCKC, Kp) * 2), barB);
   }
-  if (issuer) {
+  if (issuer_warp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(sT)),
                  "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  if (tid < TCT)
+    for (int c = tid; c < nNt * NT; c += TCT) sF[c] = fexp[c];
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  __syncthreads();   // barriers, tensor-memory address and sF visible to every warp
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *sT;
+  const uint32_t sA0 = su32(sA), sB0 = su32(sB);
   bool ok = true;
 
-  if (issuer) {
+  if (issuer_warp) {
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
-                             ((uint32_t)(TCM >> 4) << 24);   // bf16 x bf16 -> fp32, K-major
-      const uint32_t sA0 = su32(sA), sB0 = su32(sB);
-      for (int ch = 0; ch < nchunk; ++ch) {
-        const int KCc = min(TCKC, Kp - ch * TCKC);
-        if (ch > 0) {
-          // the previous chunk's last plane (t = 8 ch - 1, buffer 1) must be consumed first
-          ok = mbar_wait(barEmpty + 8, ((8 * ch - 1) >> 1) & 1) && ok;
-          bulk_load(sB0, bdig + (size_t)nt * bslice + (size_t)ch * 8 * NT * TCKC,
-                    (uint32_t)(8 * NT * KCc * 2), barB);
-        }
-        ok = mbar_wait(barB, ch & 1) && ok;
-        for (int i = 0; i < 8; ++i) {
-          const int t = ch * 8 + i, bf = t & 1;
-          ok = mbar_wait(barFull + 8 * bf, (t >> 1) & 1) && ok;
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          // descriptors of k-step 0; a k-step adds 2 core-matrix groups to the start address
-          const uint64_t ad = sdesc(sA0 + (uint32_t)(bf * TCM * TCKC * 2), 2048, 128);
-          for (int j = 0; i + j < 8; ++j) {
-            const uint64_t bd =
-                sdesc(sB0 + (uint32_t)(j * NT * KCc * 2), (NT / 8) * 128, 128);
-            const uint32_t dt = tmem + (uint32_t)((i + j) * NT);
-            for (int s = 0; s < KCc / 16; ++s)
-              mma_bf16(dt, ad + (uint64_t)(s * 256), bd + (uint64_t)(s * 16 * (NT / 8)), idesc,
-                       (uint32_t)((ch | i | s) != 0));
+      // bf16 x bf16 -> fp32, both K-major, M = 128 (N added per MMA)
+      const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCM >> 4) << 24);
+      int t = 0, u = 0, S = 0;           // plane, B copy and slice counters (all tiles)
+      int nfull[2] = {0, 0}, nload[2] = {0, 0};
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int sl = 0; sl < nNt; ++sl, ++S) {
+          for (int ch = 0; ch < nchunk; ++ch, ++u) {
+            const int KCc = min(TCKC, Kp - ch * TCKC);
+            // the previous plane (t - 1) read B; it must be consumed before B is replaced
+            if (u > 0) ok = mbar_wait(barEmpty + 8 * ((t - 1) & 1), ((t - 1) >> 1) & 1) && ok;
+            bulk_load(sB0, bdig + (size_t)sl * bslice + (size_t)ch * 8 * NT * TCKC,
+                      (uint32_t)(8 * NT * KCc * 2), barB);
+            if (sl > 0) {   // first cached plane of this chunk into buffer t % 2
+              if (t >= 2) ok = mbar_wait(barEmpty + 8 * (t & 1), ((t - 2) >> 1) & 1) && ok;
+              // the producers' global stores (acquired through `full`) before the async copy
+              asm volatile("fence.proxy.async.global;" ::: "memory");
+              bulk_load(sA0 + (uint32_t)((t & 1) * kPlaneBytes), ccta + (size_t)ch * 8 * (kPlaneBytes / 4),
+                        kPlaneBytes, barLoad + 8 * (t & 1));
+            }
+            ok = mbar_wait(barB, u & 1) && ok;
+            if (ch == 0 && S > 0) ok = mbar_wait(barDrain, (S - 1) & 1) && ok;
+            for (int i = 0; i < 8; ++i, ++t) {
+              const int bf = t & 1;
+              if (sl == 0) {
+                ok = mbar_wait(barFull + 8 * bf, nfull[bf] & 1) && ok;
+                ++nfull[bf];
+              } else {
+                ok = mbar_wait(barLoad + 8 * bf, nload[bf] & 1) && ok;
+                ++nload[bf];
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              // A plane i times B planes 0 .. 7-i at once: the stacked B rows j NT + n land in
+              // accumulator columns i NT + j NT + n = (i + j) NT + n, the diagonal of (i, j).
+              // N = (8 - i) NT is issued in pieces of at most 256.  A k-step adds 2 core-matrix
+              // groups to both start addresses (4096 bytes of A, 2 NT 128 bytes of B).
+              const uint64_t ad = sdesc(sA0 + (uint32_t)(bf * kPlaneBytes), 2048, 128);
+              const int ntot = (8 - i) * NT;
+              for (int s = 0; s < KCc / 16; ++s)
+                for (int n0 = 0; n0 < ntot; n0 += 256) {
+                  const int nlen = min(256, ntot - n0);
+                  const uint64_t bd = sdesc(sB0 + (uint32_t)(n0 / 8 * 128), NT * 128, 128);
+                  mma_bf16(tmem + (uint32_t)(i * NT + n0), ad + (uint64_t)(s * 256),
+                           bd + (uint64_t)(s * 16 * NT), idesc0 | ((uint32_t)(nlen >> 3) << 17),
+                           (uint32_t)((ch | i | s) != 0));
+                }
+              mma_commit(barEmpty + 8 * bf);
+              if (i == 7 && ch == nchunk - 1) mma_commit(barSlice);
+              if (sl > 0 && i < 7) {
+                // the next cached plane into the other buffer, once its MMAs (plane t - 1) ended
+                const int tn = t + 1;
+                if (tn >= 2) ok = mbar_wait(barEmpty + 8 * (tn & 1), ((tn - 2) >> 1) & 1) && ok;
+                bulk_load(sA0 + (uint32_t)((tn & 1) * kPlaneBytes),
+                          ccta + (size_t)(ch * 8 + i + 1) * (kPlaneBytes / 4), kPlaneBytes,
+                          barLoad + 8 * (tn & 1));
+              }
+            }
           }
-          mma_commit(barEmpty + 8 * bf);
         }
       }
     }
@@ -322,45 +374,41 @@ __global__ void __launch_bounds__(TCT + 32, 1)
     // producers: warp = 8-row core-matrix group, lane = (row in the group, pair of k)
     const int r = lane >> 2, q = lane & 3;
     const int m = warp * 8 + r;
-    const int line = line0 + (m >> 1);
-    const bool rowok = line < nlines;
-    const TI* src = in + ((size_t)fld * fsi + (size_t)(rowok ? line : 0) * Nz) * 2 + (m & 1);
-    // chunk 0 in registers; the largest exponent field of the row over all of K
-    unsigned long long y[2 * TCG];
-    int maxe = 1;
-    {
-      const int ngr = min(TCKC, Kp) / 8;
+    constexpr int CW = NT / 4;
+    const int qd = warp & 3, cg = warp >> 2;
+    const int mm = qd * 32 + lane;
+    const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(cg * CW);
+    int t = 0, S = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int fld = tile / tpf;
+      const int line0 = (tile - fld * tpf) * (TCM / 2);
+      const int line = line0 + (m >> 1);
+      const bool rowok = line < nlines;
+      const TI* src = in + ((size_t)fld * fsi + (size_t)(rowok ? line : 0) * Nz) * 2 + (m & 1);
+      // the largest exponent field of the row over all of K
+      int maxe = 1;
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const int ngc = min(TCKC, Kp - ch * TCKC) / 8;
 #pragma unroll
-      for (int gl = 0; gl < TCG; ++gl)
+        for (int gl = 0; gl < TCG; ++gl)
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int k = 8 * gl + 2 * q + e;
-          U b = 0;
-          if (gl < ngr && rowok && k < Nz) b = F::bits(src[2 * (size_t)k]);
-          y[2 * gl + e] = (unsigned long long)b;
-          maxe = max(maxe, (int)((b >> F::MB) & (U)F::EMAX));
-        }
-    }
-    for (int ch = 1; ch < nchunk; ++ch) {
-      const int ngr = min(TCKC, Kp - ch * TCKC) / 8;
-#pragma unroll
-      for (int gl = 0; gl < TCG; ++gl)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int k = ch * TCKC + 8 * gl + 2 * q + e;
-          if (gl < ngr && rowok && k < Nz)
-            maxe = max(maxe, (int)((F::bits(src[2 * (size_t)k]) >> F::MB) & (U)F::EMAX));
-        }
-    }
-    maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, 1));
-    maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, 2));
-    if (q == 0) sE[m] = maxe;
-    for (int ch = 0; ch < nchunk; ++ch) {
-      const int ngr = min(TCKC, Kp - ch * TCKC) / 8;
-      if (ch == 0) {
-#pragma unroll
-        for (int i = 0; i < 2 * TCG; ++i) y[i] = to_biased<TI>((U)y[i], maxe);
-      } else {
+          for (int e = 0; e < 2; ++e) {
+            const int k = ch * TCKC + 8 * gl + 2 * q + e;
+            if (gl < ngc && rowok && k < Nz)
+              maxe = max(maxe, (int)((F::bits(src[2 * (size_t)k]) >> F::MB) & (U)F::EMAX));
+          }
+      }
+      maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, 1));
+      maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, 2));
+      // sE: every producer warp has read the previous tile's entries (before its slice loop)
+      asm volatile("bar.sync 1, %0;" ::"r"(TCT) : "memory");
+      if (q == 0) sE[m] = maxe;
+      asm volatile("bar.sync 1, %0;" ::"r"(TCT) : "memory");
+      const int me = sE[mm];
+      // first slice: generate the planes of every chunk (cached for the later slices)
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const int ngr = min(TCKC, Kp - ch * TCKC) / 8;
+        uint32_t yh[2 * TCG], yl[2 * TCG];   // bits 28..55 and 0..27 of X + bias
 #pragma unroll
         for (int gl = 0; gl < TCG; ++gl)
 #pragma unroll
@@ -368,67 +416,79 @@ __global__ void __launch_bounds__(TCT + 32, 1)
             const int k = ch * TCKC + 8 * gl + 2 * q + e;
             U b = 0;
             if (gl < ngr && rowok && k < Nz) b = F::bits(src[2 * (size_t)k]);
-            y[2 * gl + e] = to_biased<TI>(b, maxe);
+            const unsigned long long y = to_biased<TI>(b, maxe);
+            yh[2 * gl + e] = (uint32_t)(y >> 28);
+            yl[2 * gl + e] = (uint32_t)y & 0xFFFFFFFu;
           }
-      }
-      for (int i = 0; i < 8; ++i) {
-        const int t = ch * 8 + i, bf = t & 1;
-        if (t >= 2) ok = mbar_wait(barEmpty + 8 * bf, ((t - 2) >> 1) & 1) && ok;
-        uint32_t* dst = reinterpret_cast<uint32_t*>(sA + (size_t)bf * TCM * TCKC * 2);
-        const int sh = 7 * (7 - i);
+        for (int i = 0; i < 8; ++i, ++t) {
+          const int bf = t & 1;
+          if (t >= 2) ok = mbar_wait(barEmpty + 8 * bf, ((t - 2) >> 1) & 1) && ok;
+          uint32_t* dst = reinterpret_cast<uint32_t*>(sA + (size_t)bf * kPlaneBytes);
+          uint32_t* gdst = ccta + (size_t)(ch * 8 + i) * (kPlaneBytes / 4);
+          const int sh = 7 * (3 - (i & 3));
 #pragma unroll
-        for (int gl = 0; gl < TCG; ++gl)
-          if (gl < ngr)
-            dst[(gl * 16 + warp) * 32 + lane] = digit_pair(y[2 * gl], y[2 * gl + 1], sh);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          for (int gl = 0; gl < TCG; ++gl)
+            if (gl < ngr) {
+              const uint32_t w = i < 4 ? digit_pair(yh[2 * gl], yh[2 * gl + 1], sh)
+                                       : digit_pair(yl[2 * gl], yl[2 * gl + 1], sh);
+              dst[(gl * 16 + warp) * 32 + lane] = w;
+              __stcg(gdst + (gl * 16 + warp) * 32 + lane, w);   // to L2, read by bulk copies
+            }
+          // shared-memory plane for the MMAs; global copy for the issuer's later bulk copies
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(barFull + 8 * bf)
+                         : "memory");
+        }
+      }
+      const int oline = line0 + (mm >> 1);
+      TO* dstp =
+          out + ((size_t)fld * fso + (size_t)(oline < nlines ? oline : 0) * Nz) * 2 + (mm & 1);
+      for (int sl = 0; sl < nNt; ++sl, ++S) {
+        if (sl > 0) t += 8 * nchunk;   // planes the issuer copies
+        // every MMA of the slice done
+        ok = mbar_wait(barSlice, S & 1) && ok;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its rows), columns
+        // (w / 4) NT/4 .. + NT/4 - 1 of each of the eight accumulators, 4 at a time
+        const bool orow = ok && oline < nlines;
+        for (int c0 = 0; c0 < CW; c0 += 4) {
+          uint32_t v[8][4];
+          tmem_ld8x4(tb + (uint32_t)c0, NT, v);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int n = sl * NT + cg * CW + c0 + e;
+            if (orow && n < Nz) {
+              int g[8];
+              if (Kp <= TCKC) {
+#pragma unroll
+                for (int d = 0; d < 8; ++d) g[d] = acc_int_small(v[d][e]);
+              } else {
+#pragma unroll
+                for (int d = 0; d < 8; ++d) g[d] = acc_int(v[d][e]);
+              }
+              const long long H = ((long long)(g[0] * 128 + g[1]) * 128 + g[2]) * 128 + g[3];
+              const long long L = ((long long)(g[4] * 128 + g[5]) * 128 + g[6]) * 128 + g[7];
+              const long long T = H * 262144ll + (L >> 10);   // (H 2^28 + L) / 2^10
+              // sum = 2^(E + F - 108) 2^49 (H 2^28 + L) = T 2^(E + F - 49)
+              dstp[2 * (size_t)n] =
+                  me >= F::EMAX ? qnan<TO>() : scaled<TO>(T, me - F::EOFF - 49 + sF[n]);
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0)
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(barFull + 8 * bf)
-                       : "memory");
-      }
-    }
-    const int tl = 8 * nchunk - 1;
-    ok = mbar_wait(barEmpty + 8 * (tl & 1), (tl >> 1) & 1) && ok;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // sE of the other warps' rows: written before their first plane, read after all MMAs,
-    // which needed every warp's planes; the named barrier below orders it for the compiler
-    asm volatile("bar.sync 1, %0;" ::"r"(TCT) : "memory");
-
-    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its rows), columns
-    // (w / 4) NT/4 .. + NT/4 - 1 of each of the eight accumulators
-    constexpr int CW = NT / 4;
-    const int qd = warp & 3, cg = warp >> 2;
-    const int mm = qd * 32 + lane;
-    const int oline = line0 + (mm >> 1);
-    const int me = sE[mm];
-    const bool orow = ok && oline < nlines;
-    TO* dstp =
-        out + ((size_t)fld * fso + (size_t)(oline < nlines ? oline : 0) * Nz) * 2 + (mm & 1);
-    const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(cg * CW);
-    for (int c0 = 0; c0 < CW; c0 += 4) {
-      uint32_t v[8][4];
-      tmem_ld8x4(tb + (uint32_t)c0, NT, v);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int n = nt * NT + cg * CW + c0 + e;
-        if (orow && n < Nz) {
-          long long H = 0, L = 0;
-#pragma unroll
-          for (int d = 0; d < 4; ++d) H = H * 128 + acc_int(v[d][e]);
-#pragma unroll
-          for (int d = 4; d < 8; ++d) L = L * 128 + acc_int(v[d][e]);
-          const long long T = H * 262144ll + (L >> 10);   // (H 2^28 + L) / 2^10
-          // sum = 2^(E + F - 108) 2^49 (H 2^28 + L) = T 2^(E + F - 49)
-          dstp[2 * (size_t)n] =
-              me >= F::EMAX ? qnan<TO>() : scaled<TO>(T, me - F::EOFF + fexp[n] - 49);
-        }
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(barDrain) : "memory");
       }
     }
   }
   if (!ok) atomicOr(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (issuer)
+  if (issuer_warp)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
@@ -437,10 +497,12 @@ cudaError_t launch_t(const void* in, long long fsi, void* out, long long fso, in
                      int Nz, const ChebTc& t, int* err, cudaStream_t s) {
   const size_t smem = tc_smem_bytes(NT);
   const int tpf = (nlines + TCM / 2 - 1) / (TCM / 2);
-  const long long nblk = (long long)nf * tpf * t.nNt;
-  if (nblk <= 0) return cudaSuccess;
-  cheb_tc_kernel<TI, TO, NT><<<(unsigned)nblk, TCT + 32, smem, s>>>(
-      (const TI*)in, fsi, (TO*)out, fso, nlines, Nz, t.Kp, tpf, t.nNt, t.dig, t.fexp, err);
+  const long long ntiles = (long long)nf * tpf;
+  if (ntiles <= 0) return cudaSuccess;
+  const int grid = (int)std::min<long long>(ntiles, t.ctas);
+  cheb_tc_kernel<TI, TO, NT><<<grid, TCT + 32, smem, s>>>(
+      (const TI*)in, fsi, (TO*)out, fso, nlines, Nz, t.Kp, tpf, (int)ntiles, t.nNt, t.dig,
+      t.fexp, t.cache, err);
   return cudaGetLastError();
 }
 
@@ -468,6 +530,7 @@ int cheb_tc_tables(int N, int dir, std::vector<uint16_t>& dig, std::vector<int>&
   const int c48 = (Nz + 47) / 48 * 48, c64 = (Nz + 63) / 64 * 64;
   NT = (5 * c48 <= 4 * c64) ? 48 : 64;
   nNt = (Nz + NT - 1) / NT;
+  if (nNt * NT > 512) return -1;   // the kernel keeps F_n of at most 512 columns
   dig.assign((size_t)nNt * 8 * NT * Kp, 0);
   fexp.assign((size_t)nNt * NT, 0);
   const long double pi = 3.141592653589793238462643383279502884L;
@@ -513,10 +576,13 @@ int cheb_tc_tables(int N, int dir, std::vector<uint16_t>& dig, std::vector<int>&
       const int ch = k / TCKC, kl = k % TCKC;
       const int KCc = std::min(TCKC, Kp - ch * TCKC);
       const size_t base = (size_t)nt * 8 * NT * Kp + (size_t)ch * 8 * NT * TCKC;
-      const size_t off = ((size_t)(kl / 8) * (NT / 8) + nl / 8) * 64 + (nl % 8) * 8 + kl % 8;
+      (void)KCc;
       for (int j = 0; j < 8; ++j) {
+        // plane j occupies rows j NT .. j NT + NT - 1 of one 8 NT-row K-major matrix
+        const int row = j * NT + nl;
+        const size_t off = ((size_t)(kl / 8) * NT + row / 8) * 64 + (row % 8) * 8 + kl % 8;
         const int d = (int)((yb >> (7 * (7 - j))) & 127ull) - 64;
-        dig[base + (size_t)j * NT * KCc + off] = bf16_bits((float)d);
+        dig[base + off] = bf16_bits((float)d);
       }
     }
   }
@@ -524,6 +590,10 @@ int cheb_tc_tables(int N, int dir, std::vector<uint16_t>& dig, std::vector<int>&
 }
 
 size_t cheb_tc_smem(int NT) { return tc_smem_bytes(NT); }
+
+size_t cheb_tc_cache_bytes(int Kp) {
+  return (size_t)((Kp + TCKC - 1) / TCKC) * 8 * TCM * TCKC * 2;
+}
 
 cudaError_t cheb_tc_prepare(int NT) {
   const size_t smem = tc_smem_bytes(NT);
