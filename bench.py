@@ -234,27 +234,32 @@ def precision_accuracy(binding, w, fields, steps, device, prec=1):
 
 
 def precision_variants(binding, w, fields, kw, steps, device):
-    """The same workload in the other precision modes: device time per step over `steps` steps
-    (after 3 warm-up steps) and, for double-float, the max relative field difference from the
-    float64 path after 3 + `steps` steps from the same fields."""
+    """The same workload in the other precision modes and with the tensor-core Chebyshev
+    transforms: device time per step over `steps` steps (after 3 warm-up steps) and the max
+    relative field difference from the float64 FFT path after 3 + `steps` steps from the same
+    fields."""
     import torch
     out, final = {}, {}
-    for pr in (0, 2, 1):
+    pts = w["nx"] * w["ny"] * w["nz"]
+    # (precision, Chebyshev method): the float64 FFT path first (the comparison base)
+    for pr, cheb in ((0, 0), (2, 0), (1, 0), (0, 1), (1, 1)):
         g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=pr, device=device, **kw)
+        g.set_chebyshev(cheb)
         g.set_fields(*[torch.from_numpy(f) for f in fields])
         g.step(3)
         tot, _ = g.step_timed(steps)
-        final[pr] = [f.cpu() for f in g.get_fields()]
+        final[(pr, cheb)] = [f.cpu() for f in g.get_fields()]
         g.close()
         torch.cuda.empty_cache()
-        if pr:
-            pts = w["nx"] * w["ny"] * w["nz"]
-            out[PREC_NAMES[pr]] = {"ms_per_step": tot / steps, "dtype": DTYPES[pr],
-                                   "value": pts * steps / (tot * 1e-3) / 1e6}
-    out["dfloat"]["max_rel_field_diff_vs_fp64"] = max(
-        float((a - b).abs().max() / b.abs().max()) for a, b in zip(final[2], final[0]))
-    out["mixed"]["max_rel_field_diff_vs_fp64"] = max(
-        float((a - b).abs().max() / b.abs().max()) for a, b in zip(final[1], final[0]))
+        if (pr, cheb) != (0, 0):
+            name = PREC_NAMES[pr] + ("_tc" if cheb else "")
+            dt = DTYPES[pr] + (" (Chebyshev transforms: exact-split bf16 tensor-core products, "
+                               "float64-accurate)" if cheb else "")
+            out[name] = {"ms_per_step": tot / steps, "dtype": dt,
+                         "value": pts * steps / (tot * 1e-3) / 1e6,
+                         "max_rel_field_diff_vs_fp64": max(
+                             float((a - b).abs().max() / b.abs().max())
+                             for a, b in zip(final[(pr, cheb)], final[(0, 0)]))}
     return out
 
 

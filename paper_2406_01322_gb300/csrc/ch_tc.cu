@@ -25,13 +25,18 @@
 // is recombined in 64-bit integers and rounded once to float64 (or float32) with integer
 // operations only (the float64 pipe is the scarce resource on this part).
 //
-// One CTA (512 threads, 1 per SM) computes a 128-row x NT-column tile: the 128 rows are the re
-// and im parts of 64 lines of one field, the NT columns one slice of the outputs.  Per K-chunk of
-// at most 144: the eight B digit planes of the slice arrive by one bulk async copy; the threads
-// turn their row elements into the biased integers X + bias (registers) and write one A digit
-// plane at a time into a double-buffered shared-memory tile in the tensor cores' canonical
-// no-swizzle K-major layout, while one thread issues the MMAs of the previous plane.  The eight
-// accumulators G_0..G_7 (8 NT fp32 columns) live in tensor memory until the epilogue.
+// Tiles and data flow.  A tile is 128 rows (re and im of 64 lines of one field) by all Nz
+// outputs, computed as nNt output slices of NT (48 or 64) columns; the eight accumulators
+// G_0..G_7 of a slice (8 NT fp32 columns) live in tensor memory.  The eight B digit planes of a
+// slice are stacked into one 8 NT-row operand, so A plane i needs a single MMA chain over rows
+// 0 .. (8-i) NT with its accumulator starting at column i NT: product (i, j) lands on diagonal
+// i + j.  (The MMA issue rate, about one instruction per 50..128 cycles, is what limits the
+// kernel; merging the pairs this way cuts 36 small MMAs per k-step to 8..12 large ones.)
+// Persistent CTAs (one per SM) walk the tiles with 16 producer warps and one issuer warp: the
+// producers convert their rows to fixed point once per tile, write the digit planes of the first
+// slice into a double-buffered shared tile and into a per-CTA plane cache in global memory (L2);
+// the issuer copies the cached planes back for the later slices, one plane ahead of the MMAs.
+// Row lengths above 144 (nz = 257) are split into K chunks with the same accumulators.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
