@@ -656,12 +656,70 @@ __global__ void __launch_bounds__(ST) zsolve_kernel(GridDev g, double2* __restri
 
 constexpr int TL = 32;    // lines per tile-variant CTA (64 threads: one per (line, parity))
 
-// zsolve, tile variant (short lines): TL lines per CTA staged in shared memory, thread = (line, parity).  R holds [omega | theta-w | phi] right-hand
-// sides on entry and the solved sums / new phi on exit (line-major, like the state).
+// One of the three implicit problems of one line (row = its coefficients in shared memory,
+// parity p of the chain): 0 omega (or the mean flow), 1 the w influence problem, 2 phi.
+__device__ __forceinline__ void solve_tile_problem(const GridDev& g, double2* __restrict__ row,
+                                                   int prob, int p, int K, double k2, bool is00,
+                                                   const double* __restrict__ t1,
+                                                   const double* __restrict__ t2,
+                                                   const double* __restrict__ t3, unsigned pm) {
+  const int N = g.N;
+  if (prob == 0) {
+    const bool fsl = (g.bc == 1);     // free-slip: Neumann rows (op 3)
+    const int oo = fsl ? 3 : 0;
+    if (g.bc >= 2)                    // a different condition on each wall
+      tau_sweep_mixed(row, p, N, k2 + g.beta, g.bc, t1, t2, t3, fac_ptr(g, 0, 0, K),
+                      fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK,
+                      g.fac + fac_mixed_off(g, 0) + K, pm);
+    else
+      tau_sweep_c(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K),
+                  fac_ptr(g, oo, 1, K), fac_ptr(g, oo, 2, K), g.NK, fac_rsq(g, oo, p, K));
+  } else if (prob == 1) {
+    if (is00) {
+      for (int n = p; n <= N; n += 2) row[n] = make_double2(0.0, 0.0);
+    } else {
+      tau_sweep_c(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
+                  fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
+      tau_sweep_c(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K), fac_ptr(g, 1, 1, K),
+                  fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
+    }
+    if (!is00 && g.bc >= 2) {
+      w_correct_mixed(g, row, p, K, pm);
+    } else if (!is00) {
+      // influence matrix: Omega = Omega_p + c Omega_h with D Omega(+-1) = 0 (no-slip) or
+      // D^2 Omega(+-1) = 0 (free-slip), parity p
+      const double* oh = fac_oh(g, K);
+      double2 sacc = make_double2(0.0, 0.0);
+      for (int n = p; n <= N; n += 2) {
+        const double n2 = infl_weight(g.bc, n);
+        sacc.x = fma(n2, row[n].x, sacc.x);
+        sacc.y = fma(n2, row[n].y, sacc.y);
+      }
+      const double rsh = g.bc == 1 ? fac_rsh2(g, p, K) : fac_rsh(g, p, K);
+      const double2 c = make_double2(-sacc.x * rsh, -sacc.y * rsh);
+      for (int n = p; n <= N; n += 2) {
+        const double h = oh[(size_t)n * g.NK];
+        double2 v = row[n];
+        v.x = fma(c.x, h, v.x);
+        v.y = fma(c.y, h, v.y);
+        row[n] = v;
+      }
+    }
+  } else {
+    const double a = k2 + g.lam;
+    for (int rep = 0; rep < 2; ++rep)
+      tau_sweep_c(row, p, N, a, true, t1, t2, t3, fac_ptr(g, 2, 0, K), fac_ptr(g, 2, 1, K),
+                  fac_ptr(g, 2, 2, K), g.NK, fac_rsq(g, 2, p, K));
+  }
+}
+
+// zsolve, tile variant (short lines): TL lines per CTA staged in shared memory, thread = (line,
+// parity), the three problems in turn.  R holds [omega | theta-w | phi] right-hand sides on
+// entry and the solved sums / new phi on exit (line-major, like the state).
 __device__ __forceinline__ void zsolve_tile_body(const GridDev& g, double2* __restrict__ R,
                                                  long long fs, int nlines, int bid) {
   extern __shared__ double2 ssm[];
-  const int Nz = g.nz, N = g.N;
+  const int Nz = g.nz;
   double2* tile = ssm;
   double* t1 = reinterpret_cast<double*>(ssm + TL * Nz);
   double* t2 = t1 + Nz;
@@ -685,61 +743,12 @@ __device__ __forceinline__ void zsolve_tile_body(const GridDev& g, double2* __re
   const double k2 = kx * kx + ky * ky;
   const bool is00 = (mx == 0 && j == 0);
   const int ntile = min(TL, nlines - line0);
+  const unsigned pm = 0x3u << (threadIdx.x & 30);  // the two lanes of this line
   for (int prob = 0; prob < 3; ++prob) {
     double2* Rp = R + prob * fs + (size_t)line0 * Nz;
     for (int idx = tid; idx < ntile * Nz; idx += blockDim.x) tile[idx] = Rp[idx];
     __syncthreads();
-    if (valid) {
-      double2* row = tile + l * Nz;
-      const unsigned pm = 0x3u << (threadIdx.x & 30);  // the two lanes of this line
-      if (prob == 0) {
-        const bool fsl = (g.bc == 1);     // free-slip: Neumann rows (op 3)
-        const int oo = fsl ? 3 : 0;
-        if (g.bc >= 2)                    // a different condition on each wall
-          tau_sweep_mixed(row, p, N, k2 + g.beta, g.bc, t1, t2, t3, fac_ptr(g, 0, 0, K),
-                          fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK,
-                          g.fac + fac_mixed_off(g, 0) + K, pm);
-        else
-          tau_sweep_c(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K),
-                      fac_ptr(g, oo, 1, K), fac_ptr(g, oo, 2, K), g.NK, fac_rsq(g, oo, p, K));
-      } else if (prob == 1) {
-        if (is00) {
-          for (int n = p; n <= N; n += 2) row[n] = make_double2(0.0, 0.0);
-        } else {
-          tau_sweep_c(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
-                      fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
-          tau_sweep_c(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K),
-                      fac_ptr(g, 1, 1, K), fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
-        }
-        if (!is00 && g.bc >= 2) {
-          w_correct_mixed(g, row, p, K, pm);
-        } else if (!is00) {
-          // influence matrix: Omega = Omega_p + c Omega_h with D Omega(+-1) = 0 (no-slip) or
-          // D^2 Omega(+-1) = 0 (free-slip), parity p
-          const double* oh = fac_oh(g, K);
-          double2 s = make_double2(0.0, 0.0);
-          for (int n = p; n <= N; n += 2) {
-            const double n2 = infl_weight(g.bc, n);
-            s.x = fma(n2, row[n].x, s.x);
-            s.y = fma(n2, row[n].y, s.y);
-          }
-          const double rsh = g.bc == 1 ? fac_rsh2(g, p, K) : fac_rsh(g, p, K);
-          const double2 c = make_double2(-s.x * rsh, -s.y * rsh);
-          for (int n = p; n <= N; n += 2) {
-            const double h = oh[(size_t)n * g.NK];
-            double2 v = row[n];
-            v.x = fma(c.x, h, v.x);
-            v.y = fma(c.y, h, v.y);
-            row[n] = v;
-          }
-        }
-      } else {
-        const double a = k2 + g.lam;
-        for (int rep = 0; rep < 2; ++rep)
-          tau_sweep_c(row, p, N, a, true, t1, t2, t3, fac_ptr(g, 2, 0, K), fac_ptr(g, 2, 1, K),
-                      fac_ptr(g, 2, 2, K), g.NK, fac_rsq(g, 2, p, K));
-      }
-    }
+    if (valid) solve_tile_problem(g, tile + l * Nz, prob, p, K, k2, is00, t1, t2, t3, pm);
     __syncthreads();
     for (int idx = tid; idx < ntile * Nz; idx += blockDim.x) Rp[idx] = tile[idx];
     __syncthreads();
