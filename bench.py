@@ -242,7 +242,7 @@ def precision_variants(binding, w, fields, kw, steps, device):
     out, final = {}, {}
     pts = w["nx"] * w["ny"] * w["nz"]
     # (precision, Chebyshev method): the float64 FFT path first (the comparison base)
-    for pr, cheb in ((0, 0), (2, 0), (1, 0), (0, 1), (1, 1)):
+    for pr, cheb in ((0, 0), (2, 0), (1, 0), (0, 1), (2, 1), (1, 1)):
         g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=pr, device=device, **kw)
         g.set_chebyshev(cheb)
         g.set_fields(*[torch.from_numpy(f) for f in fields])

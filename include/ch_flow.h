@@ -134,12 +134,13 @@ int ch_step(ch_grid* g, int nsteps);
  *   (bf16, Ozaki scheme; fp32 accumulation is exact for these integers) and a recombination in
  *   64-bit integers; error a few units of 2^-53 of max|row| x max_n sum_k |B_nk| per line, the
  *   accuracy of a float64 transform.  Two extra launches per step and a 9-field float64 coefficient buffer.
- *   Single grids in CH_PREC_FP64 or CH_PREC_MIXED with nz <= 496; not with the adjoint. */
+ *   Single grids (any precision) with nz <= 496; not with the adjoint. */
 #define CH_CHEB_FFT 0
 #define CH_CHEB_TC 1
 
 /* Select the step's Chebyshev method; allocates the tensor-core tables and buffer on the first
- * CH_CHEB_TC (synchronous).  CH_ERR_ARG: bad method or CH_PREC_DFLOAT; CH_ERR_SIZE: nz > 496.
+ * CH_CHEB_TC (synchronous).  CH_ERR_ARG: bad method; CH_ERR_STATE: a reverse sweep is open;
+ * CH_ERR_SIZE: nz > 496.
  * The captured step graph is rebuilt at the next ch_step. */
 int ch_set_chebyshev(ch_grid* g, int method);
 int ch_get_chebyshev(const ch_grid* g);

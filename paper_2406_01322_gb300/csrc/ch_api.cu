@@ -197,7 +197,7 @@ int launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev = nullptr
   nvtxRangePushA("ch step");
   if (tc) {
     nvtxRangePushA("cheb fwd (tensor cores)");
-    e[6] = chf::launch_cheb_tc(G->prec == 1 ? 1 : 0, 0, G->nl, G->fs, G->cf, G->fs, kNl, nlines,
+    e[6] = chf::launch_cheb_tc(G->prec, 0, G->nl, G->fs, G->cf, G->fs, kNl, nlines,
                                g.nz, G->tcf, G->tc_err, s);
     nvtxRangePop();
   }
@@ -221,7 +221,7 @@ int launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev = nullptr
   if (ev) cudaEventRecord(ev[3], s);
   if (tc) {
     nvtxRangePushA("cheb bwd (tensor cores)");
-    e[7] = chf::launch_cheb_tc(0, G->prec == 1 ? 1 : 0, G->cf, G->fs, G->bw, G->fs, kBw, nlines,
+    e[7] = chf::launch_cheb_tc(0, G->prec, G->cf, G->fs, G->bw, G->fs, kBw, nlines,
                                g.nz, G->tcb, G->tc_err, s);
     nvtxRangePop();
   }
@@ -770,7 +770,6 @@ int ch_set_chebyshev(ch_grid* G, int method) {
   if (!G || (method != CH_CHEB_FFT && method != CH_CHEB_TC)) return CH_ERR_ARG;
   if (G->adj_block) return CH_ERR_STATE;   // not while a reverse sweep is open
   if (method == CH_CHEB_TC) {
-    if (G->prec == CH_PREC_DFLOAT) return CH_ERR_ARG;
     if (!G->cf) {
       const GridDev& g = G->g;
       std::vector<uint16_t> dig[2];

@@ -194,7 +194,9 @@ int cheb_tc_tables(int N, int dir, std::vector<uint16_t>& dig, std::vector<int>&
 size_t cheb_tc_smem(int NT);
 // raise the shared-memory limit of every instantiation for slice width NT (before any capture)
 cudaError_t cheb_tc_prepare(int NT);
-// nf fields of complex lines, element type tin / tout (0 float64, 1 float32), field strides
+// nf fields of complex lines, element type tin / tout (0 float64, 1 float32, 2 double-float; the
+// pairs float64 -> float64, float32 -> float64, double-float -> float64 and float64 -> float32 /
+// double-float), field strides
 // fsi / fso (complex elements), nlines lines of Nz; *err |= 1 if a bounded wait gave up
 cudaError_t launch_cheb_tc(int tin, int tout, const void* in, long long fsi, void* out,
                            long long fso, int nf, int nlines, int Nz, const ChebTc& t, int* err,

@@ -144,11 +144,23 @@ template <> struct FBits<double> {
   typedef unsigned long long U;
   static constexpr int MB = 52, EMAX = 0x7FF, SH0 = 1, EOFF = 1022;
   __device__ static U bits(double x) { return (U)__double_as_longlong(x); }
+  __device__ static int expo(U b) { return (int)((b >> 52) & 0x7FFull); }
 };
 template <> struct FBits<float> {
   typedef unsigned int U;
   static constexpr int MB = 23, EMAX = 0xFF, SH0 = 30, EOFF = 126;
   __device__ static U bits(float x) { return __float_as_uint(x); }
+  __device__ static int expo(U b) { return (int)((b >> 23) & 0xFFu); }
+};
+// double-float h + l: the bits of h in the low word, of l in the high word; the row scale comes
+// from h (|h + l| < 2^E whenever |h| < 2^E, since |l| <= ulp(h) / 2)
+template <> struct FBits<df> {
+  typedef unsigned long long U;
+  static constexpr int EMAX = 0xFF, EOFF = 126;
+  __device__ static U bits(df x) {
+    return (U)__float_as_uint(x.h) | ((U)__float_as_uint(x.l) << 32);
+  }
+  __device__ static int expo(U b) { return (int)((b >> 23) & 0xFFull); }
 };
 
 // X + bias for an element with bit pattern b in a row whose largest exponent field is maxe
@@ -171,6 +183,30 @@ __device__ __forceinline__ unsigned long long to_biased(typename FBits<T>::U b, 
   }
   const bool neg = (b >> (8 * sizeof(typename F::U) - 1)) & 1;
   return neg ? kBias - X : kBias + X;
+}
+
+// round(f 2^(54-E)) of a float with bit pattern b, E = maxe - 126, as a signed integer
+__device__ __forceinline__ long long fixed_f32(unsigned b, int maxe) {
+  const int ef = (int)((b >> 23) & 0xFFu);
+  unsigned long long mant = b & 0x7FFFFFu;
+  if (ef) mant |= 1ull << 23;
+  const int s = (ef ? ef : 1) - maxe + 30;
+  unsigned long long X;
+  if (s >= 0) {
+    X = mant << s;
+  } else {
+    const int sh = -s;
+    X = sh >= 64 ? 0ull : (mant + (1ull << (sh - 1))) >> sh;
+  }
+  return (b >> 31) ? -(long long)X : (long long)X;
+}
+// X + bias of a double-float: round(h 2^(54-E)) + round(l 2^(54-E)) (one extra unit of error
+// at most, 2^-54 of the row scale)
+template <>
+__device__ __forceinline__ unsigned long long to_biased<df>(unsigned long long b, int maxe) {
+  if (maxe >= 0xFF) return kBias;
+  return kBias + (unsigned long long)(fixed_f32((unsigned)b, maxe) +
+                                      fixed_f32((unsigned)(b >> 32), maxe));
 }
 
 // digits at bit offset sh (< 28) of two elements' 28-bit halves, as two bf16 packed in one word
@@ -225,11 +261,29 @@ template <> __device__ __forceinline__ float scaled<float>(long long T, int e) {
   return __uint_as_float((unsigned)(sg >> 32) | ((unsigned)be << 23) |
                          (unsigned)(mant & 0x7FFFFFull));
 }
+// double-float result: the high part rounded to float from the integer, the low part from the
+// exact integer remainder
+template <> __device__ __forceinline__ df scaled<df>(long long T, int e) {
+  if (T == 0) return df(0.0f, 0.0f);
+  const bool neg = T < 0;
+  unsigned long long a = neg ? 0ull - (unsigned long long)T : (unsigned long long)T;
+  const int lz = __clzll((long long)a);   // |T| < 2^62.3: lz >= 1
+  const unsigned long long n = a << lz;
+  unsigned long long mant = n >> 40;
+  const unsigned long long rem = n & 0xFFFFFFFFFFull;
+  mant += (rem + (mant & 1ull)) > (1ull << 39) ? 1ull : 0ull;
+  const unsigned long long ahi = (mant << 40) >> lz;   // |T| rounded to 24 significant bits
+  const long long Thi = neg ? -(long long)ahi : (long long)ahi;
+  return df(scaled<float>(Thi, e), scaled<float>(T - Thi, e));
+}
 template <typename TO> __device__ __forceinline__ TO qnan();
 template <> __device__ __forceinline__ double qnan<double>() {
   return __longlong_as_double(0x7FF8000000000000ll);
 }
 template <> __device__ __forceinline__ float qnan<float>() { return __uint_as_float(0x7FC00000u); }
+template <> __device__ __forceinline__ df qnan<df>() {
+  return df(__uint_as_float(0x7FC00000u), __uint_as_float(0x7FC00000u));
+}
 
 __host__ __device__ constexpr size_t tc_smem_bytes(int NT) {
   // B planes, two A planes, row exponents, eight barriers and the tensor-memory address
@@ -400,7 +454,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
           for (int e = 0; e < 2; ++e) {
             const int k = ch * TCKC + 8 * gl + 2 * q + e;
             if (gl < ngc && rowok && k < Nz)
-              maxe = max(maxe, (int)((F::bits(src[2 * (size_t)k]) >> F::MB) & (U)F::EMAX));
+              maxe = max(maxe, F::expo(F::bits(src[2 * (size_t)k])));
           }
       }
       maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, 1));
@@ -604,15 +658,19 @@ cudaError_t cheb_tc_prepare(int NT) {
   const size_t smem = tc_smem_bytes(NT);
   cudaError_t e = cudaSuccess;
   if (NT == 48) {
-    static int c0 = 0, c1 = 0, c2 = 0;
+    static int c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0;
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, double, 48>, smem, &c0);
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<float, double, 48>, smem, &c1);
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, float, 48>, smem, &c2);
+    if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<df, double, 48>, smem, &c3);
+    if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, df, 48>, smem, &c4);
   } else {
-    static int c0 = 0, c1 = 0, c2 = 0;
+    static int c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0;
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, double, 64>, smem, &c0);
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<float, double, 64>, smem, &c1);
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, float, 64>, smem, &c2);
+    if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<df, double, 64>, smem, &c3);
+    if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, df, 64>, smem, &c4);
   }
   return e;
 }
@@ -626,6 +684,10 @@ cudaError_t launch_cheb_tc(int tin, int tout, const void* in, long long fsi, voi
     return launch_nt<float, double>(in, fsi, out, fso, nf, nlines, Nz, t, err, s);
   if (tin == 0 && tout == 1)
     return launch_nt<double, float>(in, fsi, out, fso, nf, nlines, Nz, t, err, s);
+  if (tin == 2 && tout == 0)
+    return launch_nt<df, double>(in, fsi, out, fso, nf, nlines, Nz, t, err, s);
+  if (tin == 0 && tout == 2)
+    return launch_nt<double, df>(in, fsi, out, fso, nf, nlines, Nz, t, err, s);
   return cudaErrorInvalidValue;
 }
 

@@ -228,11 +228,27 @@ def test_switching_methods_mid_run(binding):
         assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-12
 
 
+def test_dfloat_tc_ten_steps_within_1e_10(binding):
+    """Double-float x/y with the tensor-core transforms (double-float rows in, double-float
+    samples out) against the float64 oracle, and against the double-float FFT path."""
+    w = workload("channel_32x32x33")
+    fields = inputs.initial_fields(**w)
+    g = grid(binding, w, fields, binding.PREC_DFLOAT, binding.CHEB_TC)
+    gf = grid(binding, w, fields, binding.PREC_DFLOAT, binding.CHEB_FFT)
+    o = Channel(Params(nx=w["nx"], ny=w["ny"], nz=w["nz"], **phys_kw(w)))
+    o.set_fields(*fields)
+    g.step(10)
+    gf.step(10)
+    for _ in range(10):
+        o.step()
+    g.device_status()
+    for a, b, c, f in zip(g.get_fields(), o.get_fields(), gf.get_fields(), "uvwp"):
+        a = a.cpu().numpy()
+        assert rel(a, b) <= 1e-10, f
+        assert rel(a, c.cpu().numpy()) <= 1e-11, f
+
+
 def test_tc_rejections(binding):
-    g = binding.Grid(16, 16, 17, precision=binding.PREC_DFLOAT)
-    with pytest.raises(binding.ChError) as e:
-        g.set_chebyshev(binding.CHEB_TC)
-    assert e.value.code == -1
     g = binding.Grid(16, 16, 17)
     with pytest.raises(binding.ChError) as e:
         g.set_chebyshev(5)
