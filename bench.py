@@ -135,11 +135,13 @@ def kernel_work(w, prec):
 
 def tc_tiles(nz):
     """K padding, output slice width and slice count of the tensor-core Chebyshev kernel (the
-    library's rule: 48-wide slices unless 64-wide ones pad 20 % less)."""
+    library's rule: the slices cover the outputs n < N = nz - 1, 48 wide unless 64-wide ones pad
+    20 % less; the last output is summed exactly outside the MMAs)."""
+    N = nz - 1
     Kp = (nz + 15) // 16 * 16
-    c48, c64 = (nz + 47) // 48 * 48, (nz + 63) // 64 * 64
+    c48, c64 = (N + 47) // 48 * 48, (N + 63) // 64 * 64
     NT = 48 if 5 * c48 <= 4 * c64 else 64
-    return Kp, NT, (nz + NT - 1) // NT
+    return Kp, NT, (N + NT - 1) // NT
 
 
 def cufft_transforms_ms(w, prec, reps=5, warmup=2, dev="cuda"):

@@ -781,6 +781,7 @@ int ch_set_chebyshev(ch_grid* G, int method) {
         t[dir].NT = NT;
         t[dir].nNt = nNt;
         t[dir].Kp = Kp;
+        t[dir].dir = dir;
         void* dd = galloc(G, dig[dir].size() * sizeof(uint16_t));
         void* df = galloc(G, fe[dir].size() * sizeof(int));
         if (!dd || !df) return CH_ERR_ALLOC;

@@ -178,12 +178,14 @@ cudaError_t launch_diag(const GridDev& g, const double* phys7, long long fs,
 
 // Chebyshev transform along z as an exact-split (Ozaki) bf16 matrix product on the tensor cores
 // (ch_tc.cu).  Tables of one direction (dir 0 forward: samples -> coefficients; 1 backward):
-// nNt output slices of NT columns, K padded to Kp (a multiple of 16, < 512).
+// nNt output slices of NT columns covering the outputs n < N (the kernel sums n = N exactly),
+// K padded to Kp (a multiple of 16, < 512).
 struct ChebTc {
   const uint16_t* dig = nullptr;   // device: per slice, per K chunk, eight NT x KC digit planes
   const int* fexp = nullptr;       // device: output-row scale exponents F_n (nNt NT entries)
   uint32_t* cache = nullptr;       // device: A digit planes of one tile per persistent CTA
   int NT = 0, nNt = 0, Kp = 0;
+  int dir = 0;                     // 0 forward (samples -> coefficients), 1 backward
   int ctas = 0;                    // persistent CTAs (the cache holds ctas cheb_tc_cache_bytes)
 };
 // bytes of plane cache one persistent CTA needs for rows of padded length Kp

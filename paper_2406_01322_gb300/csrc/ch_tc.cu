@@ -276,6 +276,11 @@ template <> __device__ __forceinline__ df scaled<df>(long long T, int e) {
   const long long Thi = neg ? -(long long)ahi : (long long)ahi;
   return df(scaled<float>(Thi, e), scaled<float>(T - Thi, e));
 }
+// the forward transform's last output carries the factor 1 / (2N) (forward outputs are float64)
+template <typename TO> __device__ __forceinline__ TO last_scale(TO v, double f) { return v; }
+template <> __device__ __forceinline__ double last_scale<double>(double v, double f) {
+  return v * f;
+}
 template <typename TO> __device__ __forceinline__ TO qnan();
 template <> __device__ __forceinline__ double qnan<double>() {
   return __longlong_as_double(0x7FF8000000000000ll);
@@ -315,7 +320,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
     cheb_tc_kernel(const TI* __restrict__ in, long long fsi, TO* __restrict__ out, long long fso,
                    int nlines, int Nz, int Kp, int tpf, int ntiles, int nNt,
                    const uint16_t* __restrict__ bdig, const int* __restrict__ fexp,
-                   uint32_t* __restrict__ cache, int* __restrict__ err) {
+                   uint32_t* __restrict__ cache, int fwd, double lastf, int* __restrict__ err) {
   typedef FBits<TI> F;
   typedef typename F::U U;
   extern __shared__ __align__(1024) unsigned char tsm[];
@@ -464,7 +469,10 @@ __global__ void __launch_bounds__(TCT + 32, 1)
       if (q == 0) sE[m] = maxe;
       asm volatile("bar.sync 1, %0;" ::"r"(TCT) : "memory");
       const int me = sE[mm];
-      // first slice: generate the planes of every chunk (cached for the later slices)
+      // first slice: generate the planes of every chunk (cached for the later slices); the last
+      // output n = N, sum_k w_k X_k with w_k = e_k (-1)^k (forward) or (-1)^k (backward), is
+      // summed exactly here as S_hi 2^27 + S_lo
+      long long s_hi = 0, s_lo = 0;
       for (int ch = 0; ch < nchunk; ++ch) {
         const int ngr = min(TCKC, Kp - ch * TCKC) / 8;
         uint32_t yh[2 * TCG], yl[2 * TCG];   // bits 28..55 and 0..27 of X + bias
@@ -478,6 +486,12 @@ __global__ void __launch_bounds__(TCT + 32, 1)
             const unsigned long long y = to_biased<TI>(b, maxe);
             yh[2 * gl + e] = (uint32_t)(y >> 28);
             yl[2 * gl + e] = (uint32_t)y & 0xFFFFFFFu;
+            if (gl < ngr && k < Nz) {
+              const long long xs = (long long)(y - kBias);
+              const int w = ((k & 1) ? -1 : 1) * ((fwd && k != 0 && k != Nz - 1) ? 2 : 1);
+              s_hi += w * (xs >> 27);
+              s_lo += w * (xs & 0x7FFFFFFll);
+            }
           }
         for (int i = 0; i < 8; ++i, ++t) {
           const int bf = t & 1;
@@ -502,6 +516,18 @@ __global__ void __launch_bounds__(TCT + 32, 1)
                          : "memory");
         }
       }
+      s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 1);
+      s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 1);
+      s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 2);
+      s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 2);
+      if (q == 0 && rowok && ok) {
+        // sum_k w_k x_k = 2^(E - 54) (S_hi 2^27 + S_lo) = T 2^(E - 51), T = S_hi 2^24 + S_lo / 8
+        // (|sum w X| < 2 Kp 2^54 < 2^64, so three low bits are dropped: 2^-51 of the row scale)
+        const long long T = s_hi * 16777216ll + (s_lo >> 3);
+        TO v = maxe >= F::EMAX ? qnan<TO>() : scaled<TO>(T, maxe - F::EOFF - 51);
+        if (fwd) v = last_scale<TO>(v, lastf);
+        out[((size_t)fld * fso + (size_t)line * Nz) * 2 + (m & 1) + 2 * (size_t)(Nz - 1)] = v;
+      }
       const int oline = line0 + (mm >> 1);
       TO* dstp =
           out + ((size_t)fld * fso + (size_t)(oline < nlines ? oline : 0) * Nz) * 2 + (mm & 1);
@@ -519,7 +545,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int n = sl * NT + cg * CW + c0 + e;
-            if (orow && n < Nz) {
+            if (orow && n < Nz - 1) {
               int g[8];
               if (Kp <= TCKC) {
 #pragma unroll
@@ -561,7 +587,7 @@ cudaError_t launch_t(const void* in, long long fsi, void* out, long long fso, in
   const int grid = (int)std::min<long long>(ntiles, t.ctas);
   cheb_tc_kernel<TI, TO, NT><<<grid, TCT + 32, smem, s>>>(
       (const TI*)in, fsi, (TO*)out, fso, nlines, Nz, t.Kp, tpf, (int)ntiles, t.nNt, t.dig,
-      t.fexp, t.cache, err);
+      t.fexp, t.cache, t.dir == 0 ? 1 : 0, t.dir == 0 ? 0.5 / (double)(Nz - 1) : 1.0, err);
   return cudaGetLastError();
 }
 
@@ -585,17 +611,19 @@ int cheb_tc_tables(int N, int dir, std::vector<uint16_t>& dig, std::vector<int>&
   const int Nz = N + 1;
   Kp = (Nz + 15) / 16 * 16;
   if (N < 2 || Kp >= 512) return -1;
-  // output slice width: 48 (more MMAs, each smem-bound) or 64 (fewer padded columns)
-  const int c48 = (Nz + 47) / 48 * 48, c64 = (Nz + 63) / 64 * 64;
+  // the MMAs produce outputs n < N (the last one, n = N, has the weights +-1, +-2 and is summed
+  // exactly by the kernel's producers); output slice width 48 or 64, whichever pads less after
+  // weighting 48-wide slices by 5/4 (more MMA instructions per column)
+  const int c48 = (N + 47) / 48 * 48, c64 = (N + 63) / 64 * 64;
   NT = (5 * c48 <= 4 * c64) ? 48 : 64;
-  nNt = (Nz + NT - 1) / NT;
+  nNt = (N + NT - 1) / NT;
   if (nNt * NT > 512) return -1;   // the kernel keeps F_n of at most 512 columns
   dig.assign((size_t)nNt * 8 * NT * Kp, 0);
   fexp.assign((size_t)nNt * NT, 0);
   const long double pi = 3.141592653589793238462643383279502884L;
   std::vector<long double> row(Nz);
   std::vector<long long> Y(Nz);
-  for (int n = 0; n < Nz; ++n) {
+  for (int n = 0; n < N; ++n) {
     long double mx = 0.0L;
     for (int k = 0; k < Nz; ++k) {
       int a = (int)(((long long)n * k) % (2 * N));
