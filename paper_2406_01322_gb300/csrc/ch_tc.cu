@@ -442,15 +442,14 @@ __global__ void __launch_bounds__(TCT + 32, 1)
     const int qd = warp & 3, cg = warp >> 2;
     const int mm = qd * 32 + lane;
     const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(cg * CW);
-    int t = 0, S = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      const int fld = tile / tpf;
-      const int line0 = (tile - fld * tpf) * (TCM / 2);
-      const int line = line0 + (m >> 1);
+    // the largest exponent field of this thread's row of tile `tl` over all of K (the row's
+    // first, cold read)
+    auto row_exponent = [&](int tl) {
+      const int fld = tl / tpf;
+      const int line = (tl - fld * tpf) * (TCM / 2) + (m >> 1);
       const bool rowok = line < nlines;
       const TI* src = in + ((size_t)fld * fsi + (size_t)(rowok ? line : 0) * Nz) * 2 + (m & 1);
-      // the largest exponent field of the row over all of K
-      int maxe = 1;
+      int mx = 1;
       for (int ch = 0; ch < nchunk; ++ch) {
         const int ngc = min(TCKC, Kp - ch * TCKC) / 8;
 #pragma unroll
@@ -458,12 +457,22 @@ __global__ void __launch_bounds__(TCT + 32, 1)
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             const int k = ch * TCKC + 8 * gl + 2 * q + e;
-            if (gl < ngc && rowok && k < Nz)
-              maxe = max(maxe, F::expo(F::bits(src[2 * (size_t)k])));
+            if (gl < ngc && rowok && k < Nz) mx = max(mx, F::expo(F::bits(src[2 * (size_t)k])));
           }
       }
-      maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, 1));
-      maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, 2));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      return max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    };
+    int t = 0, S = 0;
+    int ahead = -1;   // the next tile's row exponent, read during this tile's last slice
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int fld = tile / tpf;
+      const int line0 = (tile - fld * tpf) * (TCM / 2);
+      const int line = line0 + (m >> 1);
+      const bool rowok = line < nlines;
+      const TI* src = in + ((size_t)fld * fsi + (size_t)(rowok ? line : 0) * Nz) * 2 + (m & 1);
+      const int maxe = ahead >= 0 ? ahead : row_exponent(tile);
+      ahead = -1;
       // sE: every producer warp has read the previous tile's entries (before its slice loop)
       asm volatile("bar.sync 1, %0;" ::"r"(TCT) : "memory");
       if (q == 0) sE[m] = maxe;
@@ -567,6 +576,8 @@ __global__ void __launch_bounds__(TCT + 32, 1)
         __syncwarp();
         if (lane == 0)
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(barDrain) : "memory");
+        // while the last slice's MMAs run: the next tile's cold row read
+        if (sl == nNt - 2 && tile + (int)gridDim.x < ntiles) ahead = row_exponent(tile + gridDim.x);
       }
     }
   }

@@ -170,6 +170,24 @@ def test_ten_steps_fp64_tc_within_1e_10(binding, over):
         assert rel(a.cpu().numpy(), b) <= tol, f
 
 
+@pytest.mark.parametrize("bc", [1, 2, 3], ids=["free-slip", "no-slip-bottom", "free-slip-bottom"])
+def test_walls_tc_ten_steps_within_1e_10(binding, bc):
+    """The coefficient-space zrhs / zbwd with every wall closure of the tau solves."""
+    w = workload("channel_32x32x33", bc=bc)
+    fields = inputs.initial_fields(**w)
+    g = binding.Grid(w["nx"], w["ny"], w["nz"], bc=bc, **phys_kw(w))
+    g.set_chebyshev(binding.CHEB_TC)
+    g.set_fields(*[torch.from_numpy(f) for f in fields])
+    o = Channel(Params(nx=w["nx"], ny=w["ny"], nz=w["nz"], bc=bc, **phys_kw(w)))
+    o.set_fields(*fields)
+    g.step(10)
+    for _ in range(10):
+        o.step()
+    g.device_status()
+    for a, b, f in zip(g.get_fields(), o.get_fields(), "uvwp"):
+        assert rel(a.cpu().numpy(), b) <= 1e-10, f
+
+
 def test_mixed_tc_error_bound_and_fft_agreement(binding):
     w = workload("channel_32x32x33")
     fields = inputs.initial_fields(**w)
