@@ -272,7 +272,8 @@ template <> __device__ __forceinline__ df scaled<df>(long long T, int e) {
   unsigned long long mant = n >> 40;
   const unsigned long long rem = n & 0xFFFFFFFFFFull;
   mant += (rem + (mant & 1ull)) > (1ull << 39) ? 1ull : 0ull;
-  const unsigned long long ahi = (mant << 40) >> lz;   // |T| rounded to 24 significant bits
+  // |T| rounded to 24 significant bits; mant may have rounded up to 2^24, so shift by 39 first
+  const unsigned long long ahi = (mant << 39) >> (lz - 1);
   const long long Thi = neg ? -(long long)ahi : (long long)ahi;
   return df(scaled<float>(Thi, e), scaled<float>(T - Thi, e));
 }
