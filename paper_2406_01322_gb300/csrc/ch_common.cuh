@@ -128,6 +128,12 @@ struct FftPlan {
 };
 
 // radix-R DFT of v[0..R-1] in registers; INV selects exp(+2 pi i / R).
+// a * b + c in one rounding where the type has a fused multiply-add (double-float: the product
+// and the sum of its operators)
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ df fmx(df a, df b, df c) { return a * b + c; }
+
 template <typename T, int R, bool INV> struct Dft;
 
 template <typename T, bool INV> struct Dft<T, 2, INV> {
@@ -147,10 +153,10 @@ template <typename T, bool INV> struct Dft<T, 3, INV> {
     T2 d = v[1] - v[2];
     T2 m = mk(v[0].x - (T)0.5 * t.x, v[0].y - (T)0.5 * t.y);
     v[0] = v[0] + t;
-    // forward: y1 = m - i s3 d, y2 = m + i s3 d ; inverse swaps the sign
-    T2 r = INV ? mk(-s3 * d.y, s3 * d.x) : mk(s3 * d.y, -s3 * d.x);
-    v[1] = m + r;
-    v[2] = m - r;
+    // forward: y1 = m - i s3 d, y2 = m + i s3 d; inverse swaps the sign (s3 fused into the adds)
+    const T sp = INV ? -s3 : s3;
+    v[1] = mk(fmx(sp, d.y, m.x), fmx(-sp, d.x, m.y));
+    v[2] = mk(fmx(-sp, d.y, m.x), fmx(sp, d.x, m.y));
   }
 };
 
@@ -176,23 +182,24 @@ template <typename T, bool INV> struct Dft<T, 8, INV> {
     T2 a1 = v[1] + v[5], a5 = v[1] - v[5];
     T2 a2 = v[2] + v[6], a6 = v[2] - v[6];
     T2 a3 = v[3] + v[7], a7 = v[3] - v[7];
-    // twiddles w8^1, w8^2, w8^3 on the odd half
-    if (!INV) {
-      a5 = mk(h * (a5.x + a5.y), h * (a5.y - a5.x));     // * (1 - i)/sqrt2
-      a6 = mul_mi(a6);                                   // * -i
-      a7 = mk(h * (a7.y - a7.x), -h * (a7.x + a7.y));    // * (-1 - i)/sqrt2
-    } else {
-      a5 = mk(h * (a5.x - a5.y), h * (a5.x + a5.y));     // * (1 + i)/sqrt2
-      a6 = mul_i(a6);                                    // * i
-      a7 = mk(-h * (a7.x + a7.y), h * (a7.x - a7.y));    // * (-1 + i)/sqrt2
-    }
-    // two radix-4 DFTs: even outputs from a0..a3, odd outputs from a4..a7
+    // even outputs: radix-4 DFT of a0..a3
     T2 e[4] = {a0, a1, a2, a3};
-    T2 o[4] = {a4, a5, a6, a7};
     Dft<T, 4, INV>::run(e);
-    Dft<T, 4, INV>::run(o);
     v[0] = e[0]; v[2] = e[1]; v[4] = e[2]; v[6] = e[3];
-    v[1] = o[0]; v[3] = o[1]; v[5] = o[2]; v[7] = o[3];
+    // odd outputs: radix-4 DFT of (a4, w a5, w^2 a6, w^3 a7), w = exp(-+ i pi / 4).  w a5 = h p
+    // and w^3 a7 = h r, so the radix-4's sums of those two lines are h (p + r) and h (p - r),
+    // and the factor h is fused into the output additions.
+    const T2 p = INV ? mk(a5.x - a5.y, a5.x + a5.y) : mk(a5.x + a5.y, a5.y - a5.x);
+    const T2 r = INV ? mk(-(a7.x + a7.y), a7.x - a7.y) : mk(a7.y - a7.x, -(a7.x + a7.y));
+    const T2 o2 = INV ? mul_i(a6) : mul_mi(a6);
+    const T2 t0 = a4 + o2, t1 = a4 - o2;
+    const T2 sm = p + r, df_ = p - r;
+    v[1] = mk(fmx(h, sm.x, t0.x), fmx(h, sm.y, t0.y));
+    v[5] = mk(fmx(-h, sm.x, t0.x), fmx(-h, sm.y, t0.y));
+    // (t1 +- rot(h (p - r))), rot = -i (forward) or i (inverse)
+    const T hs = INV ? -h : h;
+    v[3] = mk(fmx(hs, df_.y, t1.x), fmx(-hs, df_.x, t1.y));
+    v[7] = mk(fmx(-hs, df_.y, t1.x), fmx(hs, df_.x, t1.y));
   }
 };
 
