@@ -4,7 +4,8 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl re
 
 Prints ONE JSON line (rank 0).  A step is one full time step (Sec. 2.2 steps i)-v)) of one
 channel: six kernels - z right-hand sides (Chebyshev DCTs, assembly, AB2), tau solves, z update
-+ backward DCTs, y backward pass, fused x-line kernel (transforms + products), y forward pass.
++ backward DCTs, y backward pass, fused x-line kernel (transforms + products), y forward pass
+(eight with --cheb tc: the Chebyshev transforms then run as two tensor-core launches).
 Default workload: the 128 x 128 x 129 FP64 channel (Re_tau = 150, 8 drops).  Points = nx ny nz
 (unpadded); the metric is Mpoints * steps / s of the whole job.
 
@@ -95,7 +96,8 @@ def fft_flops(n):
 
 
 def kernel_work(w, prec):
-    """Algorithmic flops (an FMA counts 2) and bytes per launch of the six step kernels."""
+    """Algorithmic flops (an FMA counts 2) and bytes per launch of the step kernels (the six of
+    the FFT method and the two tensor-core Chebyshev transforms)."""
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     Mx, Px, Py, N = nx // 2, 3 * nx // 2, 3 * ny // 2, nz - 1
     b = 8 if prec == 1 else 16

@@ -1,7 +1,9 @@
 // C-ABI of the channel solver (declared in include/ch_flow.h): validation, plans, twiddle
 // tables, internal buffers, the per-step launch schedule and its CUDA-graph replay.
 //
-// One time step (paper Sec. 2.2, steps i)-v)) is six launches on the handle's stream:
+// One time step (paper Sec. 2.2, steps i)-v)) is six launches on the handle's stream (eight with
+// the tensor-core Chebyshev method: the forward transform of the nine products before zrhs and
+// the backward transform of the five fields after zbwd, zrhs and zbwd then skipping their DCTs):
 //   zrhs    : Chebyshev DCT-I of the nine non-linear fields (as seven combinations), assembly,
 //             AB2 / CN / IE right-hand sides;
 //   zsolve  : the Chebyshev-tau solves of every wavenumber line;
