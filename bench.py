@@ -507,7 +507,9 @@ def run_reference(args, w):
 
 def run_ensemble(args):
     """32 uneven channels (mixed precision) advanced by grouped persistent launches, after the
-    autotuner; the same members stepped one by one with their own graphs are timed beside it."""
+    autotuner; the same members stepped one by one with their own graphs are timed beside it.
+    With --cheb tc every member's z transforms run on the tensor cores (two launches per member
+    per step beside the six grouped ones)."""
     import torch
     from paper_2406_01322_gb300 import binding, build, inputs
     build.build_library()
@@ -515,6 +517,9 @@ def run_ensemble(args):
     torch.cuda.set_device(local)
     ms = inputs.ensemble_members()
     ens = binding.Ensemble(ms, precision=1, device=f"cuda:{local}")
+    tc = args.cheb == "tc"
+    if tc:
+        ens.set_chebyshev(binding.CHEB_TC)
     for i, (g, m) in enumerate(zip(ens.grids, ms)):
         g.set_fields(*[torch.from_numpy(a) for a in inputs.initial_fields(**m)])
     ens.step(1)
@@ -553,17 +558,20 @@ def run_ensemble(args):
     out = {"metric": METRIC, "value": pts * args.steps / (tot_ms * 1e-3) / 1e6, "unit": UNIT,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32 transforms/products + f64 solves",
+           "vs_baseline": None,
+           "dtype": "f32 x/y transforms and products, f64 z transforms and solves"
+                    + (" (z transforms as exact-split bf16 tensor-core products)" if tc else ""),
            "data": "synthetic",
            "config": {"workload": "ensemble_32_uneven", "members": len(ms),
-                      "points": pts, "precision": "mixed"},
+                      "points": pts, "precision": "mixed", "chebyshev": args.cheb},
            "sequential_members_ms_per_step": seq_ms / args.steps,
            "e2e": {"value": pts * args.steps / e2e_s / 1e6, "unit": UNIT,
                    "h2d_bytes_per_step": nbytes / args.steps,
                    "d2h_bytes_per_step": nbytes / args.steps,
                    "note": "set_fields_host of every member + K grouped steps + get_fields_host"},
            "stage_ms_per_step": {n: kms[i] / args.steps for i, n in enumerate(names)},
-           "tuning": tuning, "gpu_launches": 6 * args.steps, "clocks": clk.summary()}
+           "tuning": tuning, "gpu_launches": (6 + (2 * len(ms) if tc else 0)) * args.steps,
+           "clocks": clk.summary()}
     ens.close()
     print(json.dumps(out))
 

@@ -263,9 +263,10 @@ int ch_render_interface(ch_grid* g, unsigned char* rgb, double* depth, int width
  * Not in the paper: a batching service of this library.  Each member is an ordinary ch_grid
  * (created here with the given allocator and stream; all members share `precision`).  One
  * ensemble step advances every member by one time step with six grouped persistent launches
- * (one per stage; their CTAs walk a work list spanning all members), captured once into a CUDA
- * graph and replayed.  Members are set, read and diagnosed through their ch_grid handles
- * (ch_ensemble_member); ch_ensemble_step needs every member set.  ch_ensemble_autotune times the
+ * (one per stage; their CTAs walk a work list spanning all members; with CH_CHEB_TC two more per
+ * member), captured once into a CUDA graph and replayed.  Members are set, read and diagnosed
+ * through their ch_grid handles (ch_ensemble_member); ch_ensemble_step needs every member set.
+ * ch_ensemble_autotune times the
  * transforms' radix schedules and the persistent CTAs per SM of each stage on the live members
  * (their states are saved and restored bit for bit) and keeps the fastest; the choice is cached
  * per size signature for the process.  ch_ensemble_tuning writes the choice as a JSON object. */
@@ -281,6 +282,17 @@ int ch_ensemble_step(ch_ensemble* e, int nsteps);
 #define CH_ENSEMBLE_STAGES 6
 int ch_ensemble_step_timed(ch_ensemble* e, int nsteps, double* stage_ms, double* total_ms);
 int ch_ensemble_autotune(ch_ensemble* e, int reps);
+/* Chebyshev method of the ensemble step (CH_CHEB_FFT default, CH_CHEB_TC): with CH_CHEB_TC the
+ * grouped zrhs and zbwd stages read and write float64 Chebyshev coefficients and each member's
+ * z transforms run on the tensor cores (ch_set_chebyshev, Sec. 3.1 transforms), one launch per
+ * member before zrhs and one after zbwd, inside the step's graph and timed with stages 0 and 2
+ * of ch_ensemble_step_timed.  Sets every member's own method too (a later ch_set_chebyshev on a
+ * member does not change the ensemble's).  The tuning is kept per method: switching takes the
+ * cached choice for the new method or the defaults; the graph is rebuilt at the next step.
+ * Errors: CH_ERR_ARG for an unknown method or a null handle, and the errors of
+ * ch_set_chebyshev (CH_ERR_SIZE for nz > 496, CH_ERR_ALLOC); the method is unchanged then. */
+int ch_ensemble_set_chebyshev(ch_ensemble* e, int method);
+int ch_ensemble_get_chebyshev(const ch_ensemble* e);
 int ch_ensemble_tuning(const ch_ensemble* e, char* buf, size_t n);
 void ch_ensemble_destroy(ch_ensemble* e);
 

@@ -101,6 +101,8 @@ _SIGS = {
                                               ctypes.POINTER(ctypes.c_double)]),
     "ch_ensemble_autotune": (ctypes.c_int, [_P, ctypes.c_int]),
     "ch_ensemble_tuning": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    "ch_ensemble_set_chebyshev": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ch_ensemble_get_chebyshev": (ctypes.c_int, [_P]),
     "ch_ensemble_destroy": (None, [_P]),
     "ch_destroy": (None, [_P]),
     "ch_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -511,6 +513,13 @@ class Ensemble:
     def autotune(self, reps=2):
         _ck("ch_ensemble_autotune", lib().ch_ensemble_autotune(self.h, int(reps)))
         return self.tuning()
+
+    def set_chebyshev(self, method):
+        """CHEB_FFT or CHEB_TC for the grouped step (and every member); see ch_flow.h."""
+        _ck("ch_ensemble_set_chebyshev", lib().ch_ensemble_set_chebyshev(self.h, int(method)))
+
+    def chebyshev(self):
+        return int(lib().ch_ensemble_get_chebyshev(self.h))
 
     def tuning(self):
         import json

@@ -4,7 +4,10 @@
 // the ensemble is six grouped persistent launches, one per stage (z right-hand sides, tau
 // solves, z backward, y backward, x line, y forward): the CTAs of a launch walk a flat work list
 // that numbers every member's tiles, so small members share the GPU instead of each leaving it
-// mostly idle.  The six launches are captured once into a CUDA graph and replayed per step.
+// mostly idle.  With the tensor-core Chebyshev method each member adds its two z-transform
+// launches (its own persistent grid over its tiles of rows) before zrhs and after zbwd, and the
+// grouped zrhs / zbwd work on coefficients.  The launches are captured once into a CUDA graph
+// and replayed per step.
 //
 // Autotuner: for the ensemble's sizes it times, on the live ensemble (state saved and restored
 // bit for bit), the radix schedules of the x, y and z transforms (three styles each, chosen per
@@ -27,10 +30,10 @@ size_t zsolve_tile_smem(const GridDev& g);
 int zsolve_tile_lines();
 int zsolve_threads();
 cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* begin, int nmem,
-                             int grid, size_t smem, int zsolve_tile, cudaStream_t s);
+                             int grid, size_t smem, int zsolve_tile, int coef, cudaStream_t s);
 cudaError_t launch_grouped_xy(int stage, int prec, const Member* mem, const int* begin, int nmem,
                               int grid, size_t smem, cudaStream_t s);
-int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile);
+int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile, int coef);
 int occupancy_xy(int stage, int prec, size_t smem);
 
 int stage_items(int stage, const Member& m, int prec) {
@@ -61,13 +64,15 @@ size_t stage_smem(int stage, const Member& m, int prec) {
   }
 }
 
-int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile) {
-  return stage <= 2 ? occupancy_z(stage, prec, smem, zsolve_tile) : occupancy_xy(stage, prec, smem);
+int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile, int coef) {
+  return stage <= 2 ? occupancy_z(stage, prec, smem, zsolve_tile, coef)
+                    : occupancy_xy(stage, prec, smem);
 }
 
 cudaError_t launch_grouped(int stage, int prec, const Member* mem, const int* begin, int nmem,
-                           int grid, size_t smem, int zsolve_tile, cudaStream_t s) {
-  if (stage <= 2) return launch_grouped_z(stage, prec, mem, begin, nmem, grid, smem, zsolve_tile, s);
+                           int grid, size_t smem, int zsolve_tile, int coef, cudaStream_t s) {
+  if (stage <= 2)
+    return launch_grouped_z(stage, prec, mem, begin, nmem, grid, smem, zsolve_tile, coef, s);
   return launch_grouped_xy(stage, prec, mem, begin, nmem, grid, smem, s);
 }
 
@@ -93,6 +98,7 @@ std::map<std::string, Tuning> g_tune_cache;
 struct ch_ensemble {
   std::vector<ch_grid*> members;
   int prec;
+  int cheb;                     // Chebyshev method of the grouped step (CH_CHEB_FFT / CH_CHEB_TC)
   int nsm;
   cudaStream_t stream;
   cudaStream_t cap;
@@ -185,6 +191,7 @@ int build_descriptors(ch_ensemble* E) {
     M.hw = G->hw;
     M.hphi = G->hphi;
     M.R = G->R;
+    M.cf = G->cf;
     M.fs = G->fs;
     M.fsy = G->fsy;
     M.first = G->first;
@@ -237,11 +244,35 @@ int grid_of(ch_ensemble* E, int s) {
   return g < 1 ? 1 : (int)g;
 }
 
+// tensor-core Chebyshev method: one transform launch per member around the grouped z stages,
+// dir 0 (before zrhs) the nine products' samples -> coefficients, dir 1 (after zbwd) the five
+// backward fields' coefficients -> samples.  Each launch is a persistent grid over that member's
+// tiles of rows.
+cudaError_t member_transforms(ch_ensemble* E, int dir, cudaStream_t s) {
+  for (ch_grid* G : E->members) {
+    const int nlines = G->g.Mx * G->g.ny;
+    const cudaError_t e =
+        dir == 0 ? chf::launch_cheb_tc(E->prec, 0, G->nl, G->fs, G->cf, G->fs, chf::kNl, nlines,
+                                       G->g.nz, G->tcf, G->tc_err, s)
+                 : chf::launch_cheb_tc(0, E->prec, G->cf, G->fs, G->bw, G->fs, chf::kBw, nlines,
+                                       G->g.nz, G->tcb, G->tc_err, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// one ensemble step: the six grouped stages; with the tensor-core method the member transforms
+// run before stage 0 and after stage 2 and are timed with those stages
 int launch_all(ch_ensemble* E, cudaStream_t s, cudaEvent_t* ev) {
   const int n = (int)E->members.size();
+  const int tc = E->cheb == CH_CHEB_TC;
   for (int st = 0; st < kStages; ++st) {
-    cudaError_t e = chf::launch_grouped(st, E->prec, E->dmem, E->dbegin + (size_t)st * (n + 1), n,
-                                        grid_of(E, st), E->smem[st], E->zsolve_tile, s);
+    cudaError_t e = cudaSuccess;
+    if (tc && st == 0) e = member_transforms(E, 0, s);
+    if (e == cudaSuccess)
+      e = chf::launch_grouped(st, E->prec, E->dmem, E->dbegin + (size_t)st * (n + 1), n,
+                              grid_of(E, st), E->smem[st], E->zsolve_tile, tc, s);
+    if (e == cudaSuccess && tc && st == 2) e = member_transforms(E, 1, s);
     if (ev) cudaEventRecord(ev[st], s);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -249,6 +280,24 @@ int launch_all(ch_ensemble* E, cudaStream_t s, cudaEvent_t* ev) {
     }
   }
   return CH_OK;
+}
+
+void compute_occupancy(ch_ensemble* E) {
+  for (int s = 0; s < kStages; ++s)
+    E->occ[s] = chf::stage_occupancy(s, E->prec, E->smem[s], E->zsolve_tile,
+                                     E->cheb == CH_CHEB_TC);
+}
+
+// tuning cache key: member sizes, precision and Chebyshev method
+std::string signature_of(const ch_ensemble* E) {
+  std::string sig;
+  char b[64];
+  for (const ch_grid* G : E->members) {
+    snprintf(b, sizeof(b), "%dx%dx%d/", G->g.nx, G->g.ny, G->g.nz);
+    sig += b;
+  }
+  snprintf(b, sizeof(b), "p%d/c%d", E->prec, E->cheb);
+  return sig + b;
 }
 
 void drop_graph(ch_ensemble* E) {
@@ -319,6 +368,7 @@ int ch_ensemble_init(const ch_params* members, int n, ch_alloc_fn alloc, ch_free
   ch_ensemble* E = new (std::nothrow) ch_ensemble();
   if (!E) return CH_ERR_ALLOC;
   E->prec = members[0].precision;
+  E->cheb = CH_CHEB_FFT;
   E->stream = (cudaStream_t)stream;
   E->af = alloc;
   E->ff = free_fn;
@@ -333,16 +383,12 @@ int ch_ensemble_init(const ch_params* members, int n, ch_alloc_fn alloc, ch_free
     return CH_ERR_CUDA;
   }
   int st = CH_OK;
-  char sig[64];
   for (int i = 0; i < n && st == CH_OK; ++i) {
     ch_grid* G = nullptr;
     st = ch_init_grid(&members[i], alloc, free_fn, alloc_ctx, stream, &G);
     if (st == CH_OK) E->members.push_back(G);
-    snprintf(sig, sizeof(sig), "%dx%dx%d/", members[i].nx, members[i].ny, members[i].nz);
-    E->signature += sig;
   }
-  snprintf(sig, sizeof(sig), "p%d", E->prec);
-  E->signature += sig;
+  if (st == CH_OK) E->signature = signature_of(E);
   if (st == CH_OK) {
     E->dmem = (Member*)ealloc(E, n * sizeof(Member));
     E->dbegin = (int*)ealloc(E, (size_t)kStages * (n + 1) * sizeof(int));
@@ -355,7 +401,7 @@ int ch_ensemble_init(const ch_params* members, int n, ch_alloc_fn alloc, ch_free
   }
   if (st == CH_OK) st = build_descriptors(E);
   if (st == CH_OK) {
-    for (int s = 0; s < kStages; ++s) E->occ[s] = chf::stage_occupancy(s, E->prec, E->smem[s], E->zsolve_tile);
+    compute_occupancy(E);
     st = upload(E);
   }
   if (st == CH_OK && cudaStreamSynchronize(E->stream) != cudaSuccess) st = CH_ERR_CUDA;
@@ -377,6 +423,45 @@ int ch_ensemble_member(ch_ensemble* E, int i, ch_grid** out) {
   *out = E->members[i];
   return CH_OK;
 }
+
+int ch_ensemble_set_chebyshev(ch_ensemble* E, int method) {
+  if (!E || (method != CH_CHEB_FFT && method != CH_CHEB_TC)) return CH_ERR_ARG;
+  if (method == E->cheb) return CH_OK;
+  // every member takes the method (its tables and coefficient buffer stay allocated for the
+  // member's lifetime once made, so a later change of a member's own method leaves the
+  // ensemble's step intact)
+  for (size_t i = 0; i < E->members.size(); ++i) {
+    const int st = ch_set_chebyshev(E->members[i], method);
+    if (st != CH_OK) {
+      for (size_t j = 0; j < i; ++j) ch_set_chebyshev(E->members[j], E->cheb);
+      return st;
+    }
+  }
+  if (cudaStreamSynchronize(E->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return CH_ERR_CUDA;
+  }
+  E->cheb = method;
+  E->signature = signature_of(E);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(E->signature);
+    E->tune = it != g_tune_cache.end() ? it->second : Tuning();
+  }
+  int st = build_descriptors(E);
+  if (st == CH_OK) {
+    compute_occupancy(E);
+    st = upload(E);
+  }
+  drop_graph(E);
+  if (st == CH_OK && cudaStreamSynchronize(E->stream) != cudaSuccess) {
+    cudaGetLastError();
+    st = CH_ERR_CUDA;
+  }
+  return st;
+}
+
+int ch_ensemble_get_chebyshev(const ch_ensemble* E) { return E ? E->cheb : CH_ERR_ARG; }
 
 int ch_ensemble_step(ch_ensemble* E, int nsteps) {
   if (!E || nsteps < 0) return CH_ERR_ARG;
@@ -500,11 +585,11 @@ int ch_ensemble_tuning(const ch_ensemble* E, char* buf, size_t n) {
   snprintf(buf, n,
            "{\"tuned\": %d, \"radix_style\": {\"x\": %d, \"y\": %d, \"z\": %d}, "
            "\"ctas_per_sm\": [%d, %d, %d, %d, %d, %d], \"occupancy\": [%d, %d, %d, %d, %d, %d], "
-           "\"zsolve_tile\": %d}",
+           "\"zsolve_tile\": %d, \"chebyshev\": %d}",
            E->tune.tuned, E->tune.style[0], E->tune.style[1], E->tune.style[2],
            E->tune.ctas_per_sm[0], E->tune.ctas_per_sm[1], E->tune.ctas_per_sm[2],
            E->tune.ctas_per_sm[3], E->tune.ctas_per_sm[4], E->tune.ctas_per_sm[5], E->occ[0],
-           E->occ[1], E->occ[2], E->occ[3], E->occ[4], E->occ[5], E->zsolve_tile);
+           E->occ[1], E->occ[2], E->occ[3], E->occ[4], E->occ[5], E->zsolve_tile, E->cheb);
   return CH_OK;
 }
 

@@ -101,6 +101,7 @@ struct Member {
   void* ya;                       // 6 y-padded fields (Mx, Py, Nz)
   void* yb;                       // 9 y-padded product fields (Mx, Py, Nz)
   double2 *om, *w, *phi, *hom, *hw, *hphi, *R;
+  double2* cf;                    // 9 Chebyshev coefficient fields (tensor-core method), or null
   long long fs, fsy;
   int first;                      // 1: this step starts Adams-Bashforth
   int tzb, tzf;                   // y-pass z tiles (backward, forward)
@@ -113,14 +114,16 @@ struct Member {
 
 // Grouped persistent launches over all members: stage work items are numbered member by member,
 // begin[m] = first item of member m, begin[nmem] = total; `grid` CTAs loop over the items.
-// stage: 0 zrhs, 1 zsolve, 2 zbwd, 3 y backward, 4 x line, 5 y forward.
+// stage: 0 zrhs, 1 zsolve, 2 zbwd, 3 y backward, 4 x line, 5 y forward.  coef = 1: zrhs reads
+// and zbwd writes Chebyshev coefficients in Member::cf (the tensor-core transforms run around
+// them) instead of transforming along z themselves.
 cudaError_t launch_grouped(int stage, int prec, const Member* mem, const int* begin, int nmem,
-                           int grid, size_t smem, int zsolve_tile, cudaStream_t s);
+                           int grid, size_t smem, int zsolve_tile, int coef, cudaStream_t s);
 // work items of one member for a stage, and the dynamic shared memory one item needs
 int stage_items(int stage, const Member& m, int prec);
 size_t stage_smem(int stage, const Member& m, int prec);
 // CTAs per SM that the stage kernel can hold with `smem` bytes (occupancy API)
-int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile);
+int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile, int coef);
 // y-pass z tile for a padded length P (shared by single-grid and grouped launches)
 int ytile_for(int P, size_t elem);
 // x-line shared memory for a padded length Px

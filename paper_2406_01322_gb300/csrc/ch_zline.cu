@@ -1775,6 +1775,33 @@ __global__ void __launch_bounds__(ZT) grouped_zbwd_kernel(const Member* __restri
   }
 }
 
+// tensor-core Chebyshev method: the products' coefficients are in M.cf (float64 whatever the
+// working precision), and zbwd leaves the 5 backward fields' coefficients there
+__global__ void __launch_bounds__(ZT) grouped_zrhs_coef_kernel(const Member* __restrict__ mem,
+                                                               const int* __restrict__ begin,
+                                                               int nmem) {
+  const int total = begin[nmem];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int m = member_of(begin, nmem, item);
+    const Member& M = mem[m];
+    zrhs_body<double, 1>(M.g, M.cf, M.fs, M.om, M.w, M.phi, M.hom, M.hw, M.hphi, M.R, M.first,
+                         M.pz, item - begin[m]);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(ZT) grouped_zbwd_coef_kernel(const Member* __restrict__ mem,
+                                                               const int* __restrict__ begin,
+                                                               int nmem) {
+  const int total = begin[nmem];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int m = member_of(begin, nmem, item);
+    const Member& M = mem[m];
+    zbwd_body<double, 1, 5, 1>(M.g, M.R, M.om, M.w, M.phi, M.cf, M.fs, M.pz, item - begin[m]);
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(2 * TL) grouped_zsolve_tile_kernel(const Member* __restrict__ mem,
                                                                      const int* __restrict__ begin,
                                                                      int nmem) {
@@ -1883,9 +1910,19 @@ int zsolve_tile_lines() { return TL; }
 int zsolve_threads() { return ST; }
 
 cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* begin, int nmem,
-                             int grid, size_t smem, int zsolve_tile, cudaStream_t s) {
+                             int grid, size_t smem, int zsolve_tile, int coef, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (stage == 0) {
+  if (coef && stage != 1) {
+    if (stage == 0) {
+      static int cur = 0;
+      if ((e = ensure_smem(grouped_zrhs_coef_kernel, smem, &cur)) != cudaSuccess) return e;
+      grouped_zrhs_coef_kernel<<<grid, ZT, smem, s>>>(mem, begin, nmem);
+    } else {
+      static int cur = 0;
+      if ((e = ensure_smem(grouped_zbwd_coef_kernel, smem, &cur)) != cudaSuccess) return e;
+      grouped_zbwd_coef_kernel<<<grid, ZT, smem, s>>>(mem, begin, nmem);
+    }
+  } else if (stage == 0) {
     if (prec == 0) {
       static int cur = 0;
       if ((e = ensure_smem(grouped_zrhs_kernel<double>, smem, &cur)) != cudaSuccess) return e;
@@ -1917,18 +1954,24 @@ cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* 
   return cudaGetLastError();
 }
 
-int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile) {
+int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile, int coef) {
   int n = 0;
   // the opt-in above 48 KB must be in place before the query (init time, never during capture)
   if (smem > 48 * 1024) {
     const void* k = stage == 0 ? (prec == 0 ? (const void*)grouped_zrhs_kernel<double> : (const void*)grouped_zrhs_kernel<float>)
                   : stage == 1 ? (const void*)grouped_zsolve_tile_kernel
                                : (prec == 0 ? (const void*)grouped_zbwd_kernel<double> : (const void*)grouped_zbwd_kernel<float>);
+    if (coef && stage != 1)
+      k = stage == 0 ? (const void*)grouped_zrhs_coef_kernel : (const void*)grouped_zbwd_coef_kernel;
     if (stage != 1 || zsolve_tile)
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaGetLastError();
   }
-  if (stage == 0)
+  if (coef && stage != 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, stage == 0 ? (const void*)grouped_zrhs_coef_kernel : (const void*)grouped_zbwd_coef_kernel,
+        ZT, smem);
+  else if (stage == 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prec == 0 ? (const void*)grouped_zrhs_kernel<double>
                                                                 : (const void*)grouped_zrhs_kernel<float>, ZT, smem);
   else if (stage == 1)

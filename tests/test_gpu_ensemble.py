@@ -130,3 +130,76 @@ def test_ensemble_of_mixed_wall_conditions_matches_single_grids(binding):
         for a, b in zip(g.get_fields(), s.get_fields()):
             assert torch.equal(a, b)
     ens.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ensemble_tensor_core_chebyshev_matches_single_grids_bitwise(binding, precision):
+    """CHEB_TC in the ensemble: each member's z transforms are the single-grid tensor-core
+    launches and the grouped zrhs / zbwd run the single-grid coefficient kernels' arithmetic, so
+    every member matches the same channel stepped alone with CHEB_TC bit for bit."""
+    ens, singles = setup(binding, precision)
+    ens.set_chebyshev(binding.CHEB_TC)
+    assert ens.chebyshev() == binding.CHEB_TC
+    assert all(g.chebyshev() == binding.CHEB_TC for g in ens.grids)
+    assert ens.tuning()["chebyshev"] == binding.CHEB_TC
+    for s in singles:
+        s.set_chebyshev(binding.CHEB_TC)
+    ens.step(6)
+    for s in singles:
+        s.step(6)
+    for g, s in zip(ens.grids, singles):
+        g.device_status()
+        for a, b in zip(g.get_fields(), s.get_fields()):
+            assert torch.equal(a, b)
+        assert g.diagnostics()["step"] == 6
+    ens.close()
+
+
+def test_ensemble_tensor_core_chebyshev_agrees_with_fft_method(binding):
+    """FP64 ensemble, ten steps with each Chebyshev method: both transforms are float64-accurate
+    (the tensor-core one within 1e-15 of the exact transform per line), so the fields agree to
+    rounding; the timed step (member transforms counted in stages 0 and 2) gives the graph step's
+    fields."""
+    ens_f, _ = setup(binding, 0)
+    ens_t, singles = setup(binding, 0)
+    ens_t.set_chebyshev(binding.CHEB_TC)
+    ens_f.step(10)
+    tot, ks = ens_t.step_timed(4)
+    assert len(ks) == 6 and tot > 0 and min(ks) >= 0
+    ens_t.step(6)
+    for s in singles:
+        s.set_chebyshev(binding.CHEB_TC)
+        s.step(10)
+    for gf, gt, s in zip(ens_f.grids, ens_t.grids, singles):
+        for a, b, c in zip(gt.get_fields(), gf.get_fields(), s.get_fields()):
+            assert torch.equal(a, c)
+            rel = float((a - b).abs().max() / b.abs().max())
+            assert rel < 1e-11
+    ens_f.close()
+    ens_t.close()
+
+
+def test_ensemble_switches_chebyshev_method_and_autotunes(binding):
+    """Switching the ensemble's method mid-run continues the same trajectory (to rounding), an
+    unknown method is rejected without a change, and autotuning under CHEB_TC keeps the state."""
+    ens, singles = setup(binding, 0)
+    ens.step(2)
+    ens.set_chebyshev(binding.CHEB_TC)
+    ens.step(2)
+    with pytest.raises(binding.ChError) as e:
+        ens.set_chebyshev(7)
+    assert e.value.code == -1 and ens.chebyshev() == binding.CHEB_TC
+    before = [[t.clone() for t in g.get_fields()] for g in ens.grids]
+    assert ens.autotune(reps=1)["tuned"] == 1
+    for x, g in zip(before, ens.grids):
+        for a, b in zip(x, g.get_fields()):
+            assert torch.equal(a, b)
+    ens.set_chebyshev(binding.CHEB_FFT)
+    ens.step(2)
+    for s in singles:
+        s.step(6)
+    for g, s in zip(ens.grids, singles):
+        for a, b in zip(g.get_fields(), s.get_fields()):
+            rel = float((a - b).abs().max() / b.abs().max())
+            assert rel < 1e-11
+    ens.close()
