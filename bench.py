@@ -506,7 +506,8 @@ def run_reference(args, w):
 
 
 def run_ensemble(args):
-    """32 uneven channels (mixed precision) advanced by grouped persistent launches, after the
+    """32 uneven channels (mixed precision; --precision 0 or 2 for FP64 or double-float x/y)
+    advanced by grouped persistent launches, after the
     autotuner; the same members stepped one by one with their own graphs are timed beside it.
     With --cheb tc every member's z transforms run on the tensor cores (two launches per member
     per step beside the six grouped ones)."""
@@ -515,8 +516,9 @@ def run_ensemble(args):
     build.build_library()
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    ms = inputs.ensemble_members()
-    ens = binding.Ensemble(ms, precision=1, device=f"cuda:{local}")
+    prec = 1 if args.precision is None else args.precision
+    ms = [dict(m, precision=prec) for m in inputs.ensemble_members()]
+    ens = binding.Ensemble(ms, precision=prec, device=f"cuda:{local}")
     tc = args.cheb == "tc"
     if tc:
         ens.set_chebyshev(binding.CHEB_TC)
@@ -559,11 +561,12 @@ def run_ensemble(args):
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None,
-           "dtype": "f32 x/y transforms and products, f64 z transforms and solves"
+           "dtype": {0: "f64", 1: "f32 x/y transforms and products, f64 z transforms and solves",
+                     2: "double-float x/y transforms and products, f64 z transforms and solves"}[prec]
                     + (" (z transforms as exact-split bf16 tensor-core products)" if tc else ""),
            "data": "synthetic",
            "config": {"workload": "ensemble_32_uneven", "members": len(ms),
-                      "points": pts, "precision": "mixed", "chebyshev": args.cheb},
+                      "points": pts, "precision": PREC_NAMES[prec], "chebyshev": args.cheb},
            "sequential_members_ms_per_step": seq_ms / args.steps,
            "e2e": {"value": pts * args.steps / e2e_s / 1e6, "unit": UNIT,
                    "h2d_bytes_per_step": nbytes / args.steps,

@@ -70,7 +70,7 @@ typedef struct {
   double pe;          /* Peclet number                                                     */
   double dt;          /* time step (> 0)                                                   */
   double gx, gy;      /* mean pressure gradient -dp/dx, -dp/dy driving the mean flow       */
-  int precision;      /* CH_PREC_FP64, CH_PREC_MIXED or CH_PREC_DFLOAT (single grids only)   */
+  int precision;      /* CH_PREC_FP64, CH_PREC_MIXED or CH_PREC_DFLOAT                      */
   int dealias_z;      /* must be 0: no padding of the Chebyshev direction                  */
   int bc;             /* walls (Sec. 2.1: no-slip, free-slip or a combination): 0 no-slip
                          (u = v = w = dw/dz = 0) at both walls, 1 free-slip (du/dz = dv/dz = 0,
@@ -261,12 +261,12 @@ int ch_render_interface(ch_grid* g, unsigned char* rgb, double* depth, int width
 
 /* ---- Ensemble of independent channels (uneven sizes) ---------------------------------------
  * Not in the paper: a batching service of this library.  Each member is an ordinary ch_grid
- * (created here with the given allocator and stream; all members share `precision`).  One
- * ensemble step advances every member by one time step with six grouped persistent launches
- * (one per stage; their CTAs walk a work list spanning all members; with CH_CHEB_TC two more per
- * member), captured once into a CUDA graph and replayed.  Members are set, read and diagnosed
- * through their ch_grid handles (ch_ensemble_member); ch_ensemble_step needs every member set.
- * ch_ensemble_autotune times the
+ * (created here with the given allocator and stream; all members share one `precision`, any of
+ * the three; CH_ERR_ARG if they differ).  One ensemble step advances every member by one time
+ * step with six grouped persistent launches (one per stage; their CTAs walk a work list spanning
+ * all members; with CH_CHEB_TC two more per member), captured once into a CUDA graph and
+ * replayed.  Members are set, read and diagnosed through their ch_grid handles
+ * (ch_ensemble_member); ch_ensemble_step needs every member set.  ch_ensemble_autotune times the
  * transforms' radix schedules and the persistent CTAs per SM of each stage on the live members
  * (their states are saved and restored bit for bit) and keeps the fastest; the choice is cached
  * per size signature for the process.  ch_ensemble_tuning writes the choice as a JSON object. */

@@ -469,7 +469,8 @@ def objective_after(grid, u, v, w, phi, nsteps, checkpoint_every=10):
 class Ensemble:
     """Independent channels of uneven sizes advanced together by grouped persistent launches
     (one per stage, replayed from a CUDA graph).  members: list of dicts with the Grid keyword
-    arguments (nx, ny, nz, re_tau, we, ch, pe, dt, ...); all members share `precision`.
+    arguments (nx, ny, nz, re_tau, we, ch, pe, dt, ...); all members share one precision
+    (`precision`, or a member's own "precision" key, which must then agree).
     ensemble.grids[i] is a Grid view of member i (set_fields, get_fields, diagnostics ...)."""
 
     def __init__(self, members, precision=PREC_FP64, device="cuda:0", stream=None):
@@ -481,7 +482,7 @@ class Ensemble:
             arr[i] = Params(m["nx"], m["ny"], m["nz"], m.get("lx", 4 * math.pi),
                             m.get("ly", 2 * math.pi), m.get("re_tau", 150.0), m.get("we", 1.0),
                             m.get("ch", 0.05), m.get("pe", 20.0), m.get("dt", 1e-4),
-                            m.get("gx", 1.0), m.get("gy", 0.0), precision, 0,
+                            m.get("gx", 1.0), m.get("gy", 0.0), m.get("precision", precision), 0,
                             m.get("bc", BC_NO_SLIP))
         self._params = arr
         self._alloc = TorchAllocator(self.device)

@@ -53,7 +53,7 @@ int stage_items(int stage, const Member& m, int prec) {
 }
 
 size_t stage_smem(int stage, const Member& m, int prec) {
-  const size_t elem = prec == 0 ? sizeof(double2) : sizeof(float2);
+  const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);   // df2 is 16 bytes too
   switch (stage) {
     case 0:
     case 2: return zline_smem(m.g);
@@ -162,7 +162,7 @@ void apply_style(chf::FftPlan* pl, int style) {
 // host descriptors, work lists, per-stage shared memory and occupancy from the members
 int build_descriptors(ch_ensemble* E) {
   const int n = (int)E->members.size();
-  const size_t elem = E->prec == 0 ? sizeof(double2) : sizeof(float2);
+  const size_t elem = E->prec == 1 ? sizeof(float2) : sizeof(double2);   // df2 is 16 bytes too
   E->hmem.resize(n);
   E->zsolve_tile = 1;
   for (int i = 0; i < n; ++i) {
@@ -364,7 +364,6 @@ int ch_ensemble_init(const ch_params* members, int n, ch_alloc_fn alloc, ch_free
   *out = nullptr;
   for (int i = 0; i < n; ++i)
     if (members[i].precision != members[0].precision) return CH_ERR_ARG;
-  if (members[0].precision == CH_PREC_DFLOAT) return CH_ERR_ARG;  // grouped kernels: fp64/fp32
   ch_ensemble* E = new (std::nothrow) ch_ensemble();
   if (!E) return CH_ERR_ALLOC;
   E->prec = members[0].precision;

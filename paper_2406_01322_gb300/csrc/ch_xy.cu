@@ -559,19 +559,22 @@ size_t xline_smem(int Px, size_t elem) { return (size_t)17 * Px * elem; }
 cudaError_t launch_grouped_xy(int stage, int prec, const Member* mem, const int* begin, int nmem,
                               int grid, size_t smem, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  static int cur[6] = {0, 0, 0, 0, 0, 0};
+  static int cur[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 #define GL(K, idx, T_)                                                   \
   if ((e = ensure_smem(K, smem, &cur[idx])) != cudaSuccess) return e;    \
   K<<<grid, (stage == 4 ? XT : YT), smem, s>>>(mem, begin, nmem);
   if (stage == 3) {
     if (prec == 0) { GL((grouped_ypass_kernel<double, true>), 0, double) }
-    else { GL((grouped_ypass_kernel<float, true>), 1, float) }
+    else if (prec == 1) { GL((grouped_ypass_kernel<float, true>), 1, float) }
+    else { GL((grouped_ypass_kernel<df, true>), 6, df) }
   } else if (stage == 4) {
     if (prec == 0) { GL(grouped_xline_kernel<double>, 2, double) }
-    else { GL(grouped_xline_kernel<float>, 3, float) }
+    else if (prec == 1) { GL(grouped_xline_kernel<float>, 3, float) }
+    else { GL(grouped_xline_kernel<df>, 7, df) }
   } else {
     if (prec == 0) { GL((grouped_ypass_kernel<double, false>), 4, double) }
-    else { GL((grouped_ypass_kernel<float, false>), 5, float) }
+    else if (prec == 1) { GL((grouped_ypass_kernel<float, false>), 5, float) }
+    else { GL((grouped_ypass_kernel<df, false>), 8, df) }
   }
 #undef GL
   return cudaGetLastError();
@@ -580,9 +583,18 @@ cudaError_t launch_grouped_xy(int stage, int prec, const Member* mem, const int*
 int occupancy_xy(int stage, int prec, size_t smem) {
   int n = 0;
   const void* k;
-  if (stage == 3) k = prec == 0 ? (const void*)grouped_ypass_kernel<double, true> : (const void*)grouped_ypass_kernel<float, true>;
-  else if (stage == 4) k = prec == 0 ? (const void*)grouped_xline_kernel<double> : (const void*)grouped_xline_kernel<float>;
-  else k = prec == 0 ? (const void*)grouped_ypass_kernel<double, false> : (const void*)grouped_ypass_kernel<float, false>;
+  if (stage == 3)
+    k = prec == 0 ? (const void*)grouped_ypass_kernel<double, true>
+      : prec == 1 ? (const void*)grouped_ypass_kernel<float, true>
+                  : (const void*)grouped_ypass_kernel<df, true>;
+  else if (stage == 4)
+    k = prec == 0 ? (const void*)grouped_xline_kernel<double>
+      : prec == 1 ? (const void*)grouped_xline_kernel<float>
+                  : (const void*)grouped_xline_kernel<df>;
+  else
+    k = prec == 0 ? (const void*)grouped_ypass_kernel<double, false>
+      : prec == 1 ? (const void*)grouped_ypass_kernel<float, false>
+                  : (const void*)grouped_ypass_kernel<df, false>;
   if (smem > 48 * 1024) {  // opt-in first (init time, never during capture)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaGetLastError();

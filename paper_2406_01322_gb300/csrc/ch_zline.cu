@@ -1927,10 +1927,14 @@ cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* 
       static int cur = 0;
       if ((e = ensure_smem(grouped_zrhs_kernel<double>, smem, &cur)) != cudaSuccess) return e;
       grouped_zrhs_kernel<double><<<grid, ZT, smem, s>>>(mem, begin, nmem);
-    } else {
+    } else if (prec == 1) {
       static int cur = 0;
       if ((e = ensure_smem(grouped_zrhs_kernel<float>, smem, &cur)) != cudaSuccess) return e;
       grouped_zrhs_kernel<float><<<grid, ZT, smem, s>>>(mem, begin, nmem);
+    } else {
+      static int cur = 0;
+      if ((e = ensure_smem(grouped_zrhs_kernel<df>, smem, &cur)) != cudaSuccess) return e;
+      grouped_zrhs_kernel<df><<<grid, ZT, smem, s>>>(mem, begin, nmem);
     }
   } else if (stage == 1) {
     if (zsolve_tile) {
@@ -1945,22 +1949,35 @@ cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* 
       static int cur = 0;
       if ((e = ensure_smem(grouped_zbwd_kernel<double>, smem, &cur)) != cudaSuccess) return e;
       grouped_zbwd_kernel<double><<<grid, ZT, smem, s>>>(mem, begin, nmem);
-    } else {
+    } else if (prec == 1) {
       static int cur = 0;
       if ((e = ensure_smem(grouped_zbwd_kernel<float>, smem, &cur)) != cudaSuccess) return e;
       grouped_zbwd_kernel<float><<<grid, ZT, smem, s>>>(mem, begin, nmem);
+    } else {
+      static int cur = 0;
+      if ((e = ensure_smem(grouped_zbwd_kernel<df>, smem, &cur)) != cudaSuccess) return e;
+      grouped_zbwd_kernel<df><<<grid, ZT, smem, s>>>(mem, begin, nmem);
     }
   }
   return cudaGetLastError();
+}
+
+// grouped zrhs (stage 0) or zbwd (stage 2) kernel of a working precision
+static const void* zkernel(int stage, int prec) {
+  if (stage == 0)
+    return prec == 0 ? (const void*)grouped_zrhs_kernel<double>
+         : prec == 1 ? (const void*)grouped_zrhs_kernel<float>
+                     : (const void*)grouped_zrhs_kernel<df>;
+  return prec == 0 ? (const void*)grouped_zbwd_kernel<double>
+       : prec == 1 ? (const void*)grouped_zbwd_kernel<float>
+                   : (const void*)grouped_zbwd_kernel<df>;
 }
 
 int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile, int coef) {
   int n = 0;
   // the opt-in above 48 KB must be in place before the query (init time, never during capture)
   if (smem > 48 * 1024) {
-    const void* k = stage == 0 ? (prec == 0 ? (const void*)grouped_zrhs_kernel<double> : (const void*)grouped_zrhs_kernel<float>)
-                  : stage == 1 ? (const void*)grouped_zsolve_tile_kernel
-                               : (prec == 0 ? (const void*)grouped_zbwd_kernel<double> : (const void*)grouped_zbwd_kernel<float>);
+    const void* k = stage == 1 ? (const void*)grouped_zsolve_tile_kernel : zkernel(stage, prec);
     if (coef && stage != 1)
       k = stage == 0 ? (const void*)grouped_zrhs_coef_kernel : (const void*)grouped_zbwd_coef_kernel;
     if (stage != 1 || zsolve_tile)
@@ -1972,15 +1989,13 @@ int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile, int coef) {
         &n, stage == 0 ? (const void*)grouped_zrhs_coef_kernel : (const void*)grouped_zbwd_coef_kernel,
         ZT, smem);
   else if (stage == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prec == 0 ? (const void*)grouped_zrhs_kernel<double>
-                                                                : (const void*)grouped_zrhs_kernel<float>, ZT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zkernel(0, prec), ZT, smem);
   else if (stage == 1)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zsolve_tile ? (const void*)grouped_zsolve_tile_kernel
                                                                   : (const void*)grouped_zsolve_kernel,
                                                   zsolve_tile ? 2 * TL : ST, zsolve_tile ? smem : 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prec == 0 ? (const void*)grouped_zbwd_kernel<double>
-                                                                : (const void*)grouped_zbwd_kernel<float>, ZT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zkernel(2, prec), ZT, smem);
   cudaGetLastError();
   return n;
 }

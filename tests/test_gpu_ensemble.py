@@ -47,7 +47,7 @@ def setup(binding, precision):
     return ens, singles
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_ensemble_members_match_single_grids_bitwise(binding, precision):
     ens, singles = setup(binding, precision)
     ens.step(6)
@@ -102,10 +102,12 @@ def test_ensemble_requires_every_member_set(binding):
     ens.close()
 
 
-def test_ensemble_rejects_double_float(binding):
-    """The grouped kernels exist in float64 and float32 only."""
+def test_ensemble_rejects_mixed_precisions(binding):
+    """All members share one precision (one grouped kernel per stage)."""
+    ms = members()[:2]
+    ms[1]["precision"] = binding.PREC_MIXED
     with pytest.raises(binding.ChError) as e:
-        binding.Ensemble(members()[:2], precision=binding.PREC_DFLOAT)
+        binding.Ensemble(ms, precision=binding.PREC_FP64)
     assert e.value.code == -1
 
 
@@ -132,7 +134,7 @@ def test_ensemble_of_mixed_wall_conditions_matches_single_grids(binding):
     ens.close()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_ensemble_tensor_core_chebyshev_matches_single_grids_bitwise(binding, precision):
     """CHEB_TC in the ensemble: each member's z transforms are the single-grid tensor-core
     launches and the grouped zrhs / zbwd run the single-grid coefficient kernels' arithmetic, so
