@@ -44,22 +44,18 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 DFMA per clock per SM (recipe: 
 # absent entries report null.  Re-capture when a kernel changes.
 TRAFFIC_MB = {
     ("channel_128x128x129", 0, "xline"): 152.8 + 185.4,
-    ("channel_128x128x129", 0, "zrhs"): 251.8 + 76.5,
     ("channel_128x128x129", 0, "yfwd"): 228.3 + 128.6,
     ("channel_128x128x129", 0, "ybwd"): 84.6 + 135.3,
     ("channel_128x128x129", 0, "zsolve"): 93.4 + 8.9,
-    ("channel_128x128x129", 1, "zrhs"): 176.3 + 69.2,
     ("channel_128x128x129", 1, "xline"): 76.6 + 75.7,
     ("channel_128x128x129", 1, "yfwd"): 114.2 + 80.0,
     ("channel_128x128x129", 1, "ybwd"): 42.1 + 91.2,
     ("channel_128x128x129", 1, "zsolve"): 93.4 + 8.4,
-    ("channel_128x128x129", 2, "zrhs"): 251.7 + 75.8,
     ("channel_128x128x129", 2, "xline"): 153.2 + 193.1,
     ("channel_128x128x129", 2, "yfwd"): 228.3 + 128.8,
     ("channel_128x128x129", 2, "ybwd"): 84.7 + 134.8,
     ("channel_128x128x129", 2, "zsolve"): 93.4 + 8.8,
     ("channel_128x128x129_adjoint", 0, "adj_xline"): 380.7 + 130.9,
-    ("channel_128x128x129_adjoint", 0, "adj_zrhs"): 136.1 + 234.5,
     ("channel_128x128x129_adjoint", 0, "adj_zsolve"): 102.1 + 27.4,
 }
 

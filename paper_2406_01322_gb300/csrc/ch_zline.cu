@@ -126,63 +126,69 @@ __device__ __forceinline__ int line_K(const GridDev& g, int mx, int j) {
 }
 
 // ---- d/dz in Chebyshev coefficient space as warp-parallel suffix sums ----------------------
-// dst_n = (2 / c_n) sum_{p > n, p + n odd} p src_p.  For output parity q the sum runs over the
-// source class p = (1-q) + 2m, m >= i + q where n = q + 2i: a suffix sum over that class.
-// One warp per (component, output parity); tmp holds >= N/2 + 2 doubles for this warp.
-__device__ void dz_scan(const double2* src, double2* dst, int comp, int q, int N, double* tmp) {
+// dst_n = (2 / c_n) sum_{j >= 0} (n + 1 + 2j) src_{n+1+2j} (c_0 = 2, c_n = 1 otherwise; dst_N = 0):
+// within each parity class of n, a suffix sum of v_n = 2 (n + 1) src_{n+1}, halved at n = 0.
+// One warp per complex line: four 8-lane segments, one per (component, parity of n); a segment's
+// N/2 entries are cut into 8 contiguous chunks, each lane sums its chunk from the top (writing
+// the partial sums into dst) and a 3-step segmented shuffle scan supplies the chunk offsets.
+// The float64 pipe does one fused multiply-add and one addition per entry (weights 2(n+1) are
+// built from integer bits; the previous 32-lane layout spent about three times as many float64
+// instructions on the same sums, and the float64 rate is what bounds the z kernels).
+
+// a positive int as float64, assembled from its bits with integer instructions only
+__device__ __forceinline__ double int_as_f64(int m) {
+  const int e = 31 - __clz(m);
+  const unsigned long long frac =
+      ((unsigned long long)(unsigned)m << (52 - e)) & 0x000FFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(((unsigned long long)(1023 + e) << 52) | frac));
+}
+
+__device__ void dz_line(const double2* src, double2* dst, int N) {
+  const int lane = threadIdx.x & 31;
+  const int sl = lane & 7, comp = (lane >> 3) & 1, q = lane >> 4;
   const double* s = reinterpret_cast<const double*>(src) + comp;
   double* d = reinterpret_cast<double*>(dst) + comp;
-  const int lane = threadIdx.x & 31;
-  const int ps = 1 - q;
-  const int cnt = (N - ps) / 2 + 1;
-  const int E = (cnt + 31) / 32;
-  const int m0 = lane * E;
+  const int K = N / 2;                  // entries n = q + 2k, k = 0..K-1
+  const int E = (K + 7) >> 3;
+  const int k0 = sl * E;
   double acc = 0.0;
   for (int e = E - 1; e >= 0; --e) {
-    const int m = m0 + e;
-    if (m < cnt) {
-      const int p = ps + 2 * m;
-      acc = fma((double)p, s[2 * p], acc);
-      tmp[m] = acc;
+    const int k = k0 + e;
+    if (k < K) {
+      const int n = q + 2 * k;
+      acc = fma(int_as_f64(2 * n + 2), s[2 * n + 2], acc);
+      d[2 * n] = acc;
     }
   }
-  double v = acc;  // inclusive suffix scan of chunk totals over lanes
-  for (int off = 1; off < 32; off <<= 1) {
-    const double o = __shfl_down_sync(0xffffffffu, v, off);
-    if (lane + off < 32) v += o;
+  double v = acc;                       // inclusive suffix scan of the chunk sums in the segment
+  for (int off = 1; off < 8; off <<= 1) {
+    const double o = __shfl_down_sync(0xffffffffu, v, off, 8);
+    if (sl + off < 8) v += o;
   }
-  const double nxt = __shfl_down_sync(0xffffffffu, v, 1);
-  const double excl = (lane < 31) ? nxt : 0.0;
+  const double nxt = __shfl_down_sync(0xffffffffu, v, 1, 8);
+  const double excl = (sl < 7) ? nxt : 0.0;
   for (int e = 0; e < E; ++e) {
-    const int m = m0 + e;
-    if (m < cnt) tmp[m] += excl;
+    const int k = k0 + e;
+    if (k < K) d[2 * (q + 2 * k)] += excl;
   }
-  __syncwarp();
-  const int nout = (N - q) / 2 + 1;
-  for (int i = lane; i < nout; i += 32) {
-    const int n = q + 2 * i;
-    const int m = i + q;
-    const double T = (m < cnt) ? tmp[m] : 0.0;
-    d[2 * n] = (n == 0) ? T : 2.0 * T;
+  if (q == 0 && sl == 0) {
+    d[0] *= 0.5;
+    d[2 * N] = 0.0;
   }
   __syncwarp();
 }
 
-// several derivatives src[t] -> dst[t] (no aliasing): 4 scans per task spread over the warps
-__device__ void dz_tasks(double2* const* src, double2* const* dst, int ntask, int N, double* tmp) {
+// several derivatives src[t] -> dst[t] (no aliasing between a source and any destination), one
+// warp per line
+__device__ void dz_tasks(double2* const* src, double2* const* dst, int ntask, int N) {
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* mytmp = tmp + warp * (N / 2 + 2);
-  for (int s = warp; s < 4 * ntask; s += nw) {
-    const int t = s >> 2, comp = (s >> 1) & 1, q = s & 1;
-    dz_scan(src[t], dst[t], comp, q, N, mytmp);
-  }
+  for (int t = warp; t < ntask; t += nw) dz_line(src[t], dst[t], N);
 }
 
 struct ZSmem {
   double2* L;   // NLINES lines of Nz
   double2* FA;  // NBF * N
   double2* FB;
-  double* tmp;  // scan scratch, (ZT/32) * (N/2 + 2)
 };
 
 __device__ __forceinline__ ZSmem carve(double2* sm, int Nz, int N) {
@@ -190,7 +196,6 @@ __device__ __forceinline__ ZSmem carve(double2* sm, int Nz, int N) {
   z.L = sm;
   z.FA = sm + NLINES * Nz;
   z.FB = z.FA + NBF * N;
-  z.tmp = reinterpret_cast<double*>(z.FB + NBF * N);
   return z;
 }
 
@@ -387,7 +392,7 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
                        LN(z, 11, Nz)};
     double2* dst[6] = {LN(z, 7, Nz), LN(z, 8, Nz), LN(z, 9, Nz), LN(z, 13, Nz), LN(z, 14, Nz),
                        LN(z, 15, Nz)};
-    dz_tasks(src, dst, 6, N, z.tmp);   // DQ, DR, DC, D(w phi), DG, Dw
+    dz_tasks(src, dst, 6, N);   // DQ, DR, DC, D(w phi), DG, Dw
   }
   __syncthreads();
   const double rpe = 1.0 / g.pe;
@@ -397,7 +402,7 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   {
     double2* src[4] = {LN(z, 9, Nz), LN(z, 14, Nz), LN(z, 15, Nz), LN(z, 0, Nz)};
     double2* dst[4] = {LN(z, 3, Nz), LN(z, 5, Nz), LN(z, 1, Nz), LN(z, 13, Nz)};
-    dz_tasks(src, dst, is00 ? 4 : 3, N, z.tmp);   // D^2 C, D^2 G, D^2 w (, D Sxz on (0,0))
+    dz_tasks(src, dst, is00 ? 4 : 3, N);   // D^2 C, D^2 G, D^2 w (, D Sxz on (0,0))
   }
   __syncthreads();
   // h_omega, h_w, S_phi, theta^n = (D^2 - k^2) w^n; AB2; right-hand sides
@@ -942,7 +947,7 @@ __device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __res
   {
     double2* src[2] = {LN(z, 11, Nz), LN(z, 12, Nz)};
     double2* dst[2] = {LN(z, 13, Nz), LN(z, 14, Nz)};
-    dz_tasks(src, dst, 2, N, z.tmp);
+    dz_tasks(src, dst, 2, N);
   }
   __syncthreads();
   const double k2 = kx * kx + ky * ky;
@@ -1129,56 +1134,49 @@ __global__ void diag_final_kernel(GridDev g, int nblk, const double* __restrict_
 // Transposes are taken with respect to the real inner product <a, b> = sum Re(conj(a) b) over
 // the stored components, so multiplication by a complex constant c transposes to conj(c).
 
-// D^T in coefficient space as warp prefix sums: (D^T l)_p = 2 p sum_{n < p, n + p odd} l_n / c_n.
-// For output parity q the source class is n = (1-q) + 2m; output p = q + 2i collects m <= i - 1
-// (q = 0) or m <= i (q = 1).
-__device__ void dzT_scan(const double2* src, double2* dst, int comp, int q, int N, double* tmp) {
+// D^T in coefficient space: (D^T l)_p = 2 p sum_{n < p, n + p odd} l_n / c_n (c_0 = 2), so
+// (D^T l)_0 = 0 and, for p = n + 1, a prefix sum over the parity class of n of w_n = l_n / c_n,
+// times 2p.  Same warp layout as dz_line (four 8-lane segments, one per (component, parity of
+// n), contiguous chunks, segmented shuffle scan); two float64 additions and one multiplication
+// per entry.
+__device__ void dzT_line(const double2* src, double2* dst, int N) {
+  const int lane = threadIdx.x & 31;
+  const int sl = lane & 7, comp = (lane >> 3) & 1, r = lane >> 4;
   const double* s = reinterpret_cast<const double*>(src) + comp;
   double* d = reinterpret_cast<double*>(dst) + comp;
-  const int lane = threadIdx.x & 31;
-  const int ps = 1 - q;
-  const int cnt = (N - ps) / 2 + 1;
-  const int E = (cnt + 31) / 32;
-  const int m0 = lane * E;
+  const int K = N / 2;                  // sources n = r + 2k, k = 0..K-1, output p = n + 1
+  const int E = (K + 7) >> 3;
+  const int k0 = sl * E;
   double acc = 0.0;
   for (int e = 0; e < E; ++e) {
-    const int m = m0 + e;
-    if (m < cnt) {
-      const int n = ps + 2 * m;
-      acc += (n == 0 ? 0.5 : 1.0) * s[2 * n];
-      tmp[m] = acc;
+    const int k = k0 + e;
+    if (k < K) {
+      const int n = r + 2 * k;
+      acc += (n == 0) ? 0.5 * s[0] : s[2 * n];
+      d[2 * n + 2] = acc;
     }
   }
-  double v = acc;  // inclusive scan of chunk totals
-  for (int off = 1; off < 32; off <<= 1) {
-    const double o = __shfl_up_sync(0xffffffffu, v, off);
-    if (lane >= off) v += o;
+  double v = acc;                       // inclusive prefix scan of the chunk sums in the segment
+  for (int off = 1; off < 8; off <<= 1) {
+    const double o = __shfl_up_sync(0xffffffffu, v, off, 8);
+    if (sl >= off) v += o;
   }
-  const double prv = __shfl_up_sync(0xffffffffu, v, 1);
-  const double excl = (lane == 0) ? 0.0 : prv;
+  const double prv = __shfl_up_sync(0xffffffffu, v, 1, 8);
+  const double excl = (sl > 0) ? prv : 0.0;
   for (int e = 0; e < E; ++e) {
-    const int m = m0 + e;
-    if (m < cnt) tmp[m] += excl;
+    const int k = k0 + e;
+    if (k < K) {
+      const int p = r + 2 * k + 1;
+      d[2 * p] = int_as_f64(2 * p) * (d[2 * p] + excl);
+    }
   }
-  __syncwarp();
-  const int nout = (N - q) / 2 + 1;
-  for (int i = lane; i < nout; i += 32) {
-    const int pp = q + 2 * i;
-    int m = (q == 0) ? i - 1 : i;
-    if (m > cnt - 1) m = cnt - 1;
-    const double T = (m >= 0) ? tmp[m] : 0.0;
-    d[2 * pp] = 2.0 * pp * T;
-  }
+  if (r == 1 && sl == 0) d[0] = 0.0;
   __syncwarp();
 }
 
-__device__ void dzT_tasks(double2* const* src, double2* const* dst, int ntask, int N, double* tmp) {
+__device__ void dzT_tasks(double2* const* src, double2* const* dst, int ntask, int N) {
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* mytmp = tmp + warp * (N / 2 + 2);
-  for (int s = warp; s < 4 * ntask; s += nw) {
-    const int t = s >> 2, comp = (s >> 1) & 1, q = s & 1;
-    dzT_scan(src[t], dst[t], comp, q, N, mytmp);
-  }
+  for (int t = warp; t < ntask; t += nw) dzT_line(src[t], dst[t], N);
 }
 
 // transpose of tau_sweep_c for parity p of one complex line, in place (x: solution adjoint in,
@@ -1428,14 +1426,14 @@ __global__ void __launch_bounds__(ZT) adj_zrhs_kernel(GridDev g, const double2* 
                        LN(z, 1, Nz)};
     double2* dst[6] = {LN(z, 7, Nz), LN(z, 8, Nz), LN(z, 9, Nz), LN(z, 14, Nz), LN(z, 2, Nz),
                        LN(z, 3, Nz)};
-    dzT_tasks(src, dst, is00 ? 6 : 4, N, z.tmp);
+    dzT_tasks(src, dst, is00 ? 6 : 4, N);
   }
   __syncthreads();
   // second derivatives transposed: D^T(D^T hbar_w) -> 4, D^T(D^T hbar_phi) -> 5, D^T line14 -> 6
   {
     double2* src[3] = {LN(z, 8, Nz), LN(z, 9, Nz), LN(z, 14, Nz)};
     double2* dst[3] = {LN(z, 4, Nz), LN(z, 5, Nz), LN(z, 6, Nz)};
-    dzT_tasks(src, dst, 3, N, z.tmp);
+    dzT_tasks(src, dst, 3, N);
   }
   __syncthreads();
   // coefficient adjoints of the seven transformed lines c0..c6 into lines 0..6
@@ -1541,7 +1539,7 @@ __global__ void __launch_bounds__(ZT) adj_zbwd_kernel(GridDev g, const double2* 
   {
     double2* src[2] = {LN(z, 11, Nz), LN(z, 4, Nz)};
     double2* dst[2] = {LN(z, 12, Nz), LN(z, 13, Nz)};
-    dzT_tasks(src, dst, 2, N, z.tmp);
+    dzT_tasks(src, dst, 2, N);
   }
   __syncthreads();
   for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
@@ -1583,7 +1581,7 @@ __global__ void __launch_bounds__(ZT) objective_kernel(GridDev g, const double2*
   {
     double2* src[2] = {LN(z, 11, Nz), LN(z, 12, Nz)};
     double2* dst[2] = {LN(z, 13, Nz), LN(z, 14, Nz)};
-    dz_tasks(src, dst, 2, N, z.tmp);
+    dz_tasks(src, dst, 2, N);
   }
   __syncthreads();
   // lines 0 u, 1 v, 2 w, 3 D phi (coefficients)
@@ -1649,7 +1647,7 @@ __global__ void __launch_bounds__(ZT) objective_kernel(GridDev g, const double2*
   {
     double2* src[2] = {LN(z, 1, Nz), LN(z, 2, Nz)};
     double2* dst[2] = {LN(z, 9, Nz), LN(z, 13, Nz)};
-    dzT_tasks(src, dst, 2, N, z.tmp);
+    dzT_tasks(src, dst, 2, N);
   }
   __syncthreads();
   for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
@@ -1827,8 +1825,7 @@ __global__ void __launch_bounds__(ST) grouped_zsolve_kernel(const Member* __rest
 }  // namespace
 
 size_t zline_smem(const GridDev& g) {
-  return (size_t)(NLINES * g.nz + 2 * NBF * g.N) * sizeof(double2) +
-         (size_t)(ZT / 32) * (g.N / 2 + 2) * sizeof(double);
+  return (size_t)(NLINES * g.nz + 2 * NBF * g.N) * sizeof(double2);
 }
 
 size_t fac_doubles(const GridDev& g) { return ((size_t)13 * g.nz + 20) * g.NK; }
