@@ -44,23 +44,34 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 DFMA per clock per SM (recipe: 
 # absent entries report null.  Re-capture when a kernel changes.
 TRAFFIC_MB = {
     ("channel_128x128x129", 0, "xline"): 152.8 + 185.4,
+    ("channel_128x128x129", 0, "zrhs"): 251.8 + 81.0,
     ("channel_128x128x129", 0, "yfwd"): 228.3 + 128.6,
     ("channel_128x128x129", 0, "ybwd"): 84.6 + 135.3,
-    ("channel_128x128x129", 0, "zsolve"): 93.4 + 8.9,
+    ("channel_128x128x129", 1, "zrhs"): 176.3 + 75.0,
     ("channel_128x128x129", 1, "xline"): 76.6 + 75.7,
     ("channel_128x128x129", 1, "yfwd"): 114.2 + 80.0,
     ("channel_128x128x129", 1, "ybwd"): 42.1 + 91.2,
-    ("channel_128x128x129", 1, "zsolve"): 93.4 + 8.4,
+    ("channel_128x128x129", 2, "zrhs"): 251.7 + 81.0,
     ("channel_128x128x129", 2, "xline"): 153.2 + 193.1,
     ("channel_128x128x129", 2, "yfwd"): 228.3 + 128.8,
     ("channel_128x128x129", 2, "ybwd"): 84.7 + 134.8,
-    ("channel_128x128x129", 2, "zsolve"): 93.4 + 8.8,
+    # coefficient-space z kernels of the tensor-core method (the same kernels at any precision)
+    ("channel_128x128x129", 0, "zrhs_coef"): 251.7 + 72.7,
+    ("channel_128x128x129", 1, "zrhs_coef"): 251.7 + 72.7,
+    ("channel_128x128x129", 2, "zrhs_coef"): 251.7 + 72.7,
+    ("channel_128x128x129", 0, "zbwd_coef"): 83.9 + 77.6,
+    ("channel_128x128x129", 1, "zbwd_coef"): 83.9 + 77.6,
+    ("channel_128x128x129", 2, "zbwd_coef"): 83.9 + 77.6,
     ("channel_128x128x129_adjoint", 0, "adj_xline"): 380.7 + 130.9,
-    ("channel_128x128x129_adjoint", 0, "adj_zsolve"): 102.1 + 27.4,
+    ("channel_128x128x129_adjoint", 0, "adj_zrhs"): 135.1 + 223.7,
 }
 
 
-def traffic_bytes(workload, prec, kernel):
+def traffic_bytes(workload, prec, kernel, cheb="fft"):
+    """ncu DRAM bytes of one launch; the z kernels of the tensor-core method (coefficient-space
+    variants) have their own entries, "zrhs_coef" and "zbwd_coef"."""
+    if cheb == "tc" and kernel in ("zrhs", "zbwd"):
+        kernel += "_coef"
     v = TRAFFIC_MB.get((workload, prec, kernel))
     return None if v is None else v * 1e6
 
@@ -91,9 +102,10 @@ def fft_flops(n):
     return 5.0 * n * math.log2(n)
 
 
-def kernel_work(w, prec):
+def kernel_work(w, prec, cheb="fft"):
     """Algorithmic flops (an FMA counts 2) and bytes per launch of the step kernels (the six of
-    the FFT method and the two tensor-core Chebyshev transforms)."""
+    the FFT method and the two tensor-core Chebyshev transforms).  cheb = "tc": zrhs and zbwd are
+    the coefficient-space variants (no DCTs; float64 coefficients in and out)."""
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     Mx, Px, Py, N = nx // 2, 3 * nx // 2, 3 * ny // 2, nz - 1
     b = 8 if prec == 1 else 16
@@ -126,6 +138,11 @@ def kernel_work(w, prec):
     tcf_by = 9 * S * (b + 16)
     tcb_fl = 36 * 2.0 * (5 * rows) * (NT * nNt) * Kp
     tcb_by = 5 * S * (16 + b)
+    if cheb == "tc":
+        zrhs_fl = lines * (9 * 4 * nz + 150 * nz)
+        zrhs_by = S * (16 * 9 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)
+        zbwd_fl = lines * (2 * 4 * nz + 40 * nz)
+        zbwd_by = S * (16 * 3 + 16 * 2 + 16 * 3 + 16 * 5)
     return {"zrhs": (zrhs_fl, zrhs_by), "zsolve": (zsolve_fl, zsolve_by),
             "zbwd": (zbwd_fl, zbwd_by), "ybwd": (yb_fl, yb_by), "xline": (x_fl, x_by),
             "yfwd": (yf_fl, yf_by), "cheb_fwd": (tcf_fl, tcf_by), "cheb_bwd": (tcb_fl, tcb_by)}
@@ -765,7 +782,7 @@ def main():
 
     # ---- roofline of the dominant kernel
     names = list(binding.Grid.KERNELS)
-    work = kernel_work(w, prec)
+    work = kernel_work(w, prec, args.cheb)
     # the FFT method launches no tensor-core transforms: their timed entries are empty gaps
     active = [i for i, n in enumerate(names) if args.cheb == "tc" or not n.startswith("cheb")]
     if args.cheb != "tc":
@@ -788,12 +805,12 @@ def main():
         ach = fl / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": traffic_bytes(args.workload, prec, name), "kernel": name,
+                "traffic": traffic_bytes(args.workload, prec, name, args.cheb), "kernel": name,
                 "peak_kind": "float64 FMA pipe: 152 SMs x 2.07 GHz x 4 flop/clk (nominal)"}
     else:
         ach = by / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": traffic_bytes(args.workload, prec, name), "kernel": name,
+                "traffic": traffic_bytes(args.workload, prec, name, args.cheb), "kernel": name,
                 "peak_kind": f"{hbm_kind} copy bandwidth"}
     ksum = sum(kms[i] for i in active)
     roof["kernel_share"] = {names[i]: kms[i] / ksum for i in active}

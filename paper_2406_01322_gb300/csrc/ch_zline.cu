@@ -452,47 +452,81 @@ __global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T
 // Solve (D^2 - alpha) a = f (Gottlieb-Orszag rows n >= 2, homogeneous boundary row) for the
 // coefficients of parity p of one complex line, in place (x[n] = f_n on entry, a_n on exit).
 // Y, RD, Q point at (op, arr, n = 0, K) with stride NK per n; wb = 1 (Dirichlet) or n^2.
+// The table entries come from global memory (L2) and do not depend on the recurrence: each
+// sweep fetches them KP at a time into registers ahead of the dependent steps, so one memory
+// latency covers KP steps (the arithmetic and its order are unchanged).
+constexpr int KP = 8;
+
 __device__ void tau_sweep_c(double2* x, int p, int N, double alpha, bool neumann,
                             const double* t1, const double* t2, const double* t3,
-                            const double* Y, const double* RD, const double* Q, int NK,
-                            double rsq) {
+                            const double* __restrict__ Y, const double* __restrict__ RD,
+                            const double* __restrict__ Q, int NK, double rsq) {
   const int I = (N - p) / 2;
   double2 xn = make_double2(0.0, 0.0), fnp2 = make_double2(0.0, 0.0);
-  for (int i = I; i >= 1; --i) {
-    const int n = p + 2 * i;
-    const double2 fn = x[n];
-    const double2 fnm2 = x[n - 2];
-    const double a1 = t1[n], a2 = t2[n], a3 = t3[n];
-    const double U = -alpha * a3;
-    const double rd = RD[(size_t)n * NK];
-    double2 xi;
-    xi.x = fma(-U, xn.x, fma(a1, fnm2.x, fma(-a2, fn.x, a3 * fnp2.x))) * rd;
-    xi.y = fma(-U, xn.y, fma(a1, fnm2.y, fma(-a2, fn.y, a3 * fnp2.y))) * rd;
-    x[n] = xi;
-    fnp2 = fn;
-    xn = xi;
+  for (int i0 = I; i0 >= 1; i0 -= KP) {
+    double f[KP];
+#pragma unroll
+    for (int u = 0; u < KP; ++u)
+      f[u] = (i0 - u >= 1) ? __ldg(RD + (size_t)(p + 2 * (i0 - u)) * NK) : 0.0;
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      const int i = i0 - u;
+      if (i >= 1) {
+        const int n = p + 2 * i;
+        const double2 fn = x[n];
+        const double2 fnm2 = x[n - 2];
+        const double a1 = t1[n], a2 = t2[n], a3 = t3[n];
+        const double U = -alpha * a3;
+        const double rd = f[u];
+        double2 xi;
+        xi.x = fma(-U, xn.x, fma(a1, fnm2.x, fma(-a2, fn.x, a3 * fnp2.x))) * rd;
+        xi.y = fma(-U, xn.y, fma(a1, fnm2.y, fma(-a2, fn.y, a3 * fnp2.y))) * rd;
+        x[n] = xi;
+        fnp2 = fn;
+        xn = xi;
+      }
+    }
   }
   double2 P = make_double2(0.0, 0.0), sp = make_double2(0.0, 0.0);
-  for (int i = 1; i <= I; ++i) {
-    const int n = p + 2 * i;
-    const double y = Y[(size_t)n * NK];
-    const double2 xv = x[n];
-    P.x = fma(y, P.x, xv.x);
-    P.y = fma(y, P.y, xv.y);
-    x[n] = P;
-    const double wb = neumann ? (double)n * (double)n : 1.0;
-    sp.x = fma(wb, P.x, sp.x);
-    sp.y = fma(wb, P.y, sp.y);
+  for (int i0 = 1; i0 <= I; i0 += KP) {
+    double f[KP];
+#pragma unroll
+    for (int u = 0; u < KP; ++u)
+      f[u] = (i0 + u <= I) ? __ldg(Y + (size_t)(p + 2 * (i0 + u)) * NK) : 0.0;
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      const int i = i0 + u;
+      if (i <= I) {
+        const int n = p + 2 * i;
+        const double y = f[u];
+        const double2 xv = x[n];
+        P.x = fma(y, P.x, xv.x);
+        P.y = fma(y, P.y, xv.y);
+        x[n] = P;
+        const double wb = neumann ? int_as_f64(n * n) : 1.0;
+        sp.x = fma(wb, P.x, sp.x);
+        sp.y = fma(wb, P.y, sp.y);
+      }
+    }
   }
   const double2 a0 = make_double2(-sp.x * rsq, -sp.y * rsq);
   x[p] = a0;
-  for (int i = 1; i <= I; ++i) {
-    const int n = p + 2 * i;
-    const double q = Q[(size_t)n * NK];
-    double2 v = x[n];
-    v.x = fma(q, a0.x, v.x);
-    v.y = fma(q, a0.y, v.y);
-    x[n] = v;
+  for (int i0 = 1; i0 <= I; i0 += KP) {
+    double f[KP];
+#pragma unroll
+    for (int u = 0; u < KP; ++u)
+      f[u] = (i0 + u <= I) ? __ldg(Q + (size_t)(p + 2 * (i0 + u)) * NK) : 0.0;
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      const int i = i0 + u;
+      if (i <= I) {
+        const int n = p + 2 * i;
+        double2 v = x[n];
+        v.x = fma(f[u], a0.x, v.x);
+        v.y = fma(f[u], a0.y, v.y);
+        x[n] = v;
+      }
+    }
   }
 }
 
@@ -1186,21 +1220,30 @@ __device__ void dzT_tasks(double2* const* src, double2* const* dst, int ntask, i
 // row reads sum_n wb_n a_n = b (a_0 = (b - sum wb P) rsq; the forward sweep has b = 0).
 __device__ double2 tau_sweep_ct(double2* x, int p, int N, double alpha, bool neumann,
                                 const double* t1, const double* t2, const double* t3,
-                                const double* Y, const double* RD, const double* Q, int NK,
-                                double rsq) {
+                                const double* __restrict__ Y, const double* __restrict__ RD,
+                                const double* __restrict__ Q, int NK, double rsq) {
   const int I = (N - p) / 2;
-  // a_0 collects the Q-weighted adjoints of a_1..a_I
+  // a_0 collects the Q-weighted adjoints of a_1..a_I (table entries fetched KP at a time, as in
+  // tau_sweep_c)
   double2 a0 = x[p];
-  for (int i = 1; i <= I; ++i) {
-    const int n = p + 2 * i;
-    const double q = Q[(size_t)n * NK];
-    a0.x = fma(q, x[n].x, a0.x);
-    a0.y = fma(q, x[n].y, a0.y);
+  for (int i0 = 1; i0 <= I; i0 += KP) {
+    double f[KP];
+#pragma unroll
+    for (int u = 0; u < KP; ++u)
+      f[u] = (i0 + u <= I) ? __ldg(Q + (size_t)(p + 2 * (i0 + u)) * NK) : 0.0;
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      const int n = p + 2 * (i0 + u);
+      if (i0 + u <= I) {
+        a0.x = fma(f[u], x[n].x, a0.x);
+        a0.y = fma(f[u], x[n].y, a0.y);
+      }
+    }
   }
   // P_i adjoint = a_i adjoint - rsq beta_i a_0 adjoint
   for (int i = 1; i <= I; ++i) {
     const int n = p + 2 * i;
-    const double wb = neumann ? (double)n * (double)n : 1.0;
+    const double wb = neumann ? int_as_f64(n * n) : 1.0;
     const double c = -rsq * wb;
     double2 v = x[n];
     v.x = fma(c, a0.x, v.x);
@@ -1209,32 +1252,53 @@ __device__ double2 tau_sweep_ct(double2* x, int p, int N, double alpha, bool neu
   }
   // X adjoint: X_i = P_i + Y_{i+1} X_{i+1} (from the top)
   double2 xn = make_double2(0.0, 0.0);
-  for (int i = I; i >= 1; --i) {
-    const int n = p + 2 * i;
-    double2 v = x[n];
-    if (i < I) {
-      const double y = Y[(size_t)(n + 2) * NK];
-      v.x = fma(y, xn.x, v.x);
-      v.y = fma(y, xn.y, v.y);
+  for (int i0 = I; i0 >= 1; i0 -= KP) {
+    double f[KP];
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      const int i = i0 - u;
+      f[u] = (i >= 1 && i < I) ? __ldg(Y + (size_t)(p + 2 * i + 2) * NK) : 0.0;
     }
-    x[n] = v;
-    xn = v;
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      const int i = i0 - u;
+      if (i >= 1) {
+        const int n = p + 2 * i;
+        double2 v = x[n];
+        if (i < I) {
+          v.x = fma(f[u], xn.x, v.x);
+          v.y = fma(f[u], xn.y, v.y);
+        }
+        x[n] = v;
+        xn = v;
+      }
+    }
   }
   // g adjoint: g_1 = X_1 rd_1, g_i = (X_i - U_{i-1} g_{i-1}) rd_i
   double2 gp = make_double2(0.0, 0.0);
-  for (int i = 1; i <= I; ++i) {
-    const int n = p + 2 * i;
-    const double rd = RD[(size_t)n * NK];
-    double2 v = x[n];
-    if (i > 1) {
-      const double U = -alpha * t3[n - 2];
-      v.x = fma(-U, gp.x, v.x);
-      v.y = fma(-U, gp.y, v.y);
+  for (int i0 = 1; i0 <= I; i0 += KP) {
+    double f[KP];
+#pragma unroll
+    for (int u = 0; u < KP; ++u)
+      f[u] = (i0 + u <= I) ? __ldg(RD + (size_t)(p + 2 * (i0 + u)) * NK) : 0.0;
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      const int i = i0 + u;
+      if (i <= I) {
+        const int n = p + 2 * i;
+        const double rd = f[u];
+        double2 v = x[n];
+        if (i > 1) {
+          const double U = -alpha * t3[n - 2];
+          v.x = fma(-U, gp.x, v.x);
+          v.y = fma(-U, gp.y, v.y);
+        }
+        v.x *= rd;
+        v.y *= rd;
+        x[n] = v;
+        gp = v;
+      }
     }
-    v.x *= rd;
-    v.y *= rd;
-    x[n] = v;
-    gp = v;
   }
   // f adjoint from the stencil: f_{n_k} = t1[n_{k+1}] g_{k+1} - t2[n_k] g_k + t3[n_{k-1}] g_{k-1}
   double2 gprev = make_double2(0.0, 0.0);  // g_{k-1}
