@@ -110,6 +110,11 @@ __device__ __forceinline__ double fac_rsh(const GridDev& g, int p, int K) {
   return g.fac[(size_t)10 * g.nz * g.NK + (size_t)6 * g.NK + (size_t)p * g.NK + K];
 }
 
+// kx^2 + ky^2 with one explicit fused multiply-add: the same rounding in every kernel that
+// inlines it (the grouped ensemble kernels must reproduce the single-grid ones bit for bit, and an
+// implicit a*b + c*d leaves the contraction to the compiler, kernel by kernel)
+__device__ __forceinline__ double ksq(double kx, double ky) { return fma(kx, kx, ky * ky); }
+
 __device__ __forceinline__ void line_wavenumbers(const GridDev& g, int line, int& mx, int& j,
                                                  double& kx, double& ky) {
   mx = line / g.ny;
@@ -341,7 +346,7 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   }
   const ZSmem z = carve(zsm, Nz, N);
   const bool is00 = (mx == 0 && j == 0);
-  const double k2 = kx * kx + ky * ky;
+  const double k2 = ksq(kx, ky);
   for (int n = tid; n < Nz; n += blockDim.x) {
     LN(z, 10, Nz)[n] = st_om[off + n];
     LN(z, 11, Nz)[n] = st_w[off + n];
@@ -571,7 +576,7 @@ __device__ void tau_sweep_mixed(double2* __restrict__ x, int p, int N, double al
   st = pair_sum(st, pm);
   sb = pair_sum(sb, pm);
   const double m0 = minv[(size_t)(2 * p) * NK], m1 = minv[(size_t)(2 * p + 1) * NK];
-  const double2 a0 = make_double2(-(m0 * st.x + m1 * sb.x), -(m0 * st.y + m1 * sb.y));
+  const double2 a0 = make_double2(-fma(m0, st.x, m1 * sb.x), -fma(m0, st.y, m1 * sb.y));
   x[p] = a0;
   for (int i = 1; i <= I; ++i) {
     const int n = p + 2 * i;
@@ -601,7 +606,7 @@ __device__ void w_correct_mixed(const GridDev& g, double2* __restrict__ row, int
   rb = pair_sum(rb, pm);
   const double* mw = g.fac + fac_mixed_off(g, 4) + K;
   const double m0 = mw[(size_t)(2 * p) * g.NK], m1 = mw[(size_t)(2 * p + 1) * g.NK];
-  const double2 c = make_double2(-(m0 * rt.x + m1 * rb.x), -(m0 * rt.y + m1 * rb.y));
+  const double2 c = make_double2(-fma(m0, rt.x, m1 * rb.x), -fma(m0, rt.y, m1 * rb.y));
   for (int n = p; n <= N; n += 2) {
     const double h = oh[(size_t)n * g.NK];
     double2 v = row[n];
@@ -627,7 +632,7 @@ __device__ __forceinline__ void zsolve_body(const GridDev& g, double2* __restric
   double kx, ky;
   line_wavenumbers(g, line, mx, j, kx, ky);
   const int K = line_K(g, mx, j);
-  const double k2 = kx * kx + ky * ky;
+  const double k2 = ksq(kx, ky);
   const bool is00 = (mx == 0 && j == 0);
   const double* t1 = g.go1;
   const double* t2 = g.go2;
@@ -779,7 +784,7 @@ __device__ __forceinline__ void zsolve_tile_body(const GridDev& g, double2* __re
     line_wavenumbers(g, line, mx, j, kx, ky);
     K = line_K(g, mx, j);
   }
-  const double k2 = kx * kx + ky * ky;
+  const double k2 = ksq(kx, ky);
   const bool is00 = (mx == 0 && j == 0);
   const int ntile = min(TL, nlines - line0);
   const unsigned pm = 0x3u << (threadIdx.x & 30);  // the two lanes of this line
@@ -805,7 +810,7 @@ __device__ __forceinline__ void K_wavenumbers(const GridDev& g, int K, double& k
   const int mx = K / (h + 1), amy = K - mx * (h + 1);
   const double kx = 6.283185307179586476925 * mx / g.lx;
   const double ky = 6.283185307179586476925 * amy / g.ly;
-  k2 = kx * kx + ky * ky;
+  k2 = ksq(kx, ky);
 }
 
 // thread = (K, op, parity): elimination from the top coefficient down; the boundary row
@@ -984,7 +989,7 @@ __device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __res
     dz_tasks(src, dst, 2, N);
   }
   __syncthreads();
-  const double k2 = kx * kx + ky * ky;
+  const double k2 = ksq(kx, ky);
   const double rk2 = is00 ? 0.0 : 1.0 / k2;
   for (int n = tid; n < Nz; n += blockDim.x) {
     const double2 om = LN(z, 10, Nz)[n];
@@ -1343,7 +1348,7 @@ __global__ void __launch_bounds__(ST) adj_zsolve_kernel(GridDev g, const double2
   double kx, ky;
   line_wavenumbers(g, line, mx, j, kx, ky);
   const int K = line_K(g, mx, j);
-  const double k2 = kx * kx + ky * ky;
+  const double k2 = ksq(kx, ky);
   const bool is00 = (mx == 0 && j == 0);
   const bool nyq = (j == g.ny / 2);
   const double *t1 = g.go1, *t2 = g.go2, *t3 = g.go3;
@@ -1452,7 +1457,7 @@ __global__ void __launch_bounds__(ZT) adj_zrhs_kernel(GridDev g, const double2* 
   }
   const ZSmem z = carve(zsm, Nz, N);
   const bool is00 = (mx == 0 && j == 0);
-  const double k2 = kx * kx + ky * ky;
+  const double k2 = ksq(kx, ky);
   const double a = first ? 1.0 : 1.5, b = first ? 0.0 : -0.5;
   const double twoRe = 2.0 * g.re, cphi = g.pe / (g.ch * g.ch), rdt = 1.0 / g.dt, rpe = 1.0 / g.pe;
   // lines: 10 hbar_om, 11 hbar_w, 12 hbar_phi, 13 -2 beta Rb_theta (for (D^2 - k^2)^T)
@@ -1583,7 +1588,7 @@ __global__ void __launch_bounds__(ZT) adj_zbwd_kernel(GridDev g, const double2* 
   // the backward DCT matrix C[j][n] = cos(pi n j / N) is symmetric: its transpose is itself
   dct1_lines(z, 0, 4, Nz, N, pz, g.zcs, 1);
   dct1_lines(z, 4, 1, Nz, N, pz, g.zcs, 1);
-  const double k2 = kx * kx + ky * ky;
+  const double k2 = ksq(kx, ky);
   const double rk2 = is00 ? 0.0 : 1.0 / k2;
   for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
     const double2 ub = LN(z, 0, Nz)[n], vb = LN(z, 1, Nz)[n];
@@ -1633,7 +1638,7 @@ __global__ void __launch_bounds__(ZT) objective_kernel(GridDev g, const double2*
   __shared__ double red[ZT];
   const bool nyq = (j == g.ny / 2);
   const bool is00 = (mx == 0 && j == 0);
-  const double k2 = kx * kx + ky * ky;
+  const double k2 = ksq(kx, ky);
   const double rk2 = is00 ? 0.0 : 1.0 / k2;
   const double wts = (mx == 0 ? 1.0 : 2.0) * g.lx * g.ly;
   for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
