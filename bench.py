@@ -37,6 +37,11 @@ sys.path.insert(0, ROOT)
 METRIC = "time steps/s & Mpoints·step/s per grid; % HBM roofline; mixed vs FP64"
 UNIT = "Mpoints*step/s"
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 2 DFMA per clock per SM (recipe: 1.25 TF/s)
+# double-float x/y kernels run float64-equivalent arithmetic on the float32 pipe (128 lanes per SM
+# per clock): 11 float32 instructions per double-float addition, 7 per multiplication, 18 per
+# fused multiply-add (2 flops); with the float64 instruction mix of the transforms (10.2 M adds,
+# 5.4 M FMAs, 2.4 M multiplications per 128^3 zrhs) that is 9.67 instructions per flop
+DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 9.67 / 1e12
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, MB) of kernels of the
@@ -62,7 +67,11 @@ TRAFFIC_MB = {
     ("channel_128x128x129", 0, "zbwd_coef"): 83.9 + 77.6,
     ("channel_128x128x129", 1, "zbwd_coef"): 83.9 + 77.6,
     ("channel_128x128x129", 2, "zbwd_coef"): 83.9 + 77.6,
+    ("channel_128x128x129", 0, "zsolve"): 93.4 + 8.7,
+    ("channel_128x128x129", 1, "zsolve"): 93.4 + 8.7,
+    ("channel_128x128x129", 2, "zsolve"): 93.4 + 8.7,
     ("channel_128x128x129_adjoint", 0, "adj_xline"): 380.7 + 130.9,
+    ("channel_128x128x129_adjoint", 0, "adj_zsolve"): 102.4 + 28.2,
     ("channel_128x128x129_adjoint", 0, "adj_zrhs"): 135.1 + 223.7,
 }
 
@@ -792,11 +801,19 @@ def main():
     per_launch_ms = kms[k] / args.steps
     fl, by = work[name]
     hbm, hbm_kind = peaks()
-    # float64 kernels (all of precision 0, the z kernels of every precision) and the
-    # double-float kernels (float64-accurate work on the float32 pipe) are ALU-bound and are
-    # measured against the float64 peak; float32 kernels against HBM
+    # float64 kernels (all of precision 0, the z kernels of every precision) are ALU-bound and
+    # measured against the float64 peak, the double-float x/y kernels (float64-accurate work on
+    # the float32 pipe) against the double-float rate of the float32 pipe, float32 kernels
+    # against HBM
     fp64_like = (prec != 1) or name.startswith("z")
-    if name.startswith("cheb"):
+    if prec == 2 and not name.startswith("z") and not name.startswith("cheb"):
+        ach = fl / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / DF_PEAK_TFLOPS,
+                "traffic": traffic_bytes(args.workload, prec, name, args.cheb), "kernel": name,
+                "peak_kind": "double-float on the float32 pipe: 152 SMs x 128 lanes x 2.07 GHz / "
+                             "9.67 float32 instructions per float64-equivalent flop (nominal)"}
+    elif name.startswith("cheb"):
         tpk, tpk_kind = tensor_peak()
         ach = fl / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": tpk, "unit": "TFLOP/s",
