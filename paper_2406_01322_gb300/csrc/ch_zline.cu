@@ -698,7 +698,24 @@ __global__ void __launch_bounds__(ST) zsolve_kernel(GridDev g, double2* __restri
   zsolve_body(g, R, fs, nlines, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-constexpr int TL = 32;    // lines per tile-variant CTA (64 threads: one per (line, parity))
+constexpr int TL = 32;    // lines per tile-variant CTA (2 TL chains: one per (line, parity))
+constexpr int TLT = 256;  // threads of a tile-variant CTA: the first 2 TL solve, all move the tile
+
+// copy of count elements by the whole CTA with eight 16-byte loads in flight per thread (the
+// tile's moves between global and shared memory are latency-bound with few threads per SM)
+__device__ __forceinline__ void tile_copy(double2* __restrict__ dst,
+                                          const double2* __restrict__ src, int count) {
+  const int nt = blockDim.x;
+  int idx = threadIdx.x;
+  for (; idx + 7 * nt < count; idx += 8 * nt) {
+    double2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = src[idx + u * nt];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) dst[idx + u * nt] = v[u];
+  }
+  for (; idx < count; idx += nt) dst[idx] = src[idx];
+}
 
 // One of the three implicit problems of one line (row = its coefficients in shared memory,
 // parity p of the chain): 0 omega (or the mean flow), 1 the w influence problem, 2 phi.
@@ -779,7 +796,7 @@ __device__ __forceinline__ void zsolve_tile_body(const GridDev& g, double2* __re
   }
   int mx = 0, j = 0, K = 0;
   double kx = 0.0, ky = 0.0;
-  const bool valid = line < nlines;
+  const bool valid = tid < 2 * TL && line < nlines;
   if (valid) {
     line_wavenumbers(g, line, mx, j, kx, ky);
     K = line_K(g, mx, j);
@@ -790,16 +807,16 @@ __device__ __forceinline__ void zsolve_tile_body(const GridDev& g, double2* __re
   const unsigned pm = 0x3u << (threadIdx.x & 30);  // the two lanes of this line
   for (int prob = 0; prob < 3; ++prob) {
     double2* Rp = R + prob * fs + (size_t)line0 * Nz;
-    for (int idx = tid; idx < ntile * Nz; idx += blockDim.x) tile[idx] = Rp[idx];
+    tile_copy(tile, Rp, ntile * Nz);
     __syncthreads();
     if (valid) solve_tile_problem(g, tile + l * Nz, prob, p, K, k2, is00, t1, t2, t3, pm);
     __syncthreads();
-    for (int idx = tid; idx < ntile * Nz; idx += blockDim.x) Rp[idx] = tile[idx];
+    tile_copy(Rp, tile, ntile * Nz);
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(2 * TL) zsolve_tile_kernel(GridDev g, double2* __restrict__ R,
+__global__ void __launch_bounds__(TLT) zsolve_tile_kernel(GridDev g, double2* __restrict__ R,
                                                         long long fs, int nlines) {
   zsolve_tile_body(g, R, fs, nlines, blockIdx.x);
 }
@@ -1869,7 +1886,7 @@ __global__ void __launch_bounds__(ZT) grouped_zbwd_coef_kernel(const Member* __r
   }
 }
 
-__global__ void __launch_bounds__(2 * TL) grouped_zsolve_tile_kernel(const Member* __restrict__ mem,
+__global__ void __launch_bounds__(TLT) grouped_zsolve_tile_kernel(const Member* __restrict__ mem,
                                                                      const int* __restrict__ begin,
                                                                      int nmem) {
   const int total = begin[nmem];
@@ -2006,7 +2023,7 @@ cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* 
     if (zsolve_tile) {
       static int cur = 0;
       if ((e = ensure_smem(grouped_zsolve_tile_kernel, smem, &cur)) != cudaSuccess) return e;
-      grouped_zsolve_tile_kernel<<<grid, 2 * TL, smem, s>>>(mem, begin, nmem);
+      grouped_zsolve_tile_kernel<<<grid, TLT, smem, s>>>(mem, begin, nmem);
     } else {
       grouped_zsolve_kernel<<<grid, ST, 0, s>>>(mem, begin, nmem);
     }
@@ -2059,7 +2076,7 @@ int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile, int coef) {
   else if (stage == 1)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zsolve_tile ? (const void*)grouped_zsolve_tile_kernel
                                                                   : (const void*)grouped_zsolve_kernel,
-                                                  zsolve_tile ? 2 * TL : ST, zsolve_tile ? smem : 0);
+                                                  zsolve_tile ? TLT : ST, zsolve_tile ? smem : 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zkernel(2, prec), ZT, smem);
   cudaGetLastError();
@@ -2136,7 +2153,7 @@ cudaError_t launch_zsolve(const GridDev& g, double2* R, long long fs, cudaStream
     static int cur = 0;
     cudaError_t e = ensure_smem(zsolve_tile_kernel, tile, &cur);
     if (e != cudaSuccess) return e;
-    zsolve_tile_kernel<<<(nlines + TL - 1) / TL, 2 * TL, tile, s>>>(g, R, fs, nlines);
+    zsolve_tile_kernel<<<(nlines + TL - 1) / TL, TLT, tile, s>>>(g, R, fs, nlines);
   } else {
     // long lines: sweep in global memory (L1/L2), occupancy set by registers
     const int nthreads = 2 * nlines;
