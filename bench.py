@@ -67,9 +67,9 @@ TRAFFIC_MB = {
     ("channel_128x128x129", 0, "zbwd_coef"): 83.9 + 77.6,
     ("channel_128x128x129", 1, "zbwd_coef"): 83.9 + 77.6,
     ("channel_128x128x129", 2, "zbwd_coef"): 83.9 + 77.6,
-    ("channel_128x128x129", 0, "zsolve"): 93.4 + 8.7,
-    ("channel_128x128x129", 1, "zsolve"): 93.4 + 8.7,
-    ("channel_128x128x129", 2, "zsolve"): 93.4 + 8.7,
+    ("channel_128x128x129", 0, "zsolve"): 93.5 + 8.9,
+    ("channel_128x128x129", 1, "zsolve"): 93.5 + 8.9,
+    ("channel_128x128x129", 2, "zsolve"): 93.5 + 8.9,
     ("channel_128x128x129_adjoint", 0, "adj_xline"): 380.7 + 130.9,
     ("channel_128x128x129_adjoint", 0, "adj_zsolve"): 102.4 + 28.2,
     ("channel_128x128x129_adjoint", 0, "adj_zrhs"): 135.1 + 223.7,
