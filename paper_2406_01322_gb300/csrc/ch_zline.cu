@@ -1041,9 +1041,14 @@ __device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __res
     }
     return;
   }
-  for (int f0 = 0; f0 < NOUT; f0 += NBF) {
-    const int cnt = (NOUT - f0 < NBF) ? NOUT - f0 : NBF;
+  // as few rounds of at most NBF lines as possible, balanced (5 fields: 3 + 2, not 4 + 1, so no
+  // round runs a lone line through the barrier-separated FFT passes)
+  constexpr int NR = (NOUT + NBF - 1) / NBF;
+  int f0 = 0;
+  for (int r = 0; r < NR; ++r) {
+    const int cnt = (NOUT - f0 + (NR - r) - 1) / (NR - r);
     dct_backward_lines_store<T2>(z, f0, cnt, Nz, N, pz, g.zcs, bw, fs, off, f0);
+    f0 += cnt;
   }
 }
 
