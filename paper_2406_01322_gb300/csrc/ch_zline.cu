@@ -462,6 +462,9 @@ __global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T
 // latency covers KP steps (the arithmetic and its order are unchanged).
 constexpr int KP = 8;
 
+// XF: also fetch the chunk's right-hand sides x[n] ahead (x in global memory; the shared-memory
+// tile variant reads them in place)
+template <bool XF>
 __device__ void tau_sweep_c(double2* x, int p, int N, double alpha, bool neumann,
                             const double* t1, const double* t2, const double* t3,
                             const double* __restrict__ Y, const double* __restrict__ RD,
@@ -469,17 +472,23 @@ __device__ void tau_sweep_c(double2* x, int p, int N, double alpha, bool neumann
   const int I = (N - p) / 2;
   double2 xn = make_double2(0.0, 0.0), fnp2 = make_double2(0.0, 0.0);
   for (int i0 = I; i0 >= 1; i0 -= KP) {
+    // the chunk's table entries and right-hand sides (x[n] is read before its own step writes
+    // it and after no other), fetched ahead of the recurrence
     double f[KP];
+    double2 xv[KP + 1];
 #pragma unroll
     for (int u = 0; u < KP; ++u)
       f[u] = (i0 - u >= 1) ? __ldg(RD + (size_t)(p + 2 * (i0 - u)) * NK) : 0.0;
+#pragma unroll
+    for (int u = 0; u <= KP; ++u)
+      if (XF) xv[u] = (i0 - u >= 0) ? x[p + 2 * (i0 - u)] : make_double2(0.0, 0.0);
 #pragma unroll
     for (int u = 0; u < KP; ++u) {
       const int i = i0 - u;
       if (i >= 1) {
         const int n = p + 2 * i;
-        const double2 fn = x[n];
-        const double2 fnm2 = x[n - 2];
+        const double2 fn = XF ? xv[u] : x[n];
+        const double2 fnm2 = XF ? xv[u + 1] : x[n - 2];
         const double a1 = t1[n], a2 = t2[n], a3 = t3[n];
         const double U = -alpha * a3;
         const double rd = f[u];
@@ -495,16 +504,19 @@ __device__ void tau_sweep_c(double2* x, int p, int N, double alpha, bool neumann
   double2 P = make_double2(0.0, 0.0), sp = make_double2(0.0, 0.0);
   for (int i0 = 1; i0 <= I; i0 += KP) {
     double f[KP];
+    double2 xc[KP];
 #pragma unroll
-    for (int u = 0; u < KP; ++u)
+    for (int u = 0; u < KP; ++u) {
       f[u] = (i0 + u <= I) ? __ldg(Y + (size_t)(p + 2 * (i0 + u)) * NK) : 0.0;
+      if (XF) xc[u] = (i0 + u <= I) ? x[p + 2 * (i0 + u)] : make_double2(0.0, 0.0);
+    }
 #pragma unroll
     for (int u = 0; u < KP; ++u) {
       const int i = i0 + u;
       if (i <= I) {
         const int n = p + 2 * i;
         const double y = f[u];
-        const double2 xv = x[n];
+        const double2 xv = XF ? xc[u] : x[n];
         P.x = fma(y, P.x, xv.x);
         P.y = fma(y, P.y, xv.y);
         x[n] = P;
@@ -649,7 +661,7 @@ __device__ __forceinline__ void zsolve_body(const GridDev& g, double2* __restric
                     fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK,
                     g.fac + fac_mixed_off(g, 0) + K, pm);
   else
-    tau_sweep_c(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K),
+    tau_sweep_c<true>(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K),
                 fac_ptr(g, oo, 1, K), fac_ptr(g, oo, 2, K), g.NK, fac_rsq(g, oo, p, K));
   // w: influence problem (theta, w) with w = w' = 0 at both walls, or (free-slip) theta and w
   // each with Dirichlet rows
@@ -657,9 +669,9 @@ __device__ __forceinline__ void zsolve_body(const GridDev& g, double2* __restric
   if (is00) {
     for (int n = p; n <= N; n += 2) row[n] = make_double2(0.0, 0.0);
   } else {
-    tau_sweep_c(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
+    tau_sweep_c<true>(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
                 fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
-    tau_sweep_c(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K), fac_ptr(g, 1, 1, K),
+    tau_sweep_c<true>(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K), fac_ptr(g, 1, 1, K),
                 fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
   }
   if (!is00 && mixed) {
@@ -689,7 +701,7 @@ __device__ __forceinline__ void zsolve_body(const GridDev& g, double2* __restric
   row = R + 2 * fs + (size_t)line * Nz;
   const double a = k2 + g.lam;
   for (int rep = 0; rep < 2; ++rep)
-    tau_sweep_c(row, p, N, a, true, t1, t2, t3, fac_ptr(g, 2, 0, K), fac_ptr(g, 2, 1, K),
+    tau_sweep_c<true>(row, p, N, a, true, t1, t2, t3, fac_ptr(g, 2, 0, K), fac_ptr(g, 2, 1, K),
                 fac_ptr(g, 2, 2, K), g.NK, fac_rsq(g, 2, p, K));
 }
 
@@ -733,15 +745,15 @@ __device__ __forceinline__ void solve_tile_problem(const GridDev& g, double2* __
                       fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK,
                       g.fac + fac_mixed_off(g, 0) + K, pm);
     else
-      tau_sweep_c(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K),
+      tau_sweep_c<false>(row, p, N, k2 + g.beta, fsl, t1, t2, t3, fac_ptr(g, oo, 0, K),
                   fac_ptr(g, oo, 1, K), fac_ptr(g, oo, 2, K), g.NK, fac_rsq(g, oo, p, K));
   } else if (prob == 1) {
     if (is00) {
       for (int n = p; n <= N; n += 2) row[n] = make_double2(0.0, 0.0);
     } else {
-      tau_sweep_c(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
+      tau_sweep_c<false>(row, p, N, k2 + g.beta, false, t1, t2, t3, fac_ptr(g, 0, 0, K),
                   fac_ptr(g, 0, 1, K), fac_ptr(g, 0, 2, K), g.NK, fac_rsq(g, 0, p, K));
-      tau_sweep_c(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K), fac_ptr(g, 1, 1, K),
+      tau_sweep_c<false>(row, p, N, k2, false, t1, t2, t3, fac_ptr(g, 1, 0, K), fac_ptr(g, 1, 1, K),
                   fac_ptr(g, 1, 2, K), g.NK, fac_rsq(g, 1, p, K));
     }
     if (!is00 && g.bc >= 2) {
@@ -769,7 +781,7 @@ __device__ __forceinline__ void solve_tile_problem(const GridDev& g, double2* __
   } else {
     const double a = k2 + g.lam;
     for (int rep = 0; rep < 2; ++rep)
-      tau_sweep_c(row, p, N, a, true, t1, t2, t3, fac_ptr(g, 2, 0, K), fac_ptr(g, 2, 1, K),
+      tau_sweep_c<false>(row, p, N, a, true, t1, t2, t3, fac_ptr(g, 2, 0, K), fac_ptr(g, 2, 1, K),
                   fac_ptr(g, 2, 2, K), g.NK, fac_rsq(g, 2, p, K));
   }
 }
@@ -1281,17 +1293,19 @@ __device__ double2 tau_sweep_ct(double2* x, int p, int N, double alpha, bool neu
   double2 xn = make_double2(0.0, 0.0);
   for (int i0 = I; i0 >= 1; i0 -= KP) {
     double f[KP];
+    double2 xc[KP];
 #pragma unroll
     for (int u = 0; u < KP; ++u) {
       const int i = i0 - u;
       f[u] = (i >= 1 && i < I) ? __ldg(Y + (size_t)(p + 2 * i + 2) * NK) : 0.0;
+      xc[u] = (i >= 1) ? x[p + 2 * i] : make_double2(0.0, 0.0);
     }
 #pragma unroll
     for (int u = 0; u < KP; ++u) {
       const int i = i0 - u;
       if (i >= 1) {
         const int n = p + 2 * i;
-        double2 v = x[n];
+        double2 v = xc[u];
         if (i < I) {
           v.x = fma(f[u], xn.x, v.x);
           v.y = fma(f[u], xn.y, v.y);
@@ -1305,16 +1319,19 @@ __device__ double2 tau_sweep_ct(double2* x, int p, int N, double alpha, bool neu
   double2 gp = make_double2(0.0, 0.0);
   for (int i0 = 1; i0 <= I; i0 += KP) {
     double f[KP];
+    double2 xc[KP];
 #pragma unroll
-    for (int u = 0; u < KP; ++u)
+    for (int u = 0; u < KP; ++u) {
       f[u] = (i0 + u <= I) ? __ldg(RD + (size_t)(p + 2 * (i0 + u)) * NK) : 0.0;
+      xc[u] = (i0 + u <= I) ? x[p + 2 * (i0 + u)] : make_double2(0.0, 0.0);
+    }
 #pragma unroll
     for (int u = 0; u < KP; ++u) {
       const int i = i0 + u;
       if (i <= I) {
         const int n = p + 2 * i;
         const double rd = f[u];
-        double2 v = x[n];
+        double2 v = xc[u];
         if (i > 1) {
           const double U = -alpha * t3[n - 2];
           v.x = fma(-U, gp.x, v.x);
