@@ -47,7 +47,7 @@ extern "C" {
 #define CH_ERR_ALLOC (-3)    /* allocator callback or cudaMalloc returned NULL / failed   */
 #define CH_ERR_CUDA (-4)     /* a CUDA runtime call or kernel launch failed               */
 #define CH_ERR_DIVERGED (-5) /* diagnostics found NaN/Inf                                 */
-#define CH_ERR_TIMEOUT (-6)  /* reserved: bounded device-side wait gave up                */
+#define CH_ERR_TIMEOUT (-6)  /* a bounded device-side wait gave up                        */
 #define CH_ERR_STATE (-7)    /* call out of order, e.g. ch_step before ch_set_fields      */
 
 #define CH_PREC_FP64 0  /* every stage in float64                                         */
@@ -155,6 +155,14 @@ int ch_chebyshev_lines(ch_grid* g, int dir, const double* in, double* out, int n
  * wait of the tensor-core kernels gave up since the last check (its outputs are then invalid),
  * else CH_OK.  ch_diagnostics reports the same condition. */
 int ch_device_status(ch_grid* g);
+
+/* Test of the failure path of the bounded device waits (not in the paper; library
+ * infrastructure): one thread waits, with the tensor-core transform's wait helper, for an
+ * mbarrier phase that nothing completes.  The wait gives up after its bound (about one second),
+ * records the fact in device memory and the kernel returns: expected result CH_ERR_TIMEOUT, with
+ * the CUDA context still usable (no fault, trap or hang).  Synchronous, on the legacy default
+ * stream; CH_ERR_ALLOC / CH_ERR_CUDA if the test itself cannot run, CH_OK if the wait completed. */
+int ch_selftest_bounded_wait(void);
 
 /* As ch_step, but launched without the graph and bracketed by CUDA events on the stream: on
  * return (the stream is synchronised) kernel_ms[0..CH_STEP_KERNELS-1] hold the summed device

@@ -101,6 +101,7 @@ _SIGS = {
                                               ctypes.POINTER(ctypes.c_double)]),
     "ch_ensemble_autotune": (ctypes.c_int, [_P, ctypes.c_int]),
     "ch_ensemble_tuning": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
+    "ch_selftest_bounded_wait": (ctypes.c_int, []),
     "ch_ensemble_set_chebyshev": (ctypes.c_int, [_P, ctypes.c_int]),
     "ch_ensemble_get_chebyshev": (ctypes.c_int, [_P]),
     "ch_ensemble_destroy": (None, [_P]),

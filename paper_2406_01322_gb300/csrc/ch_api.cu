@@ -835,6 +835,24 @@ int ch_chebyshev_lines(ch_grid* G, int dir, const double* in, double* out, int n
   return CH_OK;
 }
 
+int ch_selftest_bounded_wait(void) {
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return CH_ERR_ALLOC;
+  }
+  int h = 0, st = CH_OK;
+  if (cudaMemset(d, 0, sizeof(int)) != cudaSuccess || chf::launch_wait_selftest(d, 0) != cudaSuccess ||
+      cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    st = CH_ERR_CUDA;
+  } else if (h) {
+    st = CH_ERR_TIMEOUT;
+  }
+  cudaFree(d);
+  return st;
+}
+
 int ch_device_status(ch_grid* G) {
   if (!G) return CH_ERR_ARG;
   CK(cudaStreamSynchronize(G->stream));

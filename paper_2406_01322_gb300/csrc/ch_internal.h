@@ -206,5 +206,7 @@ cudaError_t cheb_tc_prepare(int NT);
 cudaError_t launch_cheb_tc(int tin, int tout, const void* in, long long fsi, void* out,
                            long long fso, int nf, int nlines, int Nz, const ChebTc& t, int* err,
                            cudaStream_t s);
+// one bounded mbarrier wait that runs out on purpose (sets *err |= 1 after the wait bound)
+cudaError_t launch_wait_selftest(int* err, cudaStream_t s);
 
 }  // namespace chf

@@ -731,4 +731,22 @@ cudaError_t launch_cheb_tc(int tin, int tout, const void* in, long long fsi, voi
   return cudaErrorInvalidValue;
 }
 
+// Failure path of the bounded waits, exercised on purpose: one thread waits, with the same
+// helper as the transform's pipeline, for phase 0 of an mbarrier that nothing arrives at.  The
+// wait gives up after kWaitNs, the thread records it in *err and the kernel returns; no TMEM, no
+// asynchronous copy is involved, so nothing else is left in flight.
+__global__ void __launch_bounds__(32) wait_selftest_kernel(int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = su32(&bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(b, 0)) atomicOr(err, 1);
+}
+
+cudaError_t launch_wait_selftest(int* err, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(err);
+  return cudaGetLastError();
+}
+
 }  // namespace chf

@@ -1,6 +1,7 @@
 """Failure detection without faulting the GPU: a state carrying NaN is reported as diverged, an
 allocator that fails part-way through ch_init_grid surfaces as CH_ERR_ALLOC with everything
-already obtained released, and invalid arguments are rejected on the host."""
+already obtained released, invalid arguments are rejected on the host, and a bounded device wait
+that runs out returns CH_ERR_TIMEOUT with the context intact."""
 import math
 
 import numpy as np
@@ -74,3 +75,16 @@ def test_invalid_arguments_are_rejected_on_the_host(binding):
         with pytest.raises(binding.ChError) as e:
             binding.Grid(*n)
         assert e.value.code == -2, n
+
+
+def test_bounded_device_wait_runs_out_and_reports_timeout(binding):
+    """A wait on an mbarrier phase that nothing completes gives up after its bound (about one
+    second), the kernel records it and returns: CH_ERR_TIMEOUT, and the context stays usable (a
+    step runs and matches a fresh grid afterwards)."""
+    assert binding.lib().ch_selftest_bounded_wait() == -6
+    f = [torch.from_numpy(a) for a in inputs.initial_fields(16, 16, 17, 150.0, 0.05, 1, 0.4, 3)]
+    g = binding.Grid(16, 16, 17)
+    g.set_fields(*f)
+    g.step(2)
+    d = g.diagnostics()
+    assert d["step"] == 2 and not d["nan"]
