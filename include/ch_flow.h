@@ -292,7 +292,7 @@ int ch_ensemble_step_timed(ch_ensemble* e, int nsteps, double* stage_ms, double*
 int ch_ensemble_autotune(ch_ensemble* e, int reps);
 /* Chebyshev method of the ensemble step (CH_CHEB_FFT default, CH_CHEB_TC): with CH_CHEB_TC the
  * grouped zrhs and zbwd stages read and write float64 Chebyshev coefficients and each member's
- * z transforms run on the tensor cores (ch_set_chebyshev; the transform of Sec. 3.2.1), one launch per
+ * z transforms (Sec. 3.2.1) run on the tensor cores as in ch_set_chebyshev, one launch per
  * member before zrhs and one after zbwd, inside the step's graph and timed with stages 0 and 2
  * of ch_ensemble_step_timed.  Sets every member's own method too (a later ch_set_chebyshev on a
  * member does not change the ensemble's).  The tuning is kept per method: switching takes the
