@@ -235,13 +235,18 @@ class Channel:
 
     def solve_line(self, j, m, r_om, r_th, r_psi):
         """Solve the implicit problems of one (my, mx) line; returns (omega, w, phi)^{n+1}."""
-        k2 = self.k2[j, m]
+        return self.solve_k2(self.k2[j, m], j == 0 and m == 0, r_om, r_th, r_psi)
+
+    def solve_k2(self, k2, mean, r_om, r_th, r_psi):
+        """Solve the implicit problems of the lines whose right-hand sides are the columns of
+        r_om, r_th, r_psi ((Nz,) or (Nz, L)); all of them have the wavenumber magnitude k2, so
+        they share the three operators (one factorisation each).  mean: the kx = ky = 0 line."""
         top, bottom = WALLS[self.p.bc]
         # omega_z and the mean flow: Dirichlet at a no-slip wall, Neumann at a free-slip wall
         # (du/dz = dv/dz = 0)
         kind = {"no-slip": "dirichlet", "free-slip": "neumann"}
         om = cheb.solve_helmholtz(r_om, k2 + self.beta, (kind[top], kind[bottom]))
-        if j == 0 and m == 0:
+        if mean:
             w = np.zeros_like(r_th)
         else:
             _, w = cheb.solve_coupled_w(r_th, k2, self.beta, (top, bottom))
@@ -251,6 +256,24 @@ class Channel:
 
     def all_lines(self):
         return [(j, m) for j in range(self.p.ny) for m in range(self.Mx) if j != self.p.ny // 2]
+
+    def solve_lines(self, lines, r_om, r_th, r_psi):
+        """Solve the listed (j, m) lines, grouped by equal k2 (the mean line on its own);
+        returns {(j, m): (omega, w, phi)}."""
+        groups = {}
+        for (j, m) in lines:
+            key = "mean" if (j == 0 and m == 0) else float(self.k2[j, m])
+            groups.setdefault(key, []).append((j, m))
+        out = {}
+        for key, ls in groups.items():
+            js = np.array([j for j, _ in ls])
+            ms = np.array([m for _, m in ls])
+            k2 = 0.0 if key == "mean" else key
+            om, w, ph = self.solve_k2(k2, key == "mean", r_om[:, js, ms], r_th[:, js, ms],
+                                      r_psi[:, js, ms])
+            for i, jm in enumerate(ls):
+                out[jm] = (om[:, i], w[:, i], ph[:, i])
+        return out
 
     def step(self, lines=None):
         """One time step n -> n+1 (Sec. 2.2 i)-v)).
@@ -264,9 +287,7 @@ class Channel:
         H = tuple(1.5 * a - 0.5 * b for a, b in zip(h, prev))
         r_om, r_th, r_psi = self.rhs(H)
         todo = self.all_lines() if lines is None else lines
-        out = {}
-        for (j, m) in todo:
-            out[(j, m)] = self.solve_line(j, m, r_om[:, j, m], r_th[:, j, m], r_psi[:, j, m])
+        out = self.solve_lines(todo, r_om, r_th, r_psi)
         if lines is not None:
             return out
         om = np.zeros_like(self.omega)

@@ -10,6 +10,8 @@ the definitions, in FP64.
 Notation: N = Nz - 1 is the polynomial degree, z_j = cos(pi j / N) for j = 0..N (j = 0 is the top
 wall z = +1), c_0 = 2 and c_n = 1 otherwise, cbar_0 = cbar_N = 2 and cbar_n = 1 otherwise.
 """
+import functools
+
 import numpy as np
 
 
@@ -80,6 +82,7 @@ def clenshaw_curtis_weights(N):
     return integral_weights(N) @ forward_matrix(N)
 
 
+@functools.lru_cache(maxsize=16)
 def go_matrix(N):
     """Gottlieb-Orszag second-integral matrix G, rows n = 2..N (rows 0, 1 are zero).
 
@@ -96,6 +99,7 @@ def go_matrix(N):
             G[n, n] = -1.0 / (2.0 * (n * n - 1))
         if n + 2 <= N - 2:
             G[n, n + 2] = 1.0 / (4.0 * n * (n + 1))
+    G.setflags(write=False)          # cached: shared by every caller, never modified
     return G
 
 
@@ -134,7 +138,9 @@ def helmholtz_matrix(N, alpha, bc):
 
 
 def helmholtz_rhs(N, f, g_plus=0.0, g_minus=0.0):
-    """Right-hand side matching ``helmholtz_matrix``: BC values, then (G f)_n for n >= 2."""
+    """Right-hand side matching ``helmholtz_matrix``: BC values, then (G f)_n for n >= 2.
+
+    f may hold several right-hand sides as columns (shape (N+1, L))."""
     r = go_matrix(N) @ f
     r = r.astype(np.result_type(r, g_plus, g_minus))
     r[0] = g_plus
@@ -143,7 +149,9 @@ def helmholtz_rhs(N, f, g_plus=0.0, g_minus=0.0):
 
 
 def solve_helmholtz(f, alpha, bc, g_plus=0.0, g_minus=0.0):
-    """Solve (D^2 - alpha) a = f (tau rows 0..N-2) with two boundary conditions; dense LU."""
+    """Solve (D^2 - alpha) a = f (tau rows 0..N-2) with two boundary conditions; dense LU.
+
+    f: (N+1,) or (N+1, L) (L right-hand sides sharing alpha, one factorisation)."""
     N = len(f) - 1
     M = helmholtz_matrix(N, alpha, bc)
     r = helmholtz_rhs(N, f, g_plus, g_minus)
@@ -179,13 +187,14 @@ def coupled_w_matrix(N, k2, beta, walls="no-slip"):
 
 
 def solve_coupled_w(r, k2, beta, walls="no-slip"):
-    """Solve the (theta, w) problem of ``coupled_w_matrix`` for one right-hand side r.
+    """Solve the (theta, w) problem of ``coupled_w_matrix`` for a right-hand side r of shape
+    (N+1,) or for the columns of r (N+1, L) (one factorisation).
 
     Returns (theta, w)."""
     N = len(r) - 1
     n1 = N + 1
     M = coupled_w_matrix(N, k2, beta, walls)
-    rhs = np.zeros(2 * n1, dtype=np.result_type(r, float))
+    rhs = np.zeros((2 * n1,) + r.shape[1:], dtype=np.result_type(r, float))
     rhs[0:n1] = go_matrix(N) @ r
     rhs[0:2] = 0.0
     x = _solve_real(M, rhs)
@@ -193,8 +202,12 @@ def solve_coupled_w(r, k2, beta, walls="no-slip"):
 
 
 def _solve_real(M, r):
-    """Dense LU solve of a real matrix against a real or complex right-hand side."""
+    """Dense LU solve (numpy.linalg.solve: LAPACK gesv, partial pivoting) of a real matrix
+    against a real or complex right-hand side r of shape (n,) or (n, L): the real and imaginary
+    parts are solved as columns of one real system."""
     if np.iscomplexobj(r):
-        sol = np.linalg.solve(M, np.stack([r.real, r.imag], axis=-1))
-        return sol[..., 0] + 1j * sol[..., 1]
+        cols = r.reshape(r.shape[0], -1)
+        L = cols.shape[1]
+        sol = np.linalg.solve(M, np.concatenate([cols.real, cols.imag], axis=1))
+        return (sol[:, :L] + 1j * sol[:, L:]).reshape(r.shape)
     return np.linalg.solve(M, r)

@@ -181,3 +181,19 @@ def test_mixed_wall_pair_manufactured(N):
         # one w'' row (entries up to N^4 / 3): rounding grows like N^2 as for free-slip walls
         tol = 1e-13 * max(1, N * N / 64)
         assert np.max(np.abs(w_got - ww)) < tol * np.max(np.abs(ww)), walls
+
+
+def test_lines_sharing_k2_solve_as_one_factorisation():
+    """The oracle's step solves every line with the same k^2 against one matrix (the columns of
+    one system); each column must equal the single-line solve of that line."""
+    from oracle.channel import Channel, Params
+    c = Channel(Params(nx=8, ny=8, nz=17, dt=1e-3))
+    rng = np.random.default_rng(5)
+    shape = c.omega.shape
+    r = [rng.standard_normal(shape) + 1j * rng.standard_normal(shape) for _ in range(3)]
+    lines = [(1, 1), (7, 1), (0, 2), (1, 0), (7, 0), (0, 0), (3, 2)]   # (1,1)/(7,1) share k^2
+    got = c.solve_lines(lines, *r)
+    for (j, m) in lines:
+        one = c.solve_line(j, m, r[0][:, j, m], r[1][:, j, m], r[2][:, j, m])
+        for a, b in zip(got[(j, m)], one):
+            assert np.max(np.abs(a - b)) <= 1e-13 * max(np.max(np.abs(b)), 1e-300)
