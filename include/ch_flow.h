@@ -157,12 +157,16 @@ int ch_chebyshev_lines(ch_grid* g, int dir, const double* in, double* out, int n
 int ch_device_status(ch_grid* g);
 
 /* Test of the failure path of the bounded device waits (not in the paper; library
- * infrastructure): one thread waits, with the tensor-core transform's wait helper, for an
- * mbarrier phase that nothing completes.  The wait gives up after its bound (about one second),
- * records the fact in device memory and the kernel returns: expected result CH_ERR_TIMEOUT, with
- * the CUDA context still usable (no fault, trap or hang).  Synchronous, on the legacy default
- * stream; CH_ERR_ALLOC / CH_ERR_CUDA if the test itself cannot run, CH_OK if the wait completed. */
-int ch_selftest_bounded_wait(void);
+ * infrastructure): one thread runs a loop of nwaits (>= 1) waits, with the tensor-core
+ * transform's wait helper, on mbarrier phases that nothing completes.  The first wait gives up
+ * after its bound (about one second); every later wait of the loop returns at once (the helper
+ * short-circuits after a failure), so the kernel ends after about one bound whatever nwaits is.
+ * The failure is recorded in device memory and the kernel returns: expected result
+ * CH_ERR_TIMEOUT, with the CUDA context still usable (no fault, trap or hang), and *spun (if not
+ * NULL) = the number of waits that actually waited, 1.  Synchronous, on the legacy default
+ * stream; CH_ERR_ARG for nwaits < 1, CH_ERR_ALLOC / CH_ERR_CUDA if the test itself cannot run,
+ * CH_OK if the waits completed. */
+int ch_selftest_bounded_wait(int nwaits, int* spun);
 
 /* As ch_step, but launched without the graph and bracketed by CUDA events on the stream: on
  * return (the stream is synchronised) kernel_ms[0..CH_STEP_KERNELS-1] hold the summed device
@@ -305,19 +309,22 @@ int ch_ensemble_tuning(const ch_ensemble* e, char* buf, size_t n);
 void ch_ensemble_destroy(ch_ensemble* e);
 
 /* Allocation-free variant of ch_transform_forward, for callers that must not allocate device
- * memory when they call it: code running while a stream is being captured into a CUDA graph
- * (allocation is not allowed inside a capture), plug-ins whose host application's memory pool
- * owns the GPU, or fixed-latency loops that must stay out of the allocator.  (The paper has no
+ * memory when they call it: plug-ins whose host application's memory pool already owns the GPU's
+ * memory, or fixed-latency loops that must stay out of the allocator.  (The paper has no
  * counterpart; it is a service of this library.)
- * Same result as ch_transform_forward for a grid of nx, ny, nz (same size rules): phys is a
- * device (nz,ny,nx) float64 field, spec receives device complex float64 coefficients in the
- * layout above.  No handle, no cudaMalloc/cudaFree: the working memory is one static device
- * array of ch_noalloc_scratch_bytes() (64 MiB) that every GPU loading this library keeps until
- * the process exits; grids whose two (nx/2, ny, nz) complex work fields plus twiddles do not fit
- * in it are rejected with CH_ERR_SIZE.  The first call on a device (with that device current)
- * looks up the array's address - make it before any stream capture.  All calls share the array
- * and leave their data in it; calls that overlap on the GPU (other streams or host threads)
- * race.  Enqueued on `stream` (a cudaStream_t, NULL = default stream); returns once enqueued. */
+ * The same transform as ch_transform_forward for a grid of nx, ny, nz (same size rules and the
+ * same radix schedules), equal to it to rounding (its twiddles are computed on the device
+ * instead of in extended precision on the host: about 1e-15 relative): phys is a device
+ * (nz,ny,nx) float64 field, spec receives device complex float64 coefficients in the layout
+ * above.  No handle, no cudaMalloc/cudaFree: the working memory is one static device array of
+ * ch_noalloc_scratch_bytes() (64 MiB) that every GPU loading this library keeps until the
+ * process exits; grids whose two (nx/2, ny, nz) complex work fields plus twiddles do not fit in
+ * it are rejected with CH_ERR_SIZE.  Set-up done by the calls themselves: the first call on a
+ * device (with that device current) looks up the array's address, and the first call for a
+ * grid larger than any before it may raise a kernel's shared-memory limit; make those calls
+ * before any stream capture.  All calls share the array and leave their data in it; calls that
+ * overlap on the GPU (other streams or host threads) race.  Enqueued on `stream` (a cudaStream_t
+ * of the current device, NULL = default stream); returns once enqueued. */
 int ch_transform_forward_noalloc(int nx, int ny, int nz, const double* phys, double* spec,
                                  void* stream);
 size_t ch_noalloc_scratch_bytes(void);

@@ -101,7 +101,7 @@ _SIGS = {
                                               ctypes.POINTER(ctypes.c_double)]),
     "ch_ensemble_autotune": (ctypes.c_int, [_P, ctypes.c_int]),
     "ch_ensemble_tuning": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
-    "ch_selftest_bounded_wait": (ctypes.c_int, []),
+    "ch_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ch_ensemble_set_chebyshev": (ctypes.c_int, [_P, ctypes.c_int]),
     "ch_ensemble_get_chebyshev": (ctypes.c_int, [_P]),
     "ch_ensemble_destroy": (None, [_P]),
@@ -151,20 +151,29 @@ def _ptr(t):
 def transform_forward_noalloc(phys, spec, stream=None):
     """Allocation-free forward transform into a caller-provided spectral tensor.
 
-    phys: float64 CUDA tensor (nz, ny, nx); spec: complex128 CUDA tensor (nx/2, ny, nz) that
-    receives the coefficients.  The library allocates nothing for this call (its working memory
-    is a fixed static device array); see ch_transform_forward_noalloc in include/ch_flow.h."""
+    phys: float64 CUDA tensor (nz, ny, nx); spec: complex128 CUDA tensor (nx/2, ny, nz) on the
+    same device, which receives the coefficients.  The library allocates nothing for this call
+    (its working memory is a fixed static device array); see ch_transform_forward_noalloc in
+    include/ch_flow.h.  The call runs with phys's device current, on `stream` (default: that
+    device's current stream)."""
+    if phys.dim() != 3:
+        raise ValueError("phys must be a (nz, ny, nx) tensor")
     nz, ny, nx = phys.shape
+    if not (phys.is_cuda and spec.is_cuda) or spec.device != phys.device:
+        raise ValueError("phys and spec must be CUDA tensors on the same device")
+    if stream is not None and stream.device != phys.device:
+        raise ValueError("stream must belong to phys's device")
     if not (phys.is_contiguous() and spec.is_contiguous()):
         raise ValueError("contiguous tensors required")
     if phys.dtype != torch.float64 or spec.dtype != torch.complex128:
         raise ValueError("phys must be float64 and spec complex128")
     if tuple(spec.shape) != (nx // 2, ny, nz):
         raise ValueError(f"spec must have shape {(nx // 2, ny, nz)}")
-    s = stream if stream is not None else torch.cuda.current_stream(phys.device)
-    _ck("ch_transform_forward_noalloc",
-        lib().ch_transform_forward_noalloc(nx, ny, nz, _ptr(phys), _ptr(spec),
-                                           ctypes.c_void_p(s.cuda_stream)))
+    with torch.cuda.device(phys.device):
+        s = stream if stream is not None else torch.cuda.current_stream(phys.device)
+        _ck("ch_transform_forward_noalloc",
+            lib().ch_transform_forward_noalloc(nx, ny, nz, _ptr(phys), _ptr(spec),
+                                               ctypes.c_void_p(s.cuda_stream)))
     return spec
 
 

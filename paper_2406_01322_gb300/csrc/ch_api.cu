@@ -47,6 +47,11 @@ bool smooth23(int n) {
 
 bool make_radices(int n, FftPlan* pl) { return make_radices_style(n, 0, pl); }
 
+std::mutex& smem_limit_mutex() {
+  static std::mutex m;
+  return m;
+}
+
 bool make_radices_style(int n, int style, FftPlan* pl) {
   int a = 0, b = 0, m = n;
   while (m % 2 == 0) { m /= 2; ++a; }
@@ -835,20 +840,23 @@ int ch_chebyshev_lines(ch_grid* G, int dir, const double* in, double* out, int n
   return CH_OK;
 }
 
-int ch_selftest_bounded_wait(void) {
+int ch_selftest_bounded_wait(int nwaits, int* spun) {
+  if (nwaits < 1) return CH_ERR_ARG;
   int* d = nullptr;
-  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+  if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return CH_ERR_ALLOC;
   }
-  int h = 0, st = CH_OK;
-  if (cudaMemset(d, 0, sizeof(int)) != cudaSuccess || chf::launch_wait_selftest(d, 0) != cudaSuccess ||
-      cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+  int h[2] = {0, 0}, st = CH_OK;
+  if (cudaMemset(d, 0, 2 * sizeof(int)) != cudaSuccess ||
+      chf::launch_wait_selftest(d, nwaits, 0) != cudaSuccess ||
+      cudaMemcpy(h, d, 2 * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
     cudaGetLastError();
     st = CH_ERR_CUDA;
-  } else if (h) {
+  } else if (h[0]) {
     st = CH_ERR_TIMEOUT;
   }
+  if (spun) *spun = h[1];
   cudaFree(d);
   return st;
 }

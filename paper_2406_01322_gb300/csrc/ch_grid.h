@@ -25,10 +25,6 @@ constexpr int kBw = 5, kYa = 6, kNl = 9;
 // backward y-pass map of the step: u v w phi (phi -> i ky phi) Dphi
 YMap step_ymap();
 
-// radix schedule with a style: 0 one radix-8 for an odd power of two then 4s, 2, 3s;
-// 1 the same with the radix-3 passes first; 2 as many radix-8 passes as possible
-bool make_radices_style(int n, int style, FftPlan* pl);
-
 // header of a ch_get_state buffer (followed by om, w, phi, h_om, h_w, h_phi)
 struct StateHeader {
   uint64_t magic;

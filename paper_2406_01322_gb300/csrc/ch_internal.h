@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "ch_common.cuh"
@@ -15,21 +17,44 @@ bool smooth23(int n);
 // radix schedule (8 once for an odd power of two >= 3, then 4s, a 2, then 3s); false if n is
 // not {2,3}-smooth or needs too many passes.  Sets pl->n, pl->nst, pl->rad (not pl->tw).
 bool make_radices(int n, FftPlan* pl);
+// radix schedule with a style: 0 one radix-8 for an odd power of two then 4s, 2, 3s (as
+// make_radices); 1 the same with the radix-3 passes first; 2 as many radix-8 passes as possible
+bool make_radices_style(int n, int style, FftPlan* pl);
 // the grid-size rules of the C ABI: 0 or a negative CH_ERR_* code
 int check_sizes(int nx, int ny, int nz);
 
-// Raise a kernel's dynamic shared-memory limit to `bytes` if it is below that.  The limit is
-// per kernel; *cur remembers what was set.  Never called while a stream is being captured (the
-// first, uncaptured launch of every size comes first).
+// The dynamic shared-memory limit a kernel was raised to, per device (the attribute set by
+// cudaFuncSetAttribute belongs to the current device).  Zero-initialised as a static object.
+constexpr int kMaxSmemDevices = 64;
+struct SmemLimit {
+  std::atomic<int> v[kMaxSmemDevices];
+};
+std::mutex& smem_limit_mutex();
+
+// Raise a kernel's dynamic shared-memory limit on the current device to `bytes` if it is below
+// that; *lim remembers, per device, what was set.  Safe to call from several host threads.
+// Never called while a stream is being captured (the first, uncaptured launch of every size
+// comes first).
 template <typename K>
-inline cudaError_t ensure_smem(K* kernel, size_t bytes, int* cur) {
-  if ((int)bytes <= *cur || bytes <= 48 * 1024) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+inline cudaError_t ensure_smem(K* kernel, size_t bytes, SmemLimit* lim) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  const bool cached = dev >= 0 && dev < kMaxSmemDevices;
+  if (cached && (int)bytes <= lim->v[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(smem_limit_mutex());
+  const int have = cached ? lim->v[dev].load(std::memory_order_relaxed) : 0;
+  if ((int)bytes <= have) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();  // do not leave a non-sticky error behind
     return e;
   }
-  *cur = (int)bytes;
+  if (cached) lim->v[dev].store((int)bytes, std::memory_order_release);
   return cudaSuccess;
 }
 
@@ -207,6 +232,6 @@ cudaError_t launch_cheb_tc(int tin, int tout, const void* in, long long fsi, voi
                            long long fso, int nf, int nlines, int Nz, const ChebTc& t, int* err,
                            cudaStream_t s);
 // one bounded mbarrier wait that runs out on purpose (sets *err |= 1 after the wait bound)
-cudaError_t launch_wait_selftest(int* err, cudaStream_t s);
+cudaError_t launch_wait_selftest(int* err, int nwaits, cudaStream_t s);
 
 }  // namespace chf

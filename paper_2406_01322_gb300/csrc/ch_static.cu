@@ -1,19 +1,21 @@
 // Allocation-free forward transform: ch_transform_forward_noalloc.
 //
-// Some callers cannot allocate device memory at the moment they need a transform: code that
-// runs while a CUDA stream is being captured into a graph (cudaMalloc/cudaFree are not allowed
-// inside a capture), plug-ins hosted by an application whose memory pool already owns the
-// device's memory, or fixed-latency loops that must not enter the allocator.  This entry point
-// serves them: it computes the same physical -> spectral transform as ch_transform_forward
-// (Fourier in x and y, then the Chebyshev DCT-I) without a handle and without allocating.  Its
-// working memory is one file-scope device array of kStaticScratchBytes (64 MiB), which every
-// GPU that loads this library holds until the process exits.
+// Some callers cannot allocate device memory at the moment they need a transform: plug-ins
+// hosted by an application whose memory pool already owns the device's memory, or
+// fixed-latency loops that must not enter the allocator.  This entry point serves them: it
+// computes the same physical -> spectral transform as ch_transform_forward (Fourier in x and y,
+// then the Chebyshev DCT-I, with the handle's radix schedules) without a handle and without
+// allocating.  Its working memory is one file-scope device array of kStaticScratchBytes
+// (64 MiB), which every GPU that loads this library holds until the process exits.  Twiddles are
+// computed on the device (sincospi) rather than rounded from extended-precision host values, so
+// the result equals the handle's to rounding, not bit for bit.
 //
 // Set-up: the first call on a device (with that device current) looks up the array's device
-// address with cudaGetSymbolAddress; later calls reuse it.  Make that first call before any
-// stream capture.  Every call shares the array and leaves its contents behind; nothing in it
-// needs to start at zero (each stage writes every element the next stage reads).  Calls whose
-// work overlaps on the GPU (different streams, or different host threads) race on the array.
+// address with cudaGetSymbolAddress; later calls reuse it.  The first call for a grid larger
+// than any before may raise a kernel's dynamic shared-memory limit.  Make both before any stream
+// capture.  Every call shares the array and leaves its contents behind; nothing in it needs to
+// start at zero (each stage writes every element the next stage reads).  Calls whose work
+// overlaps on the GPU (different streams, or different host threads) race on the array.
 #include <mutex>
 
 #include "../../include/ch_flow.h"
@@ -87,6 +89,9 @@ extern "C" int ch_transform_forward_noalloc(int nx, int ny, int nz, const double
   g.Mx = nx / 2;
   g.Px = 3 * nx / 2;
   g.Py = 3 * ny / 2;
+  // the forward transform does not depend on the box size; the library's default box
+  g.lx = 4.0 * 3.14159265358979323846;
+  g.ly = 2.0 * 3.14159265358979323846;
   const long long fs = (long long)g.Mx * ny * nz;
   // scratch layout: x, y, z twiddles, then two (Mx, Ny, Nz) complex fields
   const size_t b_tx = round256((size_t)nx * sizeof(double2));
@@ -103,8 +108,10 @@ extern "C" int ch_transform_forward_noalloc(int nx, int ny, int nz, const double
   double2* A = reinterpret_cast<double2*>(base + b_tx + b_ty + b_tz);
   double2* B = reinterpret_cast<double2*>(base + b_tx + b_ty + b_tz + b_f);
   chf::FftPlan px, py, pz;
+  // the schedules of the handle's transform: default ones for the unpadded x and y lengths,
+  // maximal radix-8 for the Chebyshev lines
   if (!chf::make_radices(nx, &px) || !chf::make_radices(ny, &py) ||
-      !chf::make_radices(g.N, &pz))
+      !chf::make_radices_style(g.N, 2, &pz))
     return CH_ERR_SIZE;
   px.tw = tx;
   py.tw = ty;

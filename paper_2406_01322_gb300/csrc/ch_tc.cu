@@ -83,9 +83,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try(bar, parity)) return true;   // the common case: no clock read
-  const uint64_t t0 = gtime();
+// wait for the phase with the given parity until the global timer passes `deadline`
+__device__ __forceinline__ bool mbar_wait_until(uint32_t bar, uint32_t parity,
+                                                uint64_t deadline) {
   while (true) {
     uint32_t done;
     asm volatile(
@@ -95,9 +95,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (gtime() - t0 > kWaitNs) return false;
+    if (gtime() > deadline) return false;
   }
 }
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;   // the common case: no clock read
+  return mbar_wait_until(bar, parity, gtime() + kWaitNs);
+}
+// The waits of one thread.  The first wait that runs out clears `ok`; every later wait returns
+// false at once, so a thread spends at most one bound waiting in vain however many waits follow
+// (the transform kernel's issuer then stops issuing and drains, its producers skip their waits).
+struct Waiter {
+  bool ok = true;
+  __device__ __forceinline__ bool wait(uint32_t bar, uint32_t parity) {
+    ok = ok && mbar_wait(bar, parity);
+    return ok;
+  }
+};
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t acc) {
   asm volatile(
@@ -292,9 +306,9 @@ template <> __device__ __forceinline__ df qnan<df>() {
 }
 
 __host__ __device__ constexpr size_t tc_smem_bytes(int NT) {
-  // B planes, two A planes, row exponents, eight barriers and the tensor-memory address
-  // (80 bytes), output-column exponents (at most 512)
-  return (size_t)8 * NT * TCKC * 2 + (size_t)2 * TCM * TCKC * 2 + TCM * sizeof(int) + 80 +
+  // B planes, two A planes, row exponents, ten barriers and the tensor-memory address
+  // (88 bytes), output-column exponents (at most 512)
+  return (size_t)8 * NT * TCKC * 2 + (size_t)2 * TCM * TCKC * 2 + TCM * sizeof(int) + 88 +
          512 * sizeof(int);
 }
 
@@ -329,18 +343,19 @@ __global__ void __launch_bounds__(TCT + 32, 1)
   unsigned char* sA = sB + (size_t)8 * NT * TCKC * 2;
   int* sE = reinterpret_cast<int*>(sA + (size_t)2 * TCM * TCKC * 2);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(sE + TCM);
-  uint32_t* sT = reinterpret_cast<uint32_t*>(bars + 9);
-  int* sF = reinterpret_cast<int*>(bars + 10);   // F_n of every output column (nNt NT <= 512)
+  uint32_t* sT = reinterpret_cast<uint32_t*>(bars + 10);
+  int* sF = reinterpret_cast<int*>(bars + 11);   // F_n of every output column (nNt NT <= 512)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nchunk = (Kp + TCKC - 1) / TCKC;
   constexpr uint32_t kPlaneBytes = TCM * TCKC * 2;
   // barriers: B loaded; full[b] (16 producer warps); loaded[b] (a cached plane copied);
   // empty[b] (MMAs of the plane done); drained (16 producer warps read the accumulators);
   // sliced (every MMA of a slice done: one phase per slice, so the producers, which skip the
-  // planes of the later slices, never wait on a phase more than one ahead)
+  // planes of the later slices, never wait on a phase more than one ahead); fin (the issuer's
+  // MMAs in flight, after a wait ran out)
   const uint32_t barB = su32(&bars[0]), barFull = su32(&bars[1]), barLoad = su32(&bars[3]);
   const uint32_t barEmpty = su32(&bars[5]), barDrain = su32(&bars[7]);
-  const uint32_t barSlice = su32(&bars[8]);
+  const uint32_t barSlice = su32(&bars[8]), barFin = su32(&bars[9]);
   const size_t bslice = (size_t)8 * NT * Kp;
   uint32_t* ccta = cache + (size_t)blockIdx.x * nchunk * 8 * (kPlaneBytes / 4);
   const bool issuer_warp = (warp == TCT / 32);
@@ -355,6 +370,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barEmpty + 8));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(barDrain));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barSlice));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barFin));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (issuer_warp) {
@@ -370,7 +386,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *sT;
   const uint32_t sA0 = su32(sA), sB0 = su32(sB);
-  bool ok = true;
+  Waiter W;
 
   if (issuer_warp) {
     if (lane == 0) {
@@ -378,30 +394,36 @@ __global__ void __launch_bounds__(TCT + 32, 1)
       const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCM >> 4) << 24);
       int t = 0, u = 0, S = 0;           // plane, B copy and slice counters (all tiles)
       int nfull[2] = {0, 0}, nload[2] = {0, 0};
+      int iload[2] = {0, 0};             // cached-plane copies issued per buffer
+      bool pendB = false;                // a copy of B issued and not yet waited for
+      bool any_mma = false;
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         for (int sl = 0; sl < nNt; ++sl, ++S) {
           for (int ch = 0; ch < nchunk; ++ch, ++u) {
             const int KCc = min(TCKC, Kp - ch * TCKC);
             // the previous plane (t - 1) read B; it must be consumed before B is replaced
-            if (u > 0) ok = mbar_wait(barEmpty + 8 * ((t - 1) & 1), ((t - 1) >> 1) & 1) && ok;
+            if (u > 0 && !W.wait(barEmpty + 8 * ((t - 1) & 1), ((t - 1) >> 1) & 1)) goto drain;
             bulk_load(sB0, bdig + (size_t)sl * bslice + (size_t)ch * 8 * NT * TCKC,
                       (uint32_t)(8 * NT * KCc * 2), barB);
+            pendB = true;
             if (sl > 0) {   // first cached plane of this chunk into buffer t % 2
-              if (t >= 2) ok = mbar_wait(barEmpty + 8 * (t & 1), ((t - 2) >> 1) & 1) && ok;
+              if (t >= 2 && !W.wait(barEmpty + 8 * (t & 1), ((t - 2) >> 1) & 1)) goto drain;
               // the producers' global stores (acquired through `full`) before the async copy
               asm volatile("fence.proxy.async.global;" ::: "memory");
               bulk_load(sA0 + (uint32_t)((t & 1) * kPlaneBytes), ccta + (size_t)ch * 8 * (kPlaneBytes / 4),
                         kPlaneBytes, barLoad + 8 * (t & 1));
+              ++iload[t & 1];
             }
-            ok = mbar_wait(barB, u & 1) && ok;
-            if (ch == 0 && S > 0) ok = mbar_wait(barDrain, (S - 1) & 1) && ok;
+            if (!W.wait(barB, u & 1)) goto drain;
+            pendB = false;
+            if (ch == 0 && S > 0 && !W.wait(barDrain, (S - 1) & 1)) goto drain;
             for (int i = 0; i < 8; ++i, ++t) {
               const int bf = t & 1;
               if (sl == 0) {
-                ok = mbar_wait(barFull + 8 * bf, nfull[bf] & 1) && ok;
+                if (!W.wait(barFull + 8 * bf, nfull[bf] & 1)) goto drain;
                 ++nfull[bf];
               } else {
-                ok = mbar_wait(barLoad + 8 * bf, nload[bf] & 1) && ok;
+                if (!W.wait(barLoad + 8 * bf, nload[bf] & 1)) goto drain;
                 ++nload[bf];
               }
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -419,19 +441,35 @@ __global__ void __launch_bounds__(TCT + 32, 1)
                            bd + (uint64_t)(s * 16 * NT), idesc0 | ((uint32_t)(nlen >> 3) << 17),
                            (uint32_t)((ch | i | s) != 0));
                 }
+              any_mma = true;
               mma_commit(barEmpty + 8 * bf);
               if (i == 7 && ch == nchunk - 1) mma_commit(barSlice);
               if (sl > 0 && i < 7) {
                 // the next cached plane into the other buffer, once its MMAs (plane t - 1) ended
                 const int tn = t + 1;
-                if (tn >= 2) ok = mbar_wait(barEmpty + 8 * (tn & 1), ((tn - 2) >> 1) & 1) && ok;
+                if (tn >= 2 && !W.wait(barEmpty + 8 * (tn & 1), ((tn - 2) >> 1) & 1)) goto drain;
                 bulk_load(sA0 + (uint32_t)((tn & 1) * kPlaneBytes),
                           ccta + (size_t)(ch * 8 + i + 1) * (kPlaneBytes / 4), kPlaneBytes,
                           barLoad + 8 * (tn & 1));
+                ++iload[tn & 1];
               }
             }
           }
         }
+      }
+    drain:
+      if (!W.ok) {
+        // A wait ran out: nothing more is issued.  Before the tensor memory is released and the
+        // CTA ends, wait (one shared bound for all of them) for the MMAs and the bulk copies
+        // still in flight: the MMAs through one last commit, each copy on its own barrier phase.
+        const uint64_t dl = gtime() + kWaitNs;
+        if (any_mma) {
+          mma_commit(barFin);
+          mbar_wait_until(barFin, 0, dl);
+        }
+        if (pendB) mbar_wait_until(barB, u & 1, dl);
+        for (int b = 0; b < 2; ++b)
+          if (iload[b] > nload[b]) mbar_wait_until(barLoad + 8 * b, nload[b] & 1, dl);
       }
     }
     __syncwarp();
@@ -505,7 +543,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
           }
         for (int i = 0; i < 8; ++i, ++t) {
           const int bf = t & 1;
-          if (t >= 2) ok = mbar_wait(barEmpty + 8 * bf, ((t - 2) >> 1) & 1) && ok;
+          if (t >= 2) W.wait(barEmpty + 8 * bf, ((t - 2) >> 1) & 1);
           uint32_t* dst = reinterpret_cast<uint32_t*>(sA + (size_t)bf * kPlaneBytes);
           uint32_t* gdst = ccta + (size_t)(ch * 8 + i) * (kPlaneBytes / 4);
           const int sh = 7 * (3 - (i & 3));
@@ -530,7 +568,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
       s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 1);
       s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 2);
       s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 2);
-      if (q == 0 && rowok && ok) {
+      if (q == 0 && rowok && W.ok) {
         // sum_k w_k x_k = 2^(E - 54) (S_hi 2^27 + S_lo) = T 2^(E - 51), T = S_hi 2^24 + S_lo / 8
         // (|sum w X| < 2 Kp 2^54 < 2^64, so three low bits are dropped: 2^-51 of the row scale)
         const long long T = s_hi * 16777216ll + (s_lo >> 3);
@@ -544,11 +582,13 @@ __global__ void __launch_bounds__(TCT + 32, 1)
       for (int sl = 0; sl < nNt; ++sl, ++S) {
         if (sl > 0) t += 8 * nchunk;   // planes the issuer copies
         // every MMA of the slice done
-        ok = mbar_wait(barSlice, S & 1) && ok;
+        W.wait(barSlice, S & 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its rows), columns
-        // (w / 4) NT/4 .. + NT/4 - 1 of each of the eight accumulators, 4 at a time
-        const bool orow = ok && oline < nlines;
+        // (w / 4) NT/4 .. + NT/4 - 1 of each of the eight accumulators, 4 at a time (after a
+        // failed wait the producers keep their loop structure, which their named barrier
+        // needs, but wait no more and store nothing)
+        const bool orow = W.ok && oline < nlines;
         for (int c0 = 0; c0 < CW; c0 += 4) {
           uint32_t v[8][4];
           tmem_ld8x4(tb + (uint32_t)c0, NT, v);
@@ -582,7 +622,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
       }
     }
   }
-  if (!ok) atomicOr(err, 1);
+  if (!W.ok) atomicOr(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (issuer_warp)
@@ -698,14 +738,14 @@ cudaError_t cheb_tc_prepare(int NT) {
   const size_t smem = tc_smem_bytes(NT);
   cudaError_t e = cudaSuccess;
   if (NT == 48) {
-    static int c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+    static SmemLimit c0, c1, c2, c3, c4;
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, double, 48>, smem, &c0);
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<float, double, 48>, smem, &c1);
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, float, 48>, smem, &c2);
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<df, double, 48>, smem, &c3);
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, df, 48>, smem, &c4);
   } else {
-    static int c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+    static SmemLimit c0, c1, c2, c3, c4;
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, double, 64>, smem, &c0);
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<float, double, 64>, smem, &c1);
     if (e == cudaSuccess) e = ensure_smem(cheb_tc_kernel<double, float, 64>, smem, &c2);
@@ -731,21 +771,31 @@ cudaError_t launch_cheb_tc(int tin, int tout, const void* in, long long fsi, voi
   return cudaErrorInvalidValue;
 }
 
-// Failure path of the bounded waits, exercised on purpose: one thread waits, with the same
-// helper as the transform's pipeline, for phase 0 of an mbarrier that nothing arrives at.  The
-// wait gives up after kWaitNs, the thread records it in *err and the kernel returns; no TMEM, no
-// asynchronous copy is involved, so nothing else is left in flight.
-__global__ void __launch_bounds__(32) wait_selftest_kernel(int* __restrict__ err) {
-  __shared__ __align__(8) uint64_t bar;
+// Failure path of the bounded waits, exercised on purpose: one thread runs a loop of `nwaits`
+// waits of the transform's shape (the same Waiter, alternating the parities of two mbarriers)
+// on barriers that nothing arrives at.  The first wait gives up after kWaitNs and every later
+// one returns at once, so the kernel ends after about one bound however long the loop; the
+// thread records the failure in err[0] and the number of waits that actually spun in err[1].
+// No TMEM and no asynchronous copy is involved, so nothing else is left in flight.
+__global__ void __launch_bounds__(32) wait_selftest_kernel(int* __restrict__ err, int nwaits) {
+  __shared__ __align__(8) uint64_t bar[2];
   if (threadIdx.x != 0) return;
-  const uint32_t b = su32(&bar);
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+  const uint32_t b0 = su32(&bar[0]), b1 = su32(&bar[1]);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0));
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b1));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  if (!mbar_wait(b, 0)) atomicOr(err, 1);
+  Waiter W;
+  int spun = 0;
+  for (int i = 0; i < nwaits; ++i) {
+    if (W.ok) ++spun;
+    W.wait((i & 1) ? b1 : b0, (uint32_t)((i >> 1) & 1));
+  }
+  if (!W.ok) atomicOr(&err[0], 1);
+  atomicAdd(&err[1], spun);
 }
 
-cudaError_t launch_wait_selftest(int* err, cudaStream_t s) {
-  wait_selftest_kernel<<<1, 32, 0, s>>>(err);
+cudaError_t launch_wait_selftest(int* err, int nwaits, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(err, nwaits);
   return cudaGetLastError();
 }
 

@@ -469,7 +469,7 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
   const int TZ = ytile_local(P, elem);
   const size_t smem = (size_t)2 * TZ * P * elem;
   dim3 grid((g.nz + TZ - 1) / TZ, g.Mx, nf);
-  static int cur[6] = {0, 0, 0, 0, 0, 0};
+  static SmemLimit cur[6];
   cudaError_t e = cudaSuccess;
   if (prec == 0) e = dir == 1 ? ensure_smem(ypass_kernel<double, true>, smem, &cur[0])
                               : ensure_smem(ypass_kernel<double, false>, smem, &cur[1]);
@@ -497,7 +497,7 @@ cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out1
   const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);
   const size_t smem = (size_t)17 * g.Px * elem;
   dim3 grid((g.nz + 1) / 2, g.Py);
-  static int cur64 = 0, cur32 = 0, curdf = 0;
+  static SmemLimit cur64, cur32, curdf;
   cudaError_t e = prec == 0 ? ensure_smem(xline_kernel<double>, smem, &cur64)
                   : prec == 1 ? ensure_smem(xline_kernel<float>, smem, &cur32)
                               : ensure_smem(xline_kernel<df>, smem, &curdf);
@@ -523,7 +523,7 @@ cudaError_t launch_adj_xline(const GridDev& g, const double2* in6, const double2
                              double2* out6, long long fs, const FftPlan& px, cudaStream_t s) {
   const size_t smem = adj_xline_smem(g.Px);
   dim3 grid((g.nz + 1) / 2, g.Py);
-  static int cur = 0;
+  static SmemLimit cur;
   cudaError_t e = ensure_smem(adj_xline_kernel, smem, &cur);
   if (e != cudaSuccess) return e;
   adj_xline_kernel<<<grid, XT, smem, s>>>(in6, pb9, out6, g.Mx, g.Px, g.Py, g.nz, fs, g.kappa,
@@ -559,7 +559,7 @@ size_t xline_smem(int Px, size_t elem) { return (size_t)17 * Px * elem; }
 cudaError_t launch_grouped_xy(int stage, int prec, const Member* mem, const int* begin, int nmem,
                               int grid, size_t smem, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  static int cur[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  static SmemLimit cur[9];
 #define GL(K, idx, T_)                                                   \
   if ((e = ensure_smem(K, smem, &cur[idx])) != cudaSuccess) return e;    \
   K<<<grid, (stage == 4 ? XT : YT), smem, s>>>(mem, begin, nmem);

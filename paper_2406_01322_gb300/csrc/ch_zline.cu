@@ -1958,17 +1958,17 @@ cudaError_t launch_zrhs(int prec, const GridDev& g, const void* nl, long long fs
   const size_t smem = zline_smem(g);
   cudaError_t e;
   if (prec == 0) {
-    static int cur = 0;
+    static SmemLimit cur;
     if ((e = ensure_smem(zrhs_kernel<double>, smem, &cur)) != cudaSuccess) return e;
     zrhs_kernel<double><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const double2*)nl, fs, st_om, st_w, st_phi,
                                                       h_om, h_w, h_phi, R, first, pz);
   } else if (prec == 1) {
-    static int cur = 0;
+    static SmemLimit cur;
     if ((e = ensure_smem(zrhs_kernel<float>, smem, &cur)) != cudaSuccess) return e;
     zrhs_kernel<float><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const float2*)nl, fs, st_om, st_w, st_phi,
                                                      h_om, h_w, h_phi, R, first, pz);
   } else {
-    static int cur = 0;
+    static SmemLimit cur;
     if ((e = ensure_smem(zrhs_kernel<df>, smem, &cur)) != cudaSuccess) return e;
     zrhs_kernel<df><<<g.Mx * g.ny, ZT, smem, s>>>(g, (const df2*)nl, fs, st_om, st_w, st_phi,
                                                   h_om, h_w, h_phi, R, first, pz);
@@ -1976,7 +1976,7 @@ cudaError_t launch_zrhs(int prec, const GridDev& g, const void* nl, long long fs
   return cudaGetLastError();
 }
 
-static int cur_zrhs_coef = 0, cur_zbwd_coef = 0;
+static SmemLimit cur_zrhs_coef, cur_zbwd_coef;
 
 cudaError_t zline_coef_prepare(const GridDev& g) {
   const size_t smem = zline_smem(g);
@@ -2019,31 +2019,31 @@ cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* 
   cudaError_t e = cudaSuccess;
   if (coef && stage != 1) {
     if (stage == 0) {
-      static int cur = 0;
+      static SmemLimit cur;
       if ((e = ensure_smem(grouped_zrhs_coef_kernel, smem, &cur)) != cudaSuccess) return e;
       grouped_zrhs_coef_kernel<<<grid, ZT, smem, s>>>(mem, begin, nmem);
     } else {
-      static int cur = 0;
+      static SmemLimit cur;
       if ((e = ensure_smem(grouped_zbwd_coef_kernel, smem, &cur)) != cudaSuccess) return e;
       grouped_zbwd_coef_kernel<<<grid, ZT, smem, s>>>(mem, begin, nmem);
     }
   } else if (stage == 0) {
     if (prec == 0) {
-      static int cur = 0;
+      static SmemLimit cur;
       if ((e = ensure_smem(grouped_zrhs_kernel<double>, smem, &cur)) != cudaSuccess) return e;
       grouped_zrhs_kernel<double><<<grid, ZT, smem, s>>>(mem, begin, nmem);
     } else if (prec == 1) {
-      static int cur = 0;
+      static SmemLimit cur;
       if ((e = ensure_smem(grouped_zrhs_kernel<float>, smem, &cur)) != cudaSuccess) return e;
       grouped_zrhs_kernel<float><<<grid, ZT, smem, s>>>(mem, begin, nmem);
     } else {
-      static int cur = 0;
+      static SmemLimit cur;
       if ((e = ensure_smem(grouped_zrhs_kernel<df>, smem, &cur)) != cudaSuccess) return e;
       grouped_zrhs_kernel<df><<<grid, ZT, smem, s>>>(mem, begin, nmem);
     }
   } else if (stage == 1) {
     if (zsolve_tile) {
-      static int cur = 0;
+      static SmemLimit cur;
       if ((e = ensure_smem(grouped_zsolve_tile_kernel, smem, &cur)) != cudaSuccess) return e;
       grouped_zsolve_tile_kernel<<<grid, TLT, smem, s>>>(mem, begin, nmem);
     } else {
@@ -2051,15 +2051,15 @@ cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* 
     }
   } else {
     if (prec == 0) {
-      static int cur = 0;
+      static SmemLimit cur;
       if ((e = ensure_smem(grouped_zbwd_kernel<double>, smem, &cur)) != cudaSuccess) return e;
       grouped_zbwd_kernel<double><<<grid, ZT, smem, s>>>(mem, begin, nmem);
     } else if (prec == 1) {
-      static int cur = 0;
+      static SmemLimit cur;
       if ((e = ensure_smem(grouped_zbwd_kernel<float>, smem, &cur)) != cudaSuccess) return e;
       grouped_zbwd_kernel<float><<<grid, ZT, smem, s>>>(mem, begin, nmem);
     } else {
-      static int cur = 0;
+      static SmemLimit cur;
       if ((e = ensure_smem(grouped_zbwd_kernel<df>, smem, &cur)) != cudaSuccess) return e;
       grouped_zbwd_kernel<df><<<grid, ZT, smem, s>>>(mem, begin, nmem);
     }
@@ -2117,7 +2117,7 @@ cudaError_t launch_adj_zrhs(const GridDev& g, const double2* Rb, const double2* 
                             long long fs, int first, const double2* bb, const FftPlan& pz,
                             cudaStream_t s) {
   const size_t smem = zline_smem(g);
-  static int cur = 0;
+  static SmemLimit cur;
   cudaError_t e = ensure_smem(adj_zrhs_kernel, smem, &cur);
   if (e != cudaSuccess) return e;
   adj_zrhs_kernel<<<g.Mx * g.ny, ZT, smem, s>>>(g, Rb, L, mu, lam, mu_prev, nlb, fs, first,
@@ -2128,7 +2128,7 @@ cudaError_t launch_adj_zrhs(const GridDev& g, const double2* Rb, const double2* 
 cudaError_t launch_adj_zbwd(const GridDev& g, const double2* in5, long long fs_in, double2* lam,
                             long long fs, const FftPlan& pz, cudaStream_t s) {
   const size_t smem = zline_smem(g);
-  static int cur = 0;
+  static SmemLimit cur;
   cudaError_t e = ensure_smem(adj_zbwd_kernel, smem, &cur);
   if (e != cudaSuccess) return e;
   adj_zbwd_kernel<<<g.Mx * g.ny, ZT, smem, s>>>(g, in5, fs_in, lam, fs, pz);
@@ -2139,7 +2139,7 @@ cudaError_t launch_objective(const GridDev& g, const double2* om, const double2*
                              const double2* phi, double2* lam, long long fs, double* part,
                              cudaStream_t s) {
   const size_t smem = zline_smem(g);
-  static int cur = 0;
+  static SmemLimit cur;
   cudaError_t e = ensure_smem(objective_kernel, smem, &cur);
   if (e != cudaSuccess) return e;
   objective_kernel<<<g.Mx * g.ny, ZT, smem, s>>>(g, om, w, phi, lam, fs, part);
@@ -2149,7 +2149,7 @@ cudaError_t launch_objective(const GridDev& g, const double2* om, const double2*
 cudaError_t launch_adj_project(const GridDev& g, const double2* lam, long long fs, double2* out4,
                                const FftPlan& pz, cudaStream_t s) {
   const size_t smem = zline_smem(g);
-  static int cur = 0;
+  static SmemLimit cur;
   cudaError_t e = ensure_smem(adj_project_kernel, smem, &cur);
   if (e != cudaSuccess) return e;
   adj_project_kernel<<<g.Mx * g.ny, ZT, smem, s>>>(g, lam, fs, out4, pz);
@@ -2172,7 +2172,7 @@ cudaError_t launch_zsolve(const GridDev& g, double2* R, long long fs, cudaStream
   const size_t tile = (size_t)TL * g.nz * sizeof(double2) + (size_t)3 * g.nz * sizeof(double);
   if (tile <= 72 * 1024) {
     // short lines: a 32-line tile fits three CTAs per SM; staging in shared memory wins
-    static int cur = 0;
+    static SmemLimit cur;
     cudaError_t e = ensure_smem(zsolve_tile_kernel, tile, &cur);
     if (e != cudaSuccess) return e;
     zsolve_tile_kernel<<<(nlines + TL - 1) / TL, TLT, tile, s>>>(g, R, fs, nlines);
@@ -2190,7 +2190,7 @@ static cudaError_t launch_zbwd_t(const GridDev& g, const double2* R, double2* st
                                  const FftPlan& pz, cudaStream_t s) {
   typedef typename C2<T>::t T2;
   const size_t smem = zline_smem(g);
-  static int cur = 0;
+  static SmemLimit cur;
   cudaError_t e = ensure_smem(zbwd_kernel<T, UPDATE, NOUT>, smem, &cur);
   if (e != cudaSuccess) return e;
   zbwd_kernel<T, UPDATE, NOUT><<<g.Mx * g.ny, ZT, smem, s>>>(g, R, st_om, st_w, st_phi, (T2*)bw,
@@ -2217,7 +2217,7 @@ cudaError_t launch_project(const GridDev& g, const double2* uvwp, long long fs, 
                            double2* st_w, double2* st_phi, double2* h_om, double2* h_w,
                            double2* h_phi, const FftPlan& pz, cudaStream_t s) {
   const size_t smem = zline_smem(g);
-  static int cur = 0;
+  static SmemLimit cur;
   cudaError_t e = ensure_smem(project_kernel, smem, &cur);
   if (e != cudaSuccess) return e;
   project_kernel<<<g.Mx * g.ny, ZT, smem, s>>>(g, uvwp, fs, st_om, st_w, st_phi, h_om, h_w, h_phi, pz);
@@ -2227,7 +2227,7 @@ cudaError_t launch_project(const GridDev& g, const double2* uvwp, long long fs, 
 cudaError_t launch_dct_lines(int dir, int prec, const GridDev& g, const void* in, double2* out,
                              int nf, long long fs, const FftPlan& pz, cudaStream_t s) {
   const size_t smem = zline_smem(g);
-  static int cur64 = 0, cur32 = 0, curdf = 0;
+  static SmemLimit cur64, cur32, curdf;
   cudaError_t e = ensure_smem(dct_lines_kernel<double>, smem, &cur64);
   if (e == cudaSuccess) e = ensure_smem(dct_lines_kernel<float>, smem, &cur32);
   if (e == cudaSuccess) e = ensure_smem(dct_lines_kernel<df>, smem, &curdf);

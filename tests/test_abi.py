@@ -51,3 +51,14 @@ def test_no_cpu_fallback_when_library_missing(tmp_path):
     from paper_2406_01322_gb300 import binding
     with pytest.raises(RuntimeError):
         binding.load_library(str(tmp_path / "nope.so"))
+
+
+def test_noalloc_binding_rejects_host_tensors_before_the_library_call(libpath):
+    """A host tensor's pointer must never reach the device kernels: the binding checks that
+    both tensors are CUDA tensors on one device before it calls the library."""
+    import torch
+    from paper_2406_01322_gb300 import binding
+    phys = torch.zeros((17, 16, 16), dtype=torch.float64)
+    spec = torch.zeros((8, 16, 17), dtype=torch.complex128)
+    with pytest.raises(ValueError):
+        binding.transform_forward_noalloc(phys, spec)

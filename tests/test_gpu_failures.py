@@ -78,10 +78,23 @@ def test_invalid_arguments_are_rejected_on_the_host(binding):
 
 
 def test_bounded_device_wait_runs_out_and_reports_timeout(binding):
-    """A wait on an mbarrier phase that nothing completes gives up after its bound (about one
-    second), the kernel records it and returns: CH_ERR_TIMEOUT, and the context stays usable (a
-    step runs and matches a fresh grid afterwards)."""
-    assert binding.lib().ch_selftest_bounded_wait() == -6
+    """A loop of waits on mbarrier phases that nothing completes (the shape of the tensor-core
+    kernel's pipeline): the first wait gives up after its bound (about one second) and every
+    later one returns at once, so the whole loop ends within two bounds, not one bound per wait;
+    the kernel records the failure and returns CH_ERR_TIMEOUT, and the context stays usable (a
+    step runs afterwards)."""
+    import ctypes
+    import time
+    spun = ctypes.c_int(-1)
+    t0 = time.perf_counter()
+    assert binding.lib().ch_selftest_bounded_wait(1, ctypes.byref(spun)) == -6
+    one = time.perf_counter() - t0
+    assert spun.value == 1 and 0.9 < one < 2.0, (spun.value, one)
+    t0 = time.perf_counter()
+    assert binding.lib().ch_selftest_bounded_wait(4096, ctypes.byref(spun)) == -6
+    many = time.perf_counter() - t0
+    assert spun.value == 1 and 0.9 < many < 2.0, (spun.value, many)
+    assert binding.lib().ch_selftest_bounded_wait(0, None) == -1
     f = [torch.from_numpy(a) for a in inputs.initial_fields(16, 16, 17, 150.0, 0.05, 1, 0.4, 3)]
     g = binding.Grid(16, 16, 17)
     g.set_fields(*f)

@@ -1,11 +1,11 @@
 """The allocation-free forward transform (ch_transform_forward_noalloc) against ch_transform_forward.
 
 ch_transform_forward_noalloc exists for callers that must not allocate device memory when they
-transform a field (for example code running inside a CUDA-graph stream capture, where cudaMalloc
-is not allowed, or a plug-in whose host application owns the GPU's memory pool).  It works in a
-fixed static device array instead of buffers from an allocator.  This file is collected last so
-that a run stopping at the first failure has run every other test first; it passes alone in a
-fresh process as well.
+transform a field (for example a plug-in whose host application's memory pool owns the GPU, or a
+fixed-latency loop that must stay out of the allocator).  It works in a fixed static device array
+instead of buffers from an allocator, and equals the handle path to rounding (its twiddles come
+from the device's sincospi).  This file is collected last so that a run stopping at the first
+failure has run every other test first; it passes alone in a fresh process as well.
 """
 import numpy as np
 import pytest
