@@ -6,18 +6,23 @@ Prints ONE JSON line (rank 0).  A step is one full time step (Sec. 2.2 steps i)-
 channel: six kernels - z right-hand sides (Chebyshev DCTs, assembly, AB2), tau solves, z update
 + backward DCTs, y backward pass, fused x-line kernel (transforms + products), y forward pass
 (eight with --cheb tc: the Chebyshev transforms then run as two tensor-core launches).
-Default workload: the 128 x 128 x 129 FP64 channel (Re_tau = 150, 8 drops).  Points = nx ny nz
+Default workload: the 512 x 256 x 257 channel in mixed precision (Re_tau = 300, 64 drops; float32
+x/y transforms and products, float64 along z), the other precisions and Chebyshev methods of the
+same grid beside it (variants, with the float64 step's own roofline).  Points = nx ny nz
 (unpadded); the metric is Mpoints * steps / s of the whole job.
 
 * value: device time of K steps on the handle's stream (CUDA events, barrier + synchronize on
-  both sides, max over ranks); the per-step working set (~0.8 GB at 128^3) is larger than L2.
+  both sides, max over ranks); the per-step working set (~8 GB at 512 x 256 x 257, ~0.8 GB at
+  128^3) is larger than L2.
 * e2e: the user path through the C ABI with host buffers: upload of u, v, w, phi from pinned host
   memory, K steps, download of u, v, w, phi, timed on the host clock after a synchronize.
 * roofline: the dominant kernel of the step, its algorithmic FLOPs (or bytes) per launch over
   its CUDA-event launch time, against the float64 ALU peak (no float64 figure is in the
   measured-peaks file: 152 SMs x 2.07 GHz x 4 flop/clk/SM = 1.26 TFLOP/s nominal) or the
   measured HBM copy bandwidth.
-* cpu_baseline: the CPU oracle on a bounded sample of the same workload (rank 0, N = 1).
+* cpu_baseline: the CPU oracle on a bounded sample of the same workload (rank 0, N = 1), credited
+  with the fraction of a step it covered; --impl reference runs the same sampled oracle step as
+  its steps.
 * N > 1: N independent replicas, one per rank ("replicas only": the single-grid step does not
   shard without all-to-all transposes); value = all ranks' points * steps / max time.
 """
@@ -259,36 +264,6 @@ def precision_accuracy(binding, w, fields, steps, device, prec=1):
     return out
 
 
-def precision_variants(binding, w, fields, kw, steps, device):
-    """The same workload in the other precision modes and with the tensor-core Chebyshev
-    transforms: device time per step over `steps` steps (after 3 warm-up steps) and the max
-    relative field difference from the float64 FFT path after 3 + `steps` steps from the same
-    fields."""
-    import torch
-    out, final = {}, {}
-    pts = w["nx"] * w["ny"] * w["nz"]
-    # (precision, Chebyshev method): the float64 FFT path first (the comparison base)
-    for pr, cheb in ((0, 0), (2, 0), (1, 0), (0, 1), (2, 1), (1, 1)):
-        g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=pr, device=device, **kw)
-        g.set_chebyshev(cheb)
-        g.set_fields(*[torch.from_numpy(f) for f in fields])
-        g.step(3)
-        tot, _ = g.step_timed(steps)
-        final[(pr, cheb)] = [f.cpu() for f in g.get_fields()]
-        g.close()
-        torch.cuda.empty_cache()
-        if (pr, cheb) != (0, 0):
-            name = PREC_NAMES[pr] + ("_tc" if cheb else "")
-            dt = DTYPES[pr] + (" (Chebyshev transforms: exact-split bf16 tensor-core products, "
-                               "float64-accurate)" if cheb else "")
-            out[name] = {"ms_per_step": tot / steps, "dtype": dt,
-                         "value": pts * steps / (tot * 1e-3) / 1e6,
-                         "max_rel_field_diff_vs_fp64": max(
-                             float((a - b).abs().max() / b.abs().max())
-                             for a, b in zip(final[(pr, cheb)], final[(0, 0)]))}
-    return out
-
-
 def dct_gemm_ms(w, reps=5, warmup=2, dev="cuda"):
     """Timed comparison only: the seven forward Chebyshev transforms of one step as one dense
     float64 matrix product (cuBLAS through torch.matmul): the (N+1) x (N+1) DCT-I matrix times
@@ -417,112 +392,109 @@ def replica_throughput(points, steps, world, seconds):
     return world * points * steps / seconds / 1e6
 
 
-def oracle_sample(w, nsample_lines=None, steps=1):
-    """Time the CPU oracle on one step of the workload: the full non-linear evaluation plus the
-    implicit solves of a sample of wavenumber lines, scaled to all lines."""
-    import numpy as np
+def oracle_channel(w):
     from oracle.channel import Channel, Params
     from paper_2406_01322_gb300 import inputs
     p = Params(nx=w["nx"], ny=w["ny"], nz=w["nz"], re_tau=w["re_tau"], we=w["we"], ch=w["ch"],
                pe=w["pe"], dt=w["dt"])
     c = Channel(p)
     c.set_fields(*inputs.initial_fields(**w))
-    lines = c.all_lines()
-    if nsample_lines is None or nsample_lines >= len(lines):
-        sample = lines
-    else:
-        rng = np.random.default_rng(0)
-        idx = rng.choice(len(lines), size=nsample_lines, replace=False)
-        sample = [lines[i] for i in sorted(idx)]
-    total = 0.0
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        nl = c.nonlinear_spectral()
-        h = c.assemble(nl)
-        prev = h if c.hist is None else c.hist
-        H = tuple(1.5 * a - 0.5 * b for a, b in zip(h, prev))
-        r = c.rhs(H)
-        t1 = time.perf_counter()
-        for (j, m) in sample:
-            c.solve_line(j, m, r[0][:, j, m], r[1][:, j, m], r[2][:, j, m])
-        t2 = time.perf_counter()
-        total += (t1 - t0) + (t2 - t1) * len(lines) / len(sample)
-    pts = w["nx"] * w["ny"] * w["nz"]
-    return pts * steps / total / 1e6, total / steps, len(sample), len(lines)
+    return c
 
 
-def oracle_step_sample(c, nplanes, nlines, rng):
-    """One oracle step on a bounded sample, timed per part and scaled to the whole step.
+ORACLE_SAMPLE = dict(nplanes=1, nlines=16)
 
-    Non-linear terms: the oracle's own nonlinear_spectral on a copy of the channel whose
-    Chebyshev transform matrices keep `nplanes` random z-planes (rows of the backward matrix,
-    columns of the forward one), so the x-y transforms and products run on those planes only;
-    the parts that do not shrink with the planes (velocity recovery, d/dz) are timed on their own
-    and not scaled.  Assembly and right-hand sides: all lines.  Implicit solves: `nlines` random
-    lines, scaled to all lines.  Returns the estimated seconds of one full oracle step."""
+
+def oracle_sampled_step(c, rng, nplanes=1, nlines=16):
+    """One oracle step on a bounded sample of the workload, timed as it runs.
+
+    * non-linear terms: the oracle's own nonlinear_spectral on a copy of the channel whose
+      Chebyshev matrices keep `nplanes` random z-planes (rows of the backward matrix, columns of
+      the forward one): the velocity recovery runs on every line, the x-y transforms and products
+      on those planes only;
+    * assembly and right-hand sides (the oracle's assemble and rhs) on one random wavenumber row
+      (all kx of one ky);
+    * implicit solves (solve_lines) of `nlines` random lines of that row.
+    Returns (seconds, fraction): the sample's wall time and the smallest fraction of the full
+    step's work any part covered (planes / Nz, lines / all lines), which is what the sample is
+    credited with (an under-estimate of the work done)."""
     import copy
     import numpy as np
-    Nz = c.p.nz
+    Nz, Ny, Mx = c.p.nz, c.p.ny, c.Mx
     planes = np.sort(rng.choice(Nz, size=min(nplanes, Nz), replace=False))
+    j = int(rng.integers(1, Ny // 2))
+    ms = np.sort(rng.choice(np.arange(1, Mx), size=min(nlines, Mx - 1), replace=False))
+    t0 = time.perf_counter()
     s = copy.copy(c)
     s.Bm = c.Bm[planes]
     s.Fm = c.Fm[:, planes]
-    t0 = time.perf_counter()
-    uh, vh, wh = c.velocity_spectral()
-    c.dz(c.phi)
+    nl = s.nonlinear_spectral()
+    r = copy.copy(c)                     # the wavenumber row j as a one-row channel
+    r.iky = c.iky[:, [j], :]
+    r.k2 = c.k2[[j], :]
+    r.omega, r.w, r.phi = (a[:, [j], :] for a in (c.omega, c.w, c.phi))
+    h = r.assemble([a[:, [j], :] for a in nl])
+    H = h if c.hist is None else tuple(1.5 * a - 0.5 * b[:, [j], :] for a, b in zip(h, c.hist))
+    rr = r.rhs(H)
+    r.solve_lines([(0, int(m)) for m in ms], *rr)
     t1 = time.perf_counter()
-    s.nonlinear_spectral()
-    t2 = time.perf_counter()
-    nl = [np.zeros_like(c.phi) for _ in range(10)]     # shapes only: the values are not used
-    h = c.assemble(nl)
-    prev = h if c.hist is None else c.hist
-    H = tuple(1.5 * a - 0.5 * b for a, b in zip(h, prev))
-    r = c.rhs(H)
-    t3 = time.perf_counter()
-    lines = c.all_lines()
-    idx = rng.choice(len(lines), size=min(nlines, len(lines)), replace=False)
-    for i in idx:
-        j, m = lines[i]
-        c.solve_line(j, m, r[0][:, j, m], r[1][:, j, m], r[2][:, j, m])
-    t4 = time.perf_counter()
-    fixed = t1 - t0
-    nl_scaled = fixed + max(t2 - t1 - fixed, 0.0) * Nz / len(planes)
-    return nl_scaled + (t3 - t2) + (t4 - t3) * len(lines) / len(idx)
+    frac = min(len(planes) / Nz, len(ms) / len(c.all_lines()))
+    return t1 - t0, frac
 
 
-def run_reference(args, w):
-    """The CPU oracle (the reference arm) on the machine's host cores: each timed step is one oracle
-    step on a bounded sample (oracle_step_sample), so K steps stay within minutes."""
+def sample_note(w, nplanes, nlines):
+    return (f"per step: the oracle's non-linear terms on {nplanes} of {w['nz']} z-planes "
+            f"(velocity recovery on every line), assembly and right-hand sides of one "
+            f"wavenumber row, implicit solves of {nlines} of its lines; credited with the "
+            f"smallest fraction of the full step any part covered; numpy FP64 oracle, BLAS "
+            f"threads = host cores, FFTs single-threaded")
+
+
+def oracle_baseline(w, nsteps=2):
+    """cpu_baseline: the oracle on `nsteps` sampled steps of the workload (oracle_sampled_step).
+    Returns (Mpoints*step/s credited, seconds per sampled step, extrapolated seconds per full
+    step)."""
     import numpy as np
-    from oracle.channel import Channel, Params
-    from paper_2406_01322_gb300 import inputs
+    c = oracle_channel(w)
+    rng = np.random.default_rng(0)
+    pts = w["nx"] * w["ny"] * w["nz"]
+    tot, work = 0.0, 0.0
+    for _ in range(nsteps):
+        sec, frac = oracle_sampled_step(c, rng, **ORACLE_SAMPLE)
+        tot += sec
+        work += frac * pts
+    return work / tot / 1e6, tot / nsteps, tot / (work / pts)
+
+
+def run_reference(args, w, config):
+    """The CPU oracle (the reference arm) on the machine's host cores: each step (warm-up and timed)
+    is one sampled oracle step (oracle_sampled_step), so the whole run stays within minutes.
+    ms_per_step is the sampled step's measured time; value is the work credited to the samples
+    over that time; the extrapolated time of a full oracle step is a separate, labelled field."""
+    import numpy as np
     rank, world, _ = dist_env()
     if rank != 0:
         return
     cores = os.cpu_count()
-    p = Params(nx=w["nx"], ny=w["ny"], nz=w["nz"], re_tau=w["re_tau"], we=w["we"], ch=w["ch"],
-               pe=w["pe"], dt=w["dt"])
-    c = Channel(p)
-    c.set_fields(*inputs.initial_fields(**w))
+    c = oracle_channel(w)
     rng = np.random.default_rng(0)
-    nplanes, nlines = 3, 24
     for _ in range(args.warmup):
-        oracle_step_sample(c, nplanes, nlines, rng)
-    total = sum(oracle_step_sample(c, nplanes, nlines, rng) for _ in range(args.steps))
+        oracle_sampled_step(c, rng, **ORACLE_SAMPLE)
+    tot, fracs = 0.0, 0.0
+    for _ in range(args.steps):
+        sec, frac = oracle_sampled_step(c, rng, **ORACLE_SAMPLE)
+        tot += sec
+        fracs += frac
     pts = w["nx"] * w["ny"] * w["nz"]
-    t_step = total / max(1, args.steps)
-    val = pts / t_step / 1e6
+    val = fracs * pts / tot / 1e6
+    t_step = tot / max(1, args.steps)
     out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "impl": "reference",
-           "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]],
-                      "precision": "fp64"},
+           "data": "synthetic", "impl": "reference", "config": config,
+           "extrapolated_full_oracle_step_s": tot / fracs,
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"per step: the oracle's non-linear evaluation on "
-                                      f"{nplanes} of {w['nz']} z-planes (scaled), assembly and "
-                                      f"right-hand sides of all lines, implicit solves of "
-                                      f"{nlines} lines (scaled to all); numpy FP64 oracle"},
+                            "sample": sample_note(w, **ORACLE_SAMPLE)},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -707,22 +679,112 @@ def run_adjoint(args):
     print(json.dumps(out))
 
 
+def roofline_of(workload, w, prec, cheb, kms, steps, ms_step, names):
+    """Roofline of the dominant kernel of a timed run (kms: summed ms per kernel over `steps`
+    steps, in the order of `names`), the per-kernel times and shares, and the step-level HBM
+    fraction (the step's algorithmic bytes over its time, against the measured copy peak)."""
+    work = kernel_work(w, prec, cheb)
+    # the FFT method launches no tensor-core transforms: their timed entries are empty gaps
+    active = [i for i, n in enumerate(names) if cheb == "tc" or not n.startswith("cheb")]
+    if cheb != "tc":
+        work = {n: v for n, v in work.items() if not n.startswith("cheb")}
+    k = max(active, key=lambda i: kms[i])
+    name = names[k]
+    per_launch_ms = kms[k] / steps
+    fl, by = work[name]
+    hbm, hbm_kind = peaks()
+    traffic = traffic_bytes(workload, prec, name, cheb)
+    # float64 kernels (all of precision 0, the z kernels of every precision) are ALU-bound and
+    # measured against the float64 peak, the double-float x/y kernels (float64-accurate work on
+    # the float32 pipe) against the double-float rate of the float32 pipe, float32 kernels
+    # against HBM
+    fp64_like = (prec != 1) or name.startswith("z")
+    if prec == 2 and not name.startswith("z") and not name.startswith("cheb"):
+        ach = fl / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / DF_PEAK_TFLOPS, "traffic": traffic, "kernel": name,
+                "peak_kind": "double-float on the float32 pipe: 152 SMs x 128 lanes x 2.07 GHz / "
+                             "9.67 float32 instructions per float64-equivalent flop (nominal)"}
+    elif name.startswith("cheb"):
+        tpk, tpk_kind = tensor_peak()
+        ach = fl / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": tpk, "unit": "TFLOP/s",
+                "frac": ach / tpk, "traffic": traffic, "kernel": name, "peak_kind": tpk_kind}
+    elif fp64_like:
+        ach = fl / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": name,
+                "peak_kind": "float64 FMA pipe: 152 SMs x 2.07 GHz x 4 flop/clk (nominal)"}
+    else:
+        ach = by / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": traffic, "kernel": name, "peak_kind": f"{hbm_kind} copy bandwidth"}
+    roof["algorithmic_per_launch"] = {"flops": fl, "bytes": by}
+    ksum = sum(kms[i] for i in active)
+    roof["kernel_share"] = {names[i]: kms[i] / ksum for i in active}
+    roof["kernel_ms_per_step"] = {names[i]: kms[i] / steps for i in active}
+    step_bytes = sum(v[1] for v in work.values())
+    roof["step_algorithmic_bytes"] = step_bytes
+    roof["hbm_frac_step"] = (step_bytes / (ms_step * 1e-3) / 1e9) / hbm
+    return roof
+
+
+def precision_variants(binding, w, workload, fields, kw, steps, device, main):
+    """The same workload in the other precision modes and Chebyshev methods than the headline
+    run `main` = (precision, method): device time per step over `steps` steps (after 3 warm-up
+    steps) and the max relative field difference from the float64 FFT path after 3 + `steps`
+    steps from the same fields.  The float64 FFT step (the comparison base) also reports its
+    per-kernel times, its dominant kernel's roofline and its step-level HBM fraction."""
+    import torch
+    out, final = {}, {}
+    pts = w["nx"] * w["ny"] * w["nz"]
+    names = list(binding.Grid.KERNELS)
+    for pr, cheb in ((0, 0), (2, 0), (1, 0), (0, 1), (2, 1), (1, 1)):
+        g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=pr, device=device, **kw)
+        g.set_chebyshev(cheb)
+        g.set_fields(*[torch.from_numpy(f) for f in fields])
+        g.step(3)
+        tot, kms = g.step_timed(steps)
+        final[(pr, cheb)] = [f.cpu() for f in g.get_fields()]
+        g.close()
+        torch.cuda.empty_cache()
+        if (pr, cheb) == main:
+            continue
+        name = PREC_NAMES[pr] + ("_tc" if cheb else "")
+        dt = DTYPES[pr] + (" (Chebyshev transforms: exact-split bf16 tensor-core products, "
+                           "float64-accurate)" if cheb else "")
+        v = {"ms_per_step": tot / steps, "dtype": dt,
+             "value": pts * steps / (tot * 1e-3) / 1e6,
+             "max_rel_field_diff_vs_fp64": None if (pr, cheb) == (0, 0) else max(
+                 float((a - b).abs().max() / b.abs().max())
+                 for a, b in zip(final[(pr, cheb)], final[(0, 0)]))}
+        if (pr, cheb) == (0, 0):
+            v["roofline"] = roofline_of(workload, w, 0, "fft", kms, steps, tot / steps, names)
+        out[name] = v
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
                     help="timed steps (default 100; adjoint workload: gradients, default 5)")
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="channel_128x128x129")
+    ap.add_argument("--workload", default="channel_512x256x257_mixed")
     ap.add_argument("--precision", type=int, default=None,
                     help="0 fp64, 1 mixed (fp32 x/y), 2 double-float x/y")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the comparison against the FP64 path (precision 1 and 2)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the other precisions and Chebyshev methods of the same workload")
     ap.add_argument("--cheb", default="fft", choices=["fft", "tc"],
                     help="Chebyshev transforms of the step: N-point DCT-I in float64 (fft) or "
                          "the exact-split matrix product on the tensor cores (tc)")
+    ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                    help="run the workload's physics on another grid (smaller cases of the same "
+                         "kernels for profiling); the workload name then carries the grid")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 5 if args.workload == "channel_128x128x129_adjoint" else 100
@@ -735,9 +797,17 @@ def main():
         run_adjoint(args)
         return
     w = dict(inputs.WORKLOADS[args.workload])
+    if args.grid is not None:
+        w.update(nx=args.grid[0], ny=args.grid[1], nz=args.grid[2])
+        args.workload = f"{args.workload}@{args.grid[0]}x{args.grid[1]}x{args.grid[2]}"
     prec = w["precision"] if args.precision is None else args.precision
+    _, world0, _ = dist_env()
+    config = {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]],
+              "precision": PREC_NAMES[prec], "chebyshev": args.cheb,
+              "parallelism": "replicas" if world0 > 1 else "single",
+              "l2": "step working set larger than L2 (no flush)"}
     if args.impl == "reference":
-        run_reference(args, w)
+        run_reference(args, w, config)
         return
 
     import torch
@@ -791,48 +861,7 @@ def main():
 
     # ---- roofline of the dominant kernel
     names = list(binding.Grid.KERNELS)
-    work = kernel_work(w, prec, args.cheb)
-    # the FFT method launches no tensor-core transforms: their timed entries are empty gaps
-    active = [i for i, n in enumerate(names) if args.cheb == "tc" or not n.startswith("cheb")]
-    if args.cheb != "tc":
-        work = {n: v for n, v in work.items() if not n.startswith("cheb")}
-    k = max(active, key=lambda i: kms[i])
-    name = names[k]
-    per_launch_ms = kms[k] / args.steps
-    fl, by = work[name]
-    hbm, hbm_kind = peaks()
-    # float64 kernels (all of precision 0, the z kernels of every precision) are ALU-bound and
-    # measured against the float64 peak, the double-float x/y kernels (float64-accurate work on
-    # the float32 pipe) against the double-float rate of the float32 pipe, float32 kernels
-    # against HBM
-    fp64_like = (prec != 1) or name.startswith("z")
-    if prec == 2 and not name.startswith("z") and not name.startswith("cheb"):
-        ach = fl / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / DF_PEAK_TFLOPS,
-                "traffic": traffic_bytes(args.workload, prec, name, args.cheb), "kernel": name,
-                "peak_kind": "double-float on the float32 pipe: 152 SMs x 128 lanes x 2.07 GHz / "
-                             "9.67 float32 instructions per float64-equivalent flop (nominal)"}
-    elif name.startswith("cheb"):
-        tpk, tpk_kind = tensor_peak()
-        ach = fl / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": tpk, "unit": "TFLOP/s",
-                "frac": ach / tpk, "traffic": None, "kernel": name, "peak_kind": tpk_kind}
-    elif fp64_like:
-        ach = fl / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": traffic_bytes(args.workload, prec, name, args.cheb), "kernel": name,
-                "peak_kind": "float64 FMA pipe: 152 SMs x 2.07 GHz x 4 flop/clk (nominal)"}
-    else:
-        ach = by / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": traffic_bytes(args.workload, prec, name, args.cheb), "kernel": name,
-                "peak_kind": f"{hbm_kind} copy bandwidth"}
-    ksum = sum(kms[i] for i in active)
-    roof["kernel_share"] = {names[i]: kms[i] / ksum for i in active}
-    roof["kernel_ms_per_step"] = {names[i]: kms[i] / args.steps for i in active}
-    roof["hbm_frac_step"] = (sum(v[1] for v in work.values()) / (ms_step * 1e-3) / 1e9) / hbm
+    roof = roofline_of(args.workload, w, prec, args.cheb, kms, args.steps, ms_step, names)
 
     if rank != 0:
         g.close()
@@ -844,10 +873,7 @@ def main():
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": DTYPES[prec],
            "data": "synthetic",
-           "config": {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]],
-                      "precision": PREC_NAMES[prec], "chebyshev": args.cheb,
-                      "parallelism": "replicas" if world > 1 else "single",
-                      "l2": "step working set larger than L2 (no flush)"},
+           "config": config,
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": nbytes / args.steps,
                    "d2h_bytes_per_step": nbytes / args.steps,
                    "note": "set_fields_host + K steps + get_fields_host per job, bytes / K"},
@@ -855,18 +881,29 @@ def main():
            "roofline": roof,
            "clocks": clk.summary()}
     g.close()
-    if world == 1 and prec == 0 and args.precision is None and not args.no_accuracy:
-        out["variants"] = precision_variants(binding, w, fields, kw, args.steps, f"cuda:{local}")
+    torch.cuda.empty_cache()
+    dev = f"cuda:{local}"
+    if world == 1 and not args.no_variants:
+        out["variants"] = precision_variants(binding, w, args.workload, fields, kw, args.steps,
+                                             dev, (prec, 1 if args.cheb == "tc" else 0))
     if world == 1 and prec != 0 and not args.no_accuracy:
-        out[PREC_NAMES[prec] + "_vs_fp64"] = precision_accuracy(binding, w, fields, w["steps"],
-                                                                f"cuda:{local}", prec)
+        acc = precision_accuracy(binding, w, fields, w["steps"], dev, prec)
+        if prec == 1:
+            from paper_2406_01322_gb300.bounds import MIXED_BOUNDS
+            acc["bounds"] = MIXED_BOUNDS
+            acc["bounds_met"] = all(
+                [acc["rel_err"][n] <= MIXED_BOUNDS[n] for n in acc["rel_err"]]
+                + [abs(acc[k + "_rel_diff"]) <= MIXED_BOUNDS[k]
+                   for k in ("mass", "kinetic", "grad2", "free_energy")])
+        out[PREC_NAMES[prec] + "_vs_fp64"] = acc
     if world == 1:
         zc, xyc = cufft_transforms_ms(w, prec)
         ours_xy = sum(roof["kernel_ms_per_step"][n] for n in ("ybwd", "xline", "yfwd"))
         gm, gtf = dct_gemm_ms(w)
+        zrhs_ms = roof["kernel_ms_per_step"]["zrhs"]
         out["dct_as_gemm_comparison"] = {
             "fp64_gemm_ms_for_7_forward_dcts": gm, "fp64_gemm_tflops": gtf,
-            "ours_zrhs_ms": roof["kernel_ms_per_step"]["zrhs"],
+            "ours_zrhs_ms": zrhs_ms,
             "note": "the 7 forward DCTs of one step as one cuBLAS float64 GEMM, against our whole "
                     "zrhs kernel (7 DCTs + derivatives + assembly)"}
         out["cufft_comparison"] = {
@@ -876,12 +913,11 @@ def main():
             "note": "cuFFT (torch.fft) timed on the transforms of one step only (no products, "
                     "assembly or solves); ours_ybwd_xline_yfwd_ms also includes the products"}
     if world == 1 and not args.no_cpu_baseline:
-        nsample = max(64, (w["nx"] // 2) * w["ny"] // 64)
-        val, t_step, ns, nl = oracle_sample(w, nsample_lines=nsample, steps=1)
+        val, t_sample, t_full = oracle_baseline(w, nsteps=2)
         out["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": os.cpu_count(),
-                               "kind": "oracle",
-                               "sample": f"1 step: full non-linear evaluation + implicit solves "
-                                         f"of {ns} of {nl} lines, solve time scaled to all lines"}
+                               "kind": "oracle", "sample": sample_note(w, **ORACLE_SAMPLE),
+                               "seconds_per_sampled_step": t_sample,
+                               "extrapolated_full_oracle_step_s": t_full}
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
