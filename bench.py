@@ -237,9 +237,10 @@ DTYPES = {0: "f64", 1: "f32 transforms/products + f64 solves",
 
 def precision_accuracy(binding, w, fields, steps, device, prec=1):
     """Step of precision `prec` against the FP64 step from the same fields after `steps` steps:
-    per-field max relative difference (max |a - b| / max |b|), phi mass drift of each path
-    relative to the initial mass, and relative differences of kinetic energy, int |grad phi|^2
-    and free energy."""
+    per-field max relative difference (max |a - b| / max |b|; velocity_scale: the largest of
+    the velocity components' max |a - b| over max |u|), phi mass drift of each path relative to
+    the initial mass, and relative differences of the mass, kinetic energy, int |grad phi|^2 and
+    free energy."""
     import torch
     kw = dict(re_tau=w["re_tau"], we=w["we"], ch=w["ch"], pe=w["pe"], dt=w["dt"])
     out = {}
@@ -256,9 +257,12 @@ def precision_accuracy(binding, w, fields, steps, device, prec=1):
     (f64, d64, m64), (f32, d32, m32) = res[0], res[prec]
     out["rel_err"] = {n: float((a - b).abs().max() / b.abs().max())
                       for n, a, b in zip(("u", "v", "w", "phi"), f32, f64)}
+    umax = float(f64[0].abs().max())
+    out["rel_err"]["velocity_scale"] = max(float((a - b).abs().max()) / umax
+                                           for a, b in zip(f32[:3], f64[:3]))
     out["mass_drift_fp64"] = (d64["mass"] - m64) / abs(m64)
     out["mass_drift_" + PREC_NAMES[prec]] = (d32["mass"] - m32) / abs(m32)
-    for k in ("kinetic", "grad2", "free_energy"):
+    for k in ("mass", "kinetic", "grad2", "free_energy"):
         out[k + "_rel_diff"] = (d32[k] - d64[k]) / abs(d64[k])
     out["steps"] = steps
     return out
