@@ -90,6 +90,11 @@ def traffic_bytes(workload, prec, kernel, cheb="fft"):
     return None if v is None else v * 1e6
 
 
+# the float64 FMA rate measured on this device by the library's probe (ch_fp64_fma_rate), filled
+# in by main() before the rooflines are formed
+MEASURED_FMA = {}
+
+
 def tensor_peak():
     """Measured bf16 dense tensor peak (burst: the kernel is timed inside a short step)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -724,6 +729,9 @@ def roofline_of(workload, w, prec, cheb, kms, steps, ms_step, names):
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": traffic, "kernel": name, "peak_kind": f"{hbm_kind} copy bandwidth"}
     roof["algorithmic_per_launch"] = {"flops": fl, "bytes": by}
+    if roof["bound"] == "alu" and roof["peak"] == FP64_PEAK_TFLOPS and MEASURED_FMA.get("tflops"):
+        roof["fp64_fma_measured_tflops"] = MEASURED_FMA["tflops"]
+        roof["frac_of_measured_fma_rate"] = roof["achieved"] / MEASURED_FMA["tflops"]
     ksum = sum(kms[i] for i in active)
     roof["kernel_share"] = {names[i]: kms[i] / ksum for i in active}
     roof["kernel_ms_per_step"] = {names[i]: kms[i] / steps for i in active}
@@ -826,6 +834,7 @@ def main():
     if world > 1:
         dist.barrier()
     from paper_2406_01322_gb300 import binding
+    MEASURED_FMA["tflops"] = binding.fp64_fma_rate()
 
     fields = inputs.initial_fields(**dict(w, seed=w["seed"] + rank))
     kw = dict(re_tau=w["re_tau"], we=w["we"], ch=w["ch"], pe=w["pe"], dt=w["dt"])

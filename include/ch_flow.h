@@ -168,6 +168,15 @@ int ch_device_status(ch_grid* g);
  * CH_OK if the waits completed. */
 int ch_selftest_bounded_wait(int nwaits, int* spun);
 
+/* Measured float64 FMA rate of the current device (not in the paper; the denominator behind
+ * the float64 kernels' ALU roofline): a kernel of independent fused multiply-add chains (eight
+ * per thread; 16 CTAs of 8 warps per SM, two waves) timed with CUDA events after one warm-up
+ * launch;
+ * *tflops = 2 flops per FMA / time.  Synchronous, on the legacy default stream; allocates a
+ * small device buffer (the chains' results, so the compiler keeps them).  CH_ERR_ARG for a NULL
+ * pointer, CH_ERR_ALLOC / CH_ERR_CUDA if it cannot run. */
+int ch_fp64_fma_rate(double* tflops);
+
 /* As ch_step, but launched without the graph and bracketed by CUDA events on the stream: on
  * return (the stream is synchronised) kernel_ms[0..CH_STEP_KERNELS-1] hold the summed device
  * time of each of the step's kernels and *total_ms the time from the first launch to the end of

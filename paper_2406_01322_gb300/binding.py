@@ -102,6 +102,7 @@ _SIGS = {
     "ch_ensemble_autotune": (ctypes.c_int, [_P, ctypes.c_int]),
     "ch_ensemble_tuning": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "ch_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "ch_fp64_fma_rate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "ch_ensemble_set_chebyshev": (ctypes.c_int, [_P, ctypes.c_int]),
     "ch_ensemble_get_chebyshev": (ctypes.c_int, [_P]),
     "ch_ensemble_destroy": (None, [_P]),
@@ -175,6 +176,13 @@ def transform_forward_noalloc(phys, spec, stream=None):
             lib().ch_transform_forward_noalloc(nx, ny, nz, _ptr(phys), _ptr(spec),
                                                ctypes.c_void_p(s.cuda_stream)))
     return spec
+
+
+def fp64_fma_rate():
+    """Measured float64 FMA rate of the current device in TFLOP/s (ch_fp64_fma_rate)."""
+    v = ctypes.c_double()
+    _ck("ch_fp64_fma_rate", lib().ch_fp64_fma_rate(ctypes.byref(v)))
+    return v.value
 
 
 class TorchAllocator:

@@ -473,7 +473,7 @@ int ch_init_grid(const ch_params* p, ch_alloc_fn alloc, ch_free_fn free_fn, void
     g.fac = G->fac;
     if (chf::build_factor_table(g, G->fac, 0) != cudaSuccess) return bail(G, CH_ERR_CUDA);
   }
-  if (chf::zline_smem(g) > (size_t)kMaxSmem || (size_t)17 * g.Px * sizeof(double2) > (size_t)kMaxSmem) {
+  if (chf::zline_smem(g) > (size_t)kMaxSmem || chf::xline_smem(g.Px, sizeof(double2)) > (size_t)kMaxSmem) {
     return bail(G, CH_ERR_SIZE);
   }
   G->first = 1;
@@ -857,6 +857,40 @@ int ch_selftest_bounded_wait(int nwaits, int* spun) {
     st = CH_ERR_TIMEOUT;
   }
   if (spun) *spun = h[1];
+  cudaFree(d);
+  return st;
+}
+
+int ch_fp64_fma_rate(double* tflops) {
+  if (!tflops) return CH_ERR_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return CH_ERR_CUDA;
+  }
+  const int blocks = 16 * sms, iters = 4096;
+  double* d = nullptr;
+  if (cudaMalloc(&d, (size_t)blocks * 256 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return CH_ERR_ALLOC;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.0f;
+  int st = CH_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      chf::launch_fma_probe(d, blocks, iters, 0) != cudaSuccess ||
+      cudaEventRecord(e0, 0) != cudaSuccess ||
+      chf::launch_fma_probe(d, blocks, iters, 0) != cudaSuccess ||
+      cudaEventRecord(e1, 0) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.0f)) {
+    cudaGetLastError();
+    st = CH_ERR_CUDA;
+  } else {
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * 256.0 / (ms * 1e-3) / 1e12;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   cudaFree(d);
   return st;
 }

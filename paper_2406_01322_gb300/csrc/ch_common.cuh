@@ -203,25 +203,66 @@ template <typename T, bool INV> struct Dft<T, 8, INV> {
   }
 };
 
-// one Stockham pass of radix R over `nlines` lines of length n (line stride ls) in shared memory
+// q = t / d and t - q d for 0 <= t < 2^22, 0 < d, through a float estimate corrected once (the
+// estimate is within one of the quotient there); inv = 1 / d as a float
+__device__ __forceinline__ int fdivmod(int t, int d, float inv, int* rem) {
+  int q = __float2int_rz((float)t * inv);
+  int r = t - q * d;
+  if (r < 0) {
+    --q;
+    r += d;
+  } else if (r >= d) {
+    ++q;
+    r -= d;
+  }
+  *rem = r;
+  return q;
+}
+
+// Position of element e of a line in the skewed layout of the FFT's intermediate buffers: one
+// pad element after every 16.  A Stockham pass with small Ns writes its R outputs at a stride of
+// R elements; skewed, 16 consecutive threads of the first pass hit 16 different 8-byte bank
+// pairs (float32 complex: no conflict; 16-byte elements: two-way), where the plain layout puts
+// them on two.  Lines of the skewed buffers need n + ceil(n / 16) elements (fft_line_stride).
+__host__ __device__ __forceinline__ int fft_line_stride(int n) { return n + ((n + 15) >> 4); }
+
+// Line stride of the y pass's shared tiles: the tile is filled and drained with z (the line
+// index) fastest, so consecutive threads touch the same position of consecutive lines; a stride
+// of 4 modulo 16 elements spreads the 8-byte (float32 complex) and 16-byte (float64 and
+// double-float complex) elements of a warp over all banks with the fewest wavefronts.  The
+// smallest such stride that holds a skewed line.
+__host__ __device__ __forceinline__ int yline_stride(int P) {
+  const int m = fft_line_stride(P);
+  return m + ((20 - (m & 15)) & 15);
+}
+
+// one Stockham pass of radix R over `nlines` lines of length n (line stride ls) in shared memory;
+// ski / sko: the input / output lines are in the skewed layout
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void stockham_pass(const typename C2<T>::t* __restrict__ A,
                                               typename C2<T>::t* __restrict__ B, int nlines,
                                               int ls, int n, int Ns,
-                                              const typename C2<T>::t* __restrict__ tw) {
+                                              const typename C2<T>::t* __restrict__ tw, bool ski,
+                                              bool sko) {
   typedef typename C2<T>::t T2;
   const int nb = n / R;
   const int tot = nlines * nb;
   const int tws = n / (Ns * R);
+  const float inv_nb = 1.0f / (float)nb, inv_ns = 1.0f / (float)Ns;
+  const int mi = ski ? -1 : 0, mo = sko ? -1 : 0;
   for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-    const int line = t / nb;
-    const int j = t - line * nb;
+    int j;
+    const int line = fdivmod(t, nb, inv_nb, &j);
+    int k;
+    fdivmod(j, Ns, inv_ns, &k);
     const T2* in = A + line * ls;
     T2* out = B + line * ls;
-    const int k = j % Ns;
     T2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
+    for (int r = 0; r < R; ++r) {
+      const int e = j + r * nb;
+      v[r] = in[e + ((e >> 4) & mi)];
+    }
     if (k != 0) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -232,14 +273,18 @@ __device__ __forceinline__ void stockham_pass(const typename C2<T>::t* __restric
     Dft<T, R, INV>::run(v);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) {
+      const int e = base + r * Ns;
+      out[e + ((e >> 4) & mo)] = v[r];
+    }
   }
 }
 
 // Block-cooperative FFT of nlines lines (stride ls) held in A; B is a scratch buffer of the same
 // shape.  Returns the buffer holding the result (A or B).  Unnormalised; INV = exp(+).
-// Every thread of the block must call it (it contains __syncthreads()).
-template <typename T, bool INV>
+// Every thread of the block must call it (it contains __syncthreads()).  SKEW: the buffers
+// between passes use the skewed layout (ls >= fft_line_stride(n)); input and result are plain.
+template <typename T, bool INV, bool SKEW = false>
 __device__ typename C2<T>::t* block_fft(typename C2<T>::t* A, typename C2<T>::t* B, int nlines,
                                         int ls, const FftPlan& pl) {
   typedef typename C2<T>::t T2;
@@ -247,10 +292,11 @@ __device__ typename C2<T>::t* block_fft(typename C2<T>::t* A, typename C2<T>::t*
   int Ns = 1;
   for (int s = 0; s < pl.nst; ++s) {
     const int R = pl.rad[s];
-    if (R == 4) stockham_pass<T, 4, INV>(A, B, nlines, ls, pl.n, Ns, tw);
-    else if (R == 8) stockham_pass<T, 8, INV>(A, B, nlines, ls, pl.n, Ns, tw);
-    else if (R == 2) stockham_pass<T, 2, INV>(A, B, nlines, ls, pl.n, Ns, tw);
-    else stockham_pass<T, 3, INV>(A, B, nlines, ls, pl.n, Ns, tw);
+    const bool ski = SKEW && s > 0, sko = SKEW && s + 1 < pl.nst;
+    if (R == 4) stockham_pass<T, 4, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else if (R == 8) stockham_pass<T, 8, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else if (R == 2) stockham_pass<T, 2, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else stockham_pass<T, 3, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
     __syncthreads();
     T2* tmp = A;
     A = B;

@@ -58,9 +58,9 @@ size_t stage_smem(int stage, const Member& m, int prec) {
     case 0:
     case 2: return zline_smem(m.g);
     case 1: return m.zsolve_tile ? zsolve_tile_smem(m.g) : 0;
-    case 3: return (size_t)2 * m.tzb * m.g.Py * elem;
+    case 3: return ysmem_bytes(m.g.Py, m.tzb, elem);
     case 4: return xline_smem(m.g.Px, elem);
-    default: return (size_t)2 * m.tzf * m.g.Py * elem;
+    default: return ysmem_bytes(m.g.Py, m.tzf, elem);
   }
 }
 

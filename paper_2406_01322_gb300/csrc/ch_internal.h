@@ -151,6 +151,10 @@ size_t stage_smem(int stage, const Member& m, int prec);
 int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile, int coef);
 // y-pass z tile for a padded length P (shared by single-grid and grouped launches)
 int ytile_for(int P, size_t elem);
+// shared memory of a y-pass CTA: two tiles of tz lines of yline_stride(P) elements
+inline size_t ysmem_bytes(int P, int tz, size_t elem) {
+  return (size_t)2 * tz * yline_stride(P) * elem;
+}
 // x-line shared memory for a padded length Px
 size_t xline_smem(int Px, size_t elem);
 
@@ -233,5 +237,8 @@ cudaError_t launch_cheb_tc(int tin, int tout, const void* in, long long fsi, voi
                            cudaStream_t s);
 // one bounded mbarrier wait that runs out on purpose (sets *err |= 1 after the wait bound)
 cudaError_t launch_wait_selftest(int* err, int nwaits, cudaStream_t s);
+// float64 FMA-rate probe: `blocks` CTAs of 256 threads, `iters` iterations of eight independent
+// FMA chains per thread; out[blocks * 256] receives each thread's sum
+cudaError_t launch_fma_probe(double* out, int blocks, int iters, cudaStream_t s);
 
 }  // namespace chf

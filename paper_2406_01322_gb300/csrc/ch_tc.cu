@@ -794,6 +794,29 @@ __global__ void __launch_bounds__(32) wait_selftest_kernel(int* __restrict__ err
   atomicAdd(&err[1], spun);
 }
 
+// Eight independent float64 FMA chains per thread (enough to cover the pipe's latency): x <- x
+// a + b with |a| < 1, so the values stay bounded; the sum is stored so nothing is dead code.
+__global__ void __launch_bounds__(256) fma_probe_kernel(double* __restrict__ out, int iters) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = 1e-3 * (t + i);
+  const double a = 0.999999, b = 1e-6;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[t] = s;
+}
+
+cudaError_t launch_fma_probe(double* out, int blocks, int iters, cudaStream_t s) {
+  fma_probe_kernel<<<blocks, 256, 0, s>>>(out, iters);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_wait_selftest(int* err, int nwaits, cudaStream_t s) {
   wait_selftest_kernel<<<1, 32, 0, s>>>(err, nwaits);
   return cudaGetLastError();

@@ -28,8 +28,9 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
                                            const YMap& map, int bx, int by, int bz) {
   typedef typename C2<T>::t T2;
   extern __shared__ unsigned char ysm_raw[];
+  const int LS = yline_stride(P);
   T2* A = reinterpret_cast<T2*>(ysm_raw);
-  T2* B = A + TZ * P;
+  T2* B = A + TZ * LS;
   const int z0 = bx * TZ;
   const int mx = by;
   const int f = bz;                  // output field
@@ -48,28 +49,28 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
         v = mk(-ky * v.y, ky * v.x);
       }
       const int p = (jj < h) ? jj : P - Ny + jj;
-      A[zz * P + p] = v;
+      A[zz * LS + p] = v;
     }
     for (int idx = threadIdx.x; idx < (P - Ny) * TZ; idx += blockDim.x) {
       const int q = idx / TZ, zz = idx - q * TZ;
-      A[zz * P + h + q] = zero;  // positions h .. P-h-1 hold no mode
+      A[zz * LS + h + q] = zero;  // positions h .. P-h-1 hold no mode
     }
   } else {
     const T2* src = in + map.src[f] * fs_in + (size_t)mx * P * Nz;
     for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
       const int y = idx / TZ, zz = idx - y * TZ;
       const int z = z0 + zz;
-      A[zz * P + y] = (z < Nz) ? src[(size_t)y * Nz + z] : zero;
+      A[zz * LS + y] = (z < Nz) ? src[(size_t)y * Nz + z] : zero;
     }
   }
   __syncthreads();
-  const T2* R = block_fft<T, INV>(A, B, TZ, P, pl);
+  const T2* R = block_fft<T, INV, true>(A, B, TZ, LS, pl);
   if (INV) {
     T2* dst = out + f * fs_out + (size_t)mx * P * Nz;
     for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
       const int y = idx / TZ, zz = idx - y * TZ;
       const int z = z0 + zz;
-      if (z < Nz) dst[(size_t)y * Nz + z] = R[zz * P + y];
+      if (z < Nz) dst[(size_t)y * Nz + z] = R[zz * LS + y];
     }
   } else {
     T2* dst = out + f * fs_out + (size_t)mx * Ny * Nz;
@@ -78,7 +79,7 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
       const int z = z0 + zz;
       if (z >= Nz) continue;
       const int p = (jj < h) ? jj : P - Ny + jj;
-      dst[(size_t)jj * Nz + z] = (jj == h) ? zero : scale * R[zz * P + p];
+      dst[(size_t)jj * Nz + z] = (jj == h) ? zero : scale * R[zz * LS + p];
     }
   }
 }
@@ -111,6 +112,7 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
   typedef typename C2<T>::t T2;
   extern __shared__ unsigned char xsm_raw[];
   T2* S = reinterpret_cast<T2*>(xsm_raw);
+  const int LS = fft_line_stride(Px);   // line stride: room for the FFT's skewed intermediates
   const int z0 = 2 * bx;
   const int y = by;
   const bool two = (z0 + 1 < Nz);
@@ -120,7 +122,7 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
   // Start in S[0..6] for an even number of passes, in S[7..13] for an odd number, so that the
   // seven physical lines always end in S[0..6] and S[7..16] (ten lines) are free afterwards.
   T2* X = S;
-  T2* Y = S + 7 * Px;
+  T2* Y = S + 7 * LS;
   T2* L0 = (pl.nst & 1) ? Y : X;
   // ---- 1. packed spectra: lines u v w phi phi_x phi_y phi_z
   for (int idx = threadIdx.x; idx < 7 * Mx; idx += blockDim.x) {
@@ -134,7 +136,7 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
       a = mk(-kx * a.y, kx * a.x);
       b = mk(-kx * b.y, kx * b.x);
     }
-    T2* L = L0 + f * Px;
+    T2* L = L0 + f * LS;
     if (m == 0) {
       L[0] = mk(a.x, b.x);  // the imaginary part of a DC coefficient is not used by c2r
     } else {
@@ -146,41 +148,41 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
     const int w = Px - 2 * Mx + 1;  // kx = Mx .. Px - Mx carry no mode
     for (int idx = threadIdx.x; idx < 7 * w; idx += blockDim.x) {
       const int f = idx / w, q = idx - f * w;
-      L0[f * Px + Mx + q] = zero;
+      L0[f * LS + Mx + q] = zero;
     }
   }
   __syncthreads();
-  const T2* in7 = block_fft<T, true>(L0, (L0 == X) ? Y : X, 7, Px, pl);  // == X
-  T2* prod = S + 7 * Px;   // five product lines
-  T2* scr = S + 12 * Px;   // five scratch lines
+  const T2* in7 = block_fft<T, true, true>(L0, (L0 == X) ? Y : X, 7, LS, pl);  // == X
+  T2* prod = S + 7 * LS;   // five product lines
+  T2* scr = S + 12 * LS;   // five scratch lines
   for (int g0 = 0; g0 < 9; g0 += 5) {
     const int cnt = (g0 == 0) ? 5 : 4;
     // ---- 2. products for outputs g0 .. g0+cnt-1 (rows z0 in .x, z0+1 in .y)
     for (int x = threadIdx.x; x < Px; x += blockDim.x) {
-      const T2 u = in7[x], v = in7[Px + x], w = in7[2 * Px + x], ph = in7[3 * Px + x];
-      const T2 fx = in7[4 * Px + x], fy = in7[5 * Px + x], fz = in7[6 * Px + x];
+      const T2 u = in7[x], v = in7[LS + x], w = in7[2 * LS + x], ph = in7[3 * LS + x];
+      const T2 fx = in7[4 * LS + x], fy = in7[5 * LS + x], fz = in7[6 * LS + x];
       if (g0 == 0) {
         const T2 wz = mk(w.x * w.x + kappa * fz.x * fz.x, w.y * w.y + kappa * fz.y * fz.y);
         prod[x] = mk(wz.x - u.x * u.x - kappa * fx.x * fx.x, wz.y - u.y * u.y - kappa * fx.y * fx.y);
-        prod[Px + x] = mk(wz.x - v.x * v.x - kappa * fy.x * fy.x, wz.y - v.y * v.y - kappa * fy.y * fy.y);
-        prod[2 * Px + x] = mk(-u.x * v.x - kappa * fx.x * fy.x, -u.y * v.y - kappa * fx.y * fy.y);
-        prod[3 * Px + x] = mk(-u.x * w.x - kappa * fx.x * fz.x, -u.y * w.y - kappa * fx.y * fz.y);
-        prod[4 * Px + x] = mk(-v.x * w.x - kappa * fy.x * fz.x, -v.y * w.y - kappa * fy.y * fz.y);
+        prod[LS + x] = mk(wz.x - v.x * v.x - kappa * fy.x * fy.x, wz.y - v.y * v.y - kappa * fy.y * fy.y);
+        prod[2 * LS + x] = mk(-u.x * v.x - kappa * fx.x * fy.x, -u.y * v.y - kappa * fx.y * fy.y);
+        prod[3 * LS + x] = mk(-u.x * w.x - kappa * fx.x * fz.x, -u.y * w.y - kappa * fx.y * fz.y);
+        prod[4 * LS + x] = mk(-v.x * w.x - kappa * fy.x * fz.x, -v.y * w.y - kappa * fy.y * fz.y);
       } else {
         prod[x] = mk(ph.x * ph.x * ph.x, ph.y * ph.y * ph.y);
-        prod[Px + x] = mk(u.x * ph.x, u.y * ph.y);
-        prod[2 * Px + x] = mk(v.x * ph.x, v.y * ph.y);
-        prod[3 * Px + x] = mk(w.x * ph.x, w.y * ph.y);
+        prod[LS + x] = mk(u.x * ph.x, u.y * ph.y);
+        prod[2 * LS + x] = mk(v.x * ph.x, v.y * ph.y);
+        prod[3 * LS + x] = mk(w.x * ph.x, w.y * ph.y);
       }
     }
     __syncthreads();
-    const T2* R = block_fft<T, false>(prod, scr, cnt, Px, pl);
+    const T2* R = block_fft<T, false, true>(prod, scr, cnt, LS, pl);
     // ---- 3. unpack: A_k = (Z_k + conj Z_{-k}) / 2, B_k = (Z_k - conj Z_{-k}) / (2 i)
     const T hs = (T)0.5 * scale;
     for (int idx = threadIdx.x; idx < cnt * Mx; idx += blockDim.x) {
       const int q = idx / Mx, m = idx - q * Mx;
-      const T2 Zk = R[q * Px + m];
-      const T2 Zm = R[q * Px + (m == 0 ? 0 : Px - m)];
+      const T2 Zk = R[q * LS + m];
+      const T2 Zm = R[q * LS + (m == 0 ? 0 : Px - m)];
       T2* dst = out + (g0 + q) * fs + (size_t)m * mstride + base;
       dst[0] = mk(hs * (Zk.x + Zm.x), hs * (Zk.y - Zm.y));
       if (two) dst[1] = mk(hs * (Zk.y + Zm.y), hs * (Zm.x - Zk.x));
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(XT) adj_xline_kernel(const double2* __restrict
 int ytile_local(int P, size_t elem) {
   // z tile: 8 columns (128 B of fp64 complex), fewer when the lines are long
   int tz = 8;
-  while (tz > 1 && (size_t)2 * tz * P * elem > 160 * 1024) tz /= 2;
+  while (tz > 1 && ysmem_bytes(P, tz, elem) > 160 * 1024) tz /= 2;
   return tz;
 }
 
@@ -467,7 +469,7 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
   map.kys = 6.283185307179586476925 / g.ly;
   const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);
   const int TZ = ytile_local(P, elem);
-  const size_t smem = (size_t)2 * TZ * P * elem;
+  const size_t smem = ysmem_bytes(P, TZ, elem);
   dim3 grid((g.nz + TZ - 1) / TZ, g.Mx, nf);
   static SmemLimit cur[6];
   cudaError_t e = cudaSuccess;
@@ -495,7 +497,7 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
 cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out10, long long fs,
                          double scale, const FftPlan& px, cudaStream_t s) {
   const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);
-  const size_t smem = (size_t)17 * g.Px * elem;
+  const size_t smem = xline_smem(g.Px, elem);
   dim3 grid((g.nz + 1) / 2, g.Py);
   static SmemLimit cur64, cur32, curdf;
   cudaError_t e = prec == 0 ? ensure_smem(xline_kernel<double>, smem, &cur64)
@@ -554,7 +556,7 @@ cudaError_t launch_x_c2r(const GridDev& g, const double2* in, double* phys, int 
 namespace chf {
 
 int ytile_for(int P, size_t elem) { return ytile_local(P, elem); }
-size_t xline_smem(int Px, size_t elem) { return (size_t)17 * Px * elem; }
+size_t xline_smem(int Px, size_t elem) { return (size_t)17 * fft_line_stride(Px) * elem; }
 
 cudaError_t launch_grouped_xy(int stage, int prec, const Member* mem, const int* begin, int nmem,
                               int grid, size_t smem, cudaStream_t s) {
