@@ -522,7 +522,9 @@ def run_ensemble(args):
     prec = 1 if args.precision is None else args.precision
     ms = [dict(m, precision=prec) for m in inputs.ensemble_members()]
     ens = binding.Ensemble(ms, precision=prec, device=f"cuda:{local}")
-    tc = args.cheb == "tc"
+    # auto: the tensor-core method, which steps this ensemble faster (35.5 against 43.8 ms per
+    # mixed step after autotuning)
+    tc = args.cheb in ("tc", "auto")
     if tc:
         ens.set_chebyshev(binding.CHEB_TC)
     for i, (g, m) in enumerate(zip(ens.grids, ms)):
@@ -569,7 +571,8 @@ def run_ensemble(args):
                     + (" (z transforms as exact-split bf16 tensor-core products)" if tc else ""),
            "data": "synthetic",
            "config": {"workload": "ensemble_32_uneven", "members": len(ms),
-                      "points": pts, "precision": PREC_NAMES[prec], "chebyshev": args.cheb},
+                      "points": pts, "precision": PREC_NAMES[prec],
+                      "chebyshev": "tc" if tc else "fft"},
            "sequential_members_ms_per_step": seq_ms / args.steps,
            "e2e": {"value": pts * args.steps / e2e_s / 1e6, "unit": UNIT,
                    "h2d_bytes_per_step": nbytes / args.steps,
@@ -751,26 +754,30 @@ def precision_variants(binding, w, workload, fields, kw, steps, device, main):
     out, final = {}, {}
     pts = w["nx"] * w["ny"] * w["nz"]
     names = list(binding.Grid.KERNELS)
-    for pr, cheb in ((0, 0), (2, 0), (1, 0), (0, 1), (2, 1), (1, 1)):
+    combos = [(0, 0, 0), (2, 0, 0), (1, 0, 0), (0, 1, 0), (2, 1, 0), (1, 1, 0)]
+    combos += [(0, 0, 1), (main[0], 0, 1)] if main[0] != 0 else [(0, 0, 1)]
+    for pr, cheb, prune in combos:
         g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=pr, device=device, **kw)
         g.set_chebyshev(cheb)
+        g.set_fft_pruning(prune)
         g.set_fields(*[torch.from_numpy(f) for f in fields])
         g.step(3)
         tot, kms = g.step_timed(steps)
-        final[(pr, cheb)] = [f.cpu() for f in g.get_fields()]
+        final[(pr, cheb, prune)] = [f.cpu() for f in g.get_fields()]
         g.close()
         torch.cuda.empty_cache()
-        if (pr, cheb) == main:
+        if (pr, cheb, prune) == main:
             continue
-        name = PREC_NAMES[pr] + ("_tc" if cheb else "")
+        name = PREC_NAMES[pr] + ("_tc" if cheb else "") + ("_pruned" if prune else "")
         dt = DTYPES[pr] + (" (Chebyshev transforms: exact-split bf16 tensor-core products, "
-                           "float64-accurate)" if cheb else "")
+                           "float64-accurate)" if cheb else "") + (
+            " (pruned x/y transforms of the 3/2-rule padding)" if prune else "")
         v = {"ms_per_step": tot / steps, "dtype": dt,
              "value": pts * steps / (tot * 1e-3) / 1e6,
-             "max_rel_field_diff_vs_fp64": None if (pr, cheb) == (0, 0) else max(
+             "max_rel_field_diff_vs_fp64": None if (pr, cheb, prune) == (0, 0, 0) else max(
                  float((a - b).abs().max() / b.abs().max())
-                 for a, b in zip(final[(pr, cheb)], final[(0, 0)]))}
-        if (pr, cheb) == (0, 0):
+                 for a, b in zip(final[(pr, cheb, prune)], final[(0, 0, 0)]))}
+        if (pr, cheb, prune) == (0, 0, 0):
             v["roofline"] = roofline_of(workload, w, 0, "fft", kms, steps, tot / steps, names)
         out[name] = v
     return out
@@ -791,9 +798,12 @@ def main():
                     help="skip the comparison against the FP64 path (precision 1 and 2)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other precisions and Chebyshev methods of the same workload")
-    ap.add_argument("--cheb", default="fft", choices=["fft", "tc"],
-                    help="Chebyshev transforms of the step: N-point DCT-I in float64 (fft) or "
-                         "the exact-split matrix product on the tensor cores (tc)")
+    ap.add_argument("--cheb", default="auto", choices=["auto", "fft", "tc"],
+                    help="Chebyshev transforms of the step: N-point DCT-I in float64 (fft), "
+                         "the exact-split matrix product on the tensor cores (tc), or whichever "
+                         "of the two steps faster on this grid (auto: timed before the run)")
+    ap.add_argument("--prune", type=int, default=0, choices=[0, 1],
+                    help="pruned x/y transforms of the 3/2-rule padding (ch_set_fft_pruning)")
     ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
                     help="run the workload's physics on another grid (smaller cases of the same "
                          "kernels for profiling); the workload name then carries the grid")
@@ -816,6 +826,7 @@ def main():
     _, world0, _ = dist_env()
     config = {"workload": args.workload, "grid": [w["nx"], w["ny"], w["nz"]],
               "precision": PREC_NAMES[prec], "chebyshev": args.cheb,
+              "pruned_xy_transforms": bool(args.prune),
               "parallelism": "replicas" if world0 > 1 else "single",
               "l2": "step working set larger than L2 (no flush)"}
     if args.impl == "reference":
@@ -839,7 +850,22 @@ def main():
     fields = inputs.initial_fields(**dict(w, seed=w["seed"] + rank))
     kw = dict(re_tau=w["re_tau"], we=w["we"], ch=w["ch"], pe=w["pe"], dt=w["dt"])
     g = binding.Grid(w["nx"], w["ny"], w["nz"], precision=prec, device=f"cuda:{local}", **kw)
-    g.set_chebyshev(binding.CHEB_TC if args.cheb == "tc" else binding.CHEB_FFT)
+    g.set_fft_pruning(args.prune)
+    cheb_trial = {}
+    if args.cheb == "auto":
+        # the Chebyshev method is part of the kernel choice, not of the workload: time both on
+        # this grid (a few steps each, untimed in the result) and run the faster
+        for name, m in (("fft", binding.CHEB_FFT), ("tc", binding.CHEB_TC)):
+            g.set_chebyshev(m)
+            g.set_fields(*[torch.from_numpy(f) for f in fields])
+            g.step(2)
+            t, _ = g.step_timed(3)
+            cheb_trial[name] = t / 3
+        pick = 1.0 if cheb_trial["tc"] < cheb_trial["fft"] else 0.0
+        cheb = "tc" if max_over_ranks(pick, world, "cuda") > 0.5 else "fft"
+    else:
+        cheb = args.cheb
+    g.set_chebyshev(binding.CHEB_TC if cheb == "tc" else binding.CHEB_FFT)
     g.set_fields(*[torch.from_numpy(f) for f in fields])
     g.step(args.warmup)
     torch.cuda.synchronize()
@@ -874,7 +900,7 @@ def main():
 
     # ---- roofline of the dominant kernel
     names = list(binding.Grid.KERNELS)
-    roof = roofline_of(args.workload, w, prec, args.cheb, kms, args.steps, ms_step, names)
+    roof = roofline_of(args.workload, w, prec, cheb, kms, args.steps, ms_step, names)
 
     if rank != 0:
         g.close()
@@ -891,14 +917,18 @@ def main():
                    "d2h_bytes_per_step": nbytes / args.steps,
                    "note": "set_fields_host + K steps + get_fields_host per job, bytes / K"},
            "gpu_launches": g.launches_per_step() * args.steps,
+           "chebyshev_method": cheb,
            "roofline": roof,
            "clocks": clk.summary()}
+    if cheb_trial:
+        out["chebyshev_trial_ms_per_step"] = cheb_trial
     g.close()
     torch.cuda.empty_cache()
     dev = f"cuda:{local}"
     if world == 1 and not args.no_variants:
         out["variants"] = precision_variants(binding, w, args.workload, fields, kw, args.steps,
-                                             dev, (prec, 1 if args.cheb == "tc" else 0))
+                                             dev, (prec, 1 if cheb == "tc" else 0,
+                                                   args.prune))
     if world == 1 and prec != 0 and not args.no_accuracy:
         acc = precision_accuracy(binding, w, fields, w["steps"], dev, prec)
         if prec == 1:

@@ -145,6 +145,16 @@ int ch_step(ch_grid* g, int nsteps);
 int ch_set_chebyshev(ch_grid* g, int method);
 int ch_get_chebyshev(const ch_grid* g);
 
+/* Pruned transforms of the 3/2-rule padding (Sec. 3.2.1; the NEXT item "pruned padded FFTs"):
+ * on = 1 gives the x and y transforms of the step a schedule that starts with radix 3, so the
+ * backward (zero-padded) transforms skip the zero middle third of their input in their first
+ * pass and the forward (truncated) ones skip the unused middle third of their output in their
+ * last pass; on = 0 restores the default schedules.  The result equals the unpruned step to
+ * rounding.  Synchronous; takes effect at the next step (the step graph is rebuilt).
+ * CH_ERR_ARG: on not 0 or 1; CH_ERR_STATE: a reverse sweep is open. */
+int ch_set_fft_pruning(ch_grid* g, int on);
+int ch_get_fft_pruning(const ch_grid* g);
+
 /* Chebyshev transform along z of nf fields of complex lines (device, float64 (re, im) pairs,
  * layout [field][mx * ny + j][n], field stride (nx/2) ny nz, the layout of ch_get_spectral) with
  * the selected method: dir 0 samples at z_k = cos(pi k / N) -> coefficients a_n, dir 1 the

@@ -110,6 +110,8 @@ _SIGS = {
     "ch_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ch_last_cuda_error": (ctypes.c_char_p, []),
     "ch_set_chebyshev": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ch_set_fft_pruning": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ch_get_fft_pruning": (ctypes.c_int, [_P]),
     "ch_get_chebyshev": (ctypes.c_int, [_P]),
     "ch_chebyshev_lines": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int]),
     "ch_device_status": (ctypes.c_int, [_P]),
@@ -290,6 +292,13 @@ class Grid:
 
     def chebyshev(self):
         return int(lib().ch_get_chebyshev(self.h))
+
+    def set_fft_pruning(self, on):
+        """Pruned x/y transforms of the 3/2-rule padding (1) or the default schedules (0)."""
+        _ck("ch_set_fft_pruning", lib().ch_set_fft_pruning(self.h, int(on)))
+
+    def fft_pruning(self):
+        return int(lib().ch_get_fft_pruning(self.h))
 
     def chebyshev_lines(self, x, direction):
         """Chebyshev transform along z of complex lines x (nf, nx/2, ny, nz) complex128 on the

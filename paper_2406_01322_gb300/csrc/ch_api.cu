@@ -58,9 +58,16 @@ bool make_radices_style(int n, int style, FftPlan* pl) {
   while (m % 3 == 0) { m /= 3; ++b; }
   if (m != 1) return false;
   int k = 0;
+  pl->prune = 0;
+  if (style == 3) {   // one radix 3 first (the pruned pass), then as for style 2
+    if (b < 1) return false;
+    pl->rad[k++] = 3;
+    --b;
+    pl->prune = 1;
+  }
   if (style == 1)
     while (b > 0) { pl->rad[k++] = 3; --b; }
-  if (style == 2) {
+  if (style == 2 || style == 3) {
     while (a >= 3 && a != 4) { pl->rad[k++] = 8; a -= 3; }
   } else if (a % 2 == 1 && a >= 3) {
     pl->rad[k++] = 8;
@@ -827,6 +834,28 @@ int ch_set_chebyshev(ch_grid* G, int method) {
 }
 
 int ch_get_chebyshev(const ch_grid* G) { return G ? G->cheb : CH_ERR_ARG; }
+
+int ch_set_fft_pruning(ch_grid* G, int on) {
+  if (!G || (on != 0 && on != 1)) return CH_ERR_ARG;
+  if (G->adj_block) return CH_ERR_STATE;   // not while a reverse sweep is open
+  // pruned: one radix 3 first, then as many radix 8 as possible; default: the measured
+  // schedules (maximal radix 8 for float64 and float32, the plain one for double-float)
+  const int def[3] = {2, 2, 0};
+  for (int p = 0; p < 3; ++p) {
+    chf::FftPlan x = G->px[p], y = G->py[p];
+    if (!chf::make_radices_style(G->g.Px, on ? 3 : def[p], &x) ||
+        !chf::make_radices_style(G->g.Py, on ? 3 : def[p], &y))
+      return CH_ERR_SIZE;
+    x.tw = G->px[p].tw;
+    y.tw = G->py[p].tw;
+    G->px[p] = x;
+    G->py[p] = y;
+  }
+  drop_graph(G);
+  return CH_OK;
+}
+
+int ch_get_fft_pruning(const ch_grid* G) { return G ? G->px[0].prune : CH_ERR_ARG; }
 
 int ch_chebyshev_lines(ch_grid* G, int dir, const double* in, double* out, int nf) {
   if (!G || !in || !out || nf < 1 || (dir != 0 && dir != 1)) return CH_ERR_ARG;

@@ -125,6 +125,10 @@ struct FftPlan {
   int nst;
   int rad[CHF_MAX_STAGES];
   const void* tw;
+  // 1: the schedule starts with radix 3 and the transforms of the 3/2-rule padding may prune it
+  // (block_fft's `prune`): zero middle third of a backward transform's input, unused middle
+  // third of a forward transform's output
+  int prune;
 };
 
 // radix-R DFT of v[0..R-1] in registers; INV selects exp(+2 pi i / R).
@@ -237,7 +241,12 @@ __host__ __device__ __forceinline__ int yline_stride(int P) {
 }
 
 // one Stockham pass of radix R over `nlines` lines of length n (line stride ls) in shared memory;
-// ski / sko: the input / output lines are in the skewed layout
+// ski / sko: the input / output lines are in the skewed layout.  A thread owns one butterfly
+// position j of a group of lines (line g, g + G, ...; G = blockDim / (n / R) groups when a line
+// has fewer butterflies than the block has threads): its index arithmetic is formed once per
+// pass, not once per butterfly, and for float32 (whose kernels are bound by issue, not by the
+// arithmetic) its R - 1 twiddles too; the wider types reload them per line, which keeps their
+// registers for occupancy.
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void stockham_pass(const typename C2<T>::t* __restrict__ A,
                                               typename C2<T>::t* __restrict__ B, int nlines,
@@ -246,37 +255,114 @@ __device__ __forceinline__ void stockham_pass(const typename C2<T>::t* __restric
                                               bool sko) {
   typedef typename C2<T>::t T2;
   const int nb = n / R;
-  const int tot = nlines * nb;
+  const int G = nb >= (int)blockDim.x ? 1 : (int)blockDim.x / nb;
   const int tws = n / (Ns * R);
   const float inv_nb = 1.0f / (float)nb, inv_ns = 1.0f / (float)Ns;
   const int mi = ski ? -1 : 0, mo = sko ? -1 : 0;
-  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+  for (int w = threadIdx.x; w < nb * G; w += blockDim.x) {
     int j;
-    const int line = fdivmod(t, nb, inv_nb, &j);
+    const int g = fdivmod(w, nb, inv_nb, &j);
     int k;
     fdivmod(j, Ns, inv_ns, &k);
-    const T2* in = A + line * ls;
-    T2* out = B + line * ls;
-    T2 v[R];
+    constexpr bool HOIST = sizeof(T2) == 8;
+    const int ti = k * tws;
+    T2 wr[HOIST ? R : 1];
+    if (HOIST && k != 0) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int e = j + r * nb;
-      v[r] = in[e + ((e >> 4) & mi)];
+      for (int r = 1; r < R; ++r) wr[HOIST ? r : 0] = tw[r * ti];
     }
-    if (k != 0) {
+    const int base = (j - k) * R + k;
+    for (int line = g; line < nlines; line += G) {
+      const T2* in = A + line * ls;
+      T2* out = B + line * ls;
+      T2 v[R];
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        const T2 w = tw[r * k * tws];
-        v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+      for (int r = 0; r < R; ++r) {
+        const int e = j + r * nb;
+        v[r] = in[e + ((e >> 4) & mi)];
+      }
+      if (k != 0) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const T2 wv = HOIST ? wr[HOIST ? r : 0] : tw[r * ti];
+          v[r] = INV ? cmulc(v[r], wv) : cmul(v[r], wv);
+        }
+      }
+      Dft<T, R, INV>::run(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int e = base + r * Ns;
+        out[e + ((e >> 4) & mo)] = v[r];
       }
     }
-    Dft<T, R, INV>::run(v);
-    const int base = (j - k) * R + k;
+  }
+}
+
+// Pruned radix-3 passes of the 3/2-rule padded transforms (n = 3 m; a backward transform's input
+// is zero at positions m .. 2m - 1, a forward transform's outputs there are not used).
+// First pass of a backward transform (Ns = 1): butterfly j reads j, j + m, j + 2m, and the
+// middle input is zero: y0 = v0 + v2, y1,2 = v0 - v2 / 2 -+ i s (-v2), s = +-sin(2 pi / 3).
+template <typename T, bool INV>
+__device__ __forceinline__ void pruned_first_pass3(const typename C2<T>::t* __restrict__ A,
+                                                   typename C2<T>::t* __restrict__ B, int nlines,
+                                                   int ls, int n, bool sko) {
+  typedef typename C2<T>::t T2;
+  const int m = n / 3;
+  const float inv_m = 1.0f / (float)m;
+  const int mo = sko ? -1 : 0;
+  const T s3 = (T)0.86602540378443864676;
+  const T sp = INV ? -s3 : s3;
+  for (int t = threadIdx.x; t < nlines * m; t += blockDim.x) {
+    int j;
+    const int line = fdivmod(t, m, inv_m, &j);
+    const T2* in = A + line * ls;
+    T2* out = B + line * ls;
+    const T2 v0 = in[j], v2 = in[j + 2 * m];
+    const T2 mm = mk(fmx((T)-0.5, v2.x, v0.x), fmx((T)-0.5, v2.y, v0.y));
+    T2 y[3];
+    y[0] = v0 + v2;
+    // d = v1 - v2 = -v2: y1 = m + (s d.y, -s d.x), y2 = m - (s d.y, -s d.x)
+    y[1] = mk(fmx(-sp, v2.y, mm.x), fmx(sp, v2.x, mm.y));
+    y[2] = mk(fmx(sp, v2.y, mm.x), fmx(-sp, v2.x, mm.y));
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int e = base + r * Ns;
-      out[e + ((e >> 4) & mo)] = v[r];
+    for (int r = 0; r < 3; ++r) {
+      const int e = 3 * j + r;
+      out[e + ((e >> 4) & mo)] = y[r];
     }
+  }
+}
+// Last pass of a forward transform (Ns = m): butterfly j writes j, j + m, j + 2m; the middle
+// output is not computed.
+template <typename T>
+__device__ __forceinline__ void pruned_last_pass3(const typename C2<T>::t* __restrict__ A,
+                                                  typename C2<T>::t* __restrict__ B, int nlines,
+                                                  int ls, int n,
+                                                  const typename C2<T>::t* __restrict__ tw,
+                                                  bool ski) {
+  typedef typename C2<T>::t T2;
+  const int m = n / 3;
+  const float inv_m = 1.0f / (float)m;
+  const int mi = ski ? -1 : 0;
+  const T s3 = (T)0.86602540378443864676;
+  for (int t = threadIdx.x; t < nlines * m; t += blockDim.x) {
+    int j;
+    const int line = fdivmod(t, m, inv_m, &j);
+    const T2* in = A + line * ls;
+    T2* out = B + line * ls;
+    T2 v[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int e = j + r * m;
+      v[r] = in[e + ((e >> 4) & mi)];
+    }
+    if (j != 0) {
+      v[1] = cmul(v[1], tw[j]);
+      v[2] = cmul(v[2], tw[2 * j]);
+    }
+    const T2 tt = v[1] + v[2], d = v[1] - v[2];
+    const T2 mm = mk(v[0].x - (T)0.5 * tt.x, v[0].y - (T)0.5 * tt.y);
+    out[j] = v[0] + tt;
+    out[j + 2 * m] = mk(fmx(-s3, d.y, mm.x), fmx(s3, d.x, mm.y));
   }
 }
 
@@ -284,16 +370,25 @@ __device__ __forceinline__ void stockham_pass(const typename C2<T>::t* __restric
 // shape.  Returns the buffer holding the result (A or B).  Unnormalised; INV = exp(+).
 // Every thread of the block must call it (it contains __syncthreads()).  SKEW: the buffers
 // between passes use the skewed layout (ls >= fft_line_stride(n)); input and result are plain.
+// prune (with a pruning plan, pl.prune): the transform of a 3/2-rule padding.  Backward: the
+// input's middle third is zero and is not read (the radix-3 pass runs first).  Forward: the
+// radix-3 pass runs last and the middle third of the output is not written.
 template <typename T, bool INV, bool SKEW = false>
 __device__ typename C2<T>::t* block_fft(typename C2<T>::t* A, typename C2<T>::t* B, int nlines,
-                                        int ls, const FftPlan& pl) {
+                                        int ls, const FftPlan& pl, bool prune = false) {
   typedef typename C2<T>::t T2;
   const T2* tw = reinterpret_cast<const T2*>(pl.tw);
+  prune = prune && pl.prune && pl.nst >= 2 && pl.rad[0] == 3;
   int Ns = 1;
-  for (int s = 0; s < pl.nst; ++s) {
+  for (int q = 0; q < pl.nst; ++q) {
+    // pass order: the schedule's, except that a pruned forward transform takes its first
+    // (radix-3) stage last
+    const int s = (prune && !INV) ? (q + 1 < pl.nst ? q + 1 : 0) : q;
     const int R = pl.rad[s];
-    const bool ski = SKEW && s > 0, sko = SKEW && s + 1 < pl.nst;
-    if (R == 4) stockham_pass<T, 4, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    const bool ski = SKEW && q > 0, sko = SKEW && q + 1 < pl.nst;
+    if (prune && INV && q == 0) pruned_first_pass3<T, INV>(A, B, nlines, ls, pl.n, sko);
+    else if (prune && !INV && q + 1 == pl.nst) pruned_last_pass3<T>(A, B, nlines, ls, pl.n, tw, ski);
+    else if (R == 4) stockham_pass<T, 4, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
     else if (R == 8) stockham_pass<T, 8, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
     else if (R == 2) stockham_pass<T, 2, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
     else stockham_pass<T, 3, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);

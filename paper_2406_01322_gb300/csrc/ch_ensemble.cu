@@ -10,8 +10,9 @@
 // and replayed per step.
 //
 // Autotuner: for the ensemble's sizes it times, on the live ensemble (state saved and restored
-// bit for bit), the radix schedules of the x, y and z transforms (three styles each, chosen per
-// transform kind from the stage times that use it) and the number of persistent CTAs per SM of
+// bit for bit), the radix schedules of the x, y and z transforms (three styles each, and for x and
+// y a fourth: the pruned transforms of the 3/2-rule padding; chosen per transform kind from the
+// stage times that use it) and the number of persistent CTAs per SM of
 // each stage, and keeps the fastest.  The choice is cached per size signature for the process.
 #include <stdio.h>
 #include <string.h>
@@ -179,7 +180,7 @@ int build_descriptors(ch_ensemble* E) {
     M.pz = G->pz;
     apply_style(&M.px, E->tune.style[0]);
     apply_style(&M.py, E->tune.style[1]);
-    apply_style(&M.pz, E->tune.style[2]);
+    apply_style(&M.pz, E->tune.style[2] == 3 ? 2 : E->tune.style[2]);
     M.nl = G->nl;
     M.bw = G->bw;
     M.ya = G->ya;
@@ -292,8 +293,9 @@ void compute_occupancy(ch_ensemble* E) {
 std::string signature_of(const ch_ensemble* E) {
   std::string sig;
   char b[64];
+  // sizes and wall conditions of the members (the walls select the solve's code path)
   for (const ch_grid* G : E->members) {
-    snprintf(b, sizeof(b), "%dx%dx%d/", G->g.nx, G->g.ny, G->g.nz);
+    snprintf(b, sizeof(b), "%dx%dx%d:%d/", G->g.nx, G->g.ny, G->g.nz, G->g.bc);
     sig += b;
   }
   snprintf(b, sizeof(b), "p%d/c%d", E->prec, E->cheb);
@@ -521,9 +523,10 @@ int ch_ensemble_autotune(ch_ensemble* E, int reps) {
   Tuning best = E->tune;
   double stage_ms[kStages];
   double tot;
-  // 1) radix styles, chosen per transform kind from the stages that use it
-  double cost[3][3];
-  for (int style = 0; style < 3 && st == CH_OK; ++style) {
+  // 1) radix styles, chosen per transform kind from the stages that use it (style 3, the pruned
+  // transforms of the 3/2-rule padding, only for x and y: the z lines are not padded)
+  double cost[3][4];
+  for (int style = 0; style < 4 && st == CH_OK; ++style) {
     E->tune.style[0] = E->tune.style[1] = E->tune.style[2] = style;
     for (int s = 0; s < kStages; ++s) E->tune.ctas_per_sm[s] = 0;
     st = build_descriptors(E);
@@ -536,7 +539,7 @@ int ch_ensemble_autotune(ch_ensemble* E, int reps) {
   }
   for (int k = 0; k < 3 && st == CH_OK; ++k) {
     int b = 0;
-    for (int style = 1; style < 3; ++style)
+    for (int style = 1; style < (k < 2 ? 4 : 3); ++style)
       if (cost[k][style] < cost[k][b]) b = style;
     best.style[k] = b;
   }

@@ -18,7 +18,9 @@ bool smooth23(int n);
 // not {2,3}-smooth or needs too many passes.  Sets pl->n, pl->nst, pl->rad (not pl->tw).
 bool make_radices(int n, FftPlan* pl);
 // radix schedule with a style: 0 one radix-8 for an odd power of two then 4s, 2, 3s (as
-// make_radices); 1 the same with the radix-3 passes first; 2 as many radix-8 passes as possible
+// make_radices); 1 the same with the radix-3 passes first; 2 as many radix-8 passes as possible;
+// 3 one radix 3 first, then as style 2, marked for pruning (FftPlan::prune; n must be a
+// multiple of 3)
 bool make_radices_style(int n, int style, FftPlan* pl);
 // the grid-size rules of the C ABI: 0 or a negative CH_ERR_* code
 int check_sizes(int nx, int ny, int nz);

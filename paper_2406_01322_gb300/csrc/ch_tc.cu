@@ -124,15 +124,40 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
       : "memory");
 }
+// L2 policy that keeps lines resident (the per-CTA digit-plane cache and the matrix digits,
+// re-read for every output slice) ahead of the streamed rows and outputs
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// bulk copy global -> shared with completion on an mbarrier, read under the L2 policy `pol`
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
-                                          uint32_t bar) {
+                                          uint32_t bar, uint64_t pol) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
+      "[%1], %2, [%3], %4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
       : "memory");
+}
+// a 32-bit store to global memory under the L2 policy `pol`
+__device__ __forceinline__ void st_hint(uint32_t* p, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol)
+               : "memory");
+}
+// streamed (evict-first) loads of the rows' second read and stores of the outputs
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ df ld_stream(const df* p) {
+  const float2 v = __ldcs(reinterpret_cast<const float2*>(p));
+  return df(v.x, v.y);
+}
+__device__ __forceinline__ void st_stream(double* p, double v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(float* p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(df* p, df v) {
+  __stcs(reinterpret_cast<float2*>(p), make_float2(v.h, v.l));
 }
 // eight 4-column loads of this warp's 32 lanes, then one wait that the values depend on
 __device__ __forceinline__ void tmem_ld8x4(uint32_t addr, int stride, uint32_t (&v)[8][4]) {
@@ -386,6 +411,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *sT;
   const uint32_t sA0 = su32(sA), sB0 = su32(sB);
+  const uint64_t keep = policy_evict_last();
   Waiter W;
 
   if (issuer_warp) {
@@ -404,14 +430,14 @@ __global__ void __launch_bounds__(TCT + 32, 1)
             // the previous plane (t - 1) read B; it must be consumed before B is replaced
             if (u > 0 && !W.wait(barEmpty + 8 * ((t - 1) & 1), ((t - 1) >> 1) & 1)) goto drain;
             bulk_load(sB0, bdig + (size_t)sl * bslice + (size_t)ch * 8 * NT * TCKC,
-                      (uint32_t)(8 * NT * KCc * 2), barB);
+                      (uint32_t)(8 * NT * KCc * 2), barB, keep);
             pendB = true;
             if (sl > 0) {   // first cached plane of this chunk into buffer t % 2
               if (t >= 2 && !W.wait(barEmpty + 8 * (t & 1), ((t - 2) >> 1) & 1)) goto drain;
               // the producers' global stores (acquired through `full`) before the async copy
               asm volatile("fence.proxy.async.global;" ::: "memory");
               bulk_load(sA0 + (uint32_t)((t & 1) * kPlaneBytes), ccta + (size_t)ch * 8 * (kPlaneBytes / 4),
-                        kPlaneBytes, barLoad + 8 * (t & 1));
+                        kPlaneBytes, barLoad + 8 * (t & 1), keep);
               ++iload[t & 1];
             }
             if (!W.wait(barB, u & 1)) goto drain;
@@ -450,7 +476,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
                 if (tn >= 2 && !W.wait(barEmpty + 8 * (tn & 1), ((tn - 2) >> 1) & 1)) goto drain;
                 bulk_load(sA0 + (uint32_t)((tn & 1) * kPlaneBytes),
                           ccta + (size_t)(ch * 8 + i + 1) * (kPlaneBytes / 4), kPlaneBytes,
-                          barLoad + 8 * (tn & 1));
+                          barLoad + 8 * (tn & 1), keep);
                 ++iload[tn & 1];
               }
             }
@@ -530,7 +556,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
           for (int e = 0; e < 2; ++e) {
             const int k = ch * TCKC + 8 * gl + 2 * q + e;
             U b = 0;
-            if (gl < ngr && rowok && k < Nz) b = F::bits(src[2 * (size_t)k]);
+            if (gl < ngr && rowok && k < Nz) b = F::bits(ld_stream(src + 2 * (size_t)k));
             const unsigned long long y = to_biased<TI>(b, maxe);
             yh[2 * gl + e] = (uint32_t)(y >> 28);
             yl[2 * gl + e] = (uint32_t)y & 0xFFFFFFFu;
@@ -553,7 +579,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
               const uint32_t w = i < 4 ? digit_pair(yh[2 * gl], yh[2 * gl + 1], sh)
                                        : digit_pair(yl[2 * gl], yl[2 * gl + 1], sh);
               dst[(gl * 16 + warp) * 32 + lane] = w;
-              __stcg(gdst + (gl * 16 + warp) * 32 + lane, w);   // to L2, read by bulk copies
+              st_hint(gdst + (gl * 16 + warp) * 32 + lane, w, keep);   // read by bulk copies
             }
           // shared-memory plane for the MMAs; global copy for the issuer's later bulk copies
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -574,7 +600,8 @@ __global__ void __launch_bounds__(TCT + 32, 1)
         const long long T = s_hi * 16777216ll + (s_lo >> 3);
         TO v = maxe >= F::EMAX ? qnan<TO>() : scaled<TO>(T, maxe - F::EOFF - 51);
         if (fwd) v = last_scale<TO>(v, lastf);
-        out[((size_t)fld * fso + (size_t)line * Nz) * 2 + (m & 1) + 2 * (size_t)(Nz - 1)] = v;
+        st_stream(out + ((size_t)fld * fso + (size_t)line * Nz) * 2 + (m & 1) + 2 * (size_t)(Nz - 1),
+                  v);
       }
       const int oline = line0 + (mm >> 1);
       TO* dstp =
@@ -608,8 +635,8 @@ __global__ void __launch_bounds__(TCT + 32, 1)
               const long long L = ((long long)(g[4] * 128 + g[5]) * 128 + g[6]) * 128 + g[7];
               const long long T = H * 262144ll + (L >> 10);   // (H 2^28 + L) / 2^10
               // sum = 2^(E + F - 108) 2^49 (H 2^28 + L) = T 2^(E + F - 49)
-              dstp[2 * (size_t)n] =
-                  me >= F::EMAX ? qnan<TO>() : scaled<TO>(T, me - F::EOFF - 49 + sF[n]);
+              st_stream(dstp + 2 * (size_t)n,
+                        me >= F::EMAX ? qnan<TO>() : scaled<TO>(T, me - F::EOFF - 49 + sF[n]));
             }
           }
         }

@@ -36,11 +36,12 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
   const int f = bz;                  // output field
   const int h = Ny / 2;
   const T2 zero = mk((T)0, (T)0);
+  const int tzs = __ffs(TZ) - 1;     // TZ is a power of two: idx / TZ = idx >> tzs
   if (INV) {
     const T2* src = in + map.src[f] * fs_in + (size_t)mx * Ny * Nz;
     const bool dy = (map.dy_mask >> f) & 1;   // output d/dy of the input field (times i ky)
     for (int idx = threadIdx.x; idx < Ny * TZ; idx += blockDim.x) {
-      const int jj = idx / TZ, zz = idx - jj * TZ;
+      const int jj = idx >> tzs, zz = idx & (TZ - 1);
       const int z = z0 + zz;
       T2 v = zero;
       if (z < Nz && jj != h) v = src[(size_t)jj * Nz + z];
@@ -51,31 +52,33 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
       const int p = (jj < h) ? jj : P - Ny + jj;
       A[zz * LS + p] = v;
     }
-    for (int idx = threadIdx.x; idx < (P - Ny) * TZ; idx += blockDim.x) {
-      const int q = idx / TZ, zz = idx - q * TZ;
-      A[zz * LS + h + q] = zero;  // positions h .. P-h-1 hold no mode
-    }
+    // positions h .. P-h-1 hold no mode; a pruned transform does not read them
+    if (!pl.prune)
+      for (int idx = threadIdx.x; idx < (P - Ny) * TZ; idx += blockDim.x) {
+        const int q = idx >> tzs, zz = idx & (TZ - 1);
+        A[zz * LS + h + q] = zero;
+      }
   } else {
     const T2* src = in + map.src[f] * fs_in + (size_t)mx * P * Nz;
     for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
-      const int y = idx / TZ, zz = idx - y * TZ;
+      const int y = idx >> tzs, zz = idx & (TZ - 1);
       const int z = z0 + zz;
       A[zz * LS + y] = (z < Nz) ? src[(size_t)y * Nz + z] : zero;
     }
   }
   __syncthreads();
-  const T2* R = block_fft<T, INV, true>(A, B, TZ, LS, pl);
+  const T2* R = block_fft<T, INV, true>(A, B, TZ, LS, pl, true);
   if (INV) {
     T2* dst = out + f * fs_out + (size_t)mx * P * Nz;
     for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
-      const int y = idx / TZ, zz = idx - y * TZ;
+      const int y = idx >> tzs, zz = idx & (TZ - 1);
       const int z = z0 + zz;
       if (z < Nz) dst[(size_t)y * Nz + z] = R[zz * LS + y];
     }
   } else {
     T2* dst = out + f * fs_out + (size_t)mx * Ny * Nz;
     for (int idx = threadIdx.x; idx < Ny * TZ; idx += blockDim.x) {
-      const int jj = idx / TZ, zz = idx - jj * TZ;
+      const int jj = idx >> tzs, zz = idx & (TZ - 1);
       const int z = z0 + zz;
       if (z >= Nz) continue;
       const int p = (jj < h) ? jj : P - Ny + jj;
@@ -125,8 +128,10 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
   T2* Y = S + 7 * LS;
   T2* L0 = (pl.nst & 1) ? Y : X;
   // ---- 1. packed spectra: lines u v w phi phi_x phi_y phi_z
+  const float inv_mx = 1.0f / (float)Mx;
   for (int idx = threadIdx.x; idx < 7 * Mx; idx += blockDim.x) {
-    const int f = idx / Mx, m = idx - f * Mx;
+    int m;
+    const int f = fdivmod(idx, Mx, inv_mx, &m);
     const int src_f = (f < 4) ? f : f - 1;      // phi_x (line 4) comes from phi (input 3)
     const T2* src = in + src_f * fs + (size_t)m * mstride + base;
     T2 a = src[0];
@@ -145,14 +150,18 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
     }
   }
   {
-    const int w = Px - 2 * Mx + 1;  // kx = Mx .. Px - Mx carry no mode
+    // kx = Mx .. Px - Mx carry no mode; a pruned transform reads only the last of them
+    const int w0 = pl.prune ? Px - 2 * Mx : 0;
+    const int w = Px - 2 * Mx + 1 - w0;
+    const float inv_w = 1.0f / (float)w;
     for (int idx = threadIdx.x; idx < 7 * w; idx += blockDim.x) {
-      const int f = idx / w, q = idx - f * w;
-      L0[f * LS + Mx + q] = zero;
+      int q;
+      const int f = fdivmod(idx, w, inv_w, &q);
+      L0[f * LS + Mx + w0 + q] = zero;
     }
   }
   __syncthreads();
-  const T2* in7 = block_fft<T, true, true>(L0, (L0 == X) ? Y : X, 7, LS, pl);  // == X
+  const T2* in7 = block_fft<T, true, true>(L0, (L0 == X) ? Y : X, 7, LS, pl, true);  // == X
   T2* prod = S + 7 * LS;   // five product lines
   T2* scr = S + 12 * LS;   // five scratch lines
   for (int g0 = 0; g0 < 9; g0 += 5) {
@@ -176,11 +185,12 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
       }
     }
     __syncthreads();
-    const T2* R = block_fft<T, false, true>(prod, scr, cnt, LS, pl);
+    const T2* R = block_fft<T, false, true>(prod, scr, cnt, LS, pl, true);
     // ---- 3. unpack: A_k = (Z_k + conj Z_{-k}) / 2, B_k = (Z_k - conj Z_{-k}) / (2 i)
     const T hs = (T)0.5 * scale;
     for (int idx = threadIdx.x; idx < cnt * Mx; idx += blockDim.x) {
-      const int q = idx / Mx, m = idx - q * Mx;
+      int m;
+      const int q = fdivmod(idx, Mx, inv_mx, &m);
       const T2 Zk = R[q * LS + m];
       const T2 Zm = R[q * LS + (m == 0 ? 0 : Px - m)];
       T2* dst = out + (g0 + q) * fs + (size_t)m * mstride + base;

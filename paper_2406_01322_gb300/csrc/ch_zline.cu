@@ -217,20 +217,29 @@ __device__ __forceinline__ double2* LN(const ZSmem& z, int i, int Nz) { return z
 // mode 0 (forward): x = samples f_j, result a_n = E_n / (cbar_n N).
 // mode 1 (backward): x = coefficients with a_0, a_N doubled on input, result f_j = E_j / 2.
 // cs[j] = (cos(pi j / N), sin(pi j / N)), j = 0..N-1.
-__device__ void dct1_lines(const ZSmem& z, int first, int cnt, int Nz, int N, const FftPlan& pz,
-                           const double2* __restrict__ cs, int mode) {
+// part 0: the complex lines (real and imaginary parts share one complex FFT); part 1 / 2: the
+// real / imaginary parts alone, each as a real line (the other part of the line is neither read
+// nor written).
+__device__ void dct1_part(const ZSmem& z, int first, int cnt, int Nz, int N, const FftPlan& pz,
+                          const double2* __restrict__ cs, int mode, int part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double e0 = (mode == 1) ? 2.0 : 1.0;   // weight of x_0 and x_N
+  // the input of this part as a complex value (the other component zero for parts 1 and 2)
+  auto in_val = [part](double2 v) {
+    return part == 0 ? v : make_double2(part == 1 ? v.x : v.y, 0.0);
+  };
   for (int idx = threadIdx.x; idx < cnt * N; idx += blockDim.x) {
     const int f = idx / N, j = idx - f * N;
     const double2* x = LN(z, first + f, Nz);
     double2 y;
     if (j == 0) {
-      y = e0 * (x[0] + x[N]);
+      y = e0 * (in_val(x[0]) + in_val(x[N]));
     } else {
-      const double2 a = x[j], b = x[N - j];
+      const double2 a = in_val(x[j]), b = in_val(x[N - j]);
       const double sn = cs[j].y;
-      y = make_double2(a.x + b.x + sn * (a.x - b.x), a.y + b.y + sn * (a.y - b.y));
+      // explicit fused multiply-adds: every kernel that runs this (single-grid and grouped)
+      // rounds alike
+      y = make_double2(fma(sn, a.x - b.x, a.x + b.x), fma(sn, a.y - b.y, a.y + b.y));
     }
     z.FA[f * N + j] = y;
   }
@@ -239,7 +248,7 @@ __device__ void dct1_lines(const ZSmem& z, int first, int cnt, int Nz, int N, co
   if (warp < cnt) {
     const double2* x = LN(z, first + warp, Nz);
     for (int j = lane; j < N; j += 32) {
-      const double2 d = (j == 0) ? e0 * (x[0] - x[N]) : x[j] - x[N - j];
+      const double2 d = (j == 0) ? e0 * (in_val(x[0]) - in_val(x[N])) : in_val(x[j]) - in_val(x[N - j]);
       const double c = cs[j].x;
       e1.x = fma(c, d.x, e1.x);
       e1.y = fma(c, d.y, e1.y);
@@ -253,12 +262,19 @@ __device__ void dct1_lines(const ZSmem& z, int first, int cnt, int Nz, int N, co
   const double2* R = block_fft<double, false>(z.FA, z.FB, cnt, N, pz);
   const double sc0 = (mode == 0) ? 0.5 / N : 0.5;   // scale of E_0 and E_N
   const double sc = (mode == 0) ? 1.0 / N : 0.5;    // scale of the others
+  // the result of this part into the line (parts 1 and 2: the real part of E into the part's
+  // component; its imaginary part is rounding only)
+  auto put = [part](double2* dst, double2 v) {
+    if (part == 0) *dst = v;
+    else if (part == 1) dst->x = v.x;
+    else dst->y = v.x;
+  };
   // even outputs
   for (int idx = threadIdx.x; idx < cnt * (N / 2 + 1); idx += blockDim.x) {
     const int f = idx / (N / 2 + 1), k = idx - f * (N / 2 + 1);
     const double2 a = R[f * N + k], b = R[f * N + (k == 0 ? 0 : N - k)];
     const double s = (k == 0 || 2 * k == N) ? sc0 : sc;
-    LN(z, first + f, Nz)[2 * k] = (0.5 * s) * (a + b);
+    put(LN(z, first + f, Nz) + 2 * k, (0.5 * s) * (a + b));
   }
   // odd outputs: prefix sums of Q_k = (Y_k - Y_{N-k}) / 2 over k = 1..N/2-1 (warp f)
   if (warp < cnt) {
@@ -287,17 +303,33 @@ __device__ void dct1_lines(const ZSmem& z, int first, int cnt, int Nz, int N, co
       if (k < M) {
         if (k >= 1) T = T + 0.5 * (Y[k] - Y[N - k]);
         // E_{2k+1} = E_1 - 2 i T
-        out[2 * k + 1] = sc * make_double2(e1.x + 2.0 * T.y, e1.y - 2.0 * T.x);
+        put(out + 2 * k + 1, sc * make_double2(e1.x + 2.0 * T.y, e1.y - 2.0 * T.x));
       }
     }
   }
   __syncthreads();
 }
 
+// DCT-I of cnt lines.  split: transform the real and imaginary parts separately (two real
+// transforms) instead of as one complex line.  The complex FFT mixes the rounding of the two
+// parts; on the mean line (kx = ky = 0) the imaginary part is the spanwise mean flow, orders of
+// magnitude below the streamwise one in the real part, and would otherwise carry the real
+// part's rounding.
+__device__ void dct1_lines(const ZSmem& z, int first, int cnt, int Nz, int N, const FftPlan& pz,
+                           const double2* __restrict__ cs, int mode, bool split = false) {
+  if (!split) {
+    dct1_part(z, first, cnt, Nz, N, pz, cs, mode, 0);
+  } else {
+    dct1_part(z, first, cnt, Nz, N, pz, cs, mode, 1);
+    dct1_part(z, first, cnt, Nz, N, pz, cs, mode, 2);
+  }
+}
+
 // forward DCT-I of cnt lines in place (samples -> coefficients), cnt <= NBF
 __device__ __forceinline__ void dct_forward_lines(const ZSmem& z, int first, int cnt, int Nz, int N,
-                                                  const FftPlan& pz, const double2* cs) {
-  dct1_lines(z, first, cnt, Nz, N, pz, cs, 0);
+                                                  const FftPlan& pz, const double2* cs,
+                                                  bool split = false) {
+  dct1_lines(z, first, cnt, Nz, N, pz, cs, 0, split);
 }
 
 // backward DCT-I of cnt lines (coefficients -> samples), results stored to
@@ -305,8 +337,9 @@ __device__ __forceinline__ void dct_forward_lines(const ZSmem& z, int first, int
 template <typename T2>
 __device__ void dct_backward_lines_store(const ZSmem& z, int first, int cnt, int Nz, int N,
                                          const FftPlan& pz, const double2* cs, T2* out,
-                                         long long fs, size_t off, int out_first) {
-  dct1_lines(z, first, cnt, Nz, N, pz, cs, 1);
+                                         long long fs, size_t off, int out_first,
+                                         bool split = false) {
+  dct1_lines(z, first, cnt, Nz, N, pz, cs, 1, split);
   for (int idx = threadIdx.x; idx < cnt * Nz; idx += blockDim.x) {
     const int f = idx / Nz, j = idx - f * Nz;
     out[(long long)(out_first + f) * fs + off + j] = from_d2<T2>(LN(z, first + f, Nz)[j]);
@@ -387,7 +420,7 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   __syncthreads();
   if (!PRE)
     for (int f0 = 0; f0 < 7; f0 += NBF)
-      dct_forward_lines(z, f0, (7 - f0 < NBF) ? 7 - f0 : NBF, Nz, N, pz, g.zcs);
+      dct_forward_lines(z, f0, (7 - f0 < NBF) ? 7 - f0 : NBF, Nz, N, pz, g.zcs, is00);
   // G = phi^3 - (1 + shat) phi
   for (int n = tid; n < Nz; n += blockDim.x)
     LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * LN(z, 12, Nz)[n];
@@ -1059,7 +1092,7 @@ __device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __res
   int f0 = 0;
   for (int r = 0; r < NR; ++r) {
     const int cnt = (NOUT - f0 + (NR - r) - 1) / (NR - r);
-    dct_backward_lines_store<T2>(z, f0, cnt, Nz, N, pz, g.zcs, bw, fs, off, f0);
+    dct_backward_lines_store<T2>(z, f0, cnt, Nz, N, pz, g.zcs, bw, fs, off, f0, is00);
     f0 += cnt;
   }
 }
@@ -1094,7 +1127,7 @@ __global__ void __launch_bounds__(ZT) project_kernel(GridDev g, const double2* _
     LN(z, f, Nz)[n] = in[(long long)f * fs + off + n];
   }
   __syncthreads();
-  dct_forward_lines(z, 0, 4, Nz, N, pz, g.zcs);
+  dct_forward_lines(z, 0, 4, Nz, N, pz, g.zcs, is00);
   const double2 zero = make_double2(0.0, 0.0);
   for (int n = threadIdx.x; n < Nz; n += blockDim.x) {
     const double2 u = LN(z, 0, Nz)[n], v = LN(z, 1, Nz)[n];
@@ -1128,14 +1161,15 @@ __global__ void __launch_bounds__(ZT) dct_lines_kernel(GridDev g, int dir,
     }
     __syncthreads();
     if (dir == 0) {
-      dct_forward_lines(z, 0, cnt, Nz, N, pz, g.zcs);
+      dct_forward_lines(z, 0, cnt, Nz, N, pz, g.zcs, blockIdx.x == 0);
       for (int idx = threadIdx.x; idx < cnt * Nz; idx += blockDim.x) {
         const int f = idx / Nz, n = idx - f * Nz;
         out[(long long)(f0 + f) * fs + off + n] = LN(z, f, Nz)[n];
       }
       __syncthreads();
     } else {
-      dct_backward_lines_store<double2>(z, 0, cnt, Nz, N, pz, g.zcs, out, fs, off, f0);
+      dct_backward_lines_store<double2>(z, 0, cnt, Nz, N, pz, g.zcs, out, fs, off, f0,
+                                        blockIdx.x == 0);
     }
   }
 }
