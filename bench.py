@@ -943,12 +943,15 @@ def main():
         zc, xyc = cufft_transforms_ms(w, prec)
         ours_xy = sum(roof["kernel_ms_per_step"][n] for n in ("ybwd", "xline", "yfwd"))
         gm, gtf = dct_gemm_ms(w)
-        zrhs_ms = roof["kernel_ms_per_step"]["zrhs"]
+        kms_step = roof["kernel_ms_per_step"]
+        zrhs_ms = kms_step["zrhs"] + (kms_step.get("cheb_fwd", 0.0) if cheb == "tc" else 0.0)
         out["dct_as_gemm_comparison"] = {
             "fp64_gemm_ms_for_7_forward_dcts": gm, "fp64_gemm_tflops": gtf,
             "ours_zrhs_ms": zrhs_ms,
             "note": "the 7 forward DCTs of one step as one cuBLAS float64 GEMM, against our whole "
-                    "zrhs kernel (7 DCTs + derivatives + assembly)"}
+                    "forward z stage: zrhs (7 DCTs + derivatives + assembly), or with the "
+                    "tensor-core method its forward transform of the 9 products plus the "
+                    "coefficient-space zrhs"}
         out["cufft_comparison"] = {
             "cufft_z_dct_ms_per_step": zc, "cufft_xy_ms_per_step": xyc,
             "cufft_transforms_ms_per_step": zc + xyc,

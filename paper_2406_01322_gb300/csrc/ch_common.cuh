@@ -245,9 +245,9 @@ __host__ __device__ __forceinline__ int yline_stride(int P) {
 // position j of a group of lines (line g, g + G, ...; G = blockDim / (n / R) groups when a line
 // has fewer butterflies than the block has threads): its index arithmetic is formed once per
 // pass, not once per butterfly, and for float32 (whose kernels are bound by issue, not by the
-// arithmetic) its R - 1 twiddles too; the wider types reload them per line, which keeps their
-// registers for occupancy.
-template <typename T, int R, bool INV>
+// arithmetic) its R - 1 twiddles too; the wider types, and callers whose occupancy matters more
+// (HOIST_TW = false), reload them per line.
+template <typename T, int R, bool INV, bool HOIST_TW = (sizeof(typename C2<T>::t) == 8)>
 __device__ __forceinline__ void stockham_pass(const typename C2<T>::t* __restrict__ A,
                                               typename C2<T>::t* __restrict__ B, int nlines,
                                               int ls, int n, int Ns,
@@ -264,7 +264,7 @@ __device__ __forceinline__ void stockham_pass(const typename C2<T>::t* __restric
     const int g = fdivmod(w, nb, inv_nb, &j);
     int k;
     fdivmod(j, Ns, inv_ns, &k);
-    constexpr bool HOIST = sizeof(T2) == 8;
+    constexpr bool HOIST = HOIST_TW;
     const int ti = k * tws;
     T2 wr[HOIST ? R : 1];
     if (HOIST && k != 0) {
@@ -373,7 +373,8 @@ __device__ __forceinline__ void pruned_last_pass3(const typename C2<T>::t* __res
 // prune (with a pruning plan, pl.prune): the transform of a 3/2-rule padding.  Backward: the
 // input's middle third is zero and is not read (the radix-3 pass runs first).  Forward: the
 // radix-3 pass runs last and the middle third of the output is not written.
-template <typename T, bool INV, bool SKEW = false>
+template <typename T, bool INV, bool SKEW = false,
+          bool HOIST_TW = (sizeof(typename C2<T>::t) == 8)>
 __device__ typename C2<T>::t* block_fft(typename C2<T>::t* A, typename C2<T>::t* B, int nlines,
                                         int ls, const FftPlan& pl, bool prune = false) {
   typedef typename C2<T>::t T2;
@@ -388,10 +389,10 @@ __device__ typename C2<T>::t* block_fft(typename C2<T>::t* A, typename C2<T>::t*
     const bool ski = SKEW && q > 0, sko = SKEW && q + 1 < pl.nst;
     if (prune && INV && q == 0) pruned_first_pass3<T, INV>(A, B, nlines, ls, pl.n, sko);
     else if (prune && !INV && q + 1 == pl.nst) pruned_last_pass3<T>(A, B, nlines, ls, pl.n, tw, ski);
-    else if (R == 4) stockham_pass<T, 4, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
-    else if (R == 8) stockham_pass<T, 8, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
-    else if (R == 2) stockham_pass<T, 2, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
-    else stockham_pass<T, 3, INV>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else if (R == 4) stockham_pass<T, 4, INV, HOIST_TW>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else if (R == 8) stockham_pass<T, 8, INV, HOIST_TW>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else if (R == 2) stockham_pass<T, 2, INV, HOIST_TW>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else stockham_pass<T, 3, INV, HOIST_TW>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
     __syncthreads();
     T2* tmp = A;
     A = B;

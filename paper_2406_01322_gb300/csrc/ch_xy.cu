@@ -67,7 +67,9 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
     }
   }
   __syncthreads();
-  const T2* R = block_fft<T, INV, true>(A, B, TZ, LS, pl, true);
+  // twiddles reloaded per line: the y pass's occupancy (five CTAs per SM in float32) is worth
+  // more than the loads
+  const T2* R = block_fft<T, INV, true, false>(A, B, TZ, LS, pl, true);
   if (INV) {
     T2* dst = out + f * fs_out + (size_t)mx * P * Nz;
     for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
@@ -88,7 +90,7 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
 }
 
 template <typename T, bool INV>
-__global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __restrict__ in,
+__global__ void __launch_bounds__(YT, sizeof(T) == 4 ? 4 : 2) ypass_kernel(const typename C2<T>::t* __restrict__ in,
                                                    typename C2<T>::t* __restrict__ out, int Mx,
                                                    int Ny, int P, int Nz, int TZ, long long fs_in,
                                                    long long fs_out, T scale, FftPlan pl,
