@@ -75,6 +75,21 @@ TRAFFIC_MB = {
     ("channel_128x128x129", 0, "zsolve"): 93.5 + 8.9,
     ("channel_128x128x129", 1, "zsolve"): 93.5 + 8.9,
     ("channel_128x128x129", 2, "zsolve"): 93.5 + 8.9,
+    # 512 x 256 x 257 (full-size captures of the default bench command and of the FFT method
+    # and FP64 step on the same grid; zbwd was not captured at this size)
+    ("channel_512x256x257_mixed", 1, "cheb_fwd"): 6678.0 + 7339.3,
+    ("channel_512x256x257_mixed", 1, "cheb_bwd"): 5574.4 + 3520.3,
+    ("channel_512x256x257_mixed", 1, "zrhs_coef"): 4028.0 + 1584.2,
+    ("channel_512x256x257_mixed", 1, "zrhs"): 2820.4 + 1582.9,
+    ("channel_512x256x257_mixed", 1, "zsolve"): 4743.7 + 3612.8,
+    ("channel_512x256x257_mixed", 1, "xline"): 1221.0 + 1784.8,
+    ("channel_512x256x257_mixed", 1, "yfwd"): 1819.2 + 1383.2,
+    ("channel_512x256x257_mixed", 1, "ybwd"): 805.5 + 1373.8,
+    ("channel_512x256x257_mixed", 0, "zrhs"): 4028.0 + 1590.7,
+    ("channel_512x256x257_mixed", 0, "zsolve"): 4753.3 + 3623.4,
+    ("channel_512x256x257_mixed", 0, "xline"): 2434.1 + 3591.5,
+    ("channel_512x256x257_mixed", 0, "yfwd"): 3639.7 + 2404.3,
+    ("channel_512x256x257_mixed", 0, "ybwd"): 1610.9 + 2393.1,
     ("channel_128x128x129_adjoint", 0, "adj_xline"): 380.7 + 130.9,
     ("channel_128x128x129_adjoint", 0, "adj_zsolve"): 102.4 + 28.2,
     ("channel_128x128x129_adjoint", 0, "adj_zrhs"): 135.1 + 223.7,
@@ -83,7 +98,8 @@ TRAFFIC_MB = {
 
 def traffic_bytes(workload, prec, kernel, cheb="fft"):
     """ncu DRAM bytes of one launch; the z kernels of the tensor-core method (coefficient-space
-    variants) have their own entries, "zrhs_coef" and "zbwd_coef"."""
+    variants) have their own entries, "zrhs_coef" and "zbwd_coef"; the tensor-core transforms'
+    entries are per precision."""
     if cheb == "tc" and kernel in ("zrhs", "zbwd"):
         kernel += "_coef"
     v = TRAFFIC_MB.get((workload, prec, kernel))
