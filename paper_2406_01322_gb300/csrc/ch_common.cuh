@@ -241,13 +241,14 @@ __host__ __device__ __forceinline__ int yline_stride(int P) {
 }
 
 // one Stockham pass of radix R over `nlines` lines of length n (line stride ls) in shared memory;
-// ski / sko: the input / output lines are in the skewed layout.  A thread owns one butterfly
-// position j of a group of lines (line g, g + G, ...; G = blockDim / (n / R) groups when a line
-// has fewer butterflies than the block has threads): its index arithmetic is formed once per
-// pass, not once per butterfly, and for float32 (whose kernels are bound by issue, not by the
-// arithmetic) its R - 1 twiddles too; the wider types, and callers whose occupancy matters more
-// (HOIST_TW = false), reload them per line.
-template <typename T, int R, bool INV, bool HOIST_TW = (sizeof(typename C2<T>::t) == 8)>
+// ski / sko: the input / output lines are in the skewed layout.  Two thread mappings:
+// LOOP = false: one butterfly (line, j) per iteration (the fewest registers);
+// LOOP = true: a thread owns one butterfly position j of a group of lines (line g, g + G, ...;
+// G = blockDim / (n / R) groups when a line has fewer butterflies than the block has threads):
+// its index arithmetic is formed once per pass, not once per butterfly, and for float32 its
+// R - 1 twiddles too.  The loop costs registers, so it pays where shared memory, not registers,
+// limits the CTAs per SM (the long x lines).
+template <typename T, int R, bool INV, bool LOOP>
 __device__ __forceinline__ void stockham_pass(const typename C2<T>::t* __restrict__ A,
                                               typename C2<T>::t* __restrict__ B, int nlines,
                                               int ls, int n, int Ns,
@@ -255,16 +256,47 @@ __device__ __forceinline__ void stockham_pass(const typename C2<T>::t* __restric
                                               bool sko) {
   typedef typename C2<T>::t T2;
   const int nb = n / R;
-  const int G = nb >= (int)blockDim.x ? 1 : (int)blockDim.x / nb;
   const int tws = n / (Ns * R);
   const float inv_nb = 1.0f / (float)nb, inv_ns = 1.0f / (float)Ns;
   const int mi = ski ? -1 : 0, mo = sko ? -1 : 0;
+  if (!LOOP) {
+    for (int t = threadIdx.x; t < nlines * nb; t += blockDim.x) {
+      int j;
+      const int line = fdivmod(t, nb, inv_nb, &j);
+      int k;
+      fdivmod(j, Ns, inv_ns, &k);
+      const T2* in = A + line * ls;
+      T2* out = B + line * ls;
+      T2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int e = j + r * nb;
+        v[r] = in[e + ((e >> 4) & mi)];
+      }
+      if (k != 0) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const T2 wv = tw[r * k * tws];
+          v[r] = INV ? cmulc(v[r], wv) : cmul(v[r], wv);
+        }
+      }
+      Dft<T, R, INV>::run(v);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int e = base + r * Ns;
+        out[e + ((e >> 4) & mo)] = v[r];
+      }
+    }
+    return;
+  }
+  const int G = nb >= (int)blockDim.x ? 1 : (int)blockDim.x / nb;
   for (int w = threadIdx.x; w < nb * G; w += blockDim.x) {
     int j;
     const int g = fdivmod(w, nb, inv_nb, &j);
     int k;
     fdivmod(j, Ns, inv_ns, &k);
-    constexpr bool HOIST = HOIST_TW;
+    constexpr bool HOIST = sizeof(T2) == 8;
     const int ti = k * tws;
     T2 wr[HOIST ? R : 1];
     if (HOIST && k != 0) {
@@ -373,8 +405,7 @@ __device__ __forceinline__ void pruned_last_pass3(const typename C2<T>::t* __res
 // prune (with a pruning plan, pl.prune): the transform of a 3/2-rule padding.  Backward: the
 // input's middle third is zero and is not read (the radix-3 pass runs first).  Forward: the
 // radix-3 pass runs last and the middle third of the output is not written.
-template <typename T, bool INV, bool SKEW = false,
-          bool HOIST_TW = (sizeof(typename C2<T>::t) == 8)>
+template <typename T, bool INV, bool SKEW = false, bool LOOP = false>
 __device__ typename C2<T>::t* block_fft(typename C2<T>::t* A, typename C2<T>::t* B, int nlines,
                                         int ls, const FftPlan& pl, bool prune = false) {
   typedef typename C2<T>::t T2;
@@ -389,10 +420,10 @@ __device__ typename C2<T>::t* block_fft(typename C2<T>::t* A, typename C2<T>::t*
     const bool ski = SKEW && q > 0, sko = SKEW && q + 1 < pl.nst;
     if (prune && INV && q == 0) pruned_first_pass3<T, INV>(A, B, nlines, ls, pl.n, sko);
     else if (prune && !INV && q + 1 == pl.nst) pruned_last_pass3<T>(A, B, nlines, ls, pl.n, tw, ski);
-    else if (R == 4) stockham_pass<T, 4, INV, HOIST_TW>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
-    else if (R == 8) stockham_pass<T, 8, INV, HOIST_TW>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
-    else if (R == 2) stockham_pass<T, 2, INV, HOIST_TW>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
-    else stockham_pass<T, 3, INV, HOIST_TW>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else if (R == 4) stockham_pass<T, 4, INV, LOOP>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else if (R == 8) stockham_pass<T, 8, INV, LOOP>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else if (R == 2) stockham_pass<T, 2, INV, LOOP>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
+    else stockham_pass<T, 3, INV, LOOP>(A, B, nlines, ls, pl.n, Ns, tw, ski, sko);
     __syncthreads();
     T2* tmp = A;
     A = B;

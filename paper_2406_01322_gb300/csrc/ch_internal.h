@@ -27,6 +27,9 @@ int check_sizes(int nx, int ny, int nz);
 
 // The dynamic shared-memory limit a kernel was raised to, per device (the attribute set by
 // cudaFuncSetAttribute belongs to the current device).  Zero-initialised as a static object.
+// shared memory of one SM (the CTAs resident on it share it)
+constexpr size_t kMaxSmemPerSm = 228 * 1024;
+
 constexpr int kMaxSmemDevices = 64;
 struct SmemLimit {
   std::atomic<int> v[kMaxSmemDevices];

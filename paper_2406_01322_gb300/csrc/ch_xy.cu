@@ -67,9 +67,7 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
     }
   }
   __syncthreads();
-  // twiddles reloaded per line: the y pass's occupancy (five CTAs per SM in float32) is worth
-  // more than the loads
-  const T2* R = block_fft<T, INV, true, false>(A, B, TZ, LS, pl, true);
+  const T2* R = block_fft<T, INV, true>(A, B, TZ, LS, pl, true);
   if (INV) {
     T2* dst = out + f * fs_out + (size_t)mx * P * Nz;
     for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
@@ -90,7 +88,7 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
 }
 
 template <typename T, bool INV>
-__global__ void __launch_bounds__(YT, sizeof(T) == 4 ? 4 : 2) ypass_kernel(const typename C2<T>::t* __restrict__ in,
+__global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __restrict__ in,
                                                    typename C2<T>::t* __restrict__ out, int Mx,
                                                    int Ny, int P, int Nz, int TZ, long long fs_in,
                                                    long long fs_out, T scale, FftPlan pl,
@@ -109,7 +107,7 @@ __global__ void __launch_bounds__(YT, sizeof(T) == 4 ? 4 : 2) ypass_kernel(const
 //      phi^3, u phi, v phi, w phi;
 //   3. r2c, keep kx < Mx, times `scale`.
 // Shared memory: 7 + 5 + 5 lines of Px complex values.
-template <typename T>
+template <typename T, bool LOOP = false>
 __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__ in,
                                            typename C2<T>::t* __restrict__ out, int Mx, int Px,
                                            int Py, int Nz, long long fs, T kappa, T scale, T kxs,
@@ -163,7 +161,7 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
     }
   }
   __syncthreads();
-  const T2* in7 = block_fft<T, true, true>(L0, (L0 == X) ? Y : X, 7, LS, pl, true);  // == X
+  const T2* in7 = block_fft<T, true, true, LOOP>(L0, (L0 == X) ? Y : X, 7, LS, pl, true);  // == X
   T2* prod = S + 7 * LS;   // five product lines
   T2* scr = S + 12 * LS;   // five scratch lines
   for (int g0 = 0; g0 < 9; g0 += 5) {
@@ -187,7 +185,7 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
       }
     }
     __syncthreads();
-    const T2* R = block_fft<T, false, true>(prod, scr, cnt, LS, pl, true);
+    const T2* R = block_fft<T, false, true, LOOP>(prod, scr, cnt, LS, pl, true);
     // ---- 3. unpack: A_k = (Z_k + conj Z_{-k}) / 2, B_k = (Z_k - conj Z_{-k}) / (2 i)
     const T hs = (T)0.5 * scale;
     for (int idx = threadIdx.x; idx < cnt * Mx; idx += blockDim.x) {
@@ -203,12 +201,12 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
   }
 }
 
-template <typename T>
+template <typename T, bool LOOP>
 __global__ void __launch_bounds__(XT) xline_kernel(const typename C2<T>::t* __restrict__ in,
                                                    typename C2<T>::t* __restrict__ out, int Mx,
                                                    int Px, int Py, int Nz, long long fs, T kappa,
                                                    T scale, T kxs, FftPlan pl) {
-  xline_body<T>(in, out, Mx, Px, Py, Nz, fs, kappa, scale, kxs, pl, blockIdx.x, blockIdx.y);
+  xline_body<T, LOOP>(in, out, Mx, Px, Py, Nz, fs, kappa, scale, kxs, pl, blockIdx.x, blockIdx.y);
 }
 
 // plain r2c along x of physical rows (Nz, Ny, Nx) -> (Mx, Ny, Nz); two z rows per CTA
@@ -506,29 +504,41 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
   return cudaGetLastError();
 }
 
+template <bool LOOP>
+cudaError_t launch_xline_t(int prec, const GridDev& g, const void* in7, void* out10,
+                           long long fs, double scale, const FftPlan& px, size_t smem,
+                           cudaStream_t s) {
+  dim3 grid((g.nz + 1) / 2, g.Py);
+  static SmemLimit cur64, cur32, curdf;
+  cudaError_t e = prec == 0 ? ensure_smem(xline_kernel<double, LOOP>, smem, &cur64)
+                  : prec == 1 ? ensure_smem(xline_kernel<float, LOOP>, smem, &cur32)
+                              : ensure_smem(xline_kernel<df, LOOP>, smem, &curdf);
+  if (e != cudaSuccess) return e;
+  const double kxs = 6.283185307179586476925 / g.lx;
+  if (prec == 0) {
+    xline_kernel<double, LOOP><<<grid, XT, smem, s>>>((const double2*)in7, (double2*)out10, g.Mx,
+                                                      g.Px, g.Py, g.nz, fs, g.kappa, scale, kxs,
+                                                      px);
+  } else if (prec == 1) {
+    xline_kernel<float, LOOP><<<grid, XT, smem, s>>>((const float2*)in7, (float2*)out10, g.Mx,
+                                                     g.Px, g.Py, g.nz, fs, (float)g.kappa,
+                                                     (float)scale, (float)kxs, px);
+  } else {
+    xline_kernel<df, LOOP><<<grid, XT, smem, s>>>((const df2*)in7, (df2*)out10, g.Mx, g.Px, g.Py,
+                                                  g.nz, fs, df(g.kappa), df(scale), df(kxs), px);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out10, long long fs,
                          double scale, const FftPlan& px, cudaStream_t s) {
   const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);
   const size_t smem = xline_smem(g.Px, elem);
-  dim3 grid((g.nz + 1) / 2, g.Py);
-  static SmemLimit cur64, cur32, curdf;
-  cudaError_t e = prec == 0 ? ensure_smem(xline_kernel<double>, smem, &cur64)
-                  : prec == 1 ? ensure_smem(xline_kernel<float>, smem, &cur32)
-                              : ensure_smem(xline_kernel<df>, smem, &curdf);
-  if (e != cudaSuccess) return e;
-  const double kxs = 6.283185307179586476925 / g.lx;
-  if (prec == 0) {
-    xline_kernel<double><<<grid, XT, smem, s>>>((const double2*)in7, (double2*)out10, g.Mx, g.Px,
-                                                g.Py, g.nz, fs, g.kappa, scale, kxs, px);
-  } else if (prec == 1) {
-    xline_kernel<float><<<grid, XT, smem, s>>>((const float2*)in7, (float2*)out10, g.Mx, g.Px,
-                                               g.Py, g.nz, fs, (float)g.kappa, (float)scale,
-                                               (float)kxs, px);
-  } else {
-    xline_kernel<df><<<grid, XT, smem, s>>>((const df2*)in7, (df2*)out10, g.Mx, g.Px, g.Py, g.nz,
-                                            fs, df(g.kappa), df(scale), df(kxs), px);
-  }
-  return cudaGetLastError();
+  // the line-loop passes (more registers, less index work) where shared memory already limits
+  // the CTAs per SM to two or one (long x lines); the per-butterfly passes elsewhere
+  if (3 * smem > (size_t)kMaxSmemPerSm)
+    return launch_xline_t<true>(prec, g, in7, out10, fs, scale, px, smem, s);
+  return launch_xline_t<false>(prec, g, in7, out10, fs, scale, px, smem, s);
 }
 
 size_t adj_xline_smem(int Px) { return (size_t)24 * Px * sizeof(double2); }
