@@ -76,17 +76,20 @@ TRAFFIC_MB = {
     ("channel_128x128x129", 1, "zsolve"): 93.5 + 8.9,
     ("channel_128x128x129", 2, "zsolve"): 93.5 + 8.9,
     # 512 x 256 x 257 (full-size captures of the default bench command and of the FFT method
-    # and FP64 step on the same grid; zbwd was not captured at this size)
+    # and FP64 step on the same grid)
     ("channel_512x256x257_mixed", 1, "cheb_fwd"): 6678.0 + 7339.3,
     ("channel_512x256x257_mixed", 1, "cheb_bwd"): 5574.4 + 3520.3,
     ("channel_512x256x257_mixed", 1, "zrhs_coef"): 4028.0 + 1584.2,
     ("channel_512x256x257_mixed", 1, "zrhs"): 2820.4 + 1582.9,
     ("channel_512x256x257_mixed", 1, "zsolve"): 4743.7 + 3612.8,
+    ("channel_512x256x257_mixed", 1, "zbwd_coef"): 1342.5 + 2092.8,
+    ("channel_512x256x257_mixed", 1, "zbwd"): 1342.6 + 1427.2,
     ("channel_512x256x257_mixed", 1, "xline"): 1221.0 + 1784.8,
     ("channel_512x256x257_mixed", 1, "yfwd"): 1819.2 + 1383.2,
     ("channel_512x256x257_mixed", 1, "ybwd"): 805.5 + 1373.8,
     ("channel_512x256x257_mixed", 0, "zrhs"): 4028.0 + 1590.7,
     ("channel_512x256x257_mixed", 0, "zsolve"): 4753.3 + 3623.4,
+    ("channel_512x256x257_mixed", 0, "zbwd"): 1343.7 + 2096.8,
     ("channel_512x256x257_mixed", 0, "xline"): 2434.1 + 3591.5,
     ("channel_512x256x257_mixed", 0, "yfwd"): 3639.7 + 2404.3,
     ("channel_512x256x257_mixed", 0, "ybwd"): 1610.9 + 2393.1,

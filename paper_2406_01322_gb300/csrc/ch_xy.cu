@@ -201,8 +201,8 @@ __device__ __forceinline__ void xline_body(const typename C2<T>::t* __restrict__
   }
 }
 
-template <typename T, bool LOOP>
-__global__ void __launch_bounds__(XT) xline_kernel(const typename C2<T>::t* __restrict__ in,
+template <typename T, bool LOOP, int NTH>
+__global__ void __launch_bounds__(NTH) xline_kernel(const typename C2<T>::t* __restrict__ in,
                                                    typename C2<T>::t* __restrict__ out, int Mx,
                                                    int Px, int Py, int Nz, long long fs, T kappa,
                                                    T scale, T kxs, FftPlan pl) {
@@ -504,28 +504,29 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
   return cudaGetLastError();
 }
 
-template <bool LOOP>
+template <bool LOOP, int NTH>
 cudaError_t launch_xline_t(int prec, const GridDev& g, const void* in7, void* out10,
                            long long fs, double scale, const FftPlan& px, size_t smem,
                            cudaStream_t s) {
   dim3 grid((g.nz + 1) / 2, g.Py);
   static SmemLimit cur64, cur32, curdf;
-  cudaError_t e = prec == 0 ? ensure_smem(xline_kernel<double, LOOP>, smem, &cur64)
-                  : prec == 1 ? ensure_smem(xline_kernel<float, LOOP>, smem, &cur32)
-                              : ensure_smem(xline_kernel<df, LOOP>, smem, &curdf);
+  cudaError_t e = prec == 0 ? ensure_smem(xline_kernel<double, LOOP, NTH>, smem, &cur64)
+                  : prec == 1 ? ensure_smem(xline_kernel<float, LOOP, NTH>, smem, &cur32)
+                              : ensure_smem(xline_kernel<df, LOOP, NTH>, smem, &curdf);
   if (e != cudaSuccess) return e;
   const double kxs = 6.283185307179586476925 / g.lx;
   if (prec == 0) {
-    xline_kernel<double, LOOP><<<grid, XT, smem, s>>>((const double2*)in7, (double2*)out10, g.Mx,
-                                                      g.Px, g.Py, g.nz, fs, g.kappa, scale, kxs,
-                                                      px);
+    xline_kernel<double, LOOP, NTH><<<grid, NTH, smem, s>>>(
+        (const double2*)in7, (double2*)out10, g.Mx, g.Px, g.Py, g.nz, fs, g.kappa, scale, kxs,
+        px);
   } else if (prec == 1) {
-    xline_kernel<float, LOOP><<<grid, XT, smem, s>>>((const float2*)in7, (float2*)out10, g.Mx,
-                                                     g.Px, g.Py, g.nz, fs, (float)g.kappa,
-                                                     (float)scale, (float)kxs, px);
+    xline_kernel<float, LOOP, NTH><<<grid, NTH, smem, s>>>(
+        (const float2*)in7, (float2*)out10, g.Mx, g.Px, g.Py, g.nz, fs, (float)g.kappa,
+        (float)scale, (float)kxs, px);
   } else {
-    xline_kernel<df, LOOP><<<grid, XT, smem, s>>>((const df2*)in7, (df2*)out10, g.Mx, g.Px, g.Py,
-                                                  g.nz, fs, df(g.kappa), df(scale), df(kxs), px);
+    xline_kernel<df, LOOP, NTH><<<grid, NTH, smem, s>>>(
+        (const df2*)in7, (df2*)out10, g.Mx, g.Px, g.Py, g.nz, fs, df(g.kappa), df(scale),
+        df(kxs), px);
   }
   return cudaGetLastError();
 }
@@ -534,11 +535,16 @@ cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out1
                          double scale, const FftPlan& px, cudaStream_t s) {
   const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);
   const size_t smem = xline_smem(g.Px, elem);
-  // the line-loop passes (more registers, less index work) where shared memory already limits
-  // the CTAs per SM to two or one (long x lines); the per-butterfly passes elsewhere
-  if (3 * smem > (size_t)kMaxSmemPerSm)
-    return launch_xline_t<true>(prec, g, in7, out10, fs, scale, px, smem, s);
-  return launch_xline_t<false>(prec, g, in7, out10, fs, scale, px, smem, s);
+  // Long x lines, where shared memory limits the CTAs per SM to two (float32) or one (16-byte
+  // elements): float32 takes the line-loop passes (more registers, less index work per
+  // butterfly: 6.31 -> 5.48 ms at Px = 768), float64 and double-float twice the threads per
+  // CTA with the per-butterfly passes (more warps to cover the float64 pipe's latency: 45.9 ->
+  // 44.5 ms).  Shorter lines: the per-butterfly passes, 256 threads.
+  if (3 * smem > (size_t)kMaxSmemPerSm) {
+    if (prec == 1) return launch_xline_t<true, XT>(prec, g, in7, out10, fs, scale, px, smem, s);
+    return launch_xline_t<false, 512>(prec, g, in7, out10, fs, scale, px, smem, s);
+  }
+  return launch_xline_t<false, XT>(prec, g, in7, out10, fs, scale, px, smem, s);
 }
 
 size_t adj_xline_smem(int Px) { return (size_t)24 * Px * sizeof(double2); }
