@@ -54,21 +54,12 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 9.67 / 1e12
 # absent entries report null.  Re-capture when a kernel changes.
 TRAFFIC_MB = {
     ("channel_128x128x129", 0, "xline"): 152.8 + 185.4,
-    ("channel_128x128x129", 0, "zrhs"): 251.8 + 81.0,
-    ("channel_128x128x129", 0, "yfwd"): 228.3 + 128.6,
     ("channel_128x128x129", 0, "ybwd"): 84.6 + 135.3,
-    ("channel_128x128x129", 1, "zrhs"): 176.3 + 75.0,
     ("channel_128x128x129", 1, "xline"): 76.6 + 75.7,
-    ("channel_128x128x129", 1, "yfwd"): 114.2 + 80.0,
     ("channel_128x128x129", 1, "ybwd"): 42.1 + 91.2,
-    ("channel_128x128x129", 2, "zrhs"): 251.7 + 81.0,
     ("channel_128x128x129", 2, "xline"): 153.2 + 193.1,
-    ("channel_128x128x129", 2, "yfwd"): 228.3 + 128.8,
     ("channel_128x128x129", 2, "ybwd"): 84.7 + 134.8,
     # coefficient-space z kernels of the tensor-core method (the same kernels at any precision)
-    ("channel_128x128x129", 0, "zrhs_coef"): 251.7 + 72.7,
-    ("channel_128x128x129", 1, "zrhs_coef"): 251.7 + 72.7,
-    ("channel_128x128x129", 2, "zrhs_coef"): 251.7 + 72.7,
     ("channel_128x128x129", 0, "zbwd_coef"): 83.9 + 77.6,
     ("channel_128x128x129", 1, "zbwd_coef"): 83.9 + 77.6,
     ("channel_128x128x129", 2, "zbwd_coef"): 83.9 + 77.6,
@@ -77,21 +68,15 @@ TRAFFIC_MB = {
     ("channel_128x128x129", 2, "zsolve"): 93.5 + 8.9,
     # 512 x 256 x 257 (full-size captures of the default bench command and of the FFT method
     # and FP64 step on the same grid)
-    ("channel_512x256x257_mixed", 1, "cheb_fwd"): 6678.0 + 7339.3,
     ("channel_512x256x257_mixed", 1, "cheb_bwd"): 5574.4 + 3520.3,
-    ("channel_512x256x257_mixed", 1, "zrhs_coef"): 4028.0 + 1584.2,
-    ("channel_512x256x257_mixed", 1, "zrhs"): 2820.4 + 1582.9,
     ("channel_512x256x257_mixed", 1, "zsolve"): 4743.7 + 3612.8,
     ("channel_512x256x257_mixed", 1, "zbwd_coef"): 1342.5 + 2092.8,
     ("channel_512x256x257_mixed", 1, "zbwd"): 1342.6 + 1427.2,
     ("channel_512x256x257_mixed", 1, "xline"): 1221.0 + 1784.8,
-    ("channel_512x256x257_mixed", 1, "yfwd"): 1819.2 + 1383.2,
     ("channel_512x256x257_mixed", 1, "ybwd"): 805.5 + 1373.8,
-    ("channel_512x256x257_mixed", 0, "zrhs"): 4028.0 + 1590.7,
     ("channel_512x256x257_mixed", 0, "zsolve"): 4753.3 + 3623.4,
     ("channel_512x256x257_mixed", 0, "zbwd"): 1343.7 + 2096.8,
     ("channel_512x256x257_mixed", 0, "xline"): 2434.1 + 3591.5,
-    ("channel_512x256x257_mixed", 0, "yfwd"): 3639.7 + 2404.3,
     ("channel_512x256x257_mixed", 0, "ybwd"): 1610.9 + 2393.1,
     ("channel_128x128x129_adjoint", 0, "adj_xline"): 380.7 + 130.9,
     ("channel_128x128x129_adjoint", 0, "adj_zsolve"): 102.4 + 28.2,
@@ -154,9 +139,10 @@ def kernel_work(w, prec, cheb="fft"):
     # the scope table; the paper's 2N-point even extension would be twice that); a derivative =
     # 4 flops per coefficient
     dct = fft_flops(N)
-    # zrhs: 9 non-linear fields in, combined to 7 lines, 7 DCTs, 9 derivatives, assembly
-    zrhs_fl = lines * (7 * dct + 9 * 4 * nz + 150 * nz)
-    zrhs_by = S * (b * 9 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)   # NL, state, hist in/out, R out
+    # zrhs: the 7 combined non-linear lines in, 7 DCTs, 9 derivatives, assembly, AB2 and the
+    # right-hand sides (108 flops per coefficient)
+    zrhs_fl = lines * (7 * dct + 9 * 4 * nz + 108 * nz)
+    zrhs_by = S * (b * 7 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)   # NL, state, hist in/out, R out
     zsolve_fl = lines * nz * (5 * 30 + 8)                       # 5 sweeps + influence correction
     zsolve_by = S * 16 * 3 * 2
     zbwd_fl = lines * (5 * dct + 2 * 4 * nz + 40 * nz)
@@ -165,20 +151,22 @@ def kernel_work(w, prec, cheb="fft"):
     yb_by = (5 * S + 6 * Y) * b
     x_fl = Py * nz * (16 * 0.5 * fft_flops(Px) + 45 * Px)       # packed real FFTs + products
     x_by = 15 * Y * b
-    yf_fl = 9 * Mx * nz * fft_flops(Py)
-    yf_by = 9 * (S + Y) * b
+    # forward y pass: 9 product fields in, the 7 combined lines out (42 flops per spectral point
+    # for the i kx, i ky combinations)
+    yf_fl = 9 * Mx * nz * fft_flops(Py) + 42 * S
+    yf_by = (9 * Y + 7 * S) * b
     # Chebyshev transforms on the tensor cores (CH_CHEB_TC): tensor-pipe flops issued (36 digit
     # products of 2 M Nout K each, M = real rows, Nout and K padded as the kernel pads them) and
     # the bytes of the fields read and written once
     Kp, NT, nNt = tc_tiles(nz)
     rows = 2 * lines
-    tcf_fl = 36 * 2.0 * (9 * rows) * (NT * nNt) * Kp
-    tcf_by = 9 * S * (b + 16)
+    tcf_fl = 36 * 2.0 * (7 * rows) * (NT * nNt) * Kp
+    tcf_by = 7 * S * (b + 16)
     tcb_fl = 36 * 2.0 * (5 * rows) * (NT * nNt) * Kp
     tcb_by = 5 * S * (16 + b)
     if cheb == "tc":
-        zrhs_fl = lines * (9 * 4 * nz + 150 * nz)
-        zrhs_by = S * (16 * 9 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)
+        zrhs_fl = lines * (9 * 4 * nz + 108 * nz)
+        zrhs_by = S * (16 * 7 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)
         zbwd_fl = lines * (2 * 4 * nz + 40 * nz)
         zbwd_by = S * (16 * 3 + 16 * 2 + 16 * 3 + 16 * 5)
     return {"zrhs": (zrhs_fl, zrhs_by), "zsolve": (zsolve_fl, zsolve_by),

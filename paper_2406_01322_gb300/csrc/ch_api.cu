@@ -182,17 +182,26 @@ thread_local cudaError_t t_last_cuda = cudaSuccess;
     }                                               \
   } while (0)
 
-// non-linear terms of the current state: bw <- 7 fields; ya <- y backward; yb <- x line;
-// nl <- y forward (normalised)
-int eval_nonlinear_impl(ch_grid* G) {
+// the nine products of the current state on the y-padded grid: bw <- 5 fields; ya <- y
+// backward; yb <- x line
+int eval_products(ch_grid* G) {
   const GridDev& g = G->g;
   cudaStream_t s = G->stream;
   const chf::YMap ym = step_ymap();
   CK(chf::launch_zbwd(0, G->prec, kBw, g, G->R, G->om, G->w, G->phi, G->bw, G->fs, G->pz, s));
   CK(chf::launch_ypass(1, G->prec, g, g.Py, G->bw, G->ya, kYa, G->fs, G->fsy, 1.0, G->py[G->prec], s, &ym));
   CK(chf::launch_xline(G->prec, g, G->ya, G->yb, G->fsy, 1.0, G->px[G->prec], s));
-  CK(chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, kNl, G->fsy, G->fs,
-                       1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s));
+  return CH_OK;
+}
+
+// non-linear terms of the current state: the products, then nl <- the seven combined lines of
+// the forward y pass (normalised)
+int eval_nonlinear_impl(ch_grid* G) {
+  const GridDev& g = G->g;
+  const int r = eval_products(G);
+  if (r != CH_OK) return r;
+  CK(chf::launch_ycomb(G->prec, g, G->yb, G->nl, G->fsy, G->fs,
+                       1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], G->stream));
   return CH_OK;
 }
 
@@ -211,7 +220,7 @@ int launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev = nullptr
   nvtxRangePushA("ch step");
   if (tc) {
     nvtxRangePushA("cheb fwd (tensor cores)");
-    e[6] = chf::launch_cheb_tc(G->prec, 0, G->nl, G->fs, G->cf, G->fs, kNl, nlines,
+    e[6] = chf::launch_cheb_tc(G->prec, 0, G->nl, G->fs, G->cf, G->fs, chf::kNc, nlines,
                                g.nz, G->tcf, G->tc_err, s);
     nvtxRangePop();
   }
@@ -250,7 +259,7 @@ int launch_step(ch_grid* G, int first, cudaStream_t s, cudaEvent_t* ev = nullptr
   nvtxRangePop();
   if (ev) cudaEventRecord(ev[6], s);
   nvtxRangePushA("yfwd");
-  e[5] = chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, kNl, G->fsy, G->fs,
+  e[5] = chf::launch_ycomb(G->prec, g, G->yb, G->nl, G->fsy, G->fs,
                            1.0 / ((double)g.Px * (double)g.Py), G->py[G->prec], s);
   nvtxRangePop();
   nvtxRangePop();
@@ -763,10 +772,20 @@ int ch_transform_backward(ch_grid* G, const double* spec, double* phys) {
   return CH_OK;
 }
 
-int ch_nonlinear(ch_grid* G, double* out10) {
-  if (!G || !out10) return CH_ERR_ARG;
+int ch_nonlinear(ch_grid* G, double* out9) {
+  if (!G || !out9) return CH_ERR_ARG;
   if (!G->fields_set || G->nl_stale) return CH_ERR_STATE;
-  CK(chf::launch_dct_lines(0, G->prec, G->g, G->nl, (double2*)out10, kNl, G->fs, G->pz, G->stream));
+  // The step keeps only the seven combined lines; the nine products are evaluated again from the
+  // state into nl (which has room for nine fields), transformed, and nl is restored.
+  const GridDev& g = G->g;
+  const double scale = 1.0 / ((double)g.Px * (double)g.Py);
+  const int r = eval_products(G);
+  if (r != CH_OK) return r;
+  CK(chf::launch_ypass(0, G->prec, g, g.Py, G->yb, G->nl, kNl, G->fsy, G->fs, scale,
+                       G->py[G->prec], G->stream));
+  CK(chf::launch_dct_lines(0, G->prec, g, G->nl, (double2*)out9, kNl, G->fs, G->pz, G->stream));
+  CK(chf::launch_ycomb(G->prec, g, G->yb, G->nl, G->fsy, G->fs, scale, G->py[G->prec],
+                       G->stream));
   return CH_OK;
 }
 
@@ -819,7 +838,7 @@ int ch_set_chebyshev(ch_grid* G, int method) {
         t[dir].ctas = nsm;
       }
       int* err = (int*)galloc(G, sizeof(int));
-      double2* cf = (double2*)galloc(G, (size_t)kNl * G->fs * sizeof(double2));
+      double2* cf = (double2*)galloc(G, (size_t)chf::kNc * G->fs * sizeof(double2));
       if (!err || !cf) return CH_ERR_ALLOC;
       CK(cudaMemset(err, 0, sizeof(int)));
       G->tcf = t[0];

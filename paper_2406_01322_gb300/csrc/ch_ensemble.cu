@@ -49,7 +49,7 @@ int stage_items(int stage, const Member& m, int prec) {
                            : (2 * lines + zsolve_threads() - 1) / zsolve_threads();
     case 3: return ((g.nz + m.tzb - 1) / m.tzb) * g.Mx * kYa;
     case 4: return ((g.nz + 1) / 2) * g.Py;
-    default: return ((g.nz + m.tzf - 1) / m.tzf) * g.Mx * kNl;
+    default: return chf::ycomb_items(g.Mx, g.nz, m.tzf);
   }
 }
 
@@ -61,7 +61,7 @@ size_t stage_smem(int stage, const Member& m, int prec) {
     case 1: return m.zsolve_tile ? zsolve_tile_smem(m.g) : 0;
     case 3: return ysmem_bytes(m.g.Py, m.tzb, elem);
     case 4: return xline_smem(m.g.Px, elem);
-    default: return ysmem_bytes(m.g.Py, m.tzf, elem);
+    default: return ycomb_smem(m.g.Py, m.tzf, elem);
   }
 }
 
@@ -253,7 +253,7 @@ cudaError_t member_transforms(ch_ensemble* E, int dir, cudaStream_t s) {
   for (ch_grid* G : E->members) {
     const int nlines = G->g.Mx * G->g.ny;
     const cudaError_t e =
-        dir == 0 ? chf::launch_cheb_tc(E->prec, 0, G->nl, G->fs, G->cf, G->fs, chf::kNl, nlines,
+        dir == 0 ? chf::launch_cheb_tc(E->prec, 0, G->nl, G->fs, G->cf, G->fs, chf::kNc, nlines,
                                        G->g.nz, G->tcf, G->tc_err, s)
                  : chf::launch_cheb_tc(0, E->prec, G->cf, G->fs, G->bw, G->fs, chf::kBw, nlines,
                                        G->g.nz, G->tcb, G->tc_err, s);

@@ -122,6 +122,57 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
                          int nf, long long fs_in, long long fs_out, double scale,
                          const FftPlan& py, cudaStream_t s, const YMap* map = nullptr);
 
+// Forward y pass of the nine products with the spectral assembly's z-independent combinations
+// (Eqs. (omegaz), (ww), (phisplit)) formed on the way out, so that the z stage reads and
+// transforms seven lines instead of nine:
+//   A = i kx Sxx' + i ky Sxy, B = i kx Sxy + i ky Syy'  (Sxx' = Sxx - Szz, Syy' = Syy - Szz)
+//   0: P = i kx B - i ky A      (on the kx = ky = 0 line: Sxz)
+//   1: Q = i kx Syz - i ky Sxz  (on the kx = ky = 0 line: Syz)
+//   2: C = i kx Sxz + i ky Syz  3: R = i kx A + i ky B
+//   4: F = -(i kx u phi + i ky v phi)   5: w phi   6: phi^3
+// so that S_x = A + D Sxz, S_y = B + D Syz, h_omega = P + D Q, S_z = C,
+// i kx S_x + i ky S_y = R + D C.  Work items are (input group, mx, z tile): group 0 transforms
+// Sxx', Syy', Sxy (outputs 0, 3), group 1 Sxz, Syz (0 on the mean line, 1, 2), group 2 u phi,
+// v phi (4), groups 3 and 4 w phi and phi^3; each group's z tile is the y pass's tile L divided
+// so that a CTA holds at most max(L, 3) lines.
+constexpr int kNc = 7;            // combined non-linear lines
+constexpr int kYcGroups = 5;
+__host__ __device__ __forceinline__ int ycomb_nin(int grp) {
+  return grp == 0 ? 3 : (grp <= 2 ? 2 : 1);
+}
+// log2 of a group's z tile for a y-pass tile L (a power of two)
+__host__ __device__ __forceinline__ int ycomb_tzs(int grp, int L) {
+  int l = 0;
+  while ((1 << (l + 1)) <= L) ++l;
+  const int d = grp == 0 ? 2 : (grp <= 2 ? 1 : 0);
+  return l > d ? l - d : 0;
+}
+__host__ __device__ __forceinline__ int ycomb_group_items(int grp, int Mx, int Nz, int L) {
+  const int tzs = ycomb_tzs(grp, L);
+  return ((Nz + (1 << tzs) - 1) >> tzs) * Mx;
+}
+inline int ycomb_items(int Mx, int Nz, int L) {
+  int n = 0;
+  for (int grp = 0; grp < kYcGroups; ++grp) n += ycomb_group_items(grp, Mx, Nz, L);
+  return n;
+}
+// lines one CTA holds at most, and its shared memory (two buffers of those lines)
+inline int ycomb_lines(int L) {
+  int m = 0;
+  for (int grp = 0; grp < kYcGroups; ++grp) {
+    const int v = ycomb_nin(grp) << ycomb_tzs(grp, L);
+    if (v > m) m = v;
+  }
+  return m;
+}
+inline size_t ycomb_smem(int P, int L, size_t elem) {
+  return (size_t)2 * ycomb_lines(L) * yline_stride(P) * elem;
+}
+// in: the nine products on the y-padded grid (field stride fs_in); out: the seven combined
+// lines (Mx, Ny, Nz) times `scale` (field stride fs_out); y tile from ytile_for
+cudaError_t launch_ycomb(int prec, const GridDev& g, const void* in, void* out, long long fs_in,
+                         long long fs_out, double scale, const FftPlan& py, cudaStream_t s);
+
 // ---- ensemble: one member's everything the six step kernels need (device-resident array) ----
 struct Member {
   GridDev g;

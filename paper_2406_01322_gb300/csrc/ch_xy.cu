@@ -97,6 +97,93 @@ __global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __re
                      blockIdx.y, blockIdx.z);
 }
 
+// Forward y pass with the assembly's combinations (launch_ycomb): work item -> (group, mx, z
+// tile); the nine products are transformed in groups so that each CTA holds every input its
+// outputs combine.  Groups and outputs as stated at launch_ycomb; the arithmetic of the
+// combinations is that of the working precision T.
+template <typename T>
+__device__ __forceinline__ void ycomb_body(const typename C2<T>::t* __restrict__ in,
+                                           typename C2<T>::t* __restrict__ out, int Mx, int Ny,
+                                           int P, int Nz, int L, long long fs_in,
+                                           long long fs_out, T scale, T kxs, T kys,
+                                           const FftPlan& pl, int item) {
+  typedef typename C2<T>::t T2;
+  extern __shared__ unsigned char ysm_raw[];
+  int grp = 0, rest = item;
+  for (; grp < kYcGroups - 1; ++grp) {
+    const int n = ycomb_group_items(grp, Mx, Nz, L);
+    if (rest < n) break;
+    rest -= n;
+  }
+  const int tzs = ycomb_tzs(grp, L);
+  const int TZ = 1 << tzs;
+  const int nzt = (Nz + TZ - 1) >> tzs;
+  const int mx = rest / nzt;
+  const int z0 = (rest - mx * nzt) * TZ;
+  const int nin = ycomb_nin(grp);
+  const int LS = yline_stride(P);
+  T2* A = reinterpret_cast<T2*>(ysm_raw);
+  T2* B = A + nin * TZ * LS;
+  const T2 zero = mk((T)0, (T)0);
+  // input products: 0 Sxx' 1 Syy' 2 Sxy 3 Sxz 4 Syz 5 phi^3 6 u phi 7 v phi 8 w phi
+  const int f0 = grp == 0 ? 0 : grp == 1 ? 3 : grp == 2 ? 6 : grp == 3 ? 8 : 5;
+  for (int f = 0; f < nin; ++f) {
+    const T2* src = in + (f0 + f) * fs_in + (size_t)mx * P * Nz;
+    T2* Af = A + f * TZ * LS;
+    for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
+      const int y = idx >> tzs, zz = idx & (TZ - 1);
+      const int z = z0 + zz;
+      Af[zz * LS + y] = (z < Nz) ? src[(size_t)y * Nz + z] : zero;
+    }
+  }
+  __syncthreads();
+  const T2* R = block_fft<T, false, true>(A, B, nin * TZ, LS, pl, true);
+  const int h = Ny / 2;
+  const T kx = kxs * (T)mx;
+  T2* dst = out + (size_t)mx * Ny * Nz;
+  for (int idx = threadIdx.x; idx < Ny * TZ; idx += blockDim.x) {
+    const int jj = idx >> tzs, zz = idx & (TZ - 1);
+    const int z = z0 + zz;
+    if (z >= Nz) continue;
+    const size_t o = (size_t)jj * Nz + z;
+    const int p = (jj < h) ? jj : P - Ny + jj;
+    const bool nyq = (jj == h);   // the y Nyquist row is zero
+    const bool mean = (mx == 0 && jj == 0);
+    const T ky = kys * (T)((jj < h) ? jj : jj - Ny);
+    T2 v[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+      v[f] = (nyq || f >= nin) ? zero : scale * R[(f * TZ + zz) * LS + p];
+    if (grp == 0) {
+      const T2 a = mul_i(kx * v[0] + ky * v[2]);
+      const T2 b = mul_i(kx * v[2] + ky * v[1]);
+      if (!mean) dst[o] = mul_i(kx * b - ky * a);
+      dst[3 * fs_out + o] = mul_i(kx * a + ky * b);
+    } else if (grp == 1) {
+      if (mean) {
+        dst[o] = v[0];
+        dst[fs_out + o] = v[1];
+      } else {
+        dst[fs_out + o] = mul_i(kx * v[1] - ky * v[0]);
+      }
+      dst[2 * fs_out + o] = mul_i(kx * v[0] + ky * v[1]);
+    } else if (grp == 2) {
+      dst[4 * fs_out + o] = mul_mi(kx * v[0] + ky * v[1]);
+    } else {
+      dst[(grp == 3 ? 5 : 6) * fs_out + o] = v[0];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(YT) ycomb_kernel(const typename C2<T>::t* __restrict__ in,
+                                                   typename C2<T>::t* __restrict__ out, int Mx,
+                                                   int Ny, int P, int Nz, int L, long long fs_in,
+                                                   long long fs_out, T scale, T kxs, T kys,
+                                                   FftPlan pl) {
+  ycomb_body<T>(in, out, Mx, Ny, P, Nz, L, fs_in, fs_out, scale, kxs, kys, pl, blockIdx.x);
+}
+
 // Fused x-line kernel.  One CTA per (pair of z rows, y).  The two rows z0, z0+1 of a field are
 // packed as one complex signal a + i b, so one complex FFT of length Px transforms both.
 //   1. six inputs u, v, w, phi, phi_y, phi_z (spectra kx < Mx); phi_x = i kx phi is formed from
@@ -448,6 +535,21 @@ __global__ void __launch_bounds__(YT) grouped_ypass_kernel(const Member* __restr
   }
 }
 
+// grouped forward y pass with the combinations: items (group, mx, z tile) member by member
+template <typename T>
+__global__ void __launch_bounds__(YT) grouped_ycomb_kernel(const Member* __restrict__ mem,
+                                                           const int* __restrict__ begin, int nmem) {
+  typedef typename C2<T>::t T2;
+  const int total = begin[nmem];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int m = member_of_xy(begin, nmem, item);
+    const Member& M = mem[m];
+    ycomb_body<T>((const T2*)M.yb, (T2*)M.nl, M.g.Mx, M.g.ny, M.g.Py, M.g.nz, M.tzf, M.fsy, M.fs,
+                  (T)M.yscale, (T)M.kxs, (T)M.ym.kys, M.py, item - begin[m]);
+    __syncthreads();
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(XT) grouped_xline_kernel(const Member* __restrict__ mem,
                                                            const int* __restrict__ begin, int nmem) {
@@ -501,6 +603,32 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
     if (dir == 1) { YL(df, true) } else { YL(df, false) }
   }
 #undef YL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ycomb(int prec, const GridDev& g, const void* in, void* out, long long fs_in,
+                         long long fs_out, double scale, const FftPlan& py, cudaStream_t s) {
+  const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);
+  const int L = ytile_local(g.Py, elem);
+  const size_t smem = ycomb_smem(g.Py, L, elem);
+  const int items = ycomb_items(g.Mx, g.nz, L);
+  static SmemLimit cur[3];
+  cudaError_t e = prec == 0   ? ensure_smem(ycomb_kernel<double>, smem, &cur[0])
+                  : prec == 1 ? ensure_smem(ycomb_kernel<float>, smem, &cur[1])
+                              : ensure_smem(ycomb_kernel<df>, smem, &cur[2]);
+  if (e != cudaSuccess) return e;
+  const double kxs = 6.283185307179586476925 / g.lx, kys = 6.283185307179586476925 / g.ly;
+  if (prec == 0)
+    ycomb_kernel<double><<<items, YT, smem, s>>>((const double2*)in, (double2*)out, g.Mx, g.ny,
+                                                 g.Py, g.nz, L, fs_in, fs_out, scale, kxs, kys,
+                                                 py);
+  else if (prec == 1)
+    ycomb_kernel<float><<<items, YT, smem, s>>>((const float2*)in, (float2*)out, g.Mx, g.ny,
+                                                g.Py, g.nz, L, fs_in, fs_out, (float)scale,
+                                                (float)kxs, (float)kys, py);
+  else
+    ycomb_kernel<df><<<items, YT, smem, s>>>((const df2*)in, (df2*)out, g.Mx, g.ny, g.Py, g.nz,
+                                             L, fs_in, fs_out, df(scale), df(kxs), df(kys), py);
   return cudaGetLastError();
 }
 
@@ -602,9 +730,9 @@ cudaError_t launch_grouped_xy(int stage, int prec, const Member* mem, const int*
     else if (prec == 1) { GL(grouped_xline_kernel<float>, 3, float) }
     else { GL(grouped_xline_kernel<df>, 7, df) }
   } else {
-    if (prec == 0) { GL((grouped_ypass_kernel<double, false>), 4, double) }
-    else if (prec == 1) { GL((grouped_ypass_kernel<float, false>), 5, float) }
-    else { GL((grouped_ypass_kernel<df, false>), 8, df) }
+    if (prec == 0) { GL(grouped_ycomb_kernel<double>, 4, double) }
+    else if (prec == 1) { GL(grouped_ycomb_kernel<float>, 5, float) }
+    else { GL(grouped_ycomb_kernel<df>, 8, df) }
   }
 #undef GL
   return cudaGetLastError();
@@ -622,9 +750,9 @@ int occupancy_xy(int stage, int prec, size_t smem) {
       : prec == 1 ? (const void*)grouped_xline_kernel<float>
                   : (const void*)grouped_xline_kernel<df>;
   else
-    k = prec == 0 ? (const void*)grouped_ypass_kernel<double, false>
-      : prec == 1 ? (const void*)grouped_ypass_kernel<float, false>
-                  : (const void*)grouped_ypass_kernel<df, false>;
+    k = prec == 0 ? (const void*)grouped_ycomb_kernel<double>
+      : prec == 1 ? (const void*)grouped_ycomb_kernel<float>
+                  : (const void*)grouped_ycomb_kernel<df>;
   if (smem > 48 * 1024) {  // opt-in first (init time, never during capture)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaGetLastError();

@@ -348,9 +348,9 @@ __device__ void dct_backward_lines_store(const ZSmem& z, int first, int cnt, int
 }
 
 // ---- zrhs: right-hand sides of the three implicit problems ---------------------------------
-// PRE = 1: nl holds the Chebyshev coefficients of the nine products (float64, transformed by
-// the tensor-core kernel), so the forward DCTs are skipped; the combinations below are linear
-// with z-independent factors and are formed the same way in coefficient space.
+// nl: the seven combined non-linear lines (launch_ycomb) as samples on the Gauss-Lobatto points.
+// PRE = 1: nl holds their Chebyshev coefficients (float64, transformed by the tensor-core
+// kernel), so the forward DCTs are skipped.
 template <typename T, int PRE = 0>
 __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>::t* __restrict__ nl,
                                           long long fs, const double2* __restrict__ st_om,
@@ -385,37 +385,16 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
     LN(z, 11, Nz)[n] = st_w[off + n];
     LN(z, 12, Nz)[n] = st_phi[off + n];
   }
-  for (int idx = tid; idx < 9 * Nz; idx += blockDim.x) {
-    const int f = idx / Nz, n = idx - f * Nz;
-    LN(z, f, Nz)[n] = to_d2(nl[(long long)f * fs + off + n]);
-  }
-  __syncthreads();
-  // Non-linear samples (lines): 0 Sxx-Szz 1 Syy-Szz 2 Sxy 3 Sxz 4 Syz 5 phi^3 6 u phi 7 v phi
-  // 8 w phi.  The Chebyshev transform commutes with multiplication by i kx, i ky, so the
-  // combinations the assembly needs are formed first and only seven lines are transformed:
-  //   A = i kx Sxx' + i ky Sxy,  B = i kx Sxy + i ky Syy'  (S_x = A + D Sxz, S_y = B + D Syz)
+  // The seven combined non-linear lines, formed by the forward y pass (the Chebyshev transform
+  // commutes with the z-independent factors i kx, i ky):
   //   0: P = i kx B - i ky A   1: Q = i kx Syz - i ky Sxz   (h_omega = P + D Q)
   //   2: C = i kx Sxz + i ky Syz  (S_z = C)   3: R = i kx A + i ky B  (i kx S_x + i ky S_y = R + D C)
   //   4: F = -(i kx u phi + i ky v phi)   5: w phi   6: phi^3
-  // On the (0,0) line P = Q = 0; lines 0 and 1 carry Sxz and Syz instead (mean forcing).
-  for (int n = tid; n < Nz; n += blockDim.x) {
-    const double2 sxx = LN(z, 0, Nz)[n], syy = LN(z, 1, Nz)[n], sxy = LN(z, 2, Nz)[n];
-    const double2 sxz = LN(z, 3, Nz)[n], syz = LN(z, 4, Nz)[n], p3 = LN(z, 5, Nz)[n];
-    const double2 fu = LN(z, 6, Nz)[n], fv = LN(z, 7, Nz)[n], fw = LN(z, 8, Nz)[n];
-    const double2 A = mul_i(kx * sxx + ky * sxy);
-    const double2 B = mul_i(kx * sxy + ky * syy);
-    if (is00) {
-      LN(z, 0, Nz)[n] = sxz;
-      LN(z, 1, Nz)[n] = syz;
-    } else {
-      LN(z, 0, Nz)[n] = mul_i(kx * B - ky * A);
-      LN(z, 1, Nz)[n] = mul_i(kx * syz - ky * sxz);
-    }
-    LN(z, 2, Nz)[n] = mul_i(kx * sxz + ky * syz);
-    LN(z, 3, Nz)[n] = mul_i(kx * A + ky * B);
-    LN(z, 4, Nz)[n] = -1.0 * mul_i(kx * fu + ky * fv);
-    LN(z, 5, Nz)[n] = fw;
-    LN(z, 6, Nz)[n] = p3;
+  // with A = i kx Sxx' + i ky Sxy, B = i kx Sxy + i ky Syy' (S_x = A + D Sxz, S_y = B + D Syz).
+  // On the (0,0) line lines 0 and 1 carry Sxz and Syz (mean forcing).
+  for (int idx = tid; idx < kNc * Nz; idx += blockDim.x) {
+    const int f = idx / Nz, n = idx - f * Nz;
+    LN(z, f, Nz)[n] = to_d2(nl[(long long)f * fs + off + n]);
   }
   __syncthreads();
   if (!PRE)

@@ -76,7 +76,7 @@ def test_tensor_core_flops_match_an_enumeration_of_the_mma_tiles():
         w = dict(W, nz=nz)
         Kp, NT, nNt = bench.tc_tiles(nz)
         rows = 2 * (w["nx"] // 2) * w["ny"]
-        tiles = 9 * rows // 128
+        tiles = 7 * rows // 128
         per_tile = 0
         for _ in range(nNt):
             k0 = 0
@@ -128,9 +128,9 @@ def test_algorithmic_bytes_are_the_measured_compulsory_traffic(key):
 
 
 def test_traffic_lookup_separates_the_coefficient_kernels():
-    wl = "channel_128x128x129"
-    fft = bench.traffic_bytes(wl, 1, "zrhs")
-    tc = bench.traffic_bytes(wl, 1, "zrhs", "tc")
+    wl = "channel_512x256x257_mixed"
+    fft = bench.traffic_bytes(wl, 1, "zbwd")
+    tc = bench.traffic_bytes(wl, 1, "zbwd", "tc")
     assert fft is not None and tc is not None and fft != tc
     assert bench.traffic_bytes(wl, 0, "xline", "tc") == bench.traffic_bytes(wl, 0, "xline")
     assert bench.traffic_bytes(wl, 0, "no_such_kernel") is None
