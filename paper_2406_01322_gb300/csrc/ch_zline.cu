@@ -43,6 +43,10 @@ namespace chf {
 namespace {
 
 constexpr int ZT = 128;   // threads of a per-line CTA
+// threads of the coefficient-space per-line kernels (tensor-core Chebyshev method): no FFT
+// passes, so twice the warps per line keep more float64 work in flight (their shared memory,
+// without the DCT scratch, also leaves room for three CTAs per SM at nz = 257)
+constexpr int ZTC = 256;
 constexpr int NBF = 4;    // DCT lines transformed per FFT call (one warp each for scans)
 constexpr int NLINES = 16;
 
@@ -454,7 +458,7 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
 }
 
 template <typename T, int PRE = 0>
-__global__ void __launch_bounds__(ZT) zrhs_kernel(GridDev g, const typename C2<T>::t* __restrict__ nl,
+__global__ void __launch_bounds__(PRE ? ZTC : ZT) zrhs_kernel(GridDev g, const typename C2<T>::t* __restrict__ nl,
                                                   long long fs, const double2* __restrict__ st_om,
                                                   const double2* __restrict__ st_w,
                                                   const double2* __restrict__ st_phi,
@@ -1077,7 +1081,7 @@ __device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __res
 }
 
 template <typename T, int UPDATE, int NOUT, int COEF = 0>
-__global__ void __launch_bounds__(ZT) zbwd_kernel(GridDev g, const double2* __restrict__ R,
+__global__ void __launch_bounds__(COEF ? ZTC : ZT) zbwd_kernel(GridDev g, const double2* __restrict__ R,
                                                   double2* __restrict__ st_om,
                                                   double2* __restrict__ st_w,
                                                   double2* __restrict__ st_phi,
@@ -1948,6 +1952,10 @@ __global__ void __launch_bounds__(ST) grouped_zsolve_kernel(const Member* __rest
 size_t zline_smem(const GridDev& g) {
   return (size_t)(NLINES * g.nz + 2 * NBF * g.N) * sizeof(double2);
 }
+// the coefficient-space kernels use the lines only (no DCT scratch)
+static size_t zline_coef_smem(const GridDev& g) {
+  return (size_t)NLINES * g.nz * sizeof(double2);
+}
 
 size_t fac_doubles(const GridDev& g) { return ((size_t)13 * g.nz + 20) * g.NK; }
 
@@ -1992,7 +2000,7 @@ cudaError_t launch_zrhs(int prec, const GridDev& g, const void* nl, long long fs
 static SmemLimit cur_zrhs_coef, cur_zbwd_coef;
 
 cudaError_t zline_coef_prepare(const GridDev& g) {
-  const size_t smem = zline_smem(g);
+  const size_t smem = zline_coef_smem(g);
   cudaError_t e = ensure_smem(zrhs_kernel<double, 1>, smem, &cur_zrhs_coef);
   if (e == cudaSuccess) e = ensure_smem(zbwd_kernel<double, 1, 5, 1>, smem, &cur_zbwd_coef);
   return e;
@@ -2002,10 +2010,10 @@ cudaError_t launch_zrhs_coef(const GridDev& g, const double2* cf, long long fs,
                              const double2* st_om, const double2* st_w, const double2* st_phi,
                              double2* h_om, double2* h_w, double2* h_phi, double2* R, int first,
                              const FftPlan& pz, cudaStream_t s) {
-  const size_t smem = zline_smem(g);
+  const size_t smem = zline_coef_smem(g);
   cudaError_t e = ensure_smem(zrhs_kernel<double, 1>, smem, &cur_zrhs_coef);
   if (e != cudaSuccess) return e;
-  zrhs_kernel<double, 1><<<g.Mx * g.ny, ZT, smem, s>>>(g, cf, fs, st_om, st_w, st_phi, h_om, h_w,
+  zrhs_kernel<double, 1><<<g.Mx * g.ny, ZTC, smem, s>>>(g, cf, fs, st_om, st_w, st_phi, h_om, h_w,
                                                        h_phi, R, first, pz);
   return cudaGetLastError();
 }
@@ -2013,10 +2021,10 @@ cudaError_t launch_zrhs_coef(const GridDev& g, const double2* cf, long long fs,
 cudaError_t launch_zbwd_coef(const GridDev& g, const double2* R, double2* st_om, double2* st_w,
                              double2* st_phi, double2* cf, long long fs, const FftPlan& pz,
                              cudaStream_t s) {
-  const size_t smem = zline_smem(g);
+  const size_t smem = zline_coef_smem(g);
   cudaError_t e = ensure_smem(zbwd_kernel<double, 1, 5, 1>, smem, &cur_zbwd_coef);
   if (e != cudaSuccess) return e;
-  zbwd_kernel<double, 1, 5, 1><<<g.Mx * g.ny, ZT, smem, s>>>(g, R, st_om, st_w, st_phi, cf, fs,
+  zbwd_kernel<double, 1, 5, 1><<<g.Mx * g.ny, ZTC, smem, s>>>(g, R, st_om, st_w, st_phi, cf, fs,
                                                              pz);
   return cudaGetLastError();
 }
