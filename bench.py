@@ -139,9 +139,9 @@ def kernel_work(w, prec, cheb="fft"):
     # the scope table; the paper's 2N-point even extension would be twice that); a derivative =
     # 4 flops per coefficient
     dct = fft_flops(N)
-    # zrhs: the 7 combined non-linear lines in, 7 DCTs, 9 derivatives, assembly, AB2 and the
-    # right-hand sides (108 flops per coefficient)
-    zrhs_fl = lines * (7 * dct + 9 * 4 * nz + 108 * nz)
+    # zrhs: the 7 combined non-linear lines in, 7 DCTs, 7 derivatives, assembly, AB2 and the
+    # right-hand sides (56 flops per coefficient)
+    zrhs_fl = lines * (7 * dct + 7 * 4 * nz + 56 * nz)
     zrhs_by = S * (b * 7 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)   # NL, state, hist in/out, R out
     zsolve_fl = lines * nz * (5 * 30 + 8)                       # 5 sweeps + influence correction
     zsolve_by = S * 16 * 3 * 2
@@ -165,7 +165,7 @@ def kernel_work(w, prec, cheb="fft"):
     tcb_fl = 36 * 2.0 * (5 * rows) * (NT * nNt) * Kp
     tcb_by = 5 * S * (16 + b)
     if cheb == "tc":
-        zrhs_fl = lines * (9 * 4 * nz + 108 * nz)
+        zrhs_fl = lines * (7 * 4 * nz + 56 * nz)
         zrhs_by = S * (16 * 7 + 16 * 3 + 16 * 3 + 16 * 3 + 16 * 3)
         zbwd_fl = lines * (2 * 4 * nz + 40 * nz)
         zbwd_by = S * (16 * 3 + 16 * 2 + 16 * 3 + 16 * 5)

@@ -33,9 +33,9 @@ int zsolve_threads();
 cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* begin, int nmem,
                              int grid, size_t smem, int zsolve_tile, int coef, cudaStream_t s);
 cudaError_t launch_grouped_xy(int stage, int prec, const Member* mem, const int* begin, int nmem,
-                              int grid, size_t smem, cudaStream_t s);
+                              int grid, size_t smem, int ywq, cudaStream_t s);
 int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile, int coef);
-int occupancy_xy(int stage, int prec, size_t smem);
+int occupancy_xy(int stage, int prec, size_t smem, int ywq);
 
 int stage_items(int stage, const Member& m, int prec) {
   (void)prec;
@@ -65,16 +65,26 @@ size_t stage_smem(int stage, const Member& m, int prec) {
   }
 }
 
-int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile, int coef) {
+int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile, int coef, int ywq) {
   return stage <= 2 ? occupancy_z(stage, prec, smem, zsolve_tile, coef)
-                    : occupancy_xy(stage, prec, smem);
+                    : occupancy_xy(stage, prec, smem, ywq);
 }
 
 cudaError_t launch_grouped(int stage, int prec, const Member* mem, const int* begin, int nmem,
-                           int grid, size_t smem, int zsolve_tile, int coef, cudaStream_t s) {
+                           int grid, size_t smem, int zsolve_tile, int coef, int ywq,
+                           cudaStream_t s) {
   if (stage <= 2)
     return launch_grouped_z(stage, prec, mem, begin, nmem, grid, smem, zsolve_tile, coef, s);
-  return launch_grouped_xy(stage, prec, mem, begin, nmem, grid, smem, s);
+  return launch_grouped_xy(stage, prec, mem, begin, nmem, grid, smem, ywq, s);
+}
+
+// the grouped y-pass kernels' warp-FFT level for the members' padded y lengths (float32): 0, 2
+// or 8, the largest warp-FFT q among them rounded up to an instantiated level
+int ensemble_ywq(const std::vector<int>& py, int prec) {
+  if (prec != 1) return 0;
+  int q = 0;
+  for (int P : py) q = std::max(q, warp_fft_q(P));
+  return q == 0 ? 0 : (q <= 2 ? 2 : 8);
 }
 
 }  // namespace chf
@@ -114,6 +124,8 @@ struct ch_ensemble {
   size_t smem[kStages];
   int occ[kStages];
   int zsolve_tile;
+  int ywq;                      // warp-FFT level of the grouped y passes (ensemble_ywq)
+  int xwq;                      // the same for the grouped x line (padded x lengths)
   Tuning tune;
   std::string signature;
   cudaGraphExec_t gexec;
@@ -272,7 +284,8 @@ int launch_all(ch_ensemble* E, cudaStream_t s, cudaEvent_t* ev) {
     if (tc && st == 0) e = member_transforms(E, 0, s);
     if (e == cudaSuccess)
       e = chf::launch_grouped(st, E->prec, E->dmem, E->dbegin + (size_t)st * (n + 1), n,
-                              grid_of(E, st), E->smem[st], E->zsolve_tile, tc, s);
+                              grid_of(E, st), E->smem[st], E->zsolve_tile, tc,
+                              st == 4 ? E->xwq : E->ywq, s);
     if (e == cudaSuccess && tc && st == 2) e = member_transforms(E, 1, s);
     if (ev) cudaEventRecord(ev[st], s);
     if (e != cudaSuccess) {
@@ -284,9 +297,16 @@ int launch_all(ch_ensemble* E, cudaStream_t s, cudaEvent_t* ev) {
 }
 
 void compute_occupancy(ch_ensemble* E) {
+  std::vector<int> py, px;
+  for (ch_grid* G : E->members) {
+    py.push_back(G->g.Py);
+    px.push_back(G->g.Px);
+  }
+  E->ywq = chf::ensemble_ywq(py, E->prec);
+  E->xwq = chf::ensemble_ywq(px, E->prec);
   for (int s = 0; s < kStages; ++s)
     E->occ[s] = chf::stage_occupancy(s, E->prec, E->smem[s], E->zsolve_tile,
-                                     E->cheb == CH_CHEB_TC);
+                                     E->cheb == CH_CHEB_TC, s == 4 ? E->xwq : E->ywq);
 }
 
 // tuning cache key: member sizes, precision and Chebyshev method

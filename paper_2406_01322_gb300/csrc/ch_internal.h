@@ -135,6 +135,13 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
 // Sxx', Syy', Sxy (outputs 0, 3), group 1 Sxz, Syz (0 on the mean line, 1, 2), group 2 u phi,
 // v phi (4), groups 3 and 4 w phi and phi^3; each group's z tile is the y pass's tile L divided
 // so that a CTA holds at most max(L, 3) lines.
+// q of the float32 warp-FFT path for a line of P = 96 q points (q = 1, 2, 4, 8), 0 otherwise:
+// such lines are transformed by one warp each with the line in registers (32 lanes x 3 q)
+__host__ __device__ __forceinline__ int warp_fft_q(int P) {
+  if (P % 96 != 0) return 0;
+  const int q = P / 96;
+  return (q == 1 || q == 2 || q == 4 || q == 8) ? q : 0;
+}
 constexpr int kNc = 7;            // combined non-linear lines
 constexpr int kYcGroups = 5;
 __host__ __device__ __forceinline__ int ycomb_nin(int grp) {
@@ -199,12 +206,15 @@ struct Member {
 // and zbwd writes Chebyshev coefficients in Member::cf (the tensor-core transforms run around
 // them) instead of transforming along z themselves.
 cudaError_t launch_grouped(int stage, int prec, const Member* mem, const int* begin, int nmem,
-                           int grid, size_t smem, int zsolve_tile, int coef, cudaStream_t s);
+                           int grid, size_t smem, int zsolve_tile, int coef, int ywq,
+                           cudaStream_t s);
+// ywq: the y stages' warp-FFT level for the members' padded y lengths (ensemble_ywq)
+int ensemble_ywq(const std::vector<int>& py, int prec);
 // work items of one member for a stage, and the dynamic shared memory one item needs
 int stage_items(int stage, const Member& m, int prec);
 size_t stage_smem(int stage, const Member& m, int prec);
 // CTAs per SM that the stage kernel can hold with `smem` bytes (occupancy API)
-int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile, int coef);
+int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile, int coef, int ywq);
 // y-pass z tile for a padded length P (shared by single-grid and grouped launches)
 int ytile_for(int P, size_t elem);
 // shared memory of a y-pass CTA: two tiles of tz lines of yline_stride(P) elements

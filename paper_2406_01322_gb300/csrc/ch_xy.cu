@@ -8,6 +8,8 @@
 //
 // Layout of every intermediate array: (mx, y or ky, z) with z fastest; a CTA owns a tile of
 // lines and does the layout change through shared memory.
+#include <type_traits>
+
 #include "ch_internal.h"
 
 namespace chf {
@@ -17,10 +19,205 @@ namespace {
 constexpr int YT = 256;   // threads of a y-pass CTA
 constexpr int XT = 256;   // threads of an x-line CTA
 
+// ---- warp-level FFTs (float32, length P = 32 R, R = 3 Q) -------------------------------------
+// One warp transforms one complex line of length P = 32 R with the line in registers: lane l
+// holds element l + 32 m in register m (natural layout).  The transform is factored as
+// P = R x 32 (Sec. 3.2.1's batched Fourier transforms, written as a two-level Cooley-Tukey
+// split): an R-point DFT over the registers of each lane, the twiddles W_P^(l k), and a
+// 32-point DFT across the lanes of each register by a radix-2 network of warp shuffles.
+//   backward (exp(+i)), natural input:  R-point DFT, twiddles, decimation-in-frequency network
+//     -> lane l, register k holds output k + R rev5(l) (rev5: 5-bit reversal);
+//   forward (exp(-i)) from that layout:  decimation-in-time network (bit-reversed input,
+//     natural output), twiddles, R-point DFT -> lane l, register m holds output l + 32 m.
+// So the physical samples stay in the backward transform's permuted order: the products are
+// pointwise and the forward transform reads them in that order.  The R-point DFT is split
+// R = 3 x Q: radix-3 DFTs over (m, m + Q, m + 2Q), twiddles W_R^(m k), then Q-point DFTs.
+// A backward transform of the 3/2-rule padding has zero input in registers Q .. 2Q - 1 (modes
+// Mx .. 2 Mx - 1), which its radix-3 DFTs skip.
+
+// R-point DFT of v (R = 3 Q) in registers, natural order in and out, exp(-i) or (INV) exp(+i);
+// tw: the length-32R table W_P^t, so W_R^j = tw[32 j]; PRUNE: v[Q .. 2Q - 1] are zero.
+template <int Q, bool INV, bool PRUNE>
+__device__ __forceinline__ void dft3q(float2 (&v)[3 * Q], const float2* __restrict__ tw) {
+  float2 t[3][Q];
+  const float s3 = 0.86602540378443864676f;   // sin(2 pi / 3)
+  const float sp = INV ? -s3 : s3;
+#pragma unroll
+  for (int m = 0; m < Q; ++m) {
+    const float2 a0 = v[m], a2 = v[m + 2 * Q];
+    float2 y0, y1, y2;
+    if (PRUNE) {
+      // a1 = 0: y0 = a0 + a2, y1,2 = a0 - a2 / 2 -+ i s (-a2)
+      const float2 mm = make_float2(fmaf(-0.5f, a2.x, a0.x), fmaf(-0.5f, a2.y, a0.y));
+      y0 = a0 + a2;
+      y1 = make_float2(fmaf(-sp, a2.y, mm.x), fmaf(sp, a2.x, mm.y));
+      y2 = make_float2(fmaf(sp, a2.y, mm.x), fmaf(-sp, a2.x, mm.y));
+    } else {
+      const float2 a1 = v[m + Q];
+      const float2 s = a1 + a2, d = a1 - a2;
+      const float2 mm = make_float2(fmaf(-0.5f, s.x, a0.x), fmaf(-0.5f, s.y, a0.y));
+      y0 = a0 + s;
+      y1 = make_float2(fmaf(sp, d.y, mm.x), fmaf(-sp, d.x, mm.y));
+      y2 = make_float2(fmaf(-sp, d.y, mm.x), fmaf(sp, d.x, mm.y));
+    }
+    t[0][m] = y0;
+    if (m == 0) {
+      t[1][m] = y1;
+      t[2][m] = y2;
+    } else {
+      const float2 w1 = tw[32 * m], w2 = tw[64 * m];
+      t[1][m] = INV ? cmulc(y1, w1) : cmul(y1, w1);
+      t[2][m] = INV ? cmulc(y2, w2) : cmul(y2, w2);
+    }
+  }
+#pragma unroll
+  for (int k3 = 0; k3 < 3; ++k3) {
+    if constexpr (Q > 1) Dft<float, Q, INV>::run(t[k3]);
+#pragma unroll
+    for (int kq = 0; kq < Q; ++kq) v[k3 + 3 * kq] = t[k3][kq];
+  }
+}
+
+// 32-point DFT across the lanes of every register.  DIF (natural in, bit-reversed out) for the
+// backward transform, DIT (bit-reversed in, natural out) for the forward one; ws[s] is this
+// lane's twiddle of the stage with span 16 >> s (DIF) or 1 << s (DIT): W_{2h}^(lane mod h)
+// for the lanes whose bit h is set, 1 otherwise (conjugated by the caller for INV).
+template <int R>
+__device__ __forceinline__ void lanes_dif(float2 (&v)[R], const float2 (&ws)[5], int lane) {
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int h = 16 >> s;
+    const bool up = (lane & h) != 0;
+    const float sg = up ? -1.0f : 1.0f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const float px = __shfl_xor_sync(0xffffffffu, v[k].x, h);
+      const float py = __shfl_xor_sync(0xffffffffu, v[k].y, h);
+      const float2 d = make_float2(fmaf(sg, v[k].x, px), fmaf(sg, v[k].y, py));
+      v[k] = (s < 4) ? cmul(d, ws[s]) : d;
+    }
+  }
+}
+template <int R>
+__device__ __forceinline__ void lanes_dit(float2 (&v)[R], const float2 (&ws)[5], int lane) {
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int h = 1 << s;
+    const bool up = (lane & h) != 0;
+    const float sg = up ? -1.0f : 1.0f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const float2 x = (s > 0) ? cmul(v[k], ws[s]) : v[k];
+      const float px = __shfl_xor_sync(0xffffffffu, x.x, h);
+      const float py = __shfl_xor_sync(0xffffffffu, x.y, h);
+      v[k] = make_float2(fmaf(sg, x.x, px), fmaf(sg, x.y, py));
+    }
+  }
+}
+
+// In-place float32 FFT of one line of P = 32 R points in shared memory by one warp (natural
+// order in and out): the R-point DFTs, twiddles W_P^(-+ l k) and the DIF lane network, the result
+// written back through the register-order index k 32 + l and read by warp_line_at.  PRUNE: the
+// line's middle third (positions 32 Q .. 64 Q - 1) is zero and not read.
+template <int Q, bool INV, bool PRUNE>
+__device__ __forceinline__ void warp_fft_line(float2* __restrict__ line,
+                                              const float2* __restrict__ tw, int lane) {
+  constexpr int R = 3 * Q;
+  float2 v[R];
+#pragma unroll
+  for (int m = 0; m < R; ++m)
+    v[m] = (PRUNE && m >= Q && m < 2 * Q) ? make_float2(0.0f, 0.0f) : line[lane + 32 * m];
+  __syncwarp();
+  dft3q<Q, INV, PRUNE>(v, tw);
+#pragma unroll
+  for (int k = 1; k < R; ++k) v[k] = INV ? cmulc(v[k], tw[k * lane]) : cmul(v[k], tw[k * lane]);
+  float2 ws[5];
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int h = 16 >> s;
+    ws[s] = (lane & h) ? tw[(lane & (h - 1)) * (16 * R / h)] : make_float2(1.0f, 0.0f);
+    if (INV) ws[s].y = -ws[s].y;
+  }
+  lanes_dif<R>(v, ws, lane);
+#pragma unroll
+  for (int k = 0; k < R; ++k) line[k * 32 + lane] = v[k];
+  __syncwarp();
+}
+// shared-memory index of output position p of warp_fft_line (p = k + R rev5(l) sits at k 32 + l)
+template <int Q>
+__device__ __forceinline__ int warp_line_at(int p) {
+  constexpr int R = 3 * Q;
+  const int j = p / R;
+  return (p - j * R) * 32 + (int)(__brev((unsigned)j) >> 27);
+}
+
+// Every line of a shared-memory tile (nlines lines of stride ls) through warp_fft_line, the warps
+// of the CTA taking lines in turn; q = P / 96 (QM: the only q when EXACT, else the largest q
+// the switch covers).  mid_zero: the lines' middle thirds are zero (a backward transform of the
+// 3/2-rule padding) and are not read.
+template <bool INV, int QM, bool EXACT>
+__device__ __forceinline__ void warp_lines(float2* A, int nlines, int ls, int q,
+                                           const float2* __restrict__ tw, bool mid_zero) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int ln = warp; ln < nlines; ln += nw) {
+    float2* L = A + ln * ls;
+    if constexpr (EXACT) {
+      mid_zero ? warp_fft_line<QM, INV, true>(L, tw, lane)
+               : warp_fft_line<QM, INV, false>(L, tw, lane);
+    } else {
+      if (q == 1) {
+        mid_zero ? warp_fft_line<1, INV, true>(L, tw, lane) : warp_fft_line<1, INV, false>(L, tw, lane);
+      } else if (q == 2) {
+        mid_zero ? warp_fft_line<2, INV, true>(L, tw, lane) : warp_fft_line<2, INV, false>(L, tw, lane);
+      } else if constexpr (QM >= 4) {
+        if (q == 4) {
+          mid_zero ? warp_fft_line<4, INV, true>(L, tw, lane) : warp_fft_line<4, INV, false>(L, tw, lane);
+        } else if constexpr (QM >= 8) {
+          mid_zero ? warp_fft_line<8, INV, true>(L, tw, lane) : warp_fft_line<8, INV, false>(L, tw, lane);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+// y transform of nl lines of a tile, in place (warp path, float32) or through the block passes
+// into A or B; returns the result buffer, *wq = the warp path's q (0: block passes).  WQ > 0:
+// the warp path with q = WQ only; WQ < 0: the warp path for q <= -WQ, else the block passes;
+// WQ = 0: the block passes.
+template <typename T, bool INV, int WQ>
+__device__ __forceinline__ const typename C2<T>::t* y_transform(typename C2<T>::t* A,
+                                                                typename C2<T>::t* B, int nl,
+                                                                int LS, int P, bool mid_zero,
+                                                                const FftPlan& pl, int* wq) {
+  if constexpr (std::is_same<T, float>::value && WQ != 0) {
+    const int q = WQ > 0 ? WQ : warp_fft_q(P);
+    if (WQ > 0 || (q != 0 && q <= -WQ)) {
+      warp_lines<INV, (WQ > 0 ? WQ : -WQ), (WQ > 0)>(A, nl, LS, q,
+                                                     reinterpret_cast<const float2*>(pl.tw),
+                                                     mid_zero);
+      *wq = q;
+      return A;
+    }
+  }
+  *wq = 0;
+  if constexpr (WQ > 0) {
+    return A;   // not reached: the exact warp path always applies
+  } else {
+    return block_fft<T, INV, true>(A, B, nl, LS, pl, true);
+  }
+}
+// shared-memory index of position p of a line transformed by warp_fft_line (R = 3 q; inv_r =
+// 1 / R as a float)
+__device__ __forceinline__ int warp_pos(int p, int R, float inv_r) {
+  int k;
+  const int j = fdivmod(p, R, inv_r, &k);
+  return k * 32 + (int)(__brev((unsigned)j) >> 27);
+}
+
 // y pass: one CTA per (z tile, mx, field).
 //   INV (backward): in (Mx, Ny, Nz) modes -> out (Mx, P, Nz) samples, modes |my| < Ny/2 placed,
 //   the rest zero.  Forward: in (Mx, P, Nz) samples -> out (Mx, Ny, Nz) kept modes * scale.
-template <typename T, bool INV>
+template <typename T, bool INV, int WQ>
 __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__ in,
                                            typename C2<T>::t* __restrict__ out, int Mx, int Ny,
                                            int P, int Nz, int TZ, long long fs_in,
@@ -67,13 +264,18 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
     }
   }
   __syncthreads();
-  const T2* R = block_fft<T, INV, true>(A, B, TZ, LS, pl, true);
+  // float32 lines of 96 q points: one warp per line in registers (warp_fft_line), the result
+  // in the register order that warp_pos maps; otherwise the block-cooperative passes
+  int wq;
+  const T2* R = y_transform<T, INV, WQ>(A, B, TZ, LS, P, INV && 2 * P == 3 * Ny, pl, &wq);
+  const int wr = 3 * wq;
+  const float inv_wr = wq ? 1.0f / (float)wr : 0.0f;
   if (INV) {
     T2* dst = out + f * fs_out + (size_t)mx * P * Nz;
     for (int idx = threadIdx.x; idx < P * TZ; idx += blockDim.x) {
       const int y = idx >> tzs, zz = idx & (TZ - 1);
       const int z = z0 + zz;
-      if (z < Nz) dst[(size_t)y * Nz + z] = R[zz * LS + y];
+      if (z < Nz) dst[(size_t)y * Nz + z] = R[zz * LS + (wq ? warp_pos(y, wr, inv_wr) : y)];
     }
   } else {
     T2* dst = out + f * fs_out + (size_t)mx * Ny * Nz;
@@ -82,26 +284,27 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
       const int z = z0 + zz;
       if (z >= Nz) continue;
       const int p = (jj < h) ? jj : P - Ny + jj;
-      dst[(size_t)jj * Nz + z] = (jj == h) ? zero : scale * R[zz * LS + p];
+      dst[(size_t)jj * Nz + z] =
+          (jj == h) ? zero : scale * R[zz * LS + (wq ? warp_pos(p, wr, inv_wr) : p)];
     }
   }
 }
 
-template <typename T, bool INV>
+template <typename T, bool INV, int WQ>
 __global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __restrict__ in,
                                                    typename C2<T>::t* __restrict__ out, int Mx,
                                                    int Ny, int P, int Nz, int TZ, long long fs_in,
                                                    long long fs_out, T scale, FftPlan pl,
                                                    YMap map) {
-  ypass_body<T, INV>(in, out, Mx, Ny, P, Nz, TZ, fs_in, fs_out, scale, pl, map, blockIdx.x,
-                     blockIdx.y, blockIdx.z);
+  ypass_body<T, INV, WQ>(in, out, Mx, Ny, P, Nz, TZ, fs_in, fs_out, scale, pl, map, blockIdx.x,
+                         blockIdx.y, blockIdx.z);
 }
 
 // Forward y pass with the assembly's combinations (launch_ycomb): work item -> (group, mx, z
 // tile); the nine products are transformed in groups so that each CTA holds every input its
 // outputs combine.  Groups and outputs as stated at launch_ycomb; the arithmetic of the
 // combinations is that of the working precision T.
-template <typename T>
+template <typename T, int WQ>
 __device__ __forceinline__ void ycomb_body(const typename C2<T>::t* __restrict__ in,
                                            typename C2<T>::t* __restrict__ out, int Mx, int Ny,
                                            int P, int Nz, int L, long long fs_in,
@@ -137,7 +340,10 @@ __device__ __forceinline__ void ycomb_body(const typename C2<T>::t* __restrict__
     }
   }
   __syncthreads();
-  const T2* R = block_fft<T, false, true>(A, B, nin * TZ, LS, pl, true);
+  int wq;
+  const T2* R = y_transform<T, false, WQ>(A, B, nin * TZ, LS, P, false, pl, &wq);
+  const int wr = 3 * wq;
+  const float inv_wr = wq ? 1.0f / (float)wr : 0.0f;
   const int h = Ny / 2;
   const T kx = kxs * (T)mx;
   T2* dst = out + (size_t)mx * Ny * Nz;
@@ -146,7 +352,8 @@ __device__ __forceinline__ void ycomb_body(const typename C2<T>::t* __restrict__
     const int z = z0 + zz;
     if (z >= Nz) continue;
     const size_t o = (size_t)jj * Nz + z;
-    const int p = (jj < h) ? jj : P - Ny + jj;
+    const int p0 = (jj < h) ? jj : P - Ny + jj;
+    const int p = wq ? warp_pos(p0, wr, inv_wr) : p0;
     const bool nyq = (jj == h);   // the y Nyquist row is zero
     const bool mean = (mx == 0 && jj == 0);
     const T ky = kys * (T)((jj < h) ? jj : jj - Ny);
@@ -175,13 +382,13 @@ __device__ __forceinline__ void ycomb_body(const typename C2<T>::t* __restrict__
   }
 }
 
-template <typename T>
+template <typename T, int WQ>
 __global__ void __launch_bounds__(YT) ycomb_kernel(const typename C2<T>::t* __restrict__ in,
                                                    typename C2<T>::t* __restrict__ out, int Mx,
                                                    int Ny, int P, int Nz, int L, long long fs_in,
                                                    long long fs_out, T scale, T kxs, T kys,
                                                    FftPlan pl) {
-  ycomb_body<T>(in, out, Mx, Ny, P, Nz, L, fs_in, fs_out, scale, kxs, kys, pl, blockIdx.x);
+  ycomb_body<T, WQ>(in, out, Mx, Ny, P, Nz, L, fs_in, fs_out, scale, kxs, kys, pl, blockIdx.x);
 }
 
 // Fused x-line kernel.  One CTA per (pair of z rows, y).  The two rows z0, z0+1 of a field are
@@ -294,6 +501,146 @@ __global__ void __launch_bounds__(NTH) xline_kernel(const typename C2<T>::t* __r
                                                    int Px, int Py, int Nz, long long fs, T kappa,
                                                    T scale, T kxs, FftPlan pl) {
   xline_body<T, LOOP>(in, out, Mx, Px, Py, Nz, fs, kappa, scale, kxs, pl, blockIdx.x, blockIdx.y);
+}
+
+// Fused x line on warp FFTs: one CTA per (pair of z rows, y) as xline_body, 8 warps.  Warps
+// 0..6 transform the seven input lines (u v w phi phi_x phi_y phi_z) into shared memory in the
+// backward transform's order; each warp then forms one product line (9 over the 8 warps) in
+// registers from those samples, transforms it forward and stores its kept modes.
+// Shared memory: seven lines of P float2, the twiddles W_P^(l k) as [k][l] (R x 32 float2).
+constexpr int XWT = 256;
+template <int Q>
+__device__ __forceinline__ void xline_warp_body(const float2* __restrict__ in,
+                                                float2* __restrict__ out, int Mx, int Py, int Nz,
+                                                long long fs, float kappa, float scale, float kxs,
+                                                const float2* __restrict__ tw, int bx, int by) {
+  constexpr int R = 3 * Q, P = 32 * R;
+  extern __shared__ float2 xw_sm[];
+  float2* phys = xw_sm;                 // 7 lines of P, index k * 32 + lane
+  float2* twl = xw_sm + 7 * P;          // W_P^(l k) at [k][l]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int z0 = 2 * bx;
+  const int y = by;
+  const bool two = (z0 + 1 < Nz);
+  const size_t base = (size_t)y * Nz + z0;
+  const size_t mstride = (size_t)Py * Nz;
+  for (int i = threadIdx.x; i < R * 32; i += blockDim.x) {
+    const int k = i >> 5, l = i & 31;
+    twl[i] = tw[k * l];                 // k l < P
+  }
+  // the lane-stage twiddles W_{2h}^j = W_P^(j 16 R / h)
+  float2 wdif[5], wdit[5];
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int hf = 16 >> s, ht = 1 << s;
+    wdif[s] = (lane & hf) ? tw[(lane & (hf - 1)) * (16 * R / hf)] : make_float2(1.0f, 0.0f);
+    wdif[s].y = -wdif[s].y;             // backward: exp(+i)
+    wdit[s] = (lane & ht) ? tw[(lane & (ht - 1)) * (16 * R / ht)] : make_float2(1.0f, 0.0f);
+  }
+  __syncthreads();
+  // ---- 1. seven backward lines (two z rows packed as a + i b), warp f = line f
+  if (warp < 7) {
+    const int f = warp;
+    const int src_f = (f < 4) ? f : f - 1;      // phi_x (line 4) comes from phi (input 3)
+    const float2* src = in + src_f * fs + base;
+    float2 v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      v[m] = make_float2(0.0f, 0.0f);
+      if (m >= Q && m < 2 * Q) continue;         // modes Mx .. 2 Mx - 1: zero padding
+      const int n = lane + 32 * m;
+      const int q = (m < Q) ? n : P - n;         // mode index (the upper third: negative modes)
+      if (q >= Mx) continue;                     // mode Mx (x Nyquist) is not kept
+      float2 a = src[(size_t)q * mstride];
+      float2 b = two ? src[(size_t)q * mstride + 1] : make_float2(0.0f, 0.0f);
+      if (f == 4) {                              // i kx phi
+        const float kx = kxs * (float)q;
+        a = make_float2(-kx * a.y, kx * a.x);
+        b = make_float2(-kx * b.y, kx * b.x);
+      }
+      if (n == 0) v[m] = make_float2(a.x, b.x);  // the imaginary part of a DC coefficient is not used
+      else if (m < Q) v[m] = make_float2(a.x - b.y, a.y + b.x);   // a + i b
+      else v[m] = make_float2(a.x + b.y, b.x - a.y);              // conj(a) + i conj(b)
+    }
+    dft3q<Q, true, true>(v, tw);
+#pragma unroll
+    for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], twl[k * 32 + lane]);
+    lanes_dif<R>(v, wdif, lane);
+#pragma unroll
+    for (int k = 0; k < R; ++k) phys[(f * R + k) * 32 + lane] = v[k];
+  }
+  __syncthreads();
+  // ---- 2. products (rows z0 in .x, z0+1 in .y) and forward transforms, one line per warp
+  const float hs = 0.5f * scale;
+  for (int g = warp; g < 9; g += 8) {
+    float2 v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int i = k * 32 + lane;
+      const float2 u = phys[i], vv = phys[R * 32 + i], w = phys[2 * R * 32 + i];
+      const float2 ph = phys[3 * R * 32 + i], fx = phys[4 * R * 32 + i];
+      const float2 fy = phys[5 * R * 32 + i], fz = phys[6 * R * 32 + i];
+      float2 r;
+      switch (g) {
+        case 0:
+          r.x = w.x * w.x + kappa * fz.x * fz.x - u.x * u.x - kappa * fx.x * fx.x;
+          r.y = w.y * w.y + kappa * fz.y * fz.y - u.y * u.y - kappa * fx.y * fx.y;
+          break;
+        case 1:
+          r.x = w.x * w.x + kappa * fz.x * fz.x - vv.x * vv.x - kappa * fy.x * fy.x;
+          r.y = w.y * w.y + kappa * fz.y * fz.y - vv.y * vv.y - kappa * fy.y * fy.y;
+          break;
+        case 2:
+          r = make_float2(-u.x * vv.x - kappa * fx.x * fy.x, -u.y * vv.y - kappa * fx.y * fy.y);
+          break;
+        case 3:
+          r = make_float2(-u.x * w.x - kappa * fx.x * fz.x, -u.y * w.y - kappa * fx.y * fz.y);
+          break;
+        case 4:
+          r = make_float2(-vv.x * w.x - kappa * fy.x * fz.x, -vv.y * w.y - kappa * fy.y * fz.y);
+          break;
+        case 5: r = make_float2(ph.x * ph.x * ph.x, ph.y * ph.y * ph.y); break;
+        case 6: r = make_float2(u.x * ph.x, u.y * ph.y); break;
+        case 7: r = make_float2(vv.x * ph.x, vv.y * ph.y); break;
+        default: r = make_float2(w.x * ph.x, w.y * ph.y); break;
+      }
+      v[k] = r;
+    }
+    lanes_dit<R>(v, wdit, lane);
+#pragma unroll
+    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], twl[k * 32 + lane]);
+    dft3q<Q, false, false>(v, tw);
+    // unpack the two real rows: A_k = (Z_k + conj Z_{P-k}) / 2, B_k = (Z_k - conj Z_{P-k}) / (2 i)
+    // for the kept modes k = lane + 32 m < Mx (m < Q); Z_{P-k} sits in lane -k mod 32, register
+    // R - 1 - m (lane 0: its own register R - m)
+    float2* dst = out + g * fs + base;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      const float2 o = v[R - 1 - m];
+      const int pl = (32 - lane) & 31;
+      float2 Zm = make_float2(__shfl_sync(0xffffffffu, o.x, pl), __shfl_sync(0xffffffffu, o.y, pl));
+      if (lane == 0) Zm = (m == 0) ? v[0] : v[(R - m) % R];
+      const float2 Zk = v[m];
+      const int k = lane + 32 * m;
+      if (k < Mx) {
+        float2* d = dst + (size_t)k * mstride;
+        d[0] = make_float2(hs * (Zk.x + Zm.x), hs * (Zk.y - Zm.y));
+        if (two) d[1] = make_float2(hs * (Zk.y + Zm.y), hs * (Zm.x - Zk.x));
+      }
+    }
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(XWT, Q >= 8 ? 2 : 3)
+    xline_warp_kernel(const float2* __restrict__ in, float2* __restrict__ out, int Mx, int Py,
+                      int Nz, long long fs, float kappa, float scale, float kxs,
+                      const float2* __restrict__ tw) {
+  xline_warp_body<Q>(in, out, Mx, Py, Nz, fs, kappa, scale, kxs, tw, blockIdx.x, blockIdx.y);
+}
+// shared memory of the warp-FFT x line
+__host__ __device__ __forceinline__ size_t xline_warp_smem(int Px) {
+  return (size_t)8 * Px * sizeof(float2);
 }
 
 // plain r2c along x of physical rows (Nz, Ny, Nx) -> (Mx, Ny, Nz); two z rows per CTA
@@ -512,7 +859,9 @@ __device__ __forceinline__ int member_of_xy(const int* __restrict__ begin, int n
   return m;
 }
 
-template <typename T, bool INV>
+// GQ: the largest warp-FFT q among the members (0, 2 or 8; float32), the same path per member as
+// the single-grid launch takes
+template <typename T, bool INV, int GQ>
 __global__ void __launch_bounds__(YT) grouped_ypass_kernel(const Member* __restrict__ mem,
                                                            const int* __restrict__ begin, int nmem) {
   typedef typename C2<T>::t T2;
@@ -526,17 +875,17 @@ __global__ void __launch_bounds__(YT) grouped_ypass_kernel(const Member* __restr
     const int bx = local % nzt, rest = local / nzt;
     const int by = rest % M.g.Mx, bz = rest / M.g.Mx;
     if (INV)
-      ypass_body<T, true>((const T2*)M.bw, (T2*)M.ya, M.g.Mx, M.g.ny, M.g.Py, M.g.nz, TZ, M.fs,
-                          M.fsy, (T)1, M.py, M.ym, bx, by, bz);
+      ypass_body<T, true, -GQ>((const T2*)M.bw, (T2*)M.ya, M.g.Mx, M.g.ny, M.g.Py, M.g.nz, TZ,
+                               M.fs, M.fsy, (T)1, M.py, M.ym, bx, by, bz);
     else
-      ypass_body<T, false>((const T2*)M.yb, (T2*)M.nl, M.g.Mx, M.g.ny, M.g.Py, M.g.nz, TZ, M.fsy,
-                           M.fs, (T)M.yscale, M.py, M.yf, bx, by, bz);
+      ypass_body<T, false, -GQ>((const T2*)M.yb, (T2*)M.nl, M.g.Mx, M.g.ny, M.g.Py, M.g.nz, TZ,
+                                M.fsy, M.fs, (T)M.yscale, M.py, M.yf, bx, by, bz);
     __syncthreads();
   }
 }
 
 // grouped forward y pass with the combinations: items (group, mx, z tile) member by member
-template <typename T>
+template <typename T, int GQ>
 __global__ void __launch_bounds__(YT) grouped_ycomb_kernel(const Member* __restrict__ mem,
                                                            const int* __restrict__ begin, int nmem) {
   typedef typename C2<T>::t T2;
@@ -544,14 +893,16 @@ __global__ void __launch_bounds__(YT) grouped_ycomb_kernel(const Member* __restr
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int m = member_of_xy(begin, nmem, item);
     const Member& M = mem[m];
-    ycomb_body<T>((const T2*)M.yb, (T2*)M.nl, M.g.Mx, M.g.ny, M.g.Py, M.g.nz, M.tzf, M.fsy, M.fs,
-                  (T)M.yscale, (T)M.kxs, (T)M.ym.kys, M.py, item - begin[m]);
+    ycomb_body<T, -GQ>((const T2*)M.yb, (T2*)M.nl, M.g.Mx, M.g.ny, M.g.Py, M.g.nz, M.tzf,
+                       M.fsy, M.fs, (T)M.yscale, (T)M.kxs, (T)M.ym.kys, M.py, item - begin[m]);
     __syncthreads();
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(XT) grouped_xline_kernel(const Member* __restrict__ mem,
+// GQ: as in grouped_ypass_kernel, for the members' padded x lengths (float32 lines of 96 q
+// points take the warp-FFT body, as the single-grid launch does)
+template <typename T, int GQ>
+__global__ void __launch_bounds__(XT, GQ >= 8 ? 2 : 3) grouped_xline_kernel(const Member* __restrict__ mem,
                                                            const int* __restrict__ begin, int nmem) {
   typedef typename C2<T>::t T2;
   const int total = begin[nmem];
@@ -560,8 +911,34 @@ __global__ void __launch_bounds__(XT) grouped_xline_kernel(const Member* __restr
     const Member& M = mem[m];
     const int nzp = (M.g.nz + 1) / 2;
     const int local = item - begin[m];
-    xline_body<T>((const T2*)M.ya, (T2*)M.yb, M.g.Mx, M.g.Px, M.g.Py, M.g.nz, M.fsy,
-                  (T)M.g.kappa, (T)1, (T)M.kxs, M.px, local % nzp, local / nzp);
+    const int bx = local % nzp, by = local / nzp;
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value && GQ > 0) {
+      const int q = (M.px.n == M.g.Px) ? warp_fft_q(M.g.Px) : 0;
+      const float2* tw = (const float2*)M.px.tw;
+      if (q == 1) {
+        xline_warp_body<1>((const float2*)M.ya, (float2*)M.yb, M.g.Mx, M.g.Py, M.g.nz, M.fsy,
+                           (float)M.g.kappa, 1.0f, (float)M.kxs, tw, bx, by);
+        done = true;
+      } else if (q == 2) {
+        xline_warp_body<2>((const float2*)M.ya, (float2*)M.yb, M.g.Mx, M.g.Py, M.g.nz, M.fsy,
+                           (float)M.g.kappa, 1.0f, (float)M.kxs, tw, bx, by);
+        done = true;
+      } else if constexpr (GQ >= 8) {
+        if (q == 4) {
+          xline_warp_body<4>((const float2*)M.ya, (float2*)M.yb, M.g.Mx, M.g.Py, M.g.nz, M.fsy,
+                             (float)M.g.kappa, 1.0f, (float)M.kxs, tw, bx, by);
+          done = true;
+        } else if (q == 8) {
+          xline_warp_body<8>((const float2*)M.ya, (float2*)M.yb, M.g.Mx, M.g.Py, M.g.nz, M.fsy,
+                             (float)M.g.kappa, 1.0f, (float)M.kxs, tw, bx, by);
+          done = true;
+        }
+      }
+    }
+    if (!done)
+      xline_body<T>((const T2*)M.ya, (T2*)M.yb, M.g.Mx, M.g.Px, M.g.Py, M.g.nz, M.fsy,
+                    (T)M.g.kappa, (T)1, (T)M.kxs, M.px, bx, by);
     __syncthreads();
   }
 }
@@ -583,25 +960,34 @@ cudaError_t launch_ypass(int dir, int prec, const GridDev& g, int P, const void*
   const int TZ = ytile_local(P, elem);
   const size_t smem = ysmem_bytes(P, TZ, elem);
   dim3 grid((g.nz + TZ - 1) / TZ, g.Mx, nf);
-  static SmemLimit cur[6];
+  // float32 lines of 96 q points take the warp-FFT kernels (one instantiation per q)
+  const int wq = prec == 1 ? warp_fft_q(P) : 0;
+  static SmemLimit cur[6][5];
+  const int ci = wq == 0 ? 0 : wq == 1 ? 1 : wq == 2 ? 2 : wq == 4 ? 3 : 4;
   cudaError_t e = cudaSuccess;
-  if (prec == 0) e = dir == 1 ? ensure_smem(ypass_kernel<double, true>, smem, &cur[0])
-                              : ensure_smem(ypass_kernel<double, false>, smem, &cur[1]);
-  else if (prec == 1) e = dir == 1 ? ensure_smem(ypass_kernel<float, true>, smem, &cur[2])
-                                   : ensure_smem(ypass_kernel<float, false>, smem, &cur[3]);
-  else e = dir == 1 ? ensure_smem(ypass_kernel<df, true>, smem, &cur[4])
-                    : ensure_smem(ypass_kernel<df, false>, smem, &cur[5]);
-  if (e != cudaSuccess) return e;
-#define YL(T, INV)                                                                            \
-  ypass_kernel<T, INV><<<grid, YT, smem, s>>>((const C2<T>::t*)in, (C2<T>::t*)out, g.Mx, g.ny, \
-                                              P, g.nz, TZ, fs_in, fs_out, T(scale), py, map);
-  if (prec == 0) {
-    if (dir == 1) { YL(double, true) } else { YL(double, false) }
-  } else if (prec == 1) {
-    if (dir == 1) { YL(float, true) } else { YL(float, false) }
-  } else {
-    if (dir == 1) { YL(df, true) } else { YL(df, false) }
+#define YL(T, INV, Q, K)                                                                       \
+  {                                                                                            \
+    if ((e = ensure_smem(ypass_kernel<T, INV, Q>, smem, &cur[K][ci])) != cudaSuccess) return e;  \
+    ypass_kernel<T, INV, Q><<<grid, YT, smem, s>>>((const C2<T>::t*)in, (C2<T>::t*)out, g.Mx,   \
+                                                   g.ny, P, g.nz, TZ, fs_in, fs_out, T(scale),  \
+                                                   py, map);                                    \
   }
+#define YLF(INV, K)                                       \
+  switch (wq) {                                           \
+    case 1: YL(float, INV, 1, K) break;                   \
+    case 2: YL(float, INV, 2, K) break;                   \
+    case 4: YL(float, INV, 4, K) break;                   \
+    case 8: YL(float, INV, 8, K) break;                   \
+    default: YL(float, INV, 0, K) break;                  \
+  }
+  if (prec == 0) {
+    if (dir == 1) YL(double, true, 0, 0) else YL(double, false, 0, 1)
+  } else if (prec == 1) {
+    if (dir == 1) { YLF(true, 2) } else { YLF(false, 3) }
+  } else {
+    if (dir == 1) YL(df, true, 0, 4) else YL(df, false, 0, 5)
+  }
+#undef YLF
 #undef YL
   return cudaGetLastError();
 }
@@ -612,23 +998,31 @@ cudaError_t launch_ycomb(int prec, const GridDev& g, const void* in, void* out, 
   const int L = ytile_local(g.Py, elem);
   const size_t smem = ycomb_smem(g.Py, L, elem);
   const int items = ycomb_items(g.Mx, g.nz, L);
-  static SmemLimit cur[3];
-  cudaError_t e = prec == 0   ? ensure_smem(ycomb_kernel<double>, smem, &cur[0])
-                  : prec == 1 ? ensure_smem(ycomb_kernel<float>, smem, &cur[1])
-                              : ensure_smem(ycomb_kernel<df>, smem, &cur[2]);
-  if (e != cudaSuccess) return e;
+  const int wq = prec == 1 ? warp_fft_q(g.Py) : 0;
+  static SmemLimit cur[7];
+  cudaError_t e = cudaSuccess;
   const double kxs = 6.283185307179586476925 / g.lx, kys = 6.283185307179586476925 / g.ly;
-  if (prec == 0)
-    ycomb_kernel<double><<<items, YT, smem, s>>>((const double2*)in, (double2*)out, g.Mx, g.ny,
-                                                 g.Py, g.nz, L, fs_in, fs_out, scale, kxs, kys,
-                                                 py);
-  else if (prec == 1)
-    ycomb_kernel<float><<<items, YT, smem, s>>>((const float2*)in, (float2*)out, g.Mx, g.ny,
-                                                g.Py, g.nz, L, fs_in, fs_out, (float)scale,
-                                                (float)kxs, (float)kys, py);
-  else
-    ycomb_kernel<df><<<items, YT, smem, s>>>((const df2*)in, (df2*)out, g.Mx, g.ny, g.Py, g.nz,
-                                             L, fs_in, fs_out, df(scale), df(kxs), df(kys), py);
+#define YC(T, Q, K, ...)                                                                      \
+  {                                                                                           \
+    if ((e = ensure_smem(ycomb_kernel<T, Q>, smem, &cur[K])) != cudaSuccess) return e;         \
+    ycomb_kernel<T, Q><<<items, YT, smem, s>>>((const C2<T>::t*)in, (C2<T>::t*)out, g.Mx, g.ny, \
+                                               g.Py, g.nz, L, fs_in, fs_out, __VA_ARGS__, py);  \
+  }
+  if (prec == 0) {
+    YC(double, 0, 0, scale, kxs, kys)
+  } else if (prec == 1) {
+    const float a = (float)scale, b = (float)kxs, c = (float)kys;
+    switch (wq) {
+      case 1: YC(float, 1, 1, a, b, c) break;
+      case 2: YC(float, 2, 2, a, b, c) break;
+      case 4: YC(float, 4, 3, a, b, c) break;
+      case 8: YC(float, 8, 4, a, b, c) break;
+      default: YC(float, 0, 5, a, b, c) break;
+    }
+  } else {
+    YC(df, 0, 6, df(scale), df(kxs), df(kys))
+  }
+#undef YC
   return cudaGetLastError();
 }
 
@@ -659,8 +1053,33 @@ cudaError_t launch_xline_t(int prec, const GridDev& g, const void* in7, void* ou
   return cudaGetLastError();
 }
 
+template <int Q>
+cudaError_t launch_xline_warp(const GridDev& g, const void* in7, void* out10, long long fs,
+                              double scale, const FftPlan& px, cudaStream_t s) {
+  const size_t smem = (size_t)8 * g.Px * sizeof(float2);
+  static SmemLimit cur;
+  const cudaError_t e = ensure_smem(xline_warp_kernel<Q>, smem, &cur);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.nz + 1) / 2, g.Py);
+  xline_warp_kernel<Q><<<grid, XWT, smem, s>>>((const float2*)in7, (float2*)out10, g.Mx, g.Py,
+                                               g.nz, fs, (float)g.kappa, (float)scale,
+                                               (float)(6.283185307179586476925 / g.lx),
+                                               (const float2*)px.tw);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_xline(int prec, const GridDev& g, const void* in7, void* out10, long long fs,
                          double scale, const FftPlan& px, cudaStream_t s) {
+  // float32 lines of 96, 192, 384 or 768 points: the warp-FFT kernel
+  if (prec == 1 && g.Px % 96 == 0 && px.n == g.Px) {
+    switch (g.Px / 96) {
+      case 1: return launch_xline_warp<1>(g, in7, out10, fs, scale, px, s);
+      case 2: return launch_xline_warp<2>(g, in7, out10, fs, scale, px, s);
+      case 4: return launch_xline_warp<4>(g, in7, out10, fs, scale, px, s);
+      case 8: return launch_xline_warp<8>(g, in7, out10, fs, scale, px, s);
+      default: break;
+    }
+  }
   const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);
   const size_t smem = xline_smem(g.Px, elem);
   // Long x lines, where shared memory limits the CTAs per SM to two (float32) or one (16-byte
@@ -714,45 +1133,64 @@ namespace chf {
 int ytile_for(int P, size_t elem) { return ytile_local(P, elem); }
 size_t xline_smem(int Px, size_t elem) { return (size_t)17 * fft_line_stride(Px) * elem; }
 
-cudaError_t launch_grouped_xy(int stage, int prec, const Member* mem, const int* begin, int nmem,
-                              int grid, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaSuccess;
-  static SmemLimit cur[9];
-#define GL(K, idx, T_)                                                   \
-  if ((e = ensure_smem(K, smem, &cur[idx])) != cudaSuccess) return e;    \
-  K<<<grid, (stage == 4 ? XT : YT), smem, s>>>(mem, begin, nmem);
+// the grouped y-pass kernel of a stage (3 backward, 5 forward), precision and member warp-FFT
+// level ywq (0, 2 or 8)
+static const void* grouped_y_kernel(int stage, int prec, int ywq) {
   if (stage == 3) {
-    if (prec == 0) { GL((grouped_ypass_kernel<double, true>), 0, double) }
-    else if (prec == 1) { GL((grouped_ypass_kernel<float, true>), 1, float) }
-    else { GL((grouped_ypass_kernel<df, true>), 6, df) }
-  } else if (stage == 4) {
-    if (prec == 0) { GL(grouped_xline_kernel<double>, 2, double) }
-    else if (prec == 1) { GL(grouped_xline_kernel<float>, 3, float) }
-    else { GL(grouped_xline_kernel<df>, 7, df) }
-  } else {
-    if (prec == 0) { GL(grouped_ycomb_kernel<double>, 4, double) }
-    else if (prec == 1) { GL(grouped_ycomb_kernel<float>, 5, float) }
-    else { GL(grouped_ycomb_kernel<df>, 8, df) }
+    if (prec == 0) return (const void*)grouped_ypass_kernel<double, true, 0>;
+    if (prec == 2) return (const void*)grouped_ypass_kernel<df, true, 0>;
+    return ywq == 0 ? (const void*)grouped_ypass_kernel<float, true, 0>
+         : ywq == 2 ? (const void*)grouped_ypass_kernel<float, true, 2>
+                    : (const void*)grouped_ypass_kernel<float, true, 8>;
   }
-#undef GL
-  return cudaGetLastError();
+  if (prec == 0) return (const void*)grouped_ycomb_kernel<double, 0>;
+  if (prec == 2) return (const void*)grouped_ycomb_kernel<df, 0>;
+  return ywq == 0 ? (const void*)grouped_ycomb_kernel<float, 0>
+       : ywq == 2 ? (const void*)grouped_ycomb_kernel<float, 2>
+                  : (const void*)grouped_ycomb_kernel<float, 8>;
 }
 
-int occupancy_xy(int stage, int prec, size_t smem) {
+cudaError_t launch_grouped_xy(int stage, int prec, const Member* mem, const int* begin, int nmem,
+                              int grid, size_t smem, int ywq, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  static SmemLimit cur[5];
+  static SmemLimit cury[2][3][3];
+  if (stage == 4) {
+#define GL(K, idx)                                                     \
+  if ((e = ensure_smem(K, smem, &cur[idx])) != cudaSuccess) return e;  \
+  K<<<grid, XT, smem, s>>>(mem, begin, nmem);
+    if (prec == 0) { GL((grouped_xline_kernel<double, 0>), 0) }
+    else if (prec == 1) {
+      if (ywq == 0) { GL((grouped_xline_kernel<float, 0>), 1) }
+      else if (ywq == 2) { GL((grouped_xline_kernel<float, 2>), 3) }
+      else { GL((grouped_xline_kernel<float, 8>), 4) }
+    } else { GL((grouped_xline_kernel<df, 0>), 2) }
+#undef GL
+    return cudaGetLastError();
+  }
+  const void* k = grouped_y_kernel(stage, prec, ywq);
+  const int wi = ywq == 0 ? 0 : ywq == 2 ? 1 : 2;
+  if ((e = ensure_smem(k, smem, &cury[stage == 3 ? 0 : 1][prec][wi])) != cudaSuccess) return e;
+  void* args[] = {(void*)&mem, (void*)&begin, (void*)&nmem};
+  e = cudaLaunchKernel(k, dim3(grid), dim3(YT), args, smem, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  return cudaSuccess;
+}
+
+int occupancy_xy(int stage, int prec, size_t smem, int ywq) {
   int n = 0;
   const void* k;
-  if (stage == 3)
-    k = prec == 0 ? (const void*)grouped_ypass_kernel<double, true>
-      : prec == 1 ? (const void*)grouped_ypass_kernel<float, true>
-                  : (const void*)grouped_ypass_kernel<df, true>;
-  else if (stage == 4)
-    k = prec == 0 ? (const void*)grouped_xline_kernel<double>
-      : prec == 1 ? (const void*)grouped_xline_kernel<float>
-                  : (const void*)grouped_xline_kernel<df>;
+  if (stage == 4)
+    k = prec == 0 ? (const void*)grouped_xline_kernel<double, 0>
+      : prec == 2 ? (const void*)grouped_xline_kernel<df, 0>
+      : ywq == 0  ? (const void*)grouped_xline_kernel<float, 0>
+      : ywq == 2  ? (const void*)grouped_xline_kernel<float, 2>
+                  : (const void*)grouped_xline_kernel<float, 8>;
   else
-    k = prec == 0 ? (const void*)grouped_ycomb_kernel<double>
-      : prec == 1 ? (const void*)grouped_ycomb_kernel<float>
-                  : (const void*)grouped_ycomb_kernel<df>;
+    k = grouped_y_kernel(stage, prec, ywq);
   if (smem > 48 * 1024) {  // opt-in first (init time, never during capture)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaGetLastError();

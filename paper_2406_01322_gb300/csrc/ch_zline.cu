@@ -408,28 +408,40 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   for (int n = tid; n < Nz; n += blockDim.x)
     LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * LN(z, 12, Nz)[n];
   __syncthreads();
+  // Seven derivatives (D is linear, so the second derivatives of the assembly are taken of
+  // sums): h_w = -k^2 C - D(R + D C), S_phi = F - (k^2 / Pe) G + D(D G / Pe - w phi),
+  // theta^n = D^2 w - k^2 w, h_omega = P + D Q.
   {
-    double2* src[6] = {LN(z, 1, Nz), LN(z, 3, Nz), LN(z, 2, Nz), LN(z, 5, Nz), LN(z, 6, Nz),
-                       LN(z, 11, Nz)};
-    double2* dst[6] = {LN(z, 7, Nz), LN(z, 8, Nz), LN(z, 9, Nz), LN(z, 13, Nz), LN(z, 14, Nz),
-                       LN(z, 15, Nz)};
-    dz_tasks(src, dst, 6, N);   // DQ, DR, DC, D(w phi), DG, Dw
+    double2* src[5] = {LN(z, 1, Nz), LN(z, 2, Nz), LN(z, 6, Nz), LN(z, 11, Nz), LN(z, 0, Nz)};
+    double2* dst[5] = {LN(z, 7, Nz), LN(z, 9, Nz), LN(z, 14, Nz), LN(z, 15, Nz), LN(z, 13, Nz)};
+    dz_tasks(src, dst, is00 ? 5 : 4, N);   // DQ, DC, DG, Dw (, D Sxz on (0,0))
   }
   __syncthreads();
   const double rpe = 1.0 / g.pe;
-  for (int n = tid; n < Nz; n += blockDim.x)  // partial S_phi = F - D(w phi) - k^2 G / Pe
-    LN(z, 4, Nz)[n] = LN(z, 4, Nz)[n] - LN(z, 13, Nz)[n] - (k2 * rpe) * LN(z, 6, Nz)[n];
-  __syncthreads();
-  {
-    double2* src[4] = {LN(z, 9, Nz), LN(z, 14, Nz), LN(z, 15, Nz), LN(z, 0, Nz)};
-    double2* dst[4] = {LN(z, 3, Nz), LN(z, 5, Nz), LN(z, 1, Nz), LN(z, 13, Nz)};
-    dz_tasks(src, dst, is00 ? 4 : 3, N);   // D^2 C, D^2 G, D^2 w (, D Sxz on (0,0))
+  const double k2rpe = k2 * rpe;
+  for (int n = tid; n < Nz; n += blockDim.x) {
+    const double2 c = LN(z, 3, Nz)[n], dc = LN(z, 9, Nz)[n];
+    const double2 wp = LN(z, 5, Nz)[n], dg = LN(z, 14, Nz)[n];
+    const double2 f = LN(z, 4, Nz)[n], gg = LN(z, 6, Nz)[n];
+    LN(z, 3, Nz)[n] = c + dc;                                                  // R + D C
+    LN(z, 5, Nz)[n] = make_double2(fma(rpe, dg.x, -wp.x), fma(rpe, dg.y, -wp.y));  // D G / Pe - w phi
+    LN(z, 4, Nz)[n] = make_double2(fma(-k2rpe, gg.x, f.x), fma(-k2rpe, gg.y, f.y));  // F - k^2 G / Pe
   }
   __syncthreads();
-  // h_omega, h_w, S_phi, theta^n = (D^2 - k^2) w^n; AB2; right-hand sides
-  const double twoRe = 2.0 * g.re;
+  {
+    double2* src[3] = {LN(z, 3, Nz), LN(z, 5, Nz), LN(z, 15, Nz)};
+    double2* dst[3] = {LN(z, 8, Nz), LN(z, 9, Nz), LN(z, 14, Nz)};
+    dz_tasks(src, dst, 3, N);   // D(R + D C), D(D G / Pe - w phi), D^2 w
+  }
+  __syncthreads();
+  // h_omega, h_w, S_phi, theta^n = (D^2 - k^2) w^n; AB2 folded into the right-hand sides:
+  //   R_q = -2 beta q^n - 2 Re (a h^n + b h^{n-1}),  R_phi = (Pe / Ch^2)(phi^n / dt + a S^n + b S^{n-1})
+  // with (a, b) = (3/2, -1/2), or (1, 0) on the first step
   const double cphi = g.pe / (g.ch * g.ch);
-  const double rdt = 1.0 / g.dt;
+  const double cb = -2.0 * g.beta;
+  const double ca = first ? -2.0 * g.re : -3.0 * g.re, cm = g.re;    // -2 Re a, -2 Re b
+  const double pa = first ? cphi : 1.5 * cphi, pm = -0.5 * cphi;     // cphi a, cphi b
+  const double prd = cphi / g.dt;
   for (int n = tid; n < Nz; n += blockDim.x) {
     double2 hom, hw;
     if (is00) {  // mean flow: Sbar_x + i Sbar_y + (gx + i gy) delta_{n0}
@@ -437,23 +449,29 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
                          LN(z, 7, Nz)[n].x + (n == 0 ? g.gy : 0.0));
       hw = make_double2(0.0, 0.0);
     } else {
+      const double2 c = LN(z, 2, Nz)[n], d = LN(z, 8, Nz)[n];
       hom = LN(z, 0, Nz)[n] + LN(z, 7, Nz)[n];                                  // P + D Q
-      hw = (-k2) * LN(z, 2, Nz)[n] - LN(z, 8, Nz)[n] - LN(z, 3, Nz)[n];        // -k^2 C - DR - D^2 C
+      hw = make_double2(fma(-k2, c.x, -d.x), fma(-k2, c.y, -d.y));             // -k^2 C - D(R + D C)
     }
-    const double2 sphi = LN(z, 4, Nz)[n] + rpe * LN(z, 5, Nz)[n];
-    const double2 th = LN(z, 1, Nz)[n] - k2 * LN(z, 11, Nz)[n];
-    double2 Hom = hom, Hw = hw, Hphi = sphi;
+    const double2 sphi = LN(z, 4, Nz)[n] + LN(z, 9, Nz)[n];
+    const double2 w = LN(z, 11, Nz)[n], d2w = LN(z, 14, Nz)[n];
+    const double2 th = make_double2(fma(-k2, w.x, d2w.x), fma(-k2, w.y, d2w.y));
+    const double2 om = LN(z, 10, Nz)[n], ph = LN(z, 12, Nz)[n];
+    double2 r0 = make_double2(cb * om.x, cb * om.y);
+    double2 r1 = make_double2(cb * th.x, cb * th.y);
+    double2 r2 = make_double2(prd * ph.x, prd * ph.y);
     if (!first) {
-      Hom = 1.5 * hom - 0.5 * h_om[off + n];
-      Hw = 1.5 * hw - 0.5 * h_w[off + n];
-      Hphi = 1.5 * sphi - 0.5 * h_phi[off + n];
+      const double2 o0 = h_om[off + n], o1 = h_w[off + n], o2 = h_phi[off + n];
+      r0 = make_double2(fma(cm, o0.x, r0.x), fma(cm, o0.y, r0.y));
+      r1 = make_double2(fma(cm, o1.x, r1.x), fma(cm, o1.y, r1.y));
+      r2 = make_double2(fma(pm, o2.x, r2.x), fma(pm, o2.y, r2.y));
     }
     h_om[off + n] = hom;
     h_w[off + n] = hw;
     h_phi[off + n] = sphi;
-    Rom[off + n] = (-2.0 * g.beta) * LN(z, 10, Nz)[n] - twoRe * Hom;
-    Rth[off + n] = (-2.0 * g.beta) * th - twoRe * Hw;
-    Rps[off + n] = cphi * (rdt * LN(z, 12, Nz)[n] + Hphi);
+    Rom[off + n] = make_double2(fma(ca, hom.x, r0.x), fma(ca, hom.y, r0.y));
+    Rth[off + n] = make_double2(fma(ca, hw.x, r1.x), fma(ca, hw.y, r1.y));
+    Rps[off + n] = make_double2(fma(pa, sphi.x, r2.x), fma(pa, sphi.y, r2.y));
   }
 }
 

@@ -110,6 +110,31 @@ def test_wide_grid_nonlinear_terms(binding, wide_case, precision, tol):
     g.close()
 
 
+@pytest.mark.parametrize("nx", [64, 128, 256, 512])
+def test_float32_x_line_lengths(binding, nx):
+    """The float32 x line at every padded length its warp-FFT kernel takes (Px = 96, 192, 384,
+    768: 32 lanes x 3, 6, 12, 24 registers), on a short y/z grid: the nine non-linear fields
+    against the oracle (1e-5, the mixed single-stage tolerance) and one mixed step against one
+    float64 step (2e-5 of each spectral field: float32 products and transforms round at 6e-8,
+    and the step's transforms and divergences of the products carry that to a few 1e-6)."""
+    w = dict(inputs.WORKLOADS["channel_512x256x257_mixed"], nx=nx, ny=16, nz=9)
+    fields = inputs.initial_fields(**w)
+    o = oracle_for(w, fields)
+    r = o.nonlinear_spectral()
+    nl = [r[0] - r[2], r[1] - r[2], r[3], r[4], r[5], r[6], r[7], r[8], r[9]]
+    g = grid_for(binding, w, fields, 1)
+    got = g.nonlinear()
+    for k in range(9):
+        assert rel(spec_to_oracle(got[k]), nl[k]) < 1e-5, k
+    g64 = grid_for(binding, w, fields, 0)
+    g.step(1)
+    g64.step(1)
+    for a, b in zip(g.get_spectral(), g64.get_spectral()):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) < 2e-5
+    g.close()
+    g64.close()
+
+
 @pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "dfloat"])
 def test_wide_grid_one_step(binding, wide_case, precision):
     w, fields, _, _ = wide_case
