@@ -1031,6 +1031,15 @@ __device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __res
   }
   const ZSmem z = carve(zsm, Nz, N);
   const bool is00 = (mx == 0 && j == 0);
+  // shared lines: omega, w, phi, D w, D phi (the coefficient-space variant keeps only these
+  // five, lines 0..4, and stores its outputs straight from registers; the DCT variant keeps them
+  // in lines 10..14 and assembles the outputs in lines 0..NOUT-1 for its transforms)
+  constexpr int LOM = COEF ? 0 : 10;
+  double2* Lom = LN(z, LOM, Nz);
+  double2* Lw = LN(z, LOM + 1, Nz);
+  double2* Lph = LN(z, LOM + 2, Nz);
+  double2* Ldw = LN(z, LOM + 3, Nz);
+  double2* Ldp = LN(z, LOM + 4, Nz);
   for (int n = tid; n < Nz; n += blockDim.x) {
     double2 om = st_om[off + n], w = st_w[off + n], ph = st_phi[off + n];
     if (UPDATE) {
@@ -1041,23 +1050,23 @@ __device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __res
       st_w[off + n] = w;
       st_phi[off + n] = ph;
     }
-    LN(z, 10, Nz)[n] = om;
-    LN(z, 11, Nz)[n] = w;
-    LN(z, 12, Nz)[n] = ph;
+    Lom[n] = om;
+    Lw[n] = w;
+    Lph[n] = ph;
   }
   __syncthreads();
   {
-    double2* src[2] = {LN(z, 11, Nz), LN(z, 12, Nz)};
-    double2* dst[2] = {LN(z, 13, Nz), LN(z, 14, Nz)};
+    double2* src[2] = {Lw, Lph};
+    double2* dst[2] = {Ldw, Ldp};
     dz_tasks(src, dst, 2, N);
   }
   __syncthreads();
   const double k2 = ksq(kx, ky);
   const double rk2 = is00 ? 0.0 : 1.0 / k2;
   for (int n = tid; n < Nz; n += blockDim.x) {
-    const double2 om = LN(z, 10, Nz)[n];
-    const double2 dw = LN(z, 13, Nz)[n];
-    const double2 ph = LN(z, 12, Nz)[n];
+    const double2 om = Lom[n];
+    const double2 dw = Ldw[n];
+    const double2 ph = Lph[n];
     double2 u, v;
     if (is00) {
       u = make_double2(om.x, 0.0);
@@ -1067,26 +1076,29 @@ __device__ __forceinline__ void zbwd_body(const GridDev& g, const double2* __res
       u = rk2 * mul_i(kx * dw + ky * om);
       v = rk2 * mul_i(ky * dw - kx * om);
     }
+    if (COEF) {
+      // NOUT = 5: u v w phi D phi
+      bw[off + n] = from_d2<T2>(u);
+      bw[fs + off + n] = from_d2<T2>(v);
+      bw[2 * fs + off + n] = from_d2<T2>(Lw[n]);
+      bw[3 * fs + off + n] = from_d2<T2>(ph);
+      bw[4 * fs + off + n] = from_d2<T2>(Ldp[n]);
+      continue;
+    }
     LN(z, 0, Nz)[n] = u;
     LN(z, 1, Nz)[n] = v;
-    LN(z, 2, Nz)[n] = LN(z, 11, Nz)[n];
+    LN(z, 2, Nz)[n] = Lw[n];
     LN(z, 3, Nz)[n] = ph;
     if (NOUT == 7) {
       LN(z, 4, Nz)[n] = kx * mul_i(ph);
       LN(z, 5, Nz)[n] = ky * mul_i(ph);
-      LN(z, 6, Nz)[n] = LN(z, 14, Nz)[n];
+      LN(z, 6, Nz)[n] = Ldp[n];
     } else {
-      LN(z, 4, Nz)[n] = LN(z, 14, Nz)[n];
+      LN(z, 4, Nz)[n] = Ldp[n];
     }
   }
+  if (COEF) return;
   __syncthreads();
-  if (COEF) {
-    for (int idx = tid; idx < NOUT * Nz; idx += blockDim.x) {
-      const int f = idx / Nz, n = idx - f * Nz;
-      bw[(long long)f * fs + off + n] = from_d2<T2>(LN(z, f, Nz)[n]);
-    }
-    return;
-  }
   // as few rounds of at most NBF lines as possible, balanced (5 fields: 3 + 2, not 4 + 1, so no
   // round runs a lone line through the barrier-separated FFT passes)
   constexpr int NR = (NOUT + NBF - 1) / NBF;
@@ -1970,10 +1982,11 @@ __global__ void __launch_bounds__(ST) grouped_zsolve_kernel(const Member* __rest
 size_t zline_smem(const GridDev& g) {
   return (size_t)(NLINES * g.nz + 2 * NBF * g.N) * sizeof(double2);
 }
-// the coefficient-space kernels use the lines only (no DCT scratch)
+// the coefficient-space kernels use the lines only (no DCT scratch); zbwd five of them
 static size_t zline_coef_smem(const GridDev& g) {
   return (size_t)NLINES * g.nz * sizeof(double2);
 }
+static size_t zbwd_coef_smem(const GridDev& g) { return (size_t)5 * g.nz * sizeof(double2); }
 
 size_t fac_doubles(const GridDev& g) { return ((size_t)13 * g.nz + 20) * g.NK; }
 
@@ -2020,7 +2033,8 @@ static SmemLimit cur_zrhs_coef, cur_zbwd_coef;
 cudaError_t zline_coef_prepare(const GridDev& g) {
   const size_t smem = zline_coef_smem(g);
   cudaError_t e = ensure_smem(zrhs_kernel<double, 1>, smem, &cur_zrhs_coef);
-  if (e == cudaSuccess) e = ensure_smem(zbwd_kernel<double, 1, 5, 1>, smem, &cur_zbwd_coef);
+  if (e == cudaSuccess)
+    e = ensure_smem(zbwd_kernel<double, 1, 5, 1>, zbwd_coef_smem(g), &cur_zbwd_coef);
   return e;
 }
 
@@ -2039,7 +2053,7 @@ cudaError_t launch_zrhs_coef(const GridDev& g, const double2* cf, long long fs,
 cudaError_t launch_zbwd_coef(const GridDev& g, const double2* R, double2* st_om, double2* st_w,
                              double2* st_phi, double2* cf, long long fs, const FftPlan& pz,
                              cudaStream_t s) {
-  const size_t smem = zline_coef_smem(g);
+  const size_t smem = zbwd_coef_smem(g);
   cudaError_t e = ensure_smem(zbwd_kernel<double, 1, 5, 1>, smem, &cur_zbwd_coef);
   if (e != cudaSuccess) return e;
   zbwd_kernel<double, 1, 5, 1><<<g.Mx * g.ny, ZTC, smem, s>>>(g, R, st_om, st_w, st_phi, cf, fs,
