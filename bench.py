@@ -55,14 +55,9 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 9.67 / 1e12
 TRAFFIC_MB = {
     ("channel_128x128x129", 0, "xline"): 152.8 + 185.4,
     ("channel_128x128x129", 0, "ybwd"): 84.6 + 135.3,
-    ("channel_128x128x129", 1, "xline"): 76.6 + 75.7,
-    ("channel_128x128x129", 1, "ybwd"): 42.1 + 91.2,
     ("channel_128x128x129", 2, "xline"): 153.2 + 193.1,
     ("channel_128x128x129", 2, "ybwd"): 84.7 + 134.8,
     # coefficient-space z kernels of the tensor-core method (the same kernels at any precision)
-    ("channel_128x128x129", 0, "zbwd_coef"): 83.9 + 77.6,
-    ("channel_128x128x129", 1, "zbwd_coef"): 83.9 + 77.6,
-    ("channel_128x128x129", 2, "zbwd_coef"): 83.9 + 77.6,
     ("channel_128x128x129", 0, "zsolve"): 93.5 + 8.9,
     ("channel_128x128x129", 1, "zsolve"): 93.5 + 8.9,
     ("channel_128x128x129", 2, "zsolve"): 93.5 + 8.9,
@@ -70,10 +65,7 @@ TRAFFIC_MB = {
     # and FP64 step on the same grid)
     ("channel_512x256x257_mixed", 1, "cheb_bwd"): 5574.4 + 3520.3,
     ("channel_512x256x257_mixed", 1, "zsolve"): 4743.7 + 3612.8,
-    ("channel_512x256x257_mixed", 1, "zbwd_coef"): 1342.5 + 2092.8,
     ("channel_512x256x257_mixed", 1, "zbwd"): 1342.6 + 1427.2,
-    ("channel_512x256x257_mixed", 1, "xline"): 1221.0 + 1784.8,
-    ("channel_512x256x257_mixed", 1, "ybwd"): 805.5 + 1373.8,
     ("channel_512x256x257_mixed", 0, "zsolve"): 4753.3 + 3623.4,
     ("channel_512x256x257_mixed", 0, "zbwd"): 1343.7 + 2096.8,
     ("channel_512x256x257_mixed", 0, "xline"): 2434.1 + 3591.5,

@@ -52,8 +52,11 @@ namespace {
 
 constexpr int TCT = 512;          // threads per CTA
 constexpr int TCM = 128;          // rows per tile = tensor-memory lanes
-constexpr int TCKC = 144;         // K per chunk
+constexpr int TCKC = 96;          // K per chunk
 constexpr int TCG = TCKC / 8;     // 8-element core-matrix groups per chunk
+constexpr int kNA = 4;            // shared buffers of A digit planes (kNA - 1 copied ahead)
+constexpr int kNB = 1;            // shared buffers of B digit planes
+constexpr int kSmallK = 144;      // K up to which every accumulator stays below 2^22 in magnitude
 constexpr unsigned long long kBias = 0x0081020408102040ull;   // 64 * sum_{t<8} 128^t
 constexpr uint64_t kWaitNs = 1000000000ull;                   // bound of every device wait
 
@@ -330,11 +333,12 @@ template <> __device__ __forceinline__ df qnan<df>() {
   return df(__uint_as_float(0x7FC00000u), __uint_as_float(0x7FC00000u));
 }
 
+constexpr int kBars = 2 * kNB + 3 * kNA + 3;   // barriers (see the kernel)
 __host__ __device__ constexpr size_t tc_smem_bytes(int NT) {
-  // B planes, two A planes, row exponents, ten barriers and the tensor-memory address
-  // (88 bytes), output-column exponents (at most 512)
-  return (size_t)8 * NT * TCKC * 2 + (size_t)2 * TCM * TCKC * 2 + TCM * sizeof(int) + 88 +
-         512 * sizeof(int);
+  // B planes (kNB chunks), A planes (kNA buffers), row exponents, the barriers and the
+  // tensor-memory address, output-column exponents (at most 512)
+  return (size_t)kNB * 8 * NT * TCKC * 2 + (size_t)kNA * TCM * TCKC * 2 + TCM * sizeof(int) +
+         (size_t)(kBars + 1) * 8 + 512 * sizeof(int);
 }
 
 // ---- the transform kernel ---------------------------------------------------------------------
@@ -346,15 +350,16 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int NT) {
 //
 // Persistent CTAs (17 warps) walk the tiles of 128 rows; per tile they loop over the nNt output
 // slices.  Warps 0..15 turn the rows into fixed-point values and, for the first slice, write the
-// eight digit planes into a double-buffered shared tile (and the CTA's plane cache in global
-// memory, which stays in L2); they drain the accumulators of every slice.  Lane 0 of warp 16
-// allocates the tensor memory and issues the bulk copies and the MMAs; for the later slices it
-// copies the cached planes back itself, one plane ahead of the MMAs.  Plane t (counted over
-// tiles, slices and chunks) uses shared buffer t % 2: whoever fills it first waits for `empty`
-// of that buffer (the MMAs of plane t - 2 completed, signalled by tcgen05.commit); generated
-// planes are announced on `full` (one arrival per producer warp), copied ones on `loaded`
-// (transaction count).  The next slice's digits of B are copied while the accumulators drain;
-// its MMAs start once every producer warp has arrived on `drained`.
+// eight digit planes into kNA rotating shared buffers (and the CTA's plane cache in global
+// memory); they drain the accumulators of every slice.  Lane 0 of warp 16 allocates the tensor
+// memory and issues the bulk copies and the MMAs; for the later slices it copies the cached
+// planes back itself, up to kNA - 1 planes ahead of the MMAs.  Plane t (counted over tiles,
+// slices and chunks) uses shared buffer t % kNA: whoever fills it waits for `empty` of that
+// buffer (the MMAs of plane t - kNA completed, signalled by tcgen05.commit); generated planes
+// are announced on `full` (one arrival per producer warp), copied ones on `loaded` (transaction
+// count).  The digits of B of chunk u (counted over tiles, slices and chunks) go to buffer
+// u % kNB once `bfree` of that buffer says the MMAs of chunk u - kNB are done.  A slice's MMAs
+// start once every producer warp has arrived on `drained` for the previous slice.
 template <typename TI, typename TO, int NT>
 __global__ void __launch_bounds__(TCT + 32, 1)
     cheb_tc_kernel(const TI* __restrict__ in, long long fsi, TO* __restrict__ out, long long fso,
@@ -365,34 +370,40 @@ __global__ void __launch_bounds__(TCT + 32, 1)
   typedef typename F::U U;
   extern __shared__ __align__(1024) unsigned char tsm[];
   unsigned char* sB = tsm;
-  unsigned char* sA = sB + (size_t)8 * NT * TCKC * 2;
-  int* sE = reinterpret_cast<int*>(sA + (size_t)2 * TCM * TCKC * 2);
+  constexpr uint32_t kBBytes = 8 * NT * TCKC * 2;   // one chunk of B planes
+  unsigned char* sA = sB + (size_t)kNB * kBBytes;
+  int* sE = reinterpret_cast<int*>(sA + (size_t)kNA * TCM * TCKC * 2);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(sE + TCM);
-  uint32_t* sT = reinterpret_cast<uint32_t*>(bars + 10);
-  int* sF = reinterpret_cast<int*>(bars + 11);   // F_n of every output column (nNt NT <= 512)
+  uint32_t* sT = reinterpret_cast<uint32_t*>(bars + kBars);
+  int* sF = reinterpret_cast<int*>(bars + kBars + 1);   // F_n of every output column (<= 512)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nchunk = (Kp + TCKC - 1) / TCKC;
   constexpr uint32_t kPlaneBytes = TCM * TCKC * 2;
-  // barriers: B loaded; full[b] (16 producer warps); loaded[b] (a cached plane copied);
-  // empty[b] (MMAs of the plane done); drained (16 producer warps read the accumulators);
-  // sliced (every MMA of a slice done: one phase per slice, so the producers, which skip the
-  // planes of the later slices, never wait on a phase more than one ahead); fin (the issuer's
-  // MMAs in flight, after a wait ran out)
-  const uint32_t barB = su32(&bars[0]), barFull = su32(&bars[1]), barLoad = su32(&bars[3]);
-  const uint32_t barEmpty = su32(&bars[5]), barDrain = su32(&bars[7]);
-  const uint32_t barSlice = su32(&bars[8]), barFin = su32(&bars[9]);
+  // barriers (8 bytes each, buffer b of a kind at + 8 b): bload[kNB] (B chunk copied),
+  // bfree[kNB] (MMAs of the chunk done); full[kNA] (16 producer warps); loaded[kNA] (a cached
+  // plane copied); empty[kNA] (MMAs of the plane done); drained (16 producer warps read the
+  // accumulators); sliced (every MMA of a slice done: one phase per slice, so the producers,
+  // which skip the planes of the later slices, never wait on a phase more than one ahead); fin
+  // (the issuer's MMAs in flight, after a wait ran out)
+  const uint32_t barB = su32(&bars[0]), barBfree = su32(&bars[kNB]);
+  const uint32_t barFull = su32(&bars[2 * kNB]), barLoad = su32(&bars[2 * kNB + kNA]);
+  const uint32_t barEmpty = su32(&bars[2 * kNB + 2 * kNA]);
+  const uint32_t barDrain = su32(&bars[2 * kNB + 3 * kNA]);
+  const uint32_t barSlice = barDrain + 8, barFin = barDrain + 16;
   const size_t bslice = (size_t)8 * NT * Kp;
   uint32_t* ccta = cache + (size_t)blockIdx.x * nchunk * 8 * (kPlaneBytes / 4);
   const bool issuer_warp = (warp == TCT / 32);
   const bool issuer = issuer_warp && lane == 0;
   if (issuer) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barB));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(barFull));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(barFull + 8));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barLoad));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barLoad + 8));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barEmpty));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barEmpty + 8));
+    for (int b = 0; b < kNB; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barB + 8 * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barBfree + 8 * b));
+    }
+    for (int b = 0; b < kNA; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(barFull + 8 * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barLoad + 8 * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barEmpty + 8 * b));
+    }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(barDrain));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barSlice));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barFin));
@@ -418,33 +429,31 @@ __global__ void __launch_bounds__(TCT + 32, 1)
     if (lane == 0) {
       // bf16 x bf16 -> fp32, both K-major, M = 128 (N added per MMA)
       const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCM >> 4) << 24);
-      int t = 0, u = 0, S = 0;           // plane, B copy and slice counters (all tiles)
-      int nfull[2] = {0, 0}, nload[2] = {0, 0};
-      int iload[2] = {0, 0};             // cached-plane copies issued per buffer
-      bool pendB = false;                // a copy of B issued and not yet waited for
+      int t = 0, u = 0, S = 0;           // plane, B chunk and slice counters (all tiles)
+      int nfull[kNA] = {}, nload[kNA] = {};
+      int iload[kNA] = {};               // cached-plane copies issued per buffer
+      int nbl[kNB] = {}, ibl[kNB] = {};  // B chunks waited for / issued per buffer
       bool any_mma = false;
+      const int tplanes = nNt * 8 * nchunk;   // planes of one tile
+      int tcopy = 0;                     // next plane (all tiles) whose cached copy is due
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int t0 = t;                 // first plane of this tile
+        tcopy = t0 + 8 * nchunk;          // the copies start with slice 1
         for (int sl = 0; sl < nNt; ++sl, ++S) {
           for (int ch = 0; ch < nchunk; ++ch, ++u) {
             const int KCc = min(TCKC, Kp - ch * TCKC);
-            // the previous plane (t - 1) read B; it must be consumed before B is replaced
-            if (u > 0 && !W.wait(barEmpty + 8 * ((t - 1) & 1), ((t - 1) >> 1) & 1)) goto drain;
-            bulk_load(sB0, bdig + (size_t)sl * bslice + (size_t)ch * 8 * NT * TCKC,
-                      (uint32_t)(8 * NT * KCc * 2), barB, keep);
-            pendB = true;
-            if (sl > 0) {   // first cached plane of this chunk into buffer t % 2
-              if (t >= 2 && !W.wait(barEmpty + 8 * (t & 1), ((t - 2) >> 1) & 1)) goto drain;
-              // the producers' global stores (acquired through `full`) before the async copy
-              asm volatile("fence.proxy.async.global;" ::: "memory");
-              bulk_load(sA0 + (uint32_t)((t & 1) * kPlaneBytes), ccta + (size_t)ch * 8 * (kPlaneBytes / 4),
-                        kPlaneBytes, barLoad + 8 * (t & 1), keep);
-              ++iload[t & 1];
-            }
-            if (!W.wait(barB, u & 1)) goto drain;
-            pendB = false;
+            const int bb = u % kNB;
+            // B buffer bb: the MMAs of chunk u - kNB read it
+            if (u >= kNB && !W.wait(barBfree + 8 * bb, ((u - kNB) / kNB) & 1)) goto drain;
+            bulk_load(sB0 + (uint32_t)(bb * kBBytes),
+                      bdig + (size_t)sl * bslice + (size_t)ch * 8 * NT * TCKC,
+                      (uint32_t)(8 * NT * KCc * 2), barB + 8 * bb, keep);
+            ++ibl[bb];
+            if (!W.wait(barB + 8 * bb, nbl[bb] & 1)) goto drain;
+            ++nbl[bb];
             if (ch == 0 && S > 0 && !W.wait(barDrain, (S - 1) & 1)) goto drain;
             for (int i = 0; i < 8; ++i, ++t) {
-              const int bf = t & 1;
+              const int bf = t % kNA;
               if (sl == 0) {
                 if (!W.wait(barFull + 8 * bf, nfull[bf] & 1)) goto drain;
                 ++nfull[bf];
@@ -458,26 +467,33 @@ __global__ void __launch_bounds__(TCT + 32, 1)
               // N = (8 - i) NT is issued in pieces of at most 256.  A k-step adds 2 core-matrix
               // groups to both start addresses (4096 bytes of A, 2 NT 128 bytes of B).
               const uint64_t ad = sdesc(sA0 + (uint32_t)(bf * kPlaneBytes), 2048, 128);
+              const uint32_t sBb = sB0 + (uint32_t)(bb * kBBytes);
               const int ntot = (8 - i) * NT;
               for (int s = 0; s < KCc / 16; ++s)
                 for (int n0 = 0; n0 < ntot; n0 += 256) {
                   const int nlen = min(256, ntot - n0);
-                  const uint64_t bd = sdesc(sB0 + (uint32_t)(n0 / 8 * 128), NT * 128, 128);
+                  const uint64_t bd = sdesc(sBb + (uint32_t)(n0 / 8 * 128), NT * 128, 128);
                   mma_bf16(tmem + (uint32_t)(i * NT + n0), ad + (uint64_t)(s * 256),
                            bd + (uint64_t)(s * 16 * NT), idesc0 | ((uint32_t)(nlen >> 3) << 17),
                            (uint32_t)((ch | i | s) != 0));
                 }
               any_mma = true;
               mma_commit(barEmpty + 8 * bf);
+              if (i == 7) mma_commit(barBfree + 8 * bb);
               if (i == 7 && ch == nchunk - 1) mma_commit(barSlice);
-              if (sl > 0 && i < 7) {
-                // the next cached plane into the other buffer, once its MMAs (plane t - 1) ended
-                const int tn = t + 1;
-                if (tn >= 2 && !W.wait(barEmpty + 8 * (tn & 1), ((tn - 2) >> 1) & 1)) goto drain;
-                bulk_load(sA0 + (uint32_t)((tn & 1) * kPlaneBytes),
-                          ccta + (size_t)(ch * 8 + i + 1) * (kPlaneBytes / 4), kPlaneBytes,
-                          barLoad + 8 * (tn & 1), keep);
-                ++iload[tn & 1];
+              // cached planes of the later slices, up to kNA - 1 ahead: buffer tc % kNA is free
+              // once the MMAs of plane tc - kNA (at most plane t - 1) are done
+              while (tcopy <= t + kNA - 1 && tcopy < t0 + tplanes) {
+                const int tc = tcopy;
+                const int bc = tc % kNA;
+                if (tc >= kNA && !W.wait(barEmpty + 8 * bc, ((tc - kNA) / kNA) & 1)) goto drain;
+                // the producers' global stores (acquired through `full`) before the async copy
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                const int c = (tc - t0) % (8 * nchunk);   // cache entry: chunk c / 8, plane c % 8
+                bulk_load(sA0 + (uint32_t)(bc * kPlaneBytes), ccta + (size_t)c * (kPlaneBytes / 4),
+                          kPlaneBytes, barLoad + 8 * bc, keep);
+                ++iload[bc];
+                ++tcopy;
               }
             }
           }
@@ -493,9 +509,10 @@ __global__ void __launch_bounds__(TCT + 32, 1)
           mma_commit(barFin);
           mbar_wait_until(barFin, 0, dl);
         }
-        if (pendB) mbar_wait_until(barB, u & 1, dl);
-        for (int b = 0; b < 2; ++b)
-          if (iload[b] > nload[b]) mbar_wait_until(barLoad + 8 * b, nload[b] & 1, dl);
+        for (int b = 0; b < kNB; ++b)
+          if (ibl[b] > nbl[b]) mbar_wait_until(barB + 8 * b, nbl[b] & 1, dl);
+        for (int b = 0; b < kNA; ++b)
+          for (int k = nload[b]; k < iload[b]; ++k) mbar_wait_until(barLoad + 8 * b, k & 1, dl);
       }
     }
     __syncwarp();
@@ -568,8 +585,8 @@ __global__ void __launch_bounds__(TCT + 32, 1)
             }
           }
         for (int i = 0; i < 8; ++i, ++t) {
-          const int bf = t & 1;
-          if (t >= 2) W.wait(barEmpty + 8 * bf, ((t - 2) >> 1) & 1);
+          const int bf = t % kNA;
+          if (t >= kNA) W.wait(barEmpty + 8 * bf, ((t - kNA) / kNA) & 1);
           uint32_t* dst = reinterpret_cast<uint32_t*>(sA + (size_t)bf * kPlaneBytes);
           uint32_t* gdst = ccta + (size_t)(ch * 8 + i) * (kPlaneBytes / 4);
           const int sh = 7 * (3 - (i & 3));
@@ -624,7 +641,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
             const int n = sl * NT + cg * CW + c0 + e;
             if (orow && n < Nz - 1) {
               int g[8];
-              if (Kp <= TCKC) {
+              if (Kp <= kSmallK) {
 #pragma unroll
                 for (int d = 0; d < 8; ++d) g[d] = acc_int_small(v[d][e]);
               } else {
