@@ -53,11 +53,11 @@ int stage_items(int stage, const Member& m, int prec) {
   }
 }
 
-size_t stage_smem(int stage, const Member& m, int prec) {
+size_t stage_smem(int stage, const Member& m, int prec, int coef) {
   const size_t elem = prec == 1 ? sizeof(float2) : sizeof(double2);   // df2 is 16 bytes too
   switch (stage) {
     case 0:
-    case 2: return zline_smem(m.g);
+    case 2: return coef ? zline_coef_stage_smem(m.g, stage) : zline_smem(m.g);
     case 1: return m.zsolve_tile ? zsolve_tile_smem(m.g) : 0;
     case 3: return ysmem_bytes(m.g.Py, m.tzb, elem);
     case 4: return xline_smem(m.g.Px, elem);
@@ -225,7 +225,7 @@ int build_descriptors(ch_ensemble* E) {
     int* b = &E->hbegin[(size_t)s * (n + 1)];
     for (int i = 0; i < n; ++i) {
       b[i + 1] = b[i] + chf::stage_items(s, E->hmem[i], E->prec);
-      const size_t sm = chf::stage_smem(s, E->hmem[i], E->prec);
+      const size_t sm = chf::stage_smem(s, E->hmem[i], E->prec, E->cheb == CH_CHEB_TC);
       if (sm > mx) mx = sm;
     }
     E->smem[s] = mx;

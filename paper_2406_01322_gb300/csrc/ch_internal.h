@@ -212,7 +212,9 @@ cudaError_t launch_grouped(int stage, int prec, const Member* mem, const int* be
 int ensemble_ywq(const std::vector<int>& py, int prec);
 // work items of one member for a stage, and the dynamic shared memory one item needs
 int stage_items(int stage, const Member& m, int prec);
-size_t stage_smem(int stage, const Member& m, int prec);
+size_t stage_smem(int stage, const Member& m, int prec, int coef);
+// shared memory of the coefficient-space zrhs (stage 0) or zbwd (stage 2) of a grid
+size_t zline_coef_stage_smem(const GridDev& g, int stage);
 // CTAs per SM that the stage kernel can hold with `smem` bytes (occupancy API)
 int stage_occupancy(int stage, int prec, size_t smem, int zsolve_tile, int coef, int ywq);
 // y-pass z tile for a padded length P (shared by single-grid and grouped launches)

@@ -264,14 +264,9 @@ __device__ __forceinline__ uint32_t digit_pair(uint32_t w0, uint32_t w1, int sh)
 __device__ __forceinline__ int acc_int_small(uint32_t b) {
   return __float_as_int(__uint_as_float(b) + 12582912.0f) - 0x4B400000;
 }
-// ... and by the bit pattern for any integer value below 2^24 (larger K)
-__device__ __forceinline__ int acc_int(uint32_t b) {
-  int e = (int)((b >> 23) & 0xFF);
-  if (e < 127) return 0;
-  if (e > 150) e = 150;
-  const int v = (int)((b & 0x7FFFFFu) | 0x800000u) >> (150 - e);
-  return (b >> 31) ? -v : v;
-}
+// ... and by one float-to-integer conversion for any integer value below 2^24 (larger K; the
+// accumulator holds an exact integer, so the conversion does not round)
+__device__ __forceinline__ int acc_int(uint32_t b) { return __float2int_rz(__uint_as_float(b)); }
 
 // T 2^e rounded to nearest even, by integer operations (ldexp fallback outside the normal range)
 template <typename TO> __device__ TO scaled(long long T, int e);

@@ -1930,7 +1930,7 @@ __global__ void __launch_bounds__(ZT) grouped_zbwd_kernel(const Member* __restri
 
 // tensor-core Chebyshev method: the products' coefficients are in M.cf (float64 whatever the
 // working precision), and zbwd leaves the 5 backward fields' coefficients there
-__global__ void __launch_bounds__(ZT) grouped_zrhs_coef_kernel(const Member* __restrict__ mem,
+__global__ void __launch_bounds__(ZTC) grouped_zrhs_coef_kernel(const Member* __restrict__ mem,
                                                                const int* __restrict__ begin,
                                                                int nmem) {
   const int total = begin[nmem];
@@ -1943,7 +1943,7 @@ __global__ void __launch_bounds__(ZT) grouped_zrhs_coef_kernel(const Member* __r
   }
 }
 
-__global__ void __launch_bounds__(ZT) grouped_zbwd_coef_kernel(const Member* __restrict__ mem,
+__global__ void __launch_bounds__(ZTC) grouped_zbwd_coef_kernel(const Member* __restrict__ mem,
                                                                const int* __restrict__ begin,
                                                                int nmem) {
   const int total = begin[nmem];
@@ -1987,6 +1987,9 @@ static size_t zline_coef_smem(const GridDev& g) {
   return (size_t)NLINES * g.nz * sizeof(double2);
 }
 static size_t zbwd_coef_smem(const GridDev& g) { return (size_t)5 * g.nz * sizeof(double2); }
+size_t zline_coef_stage_smem(const GridDev& g, int stage) {
+  return stage == 0 ? zline_coef_smem(g) : zbwd_coef_smem(g);
+}
 
 size_t fac_doubles(const GridDev& g) { return ((size_t)13 * g.nz + 20) * g.NK; }
 
@@ -2074,11 +2077,11 @@ cudaError_t launch_grouped_z(int stage, int prec, const Member* mem, const int* 
     if (stage == 0) {
       static SmemLimit cur;
       if ((e = ensure_smem(grouped_zrhs_coef_kernel, smem, &cur)) != cudaSuccess) return e;
-      grouped_zrhs_coef_kernel<<<grid, ZT, smem, s>>>(mem, begin, nmem);
+      grouped_zrhs_coef_kernel<<<grid, ZTC, smem, s>>>(mem, begin, nmem);
     } else {
       static SmemLimit cur;
       if ((e = ensure_smem(grouped_zbwd_coef_kernel, smem, &cur)) != cudaSuccess) return e;
-      grouped_zbwd_coef_kernel<<<grid, ZT, smem, s>>>(mem, begin, nmem);
+      grouped_zbwd_coef_kernel<<<grid, ZTC, smem, s>>>(mem, begin, nmem);
     }
   } else if (stage == 0) {
     if (prec == 0) {
@@ -2145,7 +2148,7 @@ int occupancy_z(int stage, int prec, size_t smem, int zsolve_tile, int coef) {
   if (coef && stage != 1)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &n, stage == 0 ? (const void*)grouped_zrhs_coef_kernel : (const void*)grouped_zbwd_coef_kernel,
-        ZT, smem);
+        ZTC, smem);
   else if (stage == 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zkernel(0, prec), ZT, smem);
   else if (stage == 1)
