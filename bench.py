@@ -70,6 +70,27 @@ TRAFFIC_MB = {
     ("channel_512x256x257_mixed", 0, "zbwd"): 1343.7 + 2096.8,
     ("channel_512x256x257_mixed", 0, "xline"): 2434.1 + 3591.5,
     ("channel_512x256x257_mixed", 0, "ybwd"): 1610.9 + 2393.1,
+    # current step kernels (full-size captures of the default bench command's kernels with
+    # --cheb tc, and of the 128^3 mixed tensor-core and float64 FFT-method steps)
+    ("channel_512x256x257_mixed", 1, "cheb_fwd"): 3960.3 + 5458.9,
+    ("channel_512x256x257_mixed", 1, "cheb_bwd"): 4578.5 + 3412.2,
+    ("channel_512x256x257_mixed", 1, "zrhs_coef"): 3489.9 + 1673.7,
+    ("channel_512x256x257_mixed", 1, "zbwd_coef"): 1342.2 + 2296.5,
+    ("channel_512x256x257_mixed", 1, "xline"): 1239.7 + 1789.9,
+    ("channel_512x256x257_mixed", 1, "yfwd"): 1819.2 + 907.1,
+    ("channel_512x256x257_mixed", 1, "ybwd"): 805.6 + 1164.7,
+    ("channel_128x128x129", 1, "cheb_fwd"): 92.2 + 122.9,
+    ("channel_128x128x129", 1, "cheb_bwd"): 111.7 + 52.2,
+    ("channel_128x128x129", 1, "zrhs_coef"): 218.2 + 79.0,
+    ("channel_128x128x129", 0, "zbwd_coef"): 83.9 + 87.1,
+    ("channel_128x128x129", 1, "zbwd_coef"): 83.9 + 87.1,
+    ("channel_128x128x129", 2, "zbwd_coef"): 83.9 + 87.1,
+    ("channel_128x128x129", 1, "xline"): 77.7 + 63.1,
+    ("channel_128x128x129", 1, "yfwd"): 114.2 + 32.1,
+    ("channel_128x128x129", 1, "ybwd"): 42.0 + 28.0,
+    ("channel_128x128x129", 0, "zrhs"): 218.3 + 73.3,
+    ("channel_128x128x129", 0, "yfwd"): 228.3 + 85.9,
+    ("channel_128x128x129", 0, "zbwd"): 84.0 + 82.6,
     ("channel_128x128x129_adjoint", 0, "adj_xline"): 380.7 + 130.9,
     ("channel_128x128x129_adjoint", 0, "adj_zsolve"): 102.4 + 28.2,
     ("channel_128x128x129_adjoint", 0, "adj_zrhs"): 135.1 + 223.7,
@@ -949,8 +970,8 @@ def main():
             "ours_zrhs_ms": zrhs_ms,
             "note": "the 7 forward DCTs of one step as one cuBLAS float64 GEMM, against our whole "
                     "forward z stage: zrhs (7 DCTs + derivatives + assembly), or with the "
-                    "tensor-core method its forward transform of the 9 products plus the "
-                    "coefficient-space zrhs"}
+                    "tensor-core method its forward transform of the seven combined lines "
+                    "plus the coefficient-space zrhs"}
         out["cufft_comparison"] = {
             "cufft_z_dct_ms_per_step": zc, "cufft_xy_ms_per_step": xyc,
             "cufft_transforms_ms_per_step": zc + xyc,
