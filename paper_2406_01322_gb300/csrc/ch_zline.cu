@@ -384,11 +384,9 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   const ZSmem z = carve(zsm, Nz, N);
   const bool is00 = (mx == 0 && j == 0);
   const double k2 = ksq(kx, ky);
-  for (int n = tid; n < Nz; n += blockDim.x) {
-    LN(z, 10, Nz)[n] = st_om[off + n];
-    LN(z, 11, Nz)[n] = st_w[off + n];
-    LN(z, 12, Nz)[n] = st_phi[off + n];
-  }
+  // shared lines: 0..6 the combined non-linear lines, 11 w (omega and phi are read from global
+  // memory where they are used); 7..10 and 12 derivatives, reused as the sweep goes on
+  for (int n = tid; n < Nz; n += blockDim.x) LN(z, 11, Nz)[n] = st_w[off + n];
   // The seven combined non-linear lines, formed by the forward y pass (the Chebyshev transform
   // commutes with the z-independent factors i kx, i ky):
   //   0: P = i kx B - i ky A   1: Q = i kx Syz - i ky Sxz   (h_omega = P + D Q)
@@ -406,14 +404,14 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
       dct_forward_lines(z, f0, (7 - f0 < NBF) ? 7 - f0 : NBF, Nz, N, pz, g.zcs, is00);
   // G = phi^3 - (1 + shat) phi
   for (int n = tid; n < Nz; n += blockDim.x)
-    LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * LN(z, 12, Nz)[n];
+    LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * st_phi[off + n];
   __syncthreads();
   // Seven derivatives (D is linear, so the second derivatives of the assembly are taken of
   // sums): h_w = -k^2 C - D(R + D C), S_phi = F - (k^2 / Pe) G + D(D G / Pe - w phi),
   // theta^n = D^2 w - k^2 w, h_omega = P + D Q.
   {
     double2* src[5] = {LN(z, 1, Nz), LN(z, 2, Nz), LN(z, 6, Nz), LN(z, 11, Nz), LN(z, 0, Nz)};
-    double2* dst[5] = {LN(z, 7, Nz), LN(z, 9, Nz), LN(z, 14, Nz), LN(z, 15, Nz), LN(z, 13, Nz)};
+    double2* dst[5] = {LN(z, 7, Nz), LN(z, 9, Nz), LN(z, 8, Nz), LN(z, 12, Nz), LN(z, 10, Nz)};
     dz_tasks(src, dst, is00 ? 5 : 4, N);   // DQ, DC, DG, Dw (, D Sxz on (0,0))
   }
   __syncthreads();
@@ -421,7 +419,7 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   const double k2rpe = k2 * rpe;
   for (int n = tid; n < Nz; n += blockDim.x) {
     const double2 c = LN(z, 3, Nz)[n], dc = LN(z, 9, Nz)[n];
-    const double2 wp = LN(z, 5, Nz)[n], dg = LN(z, 14, Nz)[n];
+    const double2 wp = LN(z, 5, Nz)[n], dg = LN(z, 8, Nz)[n];
     const double2 f = LN(z, 4, Nz)[n], gg = LN(z, 6, Nz)[n];
     LN(z, 3, Nz)[n] = c + dc;                                                  // R + D C
     LN(z, 5, Nz)[n] = make_double2(fma(rpe, dg.x, -wp.x), fma(rpe, dg.y, -wp.y));  // D G / Pe - w phi
@@ -429,8 +427,8 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   }
   __syncthreads();
   {
-    double2* src[3] = {LN(z, 3, Nz), LN(z, 5, Nz), LN(z, 15, Nz)};
-    double2* dst[3] = {LN(z, 8, Nz), LN(z, 9, Nz), LN(z, 14, Nz)};
+    double2* src[3] = {LN(z, 3, Nz), LN(z, 5, Nz), LN(z, 12, Nz)};
+    double2* dst[3] = {LN(z, 8, Nz), LN(z, 9, Nz), LN(z, 1, Nz)};
     dz_tasks(src, dst, 3, N);   // D(R + D C), D(D G / Pe - w phi), D^2 w
   }
   __syncthreads();
@@ -445,7 +443,7 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   for (int n = tid; n < Nz; n += blockDim.x) {
     double2 hom, hw;
     if (is00) {  // mean flow: Sbar_x + i Sbar_y + (gx + i gy) delta_{n0}
-      hom = make_double2(LN(z, 13, Nz)[n].x + (n == 0 ? g.gx : 0.0),
+      hom = make_double2(LN(z, 10, Nz)[n].x + (n == 0 ? g.gx : 0.0),
                          LN(z, 7, Nz)[n].x + (n == 0 ? g.gy : 0.0));
       hw = make_double2(0.0, 0.0);
     } else {
@@ -454,9 +452,9 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
       hw = make_double2(fma(-k2, c.x, -d.x), fma(-k2, c.y, -d.y));             // -k^2 C - D(R + D C)
     }
     const double2 sphi = LN(z, 4, Nz)[n] + LN(z, 9, Nz)[n];
-    const double2 w = LN(z, 11, Nz)[n], d2w = LN(z, 14, Nz)[n];
+    const double2 w = LN(z, 11, Nz)[n], d2w = LN(z, 1, Nz)[n];
     const double2 th = make_double2(fma(-k2, w.x, d2w.x), fma(-k2, w.y, d2w.y));
-    const double2 om = LN(z, 10, Nz)[n], ph = LN(z, 12, Nz)[n];
+    const double2 om = st_om[off + n], ph = st_phi[off + n];
     double2 r0 = make_double2(cb * om.x, cb * om.y);
     double2 r1 = make_double2(cb * th.x, cb * th.y);
     double2 r2 = make_double2(prd * ph.x, prd * ph.y);
@@ -1982,10 +1980,9 @@ __global__ void __launch_bounds__(ST) grouped_zsolve_kernel(const Member* __rest
 size_t zline_smem(const GridDev& g) {
   return (size_t)(NLINES * g.nz + 2 * NBF * g.N) * sizeof(double2);
 }
-// the coefficient-space kernels use the lines only (no DCT scratch); zbwd five of them
-static size_t zline_coef_smem(const GridDev& g) {
-  return (size_t)NLINES * g.nz * sizeof(double2);
-}
+// the coefficient-space kernels use the lines only (no DCT scratch): zrhs lines 0..12 (four
+// CTAs per SM at nz = 257), zbwd five
+static size_t zline_coef_smem(const GridDev& g) { return (size_t)13 * g.nz * sizeof(double2); }
 static size_t zbwd_coef_smem(const GridDev& g) { return (size_t)5 * g.nz * sizeof(double2); }
 size_t zline_coef_stage_smem(const GridDev& g, int stage) {
   return stage == 0 ? zline_coef_smem(g) : zbwd_coef_smem(g);

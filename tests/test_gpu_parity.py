@@ -164,6 +164,25 @@ def test_long_lines_ten_steps_within_1e_10(binding, name, over):
         assert rel(a.cpu().numpy(), b) <= max(1e-10, 4.0 * fl), (f, fl)
 
 
+@pytest.mark.parametrize("name,over", LONG_LINES)
+@pytest.mark.parametrize("method", ["fft", "tc"])
+def test_long_lines_spectral_state_within_1e_10(binding, name, over, method):
+    """The same long lines compared where the readout adds no rounding of its own: the spectral
+    state (omega_z with the mean flow, w, phi coefficients) after 10 steps within 1e-10 of the
+    oracle's, flat, with either Chebyshev method (the float64 DCT or the exact-split tensor-core
+    product)."""
+    w = workload(name, **over)
+    g, o = make_pair(binding, w)
+    if method == "tc":
+        g.set_chebyshev(binding.CHEB_TC)
+    g.step(10)
+    for _ in range(10):
+        o.step()
+    for a, b, f in zip(g.get_spectral(), (o.omega, o.w, o.phi), ("omega", "w", "phi")):
+        assert rel(spec_to_oracle(a), b) <= 1e-10, f
+    g.close()
+
+
 @pytest.mark.parametrize("name,over", SIZES)
 def test_ten_steps_fp64_within_1e_10(binding, name, over):
     w = workload(name, **over)
