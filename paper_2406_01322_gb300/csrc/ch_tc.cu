@@ -540,6 +540,21 @@ __global__ void __launch_bounds__(TCT + 32, 1)
       mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
       return max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
     };
+    // L2 prefetch (evict-last) of the row elements of chunk ch of tile tl that this thread
+    // converts: issued one chunk ahead, so the conversion's loads, which the registers allow only
+    // a few at a time, find the rows in L2 instead of DRAM
+    auto prefetch_rows = [&](int tl, int ch) {
+      const int fld = tl / tpf;
+      const int line = (tl - fld * tpf) * (TCM / 2) + (m >> 1);
+      if (line >= nlines) return;
+      const TI* src = in + ((size_t)fld * fsi + (size_t)line * Nz) * 2 + (m & 1);
+      const int ngp = min(TCKC, Kp - ch * TCKC) / 8;
+      for (int gl = 0; gl < ngp; ++gl) {
+        const int k = ch * TCKC + 8 * gl + 2 * q;
+        if (k < Nz)
+          asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(src + 2 * (size_t)k));
+      }
+    };
     int t = 0, S = 0;
     int ahead = -1;   // the next tile's row exponent, read during this tile's last slice
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -579,6 +594,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
               s_lo += w * (xs & 0x7FFFFFFll);
             }
           }
+        if (ch + 1 < nchunk) prefetch_rows(tile, ch + 1);
         for (int i = 0; i < 8; ++i, ++t) {
           const int bf = t % kNA;
           if (t >= kNA) W.wait(barEmpty + 8 * bf, ((t - kNA) / kNA) & 1);
@@ -620,6 +636,7 @@ __global__ void __launch_bounds__(TCT + 32, 1)
           out + ((size_t)fld * fso + (size_t)(oline < nlines ? oline : 0) * Nz) * 2 + (mm & 1);
       for (int sl = 0; sl < nNt; ++sl, ++S) {
         if (sl > 0) t += 8 * nchunk;   // planes the issuer copies
+        if (sl == nNt - 1 && tile + (int)gridDim.x < ntiles) prefetch_rows(tile + gridDim.x, 0);
         // every MMA of the slice done
         W.wait(barSlice, S & 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
