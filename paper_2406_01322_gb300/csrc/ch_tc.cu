@@ -34,9 +34,10 @@
 // kernel; merging the pairs this way cuts 36 small MMAs per k-step to 8..12 large ones.)
 // Persistent CTAs (one per SM) walk the tiles with 16 producer warps and one issuer warp: the
 // producers convert their rows to fixed point once per tile, write the digit planes of the first
-// slice into a double-buffered shared tile and into a per-CTA plane cache in global memory (L2);
-// the issuer copies the cached planes back for the later slices, one plane ahead of the MMAs.
-// Row lengths above 144 (nz = 257) are split into K chunks with the same accumulators.
+// slice into rotating shared buffers and their 7-bit groups (one byte each) into a per-CTA plane
+// cache in global memory, and rebuild the later slices' planes from that cache; the issuer copies
+// the digits of B and issues the MMAs.  Rows are split into K chunks of 96 that accumulate into
+// the same tensor memory.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -57,6 +58,8 @@ constexpr int TCG = TCKC / 8;     // 8-element core-matrix groups per chunk
 constexpr int kNA = 4;            // shared buffers of A digit planes (kNA - 1 copied ahead)
 constexpr int kNB = 1;            // shared buffers of B digit planes
 constexpr int kSmallK = 144;      // K up to which every accumulator stays below 2^22 in magnitude
+// 32-bit words of one cached plane (four 7-bit groups per word, TCM x TCKC groups)
+constexpr int kCacheWords = TCM * TCKC / 4;
 constexpr unsigned long long kBias = 0x0081020408102040ull;   // 64 * sum_{t<8} 128^t
 constexpr uint64_t kWaitNs = 1000000000ull;                   // bound of every device wait
 
@@ -259,6 +262,26 @@ __device__ __forceinline__ uint32_t digit_pair(uint32_t w0, uint32_t w1, int sh)
   return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
 }
 
+// the 7-bit groups at bit offset sh of four elements' 28-bit halves as four bytes (first in the
+// lowest byte): the plane cache's format, half the size of the bf16 digits
+__device__ __forceinline__ uint32_t pack_groups(uint32_t w0, uint32_t w1, uint32_t w2,
+                                                uint32_t w3, int sh) {
+  return ((w0 >> sh) & 127u) | (((w1 >> sh) & 127u) << 8) | (((w2 >> sh) & 127u) << 16) |
+         (((w3 >> sh) & 127u) << 24);
+}
+// two bytes of the plane cache (7-bit groups u, digit u - 64) as two bf16 digits in one word
+__device__ __forceinline__ uint32_t group_pair(uint32_t b2) {
+  const float f0 = __uint_as_float(0x4B000000u | (b2 & 127u)) - 8388672.0f;
+  const float f1 = __uint_as_float(0x4B000000u | ((b2 >> 8) & 127u)) - 8388672.0f;
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+// a 32-bit load under the L2 policy `pol`
+__device__ __forceinline__ uint32_t ld_keep(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
 // integer value of an fp32 accumulator: exact for integer values of magnitude <= 2^22 through
 // the float 1.5 2^23 + v (small K) ...
 __device__ __forceinline__ int acc_int_small(uint32_t b) {
@@ -328,7 +351,7 @@ template <> __device__ __forceinline__ df qnan<df>() {
   return df(__uint_as_float(0x7FC00000u), __uint_as_float(0x7FC00000u));
 }
 
-constexpr int kBars = 2 * kNB + 3 * kNA + 3;   // barriers (see the kernel)
+constexpr int kBars = 2 * kNB + 2 * kNA + 3;   // barriers (see the kernel)
 __host__ __device__ constexpr size_t tc_smem_bytes(int NT) {
   // B planes (kNB chunks), A planes (kNA buffers), row exponents, the barriers and the
   // tensor-memory address, output-column exponents (at most 512)
@@ -341,20 +364,21 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int NT) {
 // elements, line stride Nz; bdig: nNt output slices of 8 NT Kp bf16 digits (per slice and chunk
 // of K: the eight digit planes stacked as one 8 NT x KC matrix in the canonical no-swizzle
 // K-major core-matrix layout, plane j in rows j NT ..); fexp: F_n; cache: per CTA, nchunk x 8
-// A digit planes of one tile (TCM x TCKC bf16 each, the shared-memory layout).
+// A digit planes of one tile as 7-bit groups, four per 32-bit word (kCacheWords words each).
 //
 // Persistent CTAs (17 warps) walk the tiles of 128 rows; per tile they loop over the nNt output
 // slices.  Warps 0..15 turn the rows into fixed-point values and, for the first slice, write the
-// eight digit planes into kNA rotating shared buffers (and the CTA's plane cache in global
-// memory); they drain the accumulators of every slice.  Lane 0 of warp 16 allocates the tensor
-// memory and issues the bulk copies and the MMAs; for the later slices it copies the cached
-// planes back itself, up to kNA - 1 planes ahead of the MMAs.  Plane t (counted over tiles,
-// slices and chunks) uses shared buffer t % kNA: whoever fills it waits for `empty` of that
-// buffer (the MMAs of plane t - kNA completed, signalled by tcgen05.commit); generated planes
-// are announced on `full` (one arrival per producer warp), copied ones on `loaded` (transaction
-// count).  The digits of B of chunk u (counted over tiles, slices and chunks) go to buffer
-// u % kNB once `bfree` of that buffer says the MMAs of chunk u - kNB are done.  A slice's MMAs
-// start once every producer warp has arrived on `drained` for the previous slice.
+// eight digit planes into kNA rotating shared buffers and their groups into the CTA's plane cache
+// (each thread reads back only what it wrote, so program order orders the two); for each later
+// slice they rebuild its first kNA planes as soon as the previous slice's MMAs are done, drain
+// the previous slice's accumulators, then rebuild the rest as the MMAs free the buffers.  Lane 0
+// of warp 16 allocates the tensor memory and issues the bulk copies of B and the MMAs.  Plane t
+// (counted over tiles, slices and chunks) uses shared buffer t % kNA: its producers wait for
+// `empty` of that buffer (the MMAs of plane t - kNA completed, signalled by tcgen05.commit) and
+// announce it on `full` (one arrival per producer warp).  The digits of B of chunk u (counted
+// over tiles, slices and chunks) go to buffer u % kNB once `bfree` of that buffer says the MMAs
+// of chunk u - kNB are done.  A slice's MMAs start once every producer warp has arrived on
+// `drained` for the previous slice.
 template <typename TI, typename TO, int NT>
 __global__ void __launch_bounds__(TCT + 32, 1)
     cheb_tc_kernel(const TI* __restrict__ in, long long fsi, TO* __restrict__ out, long long fso,
@@ -375,18 +399,17 @@ __global__ void __launch_bounds__(TCT + 32, 1)
   const int nchunk = (Kp + TCKC - 1) / TCKC;
   constexpr uint32_t kPlaneBytes = TCM * TCKC * 2;
   // barriers (8 bytes each, buffer b of a kind at + 8 b): bload[kNB] (B chunk copied),
-  // bfree[kNB] (MMAs of the chunk done); full[kNA] (16 producer warps); loaded[kNA] (a cached
-  // plane copied); empty[kNA] (MMAs of the plane done); drained (16 producer warps read the
-  // accumulators); sliced (every MMA of a slice done: one phase per slice, so the producers,
-  // which skip the planes of the later slices, never wait on a phase more than one ahead); fin
-  // (the issuer's MMAs in flight, after a wait ran out)
+  // bfree[kNB] (MMAs of the chunk done); full[kNA] (16 producer warps); empty[kNA] (MMAs of the
+  // plane done); drained (16 producer warps read the accumulators); sliced (every MMA of a slice
+  // done: one phase per slice, so the producers' epilogue waits never alias a buffer's phases);
+  // fin (the issuer's MMAs in flight, after a wait ran out)
   const uint32_t barB = su32(&bars[0]), barBfree = su32(&bars[kNB]);
-  const uint32_t barFull = su32(&bars[2 * kNB]), barLoad = su32(&bars[2 * kNB + kNA]);
-  const uint32_t barEmpty = su32(&bars[2 * kNB + 2 * kNA]);
-  const uint32_t barDrain = su32(&bars[2 * kNB + 3 * kNA]);
+  const uint32_t barFull = su32(&bars[2 * kNB]);
+  const uint32_t barEmpty = su32(&bars[2 * kNB + kNA]);
+  const uint32_t barDrain = su32(&bars[2 * kNB + 2 * kNA]);
   const uint32_t barSlice = barDrain + 8, barFin = barDrain + 16;
   const size_t bslice = (size_t)8 * NT * Kp;
-  uint32_t* ccta = cache + (size_t)blockIdx.x * nchunk * 8 * (kPlaneBytes / 4);
+  uint32_t* ccta = cache + (size_t)blockIdx.x * nchunk * 8 * kCacheWords;
   const bool issuer_warp = (warp == TCT / 32);
   const bool issuer = issuer_warp && lane == 0;
   if (issuer) {
@@ -396,7 +419,6 @@ __global__ void __launch_bounds__(TCT + 32, 1)
     }
     for (int b = 0; b < kNA; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(barFull + 8 * b));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barLoad + 8 * b));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barEmpty + 8 * b));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(barDrain));
@@ -425,15 +447,10 @@ __global__ void __launch_bounds__(TCT + 32, 1)
       // bf16 x bf16 -> fp32, both K-major, M = 128 (N added per MMA)
       const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCM >> 4) << 24);
       int t = 0, u = 0, S = 0;           // plane, B chunk and slice counters (all tiles)
-      int nfull[kNA] = {}, nload[kNA] = {};
-      int iload[kNA] = {};               // cached-plane copies issued per buffer
+      int nfull[kNA] = {};
       int nbl[kNB] = {}, ibl[kNB] = {};  // B chunks waited for / issued per buffer
       bool any_mma = false;
-      const int tplanes = nNt * 8 * nchunk;   // planes of one tile
-      int tcopy = 0;                     // next plane (all tiles) whose cached copy is due
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int t0 = t;                 // first plane of this tile
-        tcopy = t0 + 8 * nchunk;          // the copies start with slice 1
         for (int sl = 0; sl < nNt; ++sl, ++S) {
           for (int ch = 0; ch < nchunk; ++ch, ++u) {
             const int KCc = min(TCKC, Kp - ch * TCKC);
@@ -449,13 +466,8 @@ __global__ void __launch_bounds__(TCT + 32, 1)
             if (ch == 0 && S > 0 && !W.wait(barDrain, (S - 1) & 1)) goto drain;
             for (int i = 0; i < 8; ++i, ++t) {
               const int bf = t % kNA;
-              if (sl == 0) {
-                if (!W.wait(barFull + 8 * bf, nfull[bf] & 1)) goto drain;
-                ++nfull[bf];
-              } else {
-                if (!W.wait(barLoad + 8 * bf, nload[bf] & 1)) goto drain;
-                ++nload[bf];
-              }
+              if (!W.wait(barFull + 8 * bf, nfull[bf] & 1)) goto drain;
+              ++nfull[bf];
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
               // A plane i times B planes 0 .. 7-i at once: the stacked B rows j NT + n land in
               // accumulator columns i NT + j NT + n = (i + j) NT + n, the diagonal of (i, j).
@@ -476,20 +488,6 @@ __global__ void __launch_bounds__(TCT + 32, 1)
               mma_commit(barEmpty + 8 * bf);
               if (i == 7) mma_commit(barBfree + 8 * bb);
               if (i == 7 && ch == nchunk - 1) mma_commit(barSlice);
-              // cached planes of the later slices, up to kNA - 1 ahead: buffer tc % kNA is free
-              // once the MMAs of plane tc - kNA (at most plane t - 1) are done
-              while (tcopy <= t + kNA - 1 && tcopy < t0 + tplanes) {
-                const int tc = tcopy;
-                const int bc = tc % kNA;
-                if (tc >= kNA && !W.wait(barEmpty + 8 * bc, ((tc - kNA) / kNA) & 1)) goto drain;
-                // the producers' global stores (acquired through `full`) before the async copy
-                asm volatile("fence.proxy.async.global;" ::: "memory");
-                const int c = (tc - t0) % (8 * nchunk);   // cache entry: chunk c / 8, plane c % 8
-                bulk_load(sA0 + (uint32_t)(bc * kPlaneBytes), ccta + (size_t)c * (kPlaneBytes / 4),
-                          kPlaneBytes, barLoad + 8 * bc, keep);
-                ++iload[bc];
-                ++tcopy;
-              }
             }
           }
         }
@@ -506,8 +504,6 @@ __global__ void __launch_bounds__(TCT + 32, 1)
         }
         for (int b = 0; b < kNB; ++b)
           if (ibl[b] > nbl[b]) mbar_wait_until(barB + 8 * b, nbl[b] & 1, dl);
-        for (int b = 0; b < kNA; ++b)
-          for (int k = nload[b]; k < iload[b]; ++k) mbar_wait_until(barLoad + 8 * b, k & 1, dl);
       }
     }
     __syncwarp();
@@ -599,19 +595,24 @@ __global__ void __launch_bounds__(TCT + 32, 1)
           const int bf = t % kNA;
           if (t >= kNA) W.wait(barEmpty + 8 * bf, ((t - kNA) / kNA) & 1);
           uint32_t* dst = reinterpret_cast<uint32_t*>(sA + (size_t)bf * kPlaneBytes);
-          uint32_t* gdst = ccta + (size_t)(ch * 8 + i) * (kPlaneBytes / 4);
+          uint32_t* gdst = ccta + (size_t)(ch * 8 + i) * kCacheWords;
           const int sh = 7 * (3 - (i & 3));
 #pragma unroll
-          for (int gl = 0; gl < TCG; ++gl)
-            if (gl < ngr) {
-              const uint32_t w = i < 4 ? digit_pair(yh[2 * gl], yh[2 * gl + 1], sh)
-                                       : digit_pair(yl[2 * gl], yl[2 * gl + 1], sh);
-              dst[(gl * 16 + warp) * 32 + lane] = w;
-              st_hint(gdst + (gl * 16 + warp) * 32 + lane, w, keep);   // read by bulk copies
+          for (int g2 = 0; g2 < TCG / 2; ++g2)
+            if (2 * g2 < ngr) {
+              const int gl = 2 * g2;
+              const uint32_t* yy = i < 4 ? yh : yl;
+              dst[(gl * 16 + warp) * 32 + lane] = digit_pair(yy[2 * gl], yy[2 * gl + 1], sh);
+              dst[((gl + 1) * 16 + warp) * 32 + lane] =
+                  digit_pair(yy[2 * gl + 2], yy[2 * gl + 3], sh);
+              // the four 7-bit groups as bytes, read back by this same thread for the later
+              // slices (program order: no fence)
+              st_hint(gdst + (g2 * 16 + warp) * 32 + lane,
+                      pack_groups(yy[2 * gl], yy[2 * gl + 1], yy[2 * gl + 2], yy[2 * gl + 3], sh),
+                      keep);
             }
-          // shared-memory plane for the MMAs; global copy for the issuer's later bulk copies
+          // the shared-memory plane for the MMAs (async proxy)
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          asm volatile("fence.proxy.async.global;" ::: "memory");
           __syncwarp();
           if (lane == 0)
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(barFull + 8 * bf)
@@ -634,11 +635,43 @@ __global__ void __launch_bounds__(TCT + 32, 1)
       const int oline = line0 + (mm >> 1);
       TO* dstp =
           out + ((size_t)fld * fso + (size_t)(oline < nlines ? oline : 0) * Nz) * 2 + (mm & 1);
+      // the later slices' planes, rebuilt from the packed groups of the first slice: plane c
+      // (chunk c / 8, plane c % 8) of the slice that starts at plane number t0s
+      const int tplanes = 8 * nchunk;
+      int tnext = t;                     // next plane to rebuild (the slice after the current)
+      auto rebuild = [&](int upto) {
+        for (; tnext < upto; ++tnext) {
+          const int c = tnext % tplanes;   // planes of a tile are numbered slice by slice
+          const int chc = c >> 3;
+          const int ngc = min(TCKC, Kp - chc * TCKC) / 8;
+          const int bf = tnext % kNA;
+          const uint32_t* gsrc = ccta + (size_t)c * kCacheWords;
+          uint32_t wv[TCG / 2];
+#pragma unroll
+          for (int g2 = 0; g2 < TCG / 2; ++g2)
+            wv[g2] = (2 * g2 < ngc) ? ld_keep(gsrc + (g2 * 16 + warp) * 32 + lane, keep) : 0u;
+          if (tnext >= kNA) W.wait(barEmpty + 8 * bf, ((tnext - kNA) / kNA) & 1);
+          uint32_t* dst = reinterpret_cast<uint32_t*>(sA + (size_t)bf * kPlaneBytes);
+#pragma unroll
+          for (int g2 = 0; g2 < TCG / 2; ++g2)
+            if (2 * g2 < ngc) {
+              const int gl = 2 * g2;
+              dst[(gl * 16 + warp) * 32 + lane] = group_pair(wv[g2] & 0xFFFFu);
+              dst[((gl + 1) * 16 + warp) * 32 + lane] = group_pair(wv[g2] >> 16);
+            }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(barFull + 8 * bf)
+                         : "memory");
+        }
+      };
       for (int sl = 0; sl < nNt; ++sl, ++S) {
-        if (sl > 0) t += 8 * nchunk;   // planes the issuer copies
         if (sl == nNt - 1 && tile + (int)gridDim.x < ntiles) prefetch_rows(tile + gridDim.x, 0);
         // every MMA of the slice done
         W.wait(barSlice, S & 1);
+        // the next slice's first planes into the buffers its MMAs start with (free now)
+        if (sl + 1 < nNt) rebuild(t + min(kNA, tplanes));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its rows), columns
         // (w / 4) NT/4 .. + NT/4 - 1 of each of the eight accumulators, 4 at a time (after a
@@ -673,6 +706,11 @@ __global__ void __launch_bounds__(TCT + 32, 1)
         __syncwarp();
         if (lane == 0)
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(barDrain) : "memory");
+        // the rest of the next slice's planes, as its MMAs free the buffers
+        if (sl + 1 < nNt) {
+          rebuild(t + tplanes);
+          t += tplanes;
+        }
         // while the last slice's MMAs run: the next tile's cold row read
         if (sl == nNt - 2 && tile + (int)gridDim.x < ntiles) ahead = row_exponent(tile + gridDim.x);
       }
@@ -787,7 +825,7 @@ int cheb_tc_tables(int N, int dir, std::vector<uint16_t>& dig, std::vector<int>&
 size_t cheb_tc_smem(int NT) { return tc_smem_bytes(NT); }
 
 size_t cheb_tc_cache_bytes(int Kp) {
-  return (size_t)((Kp + TCKC - 1) / TCKC) * 8 * TCM * TCKC * 2;
+  return (size_t)((Kp + TCKC - 1) / TCKC) * 8 * kCacheWords * sizeof(uint32_t);
 }
 
 cudaError_t cheb_tc_prepare(int NT) {
