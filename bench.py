@@ -63,8 +63,8 @@ TRAFFIC_MB = {
     ("channel_128x128x129", 2, "zsolve"): 93.5 + 8.9,
     # 512 x 256 x 257 (full-size captures of the default bench command and of the FFT method
     # and FP64 step on the same grid)
-    ("channel_512x256x257_mixed", 1, "cheb_bwd"): 5574.4 + 3520.3,
-    ("channel_512x256x257_mixed", 1, "zsolve"): 4743.7 + 3612.8,
+    ("channel_512x256x257_mixed", 1, "cheb_bwd"): 1370.4 + 1219.1,
+    ("channel_512x256x257_mixed", 1, "zsolve"): 4723.2 + 3617.6,
     ("channel_512x256x257_mixed", 1, "zbwd"): 1342.6 + 1427.2,
     ("channel_512x256x257_mixed", 0, "zsolve"): 4753.3 + 3623.4,
     ("channel_512x256x257_mixed", 0, "zbwd"): 1343.7 + 2096.8,
@@ -72,22 +72,22 @@ TRAFFIC_MB = {
     ("channel_512x256x257_mixed", 0, "ybwd"): 1610.9 + 2393.1,
     # current step kernels (full-size captures of the default bench command's kernels with
     # --cheb tc, and of the 128^3 mixed tensor-core and float64 FFT-method steps)
-    ("channel_512x256x257_mixed", 1, "cheb_fwd"): 3960.3 + 5458.9,
-    ("channel_512x256x257_mixed", 1, "cheb_bwd"): 4578.5 + 3412.2,
-    ("channel_512x256x257_mixed", 1, "zrhs_coef"): 3489.9 + 1673.7,
-    ("channel_512x256x257_mixed", 1, "zbwd_coef"): 1342.2 + 2296.5,
-    ("channel_512x256x257_mixed", 1, "xline"): 1239.7 + 1789.9,
-    ("channel_512x256x257_mixed", 1, "yfwd"): 1819.2 + 907.1,
-    ("channel_512x256x257_mixed", 1, "ybwd"): 805.6 + 1164.7,
-    ("channel_128x128x129", 1, "cheb_fwd"): 92.2 + 122.9,
-    ("channel_128x128x129", 1, "cheb_bwd"): 111.7 + 52.2,
-    ("channel_128x128x129", 1, "zrhs_coef"): 218.2 + 79.0,
-    ("channel_128x128x129", 0, "zbwd_coef"): 83.9 + 87.1,
-    ("channel_128x128x129", 1, "zbwd_coef"): 83.9 + 87.1,
-    ("channel_128x128x129", 2, "zbwd_coef"): 83.9 + 87.1,
-    ("channel_128x128x129", 1, "xline"): 77.7 + 63.1,
-    ("channel_128x128x129", 1, "yfwd"): 114.2 + 32.1,
-    ("channel_128x128x129", 1, "ybwd"): 42.0 + 28.0,
+    ("channel_512x256x257_mixed", 1, "cheb_fwd"): 967.0 + 2368.5,
+    ("channel_512x256x257_mixed", 1, "cheb_bwd"): 1370.4 + 1219.1,
+    ("channel_512x256x257_mixed", 1, "zrhs_coef"): 3491.0 + 1965.3,
+    ("channel_512x256x257_mixed", 1, "zbwd_coef"): 1342.5 + 2296.4,
+    ("channel_512x256x257_mixed", 1, "xline"): 1242.4 + 1791.8,
+    ("channel_512x256x257_mixed", 1, "yfwd"): 1819.9 + 906.5,
+    ("channel_512x256x257_mixed", 1, "ybwd"): 805.6 + 1174.2,
+    ("channel_128x128x129", 1, "cheb_fwd"): 60.6 + 63.3,
+    ("channel_128x128x129", 1, "cheb_bwd"): 85.3 + 8.3,
+    ("channel_128x128x129", 1, "zrhs_coef"): 218.3 + 80.1,
+    ("channel_128x128x129", 0, "zbwd_coef"): 83.9 + 88.1,
+    ("channel_128x128x129", 1, "zbwd_coef"): 83.9 + 88.1,
+    ("channel_128x128x129", 2, "zbwd_coef"): 83.9 + 88.1,
+    ("channel_128x128x129", 1, "xline"): 77.6 + 62.7,
+    ("channel_128x128x129", 1, "yfwd"): 114.2 + 32.6,
+    ("channel_128x128x129", 1, "ybwd"): 42.0 + 27.9,
     ("channel_128x128x129", 0, "zrhs"): 218.3 + 73.3,
     ("channel_128x128x129", 0, "yfwd"): 228.3 + 85.9,
     ("channel_128x128x129", 0, "zbwd"): 84.0 + 82.6,

@@ -291,7 +291,7 @@ __device__ __forceinline__ void ypass_body(const typename C2<T>::t* __restrict__
 }
 
 template <typename T, bool INV, int WQ>
-__global__ void __launch_bounds__(YT) ypass_kernel(const typename C2<T>::t* __restrict__ in,
+__global__ void __launch_bounds__(YT, (WQ >= 1 && WQ <= 4) ? 4 : 1) ypass_kernel(const typename C2<T>::t* __restrict__ in,
                                                    typename C2<T>::t* __restrict__ out, int Mx,
                                                    int Ny, int P, int Nz, int TZ, long long fs_in,
                                                    long long fs_out, T scale, FftPlan pl,
@@ -361,21 +361,26 @@ __device__ __forceinline__ void ycomb_body(const typename C2<T>::t* __restrict__
 #pragma unroll
     for (int f = 0; f < 3; ++f)
       v[f] = (nyq || f >= nin) ? zero : scale * R[(f * TZ + zz) * LS + p];
+    // ca x + cb y with explicit fused multiply-adds (the single-grid and grouped kernels round
+    // alike)
+    auto lin = [](T ca, T2 x, T cb, T2 y) {
+      return mk(fmx(ca, x.x, cb * y.x), fmx(ca, x.y, cb * y.y));
+    };
     if (grp == 0) {
-      const T2 a = mul_i(kx * v[0] + ky * v[2]);
-      const T2 b = mul_i(kx * v[2] + ky * v[1]);
-      if (!mean) dst[o] = mul_i(kx * b - ky * a);
-      dst[3 * fs_out + o] = mul_i(kx * a + ky * b);
+      const T2 a = mul_i(lin(kx, v[0], ky, v[2]));
+      const T2 b = mul_i(lin(kx, v[2], ky, v[1]));
+      if (!mean) dst[o] = mul_i(lin(kx, b, -ky, a));
+      dst[3 * fs_out + o] = mul_i(lin(kx, a, ky, b));
     } else if (grp == 1) {
       if (mean) {
         dst[o] = v[0];
         dst[fs_out + o] = v[1];
       } else {
-        dst[fs_out + o] = mul_i(kx * v[1] - ky * v[0]);
+        dst[fs_out + o] = mul_i(lin(kx, v[1], -ky, v[0]));
       }
-      dst[2 * fs_out + o] = mul_i(kx * v[0] + ky * v[1]);
+      dst[2 * fs_out + o] = mul_i(lin(kx, v[0], ky, v[1]));
     } else if (grp == 2) {
-      dst[4 * fs_out + o] = mul_mi(kx * v[0] + ky * v[1]);
+      dst[4 * fs_out + o] = mul_mi(lin(kx, v[0], ky, v[1]));
     } else {
       dst[(grp == 3 ? 5 : 6) * fs_out + o] = v[0];
     }
@@ -383,7 +388,7 @@ __device__ __forceinline__ void ycomb_body(const typename C2<T>::t* __restrict__
 }
 
 template <typename T, int WQ>
-__global__ void __launch_bounds__(YT) ycomb_kernel(const typename C2<T>::t* __restrict__ in,
+__global__ void __launch_bounds__(YT, (WQ >= 1 && WQ <= 4) ? 4 : 1) ycomb_kernel(const typename C2<T>::t* __restrict__ in,
                                                    typename C2<T>::t* __restrict__ out, int Mx,
                                                    int Ny, int P, int Nz, int L, long long fs_in,
                                                    long long fs_out, T scale, T kxs, T kys,
@@ -580,24 +585,25 @@ __device__ __forceinline__ void xline_warp_body(const float2* __restrict__ in,
       const float2 u = phys[i], vv = phys[R * 32 + i], w = phys[2 * R * 32 + i];
       const float2 ph = phys[3 * R * 32 + i], fx = phys[4 * R * 32 + i];
       const float2 fy = phys[5 * R * 32 + i], fz = phys[6 * R * 32 + i];
+      // explicit fused multiply-adds: the single-grid and grouped kernels round alike
       float2 r;
       switch (g) {
         case 0:
-          r.x = w.x * w.x + kappa * fz.x * fz.x - u.x * u.x - kappa * fx.x * fx.x;
-          r.y = w.y * w.y + kappa * fz.y * fz.y - u.y * u.y - kappa * fx.y * fx.y;
+          r.x = fmaf(kappa * fz.x, fz.x, w.x * w.x) - fmaf(kappa * fx.x, fx.x, u.x * u.x);
+          r.y = fmaf(kappa * fz.y, fz.y, w.y * w.y) - fmaf(kappa * fx.y, fx.y, u.y * u.y);
           break;
         case 1:
-          r.x = w.x * w.x + kappa * fz.x * fz.x - vv.x * vv.x - kappa * fy.x * fy.x;
-          r.y = w.y * w.y + kappa * fz.y * fz.y - vv.y * vv.y - kappa * fy.y * fy.y;
+          r.x = fmaf(kappa * fz.x, fz.x, w.x * w.x) - fmaf(kappa * fy.x, fy.x, vv.x * vv.x);
+          r.y = fmaf(kappa * fz.y, fz.y, w.y * w.y) - fmaf(kappa * fy.y, fy.y, vv.y * vv.y);
           break;
         case 2:
-          r = make_float2(-u.x * vv.x - kappa * fx.x * fy.x, -u.y * vv.y - kappa * fx.y * fy.y);
+          r = make_float2(-fmaf(kappa * fx.x, fy.x, u.x * vv.x), -fmaf(kappa * fx.y, fy.y, u.y * vv.y));
           break;
         case 3:
-          r = make_float2(-u.x * w.x - kappa * fx.x * fz.x, -u.y * w.y - kappa * fx.y * fz.y);
+          r = make_float2(-fmaf(kappa * fx.x, fz.x, u.x * w.x), -fmaf(kappa * fx.y, fz.y, u.y * w.y));
           break;
         case 4:
-          r = make_float2(-vv.x * w.x - kappa * fy.x * fz.x, -vv.y * w.y - kappa * fy.y * fz.y);
+          r = make_float2(-fmaf(kappa * fy.x, fz.x, vv.x * w.x), -fmaf(kappa * fy.y, fz.y, vv.y * w.y));
           break;
         case 5: r = make_float2(ph.x * ph.x * ph.x, ph.y * ph.y * ph.y); break;
         case 6: r = make_float2(u.x * ph.x, u.y * ph.y); break;

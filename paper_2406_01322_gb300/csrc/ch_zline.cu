@@ -384,9 +384,19 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   const ZSmem z = carve(zsm, Nz, N);
   const bool is00 = (mx == 0 && j == 0);
   const double k2 = ksq(kx, ky);
-  // shared lines: 0..6 the combined non-linear lines, 11 w (omega and phi are read from global
-  // memory where they are used); 7..10 and 12 derivatives, reused as the sweep goes on
-  for (int n = tid; n < Nz; n += blockDim.x) LN(z, 11, Nz)[n] = st_w[off + n];
+  // shared lines: 0..6 the combined non-linear lines, 11 w; 7..10 and 12 derivatives, reused as
+  // the sweep goes on.  omega and phi: lines 13 and 14 in the DCT variant (its shared memory has
+  // room for sixteen lines), read from global memory where they are used in the coefficient-space
+  // variant (thirteen lines: four CTAs per SM at nz = 257)
+  for (int n = tid; n < Nz; n += blockDim.x) {
+    LN(z, 11, Nz)[n] = st_w[off + n];
+    if (!PRE) {
+      LN(z, 13, Nz)[n] = st_om[off + n];
+      LN(z, 14, Nz)[n] = st_phi[off + n];
+    }
+  }
+  const double2* phs = PRE ? st_phi + off : LN(z, 14, Nz);   // phi^n and omega^n of this line
+  const double2* oms = PRE ? st_om + off : LN(z, 13, Nz);
   // The seven combined non-linear lines, formed by the forward y pass (the Chebyshev transform
   // commutes with the z-independent factors i kx, i ky):
   //   0: P = i kx B - i ky A   1: Q = i kx Syz - i ky Sxz   (h_omega = P + D Q)
@@ -404,7 +414,7 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
       dct_forward_lines(z, f0, (7 - f0 < NBF) ? 7 - f0 : NBF, Nz, N, pz, g.zcs, is00);
   // G = phi^3 - (1 + shat) phi
   for (int n = tid; n < Nz; n += blockDim.x)
-    LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * st_phi[off + n];
+    LN(z, 6, Nz)[n] = LN(z, 6, Nz)[n] - (1.0 + g.shat) * phs[n];
   __syncthreads();
   // Seven derivatives (D is linear, so the second derivatives of the assembly are taken of
   // sums): h_w = -k^2 C - D(R + D C), S_phi = F - (k^2 / Pe) G + D(D G / Pe - w phi),
@@ -454,7 +464,7 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
     const double2 sphi = LN(z, 4, Nz)[n] + LN(z, 9, Nz)[n];
     const double2 w = LN(z, 11, Nz)[n], d2w = LN(z, 1, Nz)[n];
     const double2 th = make_double2(fma(-k2, w.x, d2w.x), fma(-k2, w.y, d2w.y));
-    const double2 om = st_om[off + n], ph = st_phi[off + n];
+    const double2 om = oms[n], ph = phs[n];
     double2 r0 = make_double2(cb * om.x, cb * om.y);
     double2 r1 = make_double2(cb * th.x, cb * th.y);
     double2 r2 = make_double2(prd * ph.x, prd * ph.y);

@@ -60,6 +60,27 @@ def test_ensemble_members_match_single_grids_bitwise(binding, precision):
     ens.close()
 
 
+def test_warp_fft_members_match_single_grids_bitwise(binding):
+    """Members whose float32 x and y lines take the warp-level FFTs (Px, Py = 96 and 192: nx, ny
+    = 64 and 128), beside one that takes the block passes: each evolves exactly as the same
+    channel stepped alone (mixed precision, 6 steps)."""
+    ms = [dict(nx=nx, ny=ny, nz=nz, **PHYS) for nx, ny, nz in [(64, 64, 17), (128, 16, 9),
+                                                                (32, 32, 17)]]
+    ens = binding.Ensemble(ms, precision=1)
+    singles = [binding.Grid(precision=1, **m) for m in ms]
+    for i, (g, s, m) in enumerate(zip(ens.grids, singles, ms)):
+        f = [torch.from_numpy(a) for a in fields_of(m, 2000 + i)]
+        g.set_fields(*f)
+        s.set_fields(*f)
+    ens.step(6)
+    for s in singles:
+        s.step(6)
+    for g, s in zip(ens.grids, singles):
+        for a, b in zip(g.get_fields(), s.get_fields()):
+            assert torch.equal(a, b)
+    ens.close()
+
+
 def test_ensemble_timed_steps_match_graph_steps(binding):
     ens, singles = setup(binding, 0)
     tot, ks = ens.step_timed(3)
