@@ -355,7 +355,7 @@ __device__ void dct_backward_lines_store(const ZSmem& z, int first, int cnt, int
 // nl: the seven combined non-linear lines (launch_ycomb) as samples on the Gauss-Lobatto points.
 // PRE = 1: nl holds their Chebyshev coefficients (float64, transformed by the tensor-core
 // kernel), so the forward DCTs are skipped.
-template <typename T, int PRE = 0>
+template <typename T, int PRE = 0, int GST = PRE>
 __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>::t* __restrict__ nl,
                                           long long fs, const double2* __restrict__ st_om,
                                           const double2* __restrict__ st_w,
@@ -385,18 +385,18 @@ __device__ __forceinline__ void zrhs_body(const GridDev& g, const typename C2<T>
   const bool is00 = (mx == 0 && j == 0);
   const double k2 = ksq(kx, ky);
   // shared lines: 0..6 the combined non-linear lines, 11 w; 7..10 and 12 derivatives, reused as
-  // the sweep goes on.  omega and phi: lines 13 and 14 in the DCT variant (its shared memory has
-  // room for sixteen lines), read from global memory where they are used in the coefficient-space
-  // variant (thirteen lines: four CTAs per SM at nz = 257)
+  // the sweep goes on.  omega and phi: lines 13 and 14 (GST = 0), or read from global memory
+  // where they are used (GST = 1, the single-grid coefficient-space variant: thirteen lines,
+  // four CTAs per SM at nz = 257); the arithmetic is the same either way
   for (int n = tid; n < Nz; n += blockDim.x) {
     LN(z, 11, Nz)[n] = st_w[off + n];
-    if (!PRE) {
+    if (!GST) {
       LN(z, 13, Nz)[n] = st_om[off + n];
       LN(z, 14, Nz)[n] = st_phi[off + n];
     }
   }
-  const double2* phs = PRE ? st_phi + off : LN(z, 14, Nz);   // phi^n and omega^n of this line
-  const double2* oms = PRE ? st_om + off : LN(z, 13, Nz);
+  const double2* phs = GST ? st_phi + off : LN(z, 14, Nz);   // phi^n and omega^n of this line
+  const double2* oms = GST ? st_om + off : LN(z, 13, Nz);
   // The seven combined non-linear lines, formed by the forward y pass (the Chebyshev transform
   // commutes with the z-independent factors i kx, i ky):
   //   0: P = i kx B - i ky A   1: Q = i kx Syz - i ky Sxz   (h_omega = P + D Q)
@@ -1945,7 +1945,7 @@ __global__ void __launch_bounds__(ZTC) grouped_zrhs_coef_kernel(const Member* __
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     const int m = member_of(begin, nmem, item);
     const Member& M = mem[m];
-    zrhs_body<double, 1>(M.g, M.cf, M.fs, M.om, M.w, M.phi, M.hom, M.hw, M.hphi, M.R, M.first,
+    zrhs_body<double, 1, 0>(M.g, M.cf, M.fs, M.om, M.w, M.phi, M.hom, M.hw, M.hphi, M.R, M.first,
                          M.pz, item - begin[m]);
     __syncthreads();
   }
@@ -1995,7 +1995,8 @@ size_t zline_smem(const GridDev& g) {
 static size_t zline_coef_smem(const GridDev& g) { return (size_t)13 * g.nz * sizeof(double2); }
 static size_t zbwd_coef_smem(const GridDev& g) { return (size_t)5 * g.nz * sizeof(double2); }
 size_t zline_coef_stage_smem(const GridDev& g, int stage) {
-  return stage == 0 ? zline_coef_smem(g) : zbwd_coef_smem(g);
+  // the grouped coefficient-space zrhs keeps omega and phi in shared memory (sixteen lines)
+  return stage == 0 ? (size_t)NLINES * g.nz * sizeof(double2) : zbwd_coef_smem(g);
 }
 
 size_t fac_doubles(const GridDev& g) { return ((size_t)13 * g.nz + 20) * g.NK; }
