@@ -8,6 +8,7 @@
 //
 // Layout of every intermediate array: (mx, y or ky, z) with z fastest; a CTA owns a tile of
 // lines and does the layout change through shared memory.
+#include <algorithm>
 #include <type_traits>
 
 #include "ch_internal.h"
@@ -508,12 +509,134 @@ __global__ void __launch_bounds__(NTH) xline_kernel(const typename C2<T>::t* __r
   xline_body<T, LOOP>(in, out, Mx, Px, Py, Nz, fs, kappa, scale, kxs, pl, blockIdx.x, blockIdx.y);
 }
 
-// Fused x line on warp FFTs: one CTA per (pair of z rows, y) as xline_body, 8 warps.  Warps
-// 0..6 transform the seven input lines (u v w phi phi_x phi_y phi_z) into shared memory in the
-// backward transform's order; each warp then forms one product line (9 over the 8 warps) in
-// registers from those samples, transforms it forward and stores its kept modes.
-// Shared memory: seven lines of P float2, the twiddles W_P^(l k) as [k][l] (R x 32 float2).
+// Fused x line on warp FFTs, one item = (pair of z rows, y) as in xline_body.  A backward line
+// takes input line f (u v w phi phi_x phi_y phi_z) of an item to physical space in the backward
+// transform's order (shared memory, P float2, index k * 32 + lane); a forward line forms product
+// g (of nine) in registers from the seven samples, transforms it forward and stores its kept
+// modes.  One warp does each line.  The twiddles W_P^(l k) sit in shared memory as [k][l]
+// (R x 32 float2).
 constexpr int XWT = 256;
+template <int Q>
+__device__ __forceinline__ void xw_backward(const float2* __restrict__ in, float2* __restrict__ phys,
+                                            int f, int Mx, size_t base, size_t mstride, bool two,
+                                            long long fs, float kxs,
+                                            const float2* __restrict__ tw,
+                                            const float2* __restrict__ twl, int lane) {
+  constexpr int R = 3 * Q, P = 32 * R;
+  // the lane-stage twiddles W_{2h}^j = W_P^(j 16 R / h), conjugated (backward: exp(+i))
+  float2 wdif[5];
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int hf = 16 >> s;
+    wdif[s] = (lane & hf) ? tw[(lane & (hf - 1)) * (16 * R / hf)] : make_float2(1.0f, 0.0f);
+    wdif[s].y = -wdif[s].y;
+  }
+  const int src_f = (f < 4) ? f : f - 1;      // phi_x (line 4) comes from phi (input 3)
+  const float2* src = in + src_f * fs + base;
+  float2 v[R];
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    v[m] = make_float2(0.0f, 0.0f);
+    if (m >= Q && m < 2 * Q) continue;         // modes Mx .. 2 Mx - 1: zero padding
+    const int n = lane + 32 * m;
+    const int q = (m < Q) ? n : P - n;         // mode index (the upper third: negative modes)
+    if (q >= Mx) continue;                     // mode Mx (x Nyquist) is not kept
+    float2 a = src[(size_t)q * mstride];
+    float2 b = two ? src[(size_t)q * mstride + 1] : make_float2(0.0f, 0.0f);
+    if (f == 4) {                              // i kx phi
+      const float kx = kxs * (float)q;
+      a = make_float2(-kx * a.y, kx * a.x);
+      b = make_float2(-kx * b.y, kx * b.x);
+    }
+    if (n == 0) v[m] = make_float2(a.x, b.x);  // the imaginary part of a DC coefficient is not used
+    else if (m < Q) v[m] = make_float2(a.x - b.y, a.y + b.x);   // a + i b
+    else v[m] = make_float2(a.x + b.y, b.x - a.y);              // conj(a) + i conj(b)
+  }
+  dft3q<Q, true, true>(v, tw);
+#pragma unroll
+  for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], twl[k * 32 + lane]);
+  lanes_dif<R>(v, wdif, lane);
+#pragma unroll
+  for (int k = 0; k < R; ++k) phys[(f * R + k) * 32 + lane] = v[k];
+}
+
+// product g (rows z0 in .x, z0+1 in .y) of the seven samples in `phys`, forward transform, kept
+// modes to `out`
+template <int Q>
+__device__ __forceinline__ void xw_forward(const float2* __restrict__ phys, float2* __restrict__ out,
+                                           int g, int Mx, size_t base, size_t mstride, bool two,
+                                           long long fs, float kappa, float scale,
+                                           const float2* __restrict__ tw,
+                                           const float2* __restrict__ twl, int lane) {
+  constexpr int R = 3 * Q;
+  float2 wdit[5];
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int ht = 1 << s;
+    wdit[s] = (lane & ht) ? tw[(lane & (ht - 1)) * (16 * R / ht)] : make_float2(1.0f, 0.0f);
+  }
+  const float hs = 0.5f * scale;
+  float2 v[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int i = k * 32 + lane;
+    const float2 u = phys[i], vv = phys[R * 32 + i], w = phys[2 * R * 32 + i];
+    const float2 ph = phys[3 * R * 32 + i], fx = phys[4 * R * 32 + i];
+    const float2 fy = phys[5 * R * 32 + i], fz = phys[6 * R * 32 + i];
+    // explicit fused multiply-adds: the single-grid and grouped kernels round alike
+    float2 r;
+    switch (g) {
+      case 0:
+        r.x = fmaf(kappa * fz.x, fz.x, w.x * w.x) - fmaf(kappa * fx.x, fx.x, u.x * u.x);
+        r.y = fmaf(kappa * fz.y, fz.y, w.y * w.y) - fmaf(kappa * fx.y, fx.y, u.y * u.y);
+        break;
+      case 1:
+        r.x = fmaf(kappa * fz.x, fz.x, w.x * w.x) - fmaf(kappa * fy.x, fy.x, vv.x * vv.x);
+        r.y = fmaf(kappa * fz.y, fz.y, w.y * w.y) - fmaf(kappa * fy.y, fy.y, vv.y * vv.y);
+        break;
+      case 2:
+        r = make_float2(-fmaf(kappa * fx.x, fy.x, u.x * vv.x), -fmaf(kappa * fx.y, fy.y, u.y * vv.y));
+        break;
+      case 3:
+        r = make_float2(-fmaf(kappa * fx.x, fz.x, u.x * w.x), -fmaf(kappa * fx.y, fz.y, u.y * w.y));
+        break;
+      case 4:
+        r = make_float2(-fmaf(kappa * fy.x, fz.x, vv.x * w.x), -fmaf(kappa * fy.y, fz.y, vv.y * w.y));
+        break;
+      case 5: r = make_float2(ph.x * ph.x * ph.x, ph.y * ph.y * ph.y); break;
+      case 6: r = make_float2(u.x * ph.x, u.y * ph.y); break;
+      case 7: r = make_float2(vv.x * ph.x, vv.y * ph.y); break;
+      default: r = make_float2(w.x * ph.x, w.y * ph.y); break;
+    }
+    v[k] = r;
+  }
+  lanes_dit<R>(v, wdit, lane);
+#pragma unroll
+  for (int k = 1; k < R; ++k) v[k] = cmul(v[k], twl[k * 32 + lane]);
+  dft3q<Q, false, false>(v, tw);
+  // unpack the two real rows: A_k = (Z_k + conj Z_{P-k}) / 2, B_k = (Z_k - conj Z_{P-k}) / (2 i)
+  // for the kept modes k = lane + 32 m < Mx (m < Q); Z_{P-k} sits in lane -k mod 32, register
+  // R - 1 - m (lane 0: its own register R - m)
+  float2* dst = out + g * fs + base;
+#pragma unroll
+  for (int m = 0; m < Q; ++m) {
+    const float2 o = v[R - 1 - m];
+    const int pl = (32 - lane) & 31;
+    float2 Zm = make_float2(__shfl_sync(0xffffffffu, o.x, pl), __shfl_sync(0xffffffffu, o.y, pl));
+    if (lane == 0) Zm = (m == 0) ? v[0] : v[(R - m) % R];
+    const float2 Zk = v[m];
+    const int k = lane + 32 * m;
+    if (k < Mx) {
+      float2* d = dst + (size_t)k * mstride;
+      d[0] = make_float2(hs * (Zk.x + Zm.x), hs * (Zk.y - Zm.y));
+      if (two) d[1] = make_float2(hs * (Zk.y + Zm.y), hs * (Zm.x - Zk.x));
+    }
+  }
+}
+
+// One item (z rows 2 bx, 2 bx + 1 at y = by) with 8 warps: warps 0..6 the backward lines, then
+// each warp a product line (9 over the 8 warps).  Shared memory: seven lines of P float2 and the
+// twiddle table.
 template <int Q>
 __device__ __forceinline__ void xline_warp_body(const float2* __restrict__ in,
                                                 float2* __restrict__ out, int Mx, int Py, int Nz,
@@ -521,132 +644,92 @@ __device__ __forceinline__ void xline_warp_body(const float2* __restrict__ in,
                                                 const float2* __restrict__ tw, int bx, int by) {
   constexpr int R = 3 * Q, P = 32 * R;
   extern __shared__ float2 xw_sm[];
-  float2* phys = xw_sm;                 // 7 lines of P, index k * 32 + lane
-  float2* twl = xw_sm + 7 * P;          // W_P^(l k) at [k][l]
+  float2* phys = xw_sm;
+  float2* twl = xw_sm + 7 * P;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int z0 = 2 * bx;
-  const int y = by;
   const bool two = (z0 + 1 < Nz);
-  const size_t base = (size_t)y * Nz + z0;
+  const size_t base = (size_t)by * Nz + z0;
   const size_t mstride = (size_t)Py * Nz;
   for (int i = threadIdx.x; i < R * 32; i += blockDim.x) {
     const int k = i >> 5, l = i & 31;
     twl[i] = tw[k * l];                 // k l < P
   }
-  // the lane-stage twiddles W_{2h}^j = W_P^(j 16 R / h)
-  float2 wdif[5], wdit[5];
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int hf = 16 >> s, ht = 1 << s;
-    wdif[s] = (lane & hf) ? tw[(lane & (hf - 1)) * (16 * R / hf)] : make_float2(1.0f, 0.0f);
-    wdif[s].y = -wdif[s].y;             // backward: exp(+i)
-    wdit[s] = (lane & ht) ? tw[(lane & (ht - 1)) * (16 * R / ht)] : make_float2(1.0f, 0.0f);
-  }
   __syncthreads();
-  // ---- 1. seven backward lines (two z rows packed as a + i b), warp f = line f
-  if (warp < 7) {
-    const int f = warp;
-    const int src_f = (f < 4) ? f : f - 1;      // phi_x (line 4) comes from phi (input 3)
-    const float2* src = in + src_f * fs + base;
-    float2 v[R];
-#pragma unroll
-    for (int m = 0; m < R; ++m) {
-      v[m] = make_float2(0.0f, 0.0f);
-      if (m >= Q && m < 2 * Q) continue;         // modes Mx .. 2 Mx - 1: zero padding
-      const int n = lane + 32 * m;
-      const int q = (m < Q) ? n : P - n;         // mode index (the upper third: negative modes)
-      if (q >= Mx) continue;                     // mode Mx (x Nyquist) is not kept
-      float2 a = src[(size_t)q * mstride];
-      float2 b = two ? src[(size_t)q * mstride + 1] : make_float2(0.0f, 0.0f);
-      if (f == 4) {                              // i kx phi
-        const float kx = kxs * (float)q;
-        a = make_float2(-kx * a.y, kx * a.x);
-        b = make_float2(-kx * b.y, kx * b.x);
-      }
-      if (n == 0) v[m] = make_float2(a.x, b.x);  // the imaginary part of a DC coefficient is not used
-      else if (m < Q) v[m] = make_float2(a.x - b.y, a.y + b.x);   // a + i b
-      else v[m] = make_float2(a.x + b.y, b.x - a.y);              // conj(a) + i conj(b)
-    }
-    dft3q<Q, true, true>(v, tw);
-#pragma unroll
-    for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], twl[k * 32 + lane]);
-    lanes_dif<R>(v, wdif, lane);
-#pragma unroll
-    for (int k = 0; k < R; ++k) phys[(f * R + k) * 32 + lane] = v[k];
-  }
+  if (warp < 7) xw_backward<Q>(in, phys, warp, Mx, base, mstride, two, fs, kxs, tw, twl, lane);
   __syncthreads();
-  // ---- 2. products (rows z0 in .x, z0+1 in .y) and forward transforms, one line per warp
-  const float hs = 0.5f * scale;
-  for (int g = warp; g < 9; g += 8) {
-    float2 v[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int i = k * 32 + lane;
-      const float2 u = phys[i], vv = phys[R * 32 + i], w = phys[2 * R * 32 + i];
-      const float2 ph = phys[3 * R * 32 + i], fx = phys[4 * R * 32 + i];
-      const float2 fy = phys[5 * R * 32 + i], fz = phys[6 * R * 32 + i];
-      // explicit fused multiply-adds: the single-grid and grouped kernels round alike
-      float2 r;
-      switch (g) {
-        case 0:
-          r.x = fmaf(kappa * fz.x, fz.x, w.x * w.x) - fmaf(kappa * fx.x, fx.x, u.x * u.x);
-          r.y = fmaf(kappa * fz.y, fz.y, w.y * w.y) - fmaf(kappa * fx.y, fx.y, u.y * u.y);
-          break;
-        case 1:
-          r.x = fmaf(kappa * fz.x, fz.x, w.x * w.x) - fmaf(kappa * fy.x, fy.x, vv.x * vv.x);
-          r.y = fmaf(kappa * fz.y, fz.y, w.y * w.y) - fmaf(kappa * fy.y, fy.y, vv.y * vv.y);
-          break;
-        case 2:
-          r = make_float2(-fmaf(kappa * fx.x, fy.x, u.x * vv.x), -fmaf(kappa * fx.y, fy.y, u.y * vv.y));
-          break;
-        case 3:
-          r = make_float2(-fmaf(kappa * fx.x, fz.x, u.x * w.x), -fmaf(kappa * fx.y, fz.y, u.y * w.y));
-          break;
-        case 4:
-          r = make_float2(-fmaf(kappa * fy.x, fz.x, vv.x * w.x), -fmaf(kappa * fy.y, fz.y, vv.y * w.y));
-          break;
-        case 5: r = make_float2(ph.x * ph.x * ph.x, ph.y * ph.y * ph.y); break;
-        case 6: r = make_float2(u.x * ph.x, u.y * ph.y); break;
-        case 7: r = make_float2(vv.x * ph.x, vv.y * ph.y); break;
-        default: r = make_float2(w.x * ph.x, w.y * ph.y); break;
-      }
-      v[k] = r;
-    }
-    lanes_dit<R>(v, wdit, lane);
-#pragma unroll
-    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], twl[k * 32 + lane]);
-    dft3q<Q, false, false>(v, tw);
-    // unpack the two real rows: A_k = (Z_k + conj Z_{P-k}) / 2, B_k = (Z_k - conj Z_{P-k}) / (2 i)
-    // for the kept modes k = lane + 32 m < Mx (m < Q); Z_{P-k} sits in lane -k mod 32, register
-    // R - 1 - m (lane 0: its own register R - m)
-    float2* dst = out + g * fs + base;
-#pragma unroll
-    for (int m = 0; m < Q; ++m) {
-      const float2 o = v[R - 1 - m];
-      const int pl = (32 - lane) & 31;
-      float2 Zm = make_float2(__shfl_sync(0xffffffffu, o.x, pl), __shfl_sync(0xffffffffu, o.y, pl));
-      if (lane == 0) Zm = (m == 0) ? v[0] : v[(R - m) % R];
-      const float2 Zk = v[m];
-      const int k = lane + 32 * m;
-      if (k < Mx) {
-        float2* d = dst + (size_t)k * mstride;
-        d[0] = make_float2(hs * (Zk.x + Zm.x), hs * (Zk.y - Zm.y));
-        if (two) d[1] = make_float2(hs * (Zk.y + Zm.y), hs * (Zm.x - Zk.x));
-      }
-    }
-  }
+  for (int g = warp; g < 9; g += 8)
+    xw_forward<Q>(phys, out, g, Mx, base, mstride, two, fs, kappa, scale, tw, twl, lane);
 }
 
+// v through an opaque move that is also a compiler memory barrier: nothing derived from the
+// result is computed, and no memory access is moved, across it
+__device__ __forceinline__ int opaque_int(int v) {
+  int r;
+  asm volatile("mov.b32 %0, %1;" : "=r"(r) : "r"(v) : "memory");
+  return r;
+}
+
+// Persistent x line: each CTA walks the items t = blockIdx.x, + gridDim.x, ... (z pair fastest)
+// with two buffers of seven lines.  A round holds 16 line tasks, two per warp: the nine forward
+// lines of item t (warp w line w, warp 7 also line 8) and the seven backward lines of the next
+// item (warps 0..6) into the other buffer, so no warp idles and the next item's loads overlap
+// the products' transforms; one barrier per round.  Per line the same arithmetic as
+// xline_warp_body.
 template <int Q>
 __global__ void __launch_bounds__(XWT, Q >= 8 ? 2 : 3)
     xline_warp_kernel(const float2* __restrict__ in, float2* __restrict__ out, int Mx, int Py,
                       int Nz, long long fs, float kappa, float scale, float kxs,
-                      const float2* __restrict__ tw) {
-  xline_warp_body<Q>(in, out, Mx, Py, Nz, fs, kappa, scale, kxs, tw, blockIdx.x, blockIdx.y);
+                      const float2* __restrict__ tw0) {
+  constexpr int R = 3 * Q, P = 32 * R;
+  extern __shared__ float2 xp_sm[];
+  float2* twl = xp_sm + 14 * P;
+  const int lane0 = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nzp = (Nz + 1) / 2, nitems = nzp * Py;
+  const size_t mstride = (size_t)Py * Nz;
+  for (int i = threadIdx.x; i < R * 32; i += blockDim.x) {
+    const int k = i >> 5, l = i & 31;
+    twl[i] = tw0[k * l];
+  }
+  __syncthreads();
+  int t = blockIdx.x;
+  if (t >= nitems) return;
+  if (warp < 7) {
+    const int z0 = 2 * (t % nzp);
+    xw_backward<Q>(in, xp_sm, warp, Mx, (size_t)(t / nzp) * Nz + z0, mstride, z0 + 1 < Nz, fs,
+                   kxs, tw0, twl, lane0);
+  }
+  __syncthreads();
+  int b = 0;
+#pragma unroll 1
+  for (; t < nitems; t += gridDim.x) {
+    // the lane index passes through an opaque move before each line, so the compiler neither
+    // holds a line's mode offsets and twiddles across the loop nor starts the next line's loads
+    // inside the previous one (either would double the registers of a line)
+    const int lane = opaque_int(lane0);
+    const float2* cur = xp_sm + b * 7 * P;
+    float2* nxt = xp_sm + (b ^ 1) * 7 * P;
+    const int z0 = 2 * (t % nzp);
+    const size_t base = (size_t)(t / nzp) * Nz + z0;
+    const bool two = z0 + 1 < Nz;
+    xw_forward<Q>(cur, out, warp, Mx, base, mstride, two, fs, kappa, scale, tw0, twl, lane);
+    const int tn = t + gridDim.x;
+    __syncwarp();   // ptxas moves no memory access across it: the next line's loads start here
+    const int lane2 = opaque_int(lane0);
+    if (warp == 7) {
+      xw_forward<Q>(cur, out, 8, Mx, base, mstride, two, fs, kappa, scale, tw0, twl, lane2);
+    } else if (tn < nitems) {
+      const int zn = 2 * (tn % nzp);
+      xw_backward<Q>(in, nxt, warp, Mx, (size_t)(tn / nzp) * Nz + zn, mstride, zn + 1 < Nz, fs,
+                     kxs, tw0, twl, lane2);
+    }
+    __syncthreads();
+    b ^= 1;
+  }
 }
-// shared memory of the warp-FFT x line
+// shared memory of the persistent warp-FFT x line: two buffers of seven lines and the twiddles
 __host__ __device__ __forceinline__ size_t xline_warp_smem(int Px) {
-  return (size_t)8 * Px * sizeof(float2);
+  return (size_t)15 * Px * sizeof(float2);
 }
 
 // plain r2c along x of physical rows (Nz, Ny, Nx) -> (Mx, Ny, Nz); two z rows per CTA
@@ -1062,11 +1145,27 @@ cudaError_t launch_xline_t(int prec, const GridDev& g, const void* in7, void* ou
 template <int Q>
 cudaError_t launch_xline_warp(const GridDev& g, const void* in7, void* out10, long long fs,
                               double scale, const FftPlan& px, cudaStream_t s) {
-  const size_t smem = (size_t)8 * g.Px * sizeof(float2);
+  const size_t smem = xline_warp_smem(g.Px);
   static SmemLimit cur;
-  const cudaError_t e = ensure_smem(xline_warp_kernel<Q>, smem, &cur);
+  static SmemLimit ctas;   // persistent grid per device: SMs x resident CTAs
+  cudaError_t e = ensure_smem(xline_warp_kernel<Q>, smem, &cur);
   if (e != cudaSuccess) return e;
-  dim3 grid((g.nz + 1) / 2, g.Py);
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int nct = (dev >= 0 && dev < kMaxSmemDevices) ? ctas.v[dev].load(std::memory_order_acquire) : 0;
+  if (nct <= 0) {
+    int nsm = 0, per = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, xline_warp_kernel<Q>, XWT, smem);
+    if (e != cudaSuccess) return e;
+    nct = std::max(1, nsm * per);
+    if (dev >= 0 && dev < kMaxSmemDevices) ctas.v[dev].store(nct, std::memory_order_release);
+  }
+  const long long items = (long long)((g.nz + 1) / 2) * g.Py;
+  if (items == 0) return cudaSuccess;
+  const int grid = (int)std::min<long long>(items, nct);
   xline_warp_kernel<Q><<<grid, XWT, smem, s>>>((const float2*)in7, (float2*)out10, g.Mx, g.Py,
                                                g.nz, fs, (float)g.kappa, (float)scale,
                                                (float)(6.283185307179586476925 / g.lx),
