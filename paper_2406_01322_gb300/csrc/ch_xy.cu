@@ -8,6 +8,8 @@
 //
 // Layout of every intermediate array: (mx, y or ky, z) with z fastest; a CTA owns a tile of
 // lines and does the layout change through shared memory.
+#include <stdint.h>
+
 #include <algorithm>
 #include <type_traits>
 
@@ -541,8 +543,16 @@ __device__ __forceinline__ void xw_backward(const float2* __restrict__ in, float
     const int n = lane + 32 * m;
     const int q = (m < Q) ? n : P - n;         // mode index (the upper third: negative modes)
     if (q >= Mx) continue;                     // mode Mx (x Nyquist) is not kept
-    float2 a = src[(size_t)q * mstride];
-    float2 b = two ? src[(size_t)q * mstride + 1] : make_float2(0.0f, 0.0f);
+    const float2* pq = src + (size_t)q * mstride;
+    float2 a, b;
+    if (two && (reinterpret_cast<uintptr_t>(pq) & 15) == 0) {   // the pair in one 16-byte load
+      const float4 ab = *reinterpret_cast<const float4*>(pq);
+      a = make_float2(ab.x, ab.y);
+      b = make_float2(ab.z, ab.w);
+    } else {
+      a = pq[0];
+      b = two ? pq[1] : make_float2(0.0f, 0.0f);
+    }
     if (f == 4) {                              // i kx phi
       const float kx = kxs * (float)q;
       a = make_float2(-kx * a.y, kx * a.x);
@@ -628,13 +638,33 @@ __device__ __forceinline__ void xw_forward(const float2* __restrict__ phys, floa
     const int k = lane + 32 * m;
     if (k < Mx) {
       float2* d = dst + (size_t)k * mstride;
-      d[0] = make_float2(hs * (Zk.x + Zm.x), hs * (Zk.y - Zm.y));
-      if (two) d[1] = make_float2(hs * (Zk.y + Zm.y), hs * (Zm.x - Zk.x));
+      const float2 A = make_float2(hs * (Zk.x + Zm.x), hs * (Zk.y - Zm.y));
+      const float2 B = make_float2(hs * (Zk.y + Zm.y), hs * (Zm.x - Zk.x));
+      if (two && (reinterpret_cast<uintptr_t>(d) & 15) == 0) {
+        *reinterpret_cast<float4*>(d) = make_float4(A.x, A.y, B.x, B.y);
+      } else {
+        d[0] = A;
+        if (two) d[1] = B;
+      }
     }
   }
 }
 
-// One item (z rows 2 bx, 2 bx + 1 at y = by) with 8 warps: warps 0..6 the backward lines, then
+// Item j of row y: the z rows it packs.  Rows pair so that the pair's offset y Nz + z0 is even
+// (16-byte aligned pairs when the field's base is): where y Nz is odd, row 0 stands alone and
+// the pairs are (1, 2), (3, 4), ...; otherwise (0, 1), (2, 3), ...  Either way (Nz + 1) / 2
+// items per y.
+__device__ __forceinline__ void xw_item(int j, int y, int Nz, int* z0, bool* two) {
+  if (((long long)y * Nz & 1) == 0) {
+    *z0 = 2 * j;
+    *two = 2 * j + 1 < Nz;
+  } else {
+    *z0 = j == 0 ? 0 : 2 * j - 1;
+    *two = j > 0 && 2 * j < Nz;
+  }
+}
+
+// One item (z rows of item bx at y = by) with 8 warps: warps 0..6 the backward lines, then
 // each warp a product line (9 over the 8 warps).  Shared memory: seven lines of P float2 and the
 // twiddle table.
 template <int Q>
@@ -647,8 +677,9 @@ __device__ __forceinline__ void xline_warp_body(const float2* __restrict__ in,
   float2* phys = xw_sm;
   float2* twl = xw_sm + 7 * P;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int z0 = 2 * bx;
-  const bool two = (z0 + 1 < Nz);
+  int z0;
+  bool two;
+  xw_item(bx, by, Nz, &z0, &two);
   const size_t base = (size_t)by * Nz + z0;
   const size_t mstride = (size_t)Py * Nz;
   for (int i = threadIdx.x; i < R * 32; i += blockDim.x) {
@@ -695,9 +726,11 @@ __global__ void __launch_bounds__(XWT, Q >= 8 ? 2 : 3)
   int t = blockIdx.x;
   if (t >= nitems) return;
   if (warp < 7) {
-    const int z0 = 2 * (t % nzp);
-    xw_backward<Q>(in, xp_sm, warp, Mx, (size_t)(t / nzp) * Nz + z0, mstride, z0 + 1 < Nz, fs,
-                   kxs, tw0, twl, lane0);
+    int z0;
+    bool two;
+    xw_item(t % nzp, t / nzp, Nz, &z0, &two);
+    xw_backward<Q>(in, xp_sm, warp, Mx, (size_t)(t / nzp) * Nz + z0, mstride, two, fs, kxs,
+                   tw0, twl, lane0);
   }
   __syncthreads();
   int b = 0;
@@ -709,9 +742,10 @@ __global__ void __launch_bounds__(XWT, Q >= 8 ? 2 : 3)
     const int lane = opaque_int(lane0);
     const float2* cur = xp_sm + b * 7 * P;
     float2* nxt = xp_sm + (b ^ 1) * 7 * P;
-    const int z0 = 2 * (t % nzp);
+    int z0;
+    bool two;
+    xw_item(t % nzp, t / nzp, Nz, &z0, &two);
     const size_t base = (size_t)(t / nzp) * Nz + z0;
-    const bool two = z0 + 1 < Nz;
     xw_forward<Q>(cur, out, warp, Mx, base, mstride, two, fs, kappa, scale, tw0, twl, lane);
     const int tn = t + gridDim.x;
     __syncwarp();   // ptxas moves no memory access across it: the next line's loads start here
@@ -719,9 +753,11 @@ __global__ void __launch_bounds__(XWT, Q >= 8 ? 2 : 3)
     if (warp == 7) {
       xw_forward<Q>(cur, out, 8, Mx, base, mstride, two, fs, kappa, scale, tw0, twl, lane2);
     } else if (tn < nitems) {
-      const int zn = 2 * (tn % nzp);
-      xw_backward<Q>(in, nxt, warp, Mx, (size_t)(tn / nzp) * Nz + zn, mstride, zn + 1 < Nz, fs,
-                     kxs, tw0, twl, lane2);
+      int zn;
+      bool twon;
+      xw_item(tn % nzp, tn / nzp, Nz, &zn, &twon);
+      xw_backward<Q>(in, nxt, warp, Mx, (size_t)(tn / nzp) * Nz + zn, mstride, twon, fs, kxs,
+                     tw0, twl, lane2);
     }
     __syncthreads();
     b ^= 1;
