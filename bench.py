@@ -61,31 +61,29 @@ TRAFFIC_MB = {
     ("channel_128x128x129", 0, "zsolve"): 93.5 + 8.9,
     ("channel_128x128x129", 1, "zsolve"): 93.5 + 8.9,
     ("channel_128x128x129", 2, "zsolve"): 93.5 + 8.9,
-    # 512 x 256 x 257 (full-size captures of the default bench command and of the FFT method
-    # and FP64 step on the same grid)
-    ("channel_512x256x257_mixed", 1, "cheb_bwd"): 1370.4 + 1219.1,
-    ("channel_512x256x257_mixed", 1, "zsolve"): 4723.2 + 3617.6,
-    ("channel_512x256x257_mixed", 1, "zbwd"): 1342.6 + 1427.2,
+    # 512 x 256 x 257 (full-size captures of the default bench command, its Chebyshev method
+    # trial included, and of the FP64 step on the same grid)
+    ("channel_512x256x257_mixed", 1, "zsolve"): 4747.8 + 3621.8,
+    ("channel_512x256x257_mixed", 1, "zbwd"): 1343.6 + 1427.6,
     ("channel_512x256x257_mixed", 0, "zsolve"): 4753.3 + 3623.4,
     ("channel_512x256x257_mixed", 0, "zbwd"): 1343.7 + 2096.8,
     ("channel_512x256x257_mixed", 0, "xline"): 2434.1 + 3591.5,
     ("channel_512x256x257_mixed", 0, "ybwd"): 1610.9 + 2393.1,
     # current step kernels (full-size captures of the default bench command's kernels with
     # --cheb tc, and of the 128^3 mixed tensor-core and float64 FFT-method steps)
-    ("channel_512x256x257_mixed", 1, "cheb_fwd"): 967.0 + 2368.5,
-    ("channel_512x256x257_mixed", 1, "cheb_bwd"): 1370.4 + 1219.1,
-    ("channel_512x256x257_mixed", 1, "zrhs_coef"): 3491.0 + 1965.3,
-    ("channel_512x256x257_mixed", 1, "zbwd_coef"): 1342.5 + 2296.4,
-    ("channel_512x256x257_mixed", 1, "xline"): 1242.4 + 1791.8,
-    ("channel_512x256x257_mixed", 1, "yfwd"): 1819.9 + 906.5,
-    ("channel_512x256x257_mixed", 1, "ybwd"): 805.6 + 1174.2,
+    ("channel_512x256x257_mixed", 1, "cheb_fwd"): 964.4 + 2390.7,
+    ("channel_512x256x257_mixed", 1, "cheb_bwd"): 1368.9 + 1220.4,
+    ("channel_512x256x257_mixed", 1, "zrhs_coef"): 3331.3 + 2004.2,
+    ("channel_512x256x257_mixed", 1, "zbwd_coef"): 1342.3 + 2287.4,
+    ("channel_512x256x257_mixed", 1, "xline"): 1783.4 + 2107.7,
+    ("channel_512x256x257_mixed", 1, "yfwd"): 1819.3 + 906.6,
+    ("channel_512x256x257_mixed", 1, "ybwd"): 805.6 + 1174.0,
     ("channel_128x128x129", 1, "cheb_fwd"): 60.6 + 63.3,
     ("channel_128x128x129", 1, "cheb_bwd"): 85.3 + 8.3,
     ("channel_128x128x129", 1, "zrhs_coef"): 218.3 + 80.1,
     ("channel_128x128x129", 0, "zbwd_coef"): 83.9 + 88.1,
     ("channel_128x128x129", 1, "zbwd_coef"): 83.9 + 88.1,
     ("channel_128x128x129", 2, "zbwd_coef"): 83.9 + 88.1,
-    ("channel_128x128x129", 1, "xline"): 77.6 + 62.7,
     ("channel_128x128x129", 1, "yfwd"): 114.2 + 32.6,
     ("channel_128x128x129", 1, "ybwd"): 42.0 + 27.9,
     ("channel_128x128x129", 0, "zrhs"): 218.3 + 73.3,

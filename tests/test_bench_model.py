@@ -95,7 +95,12 @@ L2_BYTES = 129e6
 # 512 x 256 x 257 part of it leaves L2 (1.2x / 1.3x the compulsory bytes, bound 1.5x).
 # The global-memory tau sweeps of long lines (N > 128) read and write each line once per sweep
 # and read the tabulated factors (5.2x, bound 6x).
-REREAD_BOUND = {("channel_512x256x257_mixed", 1, "cheb_fwd"): 1.5,
+# The persistent float32 x line deals items (pairs of z rows) round-robin to its CTAs; two
+# neighbouring items share each 32-byte sector of their rows, and CTAs that drift apart find the
+# other half gone from L2 (1.28x, bound 1.4x; contiguous runs per CTA keep it in L2 but scatter
+# the CTAs over DRAM pages and take twice as long).
+REREAD_BOUND = {("channel_512x256x257_mixed", 1, "xline"): 1.4,
+                ("channel_512x256x257_mixed", 1, "cheb_fwd"): 1.5,
                 ("channel_512x256x257_mixed", 1, "cheb_bwd"): 1.5,
                 ("channel_512x256x257_mixed", 1, "zsolve"): 6.0,
                 ("channel_512x256x257_mixed", 0, "zsolve"): 6.0}
