@@ -705,8 +705,11 @@ __device__ __forceinline__ int opaque_int(int v) {
 // with two buffers of seven lines.  A round holds 16 line tasks, two per warp: the nine forward
 // lines of item t (warp w line w, warp 7 also line 8) and the seven backward lines of the next
 // item (warps 0..6) into the other buffer, so no warp idles and the next item's loads overlap
-// the products' transforms; one barrier per round.  Per line the same arithmetic as
-// xline_warp_body.
+// the products' transforms; one barrier per round.  Round-robin keeps the items in flight on
+// all CTAs neighbours in memory (contiguous runs per CTA spread them over the whole field and
+// ran at half the speed), at the price of some sectors whose two halves, read by neighbouring
+// items on CTAs that have drifted apart, come from DRAM twice.  Per line the same arithmetic
+// as xline_warp_body.
 template <int Q>
 __global__ void __launch_bounds__(XWT, Q >= 8 ? 2 : 3)
     xline_warp_kernel(const float2* __restrict__ in, float2* __restrict__ out, int Mx, int Py,
